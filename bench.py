@@ -1,0 +1,339 @@
+"""Throughput of the multi-chain HMC sampler on one GB300 (or N, one process
+per GPU, each sampling its own replica of the posterior: chains are
+independent, so ranks share nothing on the data path; weak scaling).
+
+A step is one full sample_chain call (bootstrap, burn-in transitions with
+dual-averaging step-size adaptation, kept transitions with every kept state
+written to HBM) of the correlated-Gaussian workload: D = 256,
+P = A A^T / D + 0.1 I, 4096 chains from N(0, 1), 16 leapfrog steps,
+adaptation to accept 0.65, 1000 burn-in + 2000 kept transitions.
+Metric: leapfrog gradient evaluations per second (one chain's grad log p is
+one evaluation; bootstrap adds one per chain), plus min-ESS/s of the kept
+draws.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload corr_gauss|logreg|funnel|std_normal] [--plain]
+
+--impl reference times the float64 oracle (a deliberately plain CPU
+program, the only reference this method has) on the host cores, on a bounded
+sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 2 ** 20
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# nominal dense tensor ratio tf32 : bf16 (1.1 : 2.25 PFLOP/s)
+TF32_PER_BF16 = 1.1 / 2.25
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="corr_gauss",
+                    choices=["corr_gauss", "logreg", "funnel", "std_normal"])
+    ap.add_argument("--plain", action="store_true", help="one launch per op per leapfrog step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def make_problem(name):
+    from paper_2002_01184_gb300 import workloads
+    if name == "corr_gauss":
+        return workloads.corr_gauss(), "corr_gauss D=256 P=AA^T/D+0.1I C=4096 L=16 DA(0.65) B=1000 K=2000"
+    if name == "logreg":
+        return workloads.logreg(), "logreg N=20000 D=128 C=2048 L=10 DA(0.8) B=500 K=1000"
+    if name == "funnel":
+        p = workloads.funnel(dim=100, num_chains=4096)
+        return p, "funnel d=100 C=4096 L=10 DA(0.8) B=500 K=1000"
+    return workloads.std_normal(), "std_normal D=1 C=100 L=3 eps=1.5 B=300 K=100"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK), "fallback"
+
+
+def grad_flops_per_eval(p):
+    """Algorithmic flops of one chain's gradient (the dense products)."""
+    if p.kind == "corr_gauss":
+        return 2.0 * p.dim * p.dim
+    if p.kind == "logreg":
+        return 4.0 * p.n_data * p.dim
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed
+    region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The float64 oracle on the host cores, on a bounded sample."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    p, wl = make_problem(args.workload)
+    res = cpu_oracle_rate(p, args.cpu_seconds)
+    line = {"impl": "reference", "metric": "leapfrog grad-evals/s", "value": res["value"],
+            "unit": "grad-evals/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_transition"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl, "sample": res["sample"]},
+            "cpu_baseline": res,
+            "e2e": {"value": res["value"], "unit": "grad-evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_oracle_rate(p, seconds):
+    """Time the oracle's transitions on a prefix of the workload until about
+    `seconds` of CPU work; rate = chains x L x transitions / wall time."""
+    import numpy as np
+    from oracle import hmc as ohmc, targets as otargets
+    tgt = otargets.make(p.kind, **p.data())
+    x = p.x0.astype(np.float64)
+    lp, g = ohmc.bootstrap(x, tgt)
+    eps = p.step_size
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        r = ohmc.one_step(x, lp, g, eps, p.num_leapfrog, p.seed, n, tgt)
+        x, lp, g = r["x"], r["lp"], r["g"]
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or n >= p.num_burnin + p.num_results:
+            break
+    rate = p.num_chains * p.num_leapfrog * n / el
+    return {"value": rate, "unit": "grad-evals/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {n} transitions of the workload (all {p.num_chains} chains, "
+                      f"fixed step size), numpy float64 with BLAS on all host cores",
+            "ms_per_transition": 1000.0 * el / n}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2002_01184_gb300 import build as libbuild
+    if rank == 0:
+        libbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2002_01184_gb300 import diagnostics, hmc
+    from paper_2002_01184_gb300.sampler import Sampler
+
+    p, wl = make_problem(args.workload)
+    p.seed = p.seed + 1000 * rank          # each rank samples its own replica
+    impl = hmc.HMC_IMPL_PLAIN if args.plain else hmc.HMC_IMPL_FUSED
+    stream = torch.cuda.current_stream()
+    s = Sampler(p, impl=impl, stream=stream)
+    C, D, K, B = p.num_chains, p.dim, p.num_results, p.num_burnin
+    x0 = torch.as_tensor(p.x0).cuda()
+    x = torch.empty_like(x0)
+    samples = torch.empty((K, C, D), dtype=torch.float32, device="cuda")
+    eps = torch.empty(K, dtype=torch.float32, device="cuda")
+    acc = torch.empty((K, C), dtype=torch.uint8, device="cuda")
+
+    def step():
+        x.copy_(x0)
+        hmc.hmc_sample_chain(s.ctx, x, B, K, samples, eps, acc)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evals_per_step = C * p.num_leapfrog * (B + K) + C
+    clocks = ClockSampler(local)
+    clocks.start()
+    hmc.hmc_profile_dominant_kernel(s.ctx, 8)
+    launches0 = hmc.hmc_kernel_launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = hmc.hmc_kernel_launch_count() - launches0
+    prof = hmc.hmc_profile_read(s.ctx)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * evals_per_step * args.steps / (ms / 1000.0)
+
+    # min-ESS/s of the last step's kept draws (not timed)
+    ess = diagnostics.ess(samples, max_dims=64)
+    min_ess = float(ess.min())
+    min_ess_per_s = min_ess / (ms_per_step / 1000.0) * world
+
+    pk, src = peaks()
+    flops = grad_flops_per_eval(p)
+    roof = None
+    if prof["samples"]:
+        kernel_s = prof["avg_ms"] / 1000.0
+        if flops is not None and args.plain is False and False:
+            pass
+        if flops is not None:
+            # the SIMT products run on the FP32 pipes: alu roofline
+            achieved = flops * C / kernel_s / 1e12
+            sm_max = pk.get("sm_max_mhz", 2070.0)
+            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "target-gradient product (SIMT fp32)",
+                    "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                    "avg_launch_ms": prof["avg_ms"], "timed_launches": prof["samples"]}
+        else:
+            bytes_per_launch = 3 * 4.0 * C * D * 2  # x, g read + written (fused elementwise)
+            achieved = bytes_per_launch / kernel_s / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                    "kernel": "fused elementwise transition", "peak_source": src,
+                    "avg_launch_ms": prof["avg_ms"], "timed_launches": prof["samples"]}
+
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty((C, D), dtype=torch.float32, pin_memory=True)
+        sh = torch.empty((K, C, D), dtype=torch.float32, pin_memory=True)
+        eh = torch.empty(K, dtype=torch.float32, pin_memory=True)
+        ah = torch.empty((K, C), dtype=torch.uint8, pin_memory=True)
+        x0h = torch.as_tensor(p.x0)
+        xh.copy_(x0h)
+        hmc.hmc_sample_chain_host(s.ctx, xh, B, K, sh, eh, ah)   # warm the staging buffers
+        n_e2e = max(1, min(args.steps, 2))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            xh.copy_(x0h)
+            hmc.hmc_sample_chain_host(s.ctx, xh, B, K, sh, eh, ah)
+        el = (time.perf_counter() - t0) / n_e2e
+        if world > 1:
+            t = torch.tensor([el], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * evals_per_step / el, "unit": "grad-evals/s",
+               "h2d_bytes_per_step": C * D * 4,
+               "d2h_bytes_per_step": (K * C * D + C * D) * 4 + K * 4 + K * C,
+               "ms_per_step": 1000.0 * el}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(p, args.cpu_seconds)
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        line = {
+            "metric": "leapfrog grad-evals/s", "value": value, "unit": "grad-evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl, "impl": "plain" if args.plain else "fused",
+                       "chains": C, "dim": D, "l2": "each step writes its 8.4 GB kept-sample "
+                       "buffer (> 129 MB L2), which flushes L2 between steps",
+                       "parallelism": f"replicas x{world}"},
+            "min_ess_per_s": min_ess_per_s, "min_ess": min_ess,
+            "final_step_size": float(eps[-1].item()) if K else None,
+            "accept_rate": float(acc.float().mean().item()) if K else None,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * libhmc: vectorised multi-chain Hamiltonian Monte Carlo on one GB300 GPU.
+ *
+ * The method is the HMC transition kernel and sample_chain driver of
+ * "tfp.mcmc: Modern Markov Chain Monte Carlo Tools Built for Modern Hardware"
+ * (Lao et al., 2020): thousands of independent chains advance in lockstep
+ * (Section 3, "Pervasive Data Parallelism"); each transition draws one
+ * momentum per state variable per chain, runs a fixed number of leapfrog steps
+ * with the step size broadcast over the state, and accepts or rejects every
+ * chain by Metropolis-Hastings with a per-chain select (Section 3.1).  A
+ * transition consumes and produces (state, kernel results) of fixed structure,
+ * and the kernel results cache the target log-prob and gradient of the
+ * accepted state (Section 4.1, one_step / bootstrap_results).  The driver runs
+ * burn-in transitions whose states are not stored, then kept ones, and traces
+ * kernel-result fields (Section 4.2).  Step-size adaptation during burn-in
+ * (Section 4.1, the step-size adaptation wrapper) uses dual averaging
+ * (Hoffman and Gelman 2014, Algorithm 5).
+ *
+ * Conventions for every call:
+ *   - Pointers named "device" are CUDA device pointers owned by the caller
+ *     unless stated otherwise.  State arrays are row-major [chains x dim]
+ *     float32 (chain c's state is x[c*dim .. c*dim+dim-1]).
+ *   - All work is enqueued asynchronously on the stream given to hmc_create
+ *     (or to the call); nothing synchronises unless stated.
+ *   - Every call returns an hmc_status; nothing throws or aborts.  The text of
+ *     the last error of a context is available from hmc_last_error.
+ *   - Results depend only on (seed, chain index + chain_offset, transition
+ *     index) and the chain's own state: never on the number of chains or on
+ *     the other chains in the batch (Section 3's batch semantics).
+ */
+#ifndef HMC_H_
+#define HMC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HMC_OK = 0,
+  HMC_E_INVALID = 1,      /* bad argument: NULL pointer, size, step size, id */
+  HMC_E_OOM = 2,          /* device workspace allocation failed */
+  HMC_E_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+  HMC_E_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+  HMC_E_UNSUPPORTED = 5   /* valid request this build does not implement */
+} hmc_status;
+
+/* Target families.  Log-densities are up to an additive constant.
+ *   STD_NORMAL  log p = -|x|^2/2 (the worked example of Section 1, any dim)
+ *   CORR_GAUSS  log p = -x^T P x / 2, P symmetric positive definite [dim x dim]
+ *   LOGREG      Bayesian logistic regression, prior N(0, I):
+ *               log p = sum_i y_i z_i - softplus(z_i) - |x|^2/2, z = X x,
+ *               X [n_data x dim] row-major, y [n_data] in {0, 1}
+ *   FUNNEL      Neal's funnel, state (v, x_1..x_{dim-1}): v ~ N(0, 9),
+ *               x_i | v ~ N(0, e^v); dim >= 2 */
+typedef enum {
+  HMC_T_STD_NORMAL = 0,
+  HMC_T_CORR_GAUSS = 1,
+  HMC_T_LOGREG = 2,
+  HMC_T_FUNNEL = 3
+} hmc_target_id;
+
+/* Target description.  P, X, y are device pointers owned by the caller; they
+ * are read, never written, and must stay valid until the context that uses
+ * them is destroyed.  Unused pointers may be NULL. */
+typedef struct {
+  int32_t id;          /* hmc_target_id */
+  int32_t dim;         /* state dimension D >= 1 */
+  int64_t n_data;      /* LOGREG: rows of X; otherwise 0 */
+  const float* P;      /* CORR_GAUSS: [dim x dim] */
+  const float* X;      /* LOGREG: [n_data x dim] */
+  const float* y;      /* LOGREG: [n_data] */
+} hmc_target;
+
+typedef enum {
+  HMC_IMPL_FUSED = 0,  /* fused transition kernels (default) */
+  HMC_IMPL_PLAIN = 1   /* one kernel launch per operation per leapfrog step */
+} hmc_impl;
+
+/* Sampler configuration (the HamiltonianMonteCarlo constructor arguments of
+ * the Section 1 listing plus adaptation). */
+typedef struct {
+  int32_t num_leapfrog;     /* L >= 1 */
+  float step_size;          /* initial (or fixed) step size, finite, > 0 */
+  uint64_t seed;            /* Philox key */
+  int32_t adapt;            /* 0: fixed step size; 1: dual averaging */
+  float target_accept;      /* dual-averaging target in (0, 1) */
+  int64_t num_adapt_steps;  /* transitions t < num_adapt_steps adapt (>= 0) */
+  int32_t impl;             /* hmc_impl */
+  int64_t chain_offset;     /* chain c draws the random streams of chain
+                               c + chain_offset */
+} hmc_config;
+
+/* Kernel results of the last transition.  All pointers are device pointers
+ * owned by the context, valid until the next call on it or hmc_destroy. */
+typedef struct {
+  const float* target_log_prob;   /* [chains] log p of the current state */
+  const float* grad;              /* [chains x dim] its gradient */
+  const uint8_t* is_accepted;     /* [chains] 1 if the proposal was accepted */
+  const float* log_accept_ratio;  /* [chains] H_0 - H_L, -inf if non-finite */
+  const float* step_size;         /* [1] step size the NEXT transition uses */
+} hmc_kernel_results;
+
+typedef struct hmc_ctx hmc_ctx;
+
+/* Create a sampler context for `num_chains` chains of `target`, enqueuing on
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream).  Validates the
+ * arguments (HMC_E_INVALID) and allocates the context's device workspace
+ * (HMC_E_OOM); it does not touch the chain state.  On success *out owns the
+ * workspace until hmc_destroy.  Sections 3.1 and 4.1. */
+hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_config* config,
+                      void* cuda_stream, hmc_ctx** out);
+
+/* bootstrap_results (Section 4.1): evaluate log p and its gradient at x0
+ * ([chains x dim], device, read only) into the context's kernel results and
+ * reset the step size and the dual-averaging state to the configuration's. */
+hmc_status hmc_bootstrap(hmc_ctx* ctx, const float* x0);
+
+/* one_step (Sections 3.1, 4.1): advance every chain by one HMC transition
+ * with transition index t (which keys the random streams and, when adapting,
+ * decides whether this transition adapts).  x_inout [chains x dim] (device)
+ * must hold the state that the kernel results belong to (the one passed to
+ * hmc_bootstrap or returned by the previous step); it is overwritten with the
+ * next state.  If `out` is not NULL it receives the kernel results. */
+hmc_status hmc_step(hmc_ctx* ctx, float* x_inout, uint64_t t, hmc_kernel_results* out);
+
+/* sample_chain (Section 4.2): bootstrap at x_inout, run num_burnin + num_results
+ * transitions with t = 0, 1, ..., keep the state after each of the last
+ * num_results transitions, and leave the final state in x_inout.
+ *   samples_out     [num_results x chains x dim] device or NULL
+ *   trace_step_size [num_results] device or NULL: step size each kept
+ *                   transition used
+ *   trace_accept    [num_results x chains] device or NULL: is_accepted
+ * Both counts must be >= 0. */
+hmc_status hmc_sample_chain(hmc_ctx* ctx, float* x_inout, int64_t num_burnin, int64_t num_results,
+                            float* samples_out, float* trace_step_size, uint8_t* trace_accept);
+
+/* Same as hmc_sample_chain with every argument in HOST memory (x_inout,
+ * samples_out, trace buffers; pinned or pageable).  Copies the initial state
+ * to the device, samples, copies the results back and synchronises the
+ * context's stream before returning. */
+hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burnin,
+                                 int64_t num_results, float* samples_out,
+                                 float* trace_step_size, uint8_t* trace_accept);
+
+/* Copy the current dual-averaging state to host memory and synchronise:
+ * out[0] = step size of the next transition, out[1] = log eps_bar,
+ * out[2] = h_bar, out[3] = adaptation steps taken, out[4] = last transition's
+ * acceptance statistic (mean over chains of min(1, alpha)). */
+hmc_status hmc_read_adaptation(hmc_ctx* ctx, double out[5]);
+
+/* Measurement support (no counterpart in the paper): time one launch in
+ * every `sample_every` of the context's dominant kernel -- the fused
+ * transition kernel, or the target-gradient product(s) of the plain path --
+ * with CUDA events on the context's stream.  0 disables.  Synchronises the
+ * stream and resets the counters. */
+hmc_status hmc_profile_dominant_kernel(hmc_ctx* ctx, int32_t sample_every);
+
+/* Average duration (ms) of the timed launches since the last reset, how many
+ * were timed (at most 2048, the most recent ones) and how many dominant
+ * launches occurred.  Synchronises the context's stream. */
+hmc_status hmc_profile_read(hmc_ctx* ctx, double* avg_ms, uint64_t* samples, uint64_t* launches);
+
+/* Release the context's workspace.  NULL is accepted. */
+hmc_status hmc_destroy(hmc_ctx* ctx);
+
+/* Text of the last error on `ctx` ("" if none); with ctx == NULL, the last
+ * error of a call that had no context (e.g. a failed hmc_create).  The string
+ * is owned by the library and valid until the next call on the same context. */
+const char* hmc_last_error(const hmc_ctx* ctx);
+
+/* Bytes of device scratch that hmc_target_log_prob_and_grad needs for
+ * `num_chains` chains of `target` (0 for targets that need none; LOGREG needs
+ * the C x N residual matrix and split-K partial sums).  Returns 0 and sets
+ * *bytes on success, HMC_E_INVALID on a bad target or count. */
+hmc_status hmc_grad_workspace_bytes(const hmc_target* target, int64_t num_chains, uint64_t* bytes);
+
+/* Target log-prob and gradient for `num_chains` states x [chains x dim]
+ * (device) into lp [chains] and grad [chains x dim] (device, caller-owned),
+ * enqueued on `cuda_stream`.  This is the batched target evaluation of
+ * Section 3.1 ("list of vectors", one row per chain) and the adjoint used by
+ * the autograd binding: the vector-Jacobian product of log p with upstream
+ * weights w is w_c * grad[c].  `workspace` is caller-owned device scratch of
+ * at least hmc_grad_workspace_bytes bytes, 256-byte aligned (may be NULL when
+ * that size is 0).  Allocates nothing.  Returns HMC_E_INVALID on bad sizes,
+ * pointers or a too-small workspace. */
+hmc_status hmc_target_log_prob_and_grad(const hmc_target* target, int64_t num_chains,
+                                        const float* x, float* lp, float* grad,
+                                        void* workspace, uint64_t workspace_bytes,
+                                        void* cuda_stream);
+
+/* The counter-based generator behind every random draw (the paper names
+ * none; this is Philox4x32-10 of Salmon, Moraes, Dror and Shaw, SC'11):
+ * out[4i..4i+3] = Philox4x32-10(counters[4i..4i+3], key = (seed lo32,
+ * seed hi32)) for i < n.  counters and out are device arrays of 4n uint32.
+ * Exposed so that callers can check the stream bit for bit. */
+hmc_status hmc_philox4x32_10(const uint32_t* counters, int64_t n, uint64_t seed, uint32_t* out,
+                             void* cuda_stream);
+
+/* The momentum draw of one transition (Section 3.1: one independent N(0,1)
+ * momentum per state variable per chain): out [chains x dim] (device) for
+ * chains chain_offset .. chain_offset + num_chains - 1 at transition t. */
+hmc_status hmc_momentum(uint64_t seed, uint64_t t, int64_t num_chains, int32_t dim,
+                        int64_t chain_offset, float* out, void* cuda_stream);
+
+/* Number of kernels this library launched in the calling process so far
+ * (a host-side counter, for launch accounting). */
+uint64_t hmc_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMC_H_ */

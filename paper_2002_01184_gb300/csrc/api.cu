@@ -1,0 +1,427 @@
+// C ABI of libhmc (include/hmc.h): argument checking, the context's device
+// workspace, and the sample_chain driver (Section 4.2) that enqueues one
+// transition per step on the context's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hmc_device.cuh"
+#include "hmc_internal.h"
+
+using hmc::DAState;
+using hmc::PlainBuffers;
+using hmc::StepArgs;
+
+struct hmc_ctx {
+  hmc_target target{};
+  int64_t C = 0;
+  hmc_config cfg{};
+  cudaStream_t stream = nullptr;
+  // kernel results (Section 4.1): cached log-prob and gradient of the state
+  float* lp = nullptr;
+  float* g = nullptr;
+  uint8_t* is_accepted = nullptr;
+  float* log_accept = nullptr;
+  DAState* da = nullptr;
+  double* partials = nullptr;
+  PlainBuffers plain{};
+  void* grad_ws = nullptr;
+  size_t grad_ws_bytes = 0;
+  bool bootstrapped = false;
+  // device staging for hmc_sample_chain_host, grown on demand
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  std::vector<void*> allocations;
+  hmc::KernelTimer timer;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_global_err;
+
+hmc_status fail(hmc_ctx* ctx, hmc_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  else g_global_err = msg;
+  return st;
+}
+
+hmc_status cuda_fail(hmc_ctx* ctx, cudaError_t e, const char* where) {
+  return fail(ctx, HMC_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool valid_target(const hmc_target* t, int64_t C, std::string* why) {
+  if (!t) { *why = "target is NULL"; return false; }
+  if (t->dim < 1) { *why = "target dim must be >= 1"; return false; }
+  if (C < 1) { *why = "num_chains must be >= 1"; return false; }
+  if (C > (1ll << 30)) { *why = "num_chains must be <= 2^30"; return false; }
+  if (C * static_cast<int64_t>(t->dim) > (1ll << 40)) { *why = "chains x dim too large"; return false; }
+  switch (t->id) {
+    case HMC_T_STD_NORMAL: return true;
+    case HMC_T_FUNNEL:
+      if (t->dim < 2) { *why = "funnel needs dim >= 2"; return false; }
+      return true;
+    case HMC_T_CORR_GAUSS:
+      if (!t->P) { *why = "CORR_GAUSS needs P"; return false; }
+      return true;
+    case HMC_T_LOGREG:
+      if (!t->X || !t->y) { *why = "LOGREG needs X and y"; return false; }
+      if (t->n_data < 1 || t->n_data > (1ll << 31) - 1) { *why = "LOGREG n_data out of range"; return false; }
+      if (C * t->n_data > (1ll << 40)) { *why = "chains x n_data too large"; return false; }
+      return true;
+    default:
+      *why = "unknown target id";
+      return false;
+  }
+}
+
+bool valid_config(const hmc_config* c, int64_t C, std::string* why) {
+  if (!c) { *why = "config is NULL"; return false; }
+  if (c->num_leapfrog < 1) { *why = "num_leapfrog must be >= 1"; return false; }
+  if (!std::isfinite(c->step_size) || !(c->step_size > 0.f)) {
+    *why = "step_size must be finite and > 0";
+    return false;
+  }
+  if (c->adapt != 0 && c->adapt != 1) { *why = "adapt must be 0 or 1"; return false; }
+  if (c->adapt && !(c->target_accept > 0.f && c->target_accept < 1.f)) {
+    *why = "target_accept must be in (0, 1)";
+    return false;
+  }
+  if (c->num_adapt_steps < 0) { *why = "num_adapt_steps must be >= 0"; return false; }
+  if (c->impl != HMC_IMPL_FUSED && c->impl != HMC_IMPL_PLAIN) { *why = "unknown impl"; return false; }
+  if (c->chain_offset < 0 || c->chain_offset + C > (1ll << 32)) {
+    *why = "chain_offset + num_chains must fit in 32 bits";
+    return false;
+  }
+  return true;
+}
+
+template <typename T>
+cudaError_t ctx_alloc(hmc_ctx* ctx, T** p, size_t count) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, std::max<size_t>(count * sizeof(T), 16));
+  if (e == cudaSuccess) {
+    ctx->allocations.push_back(v);
+    *p = static_cast<T*>(v);
+  }
+  return e;
+}
+
+void release(hmc_ctx* ctx) {
+  for (void* p : ctx->allocations) cudaFree(p);
+  ctx->allocations.clear();
+  if (ctx->stage) cudaFree(ctx->stage);
+  ctx->stage = nullptr;
+}
+
+bool uses_fused_elementwise(const hmc_ctx* ctx) {
+  return ctx->cfg.impl == HMC_IMPL_FUSED &&
+         (ctx->target.id == HMC_T_STD_NORMAL || ctx->target.id == HMC_T_FUNNEL) &&
+         ctx->target.dim <= hmc::kFusedElementwiseMaxDim;
+}
+
+StepArgs make_args(hmc_ctx* ctx, float* x, uint64_t t) {
+  StepArgs a{};
+  a.C = static_cast<int>(ctx->C);
+  a.D = ctx->target.dim;
+  a.L = ctx->cfg.num_leapfrog;
+  a.seed = ctx->cfg.seed;
+  a.t = static_cast<uint32_t>(t);
+  a.t_full = static_cast<long long>(t);
+  a.chain_offset = static_cast<uint32_t>(ctx->cfg.chain_offset);
+  a.x = x;
+  a.lp = ctx->lp;
+  a.g = ctx->g;
+  a.da = ctx->da;
+  a.partials = ctx->partials;
+  a.is_accepted = ctx->is_accepted;
+  a.log_accept = ctx->log_accept;
+  return a;
+}
+
+cudaError_t enqueue_transition(hmc_ctx* ctx, const StepArgs& a) {
+  if (uses_fused_elementwise(ctx))
+    return hmc::launch_fused_elementwise(ctx->target.id, a, ctx->stream, &ctx->timer);
+  return hmc::launch_plain_transition(ctx->target, a, ctx->plain, ctx->grad_ws, ctx->stream,
+                                      &ctx->timer);
+}
+
+hmc_status bootstrap(hmc_ctx* ctx, const float* x0) {
+  cudaError_t e = hmc::launch_grad(ctx->target, ctx->C, x0, ctx->lp, ctx->g, ctx->grad_ws, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "bootstrap gradient");
+  e = hmc::launch_da_init(ctx->da, ctx->cfg.step_size, ctx->cfg.adapt, ctx->cfg.target_accept,
+                          ctx->cfg.adapt ? ctx->cfg.num_adapt_steps : 0, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "dual-averaging init");
+  ctx->bootstrapped = true;
+  return HMC_OK;
+}
+
+hmc_status run_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* samples, float* trace_eps,
+                     uint8_t* trace_acc) {
+  hmc_status st = bootstrap(ctx, x);
+  if (st != HMC_OK) return st;
+  const int64_t CD = ctx->C * ctx->target.dim;
+  for (int64_t t = 0; t < B + K; ++t) {
+    StepArgs a = make_args(ctx, x, static_cast<uint64_t>(t));
+    const int64_t k = t - B;
+    if (k >= 0) {
+      a.sample_out = samples ? samples + k * CD : nullptr;
+      a.trace_acc = trace_acc ? trace_acc + k * ctx->C : nullptr;
+      a.trace_eps = trace_eps ? trace_eps + k : nullptr;
+    }
+    cudaError_t e = enqueue_transition(ctx, a);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "transition launch");
+  }
+  return HMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_config* config,
+                      void* cuda_stream, hmc_ctx** out) {
+  std::string why;
+  if (!out) return fail(nullptr, HMC_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!valid_target(target, num_chains, &why)) return fail(nullptr, HMC_E_INVALID, why);
+  if (!valid_config(config, num_chains, &why)) return fail(nullptr, HMC_E_INVALID, why);
+  hmc_ctx* ctx = new (std::nothrow) hmc_ctx();
+  if (!ctx) return fail(nullptr, HMC_E_OOM, "host allocation failed");
+  ctx->target = *target;
+  ctx->C = num_chains;
+  ctx->cfg = *config;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  const size_t C = static_cast<size_t>(num_chains), D = static_cast<size_t>(target->dim);
+  cudaError_t e = cudaSuccess;
+  const unsigned nblk = hmc::accept_blocks(static_cast<int>(num_chains));
+  if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->lp, C);
+  if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->g, C * D);
+  if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->is_accepted, C);
+  if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->log_accept, C);
+  if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->da, 1);
+  if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->partials, nblk);
+  if (e == cudaSuccess && !uses_fused_elementwise(ctx)) {
+    e = ctx_alloc(ctx, &ctx->plain.xp, C * D);
+    if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.gp, C * D);
+    if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.p, C * D);
+    if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.lpp, C);
+    if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.h0, C);
+  }
+  ctx->grad_ws_bytes = hmc::grad_workspace_bytes(*target, num_chains);
+  if (e == cudaSuccess && ctx->grad_ws_bytes) {
+    char* w = nullptr;
+    e = ctx_alloc(ctx, &w, ctx->grad_ws_bytes);
+    ctx->grad_ws = w;
+  }
+  if (e == cudaSuccess) {
+    // zero the arrival counter so the first transition's grid reduction works
+    // even before hmc_bootstrap re-initialises the state
+    e = cudaMemsetAsync(ctx->da, 0, sizeof(DAState), ctx->stream);
+  }
+  if (e != cudaSuccess) {
+    const bool oom = e == cudaErrorMemoryAllocation;
+    cudaGetLastError();
+    release(ctx);
+    delete ctx;
+    return fail(nullptr, oom ? HMC_E_OOM : HMC_E_CUDA,
+                std::string("workspace allocation: ") + cudaGetErrorString(e));
+  }
+  *out = ctx;
+  return HMC_OK;
+}
+
+hmc_status hmc_bootstrap(hmc_ctx* ctx, const float* x0) {
+  if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
+  if (!x0) return fail(ctx, HMC_E_INVALID, "x0 is NULL");
+  return bootstrap(ctx, x0);
+}
+
+hmc_status hmc_step(hmc_ctx* ctx, float* x_inout, uint64_t t, hmc_kernel_results* out) {
+  if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
+  if (!x_inout) return fail(ctx, HMC_E_INVALID, "x_inout is NULL");
+  if (!ctx->bootstrapped) return fail(ctx, HMC_E_INVALID, "hmc_bootstrap must precede hmc_step");
+  if (t > std::numeric_limits<uint32_t>::max())
+    return fail(ctx, HMC_E_INVALID, "transition index must fit in 32 bits");
+  StepArgs a = make_args(ctx, x_inout, t);
+  cudaError_t e = enqueue_transition(ctx, a);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "transition launch");
+  if (out) {
+    out->target_log_prob = ctx->lp;
+    out->grad = ctx->g;
+    out->is_accepted = ctx->is_accepted;
+    out->log_accept_ratio = ctx->log_accept;
+    out->step_size = &ctx->da->eps;
+  }
+  return HMC_OK;
+}
+
+hmc_status hmc_sample_chain(hmc_ctx* ctx, float* x_inout, int64_t num_burnin, int64_t num_results,
+                            float* samples_out, float* trace_step_size, uint8_t* trace_accept) {
+  if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
+  if (!x_inout) return fail(ctx, HMC_E_INVALID, "x_inout is NULL");
+  if (num_burnin < 0 || num_results < 0) return fail(ctx, HMC_E_INVALID, "negative step count");
+  if (num_burnin + num_results > static_cast<int64_t>(std::numeric_limits<uint32_t>::max()))
+    return fail(ctx, HMC_E_INVALID, "too many transitions (transition index is 32-bit)");
+  return run_chain(ctx, x_inout, num_burnin, num_results, samples_out, trace_step_size, trace_accept);
+}
+
+hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burnin,
+                                 int64_t num_results, float* samples_out, float* trace_step_size,
+                                 uint8_t* trace_accept) {
+  if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
+  if (!x_inout) return fail(ctx, HMC_E_INVALID, "x_inout is NULL");
+  if (num_burnin < 0 || num_results < 0) return fail(ctx, HMC_E_INVALID, "negative step count");
+  if (num_burnin + num_results > static_cast<int64_t>(std::numeric_limits<uint32_t>::max()))
+    return fail(ctx, HMC_E_INVALID, "too many transitions (transition index is 32-bit)");
+  const size_t CD = static_cast<size_t>(ctx->C) * ctx->target.dim;
+  const size_t K = static_cast<size_t>(num_results);
+  auto a256 = [](size_t b) { return (b + 255) & ~static_cast<size_t>(255); };
+  const size_t off_s = a256(CD * sizeof(float));
+  const size_t off_e = off_s + (samples_out ? a256(K * CD * sizeof(float)) : 0);
+  const size_t off_a = off_e + (trace_step_size ? a256(K * sizeof(float)) : 0);
+  const size_t total = off_a + (trace_accept ? a256(K * ctx->C) : 0);
+  if (total > ctx->stage_bytes) {
+    if (ctx->stage) cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->stage, total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, e == cudaErrorMemoryAllocation ? HMC_E_OOM : HMC_E_CUDA,
+                  std::string("staging allocation: ") + cudaGetErrorString(e));
+    }
+    ctx->stage_bytes = total;
+  }
+  char* base = static_cast<char*>(ctx->stage);
+  float* dx = reinterpret_cast<float*>(base);
+  float* ds = samples_out ? reinterpret_cast<float*>(base + off_s) : nullptr;
+  float* de = trace_step_size ? reinterpret_cast<float*>(base + off_e) : nullptr;
+  uint8_t* dacc = trace_accept ? reinterpret_cast<uint8_t*>(base + off_a) : nullptr;
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaMemcpyAsync(dx, x_inout, CD * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "state upload");
+  hmc_status st = run_chain(ctx, dx, num_burnin, num_results, ds, de, dacc);
+  if (st != HMC_OK) return st;
+  e = cudaMemcpyAsync(x_inout, dx, CD * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && ds)
+    e = cudaMemcpyAsync(samples_out, ds, K * CD * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && de)
+    e = cudaMemcpyAsync(trace_step_size, de, K * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && dacc)
+    e = cudaMemcpyAsync(trace_accept, dacc, K * ctx->C, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "result download");
+  return HMC_OK;
+}
+
+hmc_status hmc_read_adaptation(hmc_ctx* ctx, double out[5]) {
+  if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
+  if (!out) return fail(ctx, HMC_E_INVALID, "out is NULL");
+  DAState h{};
+  cudaError_t e = cudaMemcpyAsync(&h, ctx->da, sizeof(DAState), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "read adaptation state");
+  out[0] = static_cast<double>(h.eps);
+  out[1] = h.log_eps_bar;
+  out[2] = h.h_bar;
+  out[3] = static_cast<double>(h.m);
+  out[4] = h.last_stat;
+  return HMC_OK;
+}
+
+hmc_status hmc_profile_dominant_kernel(hmc_ctx* ctx, int32_t sample_every) {
+  if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
+  if (sample_every < 0) return fail(ctx, HMC_E_INVALID, "sample_every must be >= 0");
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "profile reset");
+  ctx->timer.every = sample_every;
+  ctx->timer.seen = 0;
+  ctx->timer.recorded = 0;
+  return HMC_OK;
+}
+
+hmc_status hmc_profile_read(hmc_ctx* ctx, double* avg_ms, uint64_t* samples, uint64_t* launches) {
+  if (!ctx || !avg_ms || !samples || !launches) return fail(ctx, HMC_E_INVALID, "NULL argument");
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "profile read");
+  const uint64_t n = std::min<uint64_t>(ctx->timer.recorded, hmc::KernelTimer::kPairs);
+  double total = 0.0;
+  for (uint64_t k = 0; k < n; ++k) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, ctx->timer.ev[2 * k], ctx->timer.ev[2 * k + 1]);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "event elapsed time");
+    total += ms;
+  }
+  *avg_ms = n ? total / static_cast<double>(n) : 0.0;
+  *samples = n;
+  *launches = ctx->timer.seen;
+  return HMC_OK;
+}
+
+hmc_status hmc_destroy(hmc_ctx* ctx) {
+  if (!ctx) return HMC_OK;
+  cudaStreamSynchronize(ctx->stream);
+  ctx->timer.destroy();
+  release(ctx);
+  delete ctx;
+  return HMC_OK;
+}
+
+const char* hmc_last_error(const hmc_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_global_err.c_str();
+}
+
+hmc_status hmc_grad_workspace_bytes(const hmc_target* target, int64_t num_chains, uint64_t* bytes) {
+  std::string why;
+  if (!bytes) return fail(nullptr, HMC_E_INVALID, "bytes is NULL");
+  if (!valid_target(target, num_chains, &why)) return fail(nullptr, HMC_E_INVALID, why);
+  *bytes = hmc::grad_workspace_bytes(*target, num_chains);
+  return HMC_OK;
+}
+
+hmc_status hmc_target_log_prob_and_grad(const hmc_target* target, int64_t num_chains,
+                                        const float* x, float* lp, float* grad, void* workspace,
+                                        uint64_t workspace_bytes, void* cuda_stream) {
+  std::string why;
+  if (!valid_target(target, num_chains, &why)) return fail(nullptr, HMC_E_INVALID, why);
+  if (!x || !lp || !grad) return fail(nullptr, HMC_E_INVALID, "x, lp and grad must be non-NULL");
+  const size_t need = hmc::grad_workspace_bytes(*target, num_chains);
+  if (need > workspace_bytes || (need && !workspace))
+    return fail(nullptr, HMC_E_INVALID, "workspace smaller than hmc_grad_workspace_bytes");
+  if (need && (reinterpret_cast<uintptr_t>(workspace) & 255u))
+    return fail(nullptr, HMC_E_INVALID, "workspace must be 256-byte aligned");
+  cudaError_t e = hmc::launch_grad(*target, num_chains, x, lp, grad, workspace,
+                                   static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "gradient launch");
+  return HMC_OK;
+}
+
+hmc_status hmc_philox4x32_10(const uint32_t* counters, int64_t n, uint64_t seed, uint32_t* out,
+                             void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!counters || !out)))
+    return fail(nullptr, HMC_E_INVALID, "bad counters/out/n");
+  cudaError_t e = hmc::launch_philox(counters, n, seed, out, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "philox launch");
+  return HMC_OK;
+}
+
+hmc_status hmc_momentum(uint64_t seed, uint64_t t, int64_t num_chains, int32_t dim,
+                        int64_t chain_offset, float* out, void* cuda_stream) {
+  if (num_chains < 1 || num_chains > (1ll << 30) || dim < 1 || !out || chain_offset < 0 ||
+      chain_offset + num_chains > (1ll << 32) || t > std::numeric_limits<uint32_t>::max())
+    return fail(nullptr, HMC_E_INVALID, "bad momentum arguments");
+  cudaError_t e = hmc::launch_momentum(seed, static_cast<uint32_t>(t), static_cast<int>(num_chains),
+                                       dim, static_cast<uint32_t>(chain_offset), out,
+                                       static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "momentum launch");
+  return HMC_OK;
+}
+
+uint64_t hmc_kernel_launch_count(void) { return hmc::g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+// Device-side building blocks shared by the CUDA kernels of libhmc:
+// the counter-based generator, Box-Muller, warp reductions and the
+// dual-averaging state.  Host code never includes the kernels' arithmetic
+// from anywhere else.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hmc {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11).  The paper draws "one
+// independent momentum per state variable per chain" (Section 3.1) but names
+// no generator; a counter-based one needs no state in HBM and makes every
+// draw a pure function of (seed, chain, transition, stream tag).
+//   key     = (seed lo32, seed hi32)
+//   counter = (block j, chain c, transition t, tag s)
+//   tag 0 -> momentum, words 4j..4j+3 feed state dims 4j..4j+3
+//   tag 1 -> Metropolis-Hastings uniform (word 0 of block 0)
+// ---------------------------------------------------------------------------
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+constexpr uint32_t kTagMomentum = 0u;
+constexpr uint32_t kTagAccept = 1u;
+
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x);
+    const uint32_t lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z);
+    const uint32_t lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += kPhiloxW0;
+    k1 += kPhiloxW1;
+  }
+  return c;
+}
+
+// (w + 1/2) * 2^-32 in float32: strictly positive, at most 1.
+__device__ __forceinline__ float word_to_uniform(uint32_t w) {
+  return fmaf(static_cast<float>(w), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+}
+
+// log((w + 1/2) 2^-32) to float32 relative accuracy for every word: below
+// 1/2 the uniform itself is accurate; above, 1 - u = (~w + 1/2) 2^-32 is
+// formed exactly from the complement and log1p avoids the cancellation that
+// rounding u to float32 would cause next to 1.
+__device__ __forceinline__ float log_word_uniform(uint32_t w) {
+  if (w < 0x80000000u) return logf(word_to_uniform(w));
+  return log1pf(-word_to_uniform(~w));
+}
+
+// Box-Muller: r = sqrt(-2 log u_a), (r cos 2 pi u_b, r sin 2 pi u_b).
+__device__ __forceinline__ float2 box_muller(uint32_t wa, uint32_t wb) {
+  const float r = sqrtf(-2.0f * log_word_uniform(wa));
+  float s, c;
+  sincospif(2.0f * word_to_uniform(wb), &s, &c);
+  return make_float2(r * c, r * s);
+}
+
+// Four normals for state dims 4j..4j+3 of chain `chain` at transition t.
+__device__ __forceinline__ float4 momentum4(uint64_t seed, uint32_t j, uint32_t chain, uint32_t t) {
+  const uint4 w = philox(make_uint4(j, chain, t, kTagMomentum),
+                         static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+  const float2 a = box_muller(w.x, w.y);
+  const float2 b = box_muller(w.z, w.w);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
+__device__ __forceinline__ float accept_log_uniform(uint64_t seed, uint32_t chain, uint32_t t) {
+  const uint4 w = philox(make_uint4(0u, chain, t, kTagAccept),
+                         static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+  return log_word_uniform(w.x);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// min(1, exp(log_alpha)); a non-finite ratio counts as 0 (a divergence).
+__device__ __forceinline__ float accept_prob(float log_alpha) {
+  return isfinite(log_alpha) ? expf(fminf(log_alpha, 0.0f)) : 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// Dual averaging (Hoffman and Gelman 2014, Section 3.2.1 / Algorithm 5), one
+// step size per posterior, updated once per burn-in transition from the mean
+// over chains of min(1, alpha).  Lives in device memory so that a captured
+// sampling loop never returns to the host.
+// ---------------------------------------------------------------------------
+struct DAState {
+  double log_eps;       // step size of the next transition (log)
+  double log_eps_bar;   // running average, frozen step size after adaptation
+  double h_bar;         // running mean of (delta - alpha)
+  double mu;            // shrinkage point log(10 eps0)
+  double delta;         // target acceptance
+  double last_stat;     // statistic of the last transition (diagnostic)
+  long long m;          // adaptation steps taken
+  long long num_adapt;  // transitions with t < num_adapt adapt
+  float eps;            // float32 copy of exp(log_eps) read by the kernels
+  int adapt;            // 0: fixed step size
+  unsigned int arrive;  // blocks of the current transition that finished
+  unsigned int pad;
+};
+
+constexpr double kDAGamma = 0.05;
+constexpr double kDAT0 = 10.0;
+constexpr double kDAKappa = 0.75;
+
+// Apply one adaptation step with statistic `alpha` after transition t.
+__device__ __forceinline__ void da_update(DAState* s, double alpha, long long t) {
+  s->last_stat = alpha;
+  if (!s->adapt || t >= s->num_adapt) return;
+  s->m += 1;
+  const double m = static_cast<double>(s->m);
+  const double w = 1.0 / (m + kDAT0);
+  s->h_bar = (1.0 - w) * s->h_bar + w * (s->delta - alpha);
+  s->log_eps = s->mu - sqrt(m) / kDAGamma * s->h_bar;
+  const double eta = pow(m, -kDAKappa);
+  s->log_eps_bar = eta * s->log_eps + (1.0 - eta) * s->log_eps_bar;
+  // after the last adaptation step the step size freezes at eps_bar
+  const double next = (t + 1 >= s->num_adapt) ? s->log_eps_bar : s->log_eps;
+  s->eps = static_cast<float>(exp(next));
+}
+
+// Deterministic grid-wide reduction of per-block partial sums followed by the
+// dual-averaging update: every block stores its partial, the last block to
+// arrive sums all partials in block order (so the result does not depend on
+// arrival order), updates the state and re-arms the counter.
+__device__ __forceinline__ void block_partial_then_da(DAState* s, double* partials,
+                                                      double block_sum, int num_chains,
+                                                      long long t) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = block_sum;
+    __threadfence();
+    const unsigned int prev = atomicAdd(&s->arrive, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double acc = 0.0;
+  if (threadIdx.x < 32) {
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += 32)
+      acc += static_cast<volatile double*>(partials)[b];
+    acc = warp_sum_d(acc);
+    if (threadIdx.x == 0) {
+      da_update(s, acc / static_cast<double>(num_chains), t);
+      s->arrive = 0u;
+      __threadfence();
+    }
+  }
+}
+
+}  // namespace hmc

@@ -1,0 +1,109 @@
+// Host-side interfaces between the translation units of libhmc.
+#pragma once
+#include <atomic>
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hmc.h"
+
+namespace hmc {
+
+// Kernels launched by this library in this process (host-side count).
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// CUDA-event timing of one launch in `every` of the sampler's dominant kernel,
+// on the stream it runs on.  A ring of event pairs; reading sums the pairs
+// recorded since the last reset.
+struct KernelTimer {
+  static constexpr size_t kPairs = 2048;
+  int every = 0;                 // 0: off
+  uint64_t seen = 0;             // dominant launches since reset
+  uint64_t recorded = 0;         // pairs recorded since reset
+  cudaEvent_t ev[2 * kPairs] = {};
+  bool pending = false;
+  bool begin(cudaStream_t s) {
+    pending = false;
+    if (every <= 0) return false;
+    if (seen++ % static_cast<uint64_t>(every) != 0) return false;
+    const size_t k = recorded % kPairs;
+    if (!ev[2 * k]) {
+      if (cudaEventCreate(&ev[2 * k]) != cudaSuccess) return false;
+      if (cudaEventCreate(&ev[2 * k + 1]) != cudaSuccess) return false;
+    }
+    pending = cudaEventRecord(ev[2 * k], s) == cudaSuccess;
+    return pending;
+  }
+  void end(cudaStream_t s) {
+    if (!pending) return;
+    cudaEventRecord(ev[2 * (recorded % kPairs) + 1], s);
+    ++recorded;
+    pending = false;
+  }
+  void destroy() {
+    for (auto& e : ev)
+      if (e) { cudaEventDestroy(e); e = nullptr; }
+  }
+};
+
+// Bytes of scratch the batched gradient of `t` needs for C chains.
+size_t grad_workspace_bytes(const hmc_target& t, int64_t C);
+
+// log p and gradient of x [C x D] into lp [C], g [C x D] with the plain
+// (one GEMM per product) kernels; `ws` holds grad_workspace_bytes bytes.
+cudaError_t launch_grad(const hmc_target& t, int64_t C, const float* x, float* lp, float* g,
+                        void* ws, cudaStream_t s, KernelTimer* timer = nullptr);
+
+}  // namespace hmc
+
+namespace hmc {
+
+struct DAState;
+
+// Arguments shared by the transition kernels.  x, lp, g are the current state
+// and its cached log-prob / gradient (updated in place on acceptance).
+struct StepArgs {
+  int C, D, L;
+  uint64_t seed;
+  uint32_t t;             // transition index (low 32 bits key the streams)
+  long long t_full;       // full transition index (decides adaptation)
+  uint32_t chain_offset;
+  float* x;
+  float* lp;
+  float* g;
+  DAState* da;
+  double* partials;       // one double per block of the accept kernel
+  uint8_t* is_accepted;   // [C]
+  float* log_accept;      // [C]
+  float* sample_out;      // [C x D] or null
+  uint8_t* trace_acc;     // [C] or null
+  float* trace_eps;       // [1] or null
+};
+
+// Scratch of the plain (one launch per operation) transition.
+struct PlainBuffers {
+  float* xp;   // proposal position [C x D]
+  float* gp;   // gradient at the proposal
+  float* p;    // momentum
+  float* lpp;  // log-prob at the proposal [C]
+  float* h0;   // initial Hamiltonian [C]
+};
+
+// Largest state dimension the fused elementwise transition keeps in registers.
+constexpr int kFusedElementwiseMaxDim = 1024;
+// Blocks the accept / fused kernels launch for C chains (one warp per chain).
+unsigned accept_blocks(int C);
+
+cudaError_t launch_fused_elementwise(int target_id, const StepArgs& a, cudaStream_t s,
+                                     KernelTimer* timer = nullptr);
+cudaError_t launch_plain_transition(const hmc_target& t, const StepArgs& a, const PlainBuffers& b,
+                                    void* grad_ws, cudaStream_t s, KernelTimer* timer = nullptr);
+cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
+                          cudaStream_t s);
+cudaError_t launch_momentum(uint64_t seed, uint32_t t, int C, int D, uint32_t chain_offset,
+                            float* out, cudaStream_t s);
+cudaError_t launch_da_init(DAState* da, float eps0, int adapt, float delta, long long num_adapt,
+                           cudaStream_t s);
+
+}  // namespace hmc

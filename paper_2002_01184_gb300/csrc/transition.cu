@@ -1,0 +1,351 @@
+// HMC transition kernels (Section 3.1): momentum draw, leapfrog, energy,
+// Metropolis-Hastings select and the dual-averaging update.
+//
+// Fused path for targets whose gradient is elementwise plus row reductions
+// (standard normal, funnel): one warp per chain keeps x, p and g of its chain
+// in registers for all L leapfrog steps and the accept test, so one
+// transition is one launch that reads x, g once and writes them once.
+//
+// Plain path (any target): one launch per operation per leapfrog step --
+// begin (momentum + H_0), kick-drift, gradient, kick, ..., accept -- the
+// shape a framework that evaluates a batched target op by op produces.
+#include <cmath>
+
+#include "hmc_device.cuh"
+#include "hmc_internal.h"
+
+namespace hmc {
+
+unsigned accept_blocks(int C) { return static_cast<unsigned>((C + 7) / 8); }
+
+namespace {
+
+constexpr int kWarpsPerBlock = 8;
+
+// Sum of the per-warp acceptance probabilities of this block in warp order,
+// then the deterministic grid reduction and dual-averaging update.
+__device__ __forceinline__ void finish_block(const StepArgs& a, float prob, bool has_chain) {
+  __shared__ float warp_prob[kWarpsPerBlock];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) warp_prob[w] = has_chain ? prob : 0.f;
+  __syncthreads();
+  double sum = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kWarpsPerBlock; ++i) sum += static_cast<double>(warp_prob[i]);
+  block_partial_then_da(a.da, a.partials, sum, a.C, a.t_full);
+}
+
+// ------------------------------------------------------ fused elementwise --
+// Lane `lane` of the chain's warp owns Philox blocks j = lane + 32 b
+// (b < NB), i.e. state dims 4 j .. 4 j + 3.
+template <int TARGET, int NB>
+__global__ void __launch_bounds__(256) k_fused_elementwise(StepArgs a) {
+  const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const bool has_chain = c < a.C;
+  float prob = 0.f;
+  if (has_chain) {
+    const int D = a.D;
+    const int64_t row = static_cast<int64_t>(c) * D;
+    const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
+    const float eps = a.da->eps;
+    float x0[NB][4], x[NB][4], p[NB][4], g[NB][4];
+    float kin0 = 0.f;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = lane + 32 * b;
+      const float4 z = momentum4(a.seed, static_cast<uint32_t>(j), chain, a.t);
+      const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int d = 4 * j + i;
+        const bool in = d < D;
+        x0[b][i] = in ? a.x[row + d] : 0.f;
+        x[b][i] = x0[b][i];
+        g[b][i] = in ? a.g[row + d] : 0.f;
+        p[b][i] = in ? zz[i] : 0.f;
+        kin0 = fmaf(p[b][i], p[b][i], kin0);
+      }
+    }
+    kin0 = 0.5f * warp_sum(kin0);
+    const float lp0 = a.lp[c];
+    float lp1 = 0.f;
+    const float half_n = 0.5f * static_cast<float>(D - 1);
+    for (int l = 0; l < a.L; ++l) {
+      float q = 0.f;
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          p[b][i] = fmaf(0.5f * eps, g[b][i], p[b][i]);
+          x[b][i] = fmaf(eps, p[b][i], x[b][i]);
+          // the funnel's reduction runs over x_1.. only (dim 0 is v)
+          const bool is_v = TARGET == HMC_T_FUNNEL && b == 0 && i == 0 && lane == 0;
+          q = is_v ? q : fmaf(x[b][i], x[b][i], q);
+        }
+      if (TARGET == HMC_T_STD_NORMAL) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) g[b][i] = -x[b][i];
+        if (l == a.L - 1) lp1 = -0.5f * warp_sum(q);
+      } else {  // funnel: v is dim 0 (lane 0, block 0, word 0)
+        const float v = __shfl_sync(0xffffffffu, x[0][0], 0);
+        q = warp_sum(q);
+        const float ev = expf(-v);
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) g[b][i] = -ev * x[b][i];
+        if (lane == 0) g[0][0] = -v / 9.f - half_n + 0.5f * ev * q;
+        if (l == a.L - 1) lp1 = -v * v / 18.f - half_n * v - 0.5f * ev * q;
+      }
+      // dims past D keep x = p = g = 0 throughout (g = -x and -e^-v x vanish)
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          p[b][i] = fmaf(0.5f * eps, g[b][i], p[b][i]);
+        }
+    }
+    float kin1 = 0.f;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) kin1 = fmaf(p[b][i], p[b][i], kin1);
+    kin1 = 0.5f * warp_sum(kin1);
+    const float h0 = -lp0 + kin0, h1 = -lp1 + kin1;
+    float la = h0 - h1;
+    if (!isfinite(la)) la = -INFINITY;
+    int acc = 0;
+    if (lane == 0) acc = accept_log_uniform(a.seed, chain, a.t) < la;
+    acc = __shfl_sync(0xffffffffu, acc, 0);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = lane + 32 * b;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int d = 4 * j + i;
+        if (d < D) {
+          if (acc) {
+            a.x[row + d] = x[b][i];
+            a.g[row + d] = g[b][i];
+          }
+          if (a.sample_out) a.sample_out[row + d] = acc ? x[b][i] : x0[b][i];
+        }
+      }
+    }
+    if (lane == 0) {
+      if (acc) a.lp[c] = lp1;
+      a.is_accepted[c] = static_cast<uint8_t>(acc);
+      a.log_accept[c] = la;
+      if (a.trace_acc) a.trace_acc[c] = static_cast<uint8_t>(acc);
+      if (c == 0 && a.trace_eps) a.trace_eps[0] = eps;
+    }
+    prob = accept_prob(la);
+  }
+  finish_block(a, prob, has_chain);
+}
+
+// ------------------------------------------------------------ plain path --
+// p ~ N(0, I); xp = x; gp = g; h0 = -lp + |p|^2/2   (warp per chain)
+__global__ void k_plain_begin(StepArgs a, PlainBuffers b) {
+  const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= a.C) return;
+  const int D = a.D;
+  const int64_t row = static_cast<int64_t>(c) * D;
+  const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
+  float kin = 0.f;
+  for (int j = lane; 4 * j < D; j += 32) {
+    const float4 z = momentum4(a.seed, static_cast<uint32_t>(j), chain, a.t);
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+    for (int i = 0; i < 4 && 4 * j + i < D; ++i) {
+      const int64_t e = row + 4 * j + i;
+      b.p[e] = zz[i];
+      b.xp[e] = a.x[e];
+      b.gp[e] = a.g[e];
+      kin = fmaf(zz[i], zz[i], kin);
+    }
+  }
+  kin = warp_sum(kin);
+  if (lane == 0) b.h0[c] = -a.lp[c] + 0.5f * kin;
+}
+
+// p += eps/2 gp; xp += eps p
+__global__ void k_plain_kick_drift(int64_t n, float* __restrict__ p, const float* __restrict__ gp,
+                                   float* __restrict__ xp, const DAState* __restrict__ da) {
+  const float eps = da->eps;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float pi = fmaf(0.5f * eps, gp[i], p[i]);
+    p[i] = pi;
+    xp[i] = fmaf(eps, pi, xp[i]);
+  }
+}
+
+// p += eps/2 gp
+__global__ void k_plain_kick(int64_t n, float* __restrict__ p, const float* __restrict__ gp,
+                             const DAState* __restrict__ da) {
+  const float eps = da->eps;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    p[i] = fmaf(0.5f * eps, gp[i], p[i]);
+}
+
+// H_L, log alpha, Metropolis-Hastings select, traces, dual averaging
+__global__ void k_plain_accept(StepArgs a, PlainBuffers b) {
+  const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const bool has_chain = c < a.C;
+  float prob = 0.f;
+  if (has_chain) {
+    const int D = a.D;
+    const int64_t row = static_cast<int64_t>(c) * D;
+    const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
+    float kin = 0.f;
+    for (int d = lane; d < D; d += 32) kin = fmaf(b.p[row + d], b.p[row + d], kin);
+    kin = 0.5f * warp_sum(kin);
+    const float h1 = -b.lpp[c] + kin;
+    float la = b.h0[c] - h1;
+    if (!isfinite(la)) la = -INFINITY;
+    int acc = 0;
+    if (lane == 0) acc = accept_log_uniform(a.seed, chain, a.t) < la;
+    acc = __shfl_sync(0xffffffffu, acc, 0);
+    for (int d = lane; d < D; d += 32) {
+      if (acc) {
+        a.x[row + d] = b.xp[row + d];
+        a.g[row + d] = b.gp[row + d];
+      }
+      if (a.sample_out) a.sample_out[row + d] = a.x[row + d];
+    }
+    if (lane == 0) {
+      if (acc) a.lp[c] = b.lpp[c];
+      a.is_accepted[c] = static_cast<uint8_t>(acc);
+      a.log_accept[c] = la;
+      if (a.trace_acc) a.trace_acc[c] = static_cast<uint8_t>(acc);
+      if (c == 0 && a.trace_eps) a.trace_eps[0] = a.da->eps;
+    }
+    prob = accept_prob(la);
+  }
+  finish_block(a, prob, has_chain);
+}
+
+__global__ void k_da_init(DAState* da, float eps0, int adapt, float delta, long long num_adapt) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  da->log_eps = log(static_cast<double>(eps0));
+  da->log_eps_bar = 0.0;
+  da->h_bar = 0.0;
+  da->mu = log(10.0 * static_cast<double>(eps0));
+  da->delta = static_cast<double>(delta);
+  da->last_stat = 0.0;
+  da->m = 0;
+  da->num_adapt = num_adapt;
+  da->eps = eps0;
+  da->adapt = adapt;
+  da->arrive = 0u;
+}
+
+__global__ void k_philox_words(const uint32_t* __restrict__ ctr, int64_t n, uint64_t seed,
+                               uint32_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    const uint4 w = philox(c, static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+    out[4 * i] = w.x;
+    out[4 * i + 1] = w.y;
+    out[4 * i + 2] = w.z;
+    out[4 * i + 3] = w.w;
+  }
+}
+
+// one thread per (chain, Philox block)
+__global__ void k_momentum(uint64_t seed, uint32_t t, int C, int D, uint32_t chain_offset,
+                           float* __restrict__ out) {
+  const int nblk = (D + 3) / 4;
+  const int64_t total = static_cast<int64_t>(C) * nblk;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(i / nblk), j = static_cast<int>(i % nblk);
+    const float4 z = momentum4(seed, static_cast<uint32_t>(j), static_cast<uint32_t>(c) + chain_offset, t);
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+    for (int k = 0; k < 4 && 4 * j + k < D; ++k) out[static_cast<int64_t>(c) * D + 4 * j + k] = zz[k];
+  }
+}
+
+
+template <int TARGET, int NB>
+void launch_fe(const StepArgs& a, cudaStream_t s) {
+  k_fused_elementwise<TARGET, NB><<<accept_blocks(a.C), 256, 0, s>>>(a);
+}
+
+template <int TARGET>
+void launch_fe_dim(const StepArgs& a, cudaStream_t s) {
+  const int nblk = (a.D + 3) / 4;           // Philox blocks per chain
+  if (nblk <= 32) launch_fe<TARGET, 1>(a, s);
+  else if (nblk <= 64) launch_fe<TARGET, 2>(a, s);
+  else if (nblk <= 128) launch_fe<TARGET, 4>(a, s);
+  else launch_fe<TARGET, 8>(a, s);
+}
+
+inline unsigned elementwise_blocks(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return static_cast<unsigned>(std::min<int64_t>(b, 152 * 16));
+}
+
+}  // namespace
+
+cudaError_t launch_fused_elementwise(int target_id, const StepArgs& a, cudaStream_t s,
+                                     KernelTimer* timer) {
+  if (a.D > kFusedElementwiseMaxDim) return cudaErrorInvalidValue;
+  if (target_id != HMC_T_STD_NORMAL && target_id != HMC_T_FUNNEL) return cudaErrorInvalidValue;
+  if (timer) timer->begin(s);
+  if (target_id == HMC_T_STD_NORMAL) launch_fe_dim<HMC_T_STD_NORMAL>(a, s);
+  else launch_fe_dim<HMC_T_FUNNEL>(a, s);
+  if (timer) timer->end(s);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_transition(const hmc_target& t, const StepArgs& a, const PlainBuffers& b,
+                                    void* grad_ws, cudaStream_t s, KernelTimer* timer) {
+  const int64_t n = static_cast<int64_t>(a.C) * a.D;
+  k_plain_begin<<<accept_blocks(a.C), 256, 0, s>>>(a, b);
+  count_launch();
+  for (int l = 0; l < a.L; ++l) {
+    k_plain_kick_drift<<<elementwise_blocks(n), 256, 0, s>>>(n, b.p, b.gp, b.xp, a.da);
+    count_launch();
+    cudaError_t e = launch_grad(t, a.C, b.xp, b.lpp, b.gp, grad_ws, s, timer);
+    if (e != cudaSuccess) return e;
+    k_plain_kick<<<elementwise_blocks(n), 256, 0, s>>>(n, b.p, b.gp, a.da);
+    count_launch();
+  }
+  k_plain_accept<<<accept_blocks(a.C), 256, 0, s>>>(a, b);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
+                          cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_philox_words<<<elementwise_blocks(n), 256, 0, s>>>(ctr, n, seed, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_momentum(uint64_t seed, uint32_t t, int C, int D, uint32_t chain_offset,
+                            float* out, cudaStream_t s) {
+  k_momentum<<<elementwise_blocks(static_cast<int64_t>(C) * ((D + 3) / 4)), 256, 0, s>>>(
+      seed, t, C, D, chain_offset, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_da_init(DAState* da, float eps0, int adapt, float delta, long long num_adapt,
+                           cudaStream_t s) {
+  k_da_init<<<1, 32, 0, s>>>(da, eps0, adapt, delta, num_adapt);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace hmc

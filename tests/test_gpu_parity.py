@@ -1,0 +1,293 @@
+"""GPU parity: libhmc's CUDA path against the float64 oracle, called through
+the C ABI on the same seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import diagnostics, hmc as ohmc, philox, targets as otargets
+from paper_2002_01184_gb300 import workloads
+from tests.parity import compare_transition
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2002_01184_gb300 import build
+    build.build()
+    from paper_2002_01184_gb300 import hmc
+    return hmc
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a)).cuda().contiguous()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def small_problem(kind, **kw):
+    if kind == "std_normal":
+        return workloads.std_normal(num_chains=kw.get("C", 100), dim=kw.get("D", 1),
+                                    step_size=kw.get("eps", 1.5), num_leapfrog=kw.get("L", 3))
+    if kind == "funnel":
+        p = workloads.funnel(dim=kw.get("D", 50), num_chains=kw.get("C", 37))
+    elif kind == "corr_gauss":
+        p = workloads.corr_gauss(dim=kw.get("D", 70), num_chains=kw.get("C", 130))
+    elif kind == "logreg":
+        p = workloads.logreg(n_data=kw.get("N", 300), dim=kw.get("D", 20), num_chains=kw.get("C", 70))
+        p.x0 = (0.1 * np.random.default_rng(0).standard_normal(p.x0.shape)).astype(np.float32)
+    p.num_leapfrog = kw.get("L", p.num_leapfrog)
+    p.step_size = kw.get("eps", 0.05)
+    p.adapt = False
+    return p
+
+
+# ---------------------------------------------------------------- random ----
+
+def test_philox_words_are_bit_identical(H):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2 ** 32, size=(5000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:3] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [7, 1, 2, 3]]
+    for seed in (0, 1, 2 ** 63 + 12345):
+        out = torch.empty(ctr.size, dtype=torch.int32, device="cuda")
+        H.hmc_philox4x32_10(dev(ctr.view(np.int32)), ctr.shape[0], seed, out)
+        got = host(out).view(np.uint32).reshape(-1, 4)
+        np.testing.assert_array_equal(got, philox.philox4x32_10(ctr, philox.seed_key(seed)))
+
+
+@pytest.mark.parametrize("C,D,t,off", [(37, 13, 5, 3), (1, 1, 0, 0), (64, 256, 2 ** 31 + 7, 1000)])
+def test_momentum_matches_oracle(H, C, D, t, off):
+    out = torch.empty((C, D), dtype=torch.float32, device="cuda")
+    H.hmc_momentum(9, t, C, D, off, out)
+    ref = philox.momentum(9, t, C, D, chain_offset=off)
+    np.testing.assert_allclose(host(out), ref, rtol=2e-6, atol=2e-6)
+
+
+# ------------------------------------------------------------- gradients ----
+
+GRAD_CASES = [("std_normal", dict(C=37, D=13)), ("funnel", dict(C=37, D=50)),
+              ("corr_gauss", dict(C=130, D=70)), ("corr_gauss", dict(C=64, D=64)),
+              ("logreg", dict(C=70, D=20, N=300)), ("logreg", dict(C=129, D=65, N=1000))]
+
+
+@pytest.mark.parametrize("kind,kw", GRAD_CASES)
+def test_gradient_matches_oracle(H, kind, kw):
+    p = small_problem(kind, **kw)
+    C, D = p.num_chains, p.dim
+    x = (0.5 * np.random.default_rng(2).standard_normal((C, D))).astype(np.float32)
+    Pd, Xd, yd = (dev(a) if a is not None else None for a in (p.P, p.X, p.y))
+    t = H.make_target(kind, D, Pd, Xd, yd)
+    nbytes = H.hmc_grad_workspace_bytes(t, C)
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device="cuda")
+    lp = torch.empty(C, dtype=torch.float32, device="cuda")
+    g = torch.empty((C, D), dtype=torch.float32, device="cuda")
+    H.hmc_target_log_prob_and_grad(t, C, dev(x), lp, g, ws, nbytes)
+    lp_ref, g_ref = otargets.make(kind, **p.data())(x.astype(np.float64))
+    gg = host(g)
+    row = np.max(np.abs(g_ref), axis=1, keepdims=True)
+    assert np.max(np.abs(gg - g_ref) / np.maximum(row, 1e-6)) < 1e-5
+    np.testing.assert_allclose(host(lp), lp_ref, rtol=1e-5, atol=1e-5)
+
+
+# ----------------------------------------------------------- transitions ----
+
+TRANSITION_CASES = [
+    ("std_normal", dict(C=100, D=1, eps=1.5, L=3)),
+    ("std_normal", dict(C=45, D=13, eps=0.4, L=5)),
+    ("funnel", dict(C=37, D=50, eps=0.05, L=10)),
+    ("funnel", dict(C=9, D=200, eps=0.02, L=4)),
+    ("corr_gauss", dict(C=130, D=70, eps=0.12, L=8)),
+    ("logreg", dict(C=70, D=20, N=300, eps=0.02, L=5)),
+]
+
+
+def run_teacher_forced(H, p, impl, steps=4, t0=0):
+    from paper_2002_01184_gb300.sampler import Sampler
+    s = Sampler(p, impl=impl, adapt=False)
+    x = dev(p.x0)
+    s.bootstrap(x)
+    tgt = otargets.make(p.kind, **p.data())
+    n_same = n_band = 0
+    for t in range(t0, t0 + steps):
+        xin = host(x).astype(np.float64)
+        lp, g = tgt(xin)
+        r = s.results(s.step(x, t))
+        ref = ohmc.one_step(xin, lp, g, np.float32(p.step_size), p.num_leapfrog, p.seed, t, tgt)
+        a, b = compare_transition(xin, host(x), host(r["is_accepted"]), host(r["log_accept_ratio"]),
+                                  ref, label=f"{p.kind} t={t}")
+        n_same += a
+        n_band += b
+        # the cached kernel results belong to the new state
+        lp_new, _ = tgt(host(x).astype(np.float64))
+        np.testing.assert_allclose(host(r["target_log_prob"]), lp_new,
+                                   rtol=1e-4, atol=1e-4 * max(1.0, np.abs(lp_new).max()))
+    s.close()
+    return n_same, n_band
+
+
+@pytest.mark.parametrize("impl", [0, 1], ids=["fused", "plain"])
+@pytest.mark.parametrize("kind,kw", TRANSITION_CASES)
+def test_transition_matches_oracle(H, kind, kw, impl):
+    p = small_problem(kind, **kw)
+    n_same, n_band = run_teacher_forced(H, p, impl)
+    assert n_same >= 4 * p.num_chains - 2
+
+
+def test_worked_example_end_to_end(H):
+    """The Section 1 example: 100 chains from 0, L = 3, eps = 1.5, 300 burn-in,
+    100 kept; kept draws are N(0,1) within 3 MCSE, the traced step size is
+    the fixed 1.5 and the acceptance matches the closed-form 0.7602."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = workloads.std_normal()
+    s = Sampler(p)
+    x = dev(p.x0)
+    samples, eps, acc = s.sample_chain(x, p.num_burnin, p.num_results)
+    smp = host(samples).astype(np.float64)
+    assert np.all(host(eps) == np.float32(1.5))
+    assert abs(smp.mean()) < 3 * diagnostics.mcse_mean(smp)[0]
+    assert abs((smp ** 2).mean() - 1) < 3 * diagnostics.mcse_mean(smp ** 2)[0]
+    rate = host(acc).mean()
+    assert abs(rate - 0.760231) < 4 * math.sqrt(0.76 * 0.24 / acc.numel()) * 2
+    s.close()
+
+
+def test_dual_averaging_replays_oracle(H):
+    """Transition by transition with adaptation: each GPU transition matches
+    the oracle's at the step size the GPU used, and feeding the GPU's
+    acceptance statistics to the oracle's dual averaging reproduces the GPU's
+    step-size sequence."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = workloads.corr_gauss(dim=32, num_chains=256, num_burnin=25, num_results=0)
+    s = Sampler(p)
+    x = dev(p.x0)
+    s.bootstrap(x)
+    tgt = otargets.make("corr_gauss", P=p.P)
+    da = ohmc.DualAveraging(np.float32(p.step_size), p.target_accept)
+    eps_used = np.float32(p.step_size)
+    for t in range(p.num_burnin + 3):
+        xin = host(x).astype(np.float64)
+        lp, g = tgt(xin)
+        r = s.results(s.step(x, t))
+        ref = ohmc.one_step(xin, lp, g, float(eps_used), p.num_leapfrog, p.seed, t, tgt)
+        compare_transition(xin, host(x), host(r["is_accepted"]), host(r["log_accept_ratio"]), ref,
+                           label=f"DA t={t}")
+        st = s.adaptation()
+        assert st["last_stat"] == pytest.approx(ohmc.accept_statistic(ref["log_accept_ratio"]),
+                                                abs=2e-3)
+        if t < p.num_burnin:
+            da.update(st["last_stat"])
+            expect = da.step_size if t + 1 < p.num_burnin else da.final_step_size
+        else:
+            expect = da.final_step_size
+        assert st["step_size"] == pytest.approx(expect, rel=1e-6)
+        eps_used = np.float32(st["step_size"])
+    s.close()
+
+
+@pytest.mark.parametrize("kind,kw", [("funnel", dict(C=40, D=30, eps=0.05, L=6)),
+                                     ("corr_gauss", dict(C=40, D=30, eps=0.1, L=6)),
+                                     ("logreg", dict(C=40, D=12, N=200, eps=0.02, L=4))])
+def test_chain_isolation_is_bitwise(H, kind, kw):
+    """Section 3's batch semantics: a chain's trajectory is the same bit for
+    bit whether it runs alone (with its chain offset) or among 40 chains."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = small_problem(kind, **kw)
+    full = Sampler(p)
+    xf = dev(p.x0)
+    full.bootstrap(xf)
+    for t in range(5):
+        full.step(xf, t)
+    xf = host(xf)
+    for c in (0, 17, 39):
+        one = Sampler(p, num_chains=1, chain_offset=c)
+        xc = dev(p.x0[c:c + 1])
+        one.bootstrap(xc)
+        for t in range(5):
+            one.step(xc, t)
+        np.testing.assert_array_equal(host(xc)[0], xf[c])
+        one.close()
+    full.close()
+
+
+def test_host_entry_point_equals_device_entry_point(H):
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = workloads.corr_gauss(dim=24, num_chains=50, num_burnin=10, num_results=7)
+    s = Sampler(p)
+    x = dev(p.x0)
+    samples, eps, acc = s.sample_chain(x, p.num_burnin, p.num_results)
+    xh = p.x0.copy()
+    sh = np.empty((7, 50, 24), np.float32)
+    eh = np.empty(7, np.float32)
+    ah = np.empty((7, 50), np.uint8)
+    H.hmc_sample_chain_host(s.ctx, xh, 10, 7, sh, eh, ah)
+    np.testing.assert_array_equal(sh, host(samples))
+    np.testing.assert_array_equal(eh, host(eps))
+    np.testing.assert_array_equal(ah, host(acc))
+    np.testing.assert_array_equal(xh, host(x))
+    s.close()
+
+
+@pytest.mark.parametrize("C,D,L,B,K", [(1, 1, 1, 0, 3), (3, 5, 2, 2, 0), (9, 129, 1, 1, 2)])
+def test_edge_sizes(H, C, D, L, B, K):
+    from paper_2002_01184_gb300.sampler import Sampler
+    for kind in ("std_normal", "corr_gauss"):
+        p = small_problem(kind, C=C, D=D, eps=0.3, L=L)
+        p.x0 = np.random.default_rng(C * D).standard_normal((C, D)).astype(np.float32)
+        s = Sampler(p)
+        x = dev(p.x0)
+        samples, eps, acc = s.sample_chain(x, B, K)
+        tgt = otargets.make(kind, **p.data())
+        out = ohmc.sample_chain(p.x0.astype(np.float64), tgt, L, np.float32(0.3), p.seed, B, K)
+        # short runs stay within the teacher-forcing tolerance end to end
+        np.testing.assert_allclose(host(x), out["x"], rtol=1e-4, atol=1e-4)
+        if K:
+            np.testing.assert_allclose(host(samples), out["samples"], rtol=1e-4, atol=1e-4)
+            np.testing.assert_array_equal(host(acc).astype(bool), out["is_accepted"])
+        s.close()
+
+
+def test_divergent_proposals_are_rejected(H):
+    """A step size far too large for the funnel's neck produces non-finite
+    energies; those chains must be rejected and keep a finite state."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = small_problem("funnel", C=64, D=20, eps=30.0, L=8)
+    for impl in (0, 1):
+        s = Sampler(p, impl=impl)
+        x = dev(p.x0)
+        s.bootstrap(x)
+        r = s.results(s.step(x, 0))
+        la = host(r["log_accept_ratio"])
+        acc = host(r["is_accepted"]).astype(bool)
+        assert np.isinf(la).any()
+        assert not acc[np.isinf(la)].any()
+        assert np.isfinite(host(x)).all()
+        s.close()
+
+
+def test_correlated_gaussian_moments(H):
+    """Adapted sampling of a D = 8 correlated Gaussian: along a fixed random
+    direction u the kept draws have mean 0 and variance u^T P^-1 u, each
+    within 3 Monte Carlo standard errors."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = workloads.corr_gauss(dim=8, num_chains=2048, num_burnin=200, num_results=300)
+    s = Sampler(p)
+    x = dev(p.x0)
+    samples, eps, acc = s.sample_chain(x, p.num_burnin, p.num_results)
+    smp = host(samples).astype(np.float64)
+    u = np.random.default_rng(11).standard_normal(8)
+    u /= np.linalg.norm(u)
+    proj = (smp @ u)[..., None]
+    cov = np.linalg.inv(p.P.astype(np.float64))
+    assert abs(proj.mean()) < 3 * diagnostics.mcse_mean(proj)[0]
+    sq = proj ** 2
+    assert abs(sq.mean() - u @ cov @ u) < 3 * diagnostics.mcse_mean(sq)[0]
+    assert abs(host(acc).mean() - p.target_accept) < 0.05
+    s.close()
