@@ -5,7 +5,12 @@ chains separate after many transitions, so the element-by-element check is
 per transition: the oracle starts from the GPU's float32 state (promoted),
 uses the same (seed, chain, t) streams and the step size the GPU used, and
 the two outcomes are compared with these tolerances:
-  * positions: |x_gpu - x_ref| / max(|x_ref|, 1e-3) <= 1e-4;
+  * positions: 1e-4 relative, read per chain in the max norm:
+    max_d |x_gpu - x_ref| / max(max_d |x_ref|, 1e-3) <= 1e-4.  (Read
+    elementwise, the bound fails for correct float32 arithmetic: a component
+    of size 1e-3 carries the absolute rounding error of the O(1) components
+    it was computed with -- a float32 emulation of the funnel on the CPU shows
+    1.5e-4 elementwise against 2.6e-7 per chain.);
   * accept decisions identical except where |log u - log alpha| < 1e-5
     (log u and log alpha both from the oracle); such chains are only checked
     to hold one of the two valid states.
@@ -17,6 +22,14 @@ POS_FLOOR = 1e-3
 DECISION_BAND = 1e-5
 
 
+def chain_error(x, ref):
+    """Per-chain max-norm relative error, floor 1e-3."""
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    scale = np.maximum(np.max(np.abs(ref), axis=1), POS_FLOOR)
+    return np.max(np.abs(x - ref), axis=1) / scale
+
+
 def compare_transition(x_before, x_after_gpu, acc_gpu, la_gpu, ref, label=""):
     acc_gpu = np.asarray(acc_gpu).astype(bool)
     acc_ref = np.asarray(ref["is_accepted"]).astype(bool)
@@ -25,14 +38,14 @@ def compare_transition(x_before, x_after_gpu, acc_gpu, la_gpu, ref, label=""):
     assert not bad.any(), f"{label}: accept decisions differ for chains {np.nonzero(bad)[0][:10]}"
     same = acc_gpu == acc_ref
     xg = np.asarray(x_after_gpu, dtype=np.float64)
-    err = np.abs(xg - ref["x"]) / np.maximum(np.abs(ref["x"]), POS_FLOOR)
+    err = chain_error(xg, ref["x"])
     if same.any():
         worst = err[same].max()
         assert worst <= POS_RTOL, f"{label}: position error {worst:.3e} > {POS_RTOL}"
     # chains inside the decision band hold either the old state or the proposal
     for c in np.nonzero(~same)[0]:
         alt = ref["proposed_x"][c] if acc_gpu[c] else x_before[c]
-        e = np.abs(xg[c] - alt) / np.maximum(np.abs(alt), POS_FLOOR)
+        e = chain_error(xg[c:c + 1], np.asarray(alt)[None])
         assert e.max() <= POS_RTOL, f"{label}: chain {c} holds neither valid state"
     # rejected chains keep their state bit for bit
     rej = ~acc_gpu
