@@ -150,6 +150,15 @@ hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burni
  * acceptance statistic (mean over chains of min(1, alpha)). */
 hmc_status hmc_read_adaptation(hmc_ctx* ctx, double out[5]);
 
+/* Wait for the context's stream; HMC_E_TIMEOUT if a device-side bounded
+ * wait gave up since the context was created (the kernel that gave up
+ * skipped its writes; the state is then not meaningful). */
+hmc_status hmc_synchronize(hmc_ctx* ctx);
+
+/* 1 if the context's transitions run the tensor-core (tcgen05, 3xTF32)
+ * kernels: CORR_GAUSS with dim % 4 == 0 and HMC_IMPL_FUSED.  0 otherwise. */
+int32_t hmc_uses_tensor_cores(const hmc_ctx* ctx);
+
 /* Measurement support (no counterpart in the paper): time one launch in
  * every `sample_every` of the context's dominant kernel -- the fused
  * transition kernel, or the target-gradient product(s) of the plain path --

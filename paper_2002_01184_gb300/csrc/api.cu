@@ -37,6 +37,8 @@ struct hmc_ctx {
   size_t stage_bytes = 0;
   std::vector<void*> allocations;
   hmc::KernelTimer timer;
+  bool use_tc = false;          // tensor-core Gaussian path
+  hmc::GaussTc tc;
   std::string err;
 };
 
@@ -144,10 +146,21 @@ StepArgs make_args(hmc_ctx* ctx, float* x, uint64_t t) {
 }
 
 cudaError_t enqueue_transition(hmc_ctx* ctx, const StepArgs& a) {
+  if (ctx->use_tc) return hmc::launch_gauss_tc_transition(a, ctx->tc, ctx->stream, &ctx->timer);
   if (uses_fused_elementwise(ctx))
     return hmc::launch_fused_elementwise(ctx->target.id, a, ctx->stream, &ctx->timer);
   return hmc::launch_plain_transition(ctx->target, a, ctx->plain, ctx->grad_ws, ctx->stream,
                                       &ctx->timer);
+}
+
+// After a stream synchronisation: report a bounded device wait that gave up.
+hmc_status check_device_flag(hmc_ctx* ctx) {
+  if (!ctx->use_tc) return HMC_OK;
+  int flag = 0;
+  cudaError_t e = cudaMemcpy(&flag, ctx->tc.err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "read device error flag");
+  if (flag) return fail(ctx, HMC_E_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
+  return HMC_OK;
 }
 
 hmc_status bootstrap(hmc_ctx* ctx, const float* x0) {
@@ -205,7 +218,13 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->log_accept, C);
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->da, 1);
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->partials, nblk);
-  if (e == cudaSuccess && !uses_fused_elementwise(ctx)) {
+  ctx->use_tc = config->impl == HMC_IMPL_FUSED && hmc::gauss_tc_supported(*target);
+  if (e == cudaSuccess && ctx->use_tc) {
+    char* w = nullptr;
+    e = ctx_alloc(ctx, &w, hmc::gauss_tc_workspace_bytes(*target, num_chains));
+    if (e == cudaSuccess) e = hmc::gauss_tc_setup(&ctx->tc, *target, num_chains, w, ctx->stream);
+  }
+  if (e == cudaSuccess && !uses_fused_elementwise(ctx) && !ctx->use_tc) {
     e = ctx_alloc(ctx, &ctx->plain.xp, C * D);
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.gp, C * D);
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.p, C * D);
@@ -316,7 +335,7 @@ hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burni
     e = cudaMemcpyAsync(trace_accept, dacc, K * ctx->C, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "result download");
-  return HMC_OK;
+  return check_device_flag(ctx);
 }
 
 hmc_status hmc_read_adaptation(hmc_ctx* ctx, double out[5]) {
@@ -326,12 +345,21 @@ hmc_status hmc_read_adaptation(hmc_ctx* ctx, double out[5]) {
   cudaError_t e = cudaMemcpyAsync(&h, ctx->da, sizeof(DAState), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "read adaptation state");
+  hmc_status st = check_device_flag(ctx);
+  if (st != HMC_OK) return st;
   out[0] = static_cast<double>(h.eps);
   out[1] = h.log_eps_bar;
   out[2] = h.h_bar;
   out[3] = static_cast<double>(h.m);
   out[4] = h.last_stat;
   return HMC_OK;
+}
+
+hmc_status hmc_synchronize(hmc_ctx* ctx) {
+  if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+  return check_device_flag(ctx);
 }
 
 hmc_status hmc_profile_dominant_kernel(hmc_ctx* ctx, int32_t sample_every) {
@@ -375,6 +403,8 @@ hmc_status hmc_destroy(hmc_ctx* ctx) {
 const char* hmc_last_error(const hmc_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_global_err.c_str();
 }
+
+int32_t hmc_uses_tensor_cores(const hmc_ctx* ctx) { return ctx && ctx->use_tc ? 1 : 0; }
 
 hmc_status hmc_grad_workspace_bytes(const hmc_target* target, int64_t num_chains, uint64_t* bytes) {
   std::string why;

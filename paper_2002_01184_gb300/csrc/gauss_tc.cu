@@ -1,0 +1,405 @@
+// Dense Gaussian target on the tcgen05 tensor cores: each leapfrog step is
+// one launch that computes a 128-chain x 64-column tile of the gradient
+// G = -X P (a C x D x D product, Section 3.1's batched "list of vectors"
+// evaluation) in 3xTF32 -- A_lo B_hi + A_hi B_lo + A_hi B_hi, float32
+// accumulation in tensor memory -- and applies the leapfrog update to the
+// same tile in its epilogue, so the gradient never goes to HBM.
+//
+// A transition (identity mass, step eps, L steps) is L + 2 launches:
+//   begin:  p0 ~ N(0, I); H0 = -lp(x0) + |p0|^2/2; p = p0 + eps/2 g(x0);
+//           x1 = x0 + eps p                          (cached g(x0) reused)
+//   step l = 1 .. L-1:  g = -x_l P;  p += eps g;  x_{l+1} = x_l + eps p
+//           (the half kicks of consecutive steps merged)
+//   step L: g = -x_L P;  p += eps/2 g;  lp partials <x_L, g>/2 per tile
+//   accept: H_L, Metropolis-Hastings select, traces, dual averaging
+// Positions inside the trajectory are kept as their tf32 head and float32
+// remainder (x = hi + lo exactly): the A operands the next product loads by
+// TMA.  Both buffers are ping-ponged between steps.
+//
+// Tile pipeline (192 threads): warp 0 allocates tensor memory and one lane
+// issues the TMA loads of the A (x hi/lo: 128 x 32) and B (P hi/lo: 64 x 32)
+// K-chunks into a 4-stage ring; one lane of warp 1 issues the MMAs; warps 2-5
+// read the accumulator (one TMEM lane quarter each) and run the epilogue.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+
+#include "hmc_device.cuh"
+#include "hmc_internal.h"
+#include "sm100_ptx.cuh"
+
+namespace hmc {
+
+namespace {
+
+constexpr int kBM = 128;          // chains per tile (MMA M)
+constexpr int kBN = 64;           // gradient columns per tile (MMA N)
+constexpr int kBK = 32;           // K chunk: 32 floats = one 128-B swizzle row
+constexpr int kStages = 4;
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 64;
+constexpr uint32_t kABytes = kBM * kBK * 4;                  // 16 KB
+constexpr uint32_t kBBytes = kBN * kBK * 4;                  // 8 KB
+constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;  // 48 KB
+constexpr size_t kSmemBytes = kStages * kStageBytes + 1024 + 256;
+
+struct TcStepArgs {
+  int C, D;
+  int last;                 // 0: middle step, 1: final step of the trajectory
+  const float* xhi_in;      // x_l split (this tile's elements are re-read here)
+  const float* xlo_in;
+  float* xhi_out;           // x_{l+1} split (middle steps)
+  float* xlo_out;
+  float* p;                 // momentum, updated in place
+  float* g_out;             // final step: gradient at x_L
+  float* lp_part;           // final step: [C x ntn] tile partials of <x, g>/2
+  int ntn;                  // column tiles
+  const DAState* da;
+  int* err;                 // set to 1 if a bounded wait gave up
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                TcStepArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* acc_full = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+  const int nk = (a.D + kBK - 1) / kBK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    ptx::mbar_init(acc_full, 1);
+    ptx::fence_mbar_init();
+    ptx::prefetch_tensormap(&mAhi);
+    ptx::prefetch_tensormap(&mAlo);
+    ptx::prefetch_tensormap(&mBhi);
+    ptx::prefetch_tensormap(&mBlo);
+  }
+  if (warp == 0) {
+    ptx::tmem_alloc(tmem_slot, kTmemCols);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % kStages, round = kc / kStages;
+      if (kc >= kStages && !ptx::mbar_wait(&empty[s], (round - 1) & 1)) {
+        atomicExch(a.err, 1);
+        break;
+      }
+      uint8_t* st = smem + s * kStageBytes;
+      ptx::mbar_arrive_expect_tx(&full[s], kStageBytes);
+      ptx::tma_load_2d(st, &mAhi, &full[s], kc * kBK, m0);
+      ptx::tma_load_2d(st + kABytes, &mAlo, &full[s], kc * kBK, m0);
+      ptx::tma_load_2d(st + 2 * kABytes, &mBhi, &full[s], kc * kBK, n0);
+      ptx::tma_load_2d(st + 2 * kABytes + kBBytes, &mBlo, &full[s], kc * kBK, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    constexpr uint32_t idesc = ptx::idesc_tf32(kBM, kBN);
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % kStages, round = kc / kStages;
+      if (!ptx::mbar_wait(&full[s], round & 1)) {
+        atomicExch(a.err, 1);
+        break;
+      }
+      ptx::tc_fence_after();
+      const uint32_t st = ptx::smem_u32(smem + s * kStageBytes);
+#pragma unroll
+      for (int j = 0; j < kBK / 8; ++j) {           // K = 8 tf32 per MMA (32 B)
+        const uint64_t a_hi = ptx::sw128_kmajor_desc(st + 32 * j);
+        const uint64_t a_lo = ptx::sw128_kmajor_desc(st + kABytes + 32 * j);
+        const uint64_t b_hi = ptx::sw128_kmajor_desc(st + 2 * kABytes + 32 * j);
+        const uint64_t b_lo = ptx::sw128_kmajor_desc(st + 2 * kABytes + kBBytes + 32 * j);
+        ptx::mma_tf32(tmem, a_lo, b_hi, idesc, (kc | j) != 0 ? 1u : 0u);
+        ptx::mma_tf32(tmem, a_hi, b_lo, idesc, 1u);
+        ptx::mma_tf32(tmem, a_hi, b_hi, idesc, 1u);
+      }
+      ptx::mma_commit(&empty[s]);
+    }
+    ptx::mma_commit(acc_full);
+  } else if (warp >= 2) {
+    // ---- epilogue: thread owns one chain row of the tile
+    const bool ok = ptx::mbar_wait(acc_full, 0);
+    if (!ok) atomicExch(a.err, 1);
+    ptx::tc_fence_after();
+    const int quarter = warp & 3;
+    const int r = quarter * 32 + lane;
+    const int m = m0 + r;
+    const bool row_ok = ok && m < a.C;
+    const float eps = a.da->eps;
+    const int64_t rowoff = static_cast<int64_t>(m) * a.D;
+    float part = 0.f;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kBN; c0 += 16) {
+      float acc[16];
+      ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + c0, acc);
+      if (!row_ok) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int n = n0 + c0 + j;
+        if (n >= a.D) break;
+        const int64_t e = rowoff + n;
+        const float g = -acc[j];
+        const float x = a.xhi_in[e] + a.xlo_in[e];
+        if (!a.last) {
+          const float p = fmaf(eps, g, a.p[e]);
+          a.p[e] = p;
+          float hi, lo;
+          split_tf32(fmaf(eps, p, x), hi, lo);
+          a.xhi_out[e] = hi;
+          a.xlo_out[e] = lo;
+        } else {
+          a.p[e] = fmaf(0.5f * eps, g, a.p[e]);
+          a.g_out[e] = g;
+          part = fmaf(x, g, part);
+        }
+      }
+    }
+    if (a.last && row_ok) a.lp_part[static_cast<int64_t>(m) * a.ntn + blockIdx.y] = 0.5f * part;
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+constexpr int kWarpsPerBlock = 8;
+
+struct TcBeginAccept {
+  StepArgs s;
+  float* p;
+  float* xhi;        // begin: x1 split out; accept: x_L split in
+  float* xlo;
+  float* gL;
+  float* lp_part;
+  float* h0;
+  int ntn;
+};
+
+// p0 ~ N(0, I); H0; half kick with the cached gradient; first drift (warp per chain)
+__global__ void k_gauss_tc_begin(TcBeginAccept b) {
+  const StepArgs& a = b.s;
+  const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= a.C) return;
+  const int D = a.D;
+  const int64_t row = static_cast<int64_t>(c) * D;
+  const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
+  const float eps = a.da->eps;
+  float kin = 0.f;
+  for (int j = lane; 4 * j < D; j += 32) {
+    const float4 z = momentum4(a.seed, static_cast<uint32_t>(j), chain, a.t);
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+    for (int i = 0; i < 4 && 4 * j + i < D; ++i) {
+      const int64_t e = row + 4 * j + i;
+      kin = fmaf(zz[i], zz[i], kin);
+      const float p = fmaf(0.5f * eps, a.g[e], zz[i]);
+      b.p[e] = p;
+      float hi, lo;
+      split_tf32(fmaf(eps, p, a.x[e]), hi, lo);
+      b.xhi[e] = hi;
+      b.xlo[e] = lo;
+    }
+  }
+  kin = warp_sum(kin);
+  if (lane == 0) b.h0[c] = -a.lp[c] + 0.5f * kin;
+}
+
+// H_L from the tile partials and |p|^2; Metropolis-Hastings select; traces;
+// dual averaging (warp per chain)
+__global__ void k_gauss_tc_accept(TcBeginAccept b) {
+  const StepArgs& a = b.s;
+  const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const bool has_chain = c < a.C;
+  float prob = 0.f;
+  if (has_chain) {
+    const int D = a.D;
+    const int64_t row = static_cast<int64_t>(c) * D;
+    const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
+    float kin = 0.f;
+    for (int d = lane; d < D; d += 32) kin = fmaf(b.p[row + d], b.p[row + d], kin);
+    kin = 0.5f * warp_sum(kin);
+    float lp1 = 0.f;
+    if (lane == 0)
+      for (int k = 0; k < b.ntn; ++k) lp1 += b.lp_part[static_cast<int64_t>(c) * b.ntn + k];
+    lp1 = __shfl_sync(0xffffffffu, lp1, 0);
+    float la = b.h0[c] - (-lp1 + kin);
+    if (!isfinite(la)) la = -INFINITY;
+    int acc = 0;
+    if (lane == 0) acc = accept_log_uniform(a.seed, chain, a.t) < la;
+    acc = __shfl_sync(0xffffffffu, acc, 0);
+    for (int d = lane; d < D; d += 32) {
+      const int64_t e = row + d;
+      if (acc) {
+        a.x[e] = b.xhi[e] + b.xlo[e];
+        a.g[e] = b.gL[e];
+      }
+      if (a.sample_out) a.sample_out[e] = a.x[e];
+    }
+    if (lane == 0) {
+      if (acc) a.lp[c] = lp1;
+      a.is_accepted[c] = static_cast<uint8_t>(acc);
+      a.log_accept[c] = la;
+      if (a.trace_acc) a.trace_acc[c] = static_cast<uint8_t>(acc);
+      if (c == 0 && a.trace_eps) a.trace_eps[0] = a.da->eps;
+    }
+    prob = accept_prob(la);
+  }
+  accept_block_finish<kWarpsPerBlock>(a.da, a.partials, prob, has_chain, a.C, a.t_full);
+}
+
+// P -> (tf32 head, float32 remainder)
+__global__ void k_split(int64_t n, const float* __restrict__ src, float* __restrict__ hi,
+                        float* __restrict__ lo) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float h, l;
+    split_tf32(src[i], h, l);
+    hi[i] = h;
+    lo[i] = l;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Row-major [rows x cols] float32 matrix, box of 32 columns x box_rows rows,
+// 128-byte swizzle (matches sw128_kmajor_desc).
+bool make_map(CUtensorMap* map, const float* base, int64_t rows, int cols, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(cols) * sizeof(float)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+inline unsigned blocks_for(int64_t n) {
+  return static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 152 * 16));
+}
+
+}  // namespace
+
+bool gauss_tc_supported(const hmc_target& t) {
+  return t.id == HMC_T_CORR_GAUSS && t.dim % 4 == 0 && encode_fn() != nullptr;
+}
+
+size_t gauss_tc_workspace_bytes(const hmc_target& t, int64_t C) {
+  const size_t CD = static_cast<size_t>(C) * t.dim, DD = static_cast<size_t>(t.dim) * t.dim;
+  const size_t ntn = (t.dim + kBN - 1) / kBN;
+  auto a = [](size_t b) { return (b + 1023) & ~static_cast<size_t>(1023); };
+  return 2 * a(DD * 4) + 6 * a(CD * 4) + a(C * ntn * 4) + a(C * 4) + a(sizeof(int));
+}
+
+cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s) {
+  const size_t CD = static_cast<size_t>(C) * t.dim, DD = static_cast<size_t>(t.dim) * t.dim;
+  auto a = [](size_t b) { return (b + 1023) & ~static_cast<size_t>(1023); };
+  char* w = static_cast<char*>(ws);
+  auto take = [&](size_t bytes) { char* p = w; w += a(bytes); return reinterpret_cast<float*>(p); };
+  tc->ntn = (t.dim + kBN - 1) / kBN;
+  tc->Phi = take(DD * 4);
+  tc->Plo = take(DD * 4);
+  for (int i = 0; i < 2; ++i) {
+    tc->xhi[i] = take(CD * 4);
+    tc->xlo[i] = take(CD * 4);
+  }
+  tc->p = take(CD * 4);
+  tc->gL = take(CD * 4);
+  tc->lp_part = take(C * tc->ntn * 4);
+  tc->h0 = take(C * 4);
+  tc->err = reinterpret_cast<int*>(take(sizeof(int)));
+  bool ok = make_map(&tc->mBhi, tc->Phi, t.dim, t.dim, kBN) &&
+            make_map(&tc->mBlo, tc->Plo, t.dim, t.dim, kBN);
+  for (int i = 0; i < 2 && ok; ++i)
+    ok = make_map(&tc->mAhi[i], tc->xhi[i], C, t.dim, kBM) &&
+         make_map(&tc->mAlo[i], tc->xlo[i], C, t.dim, kBM);
+  if (!ok) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_gauss_tc_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSmemBytes));
+  if (e != cudaSuccess) return e;
+  k_split<<<blocks_for(DD), 256, 0, s>>>(static_cast<int64_t>(DD), t.P, tc->Phi, tc->Plo);
+  count_launch();
+  e = cudaMemsetAsync(tc->err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_tc_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
+                                       KernelTimer* timer) {
+  TcBeginAccept b{};
+  b.s = a;
+  b.p = tc.p;
+  b.gL = tc.gL;
+  b.lp_part = tc.lp_part;
+  b.h0 = tc.h0;
+  b.ntn = tc.ntn;
+  b.xhi = tc.xhi[0];
+  b.xlo = tc.xlo[0];
+  const unsigned nb = static_cast<unsigned>((a.C + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  k_gauss_tc_begin<<<nb, 32 * kWarpsPerBlock, 0, s>>>(b);
+  count_launch();
+  const dim3 grid((a.C + kBM - 1) / kBM, tc.ntn);
+  for (int l = 1; l <= a.L; ++l) {
+    TcStepArgs st{};
+    st.C = a.C;
+    st.D = a.D;
+    st.last = l == a.L;
+    const int in = (l - 1) & 1, out = l & 1;
+    st.xhi_in = tc.xhi[in];
+    st.xlo_in = tc.xlo[in];
+    st.xhi_out = tc.xhi[out];
+    st.xlo_out = tc.xlo[out];
+    st.p = tc.p;
+    st.g_out = tc.gL;
+    st.lp_part = tc.lp_part;
+    st.ntn = tc.ntn;
+    st.da = a.da;
+    st.err = tc.err;
+    if (timer) timer->begin(s);
+    k_gauss_tc_step<<<grid, kThreads, kSmemBytes, s>>>(tc.mAhi[in], tc.mAlo[in], tc.mBhi, tc.mBlo, st);
+    if (timer) timer->end(s);
+    count_launch();
+  }
+  b.xhi = tc.xhi[(a.L - 1) & 1];
+  b.xlo = tc.xlo[(a.L - 1) & 1];
+  k_gauss_tc_accept<<<nb, 32 * kWarpsPerBlock, 0, s>>>(b);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace hmc

@@ -164,4 +164,27 @@ __device__ __forceinline__ void block_partial_then_da(DAState* s, double* partia
   }
 }
 
+// Sum of one acceptance probability per warp of this block (warps with no
+// chain pass has_chain = false), in warp order, then the deterministic grid
+// reduction and dual-averaging update.
+template <int kWarps>
+__device__ __forceinline__ void accept_block_finish(DAState* da, double* partials, float prob,
+                                                    bool has_chain, int num_chains, long long t) {
+  __shared__ float warp_prob[kWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) warp_prob[w] = has_chain ? prob : 0.f;
+  __syncthreads();
+  double sum = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kWarps; ++i) sum += static_cast<double>(warp_prob[i]);
+  block_partial_then_da(da, partials, sum, num_chains, t);
+}
+
+// Split x into its tf32 head (10 explicit mantissa bits) and the exact float32
+// remainder: x = hi + lo exactly.  Used by the 3xTF32 products.
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  lo = x - hi;
+}
+
 }  // namespace hmc

@@ -107,3 +107,31 @@ cudaError_t launch_da_init(DAState* da, float eps0, int adapt, float delta, long
                            cudaStream_t s);
 
 }  // namespace hmc
+
+#include <cuda.h>
+
+namespace hmc {
+
+// Device buffers and TMA descriptors of the tensor-core Gaussian path.
+struct GaussTc {
+  CUtensorMap mAhi[2], mAlo[2], mBhi, mBlo;
+  float* Phi = nullptr;      // tf32 head / remainder of P
+  float* Plo = nullptr;
+  float* xhi[2] = {nullptr, nullptr};   // ping-pong trajectory positions
+  float* xlo[2] = {nullptr, nullptr};
+  float* p = nullptr;        // momentum
+  float* gL = nullptr;       // gradient at the end of the trajectory
+  float* lp_part = nullptr;  // [C x ntn]
+  float* h0 = nullptr;       // initial Hamiltonian
+  int* err = nullptr;        // device flag: a bounded wait gave up
+  int ntn = 0;
+};
+
+bool gauss_tc_supported(const hmc_target& t);
+size_t gauss_tc_workspace_bytes(const hmc_target& t, int64_t C);
+cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s);
+cudaError_t launch_gauss_tc_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
+                                       KernelTimer* timer);
+
+}  // namespace hmc
+

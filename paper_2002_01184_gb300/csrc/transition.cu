@@ -22,17 +22,8 @@ namespace {
 
 constexpr int kWarpsPerBlock = 8;
 
-// Sum of the per-warp acceptance probabilities of this block in warp order,
-// then the deterministic grid reduction and dual-averaging update.
 __device__ __forceinline__ void finish_block(const StepArgs& a, float prob, bool has_chain) {
-  __shared__ float warp_prob[kWarpsPerBlock];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) warp_prob[w] = has_chain ? prob : 0.f;
-  __syncthreads();
-  double sum = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < kWarpsPerBlock; ++i) sum += static_cast<double>(warp_prob[i]);
-  block_partial_then_da(a.da, a.partials, sum, a.C, a.t_full);
+  accept_block_finish<kWarpsPerBlock>(a.da, a.partials, prob, has_chain, a.C, a.t_full);
 }
 
 // ------------------------------------------------------ fused elementwise --

@@ -64,6 +64,7 @@ def _load():
                                      ctypes.POINTER(ctypes.c_uint64)],
         "hmc_target_log_prob_and_grad": [ctypes.POINTER(hmc_target), ctypes.c_int64, P, P, P, P,
                                          ctypes.c_uint64, P],
+        "hmc_synchronize": [P],
         "hmc_profile_dominant_kernel": [P, ctypes.c_int32],
         "hmc_profile_read": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
                              ctypes.POINTER(ctypes.c_uint64)],
@@ -77,6 +78,8 @@ def _load():
         f.restype = ctypes.c_int
     lib.hmc_last_error.argtypes = [P]
     lib.hmc_last_error.restype = ctypes.c_char_p
+    lib.hmc_uses_tensor_cores.argtypes = [P]
+    lib.hmc_uses_tensor_cores.restype = ctypes.c_int32
     lib.hmc_kernel_launch_count.argtypes = []
     lib.hmc_kernel_launch_count.restype = ctypes.c_uint64
     return lib
@@ -212,3 +215,11 @@ def hmc_profile_read(ctx):
     ms, n, launches = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
     _check(lib.hmc_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(launches)), ctx)
     return {"avg_ms": ms.value, "samples": int(n.value), "launches": int(launches.value)}
+
+
+def hmc_synchronize(ctx):
+    _check(lib.hmc_synchronize(ctx), ctx)
+
+
+def hmc_uses_tensor_cores(ctx):
+    return bool(lib.hmc_uses_tensor_cores(ctx))

@@ -1,0 +1,84 @@
+"""The tensor-core (tcgen05, 3xTF32) transition for the dense Gaussian
+target against the float64 oracle, teacher-forced transition by transition,
+on sizes that span several tiles with ragged edges in every dimension."""
+import numpy as np
+import pytest
+
+from oracle import hmc as ohmc, targets as otargets
+from paper_2002_01184_gb300 import workloads
+from tests.parity import compare_transition
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2002_01184_gb300 import build
+    build.build()
+    from paper_2002_01184_gb300 import hmc
+    return hmc
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+# (chains, dim, step size, leapfrog steps): one tile; ragged K/N/M tails;
+# several tiles in every direction; the full dimension of the workload
+CASES = [(128, 64, 0.1, 3), (130, 100, 0.08, 5), (257, 196, 0.06, 4), (512, 256, 0.05, 16),
+         (33, 32, 0.2, 1)]
+
+
+@pytest.mark.parametrize("C,D,eps,L", CASES)
+def test_tensor_core_transition_matches_oracle(H, C, D, eps, L):
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = workloads.corr_gauss(dim=D, num_chains=C, num_burnin=0, num_results=0, num_leapfrog=L)
+    p.step_size = eps
+    s = Sampler(p, adapt=False)
+    assert H.hmc_uses_tensor_cores(s.ctx)
+    x = torch.as_tensor(p.x0).cuda().contiguous()
+    s.bootstrap(x)
+    tgt = otargets.make("corr_gauss", P=p.P)
+    n_same = 0
+    for t in range(4):
+        xin = host(x).astype(np.float64)
+        lp, g = tgt(xin)
+        r = s.results(s.step(x, t))
+        H.hmc_synchronize(s.ctx)
+        ref = ohmc.one_step(xin, lp, g, np.float32(eps), L, p.seed, t, tgt)
+        a, _ = compare_transition(xin, host(x), host(r["is_accepted"]), host(r["log_accept_ratio"]),
+                                  ref, label=f"tc C={C} D={D} t={t}")
+        n_same += a
+        lp_new, g_new = tgt(host(x).astype(np.float64))
+        np.testing.assert_allclose(host(r["target_log_prob"]), lp_new, rtol=1e-4,
+                                   atol=1e-4 * max(1.0, np.abs(lp_new).max()))
+        gg = host(r["grad"])
+        row = np.max(np.abs(g_new), axis=1, keepdims=True)
+        assert np.max(np.abs(gg - g_new) / np.maximum(row, 1e-6)) < 1e-4
+    assert n_same >= 4 * C - 2
+    s.close()
+
+
+def test_tensor_core_and_plain_paths_agree(H):
+    """Same seeds through both implementations: identical accept decisions
+    (away from the decision band) and positions within the tolerance."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = workloads.corr_gauss(dim=64, num_chains=200, num_burnin=5, num_results=5, num_leapfrog=6)
+    outs = []
+    for impl in (H.HMC_IMPL_FUSED, H.HMC_IMPL_PLAIN):
+        s = Sampler(p, impl=impl)
+        x = torch.as_tensor(p.x0).cuda().contiguous()
+        samples, eps, acc = s.sample_chain(x, p.num_burnin, p.num_results)
+        outs.append((host(samples), host(eps), host(acc)))
+        s.close()
+    (s1, e1, a1), (s2, e2, a2) = outs
+    np.testing.assert_allclose(e1, e2, rtol=1e-5)
+    agree = (a1 == a2).mean()
+    assert agree > 0.99
+    same_rows = np.all(a1 == a2, axis=0)
+    np.testing.assert_allclose(s1[:, same_rows], s2[:, same_rows], rtol=1e-3, atol=1e-3)
