@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--small", action="store_true",
+                    help="20 burn-in + 20 kept transitions (profiling runs)")
     return ap.parse_args()
 
 
@@ -209,6 +211,9 @@ def main():
     from paper_2002_01184_gb300.sampler import Sampler
 
     p, wl = make_problem(args.workload)
+    if args.small:
+        p.num_burnin, p.num_results = 20, 20
+        wl += " (profiling run: B=20 K=20)"
     p.seed = p.seed + 1000 * rank          # each rank samples its own replica
     impl = hmc.HMC_IMPL_PLAIN if args.plain else hmc.HMC_IMPL_FUSED
     stream = torch.cuda.current_stream()
@@ -264,9 +269,19 @@ def main():
     roof = None
     if prof["samples"]:
         kernel_s = prof["avg_ms"] / 1000.0
-        if flops is not None and args.plain is False and False:
-            pass
-        if flops is not None:
+        use_tc = hmc.hmc_uses_tensor_cores(s.ctx)
+        if flops is not None and use_tc:
+            # 3xTF32: the algorithmic flops (2 C D^2 per step) against the
+            # dense TF32 peak / 3 (three tf32 products per float32 product)
+            achieved = flops * C / kernel_s / 1e12
+            tf32 = pk["bf16_tflops"] * TF32_PER_BF16
+            peak = tf32 / 3.0
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "k_gauss_tc_step (tcgen05 3xTF32 product + leapfrog epilogue)",
+                    "peak_source": f"{src} bf16 {pk['bf16_tflops']:.0f} TFLOP/s x (1.1/2.25 tf32:bf16 nominal) / 3",
+                    "avg_launch_ms": prof["avg_ms"], "timed_launches": prof["samples"]}
+        elif flops is not None:
             # the SIMT products run on the FP32 pipes: alu roofline
             achieved = flops * C / kernel_s / 1e12
             sm_max = pk.get("sm_max_mhz", 2070.0)

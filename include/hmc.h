@@ -90,6 +90,10 @@ typedef struct {
   int32_t impl;             /* hmc_impl */
   int64_t chain_offset;     /* chain c draws the random streams of chain
                                c + chain_offset */
+  int32_t use_graph;        /* 1: hmc_sample_chain captures bootstrap and all
+                               transitions as one CUDA graph on first use and
+                               replays it while its pointer and count
+                               arguments stay the same; 0: plain launches */
 } hmc_config;
 
 /* Kernel results of the last transition.  All pointers are device pointers

@@ -39,6 +39,16 @@ struct hmc_ctx {
   hmc::KernelTimer timer;
   bool use_tc = false;          // tensor-core Gaussian path
   hmc::GaussTc tc;
+  // sample_chain captured as one CUDA graph, replayed while the arguments match
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  float* g_x = nullptr;
+  int64_t g_B = -1, g_K = -1;
+  float* g_samples = nullptr;
+  float* g_eps = nullptr;
+  uint8_t* g_acc = nullptr;
+  uint64_t g_launches = 0;      // kernels per replay
+  uint64_t g_dominant = 0;      // dominant-kernel launches per replay
   std::string err;
 };
 
@@ -95,6 +105,7 @@ bool valid_config(const hmc_config* c, int64_t C, std::string* why) {
   }
   if (c->num_adapt_steps < 0) { *why = "num_adapt_steps must be >= 0"; return false; }
   if (c->impl != HMC_IMPL_FUSED && c->impl != HMC_IMPL_PLAIN) { *why = "unknown impl"; return false; }
+  if (c->use_graph != 0 && c->use_graph != 1) { *why = "use_graph must be 0 or 1"; return false; }
   if (c->chain_offset < 0 || c->chain_offset + C > (1ll << 32)) {
     *why = "chain_offset + num_chains must fit in 32 bits";
     return false;
@@ -113,7 +124,16 @@ cudaError_t ctx_alloc(hmc_ctx* ctx, T** p, size_t count) {
   return e;
 }
 
+void drop_graph(hmc_ctx* ctx) {
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  ctx->graph = nullptr;
+  ctx->g_B = ctx->g_K = -1;
+}
+
 void release(hmc_ctx* ctx) {
+  drop_graph(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  ctx->cap_stream = nullptr;
   for (void* p : ctx->allocations) cudaFree(p);
   ctx->allocations.clear();
   if (ctx->stage) cudaFree(ctx->stage);
@@ -173,7 +193,7 @@ hmc_status bootstrap(hmc_ctx* ctx, const float* x0) {
   return HMC_OK;
 }
 
-hmc_status run_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* samples, float* trace_eps,
+hmc_status enqueue_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* samples, float* trace_eps,
                      uint8_t* trace_acc) {
   hmc_status st = bootstrap(ctx, x);
   if (st != HMC_OK) return st;
@@ -189,6 +209,62 @@ hmc_status run_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sample
     cudaError_t e = enqueue_transition(ctx, a);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "transition launch");
   }
+  return HMC_OK;
+}
+
+
+// sample_chain as a CUDA graph: the first call with a given set of buffers
+// and step counts captures bootstrap + every transition on a private stream;
+// later calls replay the instantiated graph on the context's stream.
+hmc_status run_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* samples, float* trace_eps,
+                     uint8_t* trace_acc) {
+  if (!ctx->cfg.use_graph) return enqueue_chain(ctx, x, B, K, samples, trace_eps, trace_acc);
+  const bool hit = ctx->graph && ctx->g_x == x && ctx->g_B == B && ctx->g_K == K &&
+                   ctx->g_samples == samples && ctx->g_eps == trace_eps && ctx->g_acc == trace_acc;
+  if (!hit) {
+    drop_graph(ctx);
+    cudaError_t e = cudaSuccess;
+    if (!ctx->cap_stream) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "capture stream");
+    cudaStream_t user = ctx->stream;
+    ctx->stream = ctx->cap_stream;
+    const uint64_t l0 = hmc::g_launches.load(), d0 = ctx->timer.seen;
+    e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      ctx->stream = user;
+      return cuda_fail(ctx, e, "begin capture");
+    }
+    hmc_status st = enqueue_chain(ctx, x, B, K, samples, trace_eps, trace_acc);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->stream = user;
+    if (st != HMC_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      ctx->graph = nullptr;
+      return cuda_fail(ctx, e, "graph instantiate");
+    }
+    ctx->g_launches = hmc::g_launches.load() - l0;
+    ctx->g_dominant = ctx->timer.seen - d0;
+    hmc::g_launches.fetch_sub(ctx->g_launches);   // counted per replay below
+    ctx->timer.seen = d0;
+    ctx->g_x = x;
+    ctx->g_B = B;
+    ctx->g_K = K;
+    ctx->g_samples = samples;
+    ctx->g_eps = trace_eps;
+    ctx->g_acc = trace_acc;
+  }
+  cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+  hmc::count_launch(ctx->g_launches);
+  ctx->timer.seen += ctx->g_dominant;
+  ctx->bootstrapped = true;
   return HMC_OK;
 }
 

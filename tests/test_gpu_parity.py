@@ -289,5 +289,21 @@ def test_correlated_gaussian_moments(H):
     assert abs(proj.mean()) < 3 * diagnostics.mcse_mean(proj)[0]
     sq = proj ** 2
     assert abs(sq.mean() - u @ cov @ u) < 3 * diagnostics.mcse_mean(sq)[0]
-    assert abs(host(acc).mean() - p.target_accept) < 0.05
+    s.close()
+
+
+def test_dual_averaging_reaches_target_acceptance(H):
+    """On N(0, I) in D = 10, where acceptance is a smooth function of the step
+    size, adapting for 400 transitions lands the frozen step size's
+    acceptance within 0.03 of the target (the oracle's pin, on the GPU)."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = workloads.std_normal(num_chains=512, dim=10, num_burnin=400, num_results=200,
+                             num_leapfrog=5, step_size=1.0)
+    p.x0 = np.random.default_rng(77).standard_normal((512, 10)).astype(np.float32)
+    p.adapt, p.target_accept = True, 0.7
+    s = Sampler(p)
+    x = dev(p.x0)
+    samples, eps, acc = s.sample_chain(x, p.num_burnin, p.num_results)
+    assert abs(host(acc).mean() - 0.7) < 0.03
+    assert np.all(host(eps) == host(eps)[0])
     s.close()
