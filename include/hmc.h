@@ -167,7 +167,10 @@ int32_t hmc_uses_tensor_cores(const hmc_ctx* ctx);
  * every `sample_every` of the context's dominant kernel -- the fused
  * transition kernel, or the target-gradient product(s) of the plain path --
  * with CUDA events on the context's stream.  0 disables.  Synchronises the
- * stream and resets the counters. */
+ * stream and resets the counters.  A sample_chain graph records the events
+ * of the setting it was captured with: changing sample_every drops the graph
+ * (the next hmc_sample_chain captures again); calling again with the same
+ * value only resets the counters. */
 hmc_status hmc_profile_dominant_kernel(hmc_ctx* ctx, int32_t sample_every);
 
 /* Average duration (ms) of the timed launches since the last reset, how many

@@ -49,6 +49,7 @@ struct hmc_ctx {
   uint8_t* g_acc = nullptr;
   uint64_t g_launches = 0;      // kernels per replay
   uint64_t g_dominant = 0;      // dominant-kernel launches per replay
+  uint64_t g_recorded = 0;      // timed event pairs inside the graph
   std::string err;
 };
 
@@ -251,6 +252,7 @@ hmc_status run_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sample
     }
     ctx->g_launches = hmc::g_launches.load() - l0;
     ctx->g_dominant = ctx->timer.seen - d0;
+    ctx->g_recorded = ctx->timer.recorded;
     hmc::g_launches.fetch_sub(ctx->g_launches);   // counted per replay below
     ctx->timer.seen = d0;
     ctx->g_x = x;
@@ -264,6 +266,8 @@ hmc_status run_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sample
   if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
   hmc::count_launch(ctx->g_launches);
   ctx->timer.seen += ctx->g_dominant;
+  // every replay re-records the event pairs captured in the graph
+  ctx->timer.recorded = std::max(ctx->timer.recorded, ctx->g_recorded);
   ctx->bootstrapped = true;
   return HMC_OK;
 }
@@ -443,6 +447,8 @@ hmc_status hmc_profile_dominant_kernel(hmc_ctx* ctx, int32_t sample_every) {
   if (sample_every < 0) return fail(ctx, HMC_E_INVALID, "sample_every must be >= 0");
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "profile reset");
+  // a captured graph holds the event records of the setting it was captured with
+  if (sample_every != ctx->timer.every) drop_graph(ctx);
   ctx->timer.every = sample_every;
   ctx->timer.seen = 0;
   ctx->timer.recorded = 0;

@@ -43,6 +43,7 @@ constexpr uint32_t kABytes = kBM * kBK * 4;                  // 16 KB
 constexpr uint32_t kBBytes = kBN * kBK * 4;                  // 8 KB
 constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;  // 48 KB
 constexpr size_t kSmemBytes = kStages * kStageBytes + 1024 + 256;
+static_assert(kBM * (kBN + 1) * 4 <= kStages * kStageBytes, "epilogue staging must fit the ring");
 
 struct TcStepArgs {
   int C, D;
@@ -136,44 +137,67 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
     }
     ptx::mma_commit(acc_full);
   } else if (warp >= 2) {
-    // ---- epilogue: thread owns one chain row of the tile
+    // ---- epilogue.  (1) each warp moves its 32 TMEM lanes (tile rows) into a
+    // padded shared-memory tile -- the pipeline's stage buffers are free once
+    // the last MMA has completed; (2) the four warps walk the tile row by row
+    // with lanes along the columns, so every global access is a coalesced
+    // 128-byte row segment.
     const bool ok = ptx::mbar_wait(acc_full, 0);
     if (!ok) atomicExch(a.err, 1);
     ptx::tc_fence_after();
     const int quarter = warp & 3;
-    const int r = quarter * 32 + lane;
-    const int m = m0 + r;
-    const bool row_ok = ok && m < a.C;
-    const float eps = a.da->eps;
-    const int64_t rowoff = static_cast<int64_t>(m) * a.D;
-    float part = 0.f;
-#pragma unroll 1
+    float* stg = reinterpret_cast<float*>(smem);
+    constexpr int kLd = kBN + 1;
+#pragma unroll
     for (int c0 = 0; c0 < kBN; c0 += 16) {
       float acc[16];
       ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + c0, acc);
-      if (!row_ok) continue;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int n = n0 + c0 + j;
-        if (n >= a.D) break;
-        const int64_t e = rowoff + n;
-        const float g = -acc[j];
-        const float x = a.xhi_in[e] + a.xlo_in[e];
-        if (!a.last) {
-          const float p = fmaf(eps, g, a.p[e]);
-          a.p[e] = p;
-          float hi, lo;
-          split_tf32(fmaf(eps, p, x), hi, lo);
-          a.xhi_out[e] = hi;
-          a.xlo_out[e] = lo;
-        } else {
-          a.p[e] = fmaf(0.5f * eps, g, a.p[e]);
-          a.g_out[e] = g;
-          part = fmaf(x, g, part);
+      for (int j = 0; j < 16; ++j) stg[(quarter * 32 + lane) * kLd + c0 + j] = acc[j];
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    const float eps = a.da->eps;
+    const float* __restrict__ xhi_in = a.xhi_in;
+    const float* __restrict__ xlo_in = a.xlo_in;
+    float* __restrict__ xhi_out = a.xhi_out;
+    float* __restrict__ xlo_out = a.xlo_out;
+    float* __restrict__ pm = a.p;
+    float* __restrict__ g_out = a.g_out;
+    const int ew = warp - 2;
+#pragma unroll 4
+    for (int rr = 0; rr < kBM / 4; ++rr) {
+      const int r = ew + 4 * rr;
+      const int m = m0 + r;
+      if (!ok || m >= a.C) continue;                  // warp-uniform
+      const int64_t rowoff = static_cast<int64_t>(m) * a.D;
+      float part = 0.f;
+#pragma unroll
+      for (int h = 0; h < kBN / 32; ++h) {
+        const int cl = lane + 32 * h;
+        const int n = n0 + cl;
+        if (n < a.D) {
+          const int64_t e = rowoff + n;
+          const float g = -stg[r * kLd + cl];
+          const float x = xhi_in[e] + xlo_in[e];
+          if (!a.last) {
+            const float p = fmaf(eps, g, pm[e]);
+            pm[e] = p;
+            float hi, lo;
+            split_tf32(fmaf(eps, p, x), hi, lo);
+            xhi_out[e] = hi;
+            xlo_out[e] = lo;
+          } else {
+            pm[e] = fmaf(0.5f * eps, g, pm[e]);
+            g_out[e] = g;
+            part = fmaf(x, g, part);
+          }
         }
       }
+      if (a.last) {
+        part = warp_sum(part);
+        if (lane == 0) a.lp_part[static_cast<int64_t>(m) * a.ntn + blockIdx.y] = 0.5f * part;
+      }
     }
-    if (a.last && row_ok) a.lp_part[static_cast<int64_t>(m) * a.ntn + blockIdx.y] = 0.5f * part;
   }
   ptx::tc_fence_before();
   __syncthreads();

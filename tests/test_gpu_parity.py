@@ -170,7 +170,8 @@ def test_dual_averaging_replays_oracle(H):
     x = dev(p.x0)
     s.bootstrap(x)
     tgt = otargets.make("corr_gauss", P=p.P)
-    da = ohmc.DualAveraging(np.float32(p.step_size), p.target_accept)
+    # the library receives the step size and the target as float32
+    da = ohmc.DualAveraging(float(np.float32(p.step_size)), float(np.float32(p.target_accept)))
     eps_used = np.float32(p.step_size)
     for t in range(p.num_burnin + 3):
         xin = host(x).astype(np.float64)
