@@ -140,6 +140,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_over_ranks(ms, units, device=None):
+    """Whole-job throughput of weakly scaled replicas: the slowest rank's time
+    and the units summed over ranks (each rank runs its own replica)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, units
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -249,16 +263,17 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    ms = e0.elapsed_time(e1)
+    ms_local = e0.elapsed_time(e1)
     launches = hmc.hmc_kernel_launch_count() - launches0
-    prof = hmc.hmc_profile_read(s.ctx)
+    try:
+        prof = hmc.hmc_profile_read(s.ctx)
+    except hmc.HMCError as exc:              # timing support only
+        print(f"dominant-kernel timing unavailable: {exc}", file=sys.stderr)
+        prof = {"avg_ms": 0.0, "samples": 0, "launches": 0}
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, total_evals = reduce_over_ranks(ms_local, evals_per_step * args.steps, device="cuda")
     ms_per_step = ms / args.steps
-    value = world * evals_per_step * args.steps / (ms / 1000.0)
+    value = total_evals / (ms / 1000.0)
 
     # min-ESS/s of the last step's kept draws (not timed)
     ess = diagnostics.ess(samples, max_dims=64)

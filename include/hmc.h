@@ -4,10 +4,10 @@
  * The method is the HMC transition kernel and sample_chain driver of
  * "tfp.mcmc: Modern Markov Chain Monte Carlo Tools Built for Modern Hardware"
  * (Lao et al., 2020): thousands of independent chains advance in lockstep
- * (Section 3, "Pervasive Data Parallelism"); each transition draws one
+ * (Section 2, "Pervasive Data Parallelism"); each transition draws one
  * momentum per state variable per chain, runs a fixed number of leapfrog steps
  * with the step size broadcast over the state, and accepts or rejects every
- * chain by Metropolis-Hastings with a per-chain select (Section 3.1).  A
+ * chain by Metropolis-Hastings with a per-chain select (Section 2.1).  A
  * transition consumes and produces (state, kernel results) of fixed structure,
  * and the kernel results cache the target log-prob and gradient of the
  * accepted state (Section 4.1, one_step / bootstrap_results).  The driver runs
@@ -26,7 +26,7 @@
  *     the last error of a context is available from hmc_last_error.
  *   - Results depend only on (seed, chain index + chain_offset, transition
  *     index) and the chain's own state: never on the number of chains or on
- *     the other chains in the batch (Section 3's batch semantics).
+ *     the other chains in the batch (Section 2's batch semantics).
  */
 #ifndef HMC_H_
 #define HMC_H_
@@ -195,7 +195,7 @@ hmc_status hmc_grad_workspace_bytes(const hmc_target* target, int64_t num_chains
 /* Target log-prob and gradient for `num_chains` states x [chains x dim]
  * (device) into lp [chains] and grad [chains x dim] (device, caller-owned),
  * enqueued on `cuda_stream`.  This is the batched target evaluation of
- * Section 3.1 ("list of vectors", one row per chain) and the adjoint used by
+ * Section 2.1 ("list of vectors", one row per chain) and the adjoint used by
  * the autograd binding: the vector-Jacobian product of log p with upstream
  * weights w is w_c * grad[c].  `workspace` is caller-owned device scratch of
  * at least hmc_grad_workspace_bytes bytes, 256-byte aligned (may be NULL when
@@ -206,6 +206,22 @@ hmc_status hmc_target_log_prob_and_grad(const hmc_target* target, int64_t num_ch
                                         void* workspace, uint64_t workspace_bytes,
                                         void* cuda_stream);
 
+/* Workspace for hmc_target_vjp: the gradient's scratch plus one float per
+ * chain. */
+hmc_status hmc_target_vjp_workspace_bytes(const hmc_target* target, int64_t num_chains,
+                                          uint64_t* bytes);
+
+/* Vector-Jacobian product of the batched log-density (the adjoint behind the
+ * autograd binding; the paper obtains gradients by automatic differentiation,
+ * Section 3 and its footnote on TF autodiff): dx[c, :] = w[c] * grad log p(x_c)
+ * for x, dx [chains x dim] and w [chains] (device, caller-owned).  The forward
+ * pass is recomputed, nothing from it is stored.  `workspace` (device,
+ * 256-byte aligned, >= hmc_target_vjp_workspace_bytes) is caller-owned.
+ * HMC_E_INVALID on bad sizes, pointers or workspace. */
+hmc_status hmc_target_vjp(const hmc_target* target, int64_t num_chains, const float* x,
+                          const float* w, float* dx, void* workspace, uint64_t workspace_bytes,
+                          void* cuda_stream);
+
 /* The counter-based generator behind every random draw (the paper names
  * none; this is Philox4x32-10 of Salmon, Moraes, Dror and Shaw, SC'11):
  * out[4i..4i+3] = Philox4x32-10(counters[4i..4i+3], key = (seed lo32,
@@ -214,7 +230,7 @@ hmc_status hmc_target_log_prob_and_grad(const hmc_target* target, int64_t num_ch
 hmc_status hmc_philox4x32_10(const uint32_t* counters, int64_t n, uint64_t seed, uint32_t* out,
                              void* cuda_stream);
 
-/* The momentum draw of one transition (Section 3.1: one independent N(0,1)
+/* The momentum draw of one transition (Section 2.1: one independent N(0,1)
  * momentum per state variable per chain): out [chains x dim] (device) for
  * chains chain_offset .. chain_offset + num_chains - 1 at transition t. */
 hmc_status hmc_momentum(uint64_t seed, uint64_t t, int64_t num_chains, int32_t dim,

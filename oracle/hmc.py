@@ -3,7 +3,7 @@ describes it.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Section 3.1 ("Case Study: HMC"): draw one momentum per state variable per
+Section 2.1 ("Case Study: HMC"): draw one momentum per state variable per
 chain, run a symplectic integrator for a fixed number of steps with the step
 size broadcast over the state, then accept or reject by Metropolis-Hastings
 with a per-chain select (the paper's tf.where, never a branch over chains).
@@ -68,7 +68,7 @@ def hamiltonian(lp, p):
 
 
 def one_step(x, lp, g, eps, num_leapfrog, seed, t, target, chain_offset=0):
-    """One HMC transition for every chain (Section 3.1 and Section 4.1).
+    """One HMC transition for every chain (Section 2.1 and Section 4.1).
 
     ``(x, lp, g)`` is the current state with its cached log-prob and gradient.
     ``eps`` is a scalar step size broadcast over the state.  Random numbers

@@ -5,7 +5,7 @@ only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may use it.
 
 The paper's HMC kernel draws "one independent momentum per state variable per
-chain" (Section 3.1, "Case Study: HMC") and a uniform for the
+chain" (Section 2.1, "Case Study: HMC") and a uniform for the
 Metropolis-Hastings test, but names no generator.  Both this oracle and the
 CUDA path implement the same counter-based generator, Philox4x32 with 10
 rounds, from its published definition (Salmon, Moraes, Dror and Shaw,

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Every function follows the paper's "batch semantics" (Section 3, the
+Every function follows the paper's "batch semantics" (Section 2, the
 batch-friendly target log-prob listing): the leading axis indexes chains and
 only the event axis is reduced, so chain i's value never depends on chain j.
 Log-densities are given up to an additive constant, which cancels in the

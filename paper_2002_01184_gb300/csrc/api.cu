@@ -513,6 +513,35 @@ hmc_status hmc_target_log_prob_and_grad(const hmc_target* target, int64_t num_ch
   return HMC_OK;
 }
 
+hmc_status hmc_target_vjp_workspace_bytes(const hmc_target* target, int64_t num_chains,
+                                          uint64_t* bytes) {
+  uint64_t g = 0;
+  hmc_status st = hmc_grad_workspace_bytes(target, num_chains, &g);
+  if (st != HMC_OK) return st;
+  *bytes = ((g + 255) & ~static_cast<uint64_t>(255)) + static_cast<uint64_t>(num_chains) * 4;
+  return HMC_OK;
+}
+
+hmc_status hmc_target_vjp(const hmc_target* target, int64_t num_chains, const float* x,
+                          const float* w, float* dx, void* workspace, uint64_t workspace_bytes,
+                          void* cuda_stream) {
+  uint64_t need = 0;
+  hmc_status st = hmc_target_vjp_workspace_bytes(target, num_chains, &need);
+  if (st != HMC_OK) return st;
+  if (!x || !w || !dx) return fail(nullptr, HMC_E_INVALID, "x, w and dx must be non-NULL");
+  if (!workspace || workspace_bytes < need)
+    return fail(nullptr, HMC_E_INVALID, "workspace smaller than hmc_target_vjp_workspace_bytes");
+  if (reinterpret_cast<uintptr_t>(workspace) & 255u)
+    return fail(nullptr, HMC_E_INVALID, "workspace must be 256-byte aligned");
+  const size_t gbytes = hmc::grad_workspace_bytes(*target, num_chains);
+  char* base = static_cast<char*>(workspace);
+  float* lp_tmp = reinterpret_cast<float*>(base + ((gbytes + 255) & ~static_cast<size_t>(255)));
+  cudaError_t e = hmc::launch_vjp(*target, num_chains, x, w, dx, lp_tmp, base,
+                                  static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "vjp launch");
+  return HMC_OK;
+}
+
 hmc_status hmc_philox4x32_10(const uint32_t* counters, int64_t n, uint64_t seed, uint32_t* out,
                              void* cuda_stream) {
   if (n < 0 || (n > 0 && (!counters || !out)))

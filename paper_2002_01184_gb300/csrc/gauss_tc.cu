@@ -1,6 +1,6 @@
 // Dense Gaussian target on the tcgen05 tensor cores: each leapfrog step is
 // one launch that computes a 128-chain x 64-column tile of the gradient
-// G = -X P (a C x D x D product, Section 3.1's batched "list of vectors"
+// G = -X P (a C x D x D product, Section 2.1's batched "list of vectors"
 // evaluation) in 3xTF32 -- A_lo B_hi + A_hi B_lo + A_hi B_hi, float32
 // accumulation in tensor memory -- and applies the leapfrog update to the
 // same tile in its epilogue, so the gradient never goes to HBM.

@@ -10,7 +10,7 @@ namespace hmc {
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11).  The paper draws "one
-// independent momentum per state variable per chain" (Section 3.1) but names
+// independent momentum per state variable per chain" (Section 2.1) but names
 // no generator; a counter-based one needs no state in HBM and makes every
 // draw a pure function of (seed, chain, transition, stream tag).
 //   key     = (seed lo32, seed hi32)

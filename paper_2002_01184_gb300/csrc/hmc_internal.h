@@ -3,6 +3,7 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "hmc.h"
@@ -32,20 +33,32 @@ struct KernelTimer {
       if (cudaEventCreate(&ev[2 * k]) != cudaSuccess) return false;
       if (cudaEventCreate(&ev[2 * k + 1]) != cudaSuccess) return false;
     }
-    pending = cudaEventRecord(ev[2 * k], s) == cudaSuccess;
+    pending = record(ev[2 * k], s);
     return pending;
   }
   void end(cudaStream_t s) {
     if (!pending) return;
-    cudaEventRecord(ev[2 * (recorded % kPairs) + 1], s);
+    record(ev[2 * (recorded % kPairs) + 1], s);
     ++recorded;
     pending = false;
+  }
+  // Inside a stream capture a plain event record is only a dependency marker;
+  // the external flag makes it a real event-record node of the graph.
+  static bool record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return false;
+    const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    return cudaEventRecordWithFlags(e, s, flags) == cudaSuccess;
   }
   void destroy() {
     for (auto& e : ev)
       if (e) { cudaEventDestroy(e); e = nullptr; }
   }
 };
+
+// dx = w[c] * grad log p(x_c) per row; lp_tmp [C] receives log p.
+cudaError_t launch_vjp(const hmc_target& t, int64_t C, const float* x, const float* w, float* dx,
+                       float* lp_tmp, void* ws, cudaStream_t s);
 
 // Bytes of scratch the batched gradient of `t` needs for C chains.
 size_t grad_workspace_bytes(const hmc_target& t, int64_t C);

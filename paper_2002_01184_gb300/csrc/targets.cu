@@ -1,5 +1,5 @@
 // Batched target log-prob and gradient kernels ("list of vectors" evaluation,
-// Section 3.1): every chain is one row, only the event axis is reduced, so a
+// Section 2.1): every chain is one row, only the event axis is reduced, so a
 // chain's result never depends on another chain's.
 //
 //   STD_NORMAL  lp = -|x|^2/2, g = -x                      (warp per chain)
@@ -259,7 +259,26 @@ inline unsigned warps_grid(int64_t C, int warps_per_block) {
   return static_cast<unsigned>((C + warps_per_block - 1) / warps_per_block);
 }
 
+// dx[c, :] = w[c] * g[c, :]   (vector-Jacobian product of log p)
+__global__ void k_scale_rows(int C, int D, const float* __restrict__ w, float* __restrict__ g) {
+  const int64_t n = static_cast<int64_t>(C) * D;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    g[i] *= w[i / D];
+}
+
 }  // namespace
+
+cudaError_t launch_vjp(const hmc_target& t, int64_t C, const float* x, const float* w, float* dx,
+                       float* lp_tmp, void* ws, cudaStream_t s) {
+  cudaError_t e = launch_grad(t, C, x, lp_tmp, dx, ws, s);
+  if (e != cudaSuccess) return e;
+  const int64_t n = C * t.dim;
+  k_scale_rows<<<static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 152 * 16)), 256, 0, s>>>(
+      static_cast<int>(C), t.dim, w, dx);
+  count_launch();
+  return cudaGetLastError();
+}
 
 size_t grad_workspace_bytes(const hmc_target& t, int64_t C) {
   if (t.id == HMC_T_LOGREG) return logreg_plan(C, t.dim, t.n_data).bytes;

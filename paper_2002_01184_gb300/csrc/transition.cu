@@ -1,4 +1,4 @@
-// HMC transition kernels (Section 3.1): momentum draw, leapfrog, energy,
+// HMC transition kernels (Section 2.1): momentum draw, leapfrog, energy,
 // Metropolis-Hastings select and the dual-averaging update.
 //
 // Fused path for targets whose gradient is elementwise plus row reductions

@@ -66,6 +66,10 @@ def _load():
         "hmc_target_log_prob_and_grad": [ctypes.POINTER(hmc_target), ctypes.c_int64, P, P, P, P,
                                          ctypes.c_uint64, P],
         "hmc_synchronize": [P],
+        "hmc_target_vjp_workspace_bytes": [ctypes.POINTER(hmc_target), ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_uint64)],
+        "hmc_target_vjp": [ctypes.POINTER(hmc_target), ctypes.c_int64, P, P, P, P, ctypes.c_uint64,
+                           P],
         "hmc_profile_dominant_kernel": [P, ctypes.c_int32],
         "hmc_profile_read": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
                              ctypes.POINTER(ctypes.c_uint64)],
@@ -224,3 +228,14 @@ def hmc_synchronize(ctx):
 
 def hmc_uses_tensor_cores(ctx):
     return bool(lib.hmc_uses_tensor_cores(ctx))
+
+
+def hmc_target_vjp_workspace_bytes(target, num_chains):
+    b = ctypes.c_uint64()
+    _check(lib.hmc_target_vjp_workspace_bytes(ctypes.byref(target), int(num_chains), ctypes.byref(b)))
+    return int(b.value)
+
+
+def hmc_target_vjp(target, num_chains, x, w, dx, workspace, workspace_bytes, stream=None):
+    _check(lib.hmc_target_vjp(ctypes.byref(target), int(num_chains), _ptr(x), _ptr(w), _ptr(dx),
+                              _ptr(workspace), int(workspace_bytes), _stream(stream)))

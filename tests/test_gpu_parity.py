@@ -197,7 +197,7 @@ def test_dual_averaging_replays_oracle(H):
                                      ("corr_gauss", dict(C=40, D=30, eps=0.1, L=6)),
                                      ("logreg", dict(C=40, D=12, N=200, eps=0.02, L=4))])
 def test_chain_isolation_is_bitwise(H, kind, kw):
-    """Section 3's batch semantics: a chain's trajectory is the same bit for
+    """Section 2's batch semantics: a chain's trajectory is the same bit for
     bit whether it runs alone (with its chain offset) or among 40 chains."""
     from paper_2002_01184_gb300.sampler import Sampler
     p = small_problem(kind, **kw)
