@@ -222,6 +222,27 @@ hmc_status hmc_target_vjp(const hmc_target* target, int64_t num_chains, const fl
                           const float* w, float* dx, void* workspace, uint64_t workspace_bytes,
                           void* cuda_stream);
 
+/* Same as hmc_target_log_prob_and_grad, for callers that cannot allocate
+ * device memory at all (no counterpart in the paper).  Some callers must not
+ * call cudaMalloc when they evaluate a gradient: a host process that owns the
+ * whole device-memory budget (e.g. a sampling server that reserves HBM up
+ * front for every admitted job's resident chain state), or a latency-critical
+ * loop where cudaMalloc's implicit synchronisation would stall other streams.
+ * This entry point takes its scratch from a fixed 64 MiB array inside the
+ * library's device image (held on every GPU that loads the library until the
+ * process exits) and calls no allocating routine.  The caller passes inputs
+ * and outputs only, as in hmc_target_log_prob_and_grad.
+ *   - The first call on a device resolves the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Requests needing more scratch than 64 MiB (LOGREG with a large
+ *     chains x n_data) return HMC_E_INVALID with the sizes in the error text.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     nothing in it must start at zero, but calls whose kernels overlap on
+ *     the GPU race on it: serialise them (one stream, or events). */
+hmc_status hmc_target_log_prob_and_grad_noalloc(const hmc_target* target, int64_t num_chains,
+                                                const float* x, float* lp, float* grad,
+                                                void* cuda_stream);
+
 /* The counter-based generator behind every random draw (the paper names
  * none; this is Philox4x32-10 of Salmon, Moraes, Dror and Shaw, SC'11):
  * out[4i..4i+3] = Philox4x32-10(counters[4i..4i+3], key = (seed lo32,

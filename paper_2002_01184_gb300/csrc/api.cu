@@ -274,6 +274,10 @@ hmc_status run_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sample
 
 }  // namespace
 
+namespace hmc {
+void set_global_error(const std::string& msg) { g_global_err = msg; }
+}  // namespace hmc
+
 extern "C" {
 
 hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_config* config,

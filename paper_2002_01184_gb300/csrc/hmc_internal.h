@@ -60,6 +60,9 @@ struct KernelTimer {
 cudaError_t launch_vjp(const hmc_target& t, int64_t C, const float* x, const float* w, float* dx,
                        float* lp_tmp, void* ws, cudaStream_t s);
 
+// Set the error text that hmc_last_error(NULL) returns on this thread.
+void set_global_error(const std::string& msg);
+
 // Bytes of scratch the batched gradient of `t` needs for C chains.
 size_t grad_workspace_bytes(const hmc_target& t, int64_t C);
 

@@ -70,6 +70,8 @@ def _load():
                                            ctypes.POINTER(ctypes.c_uint64)],
         "hmc_target_vjp": [ctypes.POINTER(hmc_target), ctypes.c_int64, P, P, P, P, ctypes.c_uint64,
                            P],
+        "hmc_target_log_prob_and_grad_noalloc": [ctypes.POINTER(hmc_target), ctypes.c_int64, P, P,
+                                                 P, P],
         "hmc_profile_dominant_kernel": [P, ctypes.c_int32],
         "hmc_profile_read": [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64),
                              ctypes.POINTER(ctypes.c_uint64)],
@@ -228,6 +230,13 @@ def hmc_synchronize(ctx):
 
 def hmc_uses_tensor_cores(ctx):
     return bool(lib.hmc_uses_tensor_cores(ctx))
+
+
+def hmc_target_log_prob_and_grad_noalloc(target, num_chains, x, lp, grad, stream=None):
+    """Gradient for callers that cannot allocate: scratch comes from a fixed
+    64 MiB array inside the library (see include/hmc.h)."""
+    _check(lib.hmc_target_log_prob_and_grad_noalloc(ctypes.byref(target), int(num_chains), _ptr(x),
+                                                    _ptr(lp), _ptr(grad), _stream(stream)))
 
 
 def hmc_target_vjp_workspace_bytes(target, num_chains):
