@@ -282,38 +282,37 @@ def main():
 
     pk, src = peaks()
     flops = grad_flops_per_eval(p)
+    kname, evals_per_launch = hmc.hmc_dominant_kernel_info(s.ctx)
     roof = None
     if prof["samples"]:
         kernel_s = prof["avg_ms"] / 1000.0
-        use_tc = hmc.hmc_uses_tensor_cores(s.ctx)
-        if flops is not None and use_tc:
-            # 3xTF32: the algorithmic flops (2 C D^2 per step) against the
-            # dense TF32 peak / 3 (three tf32 products per float32 product)
-            achieved = flops * C / kernel_s / 1e12
-            tf32 = pk["bf16_tflops"] * TF32_PER_BF16
-            peak = tf32 / 3.0
+        common = {"kernel": kname, "avg_launch_ms": prof["avg_ms"],
+                  "timed_launches": prof["samples"], "grad_evals_per_launch": evals_per_launch}
+        if flops is not None and hmc.hmc_uses_tensor_cores(s.ctx):
+            # 3xTF32: algorithmic flops (2 D^2 per gradient evaluation) against
+            # the dense TF32 peak / 3 (three tf32 products per float32 product)
+            achieved = flops * evals_per_launch / kernel_s / 1e12
+            peak = pk["bf16_tflops"] * TF32_PER_BF16 / 3.0
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
-                    "kernel": "k_gauss_tc_step (tcgen05 3xTF32 product + leapfrog epilogue)",
-                    "peak_source": f"{src} bf16 {pk['bf16_tflops']:.0f} TFLOP/s x (1.1/2.25 tf32:bf16 nominal) / 3",
-                    "avg_launch_ms": prof["avg_ms"], "timed_launches": prof["samples"]}
+                    "peak_source": f"{src} bf16 {pk['bf16_tflops']:.0f} TFLOP/s x (1.1/2.25 nominal tf32:bf16) / 3",
+                    **common}
         elif flops is not None:
-            # the SIMT products run on the FP32 pipes: alu roofline
-            achieved = flops * C / kernel_s / 1e12
+            # SIMT float32 products: FP32-pipe roofline from unit counts and clock
+            achieved = flops * evals_per_launch / kernel_s / 1e12
             sm_max = pk.get("sm_max_mhz", 2070.0)
             peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None,
-                    "kernel": "target-gradient product (SIMT fp32)",
                     "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
-                    "avg_launch_ms": prof["avg_ms"], "timed_launches": prof["samples"]}
+                    **common}
         else:
-            bytes_per_launch = 3 * 4.0 * C * D * 2  # x, g read + written (fused elementwise)
+            # fused elementwise transition: x and g read and written once per chain row
+            bytes_per_launch = 4.0 * 4 * C * D
             achieved = bytes_per_launch / kernel_s / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                    "kernel": "fused elementwise transition", "peak_source": src,
-                    "avg_launch_ms": prof["avg_ms"], "timed_launches": prof["samples"]}
+                    "peak_source": src, **common}
 
     e2e = None
     if not args.no_e2e:

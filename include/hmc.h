@@ -163,6 +163,13 @@ hmc_status hmc_synchronize(hmc_ctx* ctx);
  * kernels: CORR_GAUSS with dim % 4 == 0 and HMC_IMPL_FUSED.  0 otherwise. */
 int32_t hmc_uses_tensor_cores(const hmc_ctx* ctx);
 
+/* Measurement support (no counterpart in the paper): the name of the kernel
+ * hmc_profile_dominant_kernel times for this context and how many chain
+ * gradient evaluations one launch of it performs (chains x leapfrog steps for
+ * the one-launch-per-transition kernels, chains for one gradient product). */
+hmc_status hmc_dominant_kernel_info(const hmc_ctx* ctx, char* name, int32_t name_len,
+                                    int64_t* grad_evals_per_launch);
+
 /* Measurement support (no counterpart in the paper): time one launch in
  * every `sample_every` of the context's dominant kernel -- the fused
  * transition kernel, or the target-gradient product(s) of the plain path --

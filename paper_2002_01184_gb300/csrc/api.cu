@@ -307,6 +307,7 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     char* w = nullptr;
     e = ctx_alloc(ctx, &w, hmc::gauss_tc_workspace_bytes(*target, num_chains));
     if (e == cudaSuccess) e = hmc::gauss_tc_setup(&ctx->tc, *target, num_chains, w, ctx->stream);
+    ctx->tc.fused = hmc::gauss_fused_supported(*target);
   }
   if (e == cudaSuccess && !uses_fused_elementwise(ctx) && !ctx->use_tc) {
     e = ctx_alloc(ctx, &ctx->plain.xp, C * D);
@@ -491,6 +492,34 @@ const char* hmc_last_error(const hmc_ctx* ctx) {
 }
 
 int32_t hmc_uses_tensor_cores(const hmc_ctx* ctx) { return ctx && ctx->use_tc ? 1 : 0; }
+
+hmc_status hmc_dominant_kernel_info(const hmc_ctx* ctx, char* name, int32_t name_len,
+                                    int64_t* grad_evals_per_launch) {
+  if (!ctx || !name || name_len < 1 || !grad_evals_per_launch)
+    return fail(nullptr, HMC_E_INVALID, "NULL argument");
+  const char* n = "";
+  int64_t per = ctx->C;
+  if (ctx->use_tc && ctx->tc.fused) {
+    n = "k_gauss_fused";
+    per = ctx->C * ctx->cfg.num_leapfrog;
+  } else if (ctx->use_tc) {
+    n = "k_gauss_tc_step";
+  } else if (uses_fused_elementwise(ctx)) {
+    n = "k_fused_elementwise";
+    per = ctx->C * ctx->cfg.num_leapfrog;
+  } else if (ctx->target.id == HMC_T_CORR_GAUSS) {
+    n = "k_corr_gauss_grad";
+  } else if (ctx->target.id == HMC_T_LOGREG) {
+    n = "k_logreg_residual+k_logreg_grad_partial";
+  } else if (ctx->target.id == HMC_T_FUNNEL) {
+    n = "k_funnel_grad";
+  } else {
+    n = "k_std_normal_grad";
+  }
+  std::snprintf(name, static_cast<size_t>(name_len), "%s", n);
+  *grad_evals_per_launch = per;
+  return HMC_OK;
+}
 
 hmc_status hmc_grad_workspace_bytes(const hmc_target* target, int64_t num_chains, uint64_t* bytes) {
   std::string why;

@@ -1,0 +1,371 @@
+// One launch per HMC transition for the dense Gaussian target (dim <= 256):
+// each CTA owns NC chains for the whole transition -- momentum draw, all L
+// leapfrog steps and the Metropolis-Hastings select (Section 2.1), with the
+// chains' positions resident in shared memory and momenta in registers -- so
+// the only HBM traffic of a transition is reading and writing each chain's
+// state once.
+//
+// Gradient of step l: G^T = P X^T, computed as 3xTF32 on tcgen05 tensor
+// cores, M = output dims (two 128-row tiles of P), N = the CTA's NC chains,
+// K = dims; A = P (tf32 head / float32 remainder, streamed from L2 by TMA in
+// 128 x 32 chunks through a ring of stages), B = the chains' positions, kept
+// in shared memory as head / remainder tiles in the 128-byte-swizzled K-major
+// layout the MMA reads.  Accumulators live in tensor memory; the epilogue
+// warps read them (one output dim per thread, NC chains per thread), apply
+// the leapfrog update and write the next positions back into the B tiles.
+//
+// Warp roles (320 threads): warp 0 allocates tensor memory and one lane issues
+// the TMA loads of P; one lane of warp 1 issues the MMAs; warps 2-9 are the
+// epilogue: warp w serves tensor-memory lane quarter w % 4 of M-tile
+// (w - 2) / 4, i.e. output dim d = 128 * ((w - 2) / 4) + 32 * (w % 4) + lane.
+#include <cuda.h>
+
+#include <cmath>
+
+#include "hmc_device.cuh"
+#include "hmc_internal.h"
+#include "sm100_ptx.cuh"
+
+namespace hmc {
+
+namespace {
+
+constexpr int kMaxDim = 256;
+constexpr int kChunks = kMaxDim / 32;
+constexpr int kThreads = 320;
+constexpr int kEpiThreads = 256;
+constexpr uint32_t kAHalf = 128 * 128;           // one 128 x 32 float tile: 16 KB
+constexpr uint32_t kAStage = 2 * kAHalf;          // head + remainder
+
+template <int NC>
+struct Cfg {
+  static constexpr uint32_t kBChunk = NC * 128;               // NC rows x 128 B
+  static constexpr uint32_t kBBytes = kChunks * kBChunk;      // one of head / remainder
+  static constexpr int kStages = NC == 32 ? 4 : 2;
+  static constexpr uint32_t kTmemCols = NC == 32 ? 64 : 128;  // two M-tiles x NC columns
+  static constexpr uint32_t kSmall = 8 * (2 * kStages + 2) + 16 + 3 * 8 * NC * 4 + 2 * NC * 4;
+  static constexpr size_t kSmem = 2 * kBBytes + kStages * kAStage + kSmall + 1024;
+};
+
+struct FusedArgs {
+  StepArgs s;
+  int* err;
+};
+
+// Byte offset of element (row r, column k) of a K-major tile stored as
+// 32-column chunks of `chunk_bytes` with the 128-byte swizzle: 16-byte unit
+// index XOR (row mod 8) inside each 8-row, 1024-byte group.
+__device__ __forceinline__ uint32_t sw128_offset(int r, int k, uint32_t chunk_bytes) {
+  const int kc = k >> 5, cc = k & 31;
+  return kc * chunk_bytes + (r >> 3) * 1024 + (r & 7) * 128 + ((((cc >> 2) ^ (r & 7)) & 7) << 4) +
+         (cc & 3) * 4;
+}
+
+__device__ __forceinline__ void proxy_fence_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__device__ __forceinline__ float pick(const float4& v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+template <int NC>
+__global__ void __launch_bounds__(kThreads, 1)
+k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ CUtensorMap mPlo,
+              FusedArgs fa) {
+  using K = Cfg<NC>;
+  const StepArgs& a = fa.s;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* Bhi = smem;
+  uint8_t* Blo = smem + K::kBBytes;
+  uint8_t* Ast = smem + 2 * K::kBBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(Ast + K::kStages * kAStage);
+  uint64_t* empty = full + K::kStages;
+  uint64_t* acc_full = empty + K::kStages;
+  uint64_t* x_ready = acc_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(x_ready + 1);
+  float* red = reinterpret_cast<float*>(tmem_slot + 4);        // [3][8][NC]
+  int* acc_flag = reinterpret_cast<int*>(red + 3 * 8 * NC);    // [NC]
+  float* prob_s = reinterpret_cast<float*>(acc_flag + NC);     // [NC]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int C = a.C, D = a.D, L = a.L;
+  const int nk = (D + 31) >> 5;
+  const int ntm = (D + 127) >> 7;
+  const int c0 = blockIdx.x * NC;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < K::kStages; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    ptx::mbar_init(acc_full, 1);
+    ptx::mbar_init(x_ready, kEpiThreads);
+    ptx::fence_mbar_init();
+    ptx::prefetch_tensormap(&mPhi);
+    ptx::prefetch_tensormap(&mPlo);
+  }
+  if (warp == 0) {
+    ptx::tmem_alloc(tmem_slot, K::kTmemCols);
+    ptx::tmem_relinquish();
+  }
+  // zero the position tiles: padding rows (chains >= C) and columns (dims >= D)
+  for (uint32_t i = threadIdx.x; i < 2 * K::kBBytes / 16; i += kThreads)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  proxy_fence_smem();
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const float eps = a.da->eps;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer: P chunks (kc, M-tile) for every leapfrog step
+      int it = 0;
+      for (int l = 1; l <= L && ok; ++l)
+        for (int kc = 0; kc < nk && ok; ++kc)
+          for (int mt = 0; mt < ntm; ++mt, ++it) {
+            const int s = it % K::kStages, round = it / K::kStages;
+            if (it >= K::kStages && !ptx::mbar_wait(&empty[s], (round - 1) & 1)) {
+              atomicExch(fa.err, 1);
+              ok = false;
+              break;
+            }
+            uint8_t* st = Ast + s * kAStage;
+            ptx::mbar_arrive_expect_tx(&full[s], kAStage);
+            ptx::tma_load_2d(st, &mPhi, &full[s], kc * 32, mt * 128);
+            ptx::tma_load_2d(st + kAHalf, &mPlo, &full[s], kc * 32, mt * 128);
+          }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      constexpr uint32_t idesc = ptx::idesc_tf32(128, NC);
+      int it = 0;
+      for (int l = 1; l <= L && ok; ++l) {
+        if (!ptx::mbar_wait(x_ready, (l - 1) & 1)) {
+          atomicExch(fa.err, 1);
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        for (int kc = 0; kc < nk && ok; ++kc) {
+          const uint32_t bhi = ptx::smem_u32(Bhi + kc * K::kBChunk);
+          const uint32_t blo = ptx::smem_u32(Blo + kc * K::kBChunk);
+          for (int mt = 0; mt < ntm; ++mt, ++it) {
+            const int s = it % K::kStages, round = it / K::kStages;
+            if (!ptx::mbar_wait(&full[s], round & 1)) {
+              atomicExch(fa.err, 1);
+              ok = false;
+              break;
+            }
+            ptx::tc_fence_after();
+            const uint32_t ahi = ptx::smem_u32(Ast + s * kAStage);
+            const uint32_t alo = ahi + kAHalf;
+            const uint32_t d_tmem = tmem + mt * NC;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const uint64_t dahi = ptx::sw128_kmajor_desc(ahi + 32 * j);
+              const uint64_t dalo = ptx::sw128_kmajor_desc(alo + 32 * j);
+              const uint64_t dbhi = ptx::sw128_kmajor_desc(bhi + 32 * j);
+              const uint64_t dblo = ptx::sw128_kmajor_desc(blo + 32 * j);
+              ptx::mma_tf32(d_tmem, dalo, dbhi, idesc, (kc | j) != 0 ? 1u : 0u);
+              ptx::mma_tf32(d_tmem, dahi, dblo, idesc, 1u);
+              ptx::mma_tf32(d_tmem, dahi, dbhi, idesc, 1u);
+            }
+            ptx::mma_commit(&empty[s]);
+          }
+        }
+        ptx::mma_commit(acc_full);
+      }
+    }
+  } else {
+    // ---- epilogue: one output dim d per thread, NC chains per thread
+    const int ew = warp - 2;
+    const int mt = ew >> 2, quarter = warp & 3;
+    const int d = mt * 128 + quarter * 32 + lane;
+    const bool dvalid = d < D;
+    float p[NC], gk[NC];
+    // begin: p0 ~ N(0, I), K0 partials, p = p0 + eps/2 g0, x1 = x0 + eps p
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int chain = c0 + c;
+      const bool valid = dvalid && chain < C;
+      float z = 0.f, g0 = 0.f, x0 = 0.f;
+      if (valid) {
+        const int64_t e = static_cast<int64_t>(chain) * D + d;
+        x0 = a.x[e];
+        g0 = a.g[e];
+        const float4 m4 = momentum4(a.seed, static_cast<uint32_t>(d >> 2),
+                                    static_cast<uint32_t>(chain) + a.chain_offset, a.t);
+        z = pick(m4, d & 3);
+      }
+      const float k2 = warp_sum(z * z);
+      if (lane == 0) red[(0 * 8 + ew) * NC + c] = k2;
+      p[c] = fmaf(0.5f * eps, g0, z);
+      if (valid) {
+        float hi, lo;
+        split_tf32(fmaf(eps, p[c], x0), hi, lo);
+        const uint32_t off = sw128_offset(c, d, K::kBChunk);
+        *reinterpret_cast<float*>(Bhi + off) = hi;
+        *reinterpret_cast<float*>(Blo + off) = lo;
+      }
+    }
+    proxy_fence_smem();
+    mbar_arrive(x_ready);
+    for (int l = 1; l <= L; ++l) {
+      const bool last = l == L;
+      if (!ptx::mbar_wait(acc_full, (l - 1) & 1)) {
+        atomicExch(fa.err, 1);
+        ok = false;
+      }
+      ptx::tc_fence_after();
+#pragma unroll
+      for (int cb = 0; cb < NC / 16; ++cb) {
+        float accv[16];
+        ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + mt * NC + cb * 16, accv);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int c = cb * 16 + i;
+          const float g = -accv[i];
+          const uint32_t off = sw128_offset(c, d, K::kBChunk);
+          if (!last) {
+            p[c] = fmaf(eps, g, p[c]);
+            if (dvalid) {
+              const float x = *reinterpret_cast<const float*>(Bhi + off) +
+                              *reinterpret_cast<const float*>(Blo + off);
+              float hi, lo;
+              split_tf32(fmaf(eps, p[c], x), hi, lo);
+              *reinterpret_cast<float*>(Bhi + off) = hi;
+              *reinterpret_cast<float*>(Blo + off) = lo;
+            }
+          } else {
+            p[c] = fmaf(0.5f * eps, g, p[c]);
+            gk[c] = dvalid ? g : 0.f;
+          }
+        }
+      }
+      if (!last) {
+        proxy_fence_smem();
+        ptx::tc_fence_before();
+        mbar_arrive(x_ready);
+      }
+    }
+    // H_L partials: <x_L, g_L> / 2 and |p_L|^2 per chain
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      float xg = 0.f, pp = 0.f;
+      if (dvalid && c0 + c < C) {
+        const uint32_t off = sw128_offset(c, d, K::kBChunk);
+        const float x = *reinterpret_cast<const float*>(Bhi + off) +
+                        *reinterpret_cast<const float*>(Blo + off);
+        xg = x * gk[c];
+        pp = p[c] * p[c];
+      }
+      xg = warp_sum(xg);
+      pp = warp_sum(pp);
+      if (lane == 0) {
+        red[(1 * 8 + ew) * NC + c] = xg;
+        red[(2 * 8 + ew) * NC + c] = pp;
+      }
+    }
+    epi_barrier();
+    // Metropolis-Hastings, one thread per chain
+    const int cidx = ew * 32 + lane;
+    if (cidx < NC) {
+      const int chain = c0 + cidx;
+      float prob = 0.f;
+      int acc = 0;
+      if (chain < C) {
+        float k0 = 0.f, xg = 0.f, k1 = 0.f;
+        for (int w = 0; w < 8; ++w) {
+          k0 += red[(0 * 8 + w) * NC + cidx];
+          xg += red[(1 * 8 + w) * NC + cidx];
+          k1 += red[(2 * 8 + w) * NC + cidx];
+        }
+        const float lp0 = a.lp[chain];
+        const float lp1 = 0.5f * xg;
+        float la = (-lp0 + 0.5f * k0) - (-lp1 + 0.5f * k1);
+        if (!isfinite(la)) la = -INFINITY;
+        const uint32_t gchain = static_cast<uint32_t>(chain) + a.chain_offset;
+        acc = accept_log_uniform(a.seed, gchain, a.t) < la;
+        prob = accept_prob(la);
+        if (ok) {
+          if (acc) a.lp[chain] = lp1;
+          a.is_accepted[chain] = static_cast<uint8_t>(acc);
+          a.log_accept[chain] = la;
+          if (a.trace_acc) a.trace_acc[chain] = static_cast<uint8_t>(acc);
+        }
+      }
+      acc_flag[cidx] = acc;
+      prob_s[cidx] = prob;
+      if (blockIdx.x == 0 && cidx == 0 && a.trace_eps && ok) a.trace_eps[0] = eps;
+    }
+    epi_barrier();
+    if (ok && dvalid) {
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int chain = c0 + c;
+        if (chain >= C) continue;
+        const int64_t e = static_cast<int64_t>(chain) * D + d;
+        if (acc_flag[c]) {
+          const uint32_t off = sw128_offset(c, d, K::kBChunk);
+          const float x = *reinterpret_cast<const float*>(Bhi + off) +
+                          *reinterpret_cast<const float*>(Blo + off);
+          a.x[e] = x;
+          a.g[e] = gk[c];
+          if (a.sample_out) a.sample_out[e] = x;
+        } else if (a.sample_out) {
+          a.sample_out[e] = a.x[e];
+        }
+      }
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, K::kTmemCols);
+  }
+  // dual averaging: this block's acceptance probabilities in chain order
+  double sum = 0.0;
+  if (threadIdx.x == 0)
+    for (int c = 0; c < NC; ++c) sum += static_cast<double>(prob_s[c]);
+  block_partial_then_da(a.da, a.partials, sum, C, a.t_full);
+}
+
+}  // namespace
+
+int gauss_fused_chains_per_cta() { return 32; }
+
+bool gauss_fused_supported(const hmc_target& t) {
+  return t.id == HMC_T_CORR_GAUSS && t.dim % 4 == 0 && t.dim <= kMaxDim;
+}
+
+cudaError_t gauss_fused_setup() {
+  return cudaFuncSetAttribute(k_gauss_fused<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(Cfg<32>::kSmem));
+}
+
+cudaError_t launch_gauss_fused_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
+                                          KernelTimer* timer) {
+  FusedArgs fa{a, tc.err};
+  const unsigned grid = static_cast<unsigned>((a.C + 31) / 32);
+  if (timer) timer->begin(s);
+  k_gauss_fused<32><<<grid, kThreads, Cfg<32>::kSmem, s>>>(tc.mPhi128, tc.mPlo128, fa);
+  if (timer) timer->end(s);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace hmc

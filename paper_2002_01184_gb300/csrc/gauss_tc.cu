@@ -368,7 +368,9 @@ cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws
   tc->h0 = take(C * 4);
   tc->err = reinterpret_cast<int*>(take(sizeof(int)));
   bool ok = make_map(&tc->mBhi, tc->Phi, t.dim, t.dim, kBN) &&
-            make_map(&tc->mBlo, tc->Plo, t.dim, t.dim, kBN);
+            make_map(&tc->mBlo, tc->Plo, t.dim, t.dim, kBN) &&
+            make_map(&tc->mPhi128, tc->Phi, t.dim, t.dim, 128) &&
+            make_map(&tc->mPlo128, tc->Plo, t.dim, t.dim, 128);
   for (int i = 0; i < 2 && ok; ++i)
     ok = make_map(&tc->mAhi[i], tc->xhi[i], C, t.dim, kBM) &&
          make_map(&tc->mAlo[i], tc->xlo[i], C, t.dim, kBM);
@@ -376,6 +378,10 @@ cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws
   cudaError_t e = cudaFuncSetAttribute(k_gauss_tc_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(kSmemBytes));
   if (e != cudaSuccess) return e;
+  if (gauss_fused_supported(t)) {
+    e = gauss_fused_setup();
+    if (e != cudaSuccess) return e;
+  }
   k_split<<<blocks_for(DD), 256, 0, s>>>(static_cast<int64_t>(DD), t.P, tc->Phi, tc->Plo);
   count_launch();
   e = cudaMemsetAsync(tc->err, 0, sizeof(int), s);
@@ -385,6 +391,7 @@ cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws
 
 cudaError_t launch_gauss_tc_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
                                        KernelTimer* timer) {
+  if (tc.fused) return launch_gauss_fused_transition(a, tc, s, timer);
   TcBeginAccept b{};
   b.s = a;
   b.p = tc.p;

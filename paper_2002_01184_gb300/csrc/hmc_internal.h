@@ -131,6 +131,7 @@ namespace hmc {
 // Device buffers and TMA descriptors of the tensor-core Gaussian path.
 struct GaussTc {
   CUtensorMap mAhi[2], mAlo[2], mBhi, mBlo;
+  CUtensorMap mPhi128, mPlo128;  // P head / remainder, 32 x 128 boxes
   float* Phi = nullptr;      // tf32 head / remainder of P
   float* Plo = nullptr;
   float* xhi[2] = {nullptr, nullptr};   // ping-pong trajectory positions
@@ -141,11 +142,16 @@ struct GaussTc {
   float* h0 = nullptr;       // initial Hamiltonian
   int* err = nullptr;        // device flag: a bounded wait gave up
   int ntn = 0;
+  bool fused = false;        // one launch per transition (dim <= 256)
 };
 
 bool gauss_tc_supported(const hmc_target& t);
 size_t gauss_tc_workspace_bytes(const hmc_target& t, int64_t C);
 cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s);
+bool gauss_fused_supported(const hmc_target& t);
+cudaError_t gauss_fused_setup();
+cudaError_t launch_gauss_fused_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
+                                          KernelTimer* timer);
 cudaError_t launch_gauss_tc_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
                                        KernelTimer* timer);
 

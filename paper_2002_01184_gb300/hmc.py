@@ -66,6 +66,8 @@ def _load():
         "hmc_target_log_prob_and_grad": [ctypes.POINTER(hmc_target), ctypes.c_int64, P, P, P, P,
                                          ctypes.c_uint64, P],
         "hmc_synchronize": [P],
+        "hmc_dominant_kernel_info": [P, ctypes.c_char_p, ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_int64)],
         "hmc_target_vjp_workspace_bytes": [ctypes.POINTER(hmc_target), ctypes.c_int64,
                                            ctypes.POINTER(ctypes.c_uint64)],
         "hmc_target_vjp": [ctypes.POINTER(hmc_target), ctypes.c_int64, P, P, P, P, ctypes.c_uint64,
@@ -248,3 +250,10 @@ def hmc_target_vjp_workspace_bytes(target, num_chains):
 def hmc_target_vjp(target, num_chains, x, w, dx, workspace, workspace_bytes, stream=None):
     _check(lib.hmc_target_vjp(ctypes.byref(target), int(num_chains), _ptr(x), _ptr(w), _ptr(dx),
                               _ptr(workspace), int(workspace_bytes), _stream(stream)))
+
+
+def hmc_dominant_kernel_info(ctx):
+    buf = ctypes.create_string_buffer(128)
+    per = ctypes.c_int64()
+    _check(lib.hmc_dominant_kernel_info(ctx, buf, 128, ctypes.byref(per)), ctx)
+    return buf.value.decode(), int(per.value)

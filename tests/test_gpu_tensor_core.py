@@ -31,7 +31,9 @@ def host(t):
 # (chains, dim, step size, leapfrog steps): one tile; ragged K/N/M tails;
 # several tiles in every direction; the full dimension of the workload
 CASES = [(128, 64, 0.1, 3), (130, 100, 0.08, 5), (257, 196, 0.06, 4), (512, 256, 0.05, 16),
-         (33, 32, 0.2, 1)]
+         (33, 32, 0.2, 1), (4096, 256, 0.05, 2),
+         # dimensions past 256 take the one-launch-per-leapfrog-step kernel
+         (100, 320, 0.04, 3)]
 
 
 @pytest.mark.parametrize("C,D,eps,L", CASES)
@@ -41,6 +43,8 @@ def test_tensor_core_transition_matches_oracle(H, C, D, eps, L):
     p.step_size = eps
     s = Sampler(p, adapt=False)
     assert H.hmc_uses_tensor_cores(s.ctx)
+    name, per_launch = H.hmc_dominant_kernel_info(s.ctx)
+    assert name == ("k_gauss_fused" if D <= 256 else "k_gauss_tc_step")
     x = torch.as_tensor(p.x0).cuda().contiguous()
     s.bootstrap(x)
     tgt = otargets.make("corr_gauss", P=p.P)
