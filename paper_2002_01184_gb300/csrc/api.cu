@@ -295,7 +295,9 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   const size_t C = static_cast<size_t>(num_chains), D = static_cast<size_t>(target->dim);
   cudaError_t e = cudaSuccess;
-  const unsigned nblk = hmc::accept_blocks(static_cast<int>(num_chains));
+  // one partial sum per block of whichever transition kernel runs
+  const unsigned nblk = std::max(hmc::accept_blocks(static_cast<int>(num_chains)),
+                                 hmc::gauss_fused_grid(num_chains));
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->lp, C);
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->g, C * D);
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->is_accepted, C);

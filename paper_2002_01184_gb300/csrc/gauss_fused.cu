@@ -39,6 +39,9 @@ constexpr uint32_t kAStage = 2 * kAHalf;          // head + remainder
 
 template <int NC>
 struct Cfg {
+  // P chunks are shared by every CTA: a cluster of kCluster CTAs loads each
+  // stage once, every CTA fetching 128 / kCluster rows and multicasting them
+  static constexpr int kCluster = 4;
   static constexpr uint32_t kBChunk = NC * 128;               // NC rows x 128 B
   static constexpr uint32_t kBBytes = kChunks * kBChunk;      // one of head / remainder
   static constexpr int kStages = NC == 32 ? 4 : 2;
@@ -75,7 +78,7 @@ __device__ __forceinline__ float pick(const float4& v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-template <int NC>
+template <int NC, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ CUtensorMap mPlo,
               FusedArgs fa) {
@@ -102,10 +105,12 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
   const int ntm = (D + 127) >> 7;
   const int c0 = blockIdx.x * NC;
 
+  const uint32_t crank = CL > 1 ? ptx::cluster_rank() : 0u;
+  constexpr uint16_t kMask = static_cast<uint16_t>((1u << CL) - 1u);
   if (threadIdx.x == 0) {
     for (int s = 0; s < K::kStages; ++s) {
       ptx::mbar_init(&full[s], 1);
-      ptx::mbar_init(&empty[s], 1);
+      ptx::mbar_init(&empty[s], CL);       // released by the MMA of every CTA
     }
     ptx::mbar_init(acc_full, 1);
     ptx::mbar_init(x_ready, kEpiThreads);
@@ -123,6 +128,7 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
   proxy_fence_smem();
   ptx::tc_fence_before();
   __syncthreads();
+  if (CL > 1) ptx::cluster_sync();        // every CTA's barriers exist before any multicast
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const float eps = a.da->eps;
@@ -143,8 +149,17 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
             }
             uint8_t* st = Ast + s * kAStage;
             ptx::mbar_arrive_expect_tx(&full[s], kAStage);
-            ptx::tma_load_2d(st, &mPhi, &full[s], kc * 32, mt * 128);
-            ptx::tma_load_2d(st + kAHalf, &mPlo, &full[s], kc * 32, mt * 128);
+            if (CL == 1) {
+              ptx::tma_load_2d(st, &mPhi, &full[s], kc * 32, mt * 128);
+              ptx::tma_load_2d(st + kAHalf, &mPlo, &full[s], kc * 32, mt * 128);
+            } else {
+              constexpr int kRows = 128 / CL;
+              const uint32_t off = crank * (kAHalf / CL);
+              ptx::tma_load_2d_multicast(st + off, &mPhi, &full[s], kc * 32,
+                                         mt * 128 + static_cast<int>(crank) * kRows, kMask);
+              ptx::tma_load_2d_multicast(st + kAHalf + off, &mPlo, &full[s], kc * 32,
+                                         mt * 128 + static_cast<int>(crank) * kRows, kMask);
+            }
           }
     }
   } else if (warp == 1) {
@@ -183,7 +198,8 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
               ptx::mma_tf32(d_tmem, dahi, dblo, idesc, 1u);
               ptx::mma_tf32(d_tmem, dahi, dbhi, idesc, 1u);
             }
-            ptx::mma_commit(&empty[s]);
+            if (CL == 1) ptx::mma_commit(&empty[s]);
+            else ptx::mma_commit_multicast(&empty[s], kMask);
           }
         }
         ptx::mma_commit(acc_full);
@@ -337,6 +353,8 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem, K::kTmemCols);
   }
+  // no CTA leaves while a peer may still multicast into it or arrive on it
+  if (CL > 1) ptx::cluster_sync();
   // dual averaging: this block's acceptance probabilities in chain order
   double sum = 0.0;
   if (threadIdx.x == 0)
@@ -352,19 +370,43 @@ bool gauss_fused_supported(const hmc_target& t) {
   return t.id == HMC_T_CORR_GAUSS && t.dim % 4 == 0 && t.dim <= kMaxDim;
 }
 
+// CTAs the transition launches for C chains (a whole number of clusters).
+unsigned gauss_fused_grid(int64_t C) {
+  constexpr int CL = Cfg<32>::kCluster;
+  const int64_t ctas = (C + 31) / 32;
+  return static_cast<unsigned>((ctas + CL - 1) / CL * CL);
+}
+
 cudaError_t gauss_fused_setup() {
-  return cudaFuncSetAttribute(k_gauss_fused<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_gauss_fused<32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(Cfg<32>::kSmem));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gauss_fused<32, Cfg<32>::kCluster>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(Cfg<32>::kSmem));
 }
 
 cudaError_t launch_gauss_fused_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
                                           KernelTimer* timer) {
   FusedArgs fa{a, tc.err};
-  const unsigned grid = static_cast<unsigned>((a.C + 31) / 32);
+  constexpr int CL = Cfg<32>::kCluster;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(gauss_fused_grid(a.C));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = Cfg<32>::kSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (timer) timer->begin(s);
-  k_gauss_fused<32><<<grid, kThreads, Cfg<32>::kSmem, s>>>(tc.mPhi128, tc.mPlo128, fa);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_gauss_fused<32, CL>, tc.mPhi32, tc.mPlo32, fa);
   if (timer) timer->end(s);
   count_launch();
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

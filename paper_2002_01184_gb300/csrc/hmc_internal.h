@@ -132,6 +132,7 @@ namespace hmc {
 struct GaussTc {
   CUtensorMap mAhi[2], mAlo[2], mBhi, mBlo;
   CUtensorMap mPhi128, mPlo128;  // P head / remainder, 32 x 128 boxes
+  CUtensorMap mPhi32, mPlo32;    // 32 x 32 boxes (one CTA's share of a multicast stage)
   float* Phi = nullptr;      // tf32 head / remainder of P
   float* Plo = nullptr;
   float* xhi[2] = {nullptr, nullptr};   // ping-pong trajectory positions
@@ -149,6 +150,7 @@ bool gauss_tc_supported(const hmc_target& t);
 size_t gauss_tc_workspace_bytes(const hmc_target& t, int64_t C);
 cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s);
 bool gauss_fused_supported(const hmc_target& t);
+unsigned gauss_fused_grid(int64_t C);
 cudaError_t gauss_fused_setup();
 cudaError_t launch_gauss_fused_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
                                           KernelTimer* timer);
