@@ -140,6 +140,17 @@ hmc_status hmc_step(hmc_ctx* ctx, float* x_inout, uint64_t t, hmc_kernel_results
 hmc_status hmc_sample_chain(hmc_ctx* ctx, float* x_inout, int64_t num_burnin, int64_t num_results,
                             float* samples_out, float* trace_step_size, uint8_t* trace_accept);
 
+/* The streaming-expectations driver the paper plans (Section 4.2: for state
+ * too large to store a full trace): same transitions as hmc_sample_chain, but
+ * instead of storing kept states it updates, after every kept transition,
+ * Welford running moments per chain and dimension (device, [chains x dim],
+ * caller-owned): mean_out = mean of the kept states, m2_out = sum of squared
+ * deviations from it (variance = m2 / (num_results - 1)).  Both are left
+ * unwritten when num_results == 0.  Traces as in hmc_sample_chain. */
+hmc_status hmc_sample_chain_streaming(hmc_ctx* ctx, float* x_inout, int64_t num_burnin,
+                                      int64_t num_results, float* mean_out, float* m2_out,
+                                      float* trace_step_size, uint8_t* trace_accept);
+
 /* Same as hmc_sample_chain with every argument in HOST memory (x_inout,
  * samples_out, trace buffers; pinned or pageable).  Copies the initial state
  * to the device, samples, copies the results back and synchronises the

@@ -1,6 +1,7 @@
 // C ABI of libhmc (include/hmc.h): argument checking, the context's device
 // workspace, and the sample_chain driver (Section 4.2) that enqueues one
 // transition per step on the context's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -50,6 +51,11 @@ struct hmc_ctx {
   uint64_t g_launches = 0;      // kernels per replay
   uint64_t g_dominant = 0;      // dominant-kernel launches per replay
   uint64_t g_recorded = 0;      // timed event pairs inside the graph
+  float* g_mean = nullptr;
+  float* g_m2 = nullptr;
+  // streaming-expectations outputs of the call in progress (null: none)
+  float* s_mean = nullptr;
+  float* s_m2 = nullptr;
   std::string err;
 };
 
@@ -141,6 +147,10 @@ void release(hmc_ctx* ctx) {
   ctx->stage = nullptr;
 }
 
+bool uses_fused_logreg(const hmc_ctx* ctx) {
+  return ctx->cfg.impl == HMC_IMPL_FUSED && hmc::logreg_fused_supported(ctx->target);
+}
+
 bool uses_fused_elementwise(const hmc_ctx* ctx) {
   return ctx->cfg.impl == HMC_IMPL_FUSED &&
          (ctx->target.id == HMC_T_STD_NORMAL || ctx->target.id == HMC_T_FUNNEL) &&
@@ -168,6 +178,8 @@ StepArgs make_args(hmc_ctx* ctx, float* x, uint64_t t) {
 
 cudaError_t enqueue_transition(hmc_ctx* ctx, const StepArgs& a) {
   if (ctx->use_tc) return hmc::launch_gauss_tc_transition(a, ctx->tc, ctx->stream, &ctx->timer);
+  if (uses_fused_logreg(ctx))
+    return hmc::launch_logreg_fused_transition(ctx->target, a, ctx->stream, &ctx->timer);
   if (uses_fused_elementwise(ctx))
     return hmc::launch_fused_elementwise(ctx->target.id, a, ctx->stream, &ctx->timer);
   return hmc::launch_plain_transition(ctx->target, a, ctx->plain, ctx->grad_ws, ctx->stream,
@@ -209,6 +221,10 @@ hmc_status enqueue_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sa
     }
     cudaError_t e = enqueue_transition(ctx, a);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "transition launch");
+    if (k >= 0 && ctx->s_mean) {
+      e = hmc::launch_welford(CD, x, k, ctx->s_mean, ctx->s_m2, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "moment update launch");
+    }
   }
   return HMC_OK;
 }
@@ -221,7 +237,8 @@ hmc_status run_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sample
                      uint8_t* trace_acc) {
   if (!ctx->cfg.use_graph) return enqueue_chain(ctx, x, B, K, samples, trace_eps, trace_acc);
   const bool hit = ctx->graph && ctx->g_x == x && ctx->g_B == B && ctx->g_K == K &&
-                   ctx->g_samples == samples && ctx->g_eps == trace_eps && ctx->g_acc == trace_acc;
+                   ctx->g_samples == samples && ctx->g_eps == trace_eps && ctx->g_acc == trace_acc &&
+                   ctx->g_mean == ctx->s_mean && ctx->g_m2 == ctx->s_m2;
   if (!hit) {
     drop_graph(ctx);
     cudaError_t e = cudaSuccess;
@@ -261,6 +278,8 @@ hmc_status run_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sample
     ctx->g_samples = samples;
     ctx->g_eps = trace_eps;
     ctx->g_acc = trace_acc;
+    ctx->g_mean = ctx->s_mean;
+    ctx->g_m2 = ctx->s_m2;
   }
   cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
@@ -296,8 +315,9 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   const size_t C = static_cast<size_t>(num_chains), D = static_cast<size_t>(target->dim);
   cudaError_t e = cudaSuccess;
   // one partial sum per block of whichever transition kernel runs
-  const unsigned nblk = std::max(hmc::accept_blocks(static_cast<int>(num_chains)),
-                                 hmc::gauss_fused_grid(num_chains));
+  const unsigned nblk = std::max({hmc::accept_blocks(static_cast<int>(num_chains)),
+                                  hmc::gauss_fused_grid(num_chains),
+                                  hmc::logreg_fused_grid(num_chains)});
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->lp, C);
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->g, C * D);
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->is_accepted, C);
@@ -311,6 +331,7 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     if (e == cudaSuccess) e = hmc::gauss_tc_setup(&ctx->tc, *target, num_chains, w, ctx->stream);
     ctx->tc.fused = hmc::gauss_fused_supported(*target);
   }
+  if (e == cudaSuccess && uses_fused_logreg(ctx)) e = hmc::logreg_fused_setup(*target);
   if (e == cudaSuccess && !uses_fused_elementwise(ctx) && !ctx->use_tc) {
     e = ctx_alloc(ctx, &ctx->plain.xp, C * D);
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.gp, C * D);
@@ -374,6 +395,24 @@ hmc_status hmc_sample_chain(hmc_ctx* ctx, float* x_inout, int64_t num_burnin, in
   if (num_burnin + num_results > static_cast<int64_t>(std::numeric_limits<uint32_t>::max()))
     return fail(ctx, HMC_E_INVALID, "too many transitions (transition index is 32-bit)");
   return run_chain(ctx, x_inout, num_burnin, num_results, samples_out, trace_step_size, trace_accept);
+}
+
+hmc_status hmc_sample_chain_streaming(hmc_ctx* ctx, float* x_inout, int64_t num_burnin,
+                                      int64_t num_results, float* mean_out, float* m2_out,
+                                      float* trace_step_size, uint8_t* trace_accept) {
+  if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
+  if (!x_inout || !mean_out || !m2_out)
+    return fail(ctx, HMC_E_INVALID, "x_inout, mean_out and m2_out must be non-NULL");
+  if (num_burnin < 0 || num_results < 0) return fail(ctx, HMC_E_INVALID, "negative step count");
+  if (num_burnin + num_results > static_cast<int64_t>(std::numeric_limits<uint32_t>::max()))
+    return fail(ctx, HMC_E_INVALID, "too many transitions (transition index is 32-bit)");
+  ctx->s_mean = mean_out;
+  ctx->s_m2 = m2_out;
+  hmc_status st = run_chain(ctx, x_inout, num_burnin, num_results, nullptr, trace_step_size,
+                            trace_accept);
+  ctx->s_mean = nullptr;
+  ctx->s_m2 = nullptr;
+  return st;
 }
 
 hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burnin,
@@ -506,6 +545,9 @@ hmc_status hmc_dominant_kernel_info(const hmc_ctx* ctx, char* name, int32_t name
     per = ctx->C * ctx->cfg.num_leapfrog;
   } else if (ctx->use_tc) {
     n = "k_gauss_tc_step";
+  } else if (uses_fused_logreg(ctx)) {
+    n = "k_logreg_fused";
+    per = ctx->C * ctx->cfg.num_leapfrog;
   } else if (uses_fused_elementwise(ctx)) {
     n = "k_fused_elementwise";
     per = ctx->C * ctx->cfg.num_leapfrog;

@@ -53,6 +53,8 @@ struct Cfg {
 struct FusedArgs {
   StepArgs s;
   int* err;
+  const float* p0;      // [C x D] momenta of this transition
+  const float* kin0;    // [C] their kinetic energies
 };
 
 // Byte offset of element (row r, column k) of a K-major tile stored as
@@ -211,30 +213,33 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
     const int mt = ew >> 2, quarter = warp & 3;
     const int d = mt * 128 + quarter * 32 + lane;
     const bool dvalid = d < D;
-    float p[NC], gk[NC];
-    // begin: p0 ~ N(0, I), K0 partials, p = p0 + eps/2 g0, x1 = x0 + eps p
+    float p[NC];
+    // begin: p = p0 + eps/2 g0, x1 = x0 + eps p (p0 drawn by k_gauss_momentum);
+    // loads for a group of 8 chains are issued before any of them is used
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int chain = c0 + c;
-      const bool valid = dvalid && chain < C;
-      float z = 0.f, g0 = 0.f, x0 = 0.f;
-      if (valid) {
+    for (int c8 = 0; c8 < NC; c8 += 8) {
+      float xr[8], gr[8], zr[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int chain = c0 + c8 + i;
+        const bool valid = dvalid && chain < C;
         const int64_t e = static_cast<int64_t>(chain) * D + d;
-        x0 = a.x[e];
-        g0 = a.g[e];
-        const float4 m4 = momentum4(a.seed, static_cast<uint32_t>(d >> 2),
-                                    static_cast<uint32_t>(chain) + a.chain_offset, a.t);
-        z = pick(m4, d & 3);
+        xr[i] = valid ? a.x[e] : 0.f;
+        gr[i] = valid ? a.g[e] : 0.f;
+        zr[i] = valid ? fa.p0[e] : 0.f;
       }
-      const float k2 = warp_sum(z * z);
-      if (lane == 0) red[(0 * 8 + ew) * NC + c] = k2;
-      p[c] = fmaf(0.5f * eps, g0, z);
-      if (valid) {
-        float hi, lo;
-        split_tf32(fmaf(eps, p[c], x0), hi, lo);
-        const uint32_t off = sw128_offset(c, d, K::kBChunk);
-        *reinterpret_cast<float*>(Bhi + off) = hi;
-        *reinterpret_cast<float*>(Blo + off) = lo;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int c = c8 + i;
+        const bool valid = dvalid && c0 + c < C;
+        p[c] = fmaf(0.5f * eps, gr[i], zr[i]);
+        if (valid) {
+          float hi, lo;
+          split_tf32(fmaf(eps, p[c], xr[i]), hi, lo);
+          const uint32_t off = sw128_offset(c, d, K::kBChunk);
+          *reinterpret_cast<float*>(Bhi + off) = hi;
+          *reinterpret_cast<float*>(Blo + off) = lo;
+        }
       }
     }
     proxy_fence_smem();
@@ -266,8 +271,7 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
               *reinterpret_cast<float*>(Blo + off) = lo;
             }
           } else {
-            p[c] = fmaf(0.5f * eps, g, p[c]);
-            gk[c] = dvalid ? g : 0.f;
+            p[c] = fmaf(0.5f * eps, g, p[c]);   // g_L stays in tensor memory
           }
         }
       }
@@ -277,22 +281,29 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
         mbar_arrive(x_ready);
       }
     }
-    // H_L partials: <x_L, g_L> / 2 and |p_L|^2 per chain
+    // H_L partials: <x_L, g_L> / 2 and |p_L|^2 per chain (g_L re-read from
+    // the accumulator, which the last step left in tensor memory)
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      float xg = 0.f, pp = 0.f;
-      if (dvalid && c0 + c < C) {
-        const uint32_t off = sw128_offset(c, d, K::kBChunk);
-        const float x = *reinterpret_cast<const float*>(Bhi + off) +
-                        *reinterpret_cast<const float*>(Blo + off);
-        xg = x * gk[c];
-        pp = p[c] * p[c];
-      }
-      xg = warp_sum(xg);
-      pp = warp_sum(pp);
-      if (lane == 0) {
-        red[(1 * 8 + ew) * NC + c] = xg;
-        red[(2 * 8 + ew) * NC + c] = pp;
+    for (int cb = 0; cb < NC / 16; ++cb) {
+      float accv[16];
+      ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + mt * NC + cb * 16, accv);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int c = cb * 16 + i;
+        float xg = 0.f, pp = 0.f;
+        if (dvalid && c0 + c < C) {
+          const uint32_t off = sw128_offset(c, d, K::kBChunk);
+          const float x = *reinterpret_cast<const float*>(Bhi + off) +
+                          *reinterpret_cast<const float*>(Blo + off);
+          xg = -x * accv[i];
+          pp = p[c] * p[c];
+        }
+        xg = warp_sum(xg);
+        pp = warp_sum(pp);
+        if (lane == 0) {
+          red[(1 * 8 + ew) * NC + c] = xg;
+          red[(2 * 8 + ew) * NC + c] = pp;
+        }
       }
     }
     epi_barrier();
@@ -303,9 +314,9 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
       float prob = 0.f;
       int acc = 0;
       if (chain < C) {
-        float k0 = 0.f, xg = 0.f, k1 = 0.f;
+        const float k0 = 2.f * fa.kin0[chain];
+        float xg = 0.f, k1 = 0.f;
         for (int w = 0; w < 8; ++w) {
-          k0 += red[(0 * 8 + w) * NC + cidx];
           xg += red[(1 * 8 + w) * NC + cidx];
           k1 += red[(2 * 8 + w) * NC + cidx];
         }
@@ -328,21 +339,27 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
       if (blockIdx.x == 0 && cidx == 0 && a.trace_eps && ok) a.trace_eps[0] = eps;
     }
     epi_barrier();
-    if (ok && dvalid) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const int chain = c0 + c;
-        if (chain >= C) continue;
-        const int64_t e = static_cast<int64_t>(chain) * D + d;
-        if (acc_flag[c]) {
-          const uint32_t off = sw128_offset(c, d, K::kBChunk);
-          const float x = *reinterpret_cast<const float*>(Bhi + off) +
-                          *reinterpret_cast<const float*>(Blo + off);
-          a.x[e] = x;
-          a.g[e] = gk[c];
-          if (a.sample_out) a.sample_out[e] = x;
-        } else if (a.sample_out) {
-          a.sample_out[e] = a.x[e];
+    for (int cb = 0; cb < NC / 16; ++cb) {
+      float accv[16];
+      ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + mt * NC + cb * 16, accv);
+      if (ok && dvalid) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int c = cb * 16 + i;
+          const int chain = c0 + c;
+          if (chain >= C) continue;
+          const int64_t e = static_cast<int64_t>(chain) * D + d;
+          if (acc_flag[c]) {
+            const uint32_t off = sw128_offset(c, d, K::kBChunk);
+            const float x = *reinterpret_cast<const float*>(Bhi + off) +
+                            *reinterpret_cast<const float*>(Blo + off);
+            a.x[e] = x;
+            a.g[e] = -accv[i];
+            if (a.sample_out) a.sample_out[e] = x;
+          } else if (a.sample_out) {
+            a.sample_out[e] = a.x[e];
+          }
         }
       }
     }
@@ -360,6 +377,26 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
   if (threadIdx.x == 0)
     for (int c = 0; c < NC; ++c) sum += static_cast<double>(prob_s[c]);
   block_partial_then_da(a.da, a.partials, sum, C, a.t_full);
+}
+
+// p0 ~ N(0, I) for every chain of transition t and its kinetic energy
+// |p0|^2 / 2 (warp per chain).  The draws depend only on (seed, chain, t), so
+// this runs as its own wide launch ahead of the transition kernel.
+__global__ void k_gauss_momentum(uint64_t seed, uint32_t t, int C, int D, uint32_t chain_offset,
+                                 float* __restrict__ p0, float* __restrict__ kin0) {
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= C) return;
+  const uint32_t chain = static_cast<uint32_t>(c) + chain_offset;
+  float k = 0.f;
+  float4* row = reinterpret_cast<float4*>(p0 + static_cast<int64_t>(c) * D);
+  for (int j = lane; 4 * j < D; j += 32) {
+    const float4 z = momentum4(seed, static_cast<uint32_t>(j), chain, t);
+    row[j] = z;                                          // D % 4 == 0 on this path
+    k = fmaf(z.x, z.x, fmaf(z.y, z.y, fmaf(z.z, z.z, fmaf(z.w, z.w, k))));
+  }
+  k = warp_sum(k);
+  if (lane == 0) kin0[c] = 0.5f * k;
 }
 
 }  // namespace
@@ -388,7 +425,10 @@ cudaError_t gauss_fused_setup() {
 
 cudaError_t launch_gauss_fused_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
                                           KernelTimer* timer) {
-  FusedArgs fa{a, tc.err};
+  const unsigned mb = static_cast<unsigned>((a.C + 7) / 8);
+  k_gauss_momentum<<<mb, 256, 0, s>>>(a.seed, a.t, a.C, a.D, a.chain_offset, tc.p, tc.h0);
+  count_launch();
+  FusedArgs fa{a, tc.err, tc.p, tc.h0};
   constexpr int CL = Cfg<32>::kCluster;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(gauss_fused_grid(a.C));

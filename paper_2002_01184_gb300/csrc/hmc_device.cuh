@@ -70,6 +70,15 @@ __device__ __forceinline__ float4 momentum4(uint64_t seed, uint32_t j, uint32_t 
   return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// The normal for state dim d alone (component d % 4 of momentum4(d / 4)):
+// one Box-Muller pair instead of two.
+__device__ __forceinline__ float momentum1(uint64_t seed, uint32_t d, uint32_t chain, uint32_t t) {
+  const uint4 w = philox(make_uint4(d >> 2, chain, t, kTagMomentum),
+                         static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+  const float2 z = (d & 2u) ? box_muller(w.z, w.w) : box_muller(w.x, w.y);
+  return (d & 1u) ? z.y : z.x;
+}
+
 __device__ __forceinline__ float accept_log_uniform(uint64_t seed, uint32_t chain, uint32_t t) {
   const uint4 w = philox(make_uint4(0u, chain, t, kTagAccept),
                          static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));

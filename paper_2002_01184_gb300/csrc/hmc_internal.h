@@ -119,6 +119,13 @@ cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_
                           cudaStream_t s);
 cudaError_t launch_momentum(uint64_t seed, uint32_t t, int C, int D, uint32_t chain_offset,
                             float* out, cudaStream_t s);
+bool logreg_fused_supported(const hmc_target& t);
+cudaError_t logreg_fused_setup(const hmc_target& t);
+unsigned logreg_fused_grid(int64_t C);
+cudaError_t launch_logreg_fused_transition(const hmc_target& t, const StepArgs& a, cudaStream_t s,
+                                           KernelTimer* timer);
+cudaError_t launch_welford(int64_t n, const float* x, int64_t k, float* mean, float* m2,
+                           cudaStream_t s);
 cudaError_t launch_da_init(DAState* da, float eps0, int adapt, float delta, long long num_adapt,
                            cudaStream_t s);
 

@@ -332,6 +332,36 @@ cudaError_t launch_momentum(uint64_t seed, uint32_t t, int C, int D, uint32_t ch
   return cudaGetLastError();
 }
 
+// Welford's running mean and sum of squared deviations (Welford 1962), one
+// element per thread: after kept draws 0..k, mean is their mean and m2 the
+// sum of squared deviations from it.
+__global__ void k_welford(int64_t n, const float* __restrict__ x, int64_t k, float* __restrict__ mean,
+                          float* __restrict__ m2) {
+  const float inv = 1.0f / static_cast<float>(k + 1);
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float v = x[i];
+    if (k == 0) {
+      mean[i] = v;
+      m2[i] = 0.f;
+    } else {
+      const float m0 = mean[i];
+      const float delta = v - m0;
+      const float m1 = fmaf(delta, inv, m0);
+      mean[i] = m1;
+      m2[i] = fmaf(delta, v - m1, m2[i]);
+    }
+  }
+}
+
+cudaError_t launch_welford(int64_t n, const float* x, int64_t k, float* mean, float* m2,
+                           cudaStream_t s) {
+  k_welford<<<static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 152 * 16)), 256, 0, s>>>(
+      n, x, k, mean, m2);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_da_init(DAState* da, float eps0, int adapt, float delta, long long num_adapt,
                            cudaStream_t s) {
   k_da_init<<<1, 32, 0, s>>>(da, eps0, adapt, delta, num_adapt);

@@ -66,6 +66,7 @@ def _load():
         "hmc_target_log_prob_and_grad": [ctypes.POINTER(hmc_target), ctypes.c_int64, P, P, P, P,
                                          ctypes.c_uint64, P],
         "hmc_synchronize": [P],
+        "hmc_sample_chain_streaming": [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P, P],
         "hmc_dominant_kernel_info": [P, ctypes.c_char_p, ctypes.c_int32,
                                      ctypes.POINTER(ctypes.c_int64)],
         "hmc_target_vjp_workspace_bytes": [ctypes.POINTER(hmc_target), ctypes.c_int64,
@@ -257,3 +258,10 @@ def hmc_dominant_kernel_info(ctx):
     per = ctypes.c_int64()
     _check(lib.hmc_dominant_kernel_info(ctx, buf, 128, ctypes.byref(per)), ctx)
     return buf.value.decode(), int(per.value)
+
+
+def hmc_sample_chain_streaming(ctx, x_inout, num_burnin, num_results, mean_out, m2_out,
+                               trace_step_size=None, trace_accept=None):
+    _check(lib.hmc_sample_chain_streaming(ctx, _ptr(x_inout), int(num_burnin), int(num_results),
+                                          _ptr(mean_out), _ptr(m2_out), _ptr(trace_step_size),
+                                          _ptr(trace_accept)), ctx)
