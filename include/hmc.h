@@ -204,6 +204,45 @@ hmc_status hmc_destroy(hmc_ctx* ctx);
  * is owned by the library and valid until the next call on the same context. */
 const char* hmc_last_error(const hmc_ctx* ctx);
 
+/* ---- Batches of posteriors ------------------------------------------------
+ * Many posteriors of uneven dimension, data size and chain count sampled
+ * together (the independent-chain batching of Section 2 applied across
+ * posteriors): each transition of every posterior is one tile of a single
+ * grouped kernel launch, largest tiles first, and the whole loop runs as one
+ * CUDA graph.  Each posterior keeps its own state, kernel results and
+ * dual-averaging step size.  Supported families: LOGREG (dim <= 512), FUNNEL
+ * and STD_NORMAL (dim <= 1024); others give HMC_E_UNSUPPORTED. */
+typedef struct hmc_batch hmc_batch;
+
+/* Create a batch of num_posteriors posteriors: targets[i], num_chains[i] and
+ * configs[i] as for hmc_create (impl and use_graph are ignored).  Allocates
+ * each posterior's workspace; errors as hmc_create, text via
+ * hmc_last_error(NULL). */
+hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
+                            const int64_t* num_chains, const hmc_config* configs, void* cuda_stream,
+                            hmc_batch** out);
+
+/* sample_chain (Section 4.2) for every posterior at once: arrays of
+ * num_posteriors entries, entry i as in hmc_sample_chain for posterior i
+ * (x_inout[i] device [C_i x D_i]; samples_out / trace arrays may be NULL, and
+ * so may their entries).  Posteriors with fewer transitions stop early.  The
+ * first call with a given set of pointers and counts captures the loop as a
+ * graph; later calls replay it. */
+hmc_status hmc_batch_sample_chain(hmc_batch* batch, float* const* x_inout,
+                                  const int64_t* num_burnin, const int64_t* num_results,
+                                  float* const* samples_out, float* const* trace_step_size,
+                                  uint8_t* const* trace_accept);
+
+/* The context of posterior i (owned by the batch; for hmc_read_adaptation
+ * and hmc_synchronize).  NULL if i is out of range. */
+hmc_ctx* hmc_batch_context(hmc_batch* batch, int32_t i);
+
+/* Text of the batch's last error ("" if none). */
+const char* hmc_batch_last_error(const hmc_batch* batch);
+
+/* Release the batch and every posterior's workspace.  NULL is accepted. */
+hmc_status hmc_batch_destroy(hmc_batch* batch);
+
 /* Bytes of device scratch that hmc_target_log_prob_and_grad needs for
  * `num_chains` chains of `target` (0 for targets that need none; LOGREG needs
  * the C x N residual matrix and split-K partial sums).  Returns 0 and sets

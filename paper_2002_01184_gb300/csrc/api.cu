@@ -295,6 +295,16 @@ hmc_status run_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sample
 
 namespace hmc {
 void set_global_error(const std::string& msg) { g_global_err = msg; }
+
+StepArgs ctx_step_args(hmc_ctx* ctx, float* x, uint64_t t) { return make_args(ctx, x, t); }
+
+hmc_status ctx_bootstrap_on(hmc_ctx* ctx, const float* x0, cudaStream_t s) {
+  cudaStream_t own = ctx->stream;
+  ctx->stream = s;
+  hmc_status st = bootstrap(ctx, x0);
+  ctx->stream = own;
+  return st;
+}
 }  // namespace hmc
 
 extern "C" {

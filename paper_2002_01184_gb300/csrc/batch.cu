@@ -1,0 +1,284 @@
+// Many posteriors of uneven dimension, data size and chain count sampled
+// together: every transition of every posterior is one CTA tile of a single
+// grouped launch (k_batch_transition), the tiles of all posteriors side by
+// side, ordered by their estimated cost so the largest start first.  Each
+// posterior keeps its own chain state, kernel results and dual-averaging
+// scalar; the adaptation reduction runs over that posterior's tiles only.
+// The whole sampling loop (bootstraps + one grouped launch per transition) is
+// captured as one CUDA graph.  Section 2's premise -- independent chains,
+// batched evaluation -- applied across posteriors.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "elementwise_tile.cuh"
+#include "hmc_device.cuh"
+#include "hmc_internal.h"
+#include "logreg_tile.cuh"
+
+namespace hmc {
+
+namespace {
+
+struct BatchPost {
+  int kind;            // hmc_target_id
+  int nb;              // elementwise: Philox blocks per lane (1, 2, 4, 8)
+  int ntiles;          // CTAs of this posterior
+  int n_data;
+  StepArgs s;          // C, D, L, seed, chain_offset, state and result pointers
+  const float* X;
+  const float* y;
+  long long B, K;      // burn-in and kept transitions
+  float* samples;      // [K x C x D] or null
+  float* trace_eps;    // [K] or null
+  uint8_t* trace_acc;  // [K x C] or null
+};
+
+template <int TARGET>
+__device__ __forceinline__ void elementwise_dispatch(const StepArgs& a, int nb, int tile, int ntiles) {
+  if (nb == 1) elementwise_tile<TARGET, 1>(a, tile, ntiles);
+  else if (nb == 2) elementwise_tile<TARGET, 2>(a, tile, ntiles);
+  else if (nb == 4) elementwise_tile<TARGET, 4>(a, tile, ntiles);
+  else elementwise_tile<TARGET, 8>(a, tile, ntiles);
+}
+
+__global__ void __launch_bounds__(256) k_batch_transition(const BatchPost* __restrict__ posts,
+                                                         const int2* __restrict__ items, uint32_t t) {
+  const int2 it = items[blockIdx.x];                   // (posterior, tile)
+  const BatchPost& P = posts[it.x];
+  if (static_cast<long long>(t) >= P.B + P.K) return;  // this posterior has finished
+  StepArgs a = P.s;
+  a.t = t;
+  a.t_full = t;
+  const long long k = static_cast<long long>(t) - P.B;
+  if (k >= 0) {
+    a.sample_out = P.samples ? P.samples + k * static_cast<long long>(a.C) * a.D : nullptr;
+    a.trace_acc = P.trace_acc ? P.trace_acc + k * a.C : nullptr;
+    a.trace_eps = P.trace_eps ? P.trace_eps + k : nullptr;
+  }
+  if (P.kind == HMC_T_LOGREG) {
+    lr::LrArgs la{a, P.X, P.y, P.n_data};
+    lr::logreg_tile(la, it.y, P.ntiles);
+  } else if (P.kind == HMC_T_FUNNEL) {
+    elementwise_dispatch<HMC_T_FUNNEL>(a, P.nb, it.y, P.ntiles);
+  } else {
+    elementwise_dispatch<HMC_T_STD_NORMAL>(a, P.nb, it.y, P.ntiles);
+  }
+}
+
+int blocks_per_lane(int D) {
+  const int nblk = (D + 3) / 4;
+  return nblk <= 32 ? 1 : nblk <= 64 ? 2 : nblk <= 128 ? 4 : 8;
+}
+
+}  // namespace
+}  // namespace hmc
+
+struct hmc_batch {
+  int n = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<hmc_ctx*> ctx;
+  std::vector<hmc_target> targets;
+  std::vector<int64_t> chains;
+  std::vector<hmc::BatchPost> host_posts;
+  hmc::BatchPost* dev_posts = nullptr;
+  int2* dev_items = nullptr;
+  int num_items = 0;
+  size_t smem = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<const void*> g_key;
+  uint64_t g_launches = 0;
+  std::string err;
+};
+
+namespace {
+
+hmc_status bfail(hmc_batch* b, hmc_status st, const std::string& m) {
+  if (b) b->err = m;
+  else hmc::set_global_error(m);
+  return st;
+}
+
+void batch_release(hmc_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->dev_posts) cudaFree(b->dev_posts);
+  if (b->dev_items) cudaFree(b->dev_items);
+  for (hmc_ctx* c : b->ctx) hmc_destroy(c);
+  b->ctx.clear();
+}
+
+// Rough cost of one tile transition: chains x leapfrog x per-gradient work.
+double tile_cost(const hmc_target& t, const hmc_config& c) {
+  const double per = t.id == HMC_T_LOGREG ? 2.0 * t.n_data * t.dim : 8.0 * t.dim;
+  return per * c.num_leapfrog * 8.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
+                            const int64_t* num_chains, const hmc_config* configs, void* cuda_stream,
+                            hmc_batch** out) {
+  if (!out) return bfail(nullptr, HMC_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (num_posteriors < 1 || !targets || !num_chains || !configs)
+    return bfail(nullptr, HMC_E_INVALID, "need >= 1 posterior and non-NULL arrays");
+  hmc_batch* b = new hmc_batch();
+  b->n = num_posteriors;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<std::pair<double, int2>> items;
+  for (int i = 0; i < num_posteriors; ++i) {
+    const hmc_target& t = targets[i];
+    if (t.id == HMC_T_CORR_GAUSS || (t.id == HMC_T_LOGREG && t.dim > hmc::lr::kLrMaxDim) ||
+        ((t.id == HMC_T_FUNNEL || t.id == HMC_T_STD_NORMAL) && t.dim > hmc::kFusedElementwiseMaxDim)) {
+      batch_release(b);
+      delete b;
+      return bfail(nullptr, HMC_E_UNSUPPORTED,
+                   "batch posterior " + std::to_string(i) +
+                       ": supported are LOGREG (dim <= 512), FUNNEL and STD_NORMAL (dim <= 1024)");
+    }
+    hmc_config c = configs[i];
+    c.impl = HMC_IMPL_FUSED;
+    c.use_graph = 0;
+    hmc_ctx* ctx = nullptr;
+    hmc_status st = hmc_create(&t, num_chains[i], &c, cuda_stream, &ctx);
+    if (st != HMC_OK) {
+      const std::string m = "batch posterior " + std::to_string(i) + ": " + hmc_last_error(nullptr);
+      batch_release(b);
+      delete b;
+      return bfail(nullptr, st, m);
+    }
+    b->ctx.push_back(ctx);
+    b->targets.push_back(t);
+    b->chains.push_back(num_chains[i]);
+    hmc::BatchPost P{};
+    P.kind = t.id;
+    P.nb = hmc::blocks_per_lane(t.dim);
+    P.ntiles = static_cast<int>((num_chains[i] + 7) / 8);     // 8 chains per tile for every kind
+    P.n_data = static_cast<int>(t.n_data);
+    P.X = t.X;
+    P.y = t.y;
+    b->host_posts.push_back(P);
+    const double cost = tile_cost(t, c);
+    for (int tile = 0; tile < P.ntiles; ++tile) items.push_back({cost, make_int2(i, tile)});
+    if (t.id == HMC_T_LOGREG) b->smem = std::max(b->smem, hmc::lr::logreg_smem_bytes(t.dim));
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const auto& a, const auto& c) { return a.first > c.first; });
+  std::vector<int2> flat;
+  for (auto& it : items) flat.push_back(it.second);
+  b->num_items = static_cast<int>(flat.size());
+  cudaError_t e = cudaMalloc(&b->dev_posts, sizeof(hmc::BatchPost) * b->n);
+  if (e == cudaSuccess) e = cudaMalloc(&b->dev_items, sizeof(int2) * flat.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->dev_items, flat.data(), sizeof(int2) * flat.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && b->smem > 0)
+    e = cudaFuncSetAttribute(hmc::k_batch_transition, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(b->smem));
+  if (e != cudaSuccess) {
+    const hmc_status st = e == cudaErrorMemoryAllocation ? HMC_E_OOM : HMC_E_CUDA;
+    cudaGetLastError();
+    batch_release(b);
+    delete b;
+    return bfail(nullptr, st, std::string("batch set-up: ") + cudaGetErrorString(e));
+  }
+  *out = b;
+  return HMC_OK;
+}
+
+hmc_status hmc_batch_sample_chain(hmc_batch* b, float* const* x_inout, const int64_t* num_burnin,
+                                  const int64_t* num_results, float* const* samples_out,
+                                  float* const* trace_step_size, uint8_t* const* trace_accept) {
+  if (!b) return bfail(nullptr, HMC_E_INVALID, "batch is NULL");
+  if (!x_inout || !num_burnin || !num_results)
+    return bfail(b, HMC_E_INVALID, "x_inout, num_burnin and num_results must be non-NULL");
+  long long T = 0;
+  std::vector<const void*> key;
+  for (int i = 0; i < b->n; ++i) {
+    if (!x_inout[i]) return bfail(b, HMC_E_INVALID, "x_inout[" + std::to_string(i) + "] is NULL");
+    if (num_burnin[i] < 0 || num_results[i] < 0) return bfail(b, HMC_E_INVALID, "negative step count");
+    T = std::max<long long>(T, num_burnin[i] + num_results[i]);
+    hmc_kernel_results r{};
+    hmc::BatchPost& P = b->host_posts[i];
+    P.B = num_burnin[i];
+    P.K = num_results[i];
+    P.samples = samples_out ? samples_out[i] : nullptr;
+    P.trace_eps = trace_step_size ? trace_step_size[i] : nullptr;
+    P.trace_acc = trace_accept ? trace_accept[i] : nullptr;
+    key.insert(key.end(), {x_inout[i], P.samples, P.trace_eps, P.trace_acc,
+                           reinterpret_cast<const void*>(P.B), reinterpret_cast<const void*>(P.K)});
+  }
+  if (T > static_cast<long long>(0xFFFFFFFFll)) return bfail(b, HMC_E_INVALID, "too many transitions");
+  cudaError_t e;
+  const bool hit = b->graph && key == b->g_key;
+  if (!hit) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    if (!b->cap_stream) {
+      e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, cudaGetErrorString(e));
+    }
+    // per-posterior step arguments (state pointers live in each context)
+    for (int i = 0; i < b->n; ++i) {
+      hmc::BatchPost& P = b->host_posts[i];
+      hmc::StepArgs a = hmc::ctx_step_args(b->ctx[i], x_inout[i], 0);
+      P.s = a;
+    }
+    const uint64_t l0 = hmc::g_launches.load();
+    e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+    hmc_status st = HMC_OK;
+    e = cudaMemcpyAsync(b->dev_posts, b->host_posts.data(), sizeof(hmc::BatchPost) * b->n,
+                        cudaMemcpyHostToDevice, b->cap_stream);
+    for (int i = 0; i < b->n && st == HMC_OK && e == cudaSuccess; ++i)
+      st = hmc::ctx_bootstrap_on(b->ctx[i], x_inout[i], b->cap_stream);
+    for (long long t = 0; t < T && st == HMC_OK && e == cudaSuccess; ++t) {
+      hmc::k_batch_transition<<<b->num_items, 256, b->smem, b->cap_stream>>>(
+          b->dev_posts, b->dev_items, static_cast<uint32_t>(t));
+      hmc::count_launch();
+      e = cudaGetLastError();
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+    if (st != HMC_OK || e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (st != HMC_OK) return bfail(b, st, "bootstrap failed");
+      return bfail(b, HMC_E_CUDA, std::string("batch capture: ") +
+                                      cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->graph = nullptr;
+      return bfail(b, HMC_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    b->g_launches = hmc::g_launches.load() - l0;
+    hmc::g_launches.fetch_sub(b->g_launches);
+    b->g_key = key;
+  }
+  e = cudaGraphLaunch(b->graph, b->stream);
+  if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  hmc::count_launch(b->g_launches);
+  return HMC_OK;
+}
+
+hmc_status hmc_batch_destroy(hmc_batch* b) {
+  if (!b) return HMC_OK;
+  cudaStreamSynchronize(b->stream);
+  batch_release(b);
+  delete b;
+  return HMC_OK;
+}
+
+const char* hmc_batch_last_error(const hmc_batch* b) { return b ? b->err.c_str() : ""; }
+
+hmc_ctx* hmc_batch_context(hmc_batch* b, int32_t i) {
+  if (!b || i < 0 || i >= b->n) return nullptr;
+  return b->ctx[i];
+}
+
+}  // extern "C"

@@ -143,27 +143,28 @@ __device__ __forceinline__ void da_update(DAState* s, double alpha, long long t)
   s->eps = static_cast<float>(exp(next));
 }
 
-// Deterministic grid-wide reduction of per-block partial sums followed by the
-// dual-averaging update: every block stores its partial, the last block to
-// arrive sums all partials in block order (so the result does not depend on
-// arrival order), updates the state and re-arms the counter.
-__device__ __forceinline__ void block_partial_then_da(DAState* s, double* partials,
-                                                      double block_sum, int num_chains,
-                                                      long long t) {
+// Deterministic reduction of per-tile partial sums followed by the
+// dual-averaging update: every tile (CTA) of a posterior stores its partial,
+// the last tile to arrive sums all partials in tile order (so the result does
+// not depend on arrival order), updates the state and re-arms the counter.
+// `tile` / `ntiles` index the CTAs of this posterior (the whole grid when one
+// launch serves one posterior).
+__device__ __forceinline__ void tile_partial_then_da(DAState* s, double* partials, double block_sum,
+                                                     int num_chains, long long t, int tile,
+                                                     int ntiles) {
   __shared__ bool last;
   if (threadIdx.x == 0) {
-    partials[blockIdx.x] = block_sum;
+    partials[tile] = block_sum;
     __threadfence();
     const unsigned int prev = atomicAdd(&s->arrive, 1u);
-    last = (prev == gridDim.x - 1);
+    last = (prev == static_cast<unsigned int>(ntiles) - 1u);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   double acc = 0.0;
   if (threadIdx.x < 32) {
-    for (unsigned int b = threadIdx.x; b < gridDim.x; b += 32)
-      acc += static_cast<volatile double*>(partials)[b];
+    for (int b = threadIdx.x; b < ntiles; b += 32) acc += static_cast<volatile double*>(partials)[b];
     acc = warp_sum_d(acc);
     if (threadIdx.x == 0) {
       da_update(s, acc / static_cast<double>(num_chains), t);
@@ -173,12 +174,19 @@ __device__ __forceinline__ void block_partial_then_da(DAState* s, double* partia
   }
 }
 
+__device__ __forceinline__ void block_partial_then_da(DAState* s, double* partials, double block_sum,
+                                                      int num_chains, long long t) {
+  tile_partial_then_da(s, partials, block_sum, num_chains, t, static_cast<int>(blockIdx.x),
+                       static_cast<int>(gridDim.x));
+}
+
 // Sum of one acceptance probability per warp of this block (warps with no
 // chain pass has_chain = false), in warp order, then the deterministic grid
 // reduction and dual-averaging update.
 template <int kWarps>
-__device__ __forceinline__ void accept_block_finish(DAState* da, double* partials, float prob,
-                                                    bool has_chain, int num_chains, long long t) {
+__device__ __forceinline__ void accept_tile_finish(DAState* da, double* partials, float prob,
+                                                   bool has_chain, int num_chains, long long t,
+                                                   int tile, int ntiles) {
   __shared__ float warp_prob[kWarps];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) warp_prob[w] = has_chain ? prob : 0.f;
@@ -186,7 +194,14 @@ __device__ __forceinline__ void accept_block_finish(DAState* da, double* partial
   double sum = 0.0;
   if (threadIdx.x == 0)
     for (int i = 0; i < kWarps; ++i) sum += static_cast<double>(warp_prob[i]);
-  block_partial_then_da(da, partials, sum, num_chains, t);
+  tile_partial_then_da(da, partials, sum, num_chains, t, tile, ntiles);
+}
+
+template <int kWarps>
+__device__ __forceinline__ void accept_block_finish(DAState* da, double* partials, float prob,
+                                                    bool has_chain, int num_chains, long long t) {
+  accept_tile_finish<kWarps>(da, partials, prob, has_chain, num_chains, t,
+                             static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x));
 }
 
 // Split x into its tf32 head (10 explicit mantissa bits) and the exact float32

@@ -166,3 +166,12 @@ cudaError_t launch_gauss_tc_transition(const StepArgs& a, GaussTc& tc, cudaStrea
 
 }  // namespace hmc
 
+struct hmc_ctx;
+
+namespace hmc {
+// Step arguments of context `ctx` for state x at transition t (no traces).
+StepArgs ctx_step_args(hmc_ctx* ctx, float* x, uint64_t t);
+// hmc_bootstrap of `ctx` enqueued on stream s instead of its own stream.
+hmc_status ctx_bootstrap_on(hmc_ctx* ctx, const float* x0, cudaStream_t s);
+}  // namespace hmc
+

@@ -66,6 +66,12 @@ def _load():
         "hmc_target_log_prob_and_grad": [ctypes.POINTER(hmc_target), ctypes.c_int64, P, P, P, P,
                                          ctypes.c_uint64, P],
         "hmc_synchronize": [P],
+        "hmc_batch_create": [ctypes.c_int32, ctypes.POINTER(hmc_target), ctypes.POINTER(ctypes.c_int64),
+                             ctypes.POINTER(hmc_config), P, ctypes.POINTER(P)],
+        "hmc_batch_sample_chain": [P, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(P),
+                                   ctypes.POINTER(P), ctypes.POINTER(P)],
+        "hmc_batch_destroy": [P],
         "hmc_sample_chain_streaming": [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P, P],
         "hmc_dominant_kernel_info": [P, ctypes.c_char_p, ctypes.c_int32,
                                      ctypes.POINTER(ctypes.c_int64)],
@@ -90,6 +96,10 @@ def _load():
     lib.hmc_last_error.restype = ctypes.c_char_p
     lib.hmc_uses_tensor_cores.argtypes = [P]
     lib.hmc_uses_tensor_cores.restype = ctypes.c_int32
+    lib.hmc_batch_last_error.argtypes = [P]
+    lib.hmc_batch_last_error.restype = ctypes.c_char_p
+    lib.hmc_batch_context.argtypes = [P, ctypes.c_int32]
+    lib.hmc_batch_context.restype = P
     lib.hmc_kernel_launch_count.argtypes = []
     lib.hmc_kernel_launch_count.restype = ctypes.c_uint64
     return lib
@@ -265,3 +275,37 @@ def hmc_sample_chain_streaming(ctx, x_inout, num_burnin, num_results, mean_out, 
     _check(lib.hmc_sample_chain_streaming(ctx, _ptr(x_inout), int(num_burnin), int(num_results),
                                           _ptr(mean_out), _ptr(m2_out), _ptr(trace_step_size),
                                           _ptr(trace_accept)), ctx)
+
+
+def _check_batch(status, batch):
+    if status != HMC_OK:
+        msg = lib.hmc_batch_last_error(batch) if batch else lib.hmc_last_error(None)
+        raise HMCError(status, msg.decode() if msg else "")
+
+
+def hmc_batch_create(targets, num_chains, configs, stream=None):
+    n = len(targets)
+    T = (hmc_target * n)(*targets)
+    Cs = (ctypes.c_int64 * n)(*[int(c) for c in num_chains])
+    G = (hmc_config * n)(*configs)
+    out = ctypes.c_void_p()
+    _check_batch(lib.hmc_batch_create(n, T, Cs, G, _stream(stream), ctypes.byref(out)), None)
+    return out.value
+
+
+def hmc_batch_sample_chain(batch, xs, num_burnin, num_results, samples=None, trace_step_size=None,
+                           trace_accept=None):
+    n = len(xs)
+    arr = lambda seq: (ctypes.c_void_p * n)(*[_ptr(v) for v in seq]) if seq is not None else None
+    B = (ctypes.c_int64 * n)(*[int(v) for v in num_burnin])
+    K = (ctypes.c_int64 * n)(*[int(v) for v in num_results])
+    _check_batch(lib.hmc_batch_sample_chain(batch, arr(xs), B, K, arr(samples), arr(trace_step_size),
+                                            arr(trace_accept)), batch)
+
+
+def hmc_batch_context(batch, i):
+    return lib.hmc_batch_context(batch, int(i))
+
+
+def hmc_batch_destroy(batch):
+    _check_batch(lib.hmc_batch_destroy(batch), None)

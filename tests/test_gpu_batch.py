@@ -1,0 +1,77 @@
+"""Batched posteriors of uneven size in one grouped launch per transition:
+every posterior's chains must follow exactly the transitions they follow
+when the posterior is sampled alone (same seeds, same kernels), and each
+posterior adapts its own step size."""
+import numpy as np
+import pytest
+
+from paper_2002_01184_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2002_01184_gb300 import build
+    build.build()
+    from paper_2002_01184_gb300 import hmc
+    return hmc
+
+
+def small_batch():
+    return workloads.uneven_batch(seed=5, n_logreg=5, n_funnel=3, num_burnin=15, num_results=10,
+                                  dim_range=(8, 64), n_range=(50, 400), chain_range=(9, 70),
+                                  funnel_dim_range=(10, 40))
+
+
+def test_batch_equals_each_posterior_alone(H):
+    from paper_2002_01184_gb300.sampler import Sampler
+    probs = small_batch()
+    probs[1].num_burnin, probs[1].num_results = 5, 4      # uneven schedules too
+    dev = lambda a: torch.as_tensor(a).cuda().contiguous()
+    keep = []
+    targets, chains, configs = [], [], []
+    for p in probs:
+        Xd = dev(p.X) if p.X is not None else None
+        yd = dev(p.y) if p.y is not None else None
+        keep.append((Xd, yd))
+        targets.append(H.make_target(p.kind, p.dim, None, Xd, yd))
+        chains.append(p.num_chains)
+        configs.append(H.make_config(p.num_leapfrog, p.step_size, p.seed, p.adapt, p.target_accept,
+                                     p.num_burnin))
+    batch = H.hmc_batch_create(targets, chains, configs)
+    xs = [dev(p.x0) for p in probs]
+    samples = [torch.empty((p.num_results, p.num_chains, p.dim), device="cuda") for p in probs]
+    eps = [torch.empty(p.num_results, device="cuda") for p in probs]
+    acc = [torch.empty((p.num_results, p.num_chains), dtype=torch.uint8, device="cuda") for p in probs]
+    for rep in range(2):                    # capture, then replay the graph
+        xs = [dev(p.x0) for p in probs] if rep == 0 else xs
+        if rep == 1:
+            for x, p in zip(xs, probs):
+                x.copy_(dev(p.x0))
+        H.hmc_batch_sample_chain(batch, xs, [p.num_burnin for p in probs],
+                                 [p.num_results for p in probs], samples, eps, acc)
+        torch.cuda.synchronize()
+        for i, p in enumerate(probs):
+            s = Sampler(p)
+            x = dev(p.x0)
+            smp, e, a = s.sample_chain(x, p.num_burnin, p.num_results)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(xs[i].cpu().numpy(), x.cpu().numpy())
+            np.testing.assert_array_equal(samples[i].cpu().numpy(), smp.cpu().numpy())
+            np.testing.assert_array_equal(eps[i].cpu().numpy(), e.cpu().numpy())
+            np.testing.assert_array_equal(acc[i].cpu().numpy(), a.cpu().numpy())
+            s.close()
+    H.hmc_batch_destroy(batch)
+
+
+def test_batch_rejects_unsupported_targets(H):
+    p = workloads.corr_gauss(dim=8, num_chains=4)
+    P = torch.as_tensor(p.P).cuda()
+    with pytest.raises(H.HMCError) as ei:
+        H.hmc_batch_create([H.make_target("corr_gauss", 8, P)], [4], [H.make_config(2, 0.1)])
+    assert ei.value.status == H.HMC_E_UNSUPPORTED
