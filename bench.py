@@ -46,11 +46,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="corr_gauss",
-                    choices=["corr_gauss", "logreg", "funnel", "std_normal"])
+                    choices=["corr_gauss", "logreg", "funnel", "std_normal", "uneven_batch", "serve"])
     ap.add_argument("--plain", action="store_true", help="one launch per op per leapfrog step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--batch-scale", type=float, default=0.04,
+                    help="uneven_batch: fraction of the 500 + 1000 transitions run per posterior")
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-duration", type=float, default=10.0)
+    ap.add_argument("--serve-scale", type=float, default=0.1,
+                    help="serve: scale of chains, samples and data rows of every request")
     ap.add_argument("--small", action="store_true",
                     help="20 burn-in + 20 kept transitions (profiling runs)")
     return ap.parse_args()
@@ -204,10 +210,119 @@ def cpu_oracle_rate(p, seconds):
             "ms_per_transition": 1000.0 * el / n}
 
 
+def run_uneven_batch(args):
+    """64 logistic regressions + 16 funnels of uneven size in one grouped
+    launch per transition (ours) or one posterior after another through the
+    plain one-launch-per-operation path (--plain)."""
+    import numpy as np
+    import torch
+    from paper_2002_01184_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2002_01184_gb300 import diagnostics, hmc, workloads
+    from paper_2002_01184_gb300.sampler import Sampler
+    torch.cuda.set_device(0)
+    B = max(1, int(round(500 * args.batch_scale)))
+    K = max(2, int(round(1000 * args.batch_scale)))
+    probs = workloads.uneven_batch(num_burnin=B, num_results=K)
+    dev = lambda a: None if a is None else torch.as_tensor(a).cuda().contiguous()
+    data = [(dev(p.X), dev(p.y)) for p in probs]
+    xs0 = [dev(p.x0) for p in probs]
+    xs = [torch.empty_like(x) for x in xs0]
+    samples = [torch.empty((K, p.num_chains, p.dim), device="cuda") for p in probs]
+    evals = sum(p.num_chains * p.num_leapfrog * (B + K) + p.num_chains for p in probs)
+    stream = torch.cuda.current_stream()
+    if args.plain:
+        samplers = [Sampler(p, impl=hmc.HMC_IMPL_PLAIN, stream=stream) for p in probs]
+
+        def step():
+            for s_, x, x0, smp, p in zip(samplers, xs, xs0, samples, probs):
+                x.copy_(x0)
+                hmc.hmc_sample_chain(s_.ctx, x, B, K, smp, None, None)
+    else:
+        targets = [hmc.make_target(p.kind, p.dim, None, X, y) for p, (X, y) in zip(probs, data)]
+        configs = [hmc.make_config(p.num_leapfrog, p.step_size, p.seed, p.adapt, p.target_accept, B)
+                   for p in probs]
+        batch = hmc.hmc_batch_create(targets, [p.num_chains for p in probs], configs, stream)
+
+        def step():
+            for x, x0 in zip(xs, xs0):
+                x.copy_(x0)
+            hmc.hmc_batch_sample_chain(batch, xs, [B] * len(probs), [K] * len(probs), samples)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = hmc.hmc_kernel_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    launches = hmc.hmc_kernel_launch_count() - launches0
+    ess = min(float(diagnostics.ess(smp, max_dims=16).min()) for smp in samples)
+    line = {"metric": "leapfrog grad-evals/s", "value": evals / (ms / 1000.0), "unit": "grad-evals/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"uneven batch: 64 logreg (D,N,C log-uniform [8,512],[500,20000],"
+                                   f"[64,4096]) + 16 funnels (d in [10,200]), L=10, DA(0.8), "
+                                   f"B={B} K={K} (fraction {args.batch_scale} of 500+1000)",
+                       "impl": "plain, one posterior after another" if args.plain
+                       else "one grouped launch per transition, CUDA graph",
+                       "posteriors": len(probs)},
+            "min_ess_per_s": ess / (ms / 1000.0), "min_ess": ess,
+            "gpu_launches": int(launches), "clocks": clk, "roofline": None, "cpu_baseline": None,
+            "e2e": None}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Poisson request stream through the continuous-batching server."""
+    import torch
+    from paper_2002_01184_gb300 import build as libbuild
+    libbuild.build()
+    from paper_2002_01184_gb300 import hmc, serve, workloads
+    torch.cuda.set_device(0)
+    reqs = workloads.serve_stream(rate=args.serve_rate, duration=args.serve_duration,
+                                  size_scale=args.serve_scale)
+    # warm-up: a few requests through a throwaway server
+    serve.Server(hbm_budget_bytes=150 * 2 ** 30, slots=16).run(reqs[:4], time_scale=1e9)
+    launches0 = hmc.hmc_kernel_launch_count()
+    clocks = ClockSampler(0)
+    clocks.start()
+    server = serve.Server(hbm_budget_bytes=150 * 2 ** 30, slots=32)
+    jobs = server.run(reqs, max_wall=max(60.0, 6 * args.serve_duration))
+    clk = clocks.stop()
+    summ = serve.summarize(jobs, server.wall)
+    line = {"metric": "leapfrog grad-evals/s", "value": summ["grad_evals_per_s"],
+            "unit": "grad-evals/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": 1000.0 * server.wall, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"served stream: Poisson {args.serve_rate}/s for "
+                                   f"{args.serve_duration} s, requests from corr_gauss / logreg / "
+                                   f"uneven families, chains/samples/data rows scaled by "
+                                   f"{args.serve_scale}, HBM budget 150 GB, 32 slots",
+                       "impl": "continuous batching (slot streams, admission by HBM budget)"},
+            "serve": summ, "min_ess_per_s": summ["min_ess_per_s"],
+            "gpu_launches": int(hmc.hmc_kernel_launch_count() - launches0), "clocks": clk,
+            "roofline": None, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "uneven_batch":
+        run_uneven_batch(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
     import numpy as np
     import torch

@@ -207,11 +207,16 @@ const char* hmc_last_error(const hmc_ctx* ctx);
 /* ---- Batches of posteriors ------------------------------------------------
  * Many posteriors of uneven dimension, data size and chain count sampled
  * together (the independent-chain batching of Section 2 applied across
- * posteriors): each transition of every posterior is one tile of a single
- * grouped kernel launch, largest tiles first, and the whole loop runs as one
- * CUDA graph.  Each posterior keeps its own state, kernel results and
- * dual-averaging step size.  Supported families: LOGREG (dim <= 512), FUNNEL
- * and STD_NORMAL (dim <= 1024); others give HMC_E_UNSUPPORTED. */
+ * posteriors).  Funnels, standard normals and logistic regressions with at
+ * most 2048 data rows share one grouped kernel launch per transition (one
+ * tile per 8 chains, largest tiles first), the whole loop as one CUDA graph;
+ * logistic regressions with longer data passes run their tiled-product
+ * transitions on streams of their own, concurrently.  Each posterior keeps
+ * its own state, kernel results and dual-averaging step size, so its result
+ * equals sampling it alone.  Supported families: LOGREG (dim <= 512), FUNNEL
+ * and STD_NORMAL (dim <= 1024); others give HMC_E_UNSUPPORTED.  All work is
+ * ordered after prior work on the batch's stream and the stream waits for
+ * all of it. */
 typedef struct hmc_batch hmc_batch;
 
 /* Create a batch of num_posteriors posteriors: targets[i], num_chains[i] and

@@ -1,12 +1,18 @@
 // Many posteriors of uneven dimension, data size and chain count sampled
-// together: every transition of every posterior is one CTA tile of a single
-// grouped launch (k_batch_transition), the tiles of all posteriors side by
-// side, ordered by their estimated cost so the largest start first.  Each
-// posterior keeps its own chain state, kernel results and dual-averaging
-// scalar; the adaptation reduction runs over that posterior's tiles only.
-// The whole sampling loop (bootstraps + one grouped launch per transition) is
-// captured as one CUDA graph.  Section 2's premise -- independent chains,
-// batched evaluation -- applied across posteriors.
+// together (Section 2's premise -- independent chains, batched evaluation --
+// applied across posteriors).  Two kinds of members:
+//   grouped: every transition of every such posterior is one CTA tile of a
+//     single grouped launch (k_batch_transition), the tiles of all of them
+//     side by side, ordered by estimated cost so the largest start first;
+//     the whole loop (bootstraps + one grouped launch per transition) is one
+//     CUDA graph.  Funnels, standard normals and logistic regressions with at
+//     most kGroupedMaxRows data rows.
+//   side: logistic regressions with longer data passes, whose gradients are
+//     tiled products (the one-launch-per-operation path) on a stream of
+//     their own, running concurrently with the grouped graph.
+// Each posterior keeps its own chain state, kernel results and
+// dual-averaging scalar; a grouped posterior's adaptation reduction runs over
+// its own tiles only, so every member's result equals sampling it alone.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -67,6 +73,12 @@ __global__ void __launch_bounds__(256) k_batch_transition(const BatchPost* __res
   }
 }
 
+constexpr int64_t kGroupedMaxRows = 2048;
+
+bool grouped_member(const hmc_target& t) {
+  return t.id != HMC_T_LOGREG || t.n_data <= kGroupedMaxRows;
+}
+
 int blocks_per_lane(int D) {
   const int nblk = (D + 3) / 4;
   return nblk <= 32 ? 1 : nblk <= 64 ? 2 : nblk <= 128 ? 4 : 8;
@@ -81,7 +93,11 @@ struct hmc_batch {
   std::vector<hmc_ctx*> ctx;
   std::vector<hmc_target> targets;
   std::vector<int64_t> chains;
-  std::vector<hmc::BatchPost> host_posts;
+  std::vector<hmc::BatchPost> host_posts;   // grouped members only
+  std::vector<int> member;                  // posterior -> index in host_posts, or -1 (side)
+  std::vector<cudaStream_t> side_stream;    // per posterior (side members), else null
+  std::vector<cudaEvent_t> side_done;
+  cudaEvent_t fork = nullptr;
   hmc::BatchPost* dev_posts = nullptr;
   int2* dev_items = nullptr;
   int num_items = 0;
@@ -102,6 +118,11 @@ hmc_status bfail(hmc_batch* b, hmc_status st, const std::string& m) {
 }
 
 void batch_release(hmc_batch* b) {
+  for (cudaStream_t st : b->side_stream)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->side_done)
+    if (ev) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->dev_posts) cudaFree(b->dev_posts);
@@ -142,10 +163,24 @@ hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
                        ": supported are LOGREG (dim <= 512), FUNNEL and STD_NORMAL (dim <= 1024)");
     }
     hmc_config c = configs[i];
-    c.impl = HMC_IMPL_FUSED;
+    const bool grouped = hmc::grouped_member(t);
+    c.impl = grouped ? HMC_IMPL_FUSED : HMC_IMPL_PLAIN;
     c.use_graph = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t done = nullptr;
+    if (!grouped) {
+      if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        batch_release(b);
+        delete b;
+        return bfail(nullptr, HMC_E_CUDA, "side stream creation failed");
+      }
+    }
+    b->side_stream.push_back(side);
+    b->side_done.push_back(done);
     hmc_ctx* ctx = nullptr;
-    hmc_status st = hmc_create(&t, num_chains[i], &c, cuda_stream, &ctx);
+    hmc_status st = hmc_create(&t, num_chains[i], &c, grouped ? cuda_stream : side, &ctx);
     if (st != HMC_OK) {
       const std::string m = "batch posterior " + std::to_string(i) + ": " + hmc_last_error(nullptr);
       batch_release(b);
@@ -155,6 +190,10 @@ hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
     b->ctx.push_back(ctx);
     b->targets.push_back(t);
     b->chains.push_back(num_chains[i]);
+    if (!grouped) {
+      b->member.push_back(-1);
+      continue;
+    }
     hmc::BatchPost P{};
     P.kind = t.id;
     P.nb = hmc::blocks_per_lane(t.dim);
@@ -162,9 +201,11 @@ hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
     P.n_data = static_cast<int>(t.n_data);
     P.X = t.X;
     P.y = t.y;
+    b->member.push_back(static_cast<int>(b->host_posts.size()));
     b->host_posts.push_back(P);
     const double cost = tile_cost(t, c);
-    for (int tile = 0; tile < P.ntiles; ++tile) items.push_back({cost, make_int2(i, tile)});
+    const int gi = b->member.back();
+    for (int tile = 0; tile < P.ntiles; ++tile) items.push_back({cost, make_int2(gi, tile)});
     if (t.id == HMC_T_LOGREG) b->smem = std::max(b->smem, hmc::lr::logreg_smem_bytes(t.dim));
   }
   std::stable_sort(items.begin(), items.end(),
@@ -172,9 +213,11 @@ hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
   std::vector<int2> flat;
   for (auto& it : items) flat.push_back(it.second);
   b->num_items = static_cast<int>(flat.size());
-  cudaError_t e = cudaMalloc(&b->dev_posts, sizeof(hmc::BatchPost) * b->n);
-  if (e == cudaSuccess) e = cudaMalloc(&b->dev_items, sizeof(int2) * flat.size());
-  if (e == cudaSuccess)
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && !b->host_posts.empty())
+    e = cudaMalloc(&b->dev_posts, sizeof(hmc::BatchPost) * b->host_posts.size());
+  if (e == cudaSuccess && !flat.empty()) e = cudaMalloc(&b->dev_items, sizeof(int2) * flat.size());
+  if (e == cudaSuccess && !flat.empty())
     e = cudaMemcpy(b->dev_items, flat.data(), sizeof(int2) * flat.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && b->smem > 0)
     e = cudaFuncSetAttribute(hmc::k_batch_transition, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -201,9 +244,11 @@ hmc_status hmc_batch_sample_chain(hmc_batch* b, float* const* x_inout, const int
   for (int i = 0; i < b->n; ++i) {
     if (!x_inout[i]) return bfail(b, HMC_E_INVALID, "x_inout[" + std::to_string(i) + "] is NULL");
     if (num_burnin[i] < 0 || num_results[i] < 0) return bfail(b, HMC_E_INVALID, "negative step count");
+    if (num_burnin[i] + num_results[i] > 0xFFFFFFFFll)
+      return bfail(b, HMC_E_INVALID, "too many transitions");
+    if (b->member[i] < 0) continue;
     T = std::max<long long>(T, num_burnin[i] + num_results[i]);
-    hmc_kernel_results r{};
-    hmc::BatchPost& P = b->host_posts[i];
+    hmc::BatchPost& P = b->host_posts[b->member[i]];
     P.B = num_burnin[i];
     P.K = num_results[i];
     P.samples = samples_out ? samples_out[i] : nullptr;
@@ -212,57 +257,77 @@ hmc_status hmc_batch_sample_chain(hmc_batch* b, float* const* x_inout, const int
     key.insert(key.end(), {x_inout[i], P.samples, P.trace_eps, P.trace_acc,
                            reinterpret_cast<const void*>(P.B), reinterpret_cast<const void*>(P.K)});
   }
-  if (T > static_cast<long long>(0xFFFFFFFFll)) return bfail(b, HMC_E_INVALID, "too many transitions");
-  cudaError_t e;
-  const bool hit = b->graph && key == b->g_key;
-  if (!hit) {
-    if (b->graph) cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
-    if (!b->cap_stream) {
-      e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
-      if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, cudaGetErrorString(e));
-    }
-    // per-posterior step arguments (state pointers live in each context)
-    for (int i = 0; i < b->n; ++i) {
-      hmc::BatchPost& P = b->host_posts[i];
-      hmc::StepArgs a = hmc::ctx_step_args(b->ctx[i], x_inout[i], 0);
-      P.s = a;
-    }
-    const uint64_t l0 = hmc::g_launches.load();
-    e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
-    hmc_status st = HMC_OK;
-    e = cudaMemcpyAsync(b->dev_posts, b->host_posts.data(), sizeof(hmc::BatchPost) * b->n,
-                        cudaMemcpyHostToDevice, b->cap_stream);
-    for (int i = 0; i < b->n && st == HMC_OK && e == cudaSuccess; ++i)
-      st = hmc::ctx_bootstrap_on(b->ctx[i], x_inout[i], b->cap_stream);
-    for (long long t = 0; t < T && st == HMC_OK && e == cudaSuccess; ++t) {
-      hmc::k_batch_transition<<<b->num_items, 256, b->smem, b->cap_stream>>>(
-          b->dev_posts, b->dev_items, static_cast<uint32_t>(t));
-      hmc::count_launch();
-      e = cudaGetLastError();
-    }
-    cudaGraph_t g = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
-    if (st != HMC_OK || e != cudaSuccess || e2 != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      if (st != HMC_OK) return bfail(b, st, "bootstrap failed");
-      return bfail(b, HMC_E_CUDA, std::string("batch capture: ") +
-                                      cudaGetErrorString(e != cudaSuccess ? e : e2));
-    }
-    e = cudaGraphInstantiate(&b->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      b->graph = nullptr;
-      return bfail(b, HMC_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    }
-    b->g_launches = hmc::g_launches.load() - l0;
-    hmc::g_launches.fetch_sub(b->g_launches);
-    b->g_key = key;
+  cudaError_t e = cudaEventRecord(b->fork, b->stream);
+  if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, std::string("fork: ") + cudaGetErrorString(e));
+  // side members: their own streams, concurrent with the grouped graph
+  for (int i = 0; i < b->n; ++i) {
+    if (b->member[i] >= 0) continue;
+    e = cudaStreamWaitEvent(b->side_stream[i], b->fork, 0);
+    if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, std::string("side wait: ") + cudaGetErrorString(e));
+    hmc_status st = hmc_sample_chain(b->ctx[i], x_inout[i], num_burnin[i], num_results[i],
+                                     samples_out ? samples_out[i] : nullptr,
+                                     trace_step_size ? trace_step_size[i] : nullptr,
+                                     trace_accept ? trace_accept[i] : nullptr);
+    if (st != HMC_OK)
+      return bfail(b, st, "side posterior " + std::to_string(i) + ": " + hmc_last_error(b->ctx[i]));
+    e = cudaEventRecord(b->side_done[i], b->side_stream[i]);
+    if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, std::string("side record: ") + cudaGetErrorString(e));
   }
-  e = cudaGraphLaunch(b->graph, b->stream);
-  if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
-  hmc::count_launch(b->g_launches);
+  if (!b->host_posts.empty()) {
+    const bool hit = b->graph && key == b->g_key;
+    if (!hit) {
+      if (b->graph) cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+      if (!b->cap_stream) {
+        e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, cudaGetErrorString(e));
+      }
+      for (int i = 0; i < b->n; ++i)
+        if (b->member[i] >= 0) b->host_posts[b->member[i]].s = hmc::ctx_step_args(b->ctx[i], x_inout[i], 0);
+      const uint64_t l0 = hmc::g_launches.load();
+      e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess)
+        return bfail(b, HMC_E_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+      hmc_status st = HMC_OK;
+      e = cudaMemcpyAsync(b->dev_posts, b->host_posts.data(),
+                          sizeof(hmc::BatchPost) * b->host_posts.size(), cudaMemcpyHostToDevice,
+                          b->cap_stream);
+      for (int i = 0; i < b->n && st == HMC_OK && e == cudaSuccess; ++i)
+        if (b->member[i] >= 0) st = hmc::ctx_bootstrap_on(b->ctx[i], x_inout[i], b->cap_stream);
+      for (long long t = 0; t < T && st == HMC_OK && e == cudaSuccess; ++t) {
+        hmc::k_batch_transition<<<b->num_items, 256, b->smem, b->cap_stream>>>(
+            b->dev_posts, b->dev_items, static_cast<uint32_t>(t));
+        hmc::count_launch();
+        e = cudaGetLastError();
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+      if (st != HMC_OK || e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (st != HMC_OK) return bfail(b, st, "bootstrap failed");
+        return bfail(b, HMC_E_CUDA, std::string("batch capture: ") +
+                                        cudaGetErrorString(e != cudaSuccess ? e : e2));
+      }
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return bfail(b, HMC_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      }
+      b->g_launches = hmc::g_launches.load() - l0;
+      hmc::g_launches.fetch_sub(b->g_launches);
+      b->g_key = key;
+    }
+    e = cudaGraphLaunch(b->graph, b->stream);
+    if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    hmc::count_launch(b->g_launches);
+  }
+  // join: the caller's stream waits for every side member
+  for (int i = 0; i < b->n; ++i) {
+    if (b->member[i] >= 0) continue;
+    e = cudaStreamWaitEvent(b->stream, b->side_done[i], 0);
+    if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, std::string("join: ") + cudaGetErrorString(e));
+  }
   return HMC_OK;
 }
 

@@ -1,0 +1,157 @@
+"""Continuous-batching sampling server.
+
+Requests (posterior + sampling schedule) arrive over time.  A request is
+admitted as soon as a slot is free and its device memory fits the HBM budget;
+its chain state stays resident on the device for the whole job, its
+transitions are enqueued on the slot's own CUDA stream, so the work of every
+admitted job overlaps on the GPU, and a finished job frees its slot and memory
+for the next one.  All sampling work runs in libhmc's kernels; this loop only
+admits, polls and copies results to the host.  Because every random draw is
+keyed by (seed, chain, transition) and every job owns its state and step-size
+adaptation, a job's result is the same whether it runs alone or in the mix.
+"""
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import diagnostics, hmc
+from .sampler import Sampler
+
+
+def job_bytes(problem, keep_samples=True):
+    """Device bytes a job holds while resident: state, workspace, samples."""
+    C, D, K = problem.num_chains, problem.dim, problem.num_results
+    b = 4 * C * D * 12 + 4 * C * 16
+    if problem.P is not None:
+        b += 8 * D * D
+    if problem.X is not None:
+        b += 4 * problem.X.size + 4 * problem.y.size
+        b += 4 * C * problem.X.shape[0]                       # residual workspace
+    if keep_samples:
+        b += 4 * K * C * D + K * C + 4 * K
+    return int(b)
+
+
+@dataclass
+class Job:
+    id: int
+    arrival: float
+    problem: object
+    admitted: float = None
+    finished: float = None
+    result: dict = field(default_factory=dict)
+    _sampler: object = None
+    _x: object = None
+    _samples: object = None
+    _eps: object = None
+    _acc: object = None
+    _event: object = None
+    _bytes: int = 0
+    _slot: int = -1
+
+
+class Server:
+    def __init__(self, hbm_budget_bytes=150 * 2 ** 30, slots=16, keep_samples=True,
+                 ess_dims=8, device="cuda"):
+        self.budget = int(hbm_budget_bytes)
+        self.used = 0
+        self.keep_samples = keep_samples
+        self.ess_dims = ess_dims
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.free_slots = list(range(slots))
+        self.active = []
+        self.done = []
+
+    # -- admission ---------------------------------------------------------
+    def fits(self, job):
+        return bool(self.free_slots) and self.used + job_bytes(job.problem, self.keep_samples) <= self.budget
+
+    def admit(self, job, now):
+        p = job.problem
+        slot = self.free_slots.pop(0)
+        stream = self.streams[slot]
+        job._slot = slot
+        job._bytes = job_bytes(p, self.keep_samples)
+        self.used += job._bytes
+        job.admitted = now
+        with torch.cuda.stream(stream):
+            job._sampler = Sampler(p, stream=stream, use_graph=False)
+            x = torch.empty((p.num_chains, p.dim), dtype=torch.float32, device="cuda")
+            x.copy_(torch.from_numpy(p.x0).pin_memory(), non_blocking=True)
+            job._x = x
+            K = p.num_results
+            job._samples = torch.empty((K, p.num_chains, p.dim), device="cuda") if self.keep_samples else None
+            job._eps = torch.empty(K, device="cuda")
+            job._acc = torch.empty((K, p.num_chains), dtype=torch.uint8, device="cuda")
+            hmc.hmc_sample_chain(job._sampler.ctx, x, p.num_burnin, K, job._samples, job._eps, job._acc)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            job._event = ev
+        self.active.append(job)
+
+    # -- completion ----------------------------------------------------------
+    def poll(self, now_fn):
+        still = []
+        for job in self.active:
+            if job._event.query():
+                self.finish(job, now_fn())
+            else:
+                still.append(job)
+        self.active = still
+
+    def finish(self, job, now):
+        p = job.problem
+        stream = self.streams[job._slot]
+        with torch.cuda.stream(stream):
+            res = {"x": job._x.cpu().numpy(), "step_size": job._eps.cpu().numpy(),
+                   "accept_rate": float(job._acc.float().mean().item()) if p.num_results else None}
+            if job._samples is not None and p.num_results >= 4:
+                res["min_ess"] = float(diagnostics.ess(job._samples, max_dims=self.ess_dims).min())
+                res["mean"] = job._samples.mean(dim=(0, 1)).cpu().numpy()
+            torch.cuda.current_stream().synchronize()
+        job.finished = now
+        job.result = res
+        job._sampler.close()
+        job._sampler = job._x = job._samples = job._eps = job._acc = None
+        self.used -= job._bytes
+        self.free_slots.append(job._slot)
+        self.done.append(job)
+
+    # -- the loop ------------------------------------------------------------
+    def run(self, requests, time_scale=1.0, max_wall=None):
+        """Serve (arrival_time, problem) requests; arrival times are divided
+        by `time_scale` (to compress a long stream).  Returns the jobs."""
+        jobs = [Job(i, t / time_scale, p) for i, (t, p) in enumerate(requests)]
+        pending = list(jobs)
+        t0 = time.perf_counter()
+        now = lambda: time.perf_counter() - t0
+        while pending or self.active:
+            t = now()
+            if max_wall is not None and t > max_wall:
+                break
+            while pending and pending[0].arrival <= t and self.fits(pending[0]):
+                self.admit(pending.pop(0), now())
+            if pending and pending[0].arrival <= t and not self.active and not self.fits(pending[0]):
+                raise RuntimeError(f"request {pending[0].id} needs more than the HBM budget")
+            self.poll(now)
+            time.sleep(0.0005)
+        self.wall = now()
+        return jobs
+
+
+def summarize(jobs, wall):
+    done = [j for j in jobs if j.finished is not None]
+    lat = np.array([j.finished - j.arrival for j in done]) if done else np.array([np.nan])
+    evals = sum(j.problem.num_chains * j.problem.num_leapfrog *
+                (j.problem.num_burnin + j.problem.num_results) for j in done)
+    offered = sum(j.problem.num_chains * j.problem.num_leapfrog *
+                  (j.problem.num_burnin + j.problem.num_results) for j in jobs)
+    ess = [j.result.get("min_ess") for j in done if j.result.get("min_ess") is not None]
+    span = max(j.arrival for j in jobs) if jobs else 0.0
+    return {"requests": len(jobs), "completed": len(done), "wall_s": wall,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "grad_evals_per_s": evals / wall if wall else None,
+            "offered_grad_evals_per_s": offered / span if span else None,
+            "min_ess_per_s": (min(ess) / wall) if ess and wall else None}

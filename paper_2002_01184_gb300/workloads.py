@@ -138,3 +138,43 @@ def uneven_batch(seed=4, n_logreg=64, n_funnel=16, num_results=1000, num_burnin=
         probs.append(funnel(dim=d, num_chains=C, seed=2000 + i,
                             num_burnin=num_burnin, num_results=num_results))
     return probs
+
+
+def serve_stream(rate=50.0, duration=120.0, seed=6, size_scale=1.0, chain_range=(64, 4096),
+                 sample_range=(200, 2000)):
+    """Poisson arrivals of sampling requests, each a random posterior from the
+    correlated-Gaussian, logistic-regression or uneven-batch families (sizes
+    drawn as for those workloads), with chains and kept samples log-uniform in
+    the given ranges and burn-in = ceil(samples / 2).  `size_scale` shrinks
+    chains, samples and data rows together (for short test streams).
+    Returns a list of (arrival_time_s, Problem)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    i = 0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            break
+        fam = int(rng.integers(0, 3))
+        C = max(8, int(log_uniform_int(rng, *chain_range) * size_scale))
+        K = max(4, int(log_uniform_int(rng, *sample_range) * size_scale))
+        B = (K + 1) // 2
+        s = 10000 + i
+        if fam == 0:
+            p = corr_gauss(dim=256, num_chains=C, seed=s, num_burnin=B, num_results=K)
+        elif fam == 1:
+            p = logreg(n_data=max(64, int(20000 * size_scale)), dim=128, num_chains=C, seed=s,
+                       num_burnin=B, num_results=K)
+        else:
+            if rng.uniform() < 0.8:
+                D = int(log_uniform_int(rng, 8, 512))
+                N = max(64, int(log_uniform_int(rng, 500, 20000) * size_scale))
+                p = logreg(n_data=N, dim=D, num_chains=C, seed=s, num_burnin=B, num_results=K)
+            else:
+                d = int(rng.integers(10, 201))
+                p = funnel(dim=d, num_chains=C, seed=s, num_burnin=B, num_results=K)
+        p.meta["family"] = ["corr_gauss", "logreg", "uneven"][fam]
+        out.append((t, p))
+        i += 1
+    return out

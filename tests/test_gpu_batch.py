@@ -23,9 +23,13 @@ def H():
 
 
 def small_batch():
-    return workloads.uneven_batch(seed=5, n_logreg=5, n_funnel=3, num_burnin=15, num_results=10,
-                                  dim_range=(8, 64), n_range=(50, 400), chain_range=(9, 70),
-                                  funnel_dim_range=(10, 40))
+    probs = workloads.uneven_batch(seed=5, n_logreg=5, n_funnel=3, num_burnin=15, num_results=10,
+                                   dim_range=(8, 64), n_range=(50, 400), chain_range=(9, 70),
+                                   funnel_dim_range=(10, 40))
+    # one member with a long data pass: it runs on a side stream
+    probs.append(workloads.logreg(n_data=2500, dim=16, num_chains=33, seed=77, num_burnin=15,
+                                  num_results=10))
+    return probs
 
 
 def test_batch_equals_each_posterior_alone(H):
@@ -57,7 +61,7 @@ def test_batch_equals_each_posterior_alone(H):
                                  [p.num_results for p in probs], samples, eps, acc)
         torch.cuda.synchronize()
         for i, p in enumerate(probs):
-            s = Sampler(p)
+            s = Sampler(p, impl=1 if (p.kind == "logreg" and p.n_data > 2048) else 0)
             x = dev(p.x0)
             smp, e, a = s.sample_chain(x, p.num_burnin, p.num_results)
             torch.cuda.synchronize()
