@@ -74,8 +74,12 @@ typedef struct {
 } hmc_target;
 
 typedef enum {
-  HMC_IMPL_FUSED = 0,  /* fused transition kernels (default) */
-  HMC_IMPL_PLAIN = 1   /* one kernel launch per operation per leapfrog step */
+  HMC_IMPL_FUSED = 0,             /* fused transition kernels (default); dense
+                                     Gaussians run on CTA pairs (cta_group::2) */
+  HMC_IMPL_PLAIN = 1,             /* one kernel launch per operation per
+                                     leapfrog step */
+  HMC_IMPL_FUSED_SINGLE_CTA = 2   /* as FUSED, but the dense-Gaussian
+                                     transition on single CTAs (32 chains) */
 } hmc_impl;
 
 /* Sampler configuration (the HamiltonianMonteCarlo constructor arguments of

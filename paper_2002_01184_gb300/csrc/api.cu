@@ -111,7 +111,10 @@ bool valid_config(const hmc_config* c, int64_t C, std::string* why) {
     return false;
   }
   if (c->num_adapt_steps < 0) { *why = "num_adapt_steps must be >= 0"; return false; }
-  if (c->impl != HMC_IMPL_FUSED && c->impl != HMC_IMPL_PLAIN) { *why = "unknown impl"; return false; }
+  if (c->impl != HMC_IMPL_FUSED && c->impl != HMC_IMPL_PLAIN && c->impl != HMC_IMPL_FUSED_SINGLE_CTA) {
+    *why = "unknown impl";
+    return false;
+  }
   if (c->use_graph != 0 && c->use_graph != 1) { *why = "use_graph must be 0 or 1"; return false; }
   if (c->chain_offset < 0 || c->chain_offset + C > (1ll << 32)) {
     *why = "chain_offset + num_chains must fit in 32 bits";
@@ -147,12 +150,16 @@ void release(hmc_ctx* ctx) {
   ctx->stage = nullptr;
 }
 
+bool fused_impl(const hmc_ctx* ctx) {
+  return ctx->cfg.impl == HMC_IMPL_FUSED || ctx->cfg.impl == HMC_IMPL_FUSED_SINGLE_CTA;
+}
+
 bool uses_fused_logreg(const hmc_ctx* ctx) {
-  return ctx->cfg.impl == HMC_IMPL_FUSED && hmc::logreg_fused_supported(ctx->target);
+  return fused_impl(ctx) && hmc::logreg_fused_supported(ctx->target);
 }
 
 bool uses_fused_elementwise(const hmc_ctx* ctx) {
-  return ctx->cfg.impl == HMC_IMPL_FUSED &&
+  return fused_impl(ctx) &&
          (ctx->target.id == HMC_T_STD_NORMAL || ctx->target.id == HMC_T_FUNNEL) &&
          ctx->target.dim <= hmc::kFusedElementwiseMaxDim;
 }
@@ -327,6 +334,7 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   // one partial sum per block of whichever transition kernel runs
   const unsigned nblk = std::max({hmc::accept_blocks(static_cast<int>(num_chains)),
                                   hmc::gauss_fused_grid(num_chains),
+                                  hmc::gauss_pair_grid(num_chains),
                                   hmc::logreg_fused_grid(num_chains)});
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->lp, C);
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->g, C * D);
@@ -334,12 +342,14 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->log_accept, C);
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->da, 1);
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->partials, nblk);
-  ctx->use_tc = config->impl == HMC_IMPL_FUSED && hmc::gauss_tc_supported(*target);
+  ctx->use_tc = (config->impl == HMC_IMPL_FUSED || config->impl == HMC_IMPL_FUSED_SINGLE_CTA) &&
+                hmc::gauss_tc_supported(*target);
   if (e == cudaSuccess && ctx->use_tc) {
     char* w = nullptr;
     e = ctx_alloc(ctx, &w, hmc::gauss_tc_workspace_bytes(*target, num_chains));
     if (e == cudaSuccess) e = hmc::gauss_tc_setup(&ctx->tc, *target, num_chains, w, ctx->stream);
     ctx->tc.fused = hmc::gauss_fused_supported(*target);
+    ctx->tc.pair = ctx->tc.fused && config->impl == HMC_IMPL_FUSED;
   }
   if (e == cudaSuccess && uses_fused_logreg(ctx)) e = hmc::logreg_fused_setup(*target);
   if (e == cudaSuccess && !uses_fused_elementwise(ctx) && !ctx->use_tc) {
@@ -550,7 +560,10 @@ hmc_status hmc_dominant_kernel_info(const hmc_ctx* ctx, char* name, int32_t name
     return fail(nullptr, HMC_E_INVALID, "NULL argument");
   const char* n = "";
   int64_t per = ctx->C;
-  if (ctx->use_tc && ctx->tc.fused) {
+  if (ctx->use_tc && ctx->tc.fused && ctx->tc.pair) {
+    n = "k_gauss_pair";
+    per = ctx->C * ctx->cfg.num_leapfrog;
+  } else if (ctx->use_tc && ctx->tc.fused) {
     n = "k_gauss_fused";
     per = ctx->C * ctx->cfg.num_leapfrog;
   } else if (ctx->use_tc) {

@@ -1,0 +1,401 @@
+// One launch per HMC transition for the dense Gaussian target (dim <= 256) on
+// CTA pairs (tcgen05 cta_group::2).  A pair owns 64 chains for the whole
+// transition (Section 2.1): each leapfrog gradient G^T = P X^T is one stream
+// of M = 256 (all output dims), N = 64 (the pair's chains), K = 8 MMAs issued
+// by the pair's leader -- half as many MMA instructions per step as two
+// independent 32-chain CTAs, which matters because a 3xTF32 step at this
+// chain count is bound by the MMA issue rate, not by arithmetic or memory.
+//   * A (P head / remainder, 3xTF32): each CTA streams the 128 rows of P for
+//     its half of the output dims by TMA, completing on the leader's barrier.
+//   * B (positions, head / remainder tiles, 128-byte-swizzled K-major): each
+//     CTA holds 32 of the 64 chains.
+//   * Accumulators: each CTA's tensor memory holds its 128 output dims for
+//     all 64 chains.
+//   * Epilogue (warps 2-9 of both CTAs): one output dim per thread, 32 chains
+//     per thread; momenta and positions stay in registers, the next positions
+//     are written (split) into whichever CTA's tile holds the chain.
+// H_L, the Metropolis-Hastings decision and the dual-averaging partial are
+// formed by the leader from both CTAs' partial sums.
+#include <cuda.h>
+
+#include <cmath>
+
+#include "hmc_device.cuh"
+#include "hmc_internal.h"
+#include "sm100_ptx.cuh"
+
+namespace hmc {
+
+namespace {
+
+constexpr int kMaxDim = 256;
+constexpr int kChunks = kMaxDim / 32;
+constexpr int kThreads = 320;
+constexpr int kPairChains = 64;                   // MMA N
+constexpr int kHalf = 32;                         // chains per CTA (B rows)
+constexpr uint32_t kBChunk = kHalf * 128;         // 32 rows x 128 B
+constexpr uint32_t kBBytes = kChunks * kBChunk;   // head or remainder tile
+constexpr uint32_t kAHalf = 128 * 128;            // 128 rows x 32 floats
+constexpr uint32_t kAStage = 2 * kAHalf;
+constexpr int kStages = 4;
+constexpr uint32_t kTmemCols = 64;
+// barriers, tmem slot, red [2][4][64], red_pair [2][64], peer_in [2][64],
+// acc_flag [64], prob_s [64]
+constexpr uint32_t kSmall = 8 * (2 * kStages + 2) + 16 + (2 * 4 * 64 + 2 * 64 + 2 * 64 + 64 + 64) * 4;
+constexpr size_t kSmem = 2 * kBBytes + kStages * kAStage + kSmall + 1024;
+
+struct PairArgs {
+  StepArgs s;
+  int* err;
+  const float* p0;      // [C x D]
+  const float* kin0;    // [C]
+};
+
+__device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
+  const int kc = k >> 5, cc = k & 31;
+  return kc * kBChunk + (r >> 3) * 1024 + (r & 7) * 128 + ((((cc >> 2) ^ (r & 7)) & 7) << 4) +
+         (cc & 3) * 4;
+}
+
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__device__ __forceinline__ void proxy_fence_cluster() {
+  asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ CUtensorMap mPlo,
+             PairArgs fa) {
+  const StepArgs& a = fa.s;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* Bhi = smem;
+  uint8_t* Blo = smem + kBBytes;
+  uint8_t* Ast = smem + 2 * kBBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(Ast + kStages * kAStage);
+  uint64_t* empty = full + kStages;
+  uint64_t* acc_full = empty + kStages;
+  uint64_t* x_ready = acc_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(x_ready + 1);
+  float* red = reinterpret_cast<float*>(tmem_slot + 4);   // [2][4 quarters][64 chains]
+  float* red_pair = red + 2 * 4 * 64;                     // [2][64] this CTA's sums
+  float* peer_in = red_pair + 2 * 64;                     // [2][64] the peer's sums (leader)
+  int* acc_flag = reinterpret_cast<int*>(peer_in + 2 * 64);   // [64]
+  float* prob_s = reinterpret_cast<float*>(acc_flag + 64);    // [64]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = ptx::cluster_rank();              // 0: leader, 1: peer
+  const int C = a.C, D = a.D, L = a.L;
+  const int nk = (D + 31) >> 5;
+  const int pair_base = (blockIdx.x >> 1) * kPairChains;
+  constexpr uint16_t kPairMask = 0x3;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    ptx::mbar_init(acc_full, 1);
+    ptx::mbar_init(x_ready, 2 * 256);
+    ptx::fence_mbar_init();
+    ptx::prefetch_tensormap(&mPhi);
+    ptx::prefetch_tensormap(&mPlo);
+  }
+  if (warp == 0) {
+    ptx::tmem_alloc_pair(tmem_slot, kTmemCols);
+    ptx::tmem_relinquish_pair();
+  }
+  for (uint32_t i = threadIdx.x; i < 2 * kBBytes / 16; i += kThreads)
+    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::cluster_sync();      // both CTAs' barriers and tensor memory exist
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const float eps = a.da->eps;
+  const uint32_t x_ready_leader = ptx::mapa(ptx::smem_u32(x_ready), 0);
+  bool ok = true;
+
+  // epilogue-thread state (warps 2-9)
+  const int ew = warp - 2;
+  const int h = ew >> 2;                  // chain half 0 / 1 (= the CTA holding those chains)
+  const int quarter = warp & 3;           // tensor-memory lane quarter
+  const int d = static_cast<int>(rank) * 128 + quarter * 32 + lane;
+  const bool dvalid = warp >= 2 && d < D;
+  float p[kHalf], x[kHalf];
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- producer: this CTA's 128 rows of P, completing on the leader's barrier
+      int it = 0;
+      for (int l = 1; l <= L && ok; ++l)
+        for (int kc = 0; kc < nk; ++kc, ++it) {
+          const int s = it % kStages, round = it / kStages;
+          if (it >= kStages && !ptx::mbar_wait(&empty[s], (round - 1) & 1)) {
+            atomicExch(fa.err, 1);
+            ok = false;
+            break;
+          }
+          if (rank == 0) ptx::mbar_arrive_expect_tx(&full[s], 2 * kAStage);
+          const uint32_t bar = ptx::mapa(ptx::smem_u32(&full[s]), 0);
+          uint8_t* st = Ast + s * kAStage;
+          ptx::tma_load_2d_to_bar(st, &mPhi, bar, kc * 32, static_cast<int>(rank) * 128);
+          ptx::tma_load_2d_to_bar(st + kAHalf, &mPlo, bar, kc * 32, static_cast<int>(rank) * 128);
+        }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      // ---- MMA issuer (leader): M = 256 across the pair, N = 64 chains
+      constexpr uint32_t idesc = ptx::idesc_tf32(256, kPairChains);
+      int it = 0;
+      for (int l = 1; l <= L && ok; ++l) {
+        if (!ptx::mbar_wait_cluster(x_ready, (l - 1) & 1)) {
+          atomicExch(fa.err, 1);
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        for (int kc = 0; kc < nk; ++kc, ++it) {
+          const int s = it % kStages, round = it / kStages;
+          if (!ptx::mbar_wait(&full[s], round & 1)) {
+            atomicExch(fa.err, 1);
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t ahi = ptx::smem_u32(Ast + s * kAStage);
+          const uint32_t alo = ahi + kAHalf;
+          const uint32_t bhi = ptx::smem_u32(Bhi + kc * kBChunk);
+          const uint32_t blo = ptx::smem_u32(Blo + kc * kBChunk);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint64_t dahi = ptx::sw128_kmajor_desc(ahi + 32 * j);
+            const uint64_t dalo = ptx::sw128_kmajor_desc(alo + 32 * j);
+            const uint64_t dbhi = ptx::sw128_kmajor_desc(bhi + 32 * j);
+            const uint64_t dblo = ptx::sw128_kmajor_desc(blo + 32 * j);
+            ptx::mma_tf32_pair(tmem, dalo, dbhi, idesc, (kc | j) != 0 ? 1u : 0u);
+            ptx::mma_tf32_pair(tmem, dahi, dblo, idesc, 1u);
+            ptx::mma_tf32_pair(tmem, dahi, dbhi, idesc, 1u);
+          }
+          ptx::mma_commit_pair(&empty[s], kPairMask);
+        }
+        if (!ok) break;
+        ptx::mma_commit_pair(acc_full, kPairMask);
+      }
+    }
+  } else {
+    // ---- epilogue, both CTAs
+    const uint32_t peer = 1u - rank;
+    // B tile element of chain (half h, row i) at dim d: local if h == rank
+    auto tile_store = [&](int i, float hi, float lo) {
+      const uint32_t off = sw128_offset(i, d);
+      if (static_cast<uint32_t>(h) == rank) {
+        *reinterpret_cast<float*>(Bhi + off) = hi;
+        *reinterpret_cast<float*>(Blo + off) = lo;
+      } else {
+        ptx::st_cluster_f32(ptx::mapa(ptx::smem_u32(Bhi + off), peer), hi);
+        ptx::st_cluster_f32(ptx::mapa(ptx::smem_u32(Blo + off), peer), lo);
+      }
+    };
+    // begin: p = p0 + eps/2 g0, x1 = x0 + eps p
+#pragma unroll
+    for (int i8 = 0; i8 < kHalf; i8 += 8) {
+      float xr[8], gr[8], zr[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int chain = pair_base + h * kHalf + i8 + k;
+        const bool valid = dvalid && chain < C;
+        const int64_t e = static_cast<int64_t>(chain) * D + d;
+        xr[k] = valid ? a.x[e] : 0.f;
+        gr[k] = valid ? a.g[e] : 0.f;
+        zr[k] = valid ? fa.p0[e] : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int i = i8 + k;
+        p[i] = fmaf(0.5f * eps, gr[k], zr[k]);
+        x[i] = fmaf(eps, p[i], xr[k]);
+        if (dvalid && pair_base + h * kHalf + i < C) {
+          float hi, lo;
+          split_tf32(x[i], hi, lo);
+          tile_store(i, hi, lo);
+        }
+      }
+    }
+    proxy_fence_cluster();
+    ptx::tc_fence_before();
+    ptx::mbar_arrive_cluster(x_ready_leader);
+    for (int l = 1; l <= L; ++l) {
+      const bool last = l == L;
+      if (!ptx::mbar_wait(acc_full, (l - 1) & 1)) {
+        atomicExch(fa.err, 1);
+        ok = false;
+      }
+      ptx::tc_fence_after();
+#pragma unroll
+      for (int cb = 0; cb < kHalf / 16; ++cb) {
+        float accv[16];
+        ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + h * kHalf + cb * 16, accv);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int i = cb * 16 + k;
+          const float g = -accv[k];
+          if (!last) {
+            p[i] = fmaf(eps, g, p[i]);
+            x[i] = fmaf(eps, p[i], x[i]);
+            if (dvalid && pair_base + h * kHalf + i < C) {
+              float hi, lo;
+              split_tf32(x[i], hi, lo);
+              tile_store(i, hi, lo);
+            }
+          } else {
+            p[i] = fmaf(0.5f * eps, g, p[i]);
+          }
+        }
+      }
+      if (!last) {
+        proxy_fence_cluster();
+        ptx::tc_fence_before();
+        ptx::mbar_arrive_cluster(x_ready_leader);
+      }
+    }
+    // partial sums over this CTA's dims: <x, g> and |p|^2 per chain
+#pragma unroll
+    for (int cb = 0; cb < kHalf / 16; ++cb) {
+      float accv[16];
+      ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + h * kHalf + cb * 16, accv);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int i = cb * 16 + k;
+        const bool valid = dvalid && pair_base + h * kHalf + i < C;
+        float xg = valid ? -x[i] * accv[k] : 0.f;
+        float pp = valid ? p[i] * p[i] : 0.f;
+        xg = warp_sum(xg);
+        pp = warp_sum(pp);
+        if (lane == 0) {
+          red[(0 * 4 + quarter) * 64 + h * kHalf + i] = xg;
+          red[(1 * 4 + quarter) * 64 + h * kHalf + i] = pp;
+        }
+      }
+    }
+    epi_barrier();
+    const int c = ew * 32 + lane;                 // 0..255; chains 0..63 handled below
+    if (c < kPairChains) {
+      float xg = 0.f, pp = 0.f;
+      for (int q = 0; q < 4; ++q) {
+        xg += red[(0 * 4 + q) * 64 + c];
+        pp += red[(1 * 4 + q) * 64 + c];
+      }
+      if (rank == 0) {
+        red_pair[c] = xg;
+        red_pair[64 + c] = pp;
+      } else {
+        ptx::st_cluster_f32(ptx::mapa(ptx::smem_u32(&peer_in[c]), 0), xg);
+        ptx::st_cluster_f32(ptx::mapa(ptx::smem_u32(&peer_in[64 + c]), 0), pp);
+      }
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::cluster_sync();      // the peer's partial sums have landed in the leader
+  if (rank == 0 && threadIdx.x < kPairChains) {
+    const int c = threadIdx.x;
+    const int chain = pair_base + c;
+    float prob = 0.f;
+    int acc = 0;
+    if (chain < C) {
+      const float xg = red_pair[c] + peer_in[c];
+      const float pp = red_pair[64 + c] + peer_in[64 + c];
+      const float lp0 = a.lp[chain];
+      const float lp1 = 0.5f * xg;
+      float la = (-lp0 + fa.kin0[chain]) - (-lp1 + 0.5f * pp);
+      if (!isfinite(la)) la = -INFINITY;
+      const uint32_t gchain = static_cast<uint32_t>(chain) + a.chain_offset;
+      acc = accept_log_uniform(a.seed, gchain, a.t) < la;
+      prob = accept_prob(la);
+      if (ok) {
+        if (acc) a.lp[chain] = lp1;
+        a.is_accepted[chain] = static_cast<uint8_t>(acc);
+        a.log_accept[chain] = la;
+        if (a.trace_acc) a.trace_acc[chain] = static_cast<uint8_t>(acc);
+      }
+    }
+    acc_flag[c] = acc;
+    ptx::st_cluster_s32(ptx::mapa(ptx::smem_u32(&acc_flag[c]), 1), acc);
+    prob_s[c] = prob;
+    if (blockIdx.x == 0 && c == 0 && a.trace_eps && ok) a.trace_eps[0] = eps;
+  }
+  ptx::cluster_sync();      // decisions visible in both CTAs
+  if (warp >= 2) {
+#pragma unroll
+    for (int cb = 0; cb < kHalf / 16; ++cb) {
+      float accv[16];
+      ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + h * kHalf + cb * 16, accv);
+      if (ok && dvalid) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int i = cb * 16 + k;
+          const int chain = pair_base + h * kHalf + i;
+          if (chain >= C) continue;
+          const int64_t e = static_cast<int64_t>(chain) * D + d;
+          if (acc_flag[h * kHalf + i]) {
+            a.x[e] = x[i];
+            a.g[e] = -accv[k];
+            if (a.sample_out) a.sample_out[e] = x[i];
+          } else if (a.sample_out) {
+            a.sample_out[e] = a.x[e];
+          }
+        }
+      }
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc_pair(tmem, kTmemCols);
+  }
+  ptx::cluster_sync();
+  double sum = 0.0;
+  if (threadIdx.x == 0 && rank == 0)
+    for (int c = 0; c < kPairChains; ++c) sum += static_cast<double>(prob_s[c]);
+  block_partial_then_da(a.da, a.partials, sum, C, a.t_full);
+}
+
+}  // namespace
+
+unsigned gauss_pair_grid(int64_t C) {
+  return static_cast<unsigned>(2 * ((C + kPairChains - 1) / kPairChains));
+}
+
+cudaError_t gauss_pair_setup() {
+  return cudaFuncSetAttribute(k_gauss_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kSmem));
+}
+
+cudaError_t launch_gauss_pair_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
+                                         KernelTimer* timer) {
+  PairArgs fa{a, tc.err, tc.p, tc.h0};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(gauss_pair_grid(a.C));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (timer) timer->begin(s);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_gauss_pair, tc.mPhi128, tc.mPlo128, fa);
+  if (timer) timer->end(s);
+  count_launch();
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace hmc

@@ -382,6 +382,7 @@ cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws
   if (e != cudaSuccess) return e;
   if (gauss_fused_supported(t)) {
     e = gauss_fused_setup();
+    if (e == cudaSuccess) e = gauss_pair_setup();
     if (e != cudaSuccess) return e;
   }
   k_split<<<blocks_for(DD), 256, 0, s>>>(static_cast<int64_t>(DD), t.P, tc->Phi, tc->Plo);
@@ -393,6 +394,7 @@ cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws
 
 cudaError_t launch_gauss_tc_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
                                        KernelTimer* timer) {
+  if (tc.fused && tc.pair) return launch_gauss_pair_transition(a, tc, s, timer);
   if (tc.fused) return launch_gauss_fused_transition(a, tc, s, timer);
   TcBeginAccept b{};
   b.s = a;

@@ -151,12 +151,17 @@ struct GaussTc {
   int* err = nullptr;        // device flag: a bounded wait gave up
   int ntn = 0;
   bool fused = false;        // one launch per transition (dim <= 256)
+  bool pair = false;         // ... on CTA pairs (cta_group::2)
 };
 
 bool gauss_tc_supported(const hmc_target& t);
 size_t gauss_tc_workspace_bytes(const hmc_target& t, int64_t C);
 cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s);
 bool gauss_fused_supported(const hmc_target& t);
+unsigned gauss_pair_grid(int64_t C);
+cudaError_t gauss_pair_setup();
+cudaError_t launch_gauss_pair_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
+                                         KernelTimer* timer);
 unsigned gauss_fused_grid(int64_t C);
 cudaError_t gauss_fused_setup();
 cudaError_t launch_gauss_fused_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,

@@ -17,7 +17,7 @@ STATUS_NAMES = ["HMC_OK", "HMC_E_INVALID", "HMC_E_OOM", "HMC_E_CUDA", "HMC_E_TIM
                 "HMC_E_UNSUPPORTED"]
 HMC_T_STD_NORMAL, HMC_T_CORR_GAUSS, HMC_T_LOGREG, HMC_T_FUNNEL = range(4)
 TARGET_IDS = {"std_normal": 0, "corr_gauss": 1, "logreg": 2, "funnel": 3}
-HMC_IMPL_FUSED, HMC_IMPL_PLAIN = 0, 1
+HMC_IMPL_FUSED, HMC_IMPL_PLAIN, HMC_IMPL_FUSED_SINGLE_CTA = 0, 1, 2
 
 
 class hmc_target(ctypes.Structure):

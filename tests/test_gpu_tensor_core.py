@@ -36,15 +36,19 @@ CASES = [(128, 64, 0.1, 3), (130, 100, 0.08, 5), (257, 196, 0.06, 4), (512, 256,
          (100, 320, 0.04, 3)]
 
 
+@pytest.mark.parametrize("impl", [0, 2], ids=["pair", "single"])
 @pytest.mark.parametrize("C,D,eps,L", CASES)
-def test_tensor_core_transition_matches_oracle(H, C, D, eps, L):
+def test_tensor_core_transition_matches_oracle(H, C, D, eps, L, impl):
     from paper_2002_01184_gb300.sampler import Sampler
+    if D > 256 and impl == 2:
+        pytest.skip("one variant past dim 256")
     p = workloads.corr_gauss(dim=D, num_chains=C, num_burnin=0, num_results=0, num_leapfrog=L)
     p.step_size = eps
-    s = Sampler(p, adapt=False)
+    s = Sampler(p, adapt=False, impl=impl)
     assert H.hmc_uses_tensor_cores(s.ctx)
     name, per_launch = H.hmc_dominant_kernel_info(s.ctx)
-    assert name == ("k_gauss_fused" if D <= 256 else "k_gauss_tc_step")
+    expect = "k_gauss_tc_step" if D > 256 else ("k_gauss_pair" if impl == 0 else "k_gauss_fused")
+    assert name == expect
     x = torch.as_tensor(p.x0).cuda().contiguous()
     s.bootstrap(x)
     tgt = otargets.make("corr_gauss", P=p.P)
