@@ -199,7 +199,9 @@ hmc_status check_device_flag(hmc_ctx* ctx) {
   int flag = 0;
   cudaError_t e = cudaMemcpy(&flag, ctx->tc.err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "read device error flag");
-  if (flag) return fail(ctx, HMC_E_TIMEOUT, "a tensor-core kernel's bounded wait gave up");
+  if (flag)
+    return fail(ctx, HMC_E_TIMEOUT,
+                "a tensor-core kernel's bounded wait gave up (site " + std::to_string(flag) + ")");
   return HMC_OK;
 }
 

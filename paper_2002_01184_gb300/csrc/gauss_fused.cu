@@ -423,11 +423,17 @@ cudaError_t gauss_fused_setup() {
                               static_cast<int>(Cfg<32>::kSmem));
 }
 
-cudaError_t launch_gauss_fused_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
-                                          KernelTimer* timer) {
+cudaError_t launch_gauss_momentum(const StepArgs& a, GaussTc& tc, cudaStream_t s) {
   const unsigned mb = static_cast<unsigned>((a.C + 7) / 8);
   k_gauss_momentum<<<mb, 256, 0, s>>>(a.seed, a.t, a.C, a.D, a.chain_offset, tc.p, tc.h0);
   count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_fused_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
+                                          KernelTimer* timer) {
+  cudaError_t em = launch_gauss_momentum(a, tc, s);
+  if (em != cudaSuccess) return em;
   FusedArgs fa{a, tc.err, tc.p, tc.h0};
   constexpr int CL = Cfg<32>::kCluster;
   cudaLaunchConfig_t cfg = {};

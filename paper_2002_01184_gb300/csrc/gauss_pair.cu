@@ -134,7 +134,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         for (int kc = 0; kc < nk; ++kc, ++it) {
           const int s = it % kStages, round = it / kStages;
           if (it >= kStages && !ptx::mbar_wait(&empty[s], (round - 1) & 1)) {
-            atomicExch(fa.err, 1);
+            atomicCAS(fa.err, 0, 1);
             ok = false;
             break;
           }
@@ -152,7 +152,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       int it = 0;
       for (int l = 1; l <= L && ok; ++l) {
         if (!ptx::mbar_wait_cluster(x_ready, (l - 1) & 1)) {
-          atomicExch(fa.err, 1);
+          atomicCAS(fa.err, 0, 2);
           ok = false;
           break;
         }
@@ -160,7 +160,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         for (int kc = 0; kc < nk; ++kc, ++it) {
           const int s = it % kStages, round = it / kStages;
           if (!ptx::mbar_wait(&full[s], round & 1)) {
-            atomicExch(fa.err, 1);
+            atomicCAS(fa.err, 0, 3);
             ok = false;
             break;
           }
@@ -230,7 +230,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     for (int l = 1; l <= L; ++l) {
       const bool last = l == L;
       if (!ptx::mbar_wait(acc_full, (l - 1) & 1)) {
-        atomicExch(fa.err, 1);
+        atomicCAS(fa.err, 0, 4);
         ok = false;
       }
       ptx::tc_fence_after();
@@ -377,6 +377,8 @@ cudaError_t gauss_pair_setup() {
 
 cudaError_t launch_gauss_pair_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
                                          KernelTimer* timer) {
+  cudaError_t em = launch_gauss_momentum(a, tc, s);     // p0 and |p0|^2 / 2 of transition t
+  if (em != cudaSuccess) return em;
   PairArgs fa{a, tc.err, tc.p, tc.h0};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(gauss_pair_grid(a.C));

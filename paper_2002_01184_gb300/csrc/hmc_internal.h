@@ -159,6 +159,7 @@ size_t gauss_tc_workspace_bytes(const hmc_target& t, int64_t C);
 cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s);
 bool gauss_fused_supported(const hmc_target& t);
 unsigned gauss_pair_grid(int64_t C);
+cudaError_t launch_gauss_momentum(const StepArgs& a, GaussTc& tc, cudaStream_t s);
 cudaError_t gauss_pair_setup();
 cudaError_t launch_gauss_pair_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
                                          KernelTimer* timer);

@@ -138,12 +138,13 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
   }
 }
 
-// 2-D tiled TMA load into this CTA's shared memory, completing on an mbarrier
-// given by its shared::cluster address (the pair leader's barrier).
+// 2-D tiled TMA load into this CTA's shared memory for a CTA pair: the
+// completion is signalled on the mbarrier given by its shared::cluster
+// address, which may be in the peer CTA (the pair leader's barrier).
 __device__ __forceinline__ void tma_load_2d_to_bar(void* dst, const void* map, uint32_t bar_cluster,
                                                    int c0, int c1) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(c0), "r"(c1)
       : "memory");
