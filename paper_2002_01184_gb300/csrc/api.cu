@@ -547,6 +547,7 @@ hmc_status hmc_destroy(hmc_ctx* ctx) {
   ctx->timer.destroy();
   release(ctx);
   delete ctx;
+  cudaGetLastError();   // teardown never leaves an error pending for the next call
   return HMC_OK;
 }
 

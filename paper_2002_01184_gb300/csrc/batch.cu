@@ -118,17 +118,26 @@ hmc_status bfail(hmc_batch* b, hmc_status st, const std::string& m) {
 }
 
 void batch_release(hmc_batch* b) {
+  // contexts first: each synchronises its own stream, which may be a side stream
+  for (hmc_ctx* c : b->ctx) hmc_destroy(c);
+  b->ctx.clear();
+  if (b->graph) cudaGraphExecDestroy(b->graph);
   for (cudaStream_t st : b->side_stream)
     if (st) cudaStreamDestroy(st);
+  b->side_stream.clear();
   for (cudaEvent_t ev : b->side_done)
     if (ev) cudaEventDestroy(ev);
+  b->side_done.clear();
   if (b->fork) cudaEventDestroy(b->fork);
-  if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->dev_posts) cudaFree(b->dev_posts);
   if (b->dev_items) cudaFree(b->dev_items);
-  for (hmc_ctx* c : b->ctx) hmc_destroy(c);
-  b->ctx.clear();
+  b->graph = nullptr;
+  b->fork = nullptr;
+  b->cap_stream = nullptr;
+  b->dev_posts = nullptr;
+  b->dev_items = nullptr;
+  cudaGetLastError();   // release never leaves an error pending for the next call
 }
 
 // Rough cost of one tile transition: chains x leapfrog x per-gradient work.
