@@ -37,6 +37,10 @@ FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1
 TF32_PER_BF16 = 1.1 / 2.25
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the committed
+# ncu capture of the same kernel on the same workload (profiles/); keyed by
+# (kernel, target, chains, dim, leapfrog steps).  Absent -> traffic is null.
+PROFILED_TRAFFIC = {("k_gauss_pair", "corr_gauss", 4096, 256, 16): 13278464}
 
 
 def parse():
@@ -401,6 +405,7 @@ def main():
     roof = None
     if prof["samples"]:
         kernel_s = prof["avg_ms"] / 1000.0
+        traffic = PROFILED_TRAFFIC.get((kname, p.kind, C, D, p.num_leapfrog))
         common = {"kernel": kname, "avg_launch_ms": prof["avg_ms"],
                   "timed_launches": prof["samples"], "grad_evals_per_launch": evals_per_launch}
         if flops is not None and hmc.hmc_uses_tensor_cores(s.ctx):
@@ -409,7 +414,7 @@ def main():
             achieved = flops * evals_per_launch / kernel_s / 1e12
             peak = pk["bf16_tflops"] * TF32_PER_BF16 / 3.0
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": traffic,
                     "peak_source": f"{src} bf16 {pk['bf16_tflops']:.0f} TFLOP/s x (1.1/2.25 nominal tf32:bf16) / 3",
                     **common}
         elif flops is not None:
