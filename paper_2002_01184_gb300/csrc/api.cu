@@ -40,6 +40,9 @@ struct hmc_ctx {
   hmc::KernelTimer timer;
   bool use_tc = false;          // tensor-core Gaussian path
   hmc::GaussTc tc;
+  bool use_lrtc = false;        // tensor-core logistic-regression path
+  hmc::LogregTc lrtc;
+  int* lr_err = nullptr;
   // sample_chain captured as one CUDA graph, replayed while the arguments match
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -155,7 +158,7 @@ bool fused_impl(const hmc_ctx* ctx) {
 }
 
 bool uses_fused_logreg(const hmc_ctx* ctx) {
-  return fused_impl(ctx) && hmc::logreg_fused_supported(ctx->target);
+  return fused_impl(ctx) && !ctx->use_lrtc && hmc::logreg_fused_supported(ctx->target);
 }
 
 bool uses_fused_elementwise(const hmc_ctx* ctx) {
@@ -185,6 +188,8 @@ StepArgs make_args(hmc_ctx* ctx, float* x, uint64_t t) {
 
 cudaError_t enqueue_transition(hmc_ctx* ctx, const StepArgs& a) {
   if (ctx->use_tc) return hmc::launch_gauss_tc_transition(a, ctx->tc, ctx->stream, &ctx->timer);
+  if (ctx->use_lrtc)
+    return hmc::launch_logreg_tc_transition(a, ctx->lrtc, ctx->lr_err, ctx->stream, &ctx->timer);
   if (uses_fused_logreg(ctx))
     return hmc::launch_logreg_fused_transition(ctx->target, a, ctx->stream, &ctx->timer);
   if (uses_fused_elementwise(ctx))
@@ -195,9 +200,10 @@ cudaError_t enqueue_transition(hmc_ctx* ctx, const StepArgs& a) {
 
 // After a stream synchronisation: report a bounded device wait that gave up.
 hmc_status check_device_flag(hmc_ctx* ctx) {
-  if (!ctx->use_tc) return HMC_OK;
+  if (!ctx->use_tc && !ctx->use_lrtc) return HMC_OK;
   int flag = 0;
-  cudaError_t e = cudaMemcpy(&flag, ctx->tc.err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpy(&flag, ctx->use_tc ? ctx->tc.err : ctx->lr_err, sizeof(int),
+                             cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "read device error flag");
   if (flag)
     return fail(ctx, HMC_E_TIMEOUT,
@@ -352,6 +358,17 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     if (e == cudaSuccess) e = hmc::gauss_tc_setup(&ctx->tc, *target, num_chains, w, ctx->stream);
     ctx->tc.fused = hmc::gauss_fused_supported(*target);
     ctx->tc.pair = ctx->tc.fused && config->impl == HMC_IMPL_FUSED;
+  }
+  // logistic regressions with long data passes: tensor-core products; short
+  // ones: the shared-memory SIMT transition
+  ctx->use_lrtc = config->impl == HMC_IMPL_FUSED && hmc::logreg_tc_supported(*target) &&
+                  target->n_data > 2048;
+  if (e == cudaSuccess && ctx->use_lrtc) {
+    char* w = nullptr;
+    e = ctx_alloc(ctx, &w, hmc::logreg_tc_workspace_bytes(*target, num_chains));
+    if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->lr_err, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->lr_err, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = hmc::logreg_tc_setup(&ctx->lrtc, *target, num_chains, w, ctx->stream);
   }
   if (e == cudaSuccess && uses_fused_logreg(ctx)) e = hmc::logreg_fused_setup(*target);
   if (e == cudaSuccess && !uses_fused_elementwise(ctx) && !ctx->use_tc) {
@@ -555,7 +572,9 @@ const char* hmc_last_error(const hmc_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_global_err.c_str();
 }
 
-int32_t hmc_uses_tensor_cores(const hmc_ctx* ctx) { return ctx && ctx->use_tc ? 1 : 0; }
+int32_t hmc_uses_tensor_cores(const hmc_ctx* ctx) {
+  return ctx && (ctx->use_tc || ctx->use_lrtc) ? 1 : 0;
+}
 
 hmc_status hmc_dominant_kernel_info(const hmc_ctx* ctx, char* name, int32_t name_len,
                                     int64_t* grad_evals_per_launch) {
@@ -571,6 +590,8 @@ hmc_status hmc_dominant_kernel_info(const hmc_ctx* ctx, char* name, int32_t name
     per = ctx->C * ctx->cfg.num_leapfrog;
   } else if (ctx->use_tc) {
     n = "k_gauss_tc_step";
+  } else if (ctx->use_lrtc) {
+    n = "k_lr_grad";
   } else if (uses_fused_logreg(ctx)) {
     n = "k_logreg_fused";
     per = ctx->C * ctx->cfg.num_leapfrog;

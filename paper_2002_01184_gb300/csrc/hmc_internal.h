@@ -181,3 +181,22 @@ StepArgs ctx_step_args(hmc_ctx* ctx, float* x, uint64_t t);
 hmc_status ctx_bootstrap_on(hmc_ctx* ctx, const float* x0, cudaStream_t s);
 }  // namespace hmc
 
+namespace hmc {
+
+// Buffers and TMA descriptors of the tensor-core logistic-regression path.
+struct LogregTc {
+  CUtensorMap mThi, mTlo, mXhi, mXlo, mXThi, mXTlo;
+  float *Xhi = nullptr, *Xlo = nullptr, *XThi = nullptr, *XTlo = nullptr, *ypad = nullptr;
+  float *thi = nullptr, *tlo = nullptr, *p = nullptr, *gL = nullptr, *lpL = nullptr, *h0 = nullptr;
+  float *Gpart = nullptr, *lp_part = nullptr;
+  int npad = 0, ntiles = 0, nsplit = 0, tps = 0, groups = 0, dpad = 0, n_data = 0;
+};
+
+bool logreg_tc_supported(const hmc_target& t);
+size_t logreg_tc_workspace_bytes(const hmc_target& t, int64_t C);
+cudaError_t logreg_tc_setup(LogregTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s);
+cudaError_t launch_logreg_tc_transition(const StepArgs& a, LogregTc& tc, int* err, cudaStream_t s,
+                                        KernelTimer* timer);
+
+}  // namespace hmc
+

@@ -1,0 +1,567 @@
+// Bayesian logistic regression on the tcgen05 tensor cores: each leapfrog
+// gradient is two chain-batched products back to back (Section 2.1's batched
+// target evaluation of a "list of vectors"), 3xTF32 with float32 accumulation:
+//   Z = Theta X^T          (M = 128 chains, N = 128 data rows, K = D)
+//   R = y - sigmoid(Z)     (epilogue, straight back into tensor memory)
+//   G += R X               (M = 128 chains, N = D, K = 128 data rows; A = R
+//                           read from tensor memory, B = the transposed data)
+// One CTA per (128-chain group, range of data rows); the data tiles stream by
+// TMA through a ring of stages and every tile serves all 128 chains; Z and R
+// never reach HBM.  Per-range partial gradients and log-likelihoods are
+// summed in a fixed order by k_lr_update, which also applies the leapfrog
+// update.  A transition is: begin (momentum, half kick, drift), L x (grad,
+// update), accept.  For D <= 128 (tensor memory holds Z, R head / remainder
+// and G at once).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "hmc_device.cuh"
+#include "hmc_internal.h"
+#include "sm100_ptx.cuh"
+
+namespace hmc {
+
+namespace {
+
+constexpr int kM = 128;                     // chains per CTA
+constexpr int kRowsPerTile = 128;           // data rows per tile
+constexpr int kMaxD = 128;
+constexpr int kThreads = 320;               // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr uint32_t kTile = 128 * 128;       // 128 x 32 floats
+constexpr uint32_t kStage = 2 * kTile;      // head + remainder
+constexpr int kStages = 3;
+constexpr uint32_t kThetaBytes = 2 * 4 * kTile;   // 4 K-chunks, head + remainder
+constexpr uint32_t kColZ = 0, kColRhi = 128, kColRlo = 256, kColG = 384;
+constexpr uint32_t kTmemCols = 512;
+constexpr size_t kSmem = kThetaBytes + kStages * kStage + 1024 + 256 + 2 * 128 * 4;
+
+struct LrTcArgs {
+  int C, D, N, ntiles, tiles_per_split, nsplit, dpad;
+  const float* y;        // [Npad]
+  float* Gpart;          // [nsplit x C x D]
+  float* lp_part;        // [nsplit x C]
+  int* err;
+};
+
+__device__ __forceinline__ float sigmoid_f(float z) {
+  const float e = expf(-fabsf(z));
+  return z >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
+}
+
+__device__ __forceinline__ float softplus_f(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUtensorMap mTlo,
+          const __grid_constant__ CUtensorMap mXhi, const __grid_constant__ CUtensorMap mXlo,
+          const __grid_constant__ CUtensorMap mXThi, const __grid_constant__ CUtensorMap mXTlo,
+          LrTcArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* Th = smem;                                   // [4 chunks][hi, lo] 16 KB each
+  uint8_t* St = smem + kThetaBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(St + kStages * kStage);
+  uint64_t* empty = full + kStages;
+  uint64_t* th_full = empty + kStages;
+  uint64_t* z_full = th_full + 1;
+  uint64_t* r_ready = z_full + 1;
+  uint64_t* g_full = r_ready + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(g_full + 1);
+  float* lpred = reinterpret_cast<float*>(tmem_slot + 4);   // [2][128]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kM;
+  const int split = blockIdx.y;
+  const int t_begin = split * a.tiles_per_split;
+  const int t_end = min(a.ntiles, t_begin + a.tiles_per_split);
+  const int ntile = max(0, t_end - t_begin);
+  const int nk = (a.D + 31) >> 5;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    ptx::mbar_init(th_full, 1);
+    ptx::mbar_init(z_full, 1);
+    ptx::mbar_init(r_ready, 256);
+    ptx::mbar_init(g_full, 1);
+    ptx::fence_mbar_init();
+  }
+  if (warp == 0) {
+    ptx::tmem_alloc(tmem_slot, kTmemCols);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0 && ntile > 0) {
+      // ---- producer: the chains' positions once, then per tile the data
+      // chunks (X for the first product, X^T for the second)
+      ptx::mbar_arrive_expect_tx(th_full, 2u * nk * kTile);
+      for (int kc = 0; kc < nk; ++kc) {
+        ptx::tma_load_2d(Th + (2 * kc) * kTile, &mThi, th_full, kc * 32, m0);
+        ptx::tma_load_2d(Th + (2 * kc + 1) * kTile, &mTlo, th_full, kc * 32, m0);
+      }
+      int it = 0;
+      for (int t = t_begin; t < t_end && ok; ++t) {
+        const int row0 = t * kRowsPerTile;
+        for (int part = 0; part < nk + 4 && ok; ++part, ++it) {
+          const int s = it % kStages, round = it / kStages;
+          if (it >= kStages && !ptx::mbar_wait(&empty[s], (round - 1) & 1)) {
+            atomicCAS(a.err, 0, 11);
+            ok = false;
+            break;
+          }
+          uint8_t* st = St + s * kStage;
+          ptx::mbar_arrive_expect_tx(&full[s], kStage);
+          if (part < nk) {
+            ptx::tma_load_2d(st, &mXhi, &full[s], part * 32, row0);
+            ptx::tma_load_2d(st + kTile, &mXlo, &full[s], part * 32, row0);
+          } else {
+            const int kr = part - nk;
+            ptx::tma_load_2d(st, &mXThi, &full[s], row0 + kr * 32, 0);
+            ptx::tma_load_2d(st + kTile, &mXTlo, &full[s], row0 + kr * 32, 0);
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && ntile > 0) {
+      // ---- MMA issuer
+      const uint32_t idesc1 = ptx::idesc_tf32(kM, kRowsPerTile);
+      const uint32_t idesc2 = ptx::idesc_tf32(kM, a.dpad);
+      if (!ptx::mbar_wait(th_full, 0)) {
+        atomicCAS(a.err, 0, 12);
+        ok = false;
+      }
+      ptx::tc_fence_after();
+      int it = 0;
+      for (int ti = 0; ti < ntile && ok; ++ti) {
+        // Z = Theta X^T
+        for (int kc = 0; kc < nk && ok; ++kc, ++it) {
+          const int s = it % kStages;
+          if (!ptx::mbar_wait(&full[s], (it / kStages) & 1)) {
+            atomicCAS(a.err, 0, 13);
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t thi = ptx::smem_u32(Th + (2 * kc) * kTile);
+          const uint32_t tlo = ptx::smem_u32(Th + (2 * kc + 1) * kTile);
+          const uint32_t xhi = ptx::smem_u32(St + s * kStage);
+          const uint32_t xlo = xhi + kTile;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint64_t dth = ptx::sw128_kmajor_desc(thi + 32 * j);
+            const uint64_t dtl = ptx::sw128_kmajor_desc(tlo + 32 * j);
+            const uint64_t dxh = ptx::sw128_kmajor_desc(xhi + 32 * j);
+            const uint64_t dxl = ptx::sw128_kmajor_desc(xlo + 32 * j);
+            ptx::mma_tf32(tmem + kColZ, dtl, dxh, idesc1, (kc | j) != 0 ? 1u : 0u);
+            ptx::mma_tf32(tmem + kColZ, dth, dxl, idesc1, 1u);
+            ptx::mma_tf32(tmem + kColZ, dth, dxh, idesc1, 1u);
+          }
+          ptx::mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        ptx::mma_commit(z_full);
+        if (!ptx::mbar_wait(r_ready, ti & 1)) {
+          atomicCAS(a.err, 0, 14);
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        // G += R X   (A = R from tensor memory, K = the tile's 128 rows)
+        for (int kr = 0; kr < 4 && ok; ++kr, ++it) {
+          const int s = it % kStages;
+          if (!ptx::mbar_wait(&full[s], (it / kStages) & 1)) {
+            atomicCAS(a.err, 0, 15);
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t bhi = ptx::smem_u32(St + s * kStage);
+          const uint32_t blo = bhi + kTile;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint64_t dbh = ptx::sw128_kmajor_desc(bhi + 32 * j);
+            const uint64_t dbl = ptx::sw128_kmajor_desc(blo + 32 * j);
+            const uint32_t k = static_cast<uint32_t>(kr * 32 + 8 * j);
+            ptx::mma_tf32_tmem_a(tmem + kColG, tmem + kColRlo + k, dbh, idesc2,
+                                 (ti | kr | j) != 0 ? 1u : 0u);
+            ptx::mma_tf32_tmem_a(tmem + kColG, tmem + kColRhi + k, dbl, idesc2, 1u);
+            ptx::mma_tf32_tmem_a(tmem + kColG, tmem + kColRhi + k, dbh, idesc2, 1u);
+          }
+          ptx::mma_commit(&empty[s]);
+        }
+      }
+      ptx::mma_commit(g_full);
+    }
+  } else {
+    // ---- epilogue: thread = chain row (TMEM lane), half of the columns
+    const int ew = warp - 2;
+    const int quarter = warp & 3;
+    const int half = ew >> 2;
+    const int r = quarter * 32 + lane;
+    const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
+    float lp_acc = 0.f;
+    for (int ti = 0; ti < ntile; ++ti) {
+      const int row0 = (t_begin + ti) * kRowsPerTile;
+      if (!ptx::mbar_wait(z_full, ti & 1)) {
+        atomicCAS(a.err, 0, 16);
+        ok = false;
+      }
+      ptx::tc_fence_after();
+#pragma unroll
+      for (int cb = 0; cb < 4; ++cb) {
+        const uint32_t col = static_cast<uint32_t>(64 * half + 16 * cb);
+        float zv[16], rh[16], rl[16];
+        ptx::tmem_ld16(tmem + lane_base + kColZ + col, zv);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int n = row0 + static_cast<int>(col) + k;
+          float res = 0.f;
+          if (n < a.N) {
+            const float yv = a.y[n];
+            res = yv - sigmoid_f(zv[k]);
+            lp_acc += yv * zv[k] - softplus_f(zv[k]);
+          }
+          split_tf32(res, rh[k], rl[k]);
+        }
+        ptx::tmem_st16(tmem + lane_base + kColRhi + col, rh);
+        ptx::tmem_st16(tmem + lane_base + kColRlo + col, rl);
+      }
+      ptx::tmem_wait_st();
+      ptx::tc_fence_before();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(r_ready)) : "memory");
+    }
+    // partial gradient and log-likelihood of this row range
+    const int chain = m0 + r;
+    if (ntile > 0) {
+      if (!ptx::mbar_wait(g_full, 0)) {
+        atomicCAS(a.err, 0, 17);
+        ok = false;
+      }
+      ptx::tc_fence_after();
+    }
+    float* gout = a.Gpart + (static_cast<int64_t>(split) * a.C + chain) * a.D;
+#pragma unroll 1
+    for (int cb = 0; cb < 4; ++cb) {
+      const int d0 = 64 * half + 16 * cb;
+      if (d0 >= a.dpad) break;                    // warp-uniform
+      float gv[16];
+      if (ntile > 0) {
+        ptx::tmem_ld16(tmem + lane_base + kColG + static_cast<uint32_t>(d0), gv);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) gv[k] = 0.f;
+      }
+      if (ok && chain < a.C)
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (d0 + k < a.D) gout[d0 + k] = gv[k];
+    }
+    lpred[half * 128 + r] = lp_acc;
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp >= 2 && warp < 6) {
+    const int r = (warp & 3) * 32 + lane;
+    const int chain = m0 + r;
+    if (ok && chain < a.C)
+      a.lp_part[static_cast<int64_t>(split) * a.C + chain] = lpred[r] + lpred[128 + r];
+  }
+  if (warp == 0) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+constexpr int kWarpsPerBlock = 8;
+
+struct LrStepArgs {
+  StepArgs s;
+  float* thi;       // [C x D] positions, tf32 head / remainder (A operand)
+  float* tlo;
+  float* p;         // [C x D] momenta
+  float* gL;        // [C x D] gradient at the end of the trajectory
+  float* lpL;       // [C]
+  float* h0;        // [C]
+  const float* Gpart;
+  const float* lp_part;
+  int nsplit;
+  int last;         // update kernel: final leapfrog step
+};
+
+// p0 ~ N(0, I); H0; half kick with the cached gradient; first drift
+__global__ void k_lr_begin(LrStepArgs b) {
+  const StepArgs& a = b.s;
+  const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= a.C) return;
+  const int D = a.D;
+  const int64_t row = static_cast<int64_t>(c) * D;
+  const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
+  const float eps = a.da->eps;
+  float kin = 0.f;
+  for (int d = lane; d < D; d += 32) {
+    const float z = momentum1(a.seed, static_cast<uint32_t>(d), chain, a.t);
+    kin = fmaf(z, z, kin);
+    const float p = fmaf(0.5f * eps, a.g[row + d], z);
+    b.p[row + d] = p;
+    float hi, lo;
+    split_tf32(fmaf(eps, p, a.x[row + d]), hi, lo);
+    b.thi[row + d] = hi;
+    b.tlo[row + d] = lo;
+  }
+  kin = warp_sum(kin);
+  if (lane == 0) b.h0[c] = -a.lp[c] + 0.5f * kin;
+}
+
+// gradient and log p from the range partials (fixed order) and the prior;
+// leapfrog update (merged kicks + drift), or the final half kick
+__global__ void k_lr_update(LrStepArgs b) {
+  const StepArgs& a = b.s;
+  const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= a.C) return;
+  const int D = a.D;
+  const int64_t row = static_cast<int64_t>(c) * D;
+  const float eps = a.da->eps;
+  float sq = 0.f;
+  for (int d = lane; d < D; d += 32) {
+    const float th = b.thi[row + d] + b.tlo[row + d];
+    float g = 0.f;
+    for (int s = 0; s < b.nsplit; ++s) g += b.Gpart[(static_cast<int64_t>(s) * a.C + c) * D + d];
+    g -= th;
+    sq = fmaf(th, th, sq);
+    if (!b.last) {
+      const float p = fmaf(eps, g, b.p[row + d]);
+      b.p[row + d] = p;
+      float hi, lo;
+      split_tf32(fmaf(eps, p, th), hi, lo);
+      b.thi[row + d] = hi;
+      b.tlo[row + d] = lo;
+    } else {
+      b.p[row + d] = fmaf(0.5f * eps, g, b.p[row + d]);
+      b.gL[row + d] = g;
+    }
+  }
+  if (b.last) {
+    sq = warp_sum(sq);
+    if (lane == 0) {
+      float lp = 0.f;
+      for (int s = 0; s < b.nsplit; ++s) lp += b.lp_part[static_cast<int64_t>(s) * a.C + c];
+      b.lpL[c] = lp - 0.5f * sq;
+    }
+  }
+}
+
+// H_L, Metropolis-Hastings select, traces, dual averaging
+__global__ void k_lr_accept(LrStepArgs b) {
+  const StepArgs& a = b.s;
+  const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const bool has_chain = c < a.C;
+  float prob = 0.f;
+  if (has_chain) {
+    const int D = a.D;
+    const int64_t row = static_cast<int64_t>(c) * D;
+    const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
+    float kin = 0.f;
+    for (int d = lane; d < D; d += 32) kin = fmaf(b.p[row + d], b.p[row + d], kin);
+    kin = 0.5f * warp_sum(kin);
+    const float lp1 = b.lpL[c];
+    float la = b.h0[c] - (-lp1 + kin);
+    if (!isfinite(la)) la = -INFINITY;
+    int acc = 0;
+    if (lane == 0) acc = accept_log_uniform(a.seed, chain, a.t) < la;
+    acc = __shfl_sync(0xffffffffu, acc, 0);
+    for (int d = lane; d < D; d += 32) {
+      const int64_t e = row + d;
+      if (acc) {
+        a.x[e] = b.thi[e] + b.tlo[e];
+        a.g[e] = b.gL[e];
+      }
+      if (a.sample_out) a.sample_out[e] = a.x[e];
+    }
+    if (lane == 0) {
+      if (acc) a.lp[c] = lp1;
+      a.is_accepted[c] = static_cast<uint8_t>(acc);
+      a.log_accept[c] = la;
+      if (a.trace_acc) a.trace_acc[c] = static_cast<uint8_t>(acc);
+      if (c == 0 && a.trace_eps) a.trace_eps[0] = a.da->eps;
+    }
+    prob = accept_prob(la);
+  }
+  accept_block_finish<kWarpsPerBlock>(a.da, a.partials, prob, has_chain, a.C, a.t_full);
+}
+
+// X -> head / remainder, and the transposed copy [D x Npad]; rows >= N zero
+__global__ void k_lr_prepare(int N, int Npad, int D, const float* __restrict__ X,
+                             const float* __restrict__ y, float* __restrict__ Xhi,
+                             float* __restrict__ Xlo, float* __restrict__ XThi,
+                             float* __restrict__ XTlo, float* __restrict__ ypad) {
+  const int64_t total = static_cast<int64_t>(Npad) * D;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int n = static_cast<int>(i / D), d = static_cast<int>(i % D);
+    const float v = n < N ? X[static_cast<int64_t>(n) * D + d] : 0.f;
+    float hi, lo;
+    split_tf32(v, hi, lo);
+    Xhi[i] = hi;
+    Xlo[i] = lo;
+    XThi[static_cast<int64_t>(d) * Npad + n] = hi;
+    XTlo[static_cast<int64_t>(d) * Npad + n] = lo;
+    if (d == 0) ypad[n] = n < N ? y[n] : 0.f;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool map2d(CUtensorMap* m, const float* base, int64_t rows, int64_t cols) {
+  auto fn = encode();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(cols) * sizeof(float)};
+  cuuint32_t box[2] = {32u, 128u};
+  cuuint32_t es[2] = {1u, 1u};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+inline size_t a1k(size_t b) { return (b + 1023) & ~static_cast<size_t>(1023); }
+
+struct Plan {
+  int npad, ntiles, groups, nsplit, tps, dpad;
+};
+
+Plan plan(const hmc_target& t, int64_t C) {
+  Plan p{};
+  p.ntiles = static_cast<int>((t.n_data + kRowsPerTile - 1) / kRowsPerTile);
+  p.npad = p.ntiles * kRowsPerTile;
+  p.groups = static_cast<int>((C + kM - 1) / kM);
+  int ns = std::max(1, 152 / p.groups);
+  ns = std::min(ns, p.ntiles);
+  p.tps = (p.ntiles + ns - 1) / ns;
+  p.nsplit = (p.ntiles + p.tps - 1) / p.tps;
+  p.dpad = (t.dim + 15) / 16 * 16;
+  return p;
+}
+
+}  // namespace
+
+bool logreg_tc_supported(const hmc_target& t) {
+  return t.id == HMC_T_LOGREG && t.dim <= kMaxD && t.dim % 4 == 0 && encode() != nullptr;
+}
+
+size_t logreg_tc_workspace_bytes(const hmc_target& t, int64_t C) {
+  const Plan p = plan(t, C);
+  const size_t CD = static_cast<size_t>(C) * t.dim, ND = static_cast<size_t>(p.npad) * t.dim;
+  return 4 * a1k(ND * 4) + a1k(p.npad * 4) + 4 * a1k(CD * 4) + a1k(C * 4) * 2 +
+         a1k(static_cast<size_t>(p.nsplit) * CD * 4) + a1k(static_cast<size_t>(p.nsplit) * C * 4);
+}
+
+cudaError_t logreg_tc_setup(LogregTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s) {
+  const Plan p = plan(t, C);
+  tc->npad = p.npad;
+  tc->ntiles = p.ntiles;
+  tc->nsplit = p.nsplit;
+  tc->tps = p.tps;
+  tc->groups = p.groups;
+  tc->dpad = p.dpad;
+  tc->n_data = static_cast<int>(t.n_data);
+  const size_t CD = static_cast<size_t>(C) * t.dim, ND = static_cast<size_t>(p.npad) * t.dim;
+  char* w = static_cast<char*>(ws);
+  auto take = [&](size_t b) { char* q = w; w += a1k(b); return reinterpret_cast<float*>(q); };
+  tc->Xhi = take(ND * 4);
+  tc->Xlo = take(ND * 4);
+  tc->XThi = take(ND * 4);
+  tc->XTlo = take(ND * 4);
+  tc->ypad = take(p.npad * 4);
+  tc->thi = take(CD * 4);
+  tc->tlo = take(CD * 4);
+  tc->p = take(CD * 4);
+  tc->gL = take(CD * 4);
+  tc->lpL = take(C * 4);
+  tc->h0 = take(C * 4);
+  tc->Gpart = take(static_cast<size_t>(p.nsplit) * CD * 4);
+  tc->lp_part = take(static_cast<size_t>(p.nsplit) * C * 4);
+  const bool ok = map2d(&tc->mThi, tc->thi, C, t.dim) && map2d(&tc->mTlo, tc->tlo, C, t.dim) &&
+                  map2d(&tc->mXhi, tc->Xhi, p.npad, t.dim) && map2d(&tc->mXlo, tc->Xlo, p.npad, t.dim) &&
+                  map2d(&tc->mXThi, tc->XThi, t.dim, p.npad) &&
+                  map2d(&tc->mXTlo, tc->XTlo, t.dim, p.npad);
+  if (!ok) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_lr_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSmem));
+  if (e != cudaSuccess) return e;
+  const int64_t total = static_cast<int64_t>(p.npad) * t.dim;
+  k_lr_prepare<<<static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 152 * 16)), 256, 0, s>>>(
+      static_cast<int>(t.n_data), p.npad, t.dim, t.X, t.y, tc->Xhi, tc->Xlo, tc->XThi, tc->XTlo,
+      tc->ypad);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_logreg_tc_transition(const StepArgs& a, LogregTc& tc, int* err, cudaStream_t s,
+                                        KernelTimer* timer) {
+  LrStepArgs b{};
+  b.s = a;
+  b.thi = tc.thi;
+  b.tlo = tc.tlo;
+  b.p = tc.p;
+  b.gL = tc.gL;
+  b.lpL = tc.lpL;
+  b.h0 = tc.h0;
+  b.Gpart = tc.Gpart;
+  b.lp_part = tc.lp_part;
+  b.nsplit = tc.nsplit;
+  const unsigned nb = static_cast<unsigned>((a.C + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  k_lr_begin<<<nb, 32 * kWarpsPerBlock, 0, s>>>(b);
+  count_launch();
+  LrTcArgs g{};
+  g.C = a.C;
+  g.D = a.D;
+  g.ntiles = tc.ntiles;
+  g.tiles_per_split = tc.tps;
+  g.nsplit = tc.nsplit;
+  g.dpad = tc.dpad;
+  g.y = tc.ypad;
+  g.Gpart = tc.Gpart;
+  g.lp_part = tc.lp_part;
+  g.err = err;
+  g.N = tc.n_data;
+  const dim3 grid(tc.groups, tc.nsplit);
+  for (int l = 1; l <= a.L; ++l) {
+    if (timer) timer->begin(s);
+    k_lr_grad<<<grid, kThreads, kSmem, s>>>(tc.mThi, tc.mTlo, tc.mXhi, tc.mXlo, tc.mXThi, tc.mXTlo, g);
+    if (timer) timer->end(s);
+    b.last = l == a.L;
+    k_lr_update<<<nb, 32 * kWarpsPerBlock, 0, s>>>(b);
+    count_launch(2);
+  }
+  k_lr_accept<<<nb, 32 * kWarpsPerBlock, 0, s>>>(b);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace hmc

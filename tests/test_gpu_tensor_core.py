@@ -92,3 +92,40 @@ def test_tensor_core_and_plain_paths_agree(H):
     assert agree > 0.99
     same_rows = np.all(a1 == a2, axis=0)
     np.testing.assert_allclose(s1[:, same_rows], s2[:, same_rows], rtol=1e-3, atol=1e-3)
+
+
+# logistic regression on tensor cores: (chains, dim, data rows, step, L) --
+# ragged chain groups, ragged last data tile, dims below / at the 128 limit
+LOGREG_CASES = [(130, 64, 2500, 0.01, 3), (200, 128, 4100, 0.005, 2), (64, 20, 2049, 0.02, 4)]
+
+
+@pytest.mark.parametrize("C,D,N,eps,L", LOGREG_CASES)
+def test_tensor_core_logreg_transition_matches_oracle(H, C, D, N, eps, L):
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = workloads.logreg(n_data=N, dim=D, num_chains=C, num_burnin=0, num_results=0, num_leapfrog=L)
+    p.step_size = eps
+    p.x0 = (0.05 * np.random.default_rng(D).standard_normal((C, D))).astype(np.float32)
+    s = Sampler(p, adapt=False)
+    assert H.hmc_uses_tensor_cores(s.ctx)
+    assert H.hmc_dominant_kernel_info(s.ctx)[0] == "k_lr_grad"
+    x = torch.as_tensor(p.x0).cuda().contiguous()
+    s.bootstrap(x)
+    tgt = otargets.make("logreg", X=p.X, y=p.y)
+    n_same = 0
+    for t in range(3):
+        xin = host(x).astype(np.float64)
+        lp, g = tgt(xin)
+        r = s.results(s.step(x, t))
+        H.hmc_synchronize(s.ctx)
+        ref = ohmc.one_step(xin, lp, g, np.float32(eps), L, p.seed, t, tgt)
+        a, _ = compare_transition(xin, host(x), host(r["is_accepted"]), host(r["log_accept_ratio"]),
+                                  ref, label=f"lr-tc C={C} D={D} N={N} t={t}")
+        n_same += a
+        lp_new, g_new = tgt(host(x).astype(np.float64))
+        np.testing.assert_allclose(host(r["target_log_prob"]), lp_new, rtol=1e-4,
+                                   atol=1e-4 * max(1.0, np.abs(lp_new).max()))
+        gg = host(r["grad"])
+        row = np.max(np.abs(g_new), axis=1, keepdims=True)
+        assert np.max(np.abs(gg - g_new) / np.maximum(row, 1e-6)) < 1e-4
+    assert n_same >= 3 * C - 2
+    s.close()
