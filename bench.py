@@ -259,9 +259,11 @@ def run_uneven_batch(args):
     clocks.start()
     launches0 = hmc.hmc_kernel_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_host = time.perf_counter()
     e0.record(stream)
     for _ in range(args.steps):
         step()
+    t_enq = time.perf_counter() - t_host
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
@@ -279,6 +281,7 @@ def run_uneven_batch(args):
                        else "one grouped launch per transition, CUDA graph",
                        "posteriors": len(probs)},
             "min_ess_per_s": ess / (ms / 1000.0), "min_ess": ess,
+            "host_enqueue_ms_per_step": 1000.0 * t_enq / args.steps,
             "gpu_launches": int(launches), "clocks": clk, "roofline": None, "cpu_baseline": None,
             "e2e": None}
     print(json.dumps(line), flush=True)

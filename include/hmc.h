@@ -215,8 +215,9 @@ const char* hmc_last_error(const hmc_ctx* ctx);
  * posteriors).  Funnels, standard normals and logistic regressions with at
  * most 2048 data rows share one grouped kernel launch per transition (one
  * tile per 8 chains, largest tiles first), the whole loop as one CUDA graph;
- * logistic regressions with longer data passes run their tiled-product
- * transitions on streams of their own, concurrently.  Each posterior keeps
+ * logistic regressions with longer data passes run their own transitions
+ * (tensor-core products for dim <= 128) on streams of their own,
+ * concurrently.  Each posterior keeps
  * its own state, kernel results and dual-averaging step size, so its result
  * equals sampling it alone.  Supported families: LOGREG (dim <= 512), FUNNEL
  * and STD_NORMAL (dim <= 1024); others give HMC_E_UNSUPPORTED.  All work is

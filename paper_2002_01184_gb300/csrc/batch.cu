@@ -7,9 +7,9 @@
 //     the whole loop (bootstraps + one grouped launch per transition) is one
 //     CUDA graph.  Funnels, standard normals and logistic regressions with at
 //     most kGroupedMaxRows data rows.
-//   side: logistic regressions with longer data passes, whose gradients are
-//     tiled products (the one-launch-per-operation path) on a stream of
-//     their own, running concurrently with the grouped graph.
+//   side: logistic regressions with longer data passes, sampled by their own
+//     context (tensor-core products for dim <= 128, tiled SIMT products
+//     otherwise) on a stream of their own, concurrently with the grouped graph.
 // Each posterior keeps its own chain state, kernel results and
 // dual-averaging scalar; a grouped posterior's adaptation reduction runs over
 // its own tiles only, so every member's result equals sampling it alone.
@@ -173,7 +173,7 @@ hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
     }
     hmc_config c = configs[i];
     const bool grouped = hmc::grouped_member(t);
-    c.impl = grouped ? HMC_IMPL_FUSED : HMC_IMPL_PLAIN;
+    c.impl = HMC_IMPL_FUSED;       // side members: tensor-core products where they apply
     c.use_graph = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t done = nullptr;

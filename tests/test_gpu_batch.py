@@ -61,7 +61,7 @@ def test_batch_equals_each_posterior_alone(H):
                                  [p.num_results for p in probs], samples, eps, acc)
         torch.cuda.synchronize()
         for i, p in enumerate(probs):
-            s = Sampler(p, impl=1 if (p.kind == "logreg" and p.n_data > 2048) else 0)
+            s = Sampler(p)
             x = dev(p.x0)
             smp, e, a = s.sample_chain(x, p.num_burnin, p.num_results)
             torch.cuda.synchronize()
