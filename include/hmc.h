@@ -212,10 +212,10 @@ const char* hmc_last_error(const hmc_ctx* ctx);
 /* ---- Batches of posteriors ------------------------------------------------
  * Many posteriors of uneven dimension, data size and chain count sampled
  * together (the independent-chain batching of Section 2 applied across
- * posteriors).  Funnels, standard normals and logistic regressions with at
- * most 2048 data rows share one grouped kernel launch per transition (one
- * tile per 8 chains, largest tiles first), the whole loop as one CUDA graph;
- * logistic regressions with longer data passes run their own transitions
+ * posteriors).  Funnels, standard normals and small logistic regressions
+ * (chains x rows x dim <= 2^22) share one grouped kernel launch per
+ * transition (one tile per 8 chains, largest tiles first), the whole loop as
+ * one CUDA graph; larger logistic regressions run their own transitions
  * (tensor-core products for dim <= 128) on streams of their own,
  * concurrently.  Each posterior keeps
  * its own state, kernel results and dual-averaging step size, so its result

@@ -5,8 +5,8 @@
 //     single grouped launch (k_batch_transition), the tiles of all of them
 //     side by side, ordered by estimated cost so the largest start first;
 //     the whole loop (bootstraps + one grouped launch per transition) is one
-//     CUDA graph.  Funnels, standard normals and logistic regressions with at
-//     most kGroupedMaxRows data rows.
+//     CUDA graph.  Funnels, standard normals and small logistic regressions
+//     (kGroupedMaxWork).
 //   side: logistic regressions with longer data passes, sampled by their own
 //     context (tensor-core products for dim <= 128, tiled SIMT products
 //     otherwise) on a stream of their own, concurrently with the grouped graph.
@@ -73,10 +73,14 @@ __global__ void __launch_bounds__(256) k_batch_transition(const BatchPost* __res
   }
 }
 
-constexpr int64_t kGroupedMaxRows = 2048;
+// A logistic regression joins the grouped launch when one gradient of all
+// its chains is small (chains x rows x dim <= 2^22 multiply-adds); larger ones
+// run their own context (tensor-core products where they apply) on a side
+// stream, so that a grouped launch never waits on a long SIMT data pass.
+constexpr int64_t kGroupedMaxWork = int64_t(1) << 22;
 
-bool grouped_member(const hmc_target& t) {
-  return t.id != HMC_T_LOGREG || t.n_data <= kGroupedMaxRows;
+bool grouped_member(const hmc_target& t, int64_t C) {
+  return t.id != HMC_T_LOGREG || C * t.n_data * t.dim <= kGroupedMaxWork;
 }
 
 int blocks_per_lane(int D) {
@@ -172,7 +176,7 @@ hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
                        ": supported are LOGREG (dim <= 512), FUNNEL and STD_NORMAL (dim <= 1024)");
     }
     hmc_config c = configs[i];
-    const bool grouped = hmc::grouped_member(t);
+    const bool grouped = hmc::grouped_member(t, num_chains[i]);
     c.impl = HMC_IMPL_FUSED;       // side members: tensor-core products where they apply
     c.use_graph = 0;
     cudaStream_t side = nullptr;

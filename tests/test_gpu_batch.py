@@ -26,8 +26,11 @@ def small_batch():
     probs = workloads.uneven_batch(seed=5, n_logreg=5, n_funnel=3, num_burnin=15, num_results=10,
                                    dim_range=(8, 64), n_range=(50, 400), chain_range=(9, 70),
                                    funnel_dim_range=(10, 40))
-    # one member with a long data pass: it runs on a side stream
+    # members with long data passes run on side streams: one on the tensor
+    # cores (dim <= 128), one on the tiled SIMT products (dim > 128)
     probs.append(workloads.logreg(n_data=2500, dim=16, num_chains=33, seed=77, num_burnin=15,
+                                  num_results=10))
+    probs.append(workloads.logreg(n_data=600, dim=200, num_chains=40, seed=78, num_burnin=15,
                                   num_results=10))
     return probs
 
