@@ -209,6 +209,33 @@ hmc_status hmc_destroy(hmc_ctx* ctx);
  * is owned by the library and valid until the next call on the same context. */
 const char* hmc_last_error(const hmc_ctx* ctx);
 
+/* ---- Replica exchange ----------------------------------------------------
+ * Replica exchange Monte Carlo (Section 2.2): every chain carries K replicas
+ * whose target log-probabilities are scaled by inverse temperatures
+ * betas[k] (betas[0] = 1 is the distribution of interest); the replicas are
+ * one more batch axis -- replica k of chain c is row c * K + k of the
+ * [chains * K x dim] state -- so every replica advances by the ordinary HMC
+ * transition (its own random streams, those of row c * K + k), and after the
+ * transition with index t adjacent replicas (k, k + 1) with k = t % 2,
+ * t % 2 + 2, ... swap their states iff
+ *   log u < (betas[k] - betas[k+1]) (log p(x_{k+1}) - log p(x_k)),
+ * u from the counter generator at (k, c, t, tag 2).  Kept samples are taken
+ * after the exchange.  The context's log-prob and gradient results are the
+ * tempered ones.  Fixed step size only (adapt = 0; HMC_E_UNSUPPORTED
+ * otherwise); chain_offset must be 0.  Dense targets (CORR_GAUSS, LOGREG)
+ * use the one-launch-per-operation path; the others the fused kernels.
+ * betas: host array of num_replicas values in (0, 1].  All other calls
+ * (hmc_bootstrap, hmc_step, hmc_sample_chain, ...) take the
+ * [num_chains * num_replicas x dim] state. */
+hmc_status hmc_remc_create(const hmc_target* target, int64_t num_chains, int32_t num_replicas,
+                           const float* betas, const hmc_config* config, void* cuda_stream,
+                           hmc_ctx** out);
+
+/* Device pointer to the last exchange step's outcomes, [num_chains x
+ * (num_replicas - 1)] uint8 (1 = pair (k, k+1) swapped; 0 also for pairs not
+ * proposed at that step), owned by the context. */
+hmc_status hmc_remc_swaps(const hmc_ctx* ctx, const uint8_t** swapped);
+
 /* ---- Batches of posteriors ------------------------------------------------
  * Many posteriors of uneven dimension, data size and chain count sampled
  * together (the independent-chain batching of Section 2 applied across

@@ -43,6 +43,11 @@ struct hmc_ctx {
   bool use_lrtc = false;        // tensor-core logistic-regression path
   hmc::LogregTc lrtc;
   int* lr_err = nullptr;
+  // replica exchange (Section 2.2): K replicas per chain, rows c*K + k
+  int K = 1;
+  int64_t outer_chains = 0;
+  float* betas = nullptr;        // device [K]
+  uint8_t* swapped = nullptr;    // device [outer_chains x (K - 1)]
   // sample_chain captured as one CUDA graph, replayed while the arguments match
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -183,6 +188,8 @@ StepArgs make_args(hmc_ctx* ctx, float* x, uint64_t t) {
   a.partials = ctx->partials;
   a.is_accepted = ctx->is_accepted;
   a.log_accept = ctx->log_accept;
+  a.betas = ctx->betas;
+  a.K = ctx->K;
   return a;
 }
 
@@ -213,6 +220,8 @@ hmc_status check_device_flag(hmc_ctx* ctx) {
 
 hmc_status bootstrap(hmc_ctx* ctx, const float* x0) {
   cudaError_t e = hmc::launch_grad(ctx->target, ctx->C, x0, ctx->lp, ctx->g, ctx->grad_ws, ctx->stream);
+  if (e == cudaSuccess && ctx->K > 1)
+    e = hmc::launch_temper(ctx->C, ctx->target.dim, ctx->lp, ctx->g, ctx->betas, ctx->K, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "bootstrap gradient");
   e = hmc::launch_da_init(ctx->da, ctx->cfg.step_size, ctx->cfg.adapt, ctx->cfg.target_accept,
                           ctx->cfg.adapt ? ctx->cfg.num_adapt_steps : 0, ctx->stream);
@@ -230,12 +239,21 @@ hmc_status enqueue_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sa
     StepArgs a = make_args(ctx, x, static_cast<uint64_t>(t));
     const int64_t k = t - B;
     if (k >= 0) {
-      a.sample_out = samples ? samples + k * CD : nullptr;
+      a.sample_out = samples && ctx->K == 1 ? samples + k * CD : nullptr;
       a.trace_acc = trace_acc ? trace_acc + k * ctx->C : nullptr;
       a.trace_eps = trace_eps ? trace_eps + k : nullptr;
     }
     cudaError_t e = enqueue_transition(ctx, a);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "transition launch");
+    if (ctx->K > 1) {
+      e = hmc::launch_remc_swap(ctx->outer_chains, ctx->K, ctx->target.dim, x, ctx->lp, ctx->g,
+                                ctx->betas, ctx->cfg.seed, static_cast<uint32_t>(t), ctx->swapped,
+                                ctx->stream);
+      if (e == cudaSuccess && k >= 0 && samples)
+        e = cudaMemcpyAsync(samples + k * CD, x, CD * sizeof(float), cudaMemcpyDeviceToDevice,
+                            ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange step");
+    }
     if (k >= 0 && ctx->s_mean) {
       e = hmc::launch_welford(CD, x, k, ctx->s_mean, ctx->s_m2, ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "moment update launch");
@@ -416,6 +434,12 @@ hmc_status hmc_step(hmc_ctx* ctx, float* x_inout, uint64_t t, hmc_kernel_results
   StepArgs a = make_args(ctx, x_inout, t);
   cudaError_t e = enqueue_transition(ctx, a);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "transition launch");
+  if (ctx->K > 1) {
+    e = hmc::launch_remc_swap(ctx->outer_chains, ctx->K, ctx->target.dim, x_inout, ctx->lp, ctx->g,
+                              ctx->betas, ctx->cfg.seed, static_cast<uint32_t>(t), ctx->swapped,
+                              ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange step");
+  }
   if (out) {
     out->target_log_prob = ctx->lp;
     out->grad = ctx->g;
@@ -517,6 +541,51 @@ hmc_status hmc_read_adaptation(hmc_ctx* ctx, double out[5]) {
   out[2] = h.h_bar;
   out[3] = static_cast<double>(h.m);
   out[4] = h.last_stat;
+  return HMC_OK;
+}
+
+hmc_status hmc_remc_create(const hmc_target* target, int64_t num_chains, int32_t num_replicas,
+                           const float* betas, const hmc_config* config, void* cuda_stream,
+                           hmc_ctx** out) {
+  if (!out) return fail(nullptr, HMC_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (num_replicas < 2) return fail(nullptr, HMC_E_INVALID, "num_replicas must be >= 2");
+  if (!betas) return fail(nullptr, HMC_E_INVALID, "betas is NULL");
+  for (int k = 0; k < num_replicas; ++k)
+    if (!std::isfinite(betas[k]) || !(betas[k] > 0.f) || betas[k] > 1.f)
+      return fail(nullptr, HMC_E_INVALID, "betas must lie in (0, 1]");
+  if (!config) return fail(nullptr, HMC_E_INVALID, "config is NULL");
+  if (config->adapt) return fail(nullptr, HMC_E_UNSUPPORTED, "replica exchange uses a fixed step size");
+  if (config->chain_offset != 0) return fail(nullptr, HMC_E_INVALID, "chain_offset must be 0");
+  if (num_chains < 1 || num_chains > (1ll << 30) / num_replicas)
+    return fail(nullptr, HMC_E_INVALID, "num_chains out of range");
+  hmc_config c = *config;
+  // the dense targets' tensor-core kernels do not temper: plain path for them
+  if (target && (target->id == HMC_T_CORR_GAUSS || target->id == HMC_T_LOGREG)) c.impl = HMC_IMPL_PLAIN;
+  hmc_ctx* ctx = nullptr;
+  hmc_status st = hmc_create(target, num_chains * num_replicas, &c, cuda_stream, &ctx);
+  if (st != HMC_OK) return st;
+  ctx->K = num_replicas;
+  ctx->outer_chains = num_chains;
+  cudaError_t e = ctx_alloc(ctx, &ctx->betas, static_cast<size_t>(num_replicas));
+  if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->swapped, static_cast<size_t>(num_chains * (num_replicas - 1)));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->betas, betas, sizeof(float) * num_replicas, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(ctx->swapped, 0, static_cast<size_t>(num_chains * (num_replicas - 1)),
+                        ctx->stream);
+  if (e != cudaSuccess) {
+    hmc_destroy(ctx);
+    return fail(nullptr, e == cudaErrorMemoryAllocation ? HMC_E_OOM : HMC_E_CUDA,
+                std::string("replica set-up: ") + cudaGetErrorString(e));
+  }
+  *out = ctx;
+  return HMC_OK;
+}
+
+hmc_status hmc_remc_swaps(const hmc_ctx* ctx, const uint8_t** swapped) {
+  if (!ctx || !swapped || ctx->K < 2) return fail(nullptr, HMC_E_INVALID, "not a replica-exchange context");
+  *swapped = ctx->swapped;
   return HMC_OK;
 }
 

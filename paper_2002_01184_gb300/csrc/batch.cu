@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(256) k_batch_transition(const BatchPost* __res
 constexpr int64_t kGroupedMaxWork = int64_t(1) << 22;
 
 bool grouped_member(const hmc_target& t, int64_t C) {
-  return t.id != HMC_T_LOGREG || C * t.n_data * t.dim <= kGroupedMaxWork;
+  return t.id != HMC_T_LOGREG ||
+         (logreg_fused_supported(t) && C * t.n_data * t.dim <= kGroupedMaxWork);
 }
 
 int blocks_per_lane(int D) {
@@ -232,9 +233,10 @@ hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
   if (e == cudaSuccess && !flat.empty()) e = cudaMalloc(&b->dev_items, sizeof(int2) * flat.size());
   if (e == cudaSuccess && !flat.empty())
     e = cudaMemcpy(b->dev_items, flat.data(), sizeof(int2) * flat.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && b->smem > 0)
+  // the attribute belongs to the kernel, not to this batch: set the maximum
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(hmc::k_batch_transition, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(b->smem));
+                             static_cast<int>(hmc::lr::logreg_smem_bytes(hmc::lr::kLrMaxDim)));
   if (e != cudaSuccess) {
     const hmc_status st = e == cudaErrorMemoryAllocation ? HMC_E_OOM : HMC_E_CUDA;
     cudaGetLastError();

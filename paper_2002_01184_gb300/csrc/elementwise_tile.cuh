@@ -75,6 +75,14 @@ __device__ __forceinline__ void elementwise_tile(const StepArgs& a, int tile, in
         if (lane == 0) g[0][0] = -v / 9.f - half_n + 0.5f * ev * q;
         if (l == a.L - 1) lp1 = -v * v / 18.f - half_n * v - 0.5f * ev * q;
       }
+      if (a.K > 1) {      // replica exchange: this row targets p^beta
+        const float beta = a.betas[c % a.K];
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) g[b][i] *= beta;
+        if (l == a.L - 1) lp1 *= beta;
+      }
       // dims past D keep x = p = g = 0 throughout (g = -x and -e^-v x vanish)
 #pragma unroll
       for (int b = 0; b < NB; ++b)

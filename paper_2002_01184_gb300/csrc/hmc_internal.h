@@ -95,6 +95,8 @@ struct StepArgs {
   float* sample_out;      // [C x D] or null
   uint8_t* trace_acc;     // [C] or null
   float* trace_eps;       // [1] or null
+  const float* betas;     // replica exchange: row r targets p^betas[r % K]; null = 1
+  int K;                  // replicas per chain (1: no tempering)
 };
 
 // Scratch of the plain (one launch per operation) transition.
@@ -124,6 +126,13 @@ cudaError_t logreg_fused_setup(const hmc_target& t);
 unsigned logreg_fused_grid(int64_t C);
 cudaError_t launch_logreg_fused_transition(const hmc_target& t, const StepArgs& a, cudaStream_t s,
                                            KernelTimer* timer);
+// lp[r] *= beta, g[r, :] *= beta with beta = betas[r % K]
+cudaError_t launch_temper(int64_t rows, int D, float* lp, float* g, const float* betas, int K,
+                          cudaStream_t s);
+// replica-exchange step after transition t (pairs k = t % 2, t % 2 + 2, ...)
+cudaError_t launch_remc_swap(int64_t chains, int K, int D, float* x, float* lp, float* g,
+                             const float* betas, uint64_t seed, uint32_t t, uint8_t* swapped,
+                             cudaStream_t s);
 cudaError_t launch_welford(int64_t n, const float* x, int64_t k, float* mean, float* m2,
                            cudaStream_t s);
 cudaError_t launch_da_init(DAState* da, float eps0, int adapt, float delta, long long num_adapt,

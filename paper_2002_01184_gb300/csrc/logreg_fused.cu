@@ -23,9 +23,10 @@ bool logreg_fused_supported(const hmc_target& t) {
   return t.id == HMC_T_LOGREG && t.dim <= lr::kLrMaxDim && t.n_data <= kFusedMaxRows;
 }
 
-cudaError_t logreg_fused_setup(const hmc_target& t) {
+cudaError_t logreg_fused_setup(const hmc_target&) {
+  // the attribute belongs to the kernel, shared by every context: the maximum
   return cudaFuncSetAttribute(k_logreg_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(lr::logreg_smem_bytes(t.dim)));
+                              static_cast<int>(lr::logreg_smem_bytes(lr::kLrMaxDim)));
 }
 
 unsigned logreg_fused_grid(int64_t C) {

@@ -202,6 +202,7 @@ cudaError_t launch_plain_transition(const hmc_target& t, const StepArgs& a, cons
     k_plain_kick_drift<<<elementwise_blocks(n), 256, 0, s>>>(n, b.p, b.gp, b.xp, a.da);
     count_launch();
     cudaError_t e = launch_grad(t, a.C, b.xp, b.lpp, b.gp, grad_ws, s, timer);
+    if (e == cudaSuccess && a.K > 1) e = launch_temper(a.C, a.D, b.lpp, b.gp, a.betas, a.K, s);
     if (e != cudaSuccess) return e;
     k_plain_kick<<<elementwise_blocks(n), 256, 0, s>>>(n, b.p, b.gp, a.da);
     count_launch();
@@ -253,6 +254,85 @@ cudaError_t launch_welford(int64_t n, const float* x, int64_t k, float* mean, fl
                            cudaStream_t s) {
   k_welford<<<static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 152 * 16)), 256, 0, s>>>(
       n, x, k, mean, m2);
+  count_launch();
+  return cudaGetLastError();
+}
+
+__global__ void k_temper(int64_t rows, int D, float* __restrict__ lp, float* __restrict__ g,
+                         const float* __restrict__ betas, int K) {
+  const int64_t n = rows * D;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = i / D;
+    const float beta = betas[r % K];
+    g[i] *= beta;
+    if (i % D == 0) lp[r] *= beta;
+  }
+}
+
+cudaError_t launch_temper(int64_t rows, int D, float* lp, float* g, const float* betas, int K,
+                          cudaStream_t s) {
+  const int64_t n = rows * D;
+  k_temper<<<static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 152 * 16)), 256, 0, s>>>(
+      rows, D, lp, g, betas, K);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Replica exchange (Section 2.2): for chain c and pair (k, k+1), k = t % 2,
+// t % 2 + 2, ..., swap the two replicas' states iff
+// log u < (beta_k - beta_{k+1}) (log p(x_{k+1}) - log p(x_k)), with u drawn from
+// the counter generator at (k, c, t, tag 2).  Cached log p and gradient are
+// tempered: the untempered values are lp / beta and g / beta.  Warp per pair.
+__global__ void k_remc_swap(int64_t chains, int K, int D, float* __restrict__ x,
+                            float* __restrict__ lp, float* __restrict__ g,
+                            const float* __restrict__ betas, uint64_t seed, uint32_t t,
+                            uint8_t* __restrict__ swapped) {
+  const int npairs = K - 1;
+  const int64_t w = blockIdx.x * static_cast<int64_t>(kWarpsPerBlock) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= chains * npairs) return;
+  const int64_t c = w / npairs;
+  const int k = static_cast<int>(w % npairs);
+  if ((k & 1) != static_cast<int>(t & 1u)) {
+    if (lane == 0) swapped[w] = 0;
+    return;
+  }
+  const int64_t r0 = c * K + k, r1 = r0 + 1;
+  const float b0 = betas[k], b1 = betas[k + 1];
+  const float raw0 = lp[r0] / b0, raw1 = lp[r1] / b1;
+  const float la = (b0 - b1) * (raw1 - raw0);
+  int sw = 0;
+  if (lane == 0) {
+    const uint4 u = philox(make_uint4(static_cast<uint32_t>(k), static_cast<uint32_t>(c), t, 2u),
+                           static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
+    sw = log_word_uniform(u.x) < la;
+  }
+  sw = __shfl_sync(0xffffffffu, sw, 0);
+  if (sw) {
+    for (int d = lane; d < D; d += 32) {
+      const int64_t e0 = r0 * D + d, e1 = r1 * D + d;
+      const float xa = x[e0], xb = x[e1];
+      x[e0] = xb;
+      x[e1] = xa;
+      const float ga = g[e0], gb = g[e1];
+      g[e0] = gb / b1 * b0;
+      g[e1] = ga / b0 * b1;
+    }
+    if (lane == 0) {
+      lp[r0] = b0 * raw1;
+      lp[r1] = b1 * raw0;
+    }
+  }
+  if (lane == 0) swapped[w] = static_cast<uint8_t>(sw);
+}
+
+cudaError_t launch_remc_swap(int64_t chains, int K, int D, float* x, float* lp, float* g,
+                             const float* betas, uint64_t seed, uint32_t t, uint8_t* swapped,
+                             cudaStream_t s) {
+  const int64_t warps = chains * (K - 1);
+  k_remc_swap<<<static_cast<unsigned>((warps + kWarpsPerBlock - 1) / kWarpsPerBlock),
+                32 * kWarpsPerBlock, 0, s>>>(chains, K, D, x, lp, g, betas, seed, t, swapped);
   count_launch();
   return cudaGetLastError();
 }

@@ -66,6 +66,10 @@ def _load():
         "hmc_target_log_prob_and_grad": [ctypes.POINTER(hmc_target), ctypes.c_int64, P, P, P, P,
                                          ctypes.c_uint64, P],
         "hmc_synchronize": [P],
+        "hmc_remc_create": [ctypes.POINTER(hmc_target), ctypes.c_int64, ctypes.c_int32,
+                            ctypes.POINTER(ctypes.c_float), ctypes.POINTER(hmc_config), P,
+                            ctypes.POINTER(P)],
+        "hmc_remc_swaps": [P, ctypes.POINTER(P)],
         "hmc_batch_create": [ctypes.c_int32, ctypes.POINTER(hmc_target), ctypes.POINTER(ctypes.c_int64),
                              ctypes.POINTER(hmc_config), P, ctypes.POINTER(P)],
         "hmc_batch_sample_chain": [P, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int64),
@@ -309,3 +313,18 @@ def hmc_batch_context(batch, i):
 
 def hmc_batch_destroy(batch):
     _check_batch(lib.hmc_batch_destroy(batch), None)
+
+
+def hmc_remc_create(target, num_chains, betas, config, stream=None):
+    n = len(betas)
+    arr = (ctypes.c_float * n)(*[float(b) for b in betas])
+    ctx = ctypes.c_void_p()
+    _check(lib.hmc_remc_create(ctypes.byref(target), int(num_chains), n, arr, ctypes.byref(config),
+                               _stream(stream), ctypes.byref(ctx)))
+    return ctx.value
+
+
+def hmc_remc_swaps(ctx):
+    p = ctypes.c_void_p()
+    _check(lib.hmc_remc_swaps(ctx, ctypes.byref(p)), ctx)
+    return p.value
