@@ -179,7 +179,9 @@ hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
     hmc_config c = configs[i];
     const bool grouped = hmc::grouped_member(t, num_chains[i]);
     c.impl = HMC_IMPL_FUSED;       // side members: tensor-core products where they apply
-    c.use_graph = 0;
+    // side members replay their own graph: enqueueing thousands of launches
+    // eagerly would fill the launch queue and serialise the side streams
+    c.use_graph = grouped ? 0 : 1;
     cudaStream_t side = nullptr;
     cudaEvent_t done = nullptr;
     if (!grouped) {
