@@ -2,11 +2,13 @@
 // CTA pairs (tcgen05 cta_group::2).  A pair owns 64 chains for the whole
 // transition (Section 2.1): each leapfrog gradient G^T = P X^T is one stream
 // of M = 256 (all output dims), N = 64 (the pair's chains), K = 8 MMAs issued
-// by the pair's leader -- half as many MMA instructions per step as two
-// independent 32-chain CTAs, which matters because a 3xTF32 step at this
-// chain count is bound by the MMA issue rate, not by arithmetic or memory.
-//   * A (P head / remainder, 3xTF32): each CTA streams the 128 rows of P for
-//     its half of the output dims by TMA, completing on the leader's barrier.
+// by the pair's leader.
+//   * A (P head / remainder, 3xTF32) is resident for the whole launch: each
+//     CTA's 128 rows of P, K-chunks 0-6 (dims 0-223) in its tensor memory and
+//     chunk 7 (dims 224-255) in shared memory.  The MMAs then read only the
+//     positions from shared memory: at 64 chains an MMA that also read A from
+//     shared memory would be bound by shared-memory bandwidth, not by the
+//     tensor pipe.
 //   * B (positions, head / remainder tiles, 128-byte-swizzled K-major): each
 //     CTA holds 32 of the 64 chains.
 //   * Accumulators: each CTA's tensor memory holds its 128 output dims for
@@ -29,26 +31,33 @@ namespace hmc {
 namespace {
 
 constexpr int kMaxDim = 256;
-constexpr int kChunks = kMaxDim / 32;
+constexpr int kChunks = kMaxDim / 32;             // K-chunks of 32 dims
+constexpr int kTmemChunks = 7;                    // P chunks held in tensor memory
 constexpr int kThreads = 320;
 constexpr int kPairChains = 64;                   // MMA N
 constexpr int kHalf = 32;                         // chains per CTA (B rows)
 constexpr uint32_t kBChunk = kHalf * 128;         // 32 rows x 128 B
 constexpr uint32_t kBBytes = kChunks * kBChunk;   // head or remainder tile
 constexpr uint32_t kAHalf = 128 * 128;            // 128 rows x 32 floats
-constexpr uint32_t kAStage = 2 * kAHalf;
-constexpr int kStages = 4;
-constexpr uint32_t kTmemCols = 64;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kColAcc = 0;                   // accumulators: 64 columns
+constexpr uint32_t kColP = 64;                    // chunk kc: head at kColP + 64 kc, remainder + 32
 // barriers, tmem slot, red [2][4][64], red_pair [2][64], peer_in [2][64],
 // acc_flag [64], prob_s [64]
-constexpr uint32_t kSmall = 8 * (2 * kStages + 2) + 16 + (2 * 4 * 64 + 2 * 64 + 2 * 64 + 64 + 64) * 4;
-constexpr size_t kSmem = 2 * kBBytes + kStages * kAStage + kSmall + 1024;
+constexpr uint32_t kSmall = 8 * 3 + 8 + (2 * 4 * 64 + 2 * 64 + 2 * 64 + 64 + 64) * 4;
+constexpr size_t kSmemUsed = 2 * kBBytes + 2 * kAHalf + kSmall + 1024;
+// Above half of an SM's shared memory, so that one CTA runs per SM: a CTA
+// allocates all 512 tensor-memory columns and must never queue in
+// tcgen05.alloc behind another CTA of the launch.
+constexpr size_t kSmem = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
 
 struct PairArgs {
   StepArgs s;
   int* err;
   const float* p0;      // [C x D]
   const float* kin0;    // [C]
+  const float* Phi;     // [D x D] tf32 head of P
+  const float* Plo;     // [D x D] remainder
 };
 
 __device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
@@ -72,13 +81,12 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint8_t* Bhi = smem;
   uint8_t* Blo = smem + kBBytes;
-  uint8_t* Ast = smem + 2 * kBBytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(Ast + kStages * kAStage);
-  uint64_t* empty = full + kStages;
-  uint64_t* acc_full = empty + kStages;
+  uint8_t* A7 = smem + 2 * kBBytes;                        // P chunk 7: head, remainder
+  uint64_t* a7_full = reinterpret_cast<uint64_t*>(A7 + 2 * kAHalf);
+  uint64_t* acc_full = a7_full + 1;
   uint64_t* x_ready = acc_full + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(x_ready + 1);
-  float* red = reinterpret_cast<float*>(tmem_slot + 4);   // [2][4 quarters][64 chains]
+  float* red = reinterpret_cast<float*>(tmem_slot + 2);   // [2][4 quarters][64 chains]
   float* red_pair = red + 2 * 4 * 64;                     // [2][64] this CTA's sums
   float* peer_in = red_pair + 2 * 64;                     // [2][64] the peer's sums (leader)
   int* acc_flag = reinterpret_cast<int*>(peer_in + 2 * 64);   // [64]
@@ -92,10 +100,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   constexpr uint16_t kPairMask = 0x3;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      ptx::mbar_init(&full[s], 1);
-      ptx::mbar_init(&empty[s], 1);
-    }
+    ptx::mbar_init(a7_full, 1);
     ptx::mbar_init(acc_full, 1);
     ptx::mbar_init(x_ready, 2 * 256);
     ptx::fence_mbar_init();
@@ -127,29 +132,21 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   float p[kHalf], x[kHalf];
 
   if (warp == 0) {
-    if (lane == 0) {
-      // ---- producer: this CTA's 128 rows of P, completing on the leader's barrier
-      int it = 0;
-      for (int l = 1; l <= L && ok; ++l)
-        for (int kc = 0; kc < nk; ++kc, ++it) {
-          const int s = it % kStages, round = it / kStages;
-          if (it >= kStages && !ptx::mbar_wait(&empty[s], (round - 1) & 1)) {
-            atomicCAS(fa.err, 0, 1);
-            ok = false;
-            break;
-          }
-          if (rank == 0) ptx::mbar_arrive_expect_tx(&full[s], 2 * kAStage);
-          const uint32_t bar = ptx::mapa(ptx::smem_u32(&full[s]), 0);
-          uint8_t* st = Ast + s * kAStage;
-          ptx::tma_load_2d_to_bar(st, &mPhi, bar, kc * 32, static_cast<int>(rank) * 128);
-          ptx::tma_load_2d_to_bar(st + kAHalf, &mPlo, bar, kc * 32, static_cast<int>(rank) * 128);
-        }
+    if (lane == 0 && nk > kTmemChunks) {
+      // ---- P chunk 7 of this CTA's rows, once, completing on the leader's barrier
+      if (rank == 0) ptx::mbar_arrive_expect_tx(a7_full, 4 * kAHalf);
+      const uint32_t bar = ptx::mapa(ptx::smem_u32(a7_full), 0);
+      ptx::tma_load_2d_to_bar(A7, &mPhi, bar, kTmemChunks * 32, static_cast<int>(rank) * 128);
+      ptx::tma_load_2d_to_bar(A7 + kAHalf, &mPlo, bar, kTmemChunks * 32, static_cast<int>(rank) * 128);
     }
   } else if (warp == 1) {
     if (lane == 0 && rank == 0) {
       // ---- MMA issuer (leader): M = 256 across the pair, N = 64 chains
       constexpr uint32_t idesc = ptx::idesc_tf32(256, kPairChains);
-      int it = 0;
+      if (nk > kTmemChunks && !ptx::mbar_wait(a7_full, 0)) {
+        atomicCAS(fa.err, 0, 1);
+        ok = false;
+      }
       for (int l = 1; l <= L && ok; ++l) {
         if (!ptx::mbar_wait_cluster(x_ready, (l - 1) & 1)) {
           atomicCAS(fa.err, 0, 2);
@@ -157,31 +154,35 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
           break;
         }
         ptx::tc_fence_after();
-        for (int kc = 0; kc < nk; ++kc, ++it) {
-          const int s = it % kStages, round = it / kStages;
-          if (!ptx::mbar_wait(&full[s], round & 1)) {
-            atomicCAS(fa.err, 0, 3);
-            ok = false;
-            break;
-          }
-          ptx::tc_fence_after();
-          const uint32_t ahi = ptx::smem_u32(Ast + s * kAStage);
-          const uint32_t alo = ahi + kAHalf;
+        for (int kc = 0; kc < nk; ++kc) {
           const uint32_t bhi = ptx::smem_u32(Bhi + kc * kBChunk);
           const uint32_t blo = ptx::smem_u32(Blo + kc * kBChunk);
+          if (kc < kTmemChunks) {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const uint64_t dahi = ptx::sw128_kmajor_desc(ahi + 32 * j);
-            const uint64_t dalo = ptx::sw128_kmajor_desc(alo + 32 * j);
-            const uint64_t dbhi = ptx::sw128_kmajor_desc(bhi + 32 * j);
-            const uint64_t dblo = ptx::sw128_kmajor_desc(blo + 32 * j);
-            ptx::mma_tf32_pair(tmem, dalo, dbhi, idesc, (kc | j) != 0 ? 1u : 0u);
-            ptx::mma_tf32_pair(tmem, dahi, dblo, idesc, 1u);
-            ptx::mma_tf32_pair(tmem, dahi, dbhi, idesc, 1u);
+            for (int j = 0; j < 4; ++j) {
+              const uint64_t dbhi = ptx::sw128_kmajor_desc(bhi + 32 * j);
+              const uint64_t dblo = ptx::sw128_kmajor_desc(blo + 32 * j);
+              const uint32_t ahi = tmem + kColP + 64 * kc + 8 * j;
+              const uint32_t alo = ahi + 32;
+              ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, alo, dbhi, idesc, (kc | j) != 0 ? 1u : 0u);
+              ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, ahi, dblo, idesc, 1u);
+              ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, ahi, dbhi, idesc, 1u);
+            }
+          } else {
+            const uint32_t ahi = ptx::smem_u32(A7);
+            const uint32_t alo = ahi + kAHalf;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const uint64_t dahi = ptx::sw128_kmajor_desc(ahi + 32 * j);
+              const uint64_t dalo = ptx::sw128_kmajor_desc(alo + 32 * j);
+              const uint64_t dbhi = ptx::sw128_kmajor_desc(bhi + 32 * j);
+              const uint64_t dblo = ptx::sw128_kmajor_desc(blo + 32 * j);
+              ptx::mma_tf32_pair(tmem + kColAcc, dalo, dbhi, idesc, 1u);
+              ptx::mma_tf32_pair(tmem + kColAcc, dahi, dblo, idesc, 1u);
+              ptx::mma_tf32_pair(tmem + kColAcc, dahi, dbhi, idesc, 1u);
+            }
           }
-          ptx::mma_commit_pair(&empty[s], kPairMask);
         }
-        if (!ok) break;
         ptx::mma_commit_pair(acc_full, kPairMask);
       }
     }
@@ -199,6 +200,33 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         ptx::st_cluster_f32(ptx::mapa(ptx::smem_u32(Blo + off), peer), lo);
       }
     };
+    // P rows of this CTA (row = output dim d = TMEM lane) into tensor memory:
+    // the two warps of a lane quarter split chunks 0-3 and 4-6
+    {
+      const int kc_end = min(nk, kTmemChunks);
+      const bool row_ok = d < D;
+      for (int kc = h == 0 ? 0 : 4; kc < (h == 0 ? min(kc_end, 4) : kc_end); ++kc) {
+#pragma unroll
+        for (int q16 = 0; q16 < 2; ++q16) {
+          float vh[16], vl[16];
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) {
+            const int k = kc * 32 + q16 * 16 + q4 * 4;     // D % 4 == 0: all four in or out
+            float4 u = make_float4(0.f, 0.f, 0.f, 0.f), w = u;
+            if (row_ok && k < D) {
+              u = *reinterpret_cast<const float4*>(fa.Phi + static_cast<int64_t>(d) * D + k);
+              w = *reinterpret_cast<const float4*>(fa.Plo + static_cast<int64_t>(d) * D + k);
+            }
+            vh[4 * q4] = u.x; vh[4 * q4 + 1] = u.y; vh[4 * q4 + 2] = u.z; vh[4 * q4 + 3] = u.w;
+            vl[4 * q4] = w.x; vl[4 * q4 + 1] = w.y; vl[4 * q4 + 2] = w.z; vl[4 * q4 + 3] = w.w;
+          }
+          const uint32_t col = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + kColP + 64 * kc + 16 * q16;
+          ptx::tmem_st16(col, vh);
+          ptx::tmem_st16(col + 32, vl);
+        }
+      }
+      ptx::tmem_wait_st();
+    }
     // begin: p = p0 + eps/2 g0, x1 = x0 + eps p
 #pragma unroll
     for (int i8 = 0; i8 < kHalf; i8 += 8) {
@@ -379,7 +407,7 @@ cudaError_t launch_gauss_pair_transition(const StepArgs& a, GaussTc& tc, cudaStr
                                          KernelTimer* timer) {
   cudaError_t em = launch_gauss_momentum(a, tc, s);     // p0 and |p0|^2 / 2 of transition t
   if (em != cudaSuccess) return em;
-  PairArgs fa{a, tc.err, tc.p, tc.h0};
+  PairArgs fa{a, tc.err, tc.p, tc.h0, tc.Phi, tc.Plo};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(gauss_pair_grid(a.C));
   cfg.blockDim = dim3(kThreads);

@@ -40,18 +40,26 @@ constexpr size_t kSmem = kThetaBytes + kStages * kStage + 1024 + 256 + 2 * 128 *
 
 struct LrTcArgs {
   int C, D, N, ntiles, tiles_per_split, nsplit, dpad;
+  int need_lp;           // log-likelihood partials too (last leapfrog step only)
   const float* y;        // [Npad]
   float* Gpart;          // [nsplit x C x D]
   float* lp_part;        // [nsplit x C]
   int* err;
 };
 
-__device__ __forceinline__ float sigmoid_f(float z) {
-  const float e = expf(-fabsf(z));
-  return z >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
+// y - sigmoid(z) for the gradient: the fast exponential and divide (a few
+// ulp; the gradient tolerance is orders of magnitude looser)
+__device__ __forceinline__ float residual_f(float y, float z) {
+  const float e = __expf(-fabsf(z));
+  const float inv = __fdividef(1.f, 1.f + e);
+  return y - (z >= 0.f ? inv : e * inv);
 }
 
-__device__ __forceinline__ float softplus_f(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
+// y z - softplus(z) for log p, correctly rounded building blocks (the
+// accept test compares sums over all rows)
+__device__ __forceinline__ float loglik_f(float y, float z) {
+  return y * z - (fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))));
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
 k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUtensorMap mTlo,
@@ -212,6 +220,7 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
     const int r = quarter * 32 + lane;
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
     float lp_acc = 0.f;
+    const bool need_lp = a.need_lp != 0;
     for (int ti = 0; ti < ntile; ++ti) {
       const int row0 = (t_begin + ti) * kRowsPerTile;
       if (!ptx::mbar_wait(z_full, ti & 1)) {
@@ -228,10 +237,10 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
         for (int k = 0; k < 16; ++k) {
           const int n = row0 + static_cast<int>(col) + k;
           float res = 0.f;
-          if (n < a.N) {
+          if (n < a.N) {              // warp-uniform: a warp's lanes are chains
             const float yv = a.y[n];
-            res = yv - sigmoid_f(zv[k]);
-            lp_acc += yv * zv[k] - softplus_f(zv[k]);
+            res = residual_f(yv, zv[k]);
+            if (need_lp) lp_acc += loglik_f(yv, zv[k]);
           }
           split_tf32(res, rh[k], rl[k]);
         }
@@ -552,6 +561,7 @@ cudaError_t launch_logreg_tc_transition(const StepArgs& a, LogregTc& tc, int* er
   g.N = tc.n_data;
   const dim3 grid(tc.groups, tc.nsplit);
   for (int l = 1; l <= a.L; ++l) {
+    g.need_lp = l == a.L;
     if (timer) timer->begin(s);
     k_lr_grad<<<grid, kThreads, kSmem, s>>>(tc.mThi, tc.mTlo, tc.mXhi, tc.mXlo, tc.mXThi, tc.mXTlo, g);
     if (timer) timer->end(s);

@@ -30,9 +30,11 @@ struct LrArgs {
   int N;
 };
 
+// gradient residual with the fast exponential and divide (a few ulp)
 __device__ __forceinline__ float sigmoid_stable(float z) {
-  const float e = expf(-fabsf(z));
-  return z >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
+  const float e = __expf(-fabsf(z));
+  const float inv = __fdividef(1.f, 1.f + e);
+  return z >= 0.f ? inv : e * inv;
 }
 
 __device__ __forceinline__ float softplus_stable(float z) {
@@ -65,8 +67,10 @@ __device__ __forceinline__ Smem carve(float* base, int ld) {
   return s;
 }
 
-// gr[c] = grad log p(th_c), returns log p(th_c) in red[c] (all threads call)
-__device__ __noinline__ static void gradient(const LrArgs& a, const Smem& s, int ld, int nvalid) {
+// gr[c] = grad log p(th_c); with need_lp also log p(th_c) in red[c] (all
+// threads call; log p is needed at the end of a trajectory only)
+__device__ __noinline__ static void gradient(const LrArgs& a, const Smem& s, int ld, int nvalid,
+                                             bool need_lp) {
   const int D = a.s.D, N = a.N;
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   for (int d = lane; d < D; d += 32) s.gr[w * ld + d] = 0.f;
@@ -90,7 +94,7 @@ __device__ __noinline__ static void gradient(const LrArgs& a, const Smem& s, int
       if (pr < rows && pc < nvalid) {
         const float yv = s.ys[pr];
         r = yv - sigmoid_stable(z);
-        lp_acc += yv * z - softplus_stable(z);
+        if (need_lp) lp_acc += yv * z - softplus_stable(z);
       }
       s.res[pr * kLrTC + pc] = r;
     }
@@ -154,7 +158,7 @@ __device__ __forceinline__ void logreg_tile(const LrArgs& a, int tile, int ntile
   kin0 = 0.5f * warp_sum(kin0);
   __syncthreads();
   for (int l = 1; l <= A.L; ++l) {
-    gradient(a, s, ld, nvalid);
+    gradient(a, s, ld, nvalid, l == A.L);
     const float kick = l < A.L ? eps : 0.5f * eps;
     for (int d = lane; d < D; d += 32) {
       const float p = fmaf(kick, s.gr[w * ld + d], s.pm[w * ld + d]);
