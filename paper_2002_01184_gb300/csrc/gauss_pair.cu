@@ -14,8 +14,14 @@
 //   * Accumulators: each CTA's tensor memory holds its 128 output dims for
 //     all 64 chains.
 //   * Epilogue (warps 2-9 of both CTAs): one output dim per thread, 32 chains
-//     per thread; momenta and positions stay in registers, the next positions
-//     are written (split) into whichever CTA's tile holds the chain.
+//     per thread; momenta and positions stay in registers.  The next
+//     positions of this CTA's own chains go straight into its tile; those of
+//     the peer's chains are staged locally (in the destination's layout) and
+//     each staging warp pushes its K-chunk (head and remainder, 4 KB each) to
+//     the peer by bulk DSMEM copy, completing on the peer's tile barrier --
+//     element-wise remote stores stalled every warp's shared-memory traffic.
+//     The peer forwards the completion of its tile to the leader, whose
+//     issuer waits for both tiles.
 // H_L, the Metropolis-Hastings decision and the dual-averaging partial are
 // formed by the leader from both CTAs' partial sums.
 #include <cuda.h>
@@ -42,10 +48,12 @@ constexpr uint32_t kAHalf = 128 * 128;            // 128 rows x 32 floats
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColAcc = 0;                   // accumulators: 64 columns
 constexpr uint32_t kColP = 64;                    // chunk kc: head at kColP + 64 kc, remainder + 32
+constexpr uint32_t kStageHalf = 4 * kBChunk;      // 4 K-chunks (this CTA's 128 dims) x 32 chains
+constexpr uint32_t kStageBytes = 2 * kStageHalf;  // head + remainder: one bulk copy each
 // barriers, tmem slot, red [2][4][64], red_pair [2][64], peer_in [2][64],
 // acc_flag [64], prob_s [64]
-constexpr uint32_t kSmall = 8 * 3 + 8 + (2 * 4 * 64 + 2 * 64 + 2 * 64 + 64 + 64) * 4;
-constexpr size_t kSmemUsed = 2 * kBBytes + 2 * kAHalf + kSmall + 1024;
+constexpr uint32_t kSmall = 8 * 4 + 8 + (2 * 4 * 64 + 2 * 64 + 2 * 64 + 64 + 64) * 4;
+constexpr size_t kSmemUsed = 2 * kBBytes + 2 * kAHalf + 2 * kStageBytes + kSmall + 1024;
 // Above half of an SM's shared memory, so that one CTA runs per SM: a CTA
 // allocates all 512 tensor-memory columns and must never queue in
 // tcgen05.alloc behind another CTA of the launch.
@@ -67,9 +75,8 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
 }
 
 __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
-
-__device__ __forceinline__ void proxy_fence_cluster() {
-  asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+__device__ __forceinline__ void proxy_fence_cta() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -82,10 +89,12 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   uint8_t* Bhi = smem;
   uint8_t* Blo = smem + kBBytes;
   uint8_t* A7 = smem + 2 * kBBytes;                        // P chunk 7: head, remainder
-  uint64_t* a7_full = reinterpret_cast<uint64_t*>(A7 + 2 * kAHalf);
+  uint8_t* Stg = A7 + 2 * kAHalf;                          // [2 buffers][head, remainder]
+  uint64_t* a7_full = reinterpret_cast<uint64_t*>(Stg + 2 * kStageBytes);
   uint64_t* acc_full = a7_full + 1;
-  uint64_t* x_ready = acc_full + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(x_ready + 1);
+  uint64_t* tile_full = acc_full + 1;     // this CTA's B tile holds the next positions
+  uint64_t* peer_ok = tile_full + 1;      // leader: the peer's tile does too
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(peer_ok + 1);
   float* red = reinterpret_cast<float*>(tmem_slot + 2);   // [2][4 quarters][64 chains]
   float* red_pair = red + 2 * 4 * 64;                     // [2][64] this CTA's sums
   float* peer_in = red_pair + 2 * 64;                     // [2][64] the peer's sums (leader)
@@ -102,7 +111,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   if (threadIdx.x == 0) {
     ptx::mbar_init(a7_full, 1);
     ptx::mbar_init(acc_full, 1);
-    ptx::mbar_init(x_ready, 2 * 256);
+    ptx::mbar_init(tile_full, 128);       // the local-chain warps; one also arms the peer's copy bytes
+    ptx::mbar_init(peer_ok, 1);
     ptx::fence_mbar_init();
     ptx::prefetch_tensormap(&mPhi);
     ptx::prefetch_tensormap(&mPlo);
@@ -111,8 +121,11 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     ptx::tmem_alloc_pair(tmem_slot, kTmemCols);
     ptx::tmem_relinquish_pair();
   }
+  // B tiles and staging start zeroed: dims >= D are never written
   for (uint32_t i = threadIdx.x; i < 2 * kBBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (uint32_t i = threadIdx.x; i < 2 * kStageBytes / 16; i += kThreads)
+    reinterpret_cast<uint4*>(Stg)[i] = make_uint4(0u, 0u, 0u, 0u);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   ptx::tc_fence_before();
   __syncthreads();
@@ -120,7 +133,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const float eps = a.da->eps;
-  const uint32_t x_ready_leader = ptx::mapa(ptx::smem_u32(x_ready), 0);
+  const uint32_t peer = 1u - rank;
   bool ok = true;
 
   // epilogue-thread state (warps 2-9)
@@ -148,7 +161,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         ok = false;
       }
       for (int l = 1; l <= L && ok; ++l) {
-        if (!ptx::mbar_wait_cluster(x_ready, (l - 1) & 1)) {
+        if (!ptx::mbar_wait(tile_full, (l - 1) & 1) || !ptx::mbar_wait_cluster(peer_ok, (l - 1) & 1)) {
           atomicCAS(fa.err, 0, 2);
           ok = false;
           break;
@@ -185,19 +198,57 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         }
         ptx::mma_commit_pair(acc_full, kPairMask);
       }
+    } else if (lane == 0) {
+      // ---- peer: forward each completion of this CTA's tile to the leader
+      const uint32_t peer_ok_leader = ptx::mapa(ptx::smem_u32(peer_ok), 0);
+      for (int l = 1; l <= L; ++l) {
+        if (!ptx::mbar_wait(tile_full, (l - 1) & 1)) {
+          atomicCAS(fa.err, 0, 5);
+          break;
+        }
+        ptx::mbar_arrive_cluster(peer_ok_leader);
+      }
     }
   } else {
     // ---- epilogue, both CTAs
-    const uint32_t peer = 1u - rank;
-    // B tile element of chain (half h, row i) at dim d: local if h == rank
-    auto tile_store = [&](int i, float hi, float lo) {
-      const uint32_t off = sw128_offset(i, d);
-      if (static_cast<uint32_t>(h) == rank) {
+    const bool own = static_cast<uint32_t>(h) == rank;   // warp-uniform
+    // Position of chain (half h, row i) at dim d: into this CTA's tile if the
+    // chain is ours, else into staging buffer `buf`, laid out as K-chunks
+    // 4 rank .. 4 rank + 3 of the peer's tile (1024-byte aligned both sides,
+    // so the swizzle pattern carries over).
+    auto tile_store = [&](int i, float hi, float lo, int buf) {
+      if (own) {
+        const uint32_t off = sw128_offset(i, d);
         *reinterpret_cast<float*>(Bhi + off) = hi;
         *reinterpret_cast<float*>(Blo + off) = lo;
       } else {
-        ptx::st_cluster_f32(ptx::mapa(ptx::smem_u32(Bhi + off), peer), hi);
-        ptx::st_cluster_f32(ptx::mapa(ptx::smem_u32(Blo + off), peer), lo);
+        const uint32_t off = sw128_offset(i, d - static_cast<int>(rank) * 128);
+        uint8_t* sb = Stg + buf * kStageBytes;
+        *reinterpret_cast<float*>(sb + off) = hi;
+        *reinterpret_cast<float*>(sb + kStageHalf + off) = lo;
+      }
+    };
+    // The next positions are written: own warps arrive on this CTA's tile
+    // barrier (one arms the peer's incoming copy bytes); each staging warp
+    // pushes its K-chunk -- staging chunk `quarter`, the peer's K-chunk
+    // 4 rank + quarter -- completing on the peer's barrier.
+    auto publish = [&](int buf) {
+      proxy_fence_cta();          // generic stores -> async proxy (MMA, bulk copy)
+      ptx::tc_fence_before();     // this thread's accumulator reads precede the next MMA
+      if (own) {
+        if ((ew & 3) == 0 && lane == 0)
+          ptx::mbar_arrive_expect_tx(tile_full, kStageBytes);
+        else
+          ptx::mbar_arrive_local(tile_full);
+      } else {
+        __syncwarp();
+        if (lane == 0) {
+          const uint32_t bar = ptx::mapa(ptx::smem_u32(tile_full), peer);
+          const uint32_t chunk = (4 * rank + quarter) * kBChunk;
+          uint8_t* sb = Stg + buf * kStageBytes + quarter * kBChunk;
+          ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Bhi + chunk), peer), sb, kBChunk, bar);
+          ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Blo + chunk), peer), sb + kStageHalf, kBChunk, bar);
+        }
       }
     };
     // P rows of this CTA (row = output dim d = TMEM lane) into tensor memory:
@@ -248,13 +299,11 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         if (dvalid && pair_base + h * kHalf + i < C) {
           float hi, lo;
           split_tf32(x[i], hi, lo);
-          tile_store(i, hi, lo);
+          tile_store(i, hi, lo, 0);
         }
       }
     }
-    proxy_fence_cluster();
-    ptx::tc_fence_before();
-    ptx::mbar_arrive_cluster(x_ready_leader);
+    publish(0);
     for (int l = 1; l <= L; ++l) {
       const bool last = l == L;
       if (!ptx::mbar_wait(acc_full, (l - 1) & 1)) {
@@ -276,18 +325,14 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
             if (dvalid && pair_base + h * kHalf + i < C) {
               float hi, lo;
               split_tf32(x[i], hi, lo);
-              tile_store(i, hi, lo);
+              tile_store(i, hi, lo, l & 1);
             }
           } else {
             p[i] = fmaf(0.5f * eps, g, p[i]);
           }
         }
       }
-      if (!last) {
-        proxy_fence_cluster();
-        ptx::tc_fence_before();
-        ptx::mbar_arrive_cluster(x_ready_leader);
-      }
+      if (!last) publish(l & 1);
     }
     // partial sums over this CTA's dims: <x, g> and |p|^2 per chain
 #pragma unroll
@@ -325,6 +370,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       }
     }
   }
+  // every copy into this CTA's tile has landed (immediate unless a wait gave up)
+  if (warp == 1 && lane == 0) ptx::mbar_wait(tile_full, (L - 1) & 1);
   ptx::tc_fence_before();
   __syncthreads();
   ptx::cluster_sync();      // the peer's partial sums have landed in the leader
