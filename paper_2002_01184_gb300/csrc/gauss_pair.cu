@@ -20,8 +20,14 @@
 //     each staging warp pushes its K-chunk (head and remainder, 4 KB each) to
 //     the peer by bulk DSMEM copy, completing on the peer's tile barrier --
 //     element-wise remote stores stalled every warp's shared-memory traffic.
-//     The peer forwards the completion of its tile to the leader, whose
-//     issuer waits for both tiles.
+//   * Readiness is tracked per half of K: in each CTA's tile the K-chunks of
+//     its own dims are written locally (own_full, which every epilogue thread
+//     joins once it has read the accumulators) and the other four arrive by
+//     copy (in_full).
+//     The peer forwards both completions to the leader.  The issuer starts
+//     on K-chunks 4-7, whose leader half arrives by copy straight onto the
+//     leader's barrier, and reaches K-chunks 0-3, whose peer half needs the
+//     copy plus the forward, a quarter-step of MMAs later.
 // H_L, the Metropolis-Hastings decision and the dual-averaging partial are
 // formed by the leader from both CTAs' partial sums.
 #include <cuda.h>
@@ -52,7 +58,7 @@ constexpr uint32_t kStageHalf = 4 * kBChunk;      // 4 K-chunks (this CTA's 128 
 constexpr uint32_t kStageBytes = 2 * kStageHalf;  // head + remainder: one bulk copy each
 // barriers, tmem slot, red [2][4][64], red_pair [2][64], peer_in [2][64],
 // acc_flag [64], prob_s [64]
-constexpr uint32_t kSmall = 8 * 4 + 8 + (2 * 4 * 64 + 2 * 64 + 2 * 64 + 64 + 64) * 4;
+constexpr uint32_t kSmall = 8 * 6 + 8 + (2 * 4 * 64 + 2 * 64 + 2 * 64 + 64 + 64) * 4;
 constexpr size_t kSmemUsed = 2 * kBBytes + 2 * kAHalf + 2 * kStageBytes + kSmall + 1024;
 // Above half of an SM's shared memory, so that one CTA runs per SM: a CTA
 // allocates all 512 tensor-memory columns and must never queue in
@@ -64,14 +70,37 @@ struct PairArgs {
   int* err;
   const float* p0;      // [C x D]
   const float* kin0;    // [C]
-  const float* Phi;     // [D x D] tf32 head of P
-  const float* Plo;     // [D x D] remainder
+  const float* Ptm;     // P chunks 0-6 in tensor-memory fill order (k_tmem_image)
 };
 
-__device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
-  const int kc = k >> 5, cc = k & 31;
-  return kc * kBChunk + (r >> 3) * 1024 + (r & 7) * 128 + ((((cc >> 2) ^ (r & 7)) & 7) << 4) +
-         (cc & 3) * 4;
+// Index of element e of float4 j of lane `lane` in the tensor-memory image:
+// rank, K-chunk kc (0-6), head / remainder hl, 16-column half q16, lane
+// quarter q.  A warp's j-th float4 load of a 16-column block is 512
+// contiguous bytes.
+__host__ __device__ constexpr int image_index(int rank, int kc, int hl, int q16, int q, int j, int lane) {
+  return (((((rank * kTmemChunks + kc) * 2 + hl) * 2 + q16) * 4 + q) * 4 + j) * 128 + lane * 4;
+}
+
+__global__ void k_tmem_image(const float* __restrict__ Phi, const float* __restrict__ Plo, int D,
+                             float* __restrict__ image) {
+  constexpr int n = 2 * kTmemChunks * 2 * 2 * 4 * 4 * 32;   // float4 slots
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    int r = v;
+    const int lane = r % 32; r /= 32;
+    const int j = r % 4; r /= 4;
+    const int q = r % 4; r /= 4;
+    const int q16 = r % 2; r /= 2;
+    const int hl = r % 2; r /= 2;
+    const int kc = r % kTmemChunks;
+    const int rank = r / kTmemChunks;
+    const int row = rank * 128 + q * 32 + lane;
+    const int col = kc * 32 + q16 * 16 + j * 4;
+    const float* src = hl == 0 ? Phi : Plo;
+    float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row < D && col < D)            // D % 4 == 0: all four in or out
+      val = *reinterpret_cast<const float4*>(src + static_cast<int64_t>(row) * D + col);
+    *reinterpret_cast<float4*>(image + image_index(rank, kc, hl, q16, q, j, lane)) = val;
+  }
 }
 
 __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
@@ -92,9 +121,11 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   uint8_t* Stg = A7 + 2 * kAHalf;                          // [2 buffers][head, remainder]
   uint64_t* a7_full = reinterpret_cast<uint64_t*>(Stg + 2 * kStageBytes);
   uint64_t* acc_full = a7_full + 1;
-  uint64_t* tile_full = acc_full + 1;     // this CTA's B tile holds the next positions
-  uint64_t* peer_ok = tile_full + 1;      // leader: the peer's tile does too
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(peer_ok + 1);
+  uint64_t* own_full = acc_full + 1;      // all epilogue threads: accumulators read, own K-chunks written
+  uint64_t* in_full = own_full + 1;       // this CTA's tile: the peer's K-chunks copied in
+  uint64_t* fwd_own = in_full + 1;        // leader: the peer's own_full, forwarded
+  uint64_t* fwd_in = fwd_own + 1;         // leader: the peer's in_full, forwarded
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fwd_in + 1);
   float* red = reinterpret_cast<float*>(tmem_slot + 2);   // [2][4 quarters][64 chains]
   float* red_pair = red + 2 * 4 * 64;                     // [2][64] this CTA's sums
   float* peer_in = red_pair + 2 * 64;                     // [2][64] the peer's sums (leader)
@@ -111,8 +142,10 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   if (threadIdx.x == 0) {
     ptx::mbar_init(a7_full, 1);
     ptx::mbar_init(acc_full, 1);
-    ptx::mbar_init(tile_full, 128);       // the local-chain warps; one also arms the peer's copy bytes
-    ptx::mbar_init(peer_ok, 1);
+    ptx::mbar_init(own_full, 256);        // every epilogue thread
+    ptx::mbar_init(in_full, 1);           // armed with the copy bytes by one own-chain thread
+    ptx::mbar_init(fwd_own, 1);
+    ptx::mbar_init(fwd_in, 1);
     ptx::fence_mbar_init();
     ptx::prefetch_tensormap(&mPhi);
     ptx::prefetch_tensormap(&mPlo);
@@ -126,6 +159,20 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (uint32_t i = threadIdx.x; i < 2 * kStageBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(Stg)[i] = make_uint4(0u, 0u, 0u, 0u);
+  {
+    // the begin phase reads x, g and p0 of the pair's chains after the
+    // tensor-memory fill: start pulling this CTA's 32 rows of each into L2
+    const int c0 = pair_base + static_cast<int>(rank) * kHalf;
+    const int rows = max(0, min(kHalf, C - c0));
+    const int64_t lines = (static_cast<int64_t>(rows) * D * 4 + 127) / 128;
+    const int64_t row0 = static_cast<int64_t>(c0) * D;
+    for (int64_t i = threadIdx.x; i < 3 * lines; i += kThreads) {
+      const int64_t arr = i / lines, ln = i - arr * lines;
+      const float* base = arr == 0 ? a.x : arr == 1 ? a.g : fa.p0;
+      const int64_t off = min(ln * 128, static_cast<int64_t>(rows) * D * 4 - 4);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(base + row0) + off));
+    }
+  }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   ptx::tc_fence_before();
   __syncthreads();
@@ -160,72 +207,104 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         atomicCAS(fa.err, 0, 1);
         ok = false;
       }
+      // one K-chunk: 4 k-steps x 3 products
+      auto chunk_mmas = [&](int kc, bool& first) {
+        const uint32_t bhi = ptx::smem_u32(Bhi + kc * kBChunk);
+        const uint32_t blo = ptx::smem_u32(Blo + kc * kBChunk);
+        if (kc < kTmemChunks) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint64_t dbhi = ptx::sw128_kmajor_desc(bhi + 32 * j);
+            const uint64_t dblo = ptx::sw128_kmajor_desc(blo + 32 * j);
+            const uint32_t ahi = tmem + kColP + 64 * kc + 8 * j;
+            const uint32_t alo = ahi + 32;
+            ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, alo, dbhi, idesc, first ? 0u : 1u);
+            ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, ahi, dblo, idesc, 1u);
+            ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, ahi, dbhi, idesc, 1u);
+            first = false;
+          }
+        } else {
+          const uint32_t ahi = ptx::smem_u32(A7);
+          const uint32_t alo = ahi + kAHalf;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const uint64_t dahi = ptx::sw128_kmajor_desc(ahi + 32 * j);
+            const uint64_t dalo = ptx::sw128_kmajor_desc(alo + 32 * j);
+            const uint64_t dbhi = ptx::sw128_kmajor_desc(bhi + 32 * j);
+            const uint64_t dblo = ptx::sw128_kmajor_desc(blo + 32 * j);
+            ptx::mma_tf32_pair(tmem + kColAcc, dalo, dbhi, idesc, first ? 0u : 1u);
+            ptx::mma_tf32_pair(tmem + kColAcc, dahi, dblo, idesc, 1u);
+            ptx::mma_tf32_pair(tmem + kColAcc, dahi, dbhi, idesc, 1u);
+            first = false;
+          }
+        }
+      };
       for (int l = 1; l <= L && ok; ++l) {
-        if (!ptx::mbar_wait(tile_full, (l - 1) & 1) || !ptx::mbar_wait_cluster(peer_ok, (l - 1) & 1)) {
+        const uint32_t ph = (l - 1) & 1;
+        bool first = true;
+        // K-chunks 4-7: leader half copied in from the peer, peer half local
+        // there; own_full and fwd_own also mean both CTAs' epilogues have
+        // read the accumulators this step overwrites
+        if (!ptx::mbar_wait(own_full, ph) || !ptx::mbar_wait(in_full, ph) ||
+            !ptx::mbar_wait_cluster(fwd_own, ph)) {
           atomicCAS(fa.err, 0, 2);
           ok = false;
           break;
         }
         ptx::tc_fence_after();
-        for (int kc = 0; kc < nk; ++kc) {
-          const uint32_t bhi = ptx::smem_u32(Bhi + kc * kBChunk);
-          const uint32_t blo = ptx::smem_u32(Blo + kc * kBChunk);
-          if (kc < kTmemChunks) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const uint64_t dbhi = ptx::sw128_kmajor_desc(bhi + 32 * j);
-              const uint64_t dblo = ptx::sw128_kmajor_desc(blo + 32 * j);
-              const uint32_t ahi = tmem + kColP + 64 * kc + 8 * j;
-              const uint32_t alo = ahi + 32;
-              ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, alo, dbhi, idesc, (kc | j) != 0 ? 1u : 0u);
-              ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, ahi, dblo, idesc, 1u);
-              ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, ahi, dbhi, idesc, 1u);
-            }
-          } else {
-            const uint32_t ahi = ptx::smem_u32(A7);
-            const uint32_t alo = ahi + kAHalf;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const uint64_t dahi = ptx::sw128_kmajor_desc(ahi + 32 * j);
-              const uint64_t dalo = ptx::sw128_kmajor_desc(alo + 32 * j);
-              const uint64_t dbhi = ptx::sw128_kmajor_desc(bhi + 32 * j);
-              const uint64_t dblo = ptx::sw128_kmajor_desc(blo + 32 * j);
-              ptx::mma_tf32_pair(tmem + kColAcc, dalo, dbhi, idesc, 1u);
-              ptx::mma_tf32_pair(tmem + kColAcc, dahi, dblo, idesc, 1u);
-              ptx::mma_tf32_pair(tmem + kColAcc, dahi, dbhi, idesc, 1u);
-            }
-          }
+        for (int kc = 4; kc < nk; ++kc) chunk_mmas(kc, first);
+        // K-chunks 0-3: leader half local, peer half copied in from the leader
+        if (!ptx::mbar_wait_cluster(fwd_in, ph)) {
+          atomicCAS(fa.err, 0, 3);
+          ok = false;
+          break;
         }
+        ptx::tc_fence_after();
+        for (int kc = 0; kc < min(nk, 4); ++kc) chunk_mmas(kc, first);
         ptx::mma_commit_pair(acc_full, kPairMask);
       }
     } else if (lane == 0) {
-      // ---- peer: forward each completion of this CTA's tile to the leader
-      const uint32_t peer_ok_leader = ptx::mapa(ptx::smem_u32(peer_ok), 0);
+      // ---- peer: forward both completions of this CTA's tile to the leader
+      const uint32_t own_leader = ptx::mapa(ptx::smem_u32(fwd_own), 0);
+      const uint32_t in_leader = ptx::mapa(ptx::smem_u32(fwd_in), 0);
       for (int l = 1; l <= L; ++l) {
-        if (!ptx::mbar_wait(tile_full, (l - 1) & 1)) {
+        const uint32_t ph = (l - 1) & 1;
+        if (!ptx::mbar_wait(own_full, ph)) {
           atomicCAS(fa.err, 0, 5);
           break;
         }
-        ptx::mbar_arrive_cluster(peer_ok_leader);
+        ptx::mbar_arrive_cluster(own_leader);
+        if (!ptx::mbar_wait(in_full, ph)) {
+          atomicCAS(fa.err, 0, 6);
+          break;
+        }
+        ptx::mbar_arrive_cluster(in_leader);
       }
     }
   } else {
     // ---- epilogue, both CTAs
     const bool own = static_cast<uint32_t>(h) == rank;   // warp-uniform
-    // Position of chain (half h, row i) at dim d: into this CTA's tile if the
-    // chain is ours, else into staging buffer `buf`, laid out as K-chunks
-    // 4 rank .. 4 rank + 3 of the peer's tile (1024-byte aligned both sides,
-    // so the swizzle pattern carries over).
-    auto tile_store = [&](int i, float hi, float lo, int buf) {
-      if (own) {
-        const uint32_t off = sw128_offset(i, d);
-        *reinterpret_cast<float*>(Bhi + off) = hi;
-        *reinterpret_cast<float*>(Blo + off) = lo;
-      } else {
-        const uint32_t off = sw128_offset(i, d - static_cast<int>(rank) * 128);
-        uint8_t* sb = Stg + buf * kStageBytes;
-        *reinterpret_cast<float*>(sb + off) = hi;
-        *reinterpret_cast<float*>(sb + kStageHalf + off) = lo;
+    // Destination of this thread's positions (dim d, chain rows 0-31 of half
+    // h): this CTA's tile if the chains are ours, else staging, laid out as
+    // K-chunks 4 rank .. 4 rank + 3 of the peer's tile (1024-byte aligned both
+    // sides, so the swizzle carries over).  Row i's byte offset is
+    // col + (i / 8) * 1024 + sw[i % 8]; the eight sw terms are per thread.
+    const int dcol = own ? d : d - static_cast<int>(rank) * 128;
+    const uint32_t col = static_cast<uint32_t>((dcol >> 5) * kBChunk + (dcol & 3) * 4);
+    const uint32_t dst_hi0 = ptx::smem_u32(own ? Bhi : Stg) + col;
+    const uint32_t lo_off = own ? kBBytes : kStageHalf;
+    const uint32_t buf_off = own ? 0u : kStageBytes;       // staging double buffer stride
+    uint32_t sw[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) sw[r] = r * 128 + (((((dcol & 31) >> 2) ^ r) & 7) << 4);
+    const int nvalid = dvalid ? min(kHalf, C - (pair_base + h * kHalf)) : 0;
+    auto store_x = [&](int i, float xi, int buf) {   // position of row i, split
+      if (i < nvalid) {
+        float hi, lo;
+        split_tf32(xi, hi, lo);
+        const uint32_t a0 = dst_hi0 + buf * buf_off + (i >> 3) * 1024 + sw[i & 7];
+        asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0), "f"(hi) : "memory");
+        asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0 + lo_off), "f"(lo) : "memory");
       }
     };
     // The next positions are written: own warps arrive on this CTA's tile
@@ -235,15 +314,13 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     auto publish = [&](int buf) {
       proxy_fence_cta();          // generic stores -> async proxy (MMA, bulk copy)
       ptx::tc_fence_before();     // this thread's accumulator reads precede the next MMA
+      ptx::mbar_arrive_local(own_full);
       if (own) {
-        if ((ew & 3) == 0 && lane == 0)
-          ptx::mbar_arrive_expect_tx(tile_full, kStageBytes);
-        else
-          ptx::mbar_arrive_local(tile_full);
+        if ((ew & 3) == 0 && lane == 0) ptx::mbar_arrive_expect_tx(in_full, kStageBytes);
       } else {
         __syncwarp();
         if (lane == 0) {
-          const uint32_t bar = ptx::mapa(ptx::smem_u32(tile_full), peer);
+          const uint32_t bar = ptx::mapa(ptx::smem_u32(in_full), peer);
           const uint32_t chunk = (4 * rank + quarter) * kBChunk;
           uint8_t* sb = Stg + buf * kStageBytes + quarter * kBChunk;
           ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Bhi + chunk), peer), sb, kBChunk, bar);
@@ -251,29 +328,35 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         }
       }
     };
-    // P rows of this CTA (row = output dim d = TMEM lane) into tensor memory:
-    // the two warps of a lane quarter split chunks 0-3 and 4-6
+    const uint32_t acc_addr = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + kColAcc + h * kHalf;
+    auto wait_acc = [&](int l) {
+      if (!ptx::mbar_wait(acc_full, (l - 1) & 1)) {
+        atomicCAS(fa.err, 0, 4);
+        ok = false;
+      }
+      ptx::tc_fence_after();
+    };
+    // P rows of this CTA (row = output dim d = TMEM lane) into tensor memory
+    // from the pre-arranged image (coalesced): the two warps of a lane
+    // quarter split chunks 0-3 and 4-6
     {
       const int kc_end = min(nk, kTmemChunks);
-      const bool row_ok = d < D;
       for (int kc = h == 0 ? 0 : 4; kc < (h == 0 ? min(kc_end, 4) : kc_end); ++kc) {
 #pragma unroll
         for (int q16 = 0; q16 < 2; ++q16) {
           float vh[16], vl[16];
 #pragma unroll
           for (int q4 = 0; q4 < 4; ++q4) {
-            const int k = kc * 32 + q16 * 16 + q4 * 4;     // D % 4 == 0: all four in or out
-            float4 u = make_float4(0.f, 0.f, 0.f, 0.f), w = u;
-            if (row_ok && k < D) {
-              u = *reinterpret_cast<const float4*>(fa.Phi + static_cast<int64_t>(d) * D + k);
-              w = *reinterpret_cast<const float4*>(fa.Plo + static_cast<int64_t>(d) * D + k);
-            }
+            const float4 u = *reinterpret_cast<const float4*>(
+                fa.Ptm + image_index(static_cast<int>(rank), kc, 0, q16, quarter, q4, lane));
+            const float4 w = *reinterpret_cast<const float4*>(
+                fa.Ptm + image_index(static_cast<int>(rank), kc, 1, q16, quarter, q4, lane));
             vh[4 * q4] = u.x; vh[4 * q4 + 1] = u.y; vh[4 * q4 + 2] = u.z; vh[4 * q4 + 3] = u.w;
             vl[4 * q4] = w.x; vl[4 * q4 + 1] = w.y; vl[4 * q4 + 2] = w.z; vl[4 * q4 + 3] = w.w;
           }
-          const uint32_t col = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + kColP + 64 * kc + 16 * q16;
-          ptx::tmem_st16(col, vh);
-          ptx::tmem_st16(col + 32, vl);
+          const uint32_t tcol = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + kColP + 64 * kc + 16 * q16;
+          ptx::tmem_st16(tcol, vh);
+          ptx::tmem_st16(tcol + 32, vl);
         }
       }
       ptx::tmem_wait_st();
@@ -285,7 +368,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int chain = pair_base + h * kHalf + i8 + k;
-        const bool valid = dvalid && chain < C;
+        const bool valid = i8 + k < nvalid;
         const int64_t e = static_cast<int64_t>(chain) * D + d;
         xr[k] = valid ? a.x[e] : 0.f;
         gr[k] = valid ? a.g[e] : 0.f;
@@ -296,43 +379,35 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         const int i = i8 + k;
         p[i] = fmaf(0.5f * eps, gr[k], zr[k]);
         x[i] = fmaf(eps, p[i], xr[k]);
-        if (dvalid && pair_base + h * kHalf + i < C) {
-          float hi, lo;
-          split_tf32(x[i], hi, lo);
-          tile_store(i, hi, lo, 0);
-        }
+        store_x(i, x[i], 0);
       }
     }
     publish(0);
-    for (int l = 1; l <= L; ++l) {
-      const bool last = l == L;
-      if (!ptx::mbar_wait(acc_full, (l - 1) & 1)) {
-        atomicCAS(fa.err, 0, 4);
-        ok = false;
-      }
-      ptx::tc_fence_after();
+    // steps 1 .. L-1: merged kick + drift
+    for (int l = 1; l < L; ++l) {
+      wait_acc(l);
 #pragma unroll
       for (int cb = 0; cb < kHalf / 16; ++cb) {
         float accv[16];
-        ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + h * kHalf + cb * 16, accv);
+        ptx::tmem_ld16(acc_addr + cb * 16, accv);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const int i = cb * 16 + k;
-          const float g = -accv[k];
-          if (!last) {
-            p[i] = fmaf(eps, g, p[i]);
-            x[i] = fmaf(eps, p[i], x[i]);
-            if (dvalid && pair_base + h * kHalf + i < C) {
-              float hi, lo;
-              split_tf32(x[i], hi, lo);
-              tile_store(i, hi, lo, l & 1);
-            }
-          } else {
-            p[i] = fmaf(0.5f * eps, g, p[i]);
-          }
+          p[i] = fmaf(-eps, accv[k], p[i]);
+          x[i] = fmaf(eps, p[i], x[i]);
+          store_x(i, x[i], l & 1);
         }
       }
-      if (!last) publish(l & 1);
+      publish(l & 1);
+    }
+    // step L: final half kick
+    wait_acc(L);
+#pragma unroll
+    for (int cb = 0; cb < kHalf / 16; ++cb) {
+      float accv[16];
+      ptx::tmem_ld16(acc_addr + cb * 16, accv);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) p[cb * 16 + k] = fmaf(-0.5f * eps, accv[k], p[cb * 16 + k]);
     }
     // partial sums over this CTA's dims: <x, g> and |p|^2 per chain
 #pragma unroll
@@ -371,7 +446,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     }
   }
   // every copy into this CTA's tile has landed (immediate unless a wait gave up)
-  if (warp == 1 && lane == 0) ptx::mbar_wait(tile_full, (L - 1) & 1);
+  if (warp == 1 && lane == 0) ptx::mbar_wait(in_full, (L - 1) & 1);
   ptx::tc_fence_before();
   __syncthreads();
   ptx::cluster_sync();      // the peer's partial sums have landed in the leader
@@ -445,6 +520,14 @@ unsigned gauss_pair_grid(int64_t C) {
   return static_cast<unsigned>(2 * ((C + kPairChains - 1) / kPairChains));
 }
 
+cudaError_t launch_gauss_pair_image(const float* Phi, const float* Plo, int D, float* image,
+                                    cudaStream_t s) {
+  static_assert(kGaussPairImageFloats == 2 * kTmemChunks * 2 * 2 * 4 * 4 * 32 * 4, "image size");
+  k_tmem_image<<<static_cast<unsigned>(kGaussPairImageFloats / 4 / 256), 256, 0, s>>>(Phi, Plo, D, image);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t gauss_pair_setup() {
   return cudaFuncSetAttribute(k_gauss_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(kSmem));
@@ -454,7 +537,7 @@ cudaError_t launch_gauss_pair_transition(const StepArgs& a, GaussTc& tc, cudaStr
                                          KernelTimer* timer) {
   cudaError_t em = launch_gauss_momentum(a, tc, s);     // p0 and |p0|^2 / 2 of transition t
   if (em != cudaSuccess) return em;
-  PairArgs fa{a, tc.err, tc.p, tc.h0, tc.Phi, tc.Plo};
+  PairArgs fa{a, tc.err, tc.p, tc.h0, tc.Ptm};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(gauss_pair_grid(a.C));
   cfg.blockDim = dim3(kThreads);

@@ -347,7 +347,8 @@ size_t gauss_tc_workspace_bytes(const hmc_target& t, int64_t C) {
   const size_t CD = static_cast<size_t>(C) * t.dim, DD = static_cast<size_t>(t.dim) * t.dim;
   const size_t ntn = (t.dim + kBN - 1) / kBN;
   auto a = [](size_t b) { return (b + 1023) & ~static_cast<size_t>(1023); };
-  return 2 * a(DD * 4) + 6 * a(CD * 4) + a(C * ntn * 4) + a(C * 4) + a(sizeof(int));
+  const size_t image = t.dim <= 256 ? a(kGaussPairImageFloats * 4) : 0;
+  return 2 * a(DD * 4) + 6 * a(CD * 4) + a(C * ntn * 4) + a(C * 4) + a(sizeof(int)) + image;
 }
 
 cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s) {
@@ -367,6 +368,7 @@ cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws
   tc->lp_part = take(C * tc->ntn * 4);
   tc->h0 = take(C * 4);
   tc->err = reinterpret_cast<int*>(take(sizeof(int)));
+  tc->Ptm = t.dim <= 256 ? take(kGaussPairImageFloats * 4) : nullptr;
   bool ok = make_map(&tc->mBhi, tc->Phi, t.dim, t.dim, kBN) &&
             make_map(&tc->mBlo, tc->Plo, t.dim, t.dim, kBN) &&
             make_map(&tc->mPhi128, tc->Phi, t.dim, t.dim, 128) &&
@@ -387,6 +389,10 @@ cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws
   }
   k_split<<<blocks_for(DD), 256, 0, s>>>(static_cast<int64_t>(DD), t.P, tc->Phi, tc->Plo);
   count_launch();
+  if (tc->Ptm) {
+    e = launch_gauss_pair_image(tc->Phi, tc->Plo, t.dim, tc->Ptm, s);
+    if (e != cudaSuccess) return e;
+  }
   e = cudaMemsetAsync(tc->err, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

@@ -151,6 +151,7 @@ struct GaussTc {
   CUtensorMap mPhi32, mPlo32;    // 32 x 32 boxes (one CTA's share of a multicast stage)
   float* Phi = nullptr;      // tf32 head / remainder of P
   float* Plo = nullptr;
+  float* Ptm = nullptr;      // P in the pair kernel's tensor-memory fill order
   float* xhi[2] = {nullptr, nullptr};   // ping-pong trajectory positions
   float* xlo[2] = {nullptr, nullptr};
   float* p = nullptr;        // momentum
@@ -168,6 +169,10 @@ size_t gauss_tc_workspace_bytes(const hmc_target& t, int64_t C);
 cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s);
 bool gauss_fused_supported(const hmc_target& t);
 unsigned gauss_pair_grid(int64_t C);
+// floats of the pair kernel's tensor-memory image of P (dim <= 256)
+constexpr size_t kGaussPairImageFloats = 2 * 7 * 2 * 2 * 4 * 4 * 32 * 4;
+cudaError_t launch_gauss_pair_image(const float* Phi, const float* Plo, int D, float* image,
+                                    cudaStream_t s);
 cudaError_t launch_gauss_momentum(const StepArgs& a, GaussTc& tc, cudaStream_t s);
 cudaError_t gauss_pair_setup();
 cudaError_t launch_gauss_pair_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
