@@ -40,7 +40,7 @@ FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the committed
 # ncu capture of the same kernel on the same workload (profiles/); keyed by
 # (kernel, target, chains, dim, leapfrog steps).  Absent -> traffic is null.
-PROFILED_TRAFFIC = {("k_gauss_pair", "corr_gauss", 4096, 256, 16): 13278464}
+PROFILED_TRAFFIC = {}
 
 
 def parse():

@@ -182,7 +182,9 @@ int32_t hmc_uses_tensor_cores(const hmc_ctx* ctx);
 /* Measurement support (no counterpart in the paper): the name of the kernel
  * hmc_profile_dominant_kernel times for this context and how many chain
  * gradient evaluations one launch of it performs (chains x leapfrog steps for
- * the one-launch-per-transition kernels, chains for one gradient product). */
+ * the one-launch-per-transition kernels, times the transitions of the last
+ * hmc_sample_chain where one launch ran all of them -- the dense Gaussian on
+ * CTA pairs -- and chains for one gradient product). */
 hmc_status hmc_dominant_kernel_info(const hmc_ctx* ctx, char* name, int32_t name_len,
                                     int64_t* grad_evals_per_launch);
 

@@ -40,6 +40,8 @@ struct hmc_ctx {
   hmc::KernelTimer timer;
   bool use_tc = false;          // tensor-core Gaussian path
   hmc::GaussTc tc;
+  unsigned* grid_bar = nullptr;  // grid barrier of the multi-transition pair launch
+  int64_t dom_transitions = 1;   // transitions per launch of the dominant kernel (last chain)
   bool use_lrtc = false;        // tensor-core logistic-regression path
   hmc::LogregTc lrtc;
   int* lr_err = nullptr;
@@ -235,6 +237,18 @@ hmc_status enqueue_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sa
   hmc_status st = bootstrap(ctx, x);
   if (st != HMC_OK) return st;
   const int64_t CD = ctx->C * ctx->target.dim;
+  // dense Gaussian on CTA pairs: every transition of the chain in one launch
+  ctx->dom_transitions = 1;
+  if (ctx->use_tc && ctx->tc.pair && ctx->K == 1 && !ctx->s_mean && B + K > 1 &&
+      B + K <= (1ll << 30) && hmc::gauss_pair_persistent_ok(ctx->C)) {
+    StepArgs a = make_args(ctx, x, 0);
+    cudaError_t e = hmc::launch_gauss_pair_transitions(a, ctx->tc, static_cast<int>(B + K), B, samples,
+                                                       trace_eps, trace_acc, ctx->grid_bar,
+                                                       ctx->stream, &ctx->timer);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "multi-transition launch");
+    ctx->dom_transitions = B + K;
+    return HMC_OK;
+  }
   for (int64_t t = 0; t < B + K; ++t) {
     StepArgs a = make_args(ctx, x, static_cast<uint64_t>(t));
     const int64_t k = t - B;
@@ -367,7 +381,8 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->is_accepted, C);
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->log_accept, C);
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->da, 1);
-  if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->partials, nblk);
+  // (two transitions' worth: the multi-transition pair launch alternates)
+  if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->partials, 2 * static_cast<size_t>(nblk));
   ctx->use_tc = (config->impl == HMC_IMPL_FUSED || config->impl == HMC_IMPL_FUSED_SINGLE_CTA) &&
                 hmc::gauss_tc_supported(*target);
   if (e == cudaSuccess && ctx->use_tc) {
@@ -376,6 +391,7 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     if (e == cudaSuccess) e = hmc::gauss_tc_setup(&ctx->tc, *target, num_chains, w, ctx->stream);
     ctx->tc.fused = hmc::gauss_fused_supported(*target);
     ctx->tc.pair = ctx->tc.fused && config->impl == HMC_IMPL_FUSED;
+    if (e == cudaSuccess && ctx->tc.pair) e = ctx_alloc(ctx, &ctx->grid_bar, 1);
   }
   // logistic regressions with long data passes: tensor-core products; short
   // ones: the shared-memory SIMT transition
@@ -653,7 +669,7 @@ hmc_status hmc_dominant_kernel_info(const hmc_ctx* ctx, char* name, int32_t name
   int64_t per = ctx->C;
   if (ctx->use_tc && ctx->tc.fused && ctx->tc.pair) {
     n = "k_gauss_pair";
-    per = ctx->C * ctx->cfg.num_leapfrog;
+    per = ctx->C * ctx->cfg.num_leapfrog * ctx->dom_transitions;
   } else if (ctx->use_tc && ctx->tc.fused) {
     n = "k_gauss_fused";
     per = ctx->C * ctx->cfg.num_leapfrog;

@@ -1,8 +1,10 @@
-// One launch per HMC transition for the dense Gaussian target (dim <= 256) on
-// CTA pairs (tcgen05 cta_group::2).  A pair owns 64 chains for the whole
-// transition (Section 2.1): each leapfrog gradient G^T = P X^T is one stream
-// of M = 256 (all output dims), N = 64 (the pair's chains), K = 8 MMAs issued
-// by the pair's leader.
+// HMC transitions for the dense Gaussian target (dim <= 256) on CTA pairs
+// (tcgen05 cta_group::2).  A pair owns 64 chains; one launch runs T
+// consecutive transitions of them (Section 2.1's transition, Section 4.2's
+// driver loop), so that P stays resident across transitions and no launch
+// sits between them.  Each leapfrog gradient G^T = P X^T is one stream of
+// M = 256 (all output dims), N = 64 (the pair's chains), K = 8 MMAs issued by
+// the pair's leader.
 //   * A (P head / remainder, 3xTF32) is resident for the whole launch: each
 //     CTA's 128 rows of P, K-chunks 0-6 (dims 0-223) in its tensor memory and
 //     chunk 7 (dims 224-255) in shared memory.  The MMAs then read only the
@@ -14,22 +16,29 @@
 //   * Accumulators: each CTA's tensor memory holds its 128 output dims for
 //     all 64 chains.
 //   * Epilogue (warps 2-9 of both CTAs): one output dim per thread, 32 chains
-//     per thread; momenta and positions stay in registers.  The next
-//     positions of this CTA's own chains go straight into its tile; those of
-//     the peer's chains are staged locally (in the destination's layout) and
-//     each staging warp pushes its K-chunk (head and remainder, 4 KB each) to
-//     the peer by bulk DSMEM copy, completing on the peer's tile barrier --
-//     element-wise remote stores stalled every warp's shared-memory traffic.
+//     per thread; momenta and trajectory positions in registers, the chains'
+//     current state (position and gradient, this CTA's dims) in shared
+//     memory across transitions.  The next positions of this CTA's own
+//     chains go straight into its tile; those of the peer's chains are staged
+//     locally (in the destination's layout) and each staging warp pushes its
+//     K-chunk (head and remainder, 4 KB each) to the peer by bulk DSMEM copy,
+//     completing on the peer's tile barrier -- element-wise remote stores
+//     stalled every warp's shared-memory traffic.
 //   * Readiness is tracked per half of K: in each CTA's tile the K-chunks of
 //     its own dims are written locally (own_full, which every epilogue thread
 //     joins once it has read the accumulators) and the other four arrive by
-//     copy (in_full).
-//     The peer forwards both completions to the leader.  The issuer starts
-//     on K-chunks 4-7, whose leader half arrives by copy straight onto the
-//     leader's barrier, and reaches K-chunks 0-3, whose peer half needs the
-//     copy plus the forward, a quarter-step of MMAs later.
+//     copy (in_full).  The peer forwards both completions to the leader.  The
+//     issuer starts on K-chunks 4-7, whose leader half arrives by copy
+//     straight onto the leader's barrier, and reaches K-chunks 0-3, whose
+//     peer half needs the copy plus the forward, a quarter-step of MMAs later.
+//   * The momenta of the next transition are drawn while the epilogue waits
+//     for the MMAs (counter-based, so the draw order is free) and parked in
+//     global memory.
 // H_L, the Metropolis-Hastings decision and the dual-averaging partial are
-// formed by the leader from both CTAs' partial sums.
+// formed by the leader from both CTAs' partial sums.  With T > 1 the launch
+// is cooperative: after every transition all CTAs meet at a grid barrier and
+// each applies the same dual-averaging update to its own copy of the state;
+// a launch of one transition instead lets its last CTA update the state.
 #include <cuda.h>
 
 #include <cmath>
@@ -55,22 +64,30 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColAcc = 0;                   // accumulators: 64 columns
 constexpr uint32_t kColP = 64;                    // chunk kc: head at kColP + 64 kc, remainder + 32
 constexpr uint32_t kStageHalf = 4 * kBChunk;      // 4 K-chunks (this CTA's 128 dims) x 32 chains
-constexpr uint32_t kStageBytes = 2 * kStageHalf;  // head + remainder: one bulk copy each
-// barriers, tmem slot, red [2][4][64], red_pair [2][64], peer_in [2][64],
-// acc_flag [64], prob_s [64]
-constexpr uint32_t kSmall = 8 * 6 + 8 + (2 * 4 * 64 + 2 * 64 + 2 * 64 + 64 + 64) * 4;
-constexpr size_t kSmemUsed = 2 * kBBytes + 2 * kAHalf + 2 * kStageBytes + kSmall + 1024;
+constexpr uint32_t kStageBytes = 2 * kStageHalf;  // head + remainder
+constexpr uint32_t kStateBytes = kPairChains * 128 * 4;   // one of position / gradient
+// barriers (8), tmem slot, red [3][4][64], red_pair [3][64], peer_in [3][64],
+// acc_flag [64], prob_s [64], DA state copy, flags
+constexpr uint32_t kSmall = 8 * 8 + 16 + (3 * 4 * 64 + 3 * 64 + 3 * 64 + 64 + 64) * 4 + 128 + 16;
+constexpr size_t kSmemUsed =
+    2 * kBBytes + 2 * kAHalf + kStageBytes + 2 * kStateBytes + kSmall + 1024;
 // Above half of an SM's shared memory, so that one CTA runs per SM: a CTA
 // allocates all 512 tensor-memory columns and must never queue in
 // tcgen05.alloc behind another CTA of the launch.
 constexpr size_t kSmem = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
+static_assert(kSmem <= 227 * 1024, "shared memory");
 
 struct PairArgs {
-  StepArgs s;
+  StepArgs s;           // s.t / s.t_full: the first transition of the launch
   int* err;
-  const float* p0;      // [C x D]
-  const float* kin0;    // [C]
   const float* Ptm;     // P chunks 0-6 in tensor-memory fill order (k_tmem_image)
+  float* p0next;        // [C x D] momenta of the next transition (scratch)
+  int T;                // transitions in this launch
+  long long keep_from;  // transition t_full >= keep_from writes output k = t_full - keep_from
+  float* samples;       // [k][C x D] or null
+  float* trace_eps;     // [k] or null
+  uint8_t* trace_acc;   // [k][C] or null
+  unsigned* grid_bar;   // T > 1: grid barrier counter, zero at launch; null: one transition
 };
 
 // Index of element e of float4 j of lane `lane` in the tensor-memory image:
@@ -108,6 +125,37 @@ __device__ __forceinline__ void proxy_fence_cta() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// v[c] summed over the warp's lanes, for all 32 c at once: 31 shuffles
+// (each round halves the values a lane keeps); lane c ends with chain c's sum.
+__device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool upper = (lane & w) != 0;
+#pragma unroll
+    for (int k = 0; k < w; ++k) {
+      const float send = upper ? v[k] : v[k + w];
+      const float keep = upper ? v[k + w] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0];
+}
+
+// Grid barrier of a cooperative launch: generation `gen` (1, 2, ...) is
+// complete when every CTA has arrived `gen` times.  Bounded: false after
+// the wait limit.
+__device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned gen) {
+  __threadfence();
+  atomicAdd(counter, 1u);
+  const unsigned target = gen * gridDim.x;
+  const unsigned long long t0 = ptx::global_timer_ns();
+  while (*reinterpret_cast<volatile unsigned*>(counter) < target) {
+    if (ptx::global_timer_ns() - t0 > ptx::kWaitLimitNs) return false;
+  }
+  __threadfence();
+  return true;
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
 k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ CUtensorMap mPlo,
              PairArgs fa) {
@@ -118,26 +166,34 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   uint8_t* Bhi = smem;
   uint8_t* Blo = smem + kBBytes;
   uint8_t* A7 = smem + 2 * kBBytes;                        // P chunk 7: head, remainder
-  uint8_t* Stg = A7 + 2 * kAHalf;                          // [2 buffers][head, remainder]
-  uint64_t* a7_full = reinterpret_cast<uint64_t*>(Stg + 2 * kStageBytes);
+  uint8_t* Stg = A7 + 2 * kAHalf;                          // staging: head, remainder
+  float* xs = reinterpret_cast<float*>(Stg + kStageBytes); // [64 chains][128 dims] current position
+  float* gs = xs + kPairChains * 128;                      // [64 chains][128 dims] its gradient
+  uint64_t* a7_full = reinterpret_cast<uint64_t*>(gs + kPairChains * 128);
   uint64_t* acc_full = a7_full + 1;
   uint64_t* own_full = acc_full + 1;      // all epilogue threads: accumulators read, own K-chunks written
   uint64_t* in_full = own_full + 1;       // this CTA's tile: the peer's K-chunks copied in
   uint64_t* fwd_own = in_full + 1;        // leader: the peer's own_full, forwarded
   uint64_t* fwd_in = fwd_own + 1;         // leader: the peer's in_full, forwarded
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fwd_in + 1);
-  float* red = reinterpret_cast<float*>(tmem_slot + 2);   // [2][4 quarters][64 chains]
-  float* red_pair = red + 2 * 4 * 64;                     // [2][64] this CTA's sums
-  float* peer_in = red_pair + 2 * 64;                     // [2][64] the peer's sums (leader)
-  int* acc_flag = reinterpret_cast<int*>(peer_in + 2 * 64);   // [64]
+  uint64_t* sums_in = fwd_in + 1;         // leader: the peer's partial sums have landed
+  uint64_t* dec_in = sums_in + 1;         // peer: the leader's decisions have landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dec_in + 1);
+  float* red = reinterpret_cast<float*>(tmem_slot + 4);   // [3 sums][4 quarters][64 chains]
+  float* red_pair = red + 3 * 4 * 64;                     // [3][64] this CTA's sums
+  float* peer_in = red_pair + 3 * 64;                     // [3][64] the peer's sums (leader)
+  int* acc_flag = reinterpret_cast<int*>(peer_in + 3 * 64);   // [64]
   float* prob_s = reinterpret_cast<float*>(acc_flag + 64);    // [64]
+  DAState* da_s = reinterpret_cast<DAState*>(prob_s + 64);    // this CTA's copy (T > 1)
+  int* abort_s = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(da_s) + 128);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = ptx::cluster_rank();              // 0: leader, 1: peer
-  const int C = a.C, D = a.D, L = a.L;
+  const int C = a.C, D = a.D, L = a.L, T = fa.T;
   const int nk = (D + 31) >> 5;
   const int pair_base = (blockIdx.x >> 1) * kPairChains;
+  const bool persistent = fa.grid_bar != nullptr;
   constexpr uint16_t kPairMask = 0x3;
+  static_assert(sizeof(DAState) <= 128, "DA state copy");
 
   if (threadIdx.x == 0) {
     ptx::mbar_init(a7_full, 1);
@@ -146,9 +202,13 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     ptx::mbar_init(in_full, 1);           // armed with the copy bytes by one own-chain thread
     ptx::mbar_init(fwd_own, 1);
     ptx::mbar_init(fwd_in, 1);
+    ptx::mbar_init(sums_in, kPairChains);  // the peer's 64 summing threads
+    ptx::mbar_init(dec_in, kPairChains);   // the leader's 64 deciding threads
     ptx::fence_mbar_init();
     ptx::prefetch_tensormap(&mPhi);
     ptx::prefetch_tensormap(&mPlo);
+    if (persistent) *da_s = *a.da;
+    *abort_s = 0;
   }
   if (warp == 0) {
     ptx::tmem_alloc_pair(tmem_slot, kTmemCols);
@@ -157,29 +217,14 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   // B tiles and staging start zeroed: dims >= D are never written
   for (uint32_t i = threadIdx.x; i < 2 * kBBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
-  for (uint32_t i = threadIdx.x; i < 2 * kStageBytes / 16; i += kThreads)
+  for (uint32_t i = threadIdx.x; i < kStageBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(Stg)[i] = make_uint4(0u, 0u, 0u, 0u);
-  {
-    // the begin phase reads x, g and p0 of the pair's chains after the
-    // tensor-memory fill: start pulling this CTA's 32 rows of each into L2
-    const int c0 = pair_base + static_cast<int>(rank) * kHalf;
-    const int rows = max(0, min(kHalf, C - c0));
-    const int64_t lines = (static_cast<int64_t>(rows) * D * 4 + 127) / 128;
-    const int64_t row0 = static_cast<int64_t>(c0) * D;
-    for (int64_t i = threadIdx.x; i < 3 * lines; i += kThreads) {
-      const int64_t arr = i / lines, ln = i - arr * lines;
-      const float* base = arr == 0 ? a.x : arr == 1 ? a.g : fa.p0;
-      const int64_t off = min(ln * 128, static_cast<int64_t>(rows) * D * 4 - 4);
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(base + row0) + off));
-    }
-  }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   ptx::tc_fence_before();
   __syncthreads();
   ptx::cluster_sync();      // both CTAs' barriers and tensor memory exist
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const float eps = a.da->eps;
   const uint32_t peer = 1u - rank;
   bool ok = true;
 
@@ -187,7 +232,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   const int ew = warp - 2;
   const int h = ew >> 2;                  // chain half 0 / 1 (= the CTA holding those chains)
   const int quarter = warp & 3;           // tensor-memory lane quarter
-  const int d = static_cast<int>(rank) * 128 + quarter * 32 + lane;
+  const int dl = quarter * 32 + lane;     // this CTA's dim index 0..127
+  const int d = static_cast<int>(rank) * 128 + dl;
   const bool dvalid = warp >= 2 && d < D;
   float p[kHalf], x[kHalf];
 
@@ -239,8 +285,9 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
           }
         }
       };
-      for (int l = 1; l <= L && ok; ++l) {
-        const uint32_t ph = (l - 1) & 1;
+      // gradient step s (all transitions of the launch) consumes write s
+      for (int s = 0; s < T * L && ok; ++s) {
+        const uint32_t ph = s & 1;
         bool first = true;
         // K-chunks 4-7: leader half copied in from the peer, peer half local
         // there; own_full and fwd_own also mean both CTAs' epilogues have
@@ -267,8 +314,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       // ---- peer: forward both completions of this CTA's tile to the leader
       const uint32_t own_leader = ptx::mapa(ptx::smem_u32(fwd_own), 0);
       const uint32_t in_leader = ptx::mapa(ptx::smem_u32(fwd_in), 0);
-      for (int l = 1; l <= L; ++l) {
-        const uint32_t ph = (l - 1) & 1;
+      for (int s = 0; s < T * L; ++s) {
+        const uint32_t ph = s & 1;
         if (!ptx::mbar_wait(own_full, ph)) {
           atomicCAS(fa.err, 0, 5);
           break;
@@ -289,29 +336,31 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     // K-chunks 4 rank .. 4 rank + 3 of the peer's tile (1024-byte aligned both
     // sides, so the swizzle carries over).  Row i's byte offset is
     // col + (i / 8) * 1024 + sw[i % 8]; the eight sw terms are per thread.
-    const int dcol = own ? d : d - static_cast<int>(rank) * 128;
+    const int dcol = own ? d : dl;
     const uint32_t col = static_cast<uint32_t>((dcol >> 5) * kBChunk + (dcol & 3) * 4);
     const uint32_t dst_hi0 = ptx::smem_u32(own ? Bhi : Stg) + col;
     const uint32_t lo_off = own ? kBBytes : kStageHalf;
-    const uint32_t buf_off = own ? 0u : kStageBytes;       // staging double buffer stride
     uint32_t sw[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) sw[r] = r * 128 + (((((dcol & 31) >> 2) ^ r) & 7) << 4);
     const int nvalid = dvalid ? min(kHalf, C - (pair_base + h * kHalf)) : 0;
-    auto store_x = [&](int i, float xi, int buf) {   // position of row i, split
+    float* xrow = xs + (h * kHalf) * 128 + dl;           // + i * 128: chain row i of half h
+    float* grow = gs + (h * kHalf) * 128 + dl;
+    auto store_x = [&](int i, float xi) {   // position of row i, split, into tile / staging
       if (i < nvalid) {
         float hi, lo;
         split_tf32(xi, hi, lo);
-        const uint32_t a0 = dst_hi0 + buf * buf_off + (i >> 3) * 1024 + sw[i & 7];
+        const uint32_t a0 = dst_hi0 + (i >> 3) * 1024 + sw[i & 7];
         asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0), "f"(hi) : "memory");
         asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0 + lo_off), "f"(lo) : "memory");
       }
     };
-    // The next positions are written: own warps arrive on this CTA's tile
-    // barrier (one arms the peer's incoming copy bytes); each staging warp
-    // pushes its K-chunk -- staging chunk `quarter`, the peer's K-chunk
-    // 4 rank + quarter -- completing on the peer's barrier.
-    auto publish = [&](int buf) {
+    // The next positions are written: every thread arrives on own_full once
+    // its accumulator reads are done; an own-chain thread arms the peer's
+    // incoming copy bytes; each staging warp pushes its K-chunk -- staging
+    // chunk `quarter`, the peer's K-chunk 4 rank + quarter -- completing on
+    // the peer's in_full.
+    auto publish = [&]() {
       proxy_fence_cta();          // generic stores -> async proxy (MMA, bulk copy)
       ptx::tc_fence_before();     // this thread's accumulator reads precede the next MMA
       ptx::mbar_arrive_local(own_full);
@@ -322,20 +371,30 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         if (lane == 0) {
           const uint32_t bar = ptx::mapa(ptx::smem_u32(in_full), peer);
           const uint32_t chunk = (4 * rank + quarter) * kBChunk;
-          uint8_t* sb = Stg + buf * kStageBytes + quarter * kBChunk;
+          uint8_t* sb = Stg + quarter * kBChunk;
           ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Bhi + chunk), peer), sb, kBChunk, bar);
           ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Blo + chunk), peer), sb + kStageHalf, kBChunk, bar);
         }
       }
     };
     const uint32_t acc_addr = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + kColAcc + h * kHalf;
-    auto wait_acc = [&](int l) {
-      if (!ptx::mbar_wait(acc_full, (l - 1) & 1)) {
+    auto wait_acc = [&](int s) {
+      if (!ptx::mbar_wait(acc_full, s & 1)) {
         atomicCAS(fa.err, 0, 4);
         ok = false;
       }
       ptx::tc_fence_after();
     };
+    const uint32_t chain0 = static_cast<uint32_t>(pair_base + h * kHalf) + a.chain_offset;
+    // momenta of transition tn for rows i0 .. i1-1, parked for the next begin
+    auto draw_next = [&](int i0, int i1, uint32_t tn) {
+      for (int i = i0; i < i1; ++i)
+        if (i < nvalid)
+          fa.p0next[static_cast<int64_t>(pair_base + h * kHalf + i) * D + d] =
+              momentum1(a.seed, static_cast<uint32_t>(d), chain0 + i, tn);
+    };
+    const int per_wait = (kHalf + L - 1) / L;   // rows drawn ahead of each gradient wait
+
     // P rows of this CTA (row = output dim d = TMEM lane) into tensor memory
     // from the pre-arranged image (coalesced): the two warps of a lane
     // quarter split chunks 0-3 and 4-6
@@ -361,31 +420,144 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       }
       ptx::tmem_wait_st();
     }
-    // begin: p = p0 + eps/2 g0, x1 = x0 + eps p
-#pragma unroll
-    for (int i8 = 0; i8 < kHalf; i8 += 8) {
-      float xr[8], gr[8], zr[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int chain = pair_base + h * kHalf + i8 + k;
-        const bool valid = i8 + k < nvalid;
-        const int64_t e = static_cast<int64_t>(chain) * D + d;
-        xr[k] = valid ? a.x[e] : 0.f;
-        gr[k] = valid ? a.g[e] : 0.f;
-        zr[k] = valid ? fa.p0[e] : 0.f;
-      }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int i = i8 + k;
-        p[i] = fmaf(0.5f * eps, gr[k], zr[k]);
-        x[i] = fmaf(eps, p[i], xr[k]);
-        store_x(i, x[i], 0);
-      }
+    // the chains' current state, this CTA's dims
+#pragma unroll 4
+    for (int i = 0; i < kHalf; ++i) {
+      const bool valid = i < nvalid;
+      const int64_t e = static_cast<int64_t>(pair_base + h * kHalf + i) * D + d;
+      xrow[i * 128] = valid ? a.x[e] : 0.f;
+      grow[i * 128] = valid ? a.g[e] : 0.f;
     }
-    publish(0);
-    // steps 1 .. L-1: merged kick + drift
-    for (int l = 1; l < L; ++l) {
-      wait_acc(l);
+    // momenta of the first transition, straight into registers
+#pragma unroll
+    for (int i = 0; i < kHalf; ++i)
+      p[i] = i < nvalid ? momentum1(a.seed, static_cast<uint32_t>(d), chain0 + i, a.t) : 0.f;
+
+    for (int j = 0; j < T; ++j) {
+      const uint32_t t = a.t + static_cast<uint32_t>(j);
+      const bool more = j + 1 < T;
+      const float eps = persistent ? da_s->eps : a.da->eps;
+      if (j > 0) {
+#pragma unroll
+        for (int i = 0; i < kHalf; ++i)
+          p[i] = i < nvalid ? fa.p0next[static_cast<int64_t>(pair_base + h * kHalf + i) * D + d] : 0.f;
+      }
+      // |p0|^2 partials of this warp's dims, one per chain
+      {
+        float v[kHalf];
+#pragma unroll
+        for (int i = 0; i < kHalf; ++i) v[i] = p[i] * p[i];
+        red[(2 * 4 + quarter) * 64 + h * kHalf + lane] = transpose_reduce32(v, lane);
+      }
+      // begin: p = p0 + eps/2 g0, x1 = x0 + eps p
+#pragma unroll
+      for (int i = 0; i < kHalf; ++i) {
+        p[i] = fmaf(0.5f * eps, grow[i * 128], p[i]);
+        x[i] = fmaf(eps, p[i], xrow[i * 128]);
+        store_x(i, x[i]);
+      }
+      publish();
+      const int s0 = j * L;                 // gradient steps of this transition: s0 .. s0 + L - 1
+      // steps 1 .. L-1: merged kick + drift
+      for (int l = 1; l < L; ++l) {
+        if (more) draw_next(min(kHalf, (l - 1) * per_wait), min(kHalf, l * per_wait), t + 1);
+        wait_acc(s0 + l - 1);
+#pragma unroll
+        for (int cb = 0; cb < kHalf / 16; ++cb) {
+          float accv[16];
+          ptx::tmem_ld16(acc_addr + cb * 16, accv);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int i = cb * 16 + k;
+            p[i] = fmaf(-eps, accv[k], p[i]);
+            x[i] = fmaf(eps, p[i], x[i]);
+            store_x(i, x[i]);
+          }
+        }
+        publish();
+      }
+      // step L: final half kick; <x, g> and |p|^2 partials
+      if (more) draw_next(min(kHalf, (L - 1) * per_wait), kHalf, t + 1);
+      wait_acc(s0 + L - 1);
+      {
+        float v[kHalf];
+#pragma unroll
+        for (int cb = 0; cb < kHalf / 16; ++cb) {
+          float accv[16];
+          ptx::tmem_ld16(acc_addr + cb * 16, accv);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int i = cb * 16 + k;
+            p[i] = fmaf(-0.5f * eps, accv[k], p[i]);
+            v[i] = i < nvalid ? -x[i] * accv[k] : 0.f;
+          }
+        }
+        red[(0 * 4 + quarter) * 64 + h * kHalf + lane] = transpose_reduce32(v, lane);
+#pragma unroll
+        for (int i = 0; i < kHalf; ++i) v[i] = i < nvalid ? p[i] * p[i] : 0.f;
+        red[(1 * 4 + quarter) * 64 + h * kHalf + lane] = transpose_reduce32(v, lane);
+      }
+      epi_barrier();
+      // Only the epilogue warps run this loop, so the two CTAs meet on
+      // mbarriers: the peer's sums land in the leader (sums_in), the
+      // leader's decisions land in the peer (dec_in).
+      const int c = ew * 32 + lane;                 // 0..255; chains 0..63 handled below
+      if (c < kPairChains) {
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          float sum = 0.f;
+          for (int q = 0; q < 4; ++q) sum += red[(v * 4 + q) * 64 + c];
+          if (rank == 0)
+            red_pair[v * 64 + c] = sum;
+          else
+            ptx::st_cluster_f32(ptx::mapa(ptx::smem_u32(&peer_in[v * 64 + c]), 0), sum);
+        }
+        if (rank != 0) ptx::mbar_arrive_cluster(ptx::mapa(ptx::smem_u32(sums_in), 0));
+      }
+      const long long t_full = a.t_full + j;
+      const long long k_out = t_full - fa.keep_from;
+      if (rank == 0 && ew < 2) {
+        if (!ptx::mbar_wait_cluster(sums_in, j & 1)) {
+          atomicCAS(fa.err, 0, 8);
+          ok = false;
+        }
+        // H_L and the Metropolis-Hastings decision, chain c of the pair
+        const int chain = pair_base + c;
+        float prob = 0.f;
+        int acc = 0;
+        if (chain < C) {
+          const float xg = red_pair[c] + peer_in[c];
+          const float pp = red_pair[64 + c] + peer_in[64 + c];
+          const float kin0 = 0.5f * (red_pair[128 + c] + peer_in[128 + c]);
+          const float lp0 = a.lp[chain];
+          const float lp1 = 0.5f * xg;
+          float la = (-lp0 + kin0) - (-lp1 + 0.5f * pp);
+          if (!isfinite(la)) la = -INFINITY;
+          const uint32_t gchain = static_cast<uint32_t>(chain) + a.chain_offset;
+          acc = accept_log_uniform(a.seed, gchain, t) < la;
+          prob = accept_prob(la);
+          if (ok) {
+            if (acc) a.lp[chain] = lp1;
+            a.is_accepted[chain] = static_cast<uint8_t>(acc);
+            a.log_accept[chain] = la;
+            if (k_out >= 0 && fa.trace_acc) fa.trace_acc[k_out * C + chain] = static_cast<uint8_t>(acc);
+          }
+        }
+        acc_flag[c] = acc;
+        ptx::st_cluster_s32(ptx::mapa(ptx::smem_u32(&acc_flag[c]), 1), acc);
+        prob_s[c] = prob;
+        if (blockIdx.x == 0 && c == 0 && k_out >= 0 && fa.trace_eps && ok) fa.trace_eps[k_out] = eps;
+        ptx::mbar_arrive_cluster(ptx::mapa(ptx::smem_u32(dec_in), 1));
+      }
+      // decisions visible to every epilogue thread of both CTAs
+      if (rank == 0) {
+        epi_barrier();
+      } else if (!ptx::mbar_wait_cluster(dec_in, j & 1)) {
+        atomicCAS(fa.err, 0, 9);
+        ok = false;
+      }
+      // the accepted state (gradient from the accumulators) and the kept sample
+      float* samp = (k_out >= 0 && fa.samples) ? fa.samples + k_out * static_cast<int64_t>(C) * D : nullptr;
 #pragma unroll
       for (int cb = 0; cb < kHalf / 16; ++cb) {
         float accv[16];
@@ -393,114 +565,62 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const int i = cb * 16 + k;
-          p[i] = fmaf(-eps, accv[k], p[i]);
-          x[i] = fmaf(eps, p[i], x[i]);
-          store_x(i, x[i], l & 1);
-        }
-      }
-      publish(l & 1);
-    }
-    // step L: final half kick
-    wait_acc(L);
-#pragma unroll
-    for (int cb = 0; cb < kHalf / 16; ++cb) {
-      float accv[16];
-      ptx::tmem_ld16(acc_addr + cb * 16, accv);
-#pragma unroll
-      for (int k = 0; k < 16; ++k) p[cb * 16 + k] = fmaf(-0.5f * eps, accv[k], p[cb * 16 + k]);
-    }
-    // partial sums over this CTA's dims: <x, g> and |p|^2 per chain
-#pragma unroll
-    for (int cb = 0; cb < kHalf / 16; ++cb) {
-      float accv[16];
-      ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + h * kHalf + cb * 16, accv);
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int i = cb * 16 + k;
-        const bool valid = dvalid && pair_base + h * kHalf + i < C;
-        float xg = valid ? -x[i] * accv[k] : 0.f;
-        float pp = valid ? p[i] * p[i] : 0.f;
-        xg = warp_sum(xg);
-        pp = warp_sum(pp);
-        if (lane == 0) {
-          red[(0 * 4 + quarter) * 64 + h * kHalf + i] = xg;
-          red[(1 * 4 + quarter) * 64 + h * kHalf + i] = pp;
-        }
-      }
-    }
-    epi_barrier();
-    const int c = ew * 32 + lane;                 // 0..255; chains 0..63 handled below
-    if (c < kPairChains) {
-      float xg = 0.f, pp = 0.f;
-      for (int q = 0; q < 4; ++q) {
-        xg += red[(0 * 4 + q) * 64 + c];
-        pp += red[(1 * 4 + q) * 64 + c];
-      }
-      if (rank == 0) {
-        red_pair[c] = xg;
-        red_pair[64 + c] = pp;
-      } else {
-        ptx::st_cluster_f32(ptx::mapa(ptx::smem_u32(&peer_in[c]), 0), xg);
-        ptx::st_cluster_f32(ptx::mapa(ptx::smem_u32(&peer_in[64 + c]), 0), pp);
-      }
-    }
-  }
-  // every copy into this CTA's tile has landed (immediate unless a wait gave up)
-  if (warp == 1 && lane == 0) ptx::mbar_wait(in_full, (L - 1) & 1);
-  ptx::tc_fence_before();
-  __syncthreads();
-  ptx::cluster_sync();      // the peer's partial sums have landed in the leader
-  if (rank == 0 && threadIdx.x < kPairChains) {
-    const int c = threadIdx.x;
-    const int chain = pair_base + c;
-    float prob = 0.f;
-    int acc = 0;
-    if (chain < C) {
-      const float xg = red_pair[c] + peer_in[c];
-      const float pp = red_pair[64 + c] + peer_in[64 + c];
-      const float lp0 = a.lp[chain];
-      const float lp1 = 0.5f * xg;
-      float la = (-lp0 + fa.kin0[chain]) - (-lp1 + 0.5f * pp);
-      if (!isfinite(la)) la = -INFINITY;
-      const uint32_t gchain = static_cast<uint32_t>(chain) + a.chain_offset;
-      acc = accept_log_uniform(a.seed, gchain, a.t) < la;
-      prob = accept_prob(la);
-      if (ok) {
-        if (acc) a.lp[chain] = lp1;
-        a.is_accepted[chain] = static_cast<uint8_t>(acc);
-        a.log_accept[chain] = la;
-        if (a.trace_acc) a.trace_acc[chain] = static_cast<uint8_t>(acc);
-      }
-    }
-    acc_flag[c] = acc;
-    ptx::st_cluster_s32(ptx::mapa(ptx::smem_u32(&acc_flag[c]), 1), acc);
-    prob_s[c] = prob;
-    if (blockIdx.x == 0 && c == 0 && a.trace_eps && ok) a.trace_eps[0] = eps;
-  }
-  ptx::cluster_sync();      // decisions visible in both CTAs
-  if (warp >= 2) {
-#pragma unroll
-    for (int cb = 0; cb < kHalf / 16; ++cb) {
-      float accv[16];
-      ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + h * kHalf + cb * 16, accv);
-      if (ok && dvalid) {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const int i = cb * 16 + k;
-          const int chain = pair_base + h * kHalf + i;
-          if (chain >= C) continue;
-          const int64_t e = static_cast<int64_t>(chain) * D + d;
-          if (acc_flag[h * kHalf + i]) {
-            a.x[e] = x[i];
-            a.g[e] = -accv[k];
-            if (a.sample_out) a.sample_out[e] = x[i];
-          } else if (a.sample_out) {
-            a.sample_out[e] = a.x[e];
+          if (ok && i < nvalid) {
+            if (acc_flag[h * kHalf + i]) {
+              xrow[i * 128] = x[i];
+              grow[i * 128] = -accv[k];
+            }
+            if (samp) samp[static_cast<int64_t>(pair_base + h * kHalf + i) * D + d] = xrow[i * 128];
           }
         }
       }
+      // dual averaging over all chains of the posterior
+      if (persistent) {
+        // every CTA publishes a partial (the pair's sum in the leader, zero
+        // in the peer), meets the grid barrier once (thread 64), and warp 2
+        // sums the partials in the order of the one-transition reduction,
+        // so both launch shapes take the same step sizes
+        double* part = a.partials + (j & 1) * static_cast<int>(gridDim.x);
+        if (threadIdx.x == 64) {
+          double sum = 0.0;
+          if (rank == 0)
+            for (int q = 0; q < kPairChains; ++q) sum += static_cast<double>(prob_s[q]);
+          part[blockIdx.x] = sum;
+          if (!grid_barrier(fa.grid_bar, static_cast<unsigned>(j + 1))) {
+            atomicCAS(fa.err, 0, 7);
+            *abort_s = 1;
+          }
+        }
+        if (warp == 2) {
+          __syncwarp();
+          __threadfence();
+          const bool go = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(abort_s), 0) == 0;
+          if (go) {
+            double acc = 0.0;
+            for (int b = lane; b < static_cast<int>(gridDim.x); b += 32)
+              acc += reinterpret_cast<volatile double*>(part)[b];
+            acc = warp_sum_d(acc);
+            if (lane == 0) da_update(da_s, acc / static_cast<double>(C), t_full);
+          }
+          if (lane == 0 && *reinterpret_cast<volatile int*>(fa.err) != 0) *abort_s = 1;
+        }
+        epi_barrier();
+        if (*reinterpret_cast<volatile int*>(abort_s)) break;
+      }
     }
+    // the chains' final state back to global memory
+#pragma unroll 4
+    for (int i = 0; i < kHalf; ++i) {
+      if (ok && i < nvalid) {
+        const int64_t e = static_cast<int64_t>(pair_base + h * kHalf + i) * D + d;
+        a.x[e] = xrow[i * 128];
+        a.g[e] = grow[i * 128];
+      }
+    }
+    if (persistent && blockIdx.x == 0 && threadIdx.x == 64 && !*abort_s) *a.da = *da_s;
   }
+  // every copy into this CTA's tile has landed (immediate unless a wait gave up)
+  if (warp == 1 && lane == 0) ptx::mbar_wait(in_full, (T * L - 1) & 1);
   ptx::tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -508,10 +628,13 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     ptx::tmem_dealloc_pair(tmem, kTmemCols);
   }
   ptx::cluster_sync();
-  double sum = 0.0;
-  if (threadIdx.x == 0 && rank == 0)
-    for (int c = 0; c < kPairChains; ++c) sum += static_cast<double>(prob_s[c]);
-  block_partial_then_da(a.da, a.partials, sum, C, a.t_full);
+  if (!persistent) {
+    // one transition: the last CTA to finish applies the dual-averaging update
+    double sum = 0.0;
+    if (threadIdx.x == 0 && rank == 0)
+      for (int c = 0; c < kPairChains; ++c) sum += static_cast<double>(prob_s[c]);
+    block_partial_then_da(a.da, a.partials, sum, C, a.t_full);
+  }
 }
 
 }  // namespace
@@ -533,29 +656,72 @@ cudaError_t gauss_pair_setup() {
                               static_cast<int>(kSmem));
 }
 
-cudaError_t launch_gauss_pair_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
-                                         KernelTimer* timer) {
-  cudaError_t em = launch_gauss_momentum(a, tc, s);     // p0 and |p0|^2 / 2 of transition t
-  if (em != cudaSuccess) return em;
-  PairArgs fa{a, tc.err, tc.p, tc.h0, tc.Ptm};
+// Whether all CTA pairs of a launch for C chains can be resident at once
+// (the condition for a cooperative launch of several transitions).
+bool gauss_pair_persistent_ok(int64_t C) {
+  static int max_clusters = -1;
+  if (max_clusters < 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (gauss_pair_setup() != cudaSuccess ||
+        cudaOccupancyMaxActiveClusters(&n, k_gauss_pair, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    max_clusters = n;
+  }
+  return static_cast<int64_t>(gauss_pair_grid(C) / 2) <= max_clusters;
+}
+
+// T transitions starting at a.t / a.t_full.  T > 1 needs grid_bar (zeroed
+// here) and a cooperative launch; partials needs 2 x pairs doubles.
+cudaError_t launch_gauss_pair_transitions(const StepArgs& a, GaussTc& tc, int T, long long keep_from,
+                                          float* samples, float* trace_eps, uint8_t* trace_acc,
+                                          unsigned* grid_bar, cudaStream_t s, KernelTimer* timer) {
+  PairArgs fa{a, tc.err, tc.Ptm, tc.p, T, keep_from, samples, trace_eps, trace_acc,
+              T > 1 ? grid_bar : nullptr};
+  if (T > 1) {
+    cudaError_t e = cudaMemsetAsync(grid_bar, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(gauss_pair_grid(a.C));
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = kSmem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = T > 1 ? 2 : 1;
   if (timer) timer->begin(s);
   cudaError_t e = cudaLaunchKernelEx(&cfg, k_gauss_pair, tc.mPhi128, tc.mPlo128, fa);
   if (timer) timer->end(s);
   count_launch();
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+cudaError_t launch_gauss_pair_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
+                                         KernelTimer* timer) {
+  // one transition: its outputs, if any, are output 0
+  const bool keep = a.sample_out || a.trace_eps || a.trace_acc;
+  return launch_gauss_pair_transitions(a, tc, 1, keep ? a.t_full : a.t_full + 1, a.sample_out,
+                                       a.trace_eps, a.trace_acc, nullptr, s, timer);
 }
 
 }  // namespace hmc

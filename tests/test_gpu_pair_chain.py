@@ -1,0 +1,55 @@
+"""The dense-Gaussian pair kernel runs a whole sample_chain in one
+(cooperative) launch -- P resident across transitions, momenta drawn in the
+kernel, dual averaging over a grid barrier (Section 2.1's transition under
+Section 4.2's driver).  Its arithmetic is the one-transition launch's, so a
+chain through hmc_sample_chain must equal, bit for bit, the same transitions
+taken one hmc_step at a time; the per-transition parity with the float64
+oracle is covered by test_gpu_tensor_core.py."""
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2002_01184_gb300 import build
+    build.build()
+    from paper_2002_01184_gb300 import hmc
+    return hmc
+
+
+# (chains, dim, leapfrog steps, burn-in, kept): ragged chains and dims, the
+# full workload size
+@pytest.mark.parametrize("C,D,L,B,K", [(256, 256, 8, 6, 5), (200, 100, 5, 4, 3), (4096, 256, 16, 3, 2)])
+def test_one_launch_chain_equals_single_transitions(H, C, D, L, B, K):
+    from paper_2002_01184_gb300 import workloads
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = workloads.corr_gauss(dim=D, num_chains=C, num_burnin=B, num_results=K, num_leapfrog=L)
+    x0 = torch.as_tensor(p.x0).cuda().contiguous()
+    one = Sampler(p, adapt=True)
+    x1 = x0.clone()
+    samples, eps, acc = one.sample_chain(x1, B, K)
+    name, per = H.hmc_dominant_kernel_info(one.ctx)
+    assert name == "k_gauss_pair"
+    assert per == C * L * (B + K)            # every transition in one launch
+    each = Sampler(p, adapt=True)
+    x2 = x0.clone()
+    each.bootstrap(x2)
+    for t in range(B + K):
+        r = each.results(each.step(x2, t))
+        if t >= B:
+            k = t - B
+            torch.cuda.synchronize()
+            assert torch.equal(samples[k], x2), f"sample {k}"
+            assert torch.equal(acc[k], r["is_accepted"]), f"accept {k}"
+    H.hmc_synchronize(one.ctx)
+    H.hmc_synchronize(each.ctx)
+    assert torch.equal(x1, x2)
+    assert one.adaptation() == each.adaptation()
+    assert 0.0 < float(acc.float().mean()) <= 1.0
+    one.close()
+    each.close()
