@@ -67,8 +67,8 @@ constexpr uint32_t kStageHalf = 4 * kBChunk;      // 4 K-chunks (this CTA's 128 
 constexpr uint32_t kStageBytes = 2 * kStageHalf;  // head + remainder
 constexpr uint32_t kStateBytes = kPairChains * 128 * 4;   // one of position / gradient
 // barriers (8), tmem slot, red [3][4][64], red_pair [3][64], peer_in [3][64],
-// acc_flag [64], prob_s [64], DA state copy, flags
-constexpr uint32_t kSmall = 8 * 8 + 16 + (3 * 4 * 64 + 3 * 64 + 3 * 64 + 64 + 64) * 4 + 128 + 16;
+// acc_flag [64], prob_s [64], DA state copy, flags, DA coefficients, pair sum
+constexpr uint32_t kSmall = 8 * 8 + 16 + (3 * 4 * 64 + 3 * 64 + 3 * 64 + 64 + 64) * 4 + 128 + 16 + 32 + 16;
 constexpr size_t kSmemUsed =
     2 * kBBytes + 2 * kAHalf + kStageBytes + 2 * kStateBytes + kSmall + 1024;
 // Above half of an SM's shared memory, so that one CTA runs per SM: a CTA
@@ -185,6 +185,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   float* prob_s = reinterpret_cast<float*>(acc_flag + 64);    // [64]
   DAState* da_s = reinterpret_cast<DAState*>(prob_s + 64);    // this CTA's copy (T > 1)
   int* abort_s = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(da_s) + 128);
+  DACoef* coef_s = reinterpret_cast<DACoef*>(reinterpret_cast<uint8_t*>(da_s) + 144);
+  double* psum_s = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(da_s) + 176);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = ptx::cluster_rank();              // 0: leader, 1: peer
@@ -576,36 +578,44 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       }
       // dual averaging over all chains of the posterior
       if (persistent) {
-        // every CTA publishes a partial (the pair's sum in the leader, zero
-        // in the peer), meets the grid barrier once (thread 64), and warp 2
-        // sums the partials in the order of the one-transition reduction,
-        // so both launch shapes take the same step sizes
+        // Every CTA publishes a partial (the pair's sum in the leader, zero
+        // in the peer) and meets the grid barrier once (warp 2, lane 0)
+        // while warp 3 forms the update's coefficients; then warp 2 sums
+        // the partials in the order of the one-transition reduction, so
+        // both launch shapes take the same step sizes.
         double* part = a.partials + (j & 1) * static_cast<int>(gridDim.x);
-        if (threadIdx.x == 64) {
-          double sum = 0.0;
-          if (rank == 0)
-            for (int q = 0; q < kPairChains; ++q) sum += static_cast<double>(prob_s[q]);
-          part[blockIdx.x] = sum;
-          if (!grid_barrier(fa.grid_bar, static_cast<unsigned>(j + 1))) {
-            atomicCAS(fa.err, 0, 7);
-            *abort_s = 1;
-          }
-        }
         if (warp == 2) {
-          __syncwarp();
-          __threadfence();
-          const bool go = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(abort_s), 0) == 0;
-          if (go) {
-            double acc = 0.0;
-            for (int b = lane; b < static_cast<int>(gridDim.x); b += 32)
-              acc += reinterpret_cast<volatile double*>(part)[b];
-            acc = warp_sum_d(acc);
-            if (lane == 0) da_update(da_s, acc / static_cast<double>(C), t_full);
+          double v = rank == 0 ? static_cast<double>(prob_s[lane]) + static_cast<double>(prob_s[lane + 32]) : 0.0;
+          v = warp_sum_d(v);
+          if (lane == 0) {
+            part[blockIdx.x] = v;
+            if (!grid_barrier(fa.grid_bar, static_cast<unsigned>(j + 1))) {
+              atomicCAS(fa.err, 0, 7);
+              *abort_s = 1;
+            }
           }
-          if (lane == 0 && *reinterpret_cast<volatile int*>(fa.err) != 0) *abort_s = 1;
+        } else if (warp == 3 && lane == 0) {
+          *coef_s = da_prepare(da_s, t_full);
+        }
+        epi_barrier();
+        if (warp == 2 && *reinterpret_cast<volatile int*>(abort_s) == 0) {
+          __threadfence();
+          double acc = 0.0;
+          for (int b = lane; b < static_cast<int>(gridDim.x); b += 32)
+            acc += reinterpret_cast<volatile double*>(part)[b];
+          acc = warp_sum_d(acc);
+          if (lane == 0) {
+            da_apply(da_s, *coef_s, acc / static_cast<double>(C), t_full);
+            if (*reinterpret_cast<volatile int*>(fa.err) != 0) *abort_s = 1;
+          }
         }
         epi_barrier();
         if (*reinterpret_cast<volatile int*>(abort_s)) break;
+      } else if (warp == 2) {
+        // one transition: the pair's sum for the last-CTA update below
+        double v = rank == 0 ? static_cast<double>(prob_s[lane]) + static_cast<double>(prob_s[lane + 32]) : 0.0;
+        v = warp_sum_d(v);
+        if (lane == 0) *psum_s = v;
       }
     }
     // the chains' final state back to global memory
@@ -630,10 +640,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   ptx::cluster_sync();
   if (!persistent) {
     // one transition: the last CTA to finish applies the dual-averaging update
-    double sum = 0.0;
-    if (threadIdx.x == 0 && rank == 0)
-      for (int c = 0; c < kPairChains; ++c) sum += static_cast<double>(prob_s[c]);
-    block_partial_then_da(a.da, a.partials, sum, C, a.t_full);
+    block_partial_then_da(a.da, a.partials, threadIdx.x == 0 ? *psum_s : 0.0, C, a.t_full);
   }
 }
 

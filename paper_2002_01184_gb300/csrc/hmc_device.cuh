@@ -127,20 +127,45 @@ constexpr double kDAGamma = 0.05;
 constexpr double kDAT0 = 10.0;
 constexpr double kDAKappa = 0.75;
 
+// The coefficients of adaptation step m depend on m alone, so a kernel can
+// form them before the acceptance statistic exists: w = 1 / (m + t0),
+// sqrt(m) / gamma and eta = m^-kappa (kappa = 3/4: m^-1/2 m^-1/4).  Float64
+// is slow on this part, so the kernels keep these off the critical path.
+struct DACoef {
+  double w, sq, eta;
+  int active;      // 0: transition t does not adapt
+};
+static_assert(kDAKappa == 0.75, "eta below is m^-3/4");
+
+__device__ __forceinline__ DACoef da_prepare(const DAState* s, long long t) {
+  DACoef c{0.0, 0.0, 0.0, 0};
+  if (!s->adapt || t >= s->num_adapt) return c;
+  const double m = static_cast<double>(s->m + 1);
+  const double r = sqrt(m);
+  c.w = 1.0 / (m + kDAT0);
+  c.sq = r / kDAGamma;
+  c.eta = 1.0 / (r * sqrt(r));
+  c.active = 1;
+  return c;
+}
+
 // Apply one adaptation step with statistic `alpha` after transition t.
-__device__ __forceinline__ void da_update(DAState* s, double alpha, long long t) {
+__device__ __forceinline__ void da_apply(DAState* s, const DACoef& c, double alpha, long long t) {
   s->last_stat = alpha;
-  if (!s->adapt || t >= s->num_adapt) return;
+  if (!c.active) return;
   s->m += 1;
-  const double m = static_cast<double>(s->m);
-  const double w = 1.0 / (m + kDAT0);
-  s->h_bar = (1.0 - w) * s->h_bar + w * (s->delta - alpha);
-  s->log_eps = s->mu - sqrt(m) / kDAGamma * s->h_bar;
-  const double eta = pow(m, -kDAKappa);
-  s->log_eps_bar = eta * s->log_eps + (1.0 - eta) * s->log_eps_bar;
+  // explicit roundings: no multiply-add contraction, so every kernel that
+  // inlines this takes the same steps (and float64 evaluates as written)
+  s->h_bar = __dadd_rn(__dmul_rn(1.0 - c.w, s->h_bar), __dmul_rn(c.w, __dsub_rn(s->delta, alpha)));
+  s->log_eps = __dsub_rn(s->mu, __dmul_rn(c.sq, s->h_bar));
+  s->log_eps_bar = __dadd_rn(__dmul_rn(c.eta, s->log_eps), __dmul_rn(1.0 - c.eta, s->log_eps_bar));
   // after the last adaptation step the step size freezes at eps_bar
   const double next = (t + 1 >= s->num_adapt) ? s->log_eps_bar : s->log_eps;
   s->eps = static_cast<float>(exp(next));
+}
+
+__device__ __forceinline__ void da_update(DAState* s, double alpha, long long t) {
+  da_apply(s, da_prepare(s, t), alpha, t);
 }
 
 // Deterministic reduction of per-tile partial sums followed by the
