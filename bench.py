@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--workload", default="corr_gauss",
                     choices=["corr_gauss", "logreg", "funnel", "std_normal", "uneven_batch", "serve"])
     ap.add_argument("--plain", action="store_true", help="one launch per op per leapfrog step")
+    ap.add_argument("--max-transitions-per-launch", type=int, default=0,
+                    help="dense Gaussian: cap on transitions per kernel launch (0: whole chain; "
+                         "1 for profilers that cannot replay cooperative cluster launches)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -353,7 +356,7 @@ def main():
     p.seed = p.seed + 1000 * rank          # each rank samples its own replica
     impl = hmc.HMC_IMPL_PLAIN if args.plain else hmc.HMC_IMPL_FUSED
     stream = torch.cuda.current_stream()
-    s = Sampler(p, impl=impl, stream=stream)
+    s = Sampler(p, impl=impl, stream=stream, max_transitions_per_launch=args.max_transitions_per_launch)
     C, D, K, B = p.num_chains, p.dim, p.num_results, p.num_burnin
     x0 = torch.as_tensor(p.x0).cuda()
     x = torch.empty_like(x0)
@@ -475,7 +478,8 @@ def main():
             "config": {"workload": wl, "impl": "plain" if args.plain else "fused",
                        "chains": C, "dim": D, "l2": "each step writes its 8.4 GB kept-sample "
                        "buffer (> 129 MB L2), which flushes L2 between steps",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "transitions_per_launch": args.max_transitions_per_launch or "all"},
             "min_ess_per_s": min_ess_per_s, "min_ess": min_ess,
             "final_step_size": float(eps[-1].item()) if K else None,
             "accept_rate": float(acc.float().mean().item()) if K else None,

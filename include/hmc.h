@@ -98,6 +98,13 @@ typedef struct {
                                transitions as one CUDA graph on first use and
                                replays it while its pointer and count
                                arguments stay the same; 0: plain launches */
+  int32_t max_transitions_per_launch;
+                            /* dense Gaussian on CTA pairs: hmc_sample_chain
+                               runs at most this many transitions per kernel
+                               launch (>= 0; 0: no limit, the whole chain in
+                               one cooperative launch; 1: one launch per
+                               transition, e.g. for a profiler that cannot
+                               replay cooperative cluster launches) */
 } hmc_config;
 
 /* Kernel results of the last transition.  All pointers are device pointers

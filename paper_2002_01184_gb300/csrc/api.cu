@@ -126,6 +126,7 @@ bool valid_config(const hmc_config* c, int64_t C, std::string* why) {
     return false;
   }
   if (c->use_graph != 0 && c->use_graph != 1) { *why = "use_graph must be 0 or 1"; return false; }
+  if (c->max_transitions_per_launch < 0) { *why = "max_transitions_per_launch must be >= 0"; return false; }
   if (c->chain_offset < 0 || c->chain_offset + C > (1ll << 32)) {
     *why = "chain_offset + num_chains must fit in 32 bits";
     return false;
@@ -237,16 +238,24 @@ hmc_status enqueue_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sa
   hmc_status st = bootstrap(ctx, x);
   if (st != HMC_OK) return st;
   const int64_t CD = ctx->C * ctx->target.dim;
-  // dense Gaussian on CTA pairs: every transition of the chain in one launch
+  // dense Gaussian on CTA pairs: the chain's transitions in as few launches
+  // as allowed (all of them in one cooperative launch by default)
   ctx->dom_transitions = 1;
-  if (ctx->use_tc && ctx->tc.pair && ctx->K == 1 && !ctx->s_mean && B + K > 1 &&
-      B + K <= (1ll << 30) && hmc::gauss_pair_persistent_ok(ctx->C)) {
-    StepArgs a = make_args(ctx, x, 0);
-    cudaError_t e = hmc::launch_gauss_pair_transitions(a, ctx->tc, static_cast<int>(B + K), B, samples,
-                                                       trace_eps, trace_acc, ctx->grid_bar,
-                                                       ctx->stream, &ctx->timer);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "multi-transition launch");
-    ctx->dom_transitions = B + K;
+  const int64_t T = B + K;
+  const int64_t cap = ctx->cfg.max_transitions_per_launch > 0
+                          ? std::min<int64_t>(ctx->cfg.max_transitions_per_launch, 1ll << 30)
+                          : (1ll << 30);
+  const int64_t chunk = std::min(T, cap);
+  if (ctx->use_tc && ctx->tc.pair && ctx->K == 1 && !ctx->s_mean && T > 0 &&
+      (chunk == 1 || hmc::gauss_pair_persistent_ok(ctx->C))) {
+    for (int64_t t0 = 0; t0 < T; t0 += chunk) {
+      const int n = static_cast<int>(std::min(chunk, T - t0));
+      StepArgs a = make_args(ctx, x, static_cast<uint64_t>(t0));
+      cudaError_t e = hmc::launch_gauss_pair_transitions(a, ctx->tc, n, B, samples, trace_eps, trace_acc,
+                                                         ctx->grid_bar, ctx->stream, &ctx->timer);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "pair transition launch");
+    }
+    ctx->dom_transitions = chunk;
     return HMC_OK;
   }
   for (int64_t t = 0; t < B + K; ++t) {

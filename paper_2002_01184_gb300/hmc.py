@@ -30,7 +30,7 @@ class hmc_config(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("adapt", ctypes.c_int32),
                 ("target_accept", ctypes.c_float), ("num_adapt_steps", ctypes.c_int64),
                 ("impl", ctypes.c_int32), ("chain_offset", ctypes.c_int64),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("max_transitions_per_launch", ctypes.c_int32)]
 
 
 class hmc_kernel_results(ctypes.Structure):
@@ -153,10 +153,11 @@ def make_target(kind, dim, P=None, X=None, y=None):
 
 
 def make_config(num_leapfrog, step_size, seed=0, adapt=False, target_accept=0.65,
-                num_adapt_steps=0, impl=HMC_IMPL_FUSED, chain_offset=0, use_graph=True):
+                num_adapt_steps=0, impl=HMC_IMPL_FUSED, chain_offset=0, use_graph=True,
+                max_transitions_per_launch=0):
     return hmc_config(int(num_leapfrog), float(step_size), int(seed) & 0xFFFFFFFFFFFFFFFF,
                       int(bool(adapt)), float(target_accept), int(num_adapt_steps), int(impl),
-                      int(chain_offset), int(bool(use_graph)))
+                      int(chain_offset), int(bool(use_graph)), int(max_transitions_per_launch))
 
 
 def hmc_create(target, num_chains, config, stream=None):

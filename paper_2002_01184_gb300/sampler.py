@@ -9,7 +9,8 @@ class Sampler:
     """One posterior (a ``workloads.Problem``) bound to a libhmc context."""
 
     def __init__(self, problem, impl=hmc.HMC_IMPL_FUSED, num_chains=None, chain_offset=0,
-                 step_size=None, adapt=None, stream=None, device="cuda", use_graph=True):
+                 step_size=None, adapt=None, stream=None, device="cuda", use_graph=True,
+                 max_transitions_per_launch=0):
         self.problem = problem
         self.C = int(num_chains or problem.num_chains)
         self.D = int(problem.dim)
@@ -21,7 +22,8 @@ class Sampler:
         self.config = hmc.make_config(
             problem.num_leapfrog, problem.step_size if step_size is None else step_size,
             problem.seed, adapt, problem.target_accept,
-            problem.num_burnin if adapt else 0, impl, chain_offset, use_graph)
+            problem.num_burnin if adapt else 0, impl, chain_offset, use_graph,
+            max_transitions_per_launch)
         self.stream = stream
         self.ctx = hmc.hmc_create(self.target, self.C, self.config, stream)
 

@@ -53,3 +53,25 @@ def test_one_launch_chain_equals_single_transitions(H, C, D, L, B, K):
     assert 0.0 < float(acc.float().mean()) <= 1.0
     one.close()
     each.close()
+
+
+@pytest.mark.parametrize("cap", [1, 3])
+def test_launch_cap_splits_the_chain_without_changing_it(H, cap):
+    from paper_2002_01184_gb300 import workloads
+    from paper_2002_01184_gb300.sampler import Sampler
+    C, D, L, B, K = 192, 128, 6, 4, 4
+    p = workloads.corr_gauss(dim=D, num_chains=C, num_burnin=B, num_results=K, num_leapfrog=L)
+    x0 = torch.as_tensor(p.x0).cuda().contiguous()
+    whole = Sampler(p, adapt=True)
+    x1 = x0.clone()
+    s1, e1, a1 = whole.sample_chain(x1, B, K)
+    split = Sampler(p, adapt=True, max_transitions_per_launch=cap)
+    x2 = x0.clone()
+    s2, e2, a2 = split.sample_chain(x2, B, K)
+    assert H.hmc_dominant_kernel_info(split.ctx)[1] == C * L * cap
+    H.hmc_synchronize(whole.ctx)
+    H.hmc_synchronize(split.ctx)
+    assert torch.equal(x1, x2) and torch.equal(s1, s2) and torch.equal(e1, e2) and torch.equal(a1, a2)
+    assert whole.adaptation() == split.adaptation()
+    whole.close()
+    split.close()
