@@ -5,6 +5,10 @@
 //   R = y - sigmoid(Z)     (epilogue, straight back into tensor memory)
 //   G += R X               (M = 128 chains, N = D, K = 128 data rows; A = R
 //                           read from tensor memory, B = the transposed data)
+// Z is double-buffered in tensor memory and R's head is written over the Z it
+// came from, so the tensor pipe computes Z of the next tile while the
+// epilogue turns this tile's Z into R; R's remainder has one buffer, which
+// the epilogue refills once the previous tile's G products are done.
 // One CTA per (128-chain group, range of data rows); the data tiles stream by
 // TMA through a ring of stages and every tile serves all 128 chains; Z and R
 // never reach HBM.  Per-range partial gradients and log-likelihoods are
@@ -34,9 +38,11 @@ constexpr uint32_t kTile = 128 * 128;       // 128 x 32 floats
 constexpr uint32_t kStage = 2 * kTile;      // head + remainder
 constexpr int kStages = 3;
 constexpr uint32_t kThetaBytes = 2 * 4 * kTile;   // 4 K-chunks, head + remainder
-constexpr uint32_t kColZ = 0, kColRhi = 128, kColRlo = 256, kColG = 384;
+// Z / R head of even tiles at 0, of odd tiles at 128; R remainder; G
+constexpr uint32_t kColZR = 0, kColRlo = 256, kColG = 384;
 constexpr uint32_t kTmemCols = 512;
 constexpr size_t kSmem = kThetaBytes + kStages * kStage + 1024 + 256 + 2 * 128 * 4;
+static_assert(8 * (2 * kStages + 5) + 16 <= 256, "barriers");
 
 struct LrTcArgs {
   int C, D, N, ntiles, tiles_per_split, nsplit, dpad;
@@ -74,9 +80,10 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
   uint64_t* full = reinterpret_cast<uint64_t*>(St + kStages * kStage);
   uint64_t* empty = full + kStages;
   uint64_t* th_full = empty + kStages;
-  uint64_t* z_full = th_full + 1;
-  uint64_t* r_ready = z_full + 1;
-  uint64_t* g_full = r_ready + 1;
+  uint64_t* z_full = th_full + 1;         // [2]: Z of the tile in buffer b is complete
+  uint64_t* r_ready = z_full + 2;
+  uint64_t* g_done = r_ready + 1;         // G of a tile is complete (R remainder free)
+  uint64_t* g_full = g_done + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(g_full + 1);
   float* lpred = reinterpret_cast<float*>(tmem_slot + 4);   // [2][128]
 
@@ -94,8 +101,10 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
       ptx::mbar_init(&empty[s], 1);
     }
     ptx::mbar_init(th_full, 1);
-    ptx::mbar_init(z_full, 1);
+    ptx::mbar_init(&z_full[0], 1);
+    ptx::mbar_init(&z_full[1], 1);
     ptx::mbar_init(r_ready, 256);
+    ptx::mbar_init(g_done, 1);
     ptx::mbar_init(g_full, 1);
     ptx::fence_mbar_init();
   }
@@ -118,27 +127,34 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
         ptx::tma_load_2d(Th + (2 * kc) * kTile, &mThi, th_full, kc * 32, m0);
         ptx::tma_load_2d(Th + (2 * kc + 1) * kTile, &mTlo, th_full, kc * 32, m0);
       }
+      // stages in the order the issuer consumes them: Z(0), then per tile
+      // ti: Z(ti + 1), G(ti)
       int it = 0;
-      for (int t = t_begin; t < t_end && ok; ++t) {
-        const int row0 = t * kRowsPerTile;
-        for (int part = 0; part < nk + 4 && ok; ++part, ++it) {
-          const int s = it % kStages, round = it / kStages;
-          if (it >= kStages && !ptx::mbar_wait(&empty[s], (round - 1) & 1)) {
-            atomicCAS(a.err, 0, 11);
-            ok = false;
-            break;
-          }
-          uint8_t* st = St + s * kStage;
-          ptx::mbar_arrive_expect_tx(&full[s], kStage);
-          if (part < nk) {
-            ptx::tma_load_2d(st, &mXhi, &full[s], part * 32, row0);
-            ptx::tma_load_2d(st + kTile, &mXlo, &full[s], part * 32, row0);
-          } else {
-            const int kr = part - nk;
-            ptx::tma_load_2d(st, &mXThi, &full[s], row0 + kr * 32, 0);
-            ptx::tma_load_2d(st + kTile, &mXTlo, &full[s], row0 + kr * 32, 0);
-          }
+      auto stage = [&](const CUtensorMap* mh, const CUtensorMap* ml, int c0, int c1) {
+        const int s = it % kStages, round = it / kStages;
+        ++it;
+        if (it > kStages && !ptx::mbar_wait(&empty[s], (round - 1) & 1)) {
+          atomicCAS(a.err, 0, 11);
+          ok = false;
+          return;
         }
+        uint8_t* st = St + s * kStage;
+        ptx::mbar_arrive_expect_tx(&full[s], kStage);
+        ptx::tma_load_2d(st, mh, &full[s], c0, c1);
+        ptx::tma_load_2d(st + kTile, ml, &full[s], c0, c1);
+      };
+      auto load_z = [&](int ti) {
+        const int row0 = (t_begin + ti) * kRowsPerTile;
+        for (int part = 0; part < nk && ok; ++part) stage(&mXhi, &mXlo, part * 32, row0);
+      };
+      auto load_g = [&](int ti) {
+        const int row0 = (t_begin + ti) * kRowsPerTile;
+        for (int kr = 0; kr < 4 && ok; ++kr) stage(&mXThi, &mXTlo, row0 + kr * 32, 0);
+      };
+      load_z(0);
+      for (int ti = 0; ti < ntile && ok; ++ti) {
+        if (ti + 1 < ntile) load_z(ti + 1);
+        load_g(ti);
       }
     }
   } else if (warp == 1) {
@@ -152,8 +168,9 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
       }
       ptx::tc_fence_after();
       int it = 0;
-      for (int ti = 0; ti < ntile && ok; ++ti) {
-        // Z = Theta X^T
+      // Z = Theta X^T into buffer ti % 2
+      auto mma_z = [&](int ti) {
+        const uint32_t zcol = tmem + kColZR + 128u * static_cast<uint32_t>(ti & 1);
         for (int kc = 0; kc < nk && ok; ++kc, ++it) {
           const int s = it % kStages;
           if (!ptx::mbar_wait(&full[s], (it / kStages) & 1)) {
@@ -172,21 +189,23 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
             const uint64_t dtl = ptx::sw128_kmajor_desc(tlo + 32 * j);
             const uint64_t dxh = ptx::sw128_kmajor_desc(xhi + 32 * j);
             const uint64_t dxl = ptx::sw128_kmajor_desc(xlo + 32 * j);
-            ptx::mma_tf32(tmem + kColZ, dtl, dxh, idesc1, (kc | j) != 0 ? 1u : 0u);
-            ptx::mma_tf32(tmem + kColZ, dth, dxl, idesc1, 1u);
-            ptx::mma_tf32(tmem + kColZ, dth, dxh, idesc1, 1u);
+            ptx::mma_tf32(zcol, dtl, dxh, idesc1, (kc | j) != 0 ? 1u : 0u);
+            ptx::mma_tf32(zcol, dth, dxl, idesc1, 1u);
+            ptx::mma_tf32(zcol, dth, dxh, idesc1, 1u);
           }
           ptx::mma_commit(&empty[s]);
         }
-        if (!ok) break;
-        ptx::mma_commit(z_full);
+        if (ok) ptx::mma_commit(&z_full[ti & 1]);
+      };
+      // G += R X   (A = R from tensor memory, K = the tile's 128 rows)
+      auto mma_g = [&](int ti) {
         if (!ptx::mbar_wait(r_ready, ti & 1)) {
           atomicCAS(a.err, 0, 14);
           ok = false;
-          break;
+          return;
         }
         ptx::tc_fence_after();
-        // G += R X   (A = R from tensor memory, K = the tile's 128 rows)
+        const uint32_t rhi = tmem + kColZR + 128u * static_cast<uint32_t>(ti & 1);
         for (int kr = 0; kr < 4 && ok; ++kr, ++it) {
           const int s = it % kStages;
           if (!ptx::mbar_wait(&full[s], (it / kStages) & 1)) {
@@ -204,11 +223,19 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
             const uint32_t k = static_cast<uint32_t>(kr * 32 + 8 * j);
             ptx::mma_tf32_tmem_a(tmem + kColG, tmem + kColRlo + k, dbh, idesc2,
                                  (ti | kr | j) != 0 ? 1u : 0u);
-            ptx::mma_tf32_tmem_a(tmem + kColG, tmem + kColRhi + k, dbl, idesc2, 1u);
-            ptx::mma_tf32_tmem_a(tmem + kColG, tmem + kColRhi + k, dbh, idesc2, 1u);
+            ptx::mma_tf32_tmem_a(tmem + kColG, rhi + k, dbl, idesc2, 1u);
+            ptx::mma_tf32_tmem_a(tmem + kColG, rhi + k, dbh, idesc2, 1u);
           }
           ptx::mma_commit(&empty[s]);
         }
+        if (ok) ptx::mma_commit(g_done);
+      };
+      // MMAs execute in issue order: Z(ti + 1) overwrites the buffer G(ti - 1)
+      // read only after G(ti - 1)
+      mma_z(0);
+      for (int ti = 0; ti < ntile && ok; ++ti) {
+        if (ti + 1 < ntile) mma_z(ti + 1);
+        mma_g(ti);
       }
       ptx::mma_commit(g_full);
     }
@@ -223,7 +250,8 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
     const bool need_lp = a.need_lp != 0;
     for (int ti = 0; ti < ntile; ++ti) {
       const int row0 = (t_begin + ti) * kRowsPerTile;
-      if (!ptx::mbar_wait(z_full, ti & 1)) {
+      const uint32_t zr = tmem + lane_base + kColZR + 128u * static_cast<uint32_t>(ti & 1);
+      if (!ptx::mbar_wait(&z_full[ti & 1], (ti >> 1) & 1)) {
         atomicCAS(a.err, 0, 16);
         ok = false;
       }
@@ -232,7 +260,7 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
       for (int cb = 0; cb < 4; ++cb) {
         const uint32_t col = static_cast<uint32_t>(64 * half + 16 * cb);
         float zv[16], rh[16], rl[16];
-        ptx::tmem_ld16(tmem + lane_base + kColZ + col, zv);
+        ptx::tmem_ld16(zr + col, zv);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const int n = row0 + static_cast<int>(col) + k;
@@ -244,7 +272,15 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
           }
           split_tf32(res, rh[k], rl[k]);
         }
-        ptx::tmem_st16(tmem + lane_base + kColRhi + col, rh);
+        ptx::tmem_st16(zr + col, rh);               // R head over the Z it came from
+        if (cb == 0 && ti > 0) {
+          // R's remainder buffer is free once the previous tile's G is done
+          if (!ptx::mbar_wait(g_done, (ti - 1) & 1)) {
+            atomicCAS(a.err, 0, 18);
+            ok = false;
+          }
+          ptx::tc_fence_after();
+        }
         ptx::tmem_st16(tmem + lane_base + kColRlo + col, rl);
       }
       ptx::tmem_wait_st();
