@@ -33,7 +33,12 @@ namespace {
 constexpr int kM = 128;                     // chains per CTA
 constexpr int kRowsPerTile = 128;           // data rows per tile
 constexpr int kMaxD = 128;
-constexpr int kThreads = 320;               // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+// warp 0 TMA, warp 1 MMA, then kEpiGroups x 4 epilogue warps: a lane
+// quarter's warps split the tile's 128 columns into kEpiGroups groups
+constexpr int kEpiGroups = 4;
+constexpr int kEpiWarps = 4 * kEpiGroups;
+constexpr int kGroupCols = 128 / kEpiGroups;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTile = 128 * 128;       // 128 x 32 floats
 constexpr uint32_t kStage = 2 * kTile;      // head + remainder
 constexpr int kStages = 3;
@@ -41,7 +46,9 @@ constexpr uint32_t kThetaBytes = 2 * 4 * kTile;   // 4 K-chunks, head + remainde
 // Z / R head of even tiles at 0, of odd tiles at 128; R remainder; G
 constexpr uint32_t kColZR = 0, kColRlo = 256, kColG = 384;
 constexpr uint32_t kTmemCols = 512;
-constexpr size_t kSmem = kThetaBytes + kStages * kStage + 1024 + 256 + 2 * 128 * 4;
+constexpr size_t kSmem = kThetaBytes + kStages * kStage + 1024 + 256;
+static_assert(kSmem <= 227 * 1024, "shared memory");
+static_assert(kEpiGroups * 128 * 4 <= kStage, "log-likelihood partials reuse stage 0");
 static_assert(8 * (2 * kStages + 5) + 16 <= 256, "barriers");
 
 struct LrTcArgs {
@@ -85,7 +92,9 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
   uint64_t* g_done = r_ready + 1;         // G of a tile is complete (R remainder free)
   uint64_t* g_full = g_done + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(g_full + 1);
-  float* lpred = reinterpret_cast<float*>(tmem_slot + 4);   // [2][128]
+  // [kEpiGroups][128] log-likelihood partials: written after the last MMA,
+  // when the data stages are no longer read
+  float* lpred = reinterpret_cast<float*>(St);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kM;
@@ -103,7 +112,7 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
     ptx::mbar_init(th_full, 1);
     ptx::mbar_init(&z_full[0], 1);
     ptx::mbar_init(&z_full[1], 1);
-    ptx::mbar_init(r_ready, 256);
+    ptx::mbar_init(r_ready, 32 * kEpiWarps);
     ptx::mbar_init(g_done, 1);
     ptx::mbar_init(g_full, 1);
     ptx::fence_mbar_init();
@@ -240,10 +249,10 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
       ptx::mma_commit(g_full);
     }
   } else {
-    // ---- epilogue: thread = chain row (TMEM lane), half of the columns
+    // ---- epilogue: thread = chain row (TMEM lane), one group of columns
     const int ew = warp - 2;
     const int quarter = warp & 3;
-    const int half = ew >> 2;
+    const int group = ew >> 2;
     const int r = quarter * 32 + lane;
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
     float lp_acc = 0.f;
@@ -256,10 +265,13 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
         ok = false;
       }
       ptx::tc_fence_after();
+      // R's head goes over Z block by block; its remainder waits in
+      // registers until the previous tile's G products release the buffer
+      float rl[kGroupCols];
 #pragma unroll
-      for (int cb = 0; cb < 4; ++cb) {
-        const uint32_t col = static_cast<uint32_t>(64 * half + 16 * cb);
-        float zv[16], rh[16], rl[16];
+      for (int cb = 0; cb < kGroupCols / 16; ++cb) {
+        const uint32_t col = static_cast<uint32_t>(kGroupCols * group + 16 * cb);
+        float zv[16], rh[16];
         ptx::tmem_ld16(zr + col, zv);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
@@ -270,19 +282,20 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
             res = residual_f(yv, zv[k]);
             if (need_lp) lp_acc += loglik_f(yv, zv[k]);
           }
-          split_tf32(res, rh[k], rl[k]);
+          split_tf32(res, rh[k], rl[16 * cb + k]);
         }
-        ptx::tmem_st16(zr + col, rh);               // R head over the Z it came from
-        if (cb == 0 && ti > 0) {
-          // R's remainder buffer is free once the previous tile's G is done
-          if (!ptx::mbar_wait(g_done, (ti - 1) & 1)) {
-            atomicCAS(a.err, 0, 18);
-            ok = false;
-          }
-          ptx::tc_fence_after();
-        }
-        ptx::tmem_st16(tmem + lane_base + kColRlo + col, rl);
+        ptx::tmem_st16(zr + col, rh);
       }
+      if (ti > 0) {
+        if (!ptx::mbar_wait(g_done, (ti - 1) & 1)) {
+          atomicCAS(a.err, 0, 18);
+          ok = false;
+        }
+        ptx::tc_fence_after();
+      }
+#pragma unroll
+      for (int cb = 0; cb < kGroupCols / 16; ++cb)
+        ptx::tmem_st16(tmem + lane_base + kColRlo + kGroupCols * group + 16 * cb, rl + 16 * cb);
       ptx::tmem_wait_st();
       ptx::tc_fence_before();
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(r_ready)) : "memory");
@@ -298,8 +311,8 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
     }
     float* gout = a.Gpart + (static_cast<int64_t>(split) * a.C + chain) * a.D;
 #pragma unroll 1
-    for (int cb = 0; cb < 4; ++cb) {
-      const int d0 = 64 * half + 16 * cb;
+    for (int cb = 0; cb < kGroupCols / 16; ++cb) {
+      const int d0 = kGroupCols * group + 16 * cb;
       if (d0 >= a.dpad) break;                    // warp-uniform
       float gv[16];
       if (ntile > 0) {
@@ -313,15 +326,19 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
         for (int k = 0; k < 16; ++k)
           if (d0 + k < a.D) gout[d0 + k] = gv[k];
     }
-    lpred[half * 128 + r] = lp_acc;
+    lpred[group * 128 + r] = lp_acc;
   }
   ptx::tc_fence_before();
   __syncthreads();
   if (warp >= 2 && warp < 6) {
     const int r = (warp & 3) * 32 + lane;
     const int chain = m0 + r;
-    if (ok && chain < a.C)
-      a.lp_part[static_cast<int64_t>(split) * a.C + chain] = lpred[r] + lpred[128 + r];
+    if (ok && chain < a.C) {
+      float lp = 0.f;
+#pragma unroll
+      for (int g = 0; g < kEpiGroups; ++g) lp += lpred[g * 128 + r];
+      a.lp_part[static_cast<int64_t>(split) * a.C + chain] = lp;
+    }
   }
   if (warp == 0) {
     ptx::tc_fence_after();
