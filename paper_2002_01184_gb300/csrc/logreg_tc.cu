@@ -1,17 +1,23 @@
 // Bayesian logistic regression on the tcgen05 tensor cores: each leapfrog
 // gradient is two chain-batched products back to back (Section 2.1's batched
 // target evaluation of a "list of vectors"), 3xTF32 with float32 accumulation:
-//   Z = Theta X^T          (M = 128 chains, N = 128 data rows, K = D)
+//   Z = Theta X^T          (M = 256 chains, N = 128 data rows, K = D)
 //   R = y - sigmoid(Z)     (epilogue, straight back into tensor memory)
-//   G += R X               (M = 128 chains, N = D, K = 128 data rows; A = R
+//   G += R X               (M = 256 chains, N = D, K = 128 data rows; A = R
 //                           read from tensor memory, B = the transposed data)
+// on CTA pairs (tcgen05 cta_group::2): each CTA holds 128 of the chains (its
+// rows of Theta, Z, R and G) and loads half of every data tile -- 64 rows of
+// X for Z, half of the dims of X^T for G -- so each SM reads half the data
+// and issues half the MMAs of a one-CTA tile, and the pair exchanges nothing
+// but barrier arrivals.  With one CTA per 128 chains, the first product read
+// 8 KB of shared memory per MMA and issued at 53 ns instead of 33.
 // Z is double-buffered in tensor memory and R's head is written over the Z it
 // came from, so the tensor pipe computes Z of the next tile while the
 // epilogue turns this tile's Z into R; R's remainder has one buffer, which
 // the epilogue refills once the previous tile's G products are done.
-// One CTA per (128-chain group, range of data rows); the data tiles stream by
-// TMA through a ring of stages and every tile serves all 128 chains; Z and R
-// never reach HBM.  Per-range partial gradients and log-likelihoods are
+// One CTA pair per (256-chain group, range of data rows); the data tiles
+// stream by TMA through a ring of stages and every tile serves all 256
+// chains; Z and R never reach HBM.  Per-range partial gradients and log-likelihoods are
 // summed in a fixed order by k_lr_update, which also applies the leapfrog
 // update.  A transition is: begin (momentum, half kick, drift), L x (grad,
 // update), accept.  For D <= 128 (tensor memory holds Z, R head / remainder
@@ -31,6 +37,7 @@ namespace hmc {
 namespace {
 
 constexpr int kM = 128;                     // chains per CTA
+constexpr int kPairM = 2 * kM;              // chains per CTA pair (MMA M)
 constexpr int kRowsPerTile = 128;           // data rows per tile
 constexpr int kMaxD = 128;
 // warp 0 TMA, warp 1 MMA, then kEpiGroups x 4 epilogue warps: a lane
@@ -40,8 +47,9 @@ constexpr int kEpiWarps = 4 * kEpiGroups;
 constexpr int kGroupCols = 128 / kEpiGroups;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTile = 128 * 128;       // 128 x 32 floats
-constexpr uint32_t kStage = 2 * kTile;      // head + remainder
-constexpr int kStages = 3;
+constexpr uint32_t kHalfTile = 64 * 128;    // 64 x 32 floats: a CTA's half of a data chunk
+constexpr uint32_t kStage = 2 * kHalfTile;  // head + remainder
+constexpr int kStages = 6;
 constexpr uint32_t kThetaBytes = 2 * 4 * kTile;   // 4 K-chunks, head + remainder
 // Z / R head of even tiles at 0, of odd tiles at 128; R remainder; G
 constexpr uint32_t kColZR = 0, kColRlo = 256, kColG = 384;
@@ -83,12 +91,12 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint8_t* Th = smem;                                   // [4 chunks][hi, lo] 16 KB each
-  uint8_t* St = smem + kThetaBytes;
-  uint64_t* full = reinterpret_cast<uint64_t*>(St + kStages * kStage);
+  uint8_t* St = smem + kThetaBytes;                     // [kStages][hi, lo] 8 KB each
+  uint64_t* full = reinterpret_cast<uint64_t*>(St + kStages * kStage);   // leader's count
   uint64_t* empty = full + kStages;
-  uint64_t* th_full = empty + kStages;
+  uint64_t* th_full = empty + kStages;    // leader: both CTAs' positions loaded
   uint64_t* z_full = th_full + 1;         // [2]: Z of the tile in buffer b is complete
-  uint64_t* r_ready = z_full + 2;
+  uint64_t* r_ready = z_full + 2;         // leader: both CTAs' R written
   uint64_t* g_done = r_ready + 1;         // G of a tile is complete (R remainder free)
   uint64_t* g_full = g_done + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(g_full + 1);
@@ -97,12 +105,14 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
   float* lpred = reinterpret_cast<float*>(St);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kM;
+  const uint32_t rank = ptx::cluster_rank();             // 0: leader, 1: peer
+  const int m0 = (blockIdx.x >> 1) * kPairM + static_cast<int>(rank) * kM;   // this CTA's chains
   const int split = blockIdx.y;
   const int t_begin = split * a.tiles_per_split;
   const int t_end = min(a.ntiles, t_begin + a.tiles_per_split);
   const int ntile = max(0, t_end - t_begin);
   const int nk = (a.D + 31) >> 5;
+  constexpr uint16_t kPairMask = 0x3;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -112,32 +122,33 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
     ptx::mbar_init(th_full, 1);
     ptx::mbar_init(&z_full[0], 1);
     ptx::mbar_init(&z_full[1], 1);
-    ptx::mbar_init(r_ready, 32 * kEpiWarps);
+    ptx::mbar_init(r_ready, 2 * kEpiWarps);   // one arrival per epilogue warp of the pair
     ptx::mbar_init(g_done, 1);
     ptx::mbar_init(g_full, 1);
     ptx::fence_mbar_init();
   }
   if (warp == 0) {
-    ptx::tmem_alloc(tmem_slot, kTmemCols);
-    ptx::tmem_relinquish();
+    ptx::tmem_alloc_pair(tmem_slot, kTmemCols);
+    ptx::tmem_relinquish_pair();
   }
   ptx::tc_fence_before();
   __syncthreads();
+  ptx::cluster_sync();      // both CTAs' barriers and tensor memory exist
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
 
   if (warp == 0) {
     if (lane == 0 && ntile > 0) {
-      // ---- producer: the chains' positions once, then per tile the data
-      // chunks (X for the first product, X^T for the second)
-      ptx::mbar_arrive_expect_tx(th_full, 2u * nk * kTile);
+      // ---- producer (both CTAs): this CTA's chains' positions once, then per
+      // tile its half of the data (rows for Z, dims for G), completing on the
+      // leader's barriers
+      const uint32_t th_bar = ptx::mapa(ptx::smem_u32(th_full), 0);
+      if (rank == 0) ptx::mbar_arrive_expect_tx(th_full, 2u * 2u * nk * kTile);
       for (int kc = 0; kc < nk; ++kc) {
-        ptx::tma_load_2d(Th + (2 * kc) * kTile, &mThi, th_full, kc * 32, m0);
-        ptx::tma_load_2d(Th + (2 * kc + 1) * kTile, &mTlo, th_full, kc * 32, m0);
+        ptx::tma_load_2d_to_bar(Th + (2 * kc) * kTile, &mThi, th_bar, kc * 32, m0);
+        ptx::tma_load_2d_to_bar(Th + (2 * kc + 1) * kTile, &mTlo, th_bar, kc * 32, m0);
       }
-      // stages in the order the issuer consumes them: Z(0), then per tile
-      // ti: Z(ti + 1), G(ti)
       int it = 0;
       auto stage = [&](const CUtensorMap* mh, const CUtensorMap* ml, int c0, int c1) {
         const int s = it % kStages, round = it / kStages;
@@ -148,17 +159,22 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
           return;
         }
         uint8_t* st = St + s * kStage;
-        ptx::mbar_arrive_expect_tx(&full[s], kStage);
-        ptx::tma_load_2d(st, mh, &full[s], c0, c1);
-        ptx::tma_load_2d(st + kTile, ml, &full[s], c0, c1);
+        if (rank == 0) ptx::mbar_arrive_expect_tx(&full[s], 2u * kStage);
+        const uint32_t bar = ptx::mapa(ptx::smem_u32(&full[s]), 0);
+        ptx::tma_load_2d_to_bar(st, mh, bar, c0, c1);
+        ptx::tma_load_2d_to_bar(st + kHalfTile, ml, bar, c0, c1);
       };
+      // stages in the order the issuer consumes them: Z(0), then per tile
+      // ti: Z(ti + 1), G(ti)
+      const int dhalf = a.dpad / 2;
       auto load_z = [&](int ti) {
-        const int row0 = (t_begin + ti) * kRowsPerTile;
+        const int row0 = (t_begin + ti) * kRowsPerTile + static_cast<int>(rank) * (kRowsPerTile / 2);
         for (int part = 0; part < nk && ok; ++part) stage(&mXhi, &mXlo, part * 32, row0);
       };
       auto load_g = [&](int ti) {
         const int row0 = (t_begin + ti) * kRowsPerTile;
-        for (int kr = 0; kr < 4 && ok; ++kr) stage(&mXThi, &mXTlo, row0 + kr * 32, 0);
+        for (int kr = 0; kr < 4 && ok; ++kr)
+          stage(&mXThi, &mXTlo, row0 + kr * 32, static_cast<int>(rank) * dhalf);
       };
       load_z(0);
       for (int ti = 0; ti < ntile && ok; ++ti) {
@@ -167,17 +183,17 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
       }
     }
   } else if (warp == 1) {
-    if (lane == 0 && ntile > 0) {
-      // ---- MMA issuer
-      const uint32_t idesc1 = ptx::idesc_tf32(kM, kRowsPerTile);
-      const uint32_t idesc2 = ptx::idesc_tf32(kM, a.dpad);
+    if (lane == 0 && ntile > 0 && rank == 0) {
+      // ---- MMA issuer (leader): M = 256 chains across the pair
+      const uint32_t idesc1 = ptx::idesc_tf32(kPairM, kRowsPerTile);
+      const uint32_t idesc2 = ptx::idesc_tf32(kPairM, a.dpad);
       if (!ptx::mbar_wait(th_full, 0)) {
         atomicCAS(a.err, 0, 12);
         ok = false;
       }
       ptx::tc_fence_after();
       int it = 0;
-      // Z = Theta X^T into buffer ti % 2
+      // Z = Theta X^T into buffer ti % 2 (N = the tile's 128 rows, 64 per CTA)
       auto mma_z = [&](int ti) {
         const uint32_t zcol = tmem + kColZR + 128u * static_cast<uint32_t>(ti & 1);
         for (int kc = 0; kc < nk && ok; ++kc, ++it) {
@@ -191,24 +207,24 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
           const uint32_t thi = ptx::smem_u32(Th + (2 * kc) * kTile);
           const uint32_t tlo = ptx::smem_u32(Th + (2 * kc + 1) * kTile);
           const uint32_t xhi = ptx::smem_u32(St + s * kStage);
-          const uint32_t xlo = xhi + kTile;
+          const uint32_t xlo = xhi + kHalfTile;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const uint64_t dth = ptx::sw128_kmajor_desc(thi + 32 * j);
             const uint64_t dtl = ptx::sw128_kmajor_desc(tlo + 32 * j);
             const uint64_t dxh = ptx::sw128_kmajor_desc(xhi + 32 * j);
             const uint64_t dxl = ptx::sw128_kmajor_desc(xlo + 32 * j);
-            ptx::mma_tf32(zcol, dtl, dxh, idesc1, (kc | j) != 0 ? 1u : 0u);
-            ptx::mma_tf32(zcol, dth, dxl, idesc1, 1u);
-            ptx::mma_tf32(zcol, dth, dxh, idesc1, 1u);
+            ptx::mma_tf32_pair(zcol, dtl, dxh, idesc1, (kc | j) != 0 ? 1u : 0u);
+            ptx::mma_tf32_pair(zcol, dth, dxl, idesc1, 1u);
+            ptx::mma_tf32_pair(zcol, dth, dxh, idesc1, 1u);
           }
-          ptx::mma_commit(&empty[s]);
+          ptx::mma_commit_pair(&empty[s], kPairMask);
         }
-        if (ok) ptx::mma_commit(&z_full[ti & 1]);
+        if (ok) ptx::mma_commit_pair(&z_full[ti & 1], kPairMask);
       };
-      // G += R X   (A = R from tensor memory, K = the tile's 128 rows)
+      // G += R X   (A = R from each CTA's tensor memory, N = dims, half per CTA)
       auto mma_g = [&](int ti) {
-        if (!ptx::mbar_wait(r_ready, ti & 1)) {
+        if (!ptx::mbar_wait_cluster(r_ready, ti & 1)) {
           atomicCAS(a.err, 0, 14);
           ok = false;
           return;
@@ -224,20 +240,20 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
           }
           ptx::tc_fence_after();
           const uint32_t bhi = ptx::smem_u32(St + s * kStage);
-          const uint32_t blo = bhi + kTile;
+          const uint32_t blo = bhi + kHalfTile;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const uint64_t dbh = ptx::sw128_kmajor_desc(bhi + 32 * j);
             const uint64_t dbl = ptx::sw128_kmajor_desc(blo + 32 * j);
             const uint32_t k = static_cast<uint32_t>(kr * 32 + 8 * j);
-            ptx::mma_tf32_tmem_a(tmem + kColG, tmem + kColRlo + k, dbh, idesc2,
-                                 (ti | kr | j) != 0 ? 1u : 0u);
-            ptx::mma_tf32_tmem_a(tmem + kColG, rhi + k, dbl, idesc2, 1u);
-            ptx::mma_tf32_tmem_a(tmem + kColG, rhi + k, dbh, idesc2, 1u);
+            ptx::mma_tf32_pair_tmem_a(tmem + kColG, tmem + kColRlo + k, dbh, idesc2,
+                                      (ti | kr | j) != 0 ? 1u : 0u);
+            ptx::mma_tf32_pair_tmem_a(tmem + kColG, rhi + k, dbl, idesc2, 1u);
+            ptx::mma_tf32_pair_tmem_a(tmem + kColG, rhi + k, dbh, idesc2, 1u);
           }
-          ptx::mma_commit(&empty[s]);
+          ptx::mma_commit_pair(&empty[s], kPairMask);
         }
-        if (ok) ptx::mma_commit(g_done);
+        if (ok) ptx::mma_commit_pair(g_done, kPairMask);
       };
       // MMAs execute in issue order: Z(ti + 1) overwrites the buffer G(ti - 1)
       // read only after G(ti - 1)
@@ -246,15 +262,16 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
         if (ti + 1 < ntile) mma_z(ti + 1);
         mma_g(ti);
       }
-      ptx::mma_commit(g_full);
+      ptx::mma_commit_pair(g_full, kPairMask);
     }
   } else {
-    // ---- epilogue: thread = chain row (TMEM lane), one group of columns
+    // ---- epilogue (both CTAs): thread = chain row (TMEM lane), one group of columns
     const int ew = warp - 2;
     const int quarter = warp & 3;
     const int group = ew >> 2;
     const int r = quarter * 32 + lane;
     const uint32_t lane_base = static_cast<uint32_t>(quarter * 32) << 16;
+    const uint32_t r_ready_leader = ptx::mapa(ptx::smem_u32(r_ready), 0);
     float lp_acc = 0.f;
     const bool need_lp = a.need_lp != 0;
     for (int ti = 0; ti < ntile; ++ti) {
@@ -298,7 +315,13 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
         ptx::tmem_st16(tmem + lane_base + kColRlo + kGroupCols * group + 16 * cb, rl + 16 * cb);
       ptx::tmem_wait_st();
       ptx::tc_fence_before();
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(r_ready)) : "memory");
+      __syncwarp();
+      if (lane == 0) {
+        if (rank == 0)
+          ptx::mbar_arrive_local(r_ready);
+        else
+          ptx::mbar_arrive_cluster(r_ready_leader);
+      }
     }
     // partial gradient and log-likelihood of this row range
     const int chain = m0 + r;
@@ -340,9 +363,10 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
       a.lp_part[static_cast<int64_t>(split) * a.C + chain] = lp;
     }
   }
+  ptx::cluster_sync();      // the peer no longer needs this CTA's tensor memory
   if (warp == 0) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, kTmemCols);
+    ptx::tmem_dealloc_pair(tmem, kTmemCols);
   }
 }
 
@@ -499,12 +523,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode() {
   return fn;
 }
 
-bool map2d(CUtensorMap* m, const float* base, int64_t rows, int64_t cols) {
+bool map2d(CUtensorMap* m, const float* base, int64_t rows, int64_t cols, unsigned box_rows) {
   auto fn = encode();
   if (!fn) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(cols) * sizeof(float)};
-  cuuint32_t box[2] = {32u, 128u};
+  cuuint32_t box[2] = {32u, box_rows};
   cuuint32_t es[2] = {1u, 1u};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -521,8 +545,8 @@ Plan plan(const hmc_target& t, int64_t C) {
   Plan p{};
   p.ntiles = static_cast<int>((t.n_data + kRowsPerTile - 1) / kRowsPerTile);
   p.npad = p.ntiles * kRowsPerTile;
-  p.groups = static_cast<int>((C + kM - 1) / kM);
-  int ns = std::max(1, 152 / p.groups);
+  p.groups = static_cast<int>((C + kPairM - 1) / kPairM);   // CTA pairs
+  int ns = std::max(1, 76 / p.groups);
   ns = std::min(ns, p.ntiles);
   p.tps = (p.ntiles + ns - 1) / ns;
   p.nsplit = (p.ntiles + p.tps - 1) / p.tps;
@@ -568,10 +592,11 @@ cudaError_t logreg_tc_setup(LogregTc* tc, const hmc_target& t, int64_t C, void* 
   tc->h0 = take(C * 4);
   tc->Gpart = take(static_cast<size_t>(p.nsplit) * CD * 4);
   tc->lp_part = take(static_cast<size_t>(p.nsplit) * C * 4);
-  const bool ok = map2d(&tc->mThi, tc->thi, C, t.dim) && map2d(&tc->mTlo, tc->tlo, C, t.dim) &&
-                  map2d(&tc->mXhi, tc->Xhi, p.npad, t.dim) && map2d(&tc->mXlo, tc->Xlo, p.npad, t.dim) &&
-                  map2d(&tc->mXThi, tc->XThi, t.dim, p.npad) &&
-                  map2d(&tc->mXTlo, tc->XTlo, t.dim, p.npad);
+  const bool ok = map2d(&tc->mThi, tc->thi, C, t.dim, 128) && map2d(&tc->mTlo, tc->tlo, C, t.dim, 128) &&
+                  map2d(&tc->mXhi, tc->Xhi, p.npad, t.dim, 64) &&
+                  map2d(&tc->mXlo, tc->Xlo, p.npad, t.dim, 64) &&
+                  map2d(&tc->mXThi, tc->XThi, t.dim, p.npad, 64) &&
+                  map2d(&tc->mXTlo, tc->XTlo, t.dim, p.npad, 64);
   if (!ok) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_lr_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(kSmem));
@@ -612,12 +637,25 @@ cudaError_t launch_logreg_tc_transition(const StepArgs& a, LogregTc& tc, int* er
   g.lp_part = tc.lp_part;
   g.err = err;
   g.N = tc.n_data;
-  const dim3 grid(tc.groups, tc.nsplit);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * tc.groups, tc.nsplit);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   for (int l = 1; l <= a.L; ++l) {
     g.need_lp = l == a.L;
     if (timer) timer->begin(s);
-    k_lr_grad<<<grid, kThreads, kSmem, s>>>(tc.mThi, tc.mTlo, tc.mXhi, tc.mXlo, tc.mXThi, tc.mXTlo, g);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_lr_grad, tc.mThi, tc.mTlo, tc.mXhi, tc.mXlo, tc.mXThi,
+                                       tc.mXTlo, g);
     if (timer) timer->end(s);
+    if (e != cudaSuccess) return e;
     b.last = l == a.L;
     k_lr_update<<<nb, 32 * kWarpsPerBlock, 0, s>>>(b);
     count_launch(2);
