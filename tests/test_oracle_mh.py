@@ -20,7 +20,7 @@ def test_random_walk_acceptance_matches_its_closed_form():
     with a symmetric proposal it equals 2 P(|x'| < |x|) = 2 P(ab < 0) for
     a = x' - x, b = x' + x, jointly normal with correlation
     eps / sqrt(4 + eps^2), so 2 (1/2 - asin(.)/pi) = 1 - (2/pi) atan(eps/2).
-    One transition of 200,000 chains.""" 
+    One transition of 200,000 chains."""
     C = 200_000
     for eps, t in ((0.6, 0), (2.4, 1), (5.0, 2)):
         x = philox.momentum(123, 1000 + t, C, 1)           # exact N(0, 1) draws
@@ -61,7 +61,7 @@ def test_mala_is_hmc_with_one_leapfrog_step():
     """One leapfrog step from momentum z proposes x + eps z + eps^2/2 g, the
     Langevin proposal; its energy difference H_0 - H_1 equals the Langevin
     log acceptance ratio written from the proposal density."""
-   rng = np.random.default_rng(4)
+    rng = np.random.default_rng(4)
     for kind, data, D in (("corr_gauss", None, 6), ("funnel", None, 5), ("logreg", None, 3)):
         if kind == "corr_gauss":
             A = rng.standard_normal((D, D))
