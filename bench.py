@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--workload", default="corr_gauss",
                     choices=["corr_gauss", "logreg", "funnel", "std_normal", "uneven_batch", "serve"])
     ap.add_argument("--plain", action="store_true", help="one launch per op per leapfrog step")
+    ap.add_argument("--proposal", default="leapfrog", choices=["leapfrog", "random_walk"],
+                    help="inner kernel of the Metropolis-Hastings composition (random_walk runs "
+                         "the plain path; one target evaluation per transition)")
     ap.add_argument("--max-transitions-per-launch", type=int, default=0,
                     help="dense Gaussian: cap on transitions per kernel launch (0: whole chain; "
                          "1 for profilers that cannot replay cooperative cluster launches)")
@@ -356,7 +359,12 @@ def main():
     p.seed = p.seed + 1000 * rank          # each rank samples its own replica
     impl = hmc.HMC_IMPL_PLAIN if args.plain else hmc.HMC_IMPL_FUSED
     stream = torch.cuda.current_stream()
-    s = Sampler(p, impl=impl, stream=stream, max_transitions_per_launch=args.max_transitions_per_launch)
+    proposal = hmc.HMC_PROPOSAL_RANDOM_WALK if args.proposal == "random_walk" else hmc.HMC_PROPOSAL_LEAPFROG
+    if proposal == hmc.HMC_PROPOSAL_RANDOM_WALK:
+        p.num_leapfrog = 1                 # one target evaluation per transition
+        wl += " (random-walk Metropolis-Hastings)"
+    s = Sampler(p, impl=impl, stream=stream, max_transitions_per_launch=args.max_transitions_per_launch,
+                proposal=proposal)
     C, D, K, B = p.num_chains, p.dim, p.num_results, p.num_burnin
     x0 = torch.as_tensor(p.x0).cuda()
     x = torch.empty_like(x0)

@@ -82,6 +82,19 @@ typedef enum {
                                      transition on single CTAs (32 chains) */
 } hmc_impl;
 
+/* Inner (uncalibrated) kernel of the Metropolis-Hastings composition,
+ * Section 4.1's MetropolisHastings(Uncalibrated...(...)). */
+typedef enum {
+  HMC_PROPOSAL_LEAPFROG = 0,     /* Hamiltonian: num_leapfrog leapfrog steps from a
+                                    fresh momentum; with num_leapfrog = 1 this is
+                                    the Langevin (MALA) proposal x + eps^2/2 grad
+                                    + eps z with its exact correction */
+  HMC_PROPOSAL_RANDOM_WALK = 1   /* x' = x + eps z, z ~ N(0, I) (the momentum
+                                    stream), log alpha = log p(x') - log p(x);
+                                    num_leapfrog is ignored; runs the plain
+                                    one-launch-per-operation path */
+} hmc_proposal_kind;
+
 /* Sampler configuration (the HamiltonianMonteCarlo constructor arguments of
  * the Section 1 listing plus adaptation). */
 typedef struct {
@@ -105,6 +118,8 @@ typedef struct {
                                one cooperative launch; 1: one launch per
                                transition, e.g. for a profiler that cannot
                                replay cooperative cluster launches) */
+  int32_t proposal;         /* hmc_proposal_kind: the inner kernel of the
+                               Metropolis-Hastings composition (Section 4.1) */
 } hmc_config;
 
 /* Kernel results of the last transition.  All pointers are device pointers
@@ -209,6 +224,34 @@ hmc_status hmc_profile_dominant_kernel(hmc_ctx* ctx, int32_t sample_every);
  * were timed (at most 2048, the most recent ones) and how many dominant
  * launches occurred.  Synchronises the context's stream. */
 hmc_status hmc_profile_read(hmc_ctx* ctx, double* avg_ms, uint64_t* samples, uint64_t* launches);
+
+/* The composition's two halves as separate calls (Section 4.1:
+ * MetropolisHastings wrapping an uncalibrated kernel).  hmc_step is exactly
+ * hmc_propose followed by hmc_mh_select with the same t (bit-identical
+ * results).  Both need a context created with impl = HMC_IMPL_PLAIN (or
+ * proposal = HMC_PROPOSAL_RANDOM_WALK) and no replicas; otherwise
+ * HMC_E_UNSUPPORTED.  hmc_bootstrap must come first (HMC_E_INVALID).
+ *
+ * hmc_propose: draws transition t's proposal from the state x ([chains x
+ * dim], device, read only) and its cached log p / gradient, without
+ * accepting it.  *out receives device pointers owned by the context, valid
+ * until the next call on it: the proposed state, its log p and gradient, and
+ * log alpha per chain (-inf where non-finite). */
+typedef struct {
+  const float* x;                 /* [chains x dim] proposed state */
+  const float* target_log_prob;   /* [chains] */
+  const float* grad;              /* [chains x dim] */
+  const float* log_accept_ratio;  /* [chains] */
+} hmc_proposal;
+
+hmc_status hmc_propose(hmc_ctx* ctx, const float* x, uint64_t t, hmc_proposal* out);
+
+/* The Metropolis-Hastings step for the last hmc_propose (which must have used
+ * the same t and state): chain c takes the proposal iff log u < log alpha
+ * (u from transition t's accept stream), x_inout and the cached log p /
+ * gradient are updated in place, the step size adapts as in hmc_step, and
+ * *out (may be NULL) is filled as by hmc_step. */
+hmc_status hmc_mh_select(hmc_ctx* ctx, float* x_inout, uint64_t t, hmc_kernel_results* out);
 
 /* Release the context's workspace.  NULL is accepted. */
 hmc_status hmc_destroy(hmc_ctx* ctx);

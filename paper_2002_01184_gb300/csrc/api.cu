@@ -127,6 +127,10 @@ bool valid_config(const hmc_config* c, int64_t C, std::string* why) {
   }
   if (c->use_graph != 0 && c->use_graph != 1) { *why = "use_graph must be 0 or 1"; return false; }
   if (c->max_transitions_per_launch < 0) { *why = "max_transitions_per_launch must be >= 0"; return false; }
+  if (c->proposal != HMC_PROPOSAL_LEAPFROG && c->proposal != HMC_PROPOSAL_RANDOM_WALK) {
+    *why = "unknown proposal";
+    return false;
+  }
   if (c->chain_offset < 0 || c->chain_offset + C > (1ll << 32)) {
     *why = "chain_offset + num_chains must fit in 32 bits";
     return false;
@@ -193,6 +197,7 @@ StepArgs make_args(hmc_ctx* ctx, float* x, uint64_t t) {
   a.log_accept = ctx->log_accept;
   a.betas = ctx->betas;
   a.K = ctx->K;
+  a.proposal = ctx->cfg.proposal;
   return a;
 }
 
@@ -377,6 +382,8 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   ctx->target = *target;
   ctx->C = num_chains;
   ctx->cfg = *config;
+  // the random walk runs the plain path (its proposal is one elementwise op)
+  if (ctx->cfg.proposal == HMC_PROPOSAL_RANDOM_WALK) ctx->cfg.impl = HMC_IMPL_PLAIN;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   const size_t C = static_cast<size_t>(num_chains), D = static_cast<size_t>(target->dim);
   cudaError_t e = cudaSuccess;
@@ -392,19 +399,19 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->da, 1);
   // (two transitions' worth: the multi-transition pair launch alternates)
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->partials, 2 * static_cast<size_t>(nblk));
-  ctx->use_tc = (config->impl == HMC_IMPL_FUSED || config->impl == HMC_IMPL_FUSED_SINGLE_CTA) &&
+  ctx->use_tc = (ctx->cfg.impl == HMC_IMPL_FUSED || ctx->cfg.impl == HMC_IMPL_FUSED_SINGLE_CTA) &&
                 hmc::gauss_tc_supported(*target);
   if (e == cudaSuccess && ctx->use_tc) {
     char* w = nullptr;
     e = ctx_alloc(ctx, &w, hmc::gauss_tc_workspace_bytes(*target, num_chains));
     if (e == cudaSuccess) e = hmc::gauss_tc_setup(&ctx->tc, *target, num_chains, w, ctx->stream);
     ctx->tc.fused = hmc::gauss_fused_supported(*target);
-    ctx->tc.pair = ctx->tc.fused && config->impl == HMC_IMPL_FUSED;
+    ctx->tc.pair = ctx->tc.fused && ctx->cfg.impl == HMC_IMPL_FUSED;
     if (e == cudaSuccess && ctx->tc.pair) e = ctx_alloc(ctx, &ctx->grid_bar, 1);
   }
   // logistic regressions with long data passes: tensor-core products; short
   // ones: the shared-memory SIMT transition
-  ctx->use_lrtc = config->impl == HMC_IMPL_FUSED && hmc::logreg_tc_supported(*target) &&
+  ctx->use_lrtc = ctx->cfg.impl == HMC_IMPL_FUSED && hmc::logreg_tc_supported(*target) &&
                   target->n_data > 2048;
   if (e == cudaSuccess && ctx->use_lrtc) {
     char* w = nullptr;
@@ -420,6 +427,7 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.p, C * D);
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.lpp, C);
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.h0, C);
+    if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.la, C);
   }
   ctx->grad_ws_bytes = hmc::grad_workspace_bytes(*target, num_chains);
   if (e == cudaSuccess && ctx->grad_ws_bytes) {
@@ -465,6 +473,51 @@ hmc_status hmc_step(hmc_ctx* ctx, float* x_inout, uint64_t t, hmc_kernel_results
                               ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange step");
   }
+  if (out) {
+    out->target_log_prob = ctx->lp;
+    out->grad = ctx->g;
+    out->is_accepted = ctx->is_accepted;
+    out->log_accept_ratio = ctx->log_accept;
+    out->step_size = &ctx->da->eps;
+  }
+  return HMC_OK;
+}
+
+namespace {
+hmc_status split_ready(hmc_ctx* ctx, const void* x, uint64_t t) {
+  if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
+  if (!x) return fail(ctx, HMC_E_INVALID, "state pointer is NULL");
+  if (ctx->cfg.impl != HMC_IMPL_PLAIN || ctx->K != 1 || !ctx->plain.la)
+    return fail(ctx, HMC_E_UNSUPPORTED,
+                "the propose / select split needs impl = HMC_IMPL_PLAIN (or the random walk) and no replicas");
+  if (!ctx->bootstrapped) return fail(ctx, HMC_E_INVALID, "hmc_bootstrap must come first");
+  if (t > std::numeric_limits<uint32_t>::max())
+    return fail(ctx, HMC_E_INVALID, "transition index must fit in 32 bits");
+  return HMC_OK;
+}
+}  // namespace
+
+hmc_status hmc_propose(hmc_ctx* ctx, const float* x, uint64_t t, hmc_proposal* out) {
+  hmc_status st = split_ready(ctx, x, t);
+  if (st != HMC_OK) return st;
+  StepArgs a = make_args(ctx, const_cast<float*>(x), t);   // read only in the proposal kernels
+  cudaError_t e = hmc::launch_plain_propose(ctx->target, a, ctx->plain, ctx->grad_ws, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "proposal launch");
+  if (out) {
+    out->x = ctx->plain.xp;
+    out->target_log_prob = ctx->plain.lpp;
+    out->grad = ctx->plain.gp;
+    out->log_accept_ratio = ctx->plain.la;
+  }
+  return HMC_OK;
+}
+
+hmc_status hmc_mh_select(hmc_ctx* ctx, float* x_inout, uint64_t t, hmc_kernel_results* out) {
+  hmc_status st = split_ready(ctx, x_inout, t);
+  if (st != HMC_OK) return st;
+  StepArgs a = make_args(ctx, x_inout, t);
+  cudaError_t e = hmc::launch_plain_select(a, ctx->plain, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "select launch");
   if (out) {
     out->target_log_prob = ctx->lp;
     out->grad = ctx->g;

@@ -176,6 +176,12 @@ hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
                    "batch posterior " + std::to_string(i) +
                        ": supported are LOGREG (dim <= 512), FUNNEL and STD_NORMAL (dim <= 1024)");
     }
+    if (configs[i].proposal != HMC_PROPOSAL_LEAPFROG) {
+      batch_release(b);
+      delete b;
+      return bfail(nullptr, HMC_E_UNSUPPORTED,
+                   "batch posterior " + std::to_string(i) + ": batches run the leapfrog proposal only");
+    }
     hmc_config c = configs[i];
     const bool grouped = hmc::grouped_member(t, num_chains[i]);
     c.impl = HMC_IMPL_FUSED;       // side members: tensor-core products where they apply

@@ -97,6 +97,7 @@ struct StepArgs {
   float* trace_eps;       // [1] or null
   const float* betas;     // replica exchange: row r targets p^betas[r % K]; null = 1
   int K;                  // replicas per chain (1: no tempering)
+  int proposal;           // hmc_proposal_kind
 };
 
 // Scratch of the plain (one launch per operation) transition.
@@ -106,6 +107,7 @@ struct PlainBuffers {
   float* p;    // momentum
   float* lpp;  // log-prob at the proposal [C]
   float* h0;   // initial Hamiltonian [C]
+  float* la;   // log alpha [C] (the propose / select split)
 };
 
 // Largest state dimension the fused elementwise transition keeps in registers.
@@ -117,6 +119,11 @@ cudaError_t launch_fused_elementwise(int target_id, const StepArgs& a, cudaStrea
                                      KernelTimer* timer = nullptr);
 cudaError_t launch_plain_transition(const hmc_target& t, const StepArgs& a, const PlainBuffers& b,
                                     void* grad_ws, cudaStream_t s, KernelTimer* timer = nullptr);
+// The plain transition in two halves: the proposal with its log alpha into
+// b.la, then the Metropolis-Hastings select (same arithmetic as the whole).
+cudaError_t launch_plain_propose(const hmc_target& t, const StepArgs& a, const PlainBuffers& b,
+                                 void* grad_ws, cudaStream_t s);
+cudaError_t launch_plain_select(const StepArgs& a, const PlainBuffers& b, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out,
                           cudaStream_t s);
 cudaError_t launch_momentum(uint64_t seed, uint32_t t, int C, int D, uint32_t chain_offset,

@@ -79,41 +79,95 @@ __global__ void k_plain_kick(int64_t n, float* __restrict__ p, const float* __re
     p[i] = fmaf(0.5f * eps, gp[i], p[i]);
 }
 
+// Random-walk proposal (Section 4.1's composition with a symmetric inner
+// kernel): xp = x + eps z with z the transition's momentum draws; p = 0, so
+// the energies below reduce to log alpha = log p(xp) - log p(x).
+__global__ void k_rw_begin(StepArgs a, PlainBuffers b) {
+  const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= a.C) return;
+  const int D = a.D;
+  const int64_t row = static_cast<int64_t>(c) * D;
+  const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
+  const float eps = a.da->eps;
+  for (int j = lane; 4 * j < D; j += 32) {
+    const float4 z = momentum4(a.seed, static_cast<uint32_t>(j), chain, a.t);
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+    for (int i = 0; i < 4 && 4 * j + i < D; ++i) {
+      const int64_t e = row + 4 * j + i;
+      b.p[e] = 0.f;
+      b.xp[e] = fmaf(eps, zz[i], a.x[e]);
+    }
+  }
+  if (lane == 0) b.h0[c] = -a.lp[c];
+}
+
+// log alpha = H_0 - H_L of chain c (warp per chain; every lane gets it)
+__device__ __forceinline__ float plain_log_alpha(const StepArgs& a, const PlainBuffers& b, int c,
+                                                 int lane) {
+  const int D = a.D;
+  const int64_t row = static_cast<int64_t>(c) * D;
+  float kin = 0.f;
+  for (int d = lane; d < D; d += 32) kin = fmaf(b.p[row + d], b.p[row + d], kin);
+  kin = 0.5f * warp_sum(kin);
+  const float h1 = -b.lpp[c] + kin;
+  float la = b.h0[c] - h1;
+  if (!isfinite(la)) la = -INFINITY;
+  return la;
+}
+
+// Metropolis-Hastings select of chain c given log alpha; returns min(1, alpha)
+__device__ __forceinline__ float plain_select(const StepArgs& a, const PlainBuffers& b, int c, int lane,
+                                              float la) {
+  const int D = a.D;
+  const int64_t row = static_cast<int64_t>(c) * D;
+  const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
+  int acc = 0;
+  if (lane == 0) acc = accept_log_uniform(a.seed, chain, a.t) < la;
+  acc = __shfl_sync(0xffffffffu, acc, 0);
+  for (int d = lane; d < D; d += 32) {
+    if (acc) {
+      a.x[row + d] = b.xp[row + d];
+      a.g[row + d] = b.gp[row + d];
+    }
+    if (a.sample_out) a.sample_out[row + d] = a.x[row + d];
+  }
+  if (lane == 0) {
+    if (acc) a.lp[c] = b.lpp[c];
+    a.is_accepted[c] = static_cast<uint8_t>(acc);
+    a.log_accept[c] = la;
+    if (a.trace_acc) a.trace_acc[c] = static_cast<uint8_t>(acc);
+    if (c == 0 && a.trace_eps) a.trace_eps[0] = a.da->eps;
+  }
+  return accept_prob(la);
+}
+
 // H_L, log alpha, Metropolis-Hastings select, traces, dual averaging
 __global__ void k_plain_accept(StepArgs a, PlainBuffers b) {
   const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   const bool has_chain = c < a.C;
   float prob = 0.f;
-  if (has_chain) {
-    const int D = a.D;
-    const int64_t row = static_cast<int64_t>(c) * D;
-    const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
-    float kin = 0.f;
-    for (int d = lane; d < D; d += 32) kin = fmaf(b.p[row + d], b.p[row + d], kin);
-    kin = 0.5f * warp_sum(kin);
-    const float h1 = -b.lpp[c] + kin;
-    float la = b.h0[c] - h1;
-    if (!isfinite(la)) la = -INFINITY;
-    int acc = 0;
-    if (lane == 0) acc = accept_log_uniform(a.seed, chain, a.t) < la;
-    acc = __shfl_sync(0xffffffffu, acc, 0);
-    for (int d = lane; d < D; d += 32) {
-      if (acc) {
-        a.x[row + d] = b.xp[row + d];
-        a.g[row + d] = b.gp[row + d];
-      }
-      if (a.sample_out) a.sample_out[row + d] = a.x[row + d];
-    }
-    if (lane == 0) {
-      if (acc) a.lp[c] = b.lpp[c];
-      a.is_accepted[c] = static_cast<uint8_t>(acc);
-      a.log_accept[c] = la;
-      if (a.trace_acc) a.trace_acc[c] = static_cast<uint8_t>(acc);
-      if (c == 0 && a.trace_eps) a.trace_eps[0] = a.da->eps;
-    }
-    prob = accept_prob(la);
-  }
+  if (has_chain) prob = plain_select(a, b, c, lane, plain_log_alpha(a, b, c, lane));
+  finish_block(a, prob, has_chain);
+}
+
+// the split: log alpha only ...
+__global__ void k_plain_ratio(StepArgs a, PlainBuffers b) {
+  const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= a.C) return;
+  const float la = plain_log_alpha(a, b, c, lane);
+  if (lane == 0) b.la[c] = la;
+}
+
+// ... then the select from it
+__global__ void k_plain_select(StepArgs a, PlainBuffers b) {
+  const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const bool has_chain = c < a.C;
+  float prob = 0.f;
+  if (has_chain) prob = plain_select(a, b, c, lane, b.la[c]);
   finish_block(a, prob, has_chain);
 }
 
@@ -193,9 +247,17 @@ cudaError_t launch_fused_elementwise(int target_id, const StepArgs& a, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_plain_transition(const hmc_target& t, const StepArgs& a, const PlainBuffers& b,
-                                    void* grad_ws, cudaStream_t s, KernelTimer* timer) {
+// the proposal: leapfrog trajectory (HMC; MALA at L = 1) or random walk
+static cudaError_t plain_proposal(const hmc_target& t, const StepArgs& a, const PlainBuffers& b,
+                                  void* grad_ws, cudaStream_t s, KernelTimer* timer) {
   const int64_t n = static_cast<int64_t>(a.C) * a.D;
+  if (a.proposal == HMC_PROPOSAL_RANDOM_WALK) {
+    k_rw_begin<<<accept_blocks(a.C), 256, 0, s>>>(a, b);
+    count_launch();
+    cudaError_t e = launch_grad(t, a.C, b.xp, b.lpp, b.gp, grad_ws, s, timer);
+    if (e == cudaSuccess && a.K > 1) e = launch_temper(a.C, a.D, b.lpp, b.gp, a.betas, a.K, s);
+    return e;
+  }
   k_plain_begin<<<accept_blocks(a.C), 256, 0, s>>>(a, b);
   count_launch();
   for (int l = 0; l < a.L; ++l) {
@@ -207,7 +269,29 @@ cudaError_t launch_plain_transition(const hmc_target& t, const StepArgs& a, cons
     k_plain_kick<<<elementwise_blocks(n), 256, 0, s>>>(n, b.p, b.gp, a.da);
     count_launch();
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_transition(const hmc_target& t, const StepArgs& a, const PlainBuffers& b,
+                                    void* grad_ws, cudaStream_t s, KernelTimer* timer) {
+  cudaError_t e = plain_proposal(t, a, b, grad_ws, s, timer);
+  if (e != cudaSuccess) return e;
   k_plain_accept<<<accept_blocks(a.C), 256, 0, s>>>(a, b);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_propose(const hmc_target& t, const StepArgs& a, const PlainBuffers& b,
+                                 void* grad_ws, cudaStream_t s) {
+  cudaError_t e = plain_proposal(t, a, b, grad_ws, s, nullptr);
+  if (e != cudaSuccess) return e;
+  k_plain_ratio<<<accept_blocks(a.C), 256, 0, s>>>(a, b);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plain_select(const StepArgs& a, const PlainBuffers& b, cudaStream_t s) {
+  k_plain_select<<<accept_blocks(a.C), 256, 0, s>>>(a, b);
   count_launch();
   return cudaGetLastError();
 }

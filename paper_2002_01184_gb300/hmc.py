@@ -18,6 +18,7 @@ STATUS_NAMES = ["HMC_OK", "HMC_E_INVALID", "HMC_E_OOM", "HMC_E_CUDA", "HMC_E_TIM
 HMC_T_STD_NORMAL, HMC_T_CORR_GAUSS, HMC_T_LOGREG, HMC_T_FUNNEL = range(4)
 TARGET_IDS = {"std_normal": 0, "corr_gauss": 1, "logreg": 2, "funnel": 3}
 HMC_IMPL_FUSED, HMC_IMPL_PLAIN, HMC_IMPL_FUSED_SINGLE_CTA = 0, 1, 2
+HMC_PROPOSAL_LEAPFROG, HMC_PROPOSAL_RANDOM_WALK = 0, 1
 
 
 class hmc_target(ctypes.Structure):
@@ -30,7 +31,13 @@ class hmc_config(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("adapt", ctypes.c_int32),
                 ("target_accept", ctypes.c_float), ("num_adapt_steps", ctypes.c_int64),
                 ("impl", ctypes.c_int32), ("chain_offset", ctypes.c_int64),
-                ("use_graph", ctypes.c_int32), ("max_transitions_per_launch", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("max_transitions_per_launch", ctypes.c_int32),
+                ("proposal", ctypes.c_int32)]
+
+
+class hmc_proposal(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("target_log_prob", ctypes.c_void_p),
+                ("grad", ctypes.c_void_p), ("log_accept_ratio", ctypes.c_void_p)]
 
 
 class hmc_kernel_results(ctypes.Structure):
@@ -57,6 +64,8 @@ def _load():
                        ctypes.POINTER(P)],
         "hmc_bootstrap": [P, P],
         "hmc_step": [P, P, ctypes.c_uint64, ctypes.POINTER(hmc_kernel_results)],
+        "hmc_propose": [P, P, ctypes.c_uint64, ctypes.POINTER(hmc_proposal)],
+        "hmc_mh_select": [P, P, ctypes.c_uint64, ctypes.POINTER(hmc_kernel_results)],
         "hmc_sample_chain": [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P],
         "hmc_sample_chain_host": [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P],
         "hmc_read_adaptation": [P, ctypes.POINTER(ctypes.c_double)],
@@ -154,10 +163,11 @@ def make_target(kind, dim, P=None, X=None, y=None):
 
 def make_config(num_leapfrog, step_size, seed=0, adapt=False, target_accept=0.65,
                 num_adapt_steps=0, impl=HMC_IMPL_FUSED, chain_offset=0, use_graph=True,
-                max_transitions_per_launch=0):
+                max_transitions_per_launch=0, proposal=HMC_PROPOSAL_LEAPFROG):
     return hmc_config(int(num_leapfrog), float(step_size), int(seed) & 0xFFFFFFFFFFFFFFFF,
                       int(bool(adapt)), float(target_accept), int(num_adapt_steps), int(impl),
-                      int(chain_offset), int(bool(use_graph)), int(max_transitions_per_launch))
+                      int(chain_offset), int(bool(use_graph)), int(max_transitions_per_launch),
+                      int(proposal))
 
 
 def hmc_create(target, num_chains, config, stream=None):
@@ -174,6 +184,18 @@ def hmc_bootstrap(ctx, x0):
 def hmc_step(ctx, x_inout, t):
     out = hmc_kernel_results()
     _check(lib.hmc_step(ctx, _ptr(x_inout), int(t), ctypes.byref(out)), ctx)
+    return out
+
+
+def hmc_propose(ctx, x, t):
+    out = hmc_proposal()
+    _check(lib.hmc_propose(ctx, _ptr(x), int(t), ctypes.byref(out)), ctx)
+    return out
+
+
+def hmc_mh_select(ctx, x_inout, t):
+    out = hmc_kernel_results()
+    _check(lib.hmc_mh_select(ctx, _ptr(x_inout), int(t), ctypes.byref(out)), ctx)
     return out
 
 

@@ -10,7 +10,7 @@ class Sampler:
 
     def __init__(self, problem, impl=hmc.HMC_IMPL_FUSED, num_chains=None, chain_offset=0,
                  step_size=None, adapt=None, stream=None, device="cuda", use_graph=True,
-                 max_transitions_per_launch=0):
+                 max_transitions_per_launch=0, proposal=hmc.HMC_PROPOSAL_LEAPFROG):
         self.problem = problem
         self.C = int(num_chains or problem.num_chains)
         self.D = int(problem.dim)
@@ -23,7 +23,7 @@ class Sampler:
             problem.num_leapfrog, problem.step_size if step_size is None else step_size,
             problem.seed, adapt, problem.target_accept,
             problem.num_burnin if adapt else 0, impl, chain_offset, use_graph,
-            max_transitions_per_launch)
+            max_transitions_per_launch, proposal)
         self.stream = stream
         self.ctx = hmc.hmc_create(self.target, self.C, self.config, stream)
 
