@@ -89,10 +89,20 @@ typedef enum {
                                     fresh momentum; with num_leapfrog = 1 this is
                                     the Langevin (MALA) proposal x + eps^2/2 grad
                                     + eps z with its exact correction */
-  HMC_PROPOSAL_RANDOM_WALK = 1   /* x' = x + eps z, z ~ N(0, I) (the momentum
+  HMC_PROPOSAL_RANDOM_WALK = 1,  /* x' = x + eps z, z ~ N(0, I) (the momentum
                                     stream), log alpha = log p(x') - log p(x);
                                     num_leapfrog is ignored; runs the plain
                                     one-launch-per-operation path */
+  HMC_PROPOSAL_NUTS = 2          /* the No-U-Turn Sampler (Section 2.3) with the
+                                    recursion unrolled: num_leapfrog is the
+                                    maximum tree depth (1..10, at most 2^depth - 1
+                                    leapfrog steps per transition); targets
+                                    STD_NORMAL and FUNNEL with dim <= 512
+                                    (HMC_E_UNSUPPORTED otherwise); the step size
+                                    adapts to the mean over a tree's leaves of
+                                    min(1, exp(H0 - H)); is_accepted reports
+                                    whether the state moved, log_accept_ratio
+                                    the log of that mean */
 } hmc_proposal_kind;
 
 /* Sampler configuration (the HamiltonianMonteCarlo constructor arguments of
@@ -224,6 +234,12 @@ hmc_status hmc_profile_dominant_kernel(hmc_ctx* ctx, int32_t sample_every);
  * were timed (at most 2048, the most recent ones) and how many dominant
  * launches occurred.  Synchronises the context's stream. */
 hmc_status hmc_profile_read(hmc_ctx* ctx, double* avg_ms, uint64_t* samples, uint64_t* launches);
+
+/* Total leapfrog steps (= gradient evaluations) of the NUTS transitions run
+ * on this context since it was created (their number varies per chain and
+ * transition).  Synchronises the context's stream.  HMC_E_INVALID if the
+ * context does not run NUTS. */
+hmc_status hmc_nuts_leapfrog_count(hmc_ctx* ctx, uint64_t* out);
 
 /* The composition's two halves as separate calls (Section 4.1:
  * MetropolisHastings wrapping an uncalibrated kernel).  hmc_step is exactly

@@ -41,6 +41,8 @@ struct hmc_ctx {
   bool use_tc = false;          // tensor-core Gaussian path
   hmc::GaussTc tc;
   unsigned* grid_bar = nullptr;  // grid barrier of the multi-transition pair launch
+  float* nuts_scratch = nullptr;           // NUTS: trajectory ends, candidates, span starts
+  unsigned long long* nuts_leaves = nullptr;   // NUTS: leapfrog steps so far
   int64_t dom_transitions = 1;   // transitions per launch of the dominant kernel (last chain)
   bool use_lrtc = false;        // tensor-core logistic-regression path
   hmc::LogregTc lrtc;
@@ -127,8 +129,13 @@ bool valid_config(const hmc_config* c, int64_t C, std::string* why) {
   }
   if (c->use_graph != 0 && c->use_graph != 1) { *why = "use_graph must be 0 or 1"; return false; }
   if (c->max_transitions_per_launch < 0) { *why = "max_transitions_per_launch must be >= 0"; return false; }
-  if (c->proposal != HMC_PROPOSAL_LEAPFROG && c->proposal != HMC_PROPOSAL_RANDOM_WALK) {
+  if (c->proposal != HMC_PROPOSAL_LEAPFROG && c->proposal != HMC_PROPOSAL_RANDOM_WALK &&
+      c->proposal != HMC_PROPOSAL_NUTS) {
     *why = "unknown proposal";
+    return false;
+  }
+  if (c->proposal == HMC_PROPOSAL_NUTS && c->num_leapfrog > 10) {
+    *why = "num_leapfrog (the NUTS maximum tree depth) must be <= 10";
     return false;
   }
   if (c->chain_offset < 0 || c->chain_offset + C > (1ll << 32)) {
@@ -202,6 +209,9 @@ StepArgs make_args(hmc_ctx* ctx, float* x, uint64_t t) {
 }
 
 cudaError_t enqueue_transition(hmc_ctx* ctx, const StepArgs& a) {
+  if (ctx->cfg.proposal == HMC_PROPOSAL_NUTS)
+    return hmc::launch_nuts_transition(ctx->target, a, ctx->nuts_scratch, ctx->cfg.num_leapfrog,
+                                       ctx->nuts_leaves, ctx->stream, &ctx->timer);
   if (ctx->use_tc) return hmc::launch_gauss_tc_transition(a, ctx->tc, ctx->stream, &ctx->timer);
   if (ctx->use_lrtc)
     return hmc::launch_logreg_tc_transition(a, ctx->lrtc, ctx->lr_err, ctx->stream, &ctx->timer);
@@ -377,13 +387,15 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   *out = nullptr;
   if (!valid_target(target, num_chains, &why)) return fail(nullptr, HMC_E_INVALID, why);
   if (!valid_config(config, num_chains, &why)) return fail(nullptr, HMC_E_INVALID, why);
+  if (config->proposal == HMC_PROPOSAL_NUTS && !hmc::nuts_supported(*target))
+    return fail(nullptr, HMC_E_UNSUPPORTED, "NUTS runs the STD_NORMAL and FUNNEL targets with dim <= 512");
   hmc_ctx* ctx = new (std::nothrow) hmc_ctx();
   if (!ctx) return fail(nullptr, HMC_E_OOM, "host allocation failed");
   ctx->target = *target;
   ctx->C = num_chains;
   ctx->cfg = *config;
   // the random walk runs the plain path (its proposal is one elementwise op)
-  if (ctx->cfg.proposal == HMC_PROPOSAL_RANDOM_WALK) ctx->cfg.impl = HMC_IMPL_PLAIN;
+  if (ctx->cfg.proposal != HMC_PROPOSAL_LEAPFROG) ctx->cfg.impl = HMC_IMPL_PLAIN;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   const size_t C = static_cast<size_t>(num_chains), D = static_cast<size_t>(target->dim);
   cudaError_t e = cudaSuccess;
@@ -399,6 +411,11 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->da, 1);
   // (two transitions' worth: the multi-transition pair launch alternates)
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->partials, 2 * static_cast<size_t>(nblk));
+  if (e == cudaSuccess && ctx->cfg.proposal == HMC_PROPOSAL_NUTS) {
+    e = ctx_alloc(ctx, &ctx->nuts_scratch, hmc::nuts_scratch_floats(*target, num_chains));
+    if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->nuts_leaves, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->nuts_leaves, 0, sizeof(unsigned long long), ctx->stream);
+  }
   ctx->use_tc = (ctx->cfg.impl == HMC_IMPL_FUSED || ctx->cfg.impl == HMC_IMPL_FUSED_SINGLE_CTA) &&
                 hmc::gauss_tc_supported(*target);
   if (e == cudaSuccess && ctx->use_tc) {
@@ -487,7 +504,8 @@ namespace {
 hmc_status split_ready(hmc_ctx* ctx, const void* x, uint64_t t) {
   if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
   if (!x) return fail(ctx, HMC_E_INVALID, "state pointer is NULL");
-  if (ctx->cfg.impl != HMC_IMPL_PLAIN || ctx->K != 1 || !ctx->plain.la)
+  if (ctx->cfg.impl != HMC_IMPL_PLAIN || ctx->K != 1 || !ctx->plain.la ||
+      ctx->cfg.proposal == HMC_PROPOSAL_NUTS)
     return fail(ctx, HMC_E_UNSUPPORTED,
                 "the propose / select split needs impl = HMC_IMPL_PLAIN (or the random walk) and no replicas");
   if (!ctx->bootstrapped) return fail(ctx, HMC_E_INVALID, "hmc_bootstrap must come first");
@@ -496,6 +514,18 @@ hmc_status split_ready(hmc_ctx* ctx, const void* x, uint64_t t) {
   return HMC_OK;
 }
 }  // namespace
+
+hmc_status hmc_nuts_leapfrog_count(hmc_ctx* ctx, uint64_t* out) {
+  if (!ctx || !out) return fail(ctx, HMC_E_INVALID, "NULL argument");
+  if (ctx->cfg.proposal != HMC_PROPOSAL_NUTS || !ctx->nuts_leaves)
+    return fail(ctx, HMC_E_INVALID, "the context does not run NUTS");
+  unsigned long long v = 0;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(&v, ctx->nuts_leaves, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "read leapfrog count");
+  *out = static_cast<uint64_t>(v);
+  return HMC_OK;
+}
 
 hmc_status hmc_propose(hmc_ctx* ctx, const float* x, uint64_t t, hmc_proposal* out) {
   hmc_status st = split_ready(ctx, x, t);
@@ -634,6 +664,8 @@ hmc_status hmc_remc_create(const hmc_target* target, int64_t num_chains, int32_t
       return fail(nullptr, HMC_E_INVALID, "betas must lie in (0, 1]");
   if (!config) return fail(nullptr, HMC_E_INVALID, "config is NULL");
   if (config->adapt) return fail(nullptr, HMC_E_UNSUPPORTED, "replica exchange uses a fixed step size");
+  if (config->proposal == HMC_PROPOSAL_NUTS)
+    return fail(nullptr, HMC_E_UNSUPPORTED, "replica exchange runs the leapfrog or random-walk proposal");
   if (config->chain_offset != 0) return fail(nullptr, HMC_E_INVALID, "chain_offset must be 0");
   if (num_chains < 1 || num_chains > (1ll << 30) / num_replicas)
     return fail(nullptr, HMC_E_INVALID, "num_chains out of range");
@@ -729,7 +761,9 @@ hmc_status hmc_dominant_kernel_info(const hmc_ctx* ctx, char* name, int32_t name
     return fail(nullptr, HMC_E_INVALID, "NULL argument");
   const char* n = "";
   int64_t per = ctx->C;
-  if (ctx->use_tc && ctx->tc.fused && ctx->tc.pair) {
+  if (ctx->cfg.proposal == HMC_PROPOSAL_NUTS) {
+    n = "k_nuts";          // leapfrog steps per launch vary: hmc_nuts_leapfrog_count
+  } else if (ctx->use_tc && ctx->tc.fused && ctx->tc.pair) {
     n = "k_gauss_pair";
     per = ctx->C * ctx->cfg.num_leapfrog * ctx->dom_transitions;
   } else if (ctx->use_tc && ctx->tc.fused) {

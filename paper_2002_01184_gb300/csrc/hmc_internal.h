@@ -110,6 +110,15 @@ struct PlainBuffers {
   float* la;   // log alpha [C] (the propose / select split)
 };
 
+// NUTS (elementwise targets): per-chain scratch slots and the largest dim.
+constexpr int kNutsSlots = 30;
+constexpr int kNutsMaxDim = 512;
+bool nuts_supported(const hmc_target& t);
+size_t nuts_scratch_floats(const hmc_target& t, int64_t C);
+cudaError_t launch_nuts_transition(const hmc_target& t, const StepArgs& a, float* scratch,
+                                   int max_depth, unsigned long long* leaves, cudaStream_t s,
+                                   KernelTimer* timer);
+
 // Largest state dimension the fused elementwise transition keeps in registers.
 constexpr int kFusedElementwiseMaxDim = 1024;
 // Blocks the accept / fused kernels launch for C chains (one warp per chain).

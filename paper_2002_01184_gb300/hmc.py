@@ -18,7 +18,7 @@ STATUS_NAMES = ["HMC_OK", "HMC_E_INVALID", "HMC_E_OOM", "HMC_E_CUDA", "HMC_E_TIM
 HMC_T_STD_NORMAL, HMC_T_CORR_GAUSS, HMC_T_LOGREG, HMC_T_FUNNEL = range(4)
 TARGET_IDS = {"std_normal": 0, "corr_gauss": 1, "logreg": 2, "funnel": 3}
 HMC_IMPL_FUSED, HMC_IMPL_PLAIN, HMC_IMPL_FUSED_SINGLE_CTA = 0, 1, 2
-HMC_PROPOSAL_LEAPFROG, HMC_PROPOSAL_RANDOM_WALK = 0, 1
+HMC_PROPOSAL_LEAPFROG, HMC_PROPOSAL_RANDOM_WALK, HMC_PROPOSAL_NUTS = 0, 1, 2
 
 
 class hmc_target(ctypes.Structure):
@@ -65,6 +65,7 @@ def _load():
         "hmc_bootstrap": [P, P],
         "hmc_step": [P, P, ctypes.c_uint64, ctypes.POINTER(hmc_kernel_results)],
         "hmc_propose": [P, P, ctypes.c_uint64, ctypes.POINTER(hmc_proposal)],
+        "hmc_nuts_leapfrog_count": [P, ctypes.POINTER(ctypes.c_uint64)],
         "hmc_mh_select": [P, P, ctypes.c_uint64, ctypes.POINTER(hmc_kernel_results)],
         "hmc_sample_chain": [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P],
         "hmc_sample_chain_host": [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P],
@@ -185,6 +186,12 @@ def hmc_step(ctx, x_inout, t):
     out = hmc_kernel_results()
     _check(lib.hmc_step(ctx, _ptr(x_inout), int(t), ctypes.byref(out)), ctx)
     return out
+
+
+def hmc_nuts_leapfrog_count(ctx):
+    out = ctypes.c_uint64()
+    _check(lib.hmc_nuts_leapfrog_count(ctx, ctypes.byref(out)), ctx)
+    return int(out.value)
 
 
 def hmc_propose(ctx, x, t):

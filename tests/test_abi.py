@@ -66,6 +66,7 @@ def test_invalid_arguments_are_rejected_on_the_host(binding):
         (good_t, 8, h.make_config(3, 0.5, impl=9), "impl"),
         (good_t, 8, h.make_config(3, 0.5, chain_offset=-1), "chain_offset"),
         (good_t, 8, h.make_config(3, 0.5, proposal=5), "proposal"),
+        (good_t, 8, h.make_config(11, 0.5, proposal=h.HMC_PROPOSAL_NUTS), "tree depth"),
         (good_t, 8, h.make_config(3, 0.5, max_transitions_per_launch=-1), "max_transitions_per_launch"),
     ]
     for t, C, c, word in bad_cases:
@@ -82,6 +83,12 @@ def test_null_context_and_workspace_queries(binding):
     assert h.lib.hmc_step(None, None, 0, None) == h.HMC_E_INVALID
     assert h.lib.hmc_sample_chain(None, None, 0, 0, None, None, None) == h.HMC_E_INVALID
     assert h.lib.hmc_propose(None, None, 0, None) == h.HMC_E_INVALID
+    assert h.lib.hmc_nuts_leapfrog_count(None, None) == h.HMC_E_INVALID
+    # NUTS runs the elementwise targets only
+    with pytest.raises(h.HMCError) as ei:
+        h.hmc_create(h.hmc_target(h.HMC_T_LOGREG, 4, 10, 16, 16, 16), 8,
+                     h.make_config(5, 0.1, proposal=h.HMC_PROPOSAL_NUTS), stream=0)
+    assert ei.value.status == h.HMC_E_UNSUPPORTED
     assert h.lib.hmc_mh_select(None, None, 0, None) == h.HMC_E_INVALID
     assert h.lib.hmc_destroy(None) == h.HMC_OK
     assert h.hmc_grad_workspace_bytes(h.make_target("std_normal", 5), 10) == 0
