@@ -42,6 +42,14 @@ FP32_LANES_PER_SM = 128
 # (kernel, target, chains, dim, leapfrog steps).  Absent -> traffic is null.
 PROFILED_TRAFFIC = {}
 
+# NUTS (Section 2.3): default maximum tree depth, and the float32 operations
+# of one leaf per dimension -- leapfrog kick, drift, kick (6), the kinetic
+# energy (2), the elementwise target's value and gradient (about 2), and on
+# average one closing span's U-turn test (difference and two dot products, 5)
+NUTS_MAX_DEPTH = 10
+NUTS_LABEL = " NUTS max_depth=10"
+NUTS_FLOPS_PER_DIM = 15
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -52,9 +60,10 @@ def parse():
     ap.add_argument("--workload", default="corr_gauss",
                     choices=["corr_gauss", "logreg", "funnel", "std_normal", "uneven_batch", "serve"])
     ap.add_argument("--plain", action="store_true", help="one launch per op per leapfrog step")
-    ap.add_argument("--proposal", default="leapfrog", choices=["leapfrog", "random_walk"],
+    ap.add_argument("--proposal", default="leapfrog", choices=["leapfrog", "random_walk", "nuts"],
                     help="inner kernel of the Metropolis-Hastings composition (random_walk runs "
-                         "the plain path; one target evaluation per transition)")
+                         "the plain path; one target evaluation per transition) or NUTS "
+                         "(funnel / std_normal; maximum tree depth 10)")
     ap.add_argument("--max-transitions-per-launch", type=int, default=0,
                     help="dense Gaussian: cap on transitions per kernel launch (0: whole chain; "
                          "1 for profilers that cannot replay cooperative cluster launches)")
@@ -183,7 +192,10 @@ def run_reference(args):
     if rank != 0:
         return
     p, wl = make_problem(args.workload)
-    res = cpu_oracle_rate(p, args.cpu_seconds)
+    if args.proposal == "nuts":
+        p.num_leapfrog = NUTS_MAX_DEPTH
+        wl += NUTS_LABEL
+    res = cpu_oracle_rate(p, args.cpu_seconds, args.proposal)
     line = {"impl": "reference", "metric": "leapfrog grad-evals/s", "value": res["value"],
             "unit": "grad-evals/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["ms_per_transition"],
@@ -195,27 +207,40 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_oracle_rate(p, seconds):
+def cpu_oracle_rate(p, seconds, proposal="leapfrog"):
     """Time the oracle's transitions on a prefix of the workload until about
-    `seconds` of CPU work; rate = chains x L x transitions / wall time."""
+    `seconds` of CPU work; rate = target evaluations (chains x L per HMC
+    transition, one per random-walk transition, the leaves built by NUTS) /
+    wall time."""
     import numpy as np
-    from oracle import hmc as ohmc, targets as otargets
+    from oracle import hmc as ohmc, mh as omh, nuts as onuts, targets as otargets
     tgt = otargets.make(p.kind, **p.data())
-    x = p.x0.astype(np.float64)
+    C = p.num_chains
+    if proposal == "nuts":
+        C = min(C, 64)                 # the oracle builds each chain's tree in a Python loop
+    x = p.x0[:C].astype(np.float64)
     lp, g = ohmc.bootstrap(x, tgt)
     eps = p.step_size
     t0 = time.perf_counter()
-    n = 0
+    n = evals = 0
     while True:
-        r = ohmc.one_step(x, lp, g, eps, p.num_leapfrog, p.seed, n, tgt)
+        if proposal == "nuts":
+            r = onuts.one_step(x, lp, g, eps, p.num_leapfrog, p.seed, n, tgt)
+            evals += int(r["leaves"].sum())
+        elif proposal == "random_walk":
+            r = omh.rw_one_step(x, lp, g, eps, p.seed, n, tgt)
+            evals += C
+        else:
+            r = ohmc.one_step(x, lp, g, eps, p.num_leapfrog, p.seed, n, tgt)
+            evals += C * p.num_leapfrog
         x, lp, g = r["x"], r["lp"], r["g"]
         n += 1
         el = time.perf_counter() - t0
         if el >= seconds or n >= p.num_burnin + p.num_results:
             break
-    rate = p.num_chains * p.num_leapfrog * n / el
-    return {"value": rate, "unit": "grad-evals/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"first {n} transitions of the workload (all {p.num_chains} chains, "
+    kind = {"nuts": "NUTS", "random_walk": "random-walk"}.get(proposal, "HMC")
+    return {"value": evals / el, "unit": "grad-evals/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"first {n} {kind} transitions of the workload ({C} of {p.num_chains} chains, "
                       f"fixed step size), numpy float64 with BLAS on all host cores",
             "ms_per_transition": 1000.0 * el / n}
 
@@ -359,10 +384,14 @@ def main():
     p.seed = p.seed + 1000 * rank          # each rank samples its own replica
     impl = hmc.HMC_IMPL_PLAIN if args.plain else hmc.HMC_IMPL_FUSED
     stream = torch.cuda.current_stream()
-    proposal = hmc.HMC_PROPOSAL_RANDOM_WALK if args.proposal == "random_walk" else hmc.HMC_PROPOSAL_LEAPFROG
+    proposal = {"random_walk": hmc.HMC_PROPOSAL_RANDOM_WALK,
+                "nuts": hmc.HMC_PROPOSAL_NUTS}.get(args.proposal, hmc.HMC_PROPOSAL_LEAPFROG)
     if proposal == hmc.HMC_PROPOSAL_RANDOM_WALK:
         p.num_leapfrog = 1                 # one target evaluation per transition
         wl += " (random-walk Metropolis-Hastings)"
+    elif proposal == hmc.HMC_PROPOSAL_NUTS:
+        p.num_leapfrog = NUTS_MAX_DEPTH    # the context's num_leapfrog is the maximum tree depth
+        wl += NUTS_LABEL
     s = Sampler(p, impl=impl, stream=stream, max_transitions_per_launch=args.max_transitions_per_launch,
                 proposal=proposal)
     C, D, K, B = p.num_chains, p.dim, p.num_results, p.num_burnin
@@ -381,6 +410,9 @@ def main():
         step()
     torch.cuda.synchronize()
     evals_per_step = C * p.num_leapfrog * (B + K) + C
+    nuts = proposal == hmc.HMC_PROPOSAL_NUTS
+    if nuts:
+        leaves0 = hmc.hmc_nuts_leapfrog_count(s.ctx)
     clocks = ClockSampler(local)
     clocks.start()
     hmc.hmc_profile_dominant_kernel(s.ctx, 8)
@@ -398,6 +430,10 @@ def main():
         torch.distributed.barrier()
     ms_local = e0.elapsed_time(e1)
     launches = hmc.hmc_kernel_launch_count() - launches0
+    if nuts:
+        # the trees' sizes vary: count the leapfrog steps the timed steps built
+        # (identical every step: same start, same seed) and the bootstrap
+        evals_per_step = (hmc.hmc_nuts_leapfrog_count(s.ctx) - leaves0) / args.steps + C
     try:
         prof = hmc.hmc_profile_read(s.ctx)
     except hmc.HMCError as exc:              # timing support only
@@ -416,12 +452,27 @@ def main():
     pk, src = peaks()
     flops = grad_flops_per_eval(p)
     kname, evals_per_launch = hmc.hmc_dominant_kernel_info(s.ctx)
+    if nuts:
+        # launches of unequal work (one adapting transition each, then the
+        # fixed-step-size run): one more, untimed step with every launch
+        # timed gives the k_nuts time of a whole step
+        hmc.hmc_profile_dominant_kernel(s.ctx, 1)
+        step()
+        torch.cuda.synchronize()
+        pn = hmc.hmc_profile_read(s.ctx)
+        prof = {"samples": 0}
+        if pn["samples"] and pn["samples"] == pn["launches"]:
+            prof = {"avg_ms": pn["avg_ms"] * pn["samples"], "samples": pn["samples"]}
+        evals_per_launch = evals_per_step - C              # per step
     roof = None
     if prof["samples"]:
         kernel_s = prof["avg_ms"] / 1000.0
         traffic = PROFILED_TRAFFIC.get((kname, p.kind, C, D, p.num_leapfrog))
         common = {"kernel": kname, "avg_launch_ms": prof["avg_ms"],
                   "timed_launches": prof["samples"], "grad_evals_per_launch": evals_per_launch}
+        if nuts:
+            common = {"kernel": kname, "kernel_ms_per_step": prof["avg_ms"],
+                      "launches_per_step": prof["samples"], "leapfrog_steps_per_step": evals_per_launch}
         if flops is not None and hmc.hmc_uses_tensor_cores(s.ctx):
             # 3xTF32: algorithmic flops (2 D^2 per gradient evaluation) against
             # the dense TF32 peak / 3 (three tf32 products per float32 product)
@@ -431,6 +482,15 @@ def main():
                     "frac": achieved / peak, "traffic": traffic,
                     "peak_source": f"{src} bf16 {pk['bf16_tflops']:.0f} TFLOP/s x (1.1/2.25 nominal tf32:bf16) / 3",
                     **common}
+        elif nuts:
+            # warp per chain, state in registers: float32 ALU work per leaf
+            achieved = NUTS_FLOPS_PER_DIM * D * evals_per_launch / kernel_s / 1e12
+            sm_max = pk.get("sm_max_mhz", 2070.0)
+            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                    "flops_per_leaf": f"{NUTS_FLOPS_PER_DIM} x dim", **common}
         elif flops is not None:
             # SIMT float32 products: FP32-pipe roofline from unit counts and clock
             achieved = flops * evals_per_launch / kernel_s / 1e12
@@ -474,7 +534,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(p, args.cpu_seconds)
+        cpu = cpu_oracle_rate(p, args.cpu_seconds, args.proposal)
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     if rank == 0:

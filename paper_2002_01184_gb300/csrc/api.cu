@@ -273,7 +273,13 @@ hmc_status enqueue_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sa
     ctx->dom_transitions = chunk;
     return HMC_OK;
   }
-  for (int64_t t = 0; t < B + K; ++t) {
+  // NUTS: the transitions that do not adapt the step size run in as few
+  // launches as allowed, so that each chain's tree sizes average out over
+  // the run (those that adapt need every chain's statistic in between)
+  int64_t t_multi = T;
+  if (ctx->cfg.proposal == HMC_PROPOSAL_NUTS && ctx->K == 1 && !ctx->s_mean)
+    t_multi = std::min<int64_t>(T, ctx->cfg.adapt ? std::max<int64_t>(ctx->cfg.num_adapt_steps, 0) : 0);
+  for (int64_t t = 0; t < t_multi; ++t) {
     StepArgs a = make_args(ctx, x, static_cast<uint64_t>(t));
     const int64_t k = t - B;
     if (k >= 0) {
@@ -296,6 +302,14 @@ hmc_status enqueue_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sa
       e = hmc::launch_welford(CD, x, k, ctx->s_mean, ctx->s_m2, ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "moment update launch");
     }
+  }
+  for (int64_t t0 = t_multi; t0 < T; t0 += chunk) {
+    const int n = static_cast<int>(std::min(chunk, T - t0));
+    StepArgs a = make_args(ctx, x, static_cast<uint64_t>(t0));
+    cudaError_t e = hmc::launch_nuts_transitions(ctx->target, a, ctx->nuts_scratch, ctx->cfg.num_leapfrog,
+                                                 ctx->nuts_leaves, n, B, samples, trace_eps, trace_acc,
+                                                 ctx->stream, &ctx->timer);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "NUTS transition launch");
   }
   return HMC_OK;
 }
@@ -403,7 +417,8 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   const unsigned nblk = std::max({hmc::accept_blocks(static_cast<int>(num_chains)),
                                   hmc::gauss_fused_grid(num_chains),
                                   hmc::gauss_pair_grid(num_chains),
-                                  hmc::logreg_fused_grid(num_chains)});
+                                  hmc::logreg_fused_grid(num_chains),
+                                  hmc::nuts_grid(num_chains)});
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->lp, C);
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->g, C * D);
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->is_accepted, C);
@@ -412,7 +427,8 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   // (two transitions' worth: the multi-transition pair launch alternates)
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->partials, 2 * static_cast<size_t>(nblk));
   if (e == cudaSuccess && ctx->cfg.proposal == HMC_PROPOSAL_NUTS) {
-    e = ctx_alloc(ctx, &ctx->nuts_scratch, hmc::nuts_scratch_floats(*target, num_chains));
+    e = hmc::nuts_prepare();
+    if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->nuts_scratch, hmc::nuts_scratch_floats(*target, num_chains));
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->nuts_leaves, 1);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->nuts_leaves, 0, sizeof(unsigned long long), ctx->stream);
   }

@@ -110,14 +110,28 @@ struct PlainBuffers {
   float* la;   // log alpha [C] (the propose / select split)
 };
 
-// NUTS (elementwise targets): per-chain scratch slots and the largest dim.
+// NUTS (elementwise targets): per-chain scratch slots, the largest dim, and
+// the most dynamic shared memory a block may take for its span starts.
 constexpr int kNutsSlots = 30;
 constexpr int kNutsMaxDim = 512;
+constexpr size_t kNutsSpanSmemMax = 96 * 1024;
 bool nuts_supported(const hmc_target& t);
 size_t nuts_scratch_floats(const hmc_target& t, int64_t C);
+unsigned nuts_grid(int64_t C);   // blocks of a NUTS launch (one partial sum each)
+// allow the shared-memory form its dynamic shared memory (once per process)
+cudaError_t nuts_prepare();
+// One transition (a.t_full): state in a.x / a.lp / a.g, sample and traces at
+// a.sample_out / a.trace_eps / a.trace_acc.
 cudaError_t launch_nuts_transition(const hmc_target& t, const StepArgs& a, float* scratch,
                                    int max_depth, unsigned long long* leaves, cudaStream_t s,
                                    KernelTimer* timer);
+// T transitions a.t_full .. a.t_full + T - 1 in one launch, none of which
+// adapts the step size (T > 1); transition keep_from + k writes kept sample k
+// (samples [k][C][D], trace_eps [k], trace_acc [k][C]; each may be null).
+cudaError_t launch_nuts_transitions(const hmc_target& t, const StepArgs& a, float* scratch,
+                                    int max_depth, unsigned long long* leaves, int T,
+                                    long long keep_from, float* samples, float* trace_eps,
+                                    uint8_t* trace_acc, cudaStream_t s, KernelTimer* timer);
 
 // Largest state dimension the fused elementwise transition keeps in registers.
 constexpr int kFusedElementwiseMaxDim = 1024;

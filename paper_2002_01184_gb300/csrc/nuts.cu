@@ -1,8 +1,11 @@
 // The No-U-Turn Sampler with the recursion unrolled (Section 2.3), for the
 // targets whose gradient is elementwise plus row reductions (standard
-// normal, funnel).  One warp per chain, one launch per transition; chains
-// build their trees independently, so a warp's lanes never diverge and
-// different chains' tree sizes cost nothing to each other.
+// normal, funnel).  One warp per chain; chains build their trees
+// independently, so a warp's lanes never diverge and different chains' tree
+// sizes cost nothing to each other.  A launch runs one transition, or -- where
+// the step size is fixed (no adaptation in the range) -- a run of
+// transitions, so that each chain's tree sizes average out over the run
+// instead of every transition waiting for the deepest tree of all chains.
 //
 // The transition is Hoffman and Gelman's efficient NUTS (slice variable u)
 // as a loop: doubling j grows a subtree of 2^j leapfrog steps (step v_j eps)
@@ -10,8 +13,10 @@
 // that closes is checked for a U-turn against its first leaf, which is the
 // only state kept per level -- O(max_depth) states, not the 2^depth
 // trajectory.  The chain's working (x, p, g) lives in registers (lane owns
-// dims 4 (lane + 32 b) .. + 3); the two trajectory ends, the two candidates
-// and the span starts live in a per-chain scratch of 30 slots of D floats.
+// dims 4 (lane + 32 b) .. + 3); the span starts live in shared memory where
+// the occupancy allows (else in the per-chain scratch), the two trajectory
+// ends and the two candidates in a per-chain scratch of kNutsSlots slots of
+// D floats.
 //
 // Random choices: directions from word 0 of counter (0, chain, t, 3), the
 // subtree's choice at leaf k of doubling j from counter (k, chain, t, 4 + j),
@@ -26,12 +31,15 @@ namespace hmc {
 
 namespace {
 
-constexpr int kWarps = 8;
+constexpr int kWarps = 4;
 constexpr uint32_t kTagDirection = 3u, kTagSubtree = 4u, kTagTop = 14u;
 constexpr float kDeltaMax = 1000.f;
+constexpr int kMaxDepth = 10;
 // slots: 0-2 left end x, p, g; 3-5 right end; 6-7 candidate x, g;
 // 8-9 subtree candidate x, g; 10 + 2 (i - 1), + 1: first leaf x, p of level i
+// (scratch form of the span starts)
 constexpr int kSlotLeft = 0, kSlotRight = 3, kSlotCand = 6, kSlotSub = 8, kSlotSpan = 10;
+static_assert(kSlotSpan + 2 * (kMaxDepth - 1) <= kNutsSlots, "scratch slots");
 
 __device__ __forceinline__ uint32_t word0(uint64_t seed, uint32_t w, uint32_t chain, uint32_t t,
                                           uint32_t tag) {
@@ -44,43 +52,88 @@ __device__ __forceinline__ bool take(uint32_t w, uint32_t a, uint32_t b) {
   return (2ull * w + 1ull) * b < (static_cast<unsigned long long>(a) << 33);
 }
 
+// two warp sums in one butterfly (each the same tree as warp_sum)
+__device__ __forceinline__ void warp_sum2(float& u, float& v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    u += __shfl_xor_sync(0xffffffffu, u, o);
+    v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+}
+
+// four warp sums in one butterfly
+__device__ __forceinline__ void warp_sum4(float& u, float& v, float& w, float& z) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    u += __shfl_xor_sync(0xffffffffu, u, o);
+    v += __shfl_xor_sync(0xffffffffu, v, o);
+    w += __shfl_xor_sync(0xffffffffu, w, o);
+    z += __shfl_xor_sync(0xffffffffu, z, o);
+  }
+}
+
 struct NutsArgs {
-  StepArgs s;
+  StepArgs s;                      // transition s.t_full is the launch's first
   float* scratch;                  // [C][kNutsSlots][Dp]
   int Dp;                          // D rounded up to 4
   int max_depth;
   unsigned long long* leaves;      // total leapfrog steps (gradient evaluations)
+  int T;                           // transitions in this launch (T > 1: none adapts)
+  long long keep_from;             // transition whose new state is kept sample 0
+  float* samples;                  // [K][C][D] kept states, or null
+  float* trace_eps;                // [K] step size per kept transition, or null
+  uint8_t* trace_acc;              // [K][C] moved flags, or null
 };
 
-template <int TARGET, int NB>
-__global__ void __launch_bounds__(32 * kWarps) k_nuts(NutsArgs na) {
+// shared-memory span starts: 2 (max_depth - 1) rows of Dp floats per warp
+size_t span_smem_bytes(int Dp, int max_depth) {
+  return static_cast<size_t>(kWarps) * 2 * (max_depth > 1 ? max_depth - 1 : 0) * Dp * sizeof(float);
+}
+
+// residency: 8 blocks (32 warps) per SM at NB = 1, 4 at NB = 2, 4 (registers)
+template <int TARGET, int NB, bool SMEM>
+__global__ void __launch_bounds__(32 * kWarps, NB == 1 ? 8 : 4) k_nuts(NutsArgs na) {
+  extern __shared__ float4 span_smem[];
   const StepArgs& a = na.s;
-  const int c = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * kWarps + warp;
   const int lane = threadIdx.x & 31;
   const bool has_chain = c < a.C;
   float prob = 0.f;
   if (has_chain) {
     const int D = a.D;
     const int64_t row = static_cast<int64_t>(c) * D;
+    const int64_t CD = static_cast<int64_t>(a.C) * D;
     const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
     const float eps = a.da->eps;
     float* base = na.scratch + static_cast<int64_t>(c) * kNutsSlots * na.Dp;
+    float4* spans = span_smem + static_cast<int64_t>(warp) * 2 * (na.max_depth - 1) * (na.Dp / 4);
     float x[NB][4], p[NB][4], g[NB][4];
     auto slot4 = [&](int s, int b) {
       return reinterpret_cast<float4*>(base + static_cast<int64_t>(s) * na.Dp) + (lane + 32 * b);
     };
+    // span row r = 2 (i - 1) (x) or 2 (i - 1) + 1 (p)
+    auto span4 = [&](int r, int b) {
+      return SMEM ? spans + r * (na.Dp / 4) + (lane + 32 * b) : slot4(kSlotSpan + r, b);
+    };
     auto in_slot = [&](int b) { return 4 * (lane + 32 * b) < na.Dp; };
+    auto put = [&](float4* q, const float (&v)[NB][4], int b) {
+      *q = make_float4(v[b][0], v[b][1], v[b][2], v[b][3]);
+    };
+    auto get = [&](const float4* q, float (&v)[NB][4], int b) {
+      const float4 w = *q;
+      v[b][0] = w.x; v[b][1] = w.y; v[b][2] = w.z; v[b][3] = w.w;
+    };
     auto store = [&](int s, const float (&v)[NB][4]) {
 #pragma unroll
       for (int b = 0; b < NB; ++b)
-        if (in_slot(b)) *slot4(s, b) = make_float4(v[b][0], v[b][1], v[b][2], v[b][3]);
+        if (in_slot(b)) put(slot4(s, b), v, b);
     };
     auto load = [&](int s, float (&v)[NB][4]) {
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (in_slot(b)) q = *slot4(s, b);
-        v[b][0] = q.x; v[b][1] = q.y; v[b][2] = q.z; v[b][3] = q.w;
+        v[b][0] = v[b][1] = v[b][2] = v[b][3] = 0.f;
+        if (in_slot(b)) get(slot4(s, b), v, b);
       }
     };
     auto dot = [&](const float (&u)[NB][4], const float (&w)[NB][4]) {
@@ -91,184 +144,321 @@ __global__ void __launch_bounds__(32 * kWarps) k_nuts(NutsArgs na) {
         for (int i = 0; i < 4; ++i) acc = fmaf(u[b][i], w[b][i], acc);
       return warp_sum(acc);
     };
-    // log p and gradient at x (dims past D stay zero)
-    const float half_n = 0.5f * static_cast<float>(D - 1);
-    auto target = [&]() {
-      float q = 0.f;
+    // both ends' U-turn tests: (dx . pa) < 0 or (dx . pb) < 0
+    auto u_turn = [&](const float (&dx)[NB][4], const float (&pa)[NB][4], const float (&pb)[NB][4]) {
+      float d1 = 0.f, d2 = 0.f;
 #pragma unroll
       for (int b = 0; b < NB; ++b)
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const bool is_v = TARGET == HMC_T_FUNNEL && b == 0 && i == 0 && lane == 0;
-          q = is_v ? q : fmaf(x[b][i], x[b][i], q);
+          d1 = fmaf(dx[b][i], pa[b][i], d1);
+          d2 = fmaf(dx[b][i], pb[b][i], d2);
         }
+      warp_sum2(d1, d2);
+      return d1 < 0.f || d2 < 0.f;
+    };
+    const float half_n = 0.5f * static_cast<float>(D - 1);
+
+    // The second half kick at the drifted x and every sum the leaf needs, in
+    // one butterfly: log p (through the sum of squares), |p|^2 and, where
+    // the span of two leaves closes here (close1), its U-turn dot products
+    // dx . pf and dx . p with dx = sv (x - xf) against the span's first leaf
+    // (xf, pf).  Sets g and p; returns log p, H = -log p + |p|^2 / 2 and
+    // whether that span makes a U-turn.
+    auto leaf_sums = [&](float h, float sv, bool close1, const float (&xf)[NB][4],
+                         const float (&pf)[NB][4], float* H, bool* turn) {
+      float q = 0.f, pp = 0.f, d1 = 0.f, d2 = 0.f;
       if (TARGET == HMC_T_STD_NORMAL) {
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
-          for (int i = 0; i < 4; ++i) g[b][i] = -x[b][i];
-        return -0.5f * warp_sum(q);
+          for (int i = 0; i < 4; ++i) {
+            g[b][i] = -x[b][i];
+            p[b][i] = fmaf(h, g[b][i], p[b][i]);
+            q = fmaf(x[b][i], x[b][i], q);
+            pp = fmaf(p[b][i], p[b][i], pp);
+            const float dx = sv * (x[b][i] - xf[b][i]);
+            d1 = fmaf(dx, pf[b][i], d1);
+            d2 = fmaf(dx, p[b][i], d2);
+          }
+        warp_sum4(q, pp, d1, d2);
+        const float lp = -0.5f * q;
+        *H = -lp + 0.5f * pp;
+        *turn = close1 && (d1 < 0.f || d2 < 0.f);
+        return lp;
       } else {
+        // funnel: dim 0 (lane 0, b 0, i 0) is v; its gradient needs the sum
+        // of the others' squares, which the butterfly brings to every lane,
+        // so its terms are added after it from broadcast copies
         const float v = __shfl_sync(0xffffffffu, x[0][0], 0);
-        q = warp_sum(q);
+        const float p0 = __shfl_sync(0xffffffffu, p[0][0], 0);
+        const float xf0 = __shfl_sync(0xffffffffu, xf[0][0], 0);
+        const float pf0 = __shfl_sync(0xffffffffu, pf[0][0], 0);
         const float ev = expf(-v);
 #pragma unroll
         for (int b = 0; b < NB; ++b)
 #pragma unroll
-          for (int i = 0; i < 4; ++i) g[b][i] = -ev * x[b][i];
-        if (lane == 0) g[0][0] = -v / 9.f - half_n + 0.5f * ev * q;
-        return -v * v / 18.f - half_n * v - 0.5f * ev * q;
+          for (int i = 0; i < 4; ++i) {
+            const bool is_v = b == 0 && i == 0 && lane == 0;
+            g[b][i] = -ev * x[b][i];
+            if (!is_v) {
+              p[b][i] = fmaf(h, g[b][i], p[b][i]);
+              q = fmaf(x[b][i], x[b][i], q);
+              pp = fmaf(p[b][i], p[b][i], pp);
+              const float dx = sv * (x[b][i] - xf[b][i]);
+              d1 = fmaf(dx, pf[b][i], d1);
+              d2 = fmaf(dx, p[b][i], d2);
+            }
+          }
+        warp_sum4(q, pp, d1, d2);
+        const float g0 = v * (-1.f / 9.f) - half_n + 0.5f * ev * q;
+        const float p0n = fmaf(h, g0, p0);
+        if (lane == 0) {
+          g[0][0] = g0;
+          p[0][0] = p0n;
+        }
+        const float dx0 = sv * (v - xf0);
+        d1 = fmaf(dx0, pf0, d1);
+        d2 = fmaf(dx0, p0n, d2);
+        const float lp = v * v * (-1.f / 18.f) - half_n * v - 0.5f * ev * q;
+        *H = -lp + 0.5f * fmaf(p0n, p0n, pp);
+        *turn = close1 && (d1 < 0.f || d2 < 0.f);
+        return lp;
       }
     };
 
-    // start: x0, g0, p0 ~ N(0, I), H0, log U
+    // the chain's state at the start of the launch
     float lp = a.lp[c];
 #pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const int j = lane + 32 * b;
-      const float4 z = momentum4(a.seed, static_cast<uint32_t>(j), chain, a.t);
-      const float zz[4] = {z.x, z.y, z.z, z.w};
+    for (int b = 0; b < NB; ++b)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int d = 4 * j + i;
-        const bool in = d < D;
-        x[b][i] = in ? a.x[row + d] : 0.f;
-        g[b][i] = in ? a.g[row + d] : 0.f;
-        p[b][i] = in ? zz[i] : 0.f;
+        const int d = 4 * (lane + 32 * b) + i;
+        x[b][i] = d < D ? a.x[row + d] : 0.f;
+        g[b][i] = d < D ? a.g[row + d] : 0.f;
       }
-    }
-    const float H0 = -lp + 0.5f * dot(p, p);
-    const float logU = accept_log_uniform(a.seed, chain, a.t);
-    store(kSlotLeft, x); store(kSlotLeft + 1, p); store(kSlotLeft + 2, g);
-    store(kSlotRight, x); store(kSlotRight + 1, p); store(kSlotRight + 2, g);
-    store(kSlotCand, x); store(kSlotCand + 1, g);
-    float lp_end[2] = {lp, lp};     // [0]: left, [1]: right
-    float lpm = lp;
-    uint32_t n = 1;
+    unsigned long long leaves_total = 0ull;
     int moved = 0;
-    float a_sum = 0.f;
-    uint32_t n_a = 0;
-    const uint32_t dirs = word0(a.seed, 0u, chain, a.t, kTagDirection);
-    for (int jd = 0; jd < na.max_depth; ++jd) {
-      const int v = ((dirs >> jd) & 1u) ? 1 : -1;
-      const float ev = static_cast<float>(v) * eps;
-      const int side = v > 0 ? kSlotRight : kSlotLeft;
-      load(side, x); load(side + 1, p); load(side + 2, g);
-      lp = lp_end[v > 0 ? 1 : 0];
-      uint32_t n_sub = 0;
-      bool ok_sub = true;
-      float lps = 0.f;
-      const int leaves = 1 << jd;
-      for (int k = 0; k < leaves; ++k) {
-        // one leapfrog step of step v eps
+    for (int r = 0; r < na.T; ++r) {
+      const long long t_full = a.t_full + r;
+      const uint32_t t = static_cast<uint32_t>(t_full);
+      // start: p0 ~ N(0, I), H0, log U
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
+      for (int b = 0; b < NB; ++b) {
+        const int j = lane + 32 * b;
+        const float4 z = momentum4(a.seed, static_cast<uint32_t>(j), chain, t);
+        const float zz[4] = {z.x, z.y, z.z, z.w};
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            p[b][i] = fmaf(0.5f * ev, g[b][i], p[b][i]);
-            x[b][i] = fmaf(ev, p[b][i], x[b][i]);
+        for (int i = 0; i < 4; ++i) p[b][i] = 4 * j + i < D ? zz[i] : 0.f;
+      }
+      const float H0 = -lp + 0.5f * dot(p, p);
+      const float logU = accept_log_uniform(a.seed, chain, t);
+      store(kSlotLeft, x); store(kSlotLeft + 1, p); store(kSlotLeft + 2, g);
+      store(kSlotRight, x); store(kSlotRight + 1, p); store(kSlotRight + 2, g);
+      store(kSlotCand, x); store(kSlotCand + 1, g);
+      float lp_end[2] = {lp, lp};     // [0]: left, [1]: right
+      float lpm = lp;
+      uint32_t n = 1;
+      moved = 0;
+      float a_sum = 0.f;
+      uint32_t n_a = 0;
+      const uint32_t dirs = word0(a.seed, 0u, chain, t, kTagDirection);
+      for (int jd = 0; jd < na.max_depth; ++jd) {
+        const int v = ((dirs >> jd) & 1u) ? 1 : -1;
+        const float ev = static_cast<float>(v) * eps;
+        const float hv = 0.5f * ev;
+        const int side = v > 0 ? kSlotRight : kSlotLeft;
+        load(side, x); load(side + 1, p); load(side + 2, g);
+        lp = lp_end[v > 0 ? 1 : 0];
+        uint32_t n_sub = 0;
+        bool ok_sub = true;
+        float lps = 0.f;
+        const int leaves = 1 << jd;
+        for (int k = 0; k < leaves; ++k) {
+          // the subtree-choice word depends on nothing the leaf computes:
+          // drawn first, its arithmetic fills the butterfly's latency
+          const uint32_t wsub = word0(a.seed, static_cast<uint32_t>(k), chain, t, kTagSubtree + jd);
+          // spans of 2^i leaves closing at leaf k (2^i | k + 1); the span of
+          // two leaves (i = 1) is tested inside the leaf's butterfly
+          const int close = min(jd, __ffs(k + 1) - 1);
+          float xf[NB][4], pf[NB][4];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            xf[b][0] = xf[b][1] = xf[b][2] = xf[b][3] = 0.f;
+            pf[b][0] = pf[b][1] = pf[b][2] = pf[b][3] = 0.f;
+            if (close >= 1 && in_slot(b)) {
+              get(span4(0, b), xf, b);
+              get(span4(1, b), pf, b);
+            }
           }
-        lp = target();
+          // one leapfrog step of step v eps
 #pragma unroll
-        for (int b = 0; b < NB; ++b)
+          for (int b = 0; b < NB; ++b)
 #pragma unroll
-          for (int i = 0; i < 4; ++i) p[b][i] = fmaf(0.5f * ev, g[b][i], p[b][i]);
-        const float H = -lp + 0.5f * dot(p, p);
-        const bool finite = isfinite(H);
-        if (!finite || H - H0 >= kDeltaMax - logU) ok_sub = false;     // divergence
-        a_sum += finite ? accept_prob(H0 - H) : 0.f;
-        ++n_a;
-        if (finite && logU <= H0 - H) {
-          ++n_sub;
-          if (take(word0(a.seed, static_cast<uint32_t>(k), chain, a.t, kTagSubtree + jd), 1u, n_sub)) {
-            store(kSlotSub, x);
-            store(kSlotSub + 1, g);
-            lps = lp;
+            for (int i = 0; i < 4; ++i) {
+              p[b][i] = fmaf(hv, g[b][i], p[b][i]);
+              x[b][i] = fmaf(ev, p[b][i], x[b][i]);
+            }
+          float H;
+          bool turn;
+          lp = leaf_sums(hv, static_cast<float>(v), close >= 1, xf, pf, &H, &turn);
+          const bool finite = isfinite(H);
+          if (!finite || H - H0 >= kDeltaMax - logU) ok_sub = false;     // divergence
+          a_sum += finite ? accept_prob(H0 - H) : 0.f;
+          ++n_a;
+          if (finite && logU <= H0 - H) {
+            ++n_sub;
+            if (take(wsub, 1u, n_sub)) {
+              store(kSlotSub, x);
+              store(kSlotSub + 1, g);
+              lps = lp;
+            }
           }
-        }
-        // spans of 2^i leaves opening / closing at leaf k
-        for (int i = 1; i <= jd; ++i) {
-          const int span = 1 << i;
-          const int s = kSlotSpan + 2 * (i - 1);
-          if (k % span == 0) {
-            store(s, x);
-            store(s + 1, p);
+          if (turn) ok_sub = false;
+          // spans of 2^i leaves opening at leaf k (2^i | k); no span both
+          // opens and closes at one leaf
+          const int open = k == 0 ? jd : min(jd, __ffs(k) - 1);
+          for (int i = 1; i <= open; ++i) {
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+              if (in_slot(b)) {
+                put(span4(2 * (i - 1), b), x, b);
+                put(span4(2 * (i - 1) + 1, b), p, b);
+              }
           }
-          if ((k + 1) % span == 0) {
-            float xf[NB][4], pf[NB][4], dx[NB][4];
-            load(s, xf);
-            load(s + 1, pf);
+          for (int i = 2; i <= close && ok_sub; ++i) {
+            float dx[NB][4], pg[NB][4];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+              dx[b][0] = dx[b][1] = dx[b][2] = dx[b][3] = 0.f;
+              pg[b][0] = pg[b][1] = pg[b][2] = pg[b][3] = 0.f;
+              if (in_slot(b)) {
+                get(span4(2 * (i - 1), b), dx, b);
+                get(span4(2 * (i - 1) + 1, b), pg, b);
+              }
+            }
 #pragma unroll
             for (int b = 0; b < NB; ++b)
 #pragma unroll
-              for (int q = 0; q < 4; ++q) dx[b][q] = static_cast<float>(v) * (x[b][q] - xf[b][q]);
-            if (dot(dx, pf) < 0.f || dot(dx, p) < 0.f) ok_sub = false;
+              for (int q = 0; q < 4; ++q) dx[b][q] = static_cast<float>(v) * (x[b][q] - dx[b][q]);
+            if (u_turn(dx, pg, p)) ok_sub = false;
           }
+          if (!ok_sub) break;
         }
+        store(side, x); store(side + 1, p); store(side + 2, g);
+        lp_end[v > 0 ? 1 : 0] = lp;
         if (!ok_sub) break;
-      }
-      store(side, x); store(side + 1, p); store(side + 2, g);
-      lp_end[v > 0 ? 1 : 0] = lp;
-      if (!ok_sub) break;
-      if (n_sub > 0 && take(word0(a.seed, static_cast<uint32_t>(jd), chain, a.t, kTagTop), n_sub, n)) {
-        float t1[NB][4], t2[NB][4];
-        load(kSlotSub, t1);
-        load(kSlotSub + 1, t2);
-        store(kSlotCand, t1);
-        store(kSlotCand + 1, t2);
-        lpm = lps;
-        moved = 1;
-      }
-      n += n_sub;
-      // the whole trajectory's ends
-      float xl[NB][4], pl[NB][4], xr[NB][4], pr[NB][4];
-      load(kSlotLeft, xl); load(kSlotLeft + 1, pl);
-      load(kSlotRight, xr); load(kSlotRight + 1, pr);
+        if (n_sub > 0 && take(word0(a.seed, static_cast<uint32_t>(jd), chain, t, kTagTop), n_sub, n)) {
+          float t1[NB][4], t2[NB][4];
+          load(kSlotSub, t1);
+          load(kSlotSub + 1, t2);
+          store(kSlotCand, t1);
+          store(kSlotCand + 1, t2);
+          lpm = lps;
+          moved = 1;
+        }
+        n += n_sub;
+        // the whole trajectory's ends
+        float xl[NB][4], pl[NB][4], xr[NB][4], pr[NB][4];
+        load(kSlotLeft, xl); load(kSlotLeft + 1, pl);
+        load(kSlotRight, xr); load(kSlotRight + 1, pr);
 #pragma unroll
-      for (int b = 0; b < NB; ++b)
+        for (int b = 0; b < NB; ++b)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) xr[b][q] -= xl[b][q];
-      if (dot(xr, pl) < 0.f || dot(xr, pr) < 0.f) break;
+          for (int q = 0; q < 4; ++q) xr[b][q] -= xl[b][q];
+        if (u_turn(xr, pl, pr)) break;
+      }
+      // the new state
+      load(kSlotCand, x);
+      load(kSlotCand + 1, g);
+      lp = lpm;
+      prob = a_sum / static_cast<float>(n_a);
+      leaves_total += n_a;
+      const long long k = t_full - na.keep_from;
+      if (k >= 0) {
+        if (na.samples) {
+          float* out = na.samples + k * CD + row;
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int d = 4 * (lane + 32 * b) + i;
+              if (d < D) out[d] = x[b][i];
+            }
+        }
+        if (lane == 0) {
+          if (na.trace_acc) na.trace_acc[k * a.C + c] = static_cast<uint8_t>(moved);
+          if (c == 0 && na.trace_eps) na.trace_eps[k] = eps;
+        }
+      }
     }
-    // the new state
-    load(kSlotCand, x);
-    load(kSlotCand + 1, g);
 #pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      const int j = lane + 32 * b;
+    for (int b = 0; b < NB; ++b)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int d = 4 * j + i;
+        const int d = 4 * (lane + 32 * b) + i;
         if (d < D) {
           a.x[row + d] = x[b][i];
           a.g[row + d] = g[b][i];
-          if (a.sample_out) a.sample_out[row + d] = x[b][i];
         }
       }
-    }
-    prob = a_sum / static_cast<float>(n_a);
     if (lane == 0) {
-      a.lp[c] = lpm;
+      a.lp[c] = lp;
       a.is_accepted[c] = static_cast<uint8_t>(moved);
       a.log_accept[c] = logf(prob);
-      if (a.trace_acc) a.trace_acc[c] = static_cast<uint8_t>(moved);
-      if (c == 0 && a.trace_eps) a.trace_eps[0] = eps;
-      atomicAdd(na.leaves, static_cast<unsigned long long>(n_a));
+      atomicAdd(na.leaves, leaves_total);
     }
   }
-  accept_tile_finish<kWarps>(a.da, a.partials, prob, has_chain, a.C, a.t_full,
+  // the last transition's statistic (the only one that can adapt)
+  accept_tile_finish<kWarps>(a.da, a.partials, prob, has_chain, a.C, a.t_full + na.T - 1,
                              static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x));
+}
+
+template <int TARGET, int NB, bool SMEM>
+cudaError_t launch_v(const NutsArgs& na, size_t smem, cudaStream_t s) {
+  const unsigned grid = nuts_grid(na.s.C);
+  k_nuts<TARGET, NB, SMEM><<<grid, 32 * kWarps, SMEM ? smem : 0, s>>>(na);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int TARGET, int NB>
+cudaError_t launch_nb(const NutsArgs& na, cudaStream_t s) {
+  const size_t smem = span_smem_bytes(na.Dp, na.max_depth);
+  // shared-memory span starts unless they cost resident chains: as many
+  // blocks per SM as the scratch form, or enough for every chain
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return cudaErrorUnknown;
+  }
+  int occ_smem = 0, occ_glob = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &occ_glob, k_nuts<TARGET, NB, false>, 32 * kWarps, 0);
+  if (e == cudaSuccess && smem <= kNutsSpanSmemMax)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_smem, k_nuts<TARGET, NB, true>,
+                                                      32 * kWarps, smem);
+  if (e != cudaSuccess) return e;
+  const bool use_smem = smem > 0 && occ_smem > 0 &&
+                        (occ_smem >= occ_glob ||
+                         static_cast<int64_t>(occ_smem) * kWarps * sms >= na.s.C);
+  return use_smem ? launch_v<TARGET, NB, true>(na, smem, s) : launch_v<TARGET, NB, false>(na, 0, s);
 }
 
 template <int TARGET>
 cudaError_t launch_t(const NutsArgs& na, cudaStream_t s) {
-  const unsigned grid = static_cast<unsigned>((na.s.C + kWarps - 1) / kWarps);
   const int nb = (na.s.D + 127) / 128;
-  if (nb <= 1) k_nuts<TARGET, 1><<<grid, 32 * kWarps, 0, s>>>(na);
-  else if (nb == 2) k_nuts<TARGET, 2><<<grid, 32 * kWarps, 0, s>>>(na);
-  else k_nuts<TARGET, 4><<<grid, 32 * kWarps, 0, s>>>(na);
-  count_launch();
-  return cudaGetLastError();
+  if (nb <= 1) return launch_nb<TARGET, 1>(na, s);
+  if (nb == 2) return launch_nb<TARGET, 2>(na, s);
+  return launch_nb<TARGET, 4>(na, s);
+}
+
+template <int TARGET, int NB>
+cudaError_t allow_smem() {
+  return cudaFuncSetAttribute(k_nuts<TARGET, NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kNutsSpanSmemMax));
 }
 
 }  // namespace
@@ -281,14 +471,35 @@ size_t nuts_scratch_floats(const hmc_target& t, int64_t C) {
   return static_cast<size_t>(C) * kNutsSlots * ((t.dim + 3) / 4 * 4);
 }
 
-cudaError_t launch_nuts_transition(const hmc_target& t, const StepArgs& a, float* scratch,
-                                   int max_depth, unsigned long long* leaves, cudaStream_t s,
-                                   KernelTimer* timer) {
-  NutsArgs na{a, scratch, (t.dim + 3) / 4 * 4, max_depth, leaves};
+unsigned nuts_grid(int64_t C) { return static_cast<unsigned>((C + kWarps - 1) / kWarps); }
+
+cudaError_t nuts_prepare() {
+  cudaError_t e = allow_smem<HMC_T_STD_NORMAL, 1>();
+  if (e == cudaSuccess) e = allow_smem<HMC_T_STD_NORMAL, 2>();
+  if (e == cudaSuccess) e = allow_smem<HMC_T_STD_NORMAL, 4>();
+  if (e == cudaSuccess) e = allow_smem<HMC_T_FUNNEL, 1>();
+  if (e == cudaSuccess) e = allow_smem<HMC_T_FUNNEL, 2>();
+  if (e == cudaSuccess) e = allow_smem<HMC_T_FUNNEL, 4>();
+  return e;
+}
+
+cudaError_t launch_nuts_transitions(const hmc_target& t, const StepArgs& a, float* scratch,
+                                    int max_depth, unsigned long long* leaves, int T,
+                                    long long keep_from, float* samples, float* trace_eps,
+                                    uint8_t* trace_acc, cudaStream_t s, KernelTimer* timer) {
+  NutsArgs na{a, scratch, (t.dim + 3) / 4 * 4, max_depth, leaves, T, keep_from, samples, trace_eps,
+              trace_acc};
   if (timer) timer->begin(s);
   cudaError_t e = t.id == HMC_T_FUNNEL ? launch_t<HMC_T_FUNNEL>(na, s) : launch_t<HMC_T_STD_NORMAL>(na, s);
   if (timer) timer->end(s);
   return e;
+}
+
+cudaError_t launch_nuts_transition(const hmc_target& t, const StepArgs& a, float* scratch,
+                                   int max_depth, unsigned long long* leaves, cudaStream_t s,
+                                   KernelTimer* timer) {
+  return launch_nuts_transitions(t, a, scratch, max_depth, leaves, 1, a.t_full, a.sample_out,
+                                 a.trace_eps, a.trace_acc, s, timer);
 }
 
 }  // namespace hmc

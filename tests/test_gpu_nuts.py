@@ -34,9 +34,12 @@ def host(t):
 
 
 # (target, chains, dim, step size, max depth): a warp-tile, ragged dims, the
-# three register widths (dim <= 128, 256, 512)
+# three register widths (dim <= 128, 256, 512); span starts in shared memory
+# except the last case, whose 2 x 9 span rows of 500 floats per chain exceed
+# the shared-memory budget and live in the per-chain scratch
 CASES = [("std_normal", 64, 5, 0.3, 6), ("std_normal", 37, 130, 0.25, 5),
-         ("funnel", 40, 10, 0.1, 6), ("funnel", 19, 300, 0.03, 4)]
+         ("funnel", 40, 10, 0.1, 6), ("funnel", 19, 300, 0.03, 4),
+         ("std_normal", 21, 500, 0.08, 10)]
 
 # a decision closer than this (relative) to its threshold may go either way
 # in float32
@@ -128,3 +131,28 @@ def test_nuts_chain_samples_the_standard_normal(H):
     assert np.all(np.abs(xs.var(axis=0) - 1.0) < 5 * math.sqrt(2.0) * se)
     assert float(acc.float().mean()) > 0.5
     s.close()
+
+
+@pytest.mark.parametrize("adapt", [False, True], ids=["fixed", "adapted"])
+def test_multi_transition_launch_is_bit_identical(H, adapt):
+    """The transitions that do not adapt run in one launch (or launches of at
+    most max_transitions_per_launch): the same samples, traces, final state
+    and leapfrog count as one launch per transition."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    C, D, B, K = 150, 70, 12, 30
+    runs = []
+    for cap in (1, 7, 0):
+        p = workloads.funnel(dim=D, num_chains=C)
+        p.num_leapfrog, p.adapt, p.num_burnin, p.num_results = 6, adapt, B, K
+        p.step_size = 0.05
+        s = Sampler(p, adapt=adapt, proposal=H.HMC_PROPOSAL_NUTS, max_transitions_per_launch=cap)
+        x = dev(p.x0)
+        samples, eps, acc = s.sample_chain(x, B, K)
+        H.hmc_synchronize(s.ctx)
+        runs.append((host(samples), host(eps), host(acc), host(x), H.hmc_nuts_leapfrog_count(s.ctx)))
+        s.close()
+    for other in runs[1:]:
+        for u, w in zip(runs[0], other):
+            np.testing.assert_array_equal(u, w)
+    assert runs[0][2].any() and not runs[0][2].all()
+    assert np.unique(runs[0][0][:, 0, 0]).size > K // 2         # the chain moved
