@@ -190,7 +190,10 @@ hmc_status hmc_sample_chain_streaming(hmc_ctx* ctx, float* x_inout, int64_t num_
 /* Same as hmc_sample_chain with every argument in HOST memory (x_inout,
  * samples_out, trace buffers; pinned or pageable).  Copies the initial state
  * to the device, samples, copies the results back and synchronises the
- * context's stream before returning. */
+ * context's stream before returning.  When samples_out is pinned and holds
+ * at least 512 MiB, the kept samples are copied back in segments (at most
+ * 16, each at least 256 MiB) on a second stream while the later transitions
+ * run; the results are the same. */
 hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burnin,
                                  int64_t num_results, float* samples_out,
                                  float* trace_step_size, uint8_t* trace_accept);

@@ -36,6 +36,11 @@ struct hmc_ctx {
   // device staging for hmc_sample_chain_host, grown on demand
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  // hmc_sample_chain_host: kept samples leave on copy_stream, segment by
+  // segment, while the next segment's transitions run
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t seg_ready = nullptr;
+  cudaEvent_t copies_done = nullptr;
   std::vector<void*> allocations;
   hmc::KernelTimer timer;
   bool use_tc = false;          // tensor-core Gaussian path
@@ -74,6 +79,20 @@ struct hmc_ctx {
 namespace {
 
 thread_local std::string g_global_err;
+
+// kept-sample segments of hmc_sample_chain_host: at least this many bytes
+// each, at most this many segments
+constexpr size_t kSegmentBytes = 256ull << 20;
+constexpr int64_t kMaxSegments = 16;
+
+bool host_pinned(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
 
 hmc_status fail(hmc_ctx* ctx, hmc_status st, const std::string& msg) {
   if (ctx) ctx->err = msg;
@@ -166,6 +185,12 @@ void release(hmc_ctx* ctx) {
   drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   ctx->cap_stream = nullptr;
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  ctx->copy_stream = nullptr;
+  if (ctx->seg_ready) cudaEventDestroy(ctx->seg_ready);
+  ctx->seg_ready = nullptr;
+  if (ctx->copies_done) cudaEventDestroy(ctx->copies_done);
+  ctx->copies_done = nullptr;
   for (void* p : ctx->allocations) cudaFree(p);
   ctx->allocations.clear();
   if (ctx->stage) cudaFree(ctx->stage);
@@ -248,23 +273,23 @@ hmc_status bootstrap(hmc_ctx* ctx, const float* x0) {
   return HMC_OK;
 }
 
-hmc_status enqueue_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* samples, float* trace_eps,
-                     uint8_t* trace_acc) {
-  hmc_status st = bootstrap(ctx, x);
-  if (st != HMC_OK) return st;
+// Transitions t_begin .. t_end - 1 of a chain with B burn-in transitions
+// (transition B + k writes kept sample k), after the bootstrap.
+hmc_status enqueue_range(hmc_ctx* ctx, float* x, int64_t B, int64_t t_begin, int64_t t_end,
+                         float* samples, float* trace_eps, uint8_t* trace_acc) {
   const int64_t CD = ctx->C * ctx->target.dim;
   // dense Gaussian on CTA pairs: the chain's transitions in as few launches
   // as allowed (all of them in one cooperative launch by default)
   ctx->dom_transitions = 1;
-  const int64_t T = B + K;
+  const int64_t T = t_end - t_begin;
   const int64_t cap = ctx->cfg.max_transitions_per_launch > 0
                           ? std::min<int64_t>(ctx->cfg.max_transitions_per_launch, 1ll << 30)
                           : (1ll << 30);
-  const int64_t chunk = std::min(T, cap);
+  const int64_t chunk = std::min(std::max<int64_t>(T, 1), cap);
   if (ctx->use_tc && ctx->tc.pair && ctx->K == 1 && !ctx->s_mean && T > 0 &&
       (chunk == 1 || hmc::gauss_pair_persistent_ok(ctx->C))) {
-    for (int64_t t0 = 0; t0 < T; t0 += chunk) {
-      const int n = static_cast<int>(std::min(chunk, T - t0));
+    for (int64_t t0 = t_begin; t0 < t_end; t0 += chunk) {
+      const int n = static_cast<int>(std::min(chunk, t_end - t0));
       StepArgs a = make_args(ctx, x, static_cast<uint64_t>(t0));
       cudaError_t e = hmc::launch_gauss_pair_transitions(a, ctx->tc, n, B, samples, trace_eps, trace_acc,
                                                          ctx->grid_bar, ctx->stream, &ctx->timer);
@@ -276,10 +301,11 @@ hmc_status enqueue_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sa
   // NUTS: the transitions that do not adapt the step size run in as few
   // launches as allowed, so that each chain's tree sizes average out over
   // the run (those that adapt need every chain's statistic in between)
-  int64_t t_multi = T;
+  int64_t t_multi = t_end;
   if (ctx->cfg.proposal == HMC_PROPOSAL_NUTS && ctx->K == 1 && !ctx->s_mean)
-    t_multi = std::min<int64_t>(T, ctx->cfg.adapt ? std::max<int64_t>(ctx->cfg.num_adapt_steps, 0) : 0);
-  for (int64_t t = 0; t < t_multi; ++t) {
+    t_multi = std::min<int64_t>(
+        t_end, std::max<int64_t>(t_begin, ctx->cfg.adapt ? ctx->cfg.num_adapt_steps : 0));
+  for (int64_t t = t_begin; t < t_multi; ++t) {
     StepArgs a = make_args(ctx, x, static_cast<uint64_t>(t));
     const int64_t k = t - B;
     if (k >= 0) {
@@ -303,8 +329,8 @@ hmc_status enqueue_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sa
       if (e != cudaSuccess) return cuda_fail(ctx, e, "moment update launch");
     }
   }
-  for (int64_t t0 = t_multi; t0 < T; t0 += chunk) {
-    const int n = static_cast<int>(std::min(chunk, T - t0));
+  for (int64_t t0 = t_multi; t0 < t_end; t0 += chunk) {
+    const int n = static_cast<int>(std::min(chunk, t_end - t0));
     StepArgs a = make_args(ctx, x, static_cast<uint64_t>(t0));
     cudaError_t e = hmc::launch_nuts_transitions(ctx->target, a, ctx->nuts_scratch, ctx->cfg.num_leapfrog,
                                                  ctx->nuts_leaves, n, B, samples, trace_eps, trace_acc,
@@ -314,6 +340,13 @@ hmc_status enqueue_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sa
   return HMC_OK;
 }
 
+
+hmc_status enqueue_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* samples, float* trace_eps,
+                         uint8_t* trace_acc) {
+  hmc_status st = bootstrap(ctx, x);
+  if (st != HMC_OK) return st;
+  return enqueue_range(ctx, x, B, 0, B + K, samples, trace_eps, trace_acc);
+}
 
 // sample_chain as a CUDA graph: the first call with a given set of buffers
 // and step counts captures bootstrap + every transition on a private stream;
@@ -637,10 +670,43 @@ hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burni
   cudaStream_t s = ctx->stream;
   cudaError_t e = cudaMemcpyAsync(dx, x_inout, CD * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "state upload");
-  hmc_status st = run_chain(ctx, dx, num_burnin, num_results, ds, de, dacc);
-  if (st != HMC_OK) return st;
+  // Large sample sets bound for pinned host memory leave the device in
+  // segments of kept transitions, each copied on a second stream while the
+  // next segment runs; otherwise the whole chain (one CUDA graph) runs first.
+  const size_t sample_bytes = K * CD * sizeof(float);
+  int64_t nseg = 1;
+  if (ds && K > 1 && ctx->K == 1 && sample_bytes >= 2 * kSegmentBytes && host_pinned(samples_out))
+    nseg = std::min<int64_t>({kMaxSegments, static_cast<int64_t>(K),
+                              static_cast<int64_t>(sample_bytes / kSegmentBytes)});
+  if (nseg == 1) {
+    hmc_status st = run_chain(ctx, dx, num_burnin, num_results, ds, de, dacc);
+    if (st != HMC_OK) return st;
+  } else {
+    if (!ctx->copy_stream) e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->seg_ready) e = cudaEventCreateWithFlags(&ctx->seg_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess && !ctx->copies_done)
+      e = cudaEventCreateWithFlags(&ctx->copies_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy stream");
+    hmc_status st = bootstrap(ctx, dx);
+    if (st == HMC_OK) st = enqueue_range(ctx, dx, num_burnin, 0, num_burnin, ds, de, dacc);
+    for (int64_t i = 0; i < nseg && st == HMC_OK; ++i) {
+      const int64_t k0 = static_cast<int64_t>(K) * i / nseg, k1 = static_cast<int64_t>(K) * (i + 1) / nseg;
+      st = enqueue_range(ctx, dx, num_burnin, num_burnin + k0, num_burnin + k1, ds, de, dacc);
+      if (st != HMC_OK) break;
+      e = cudaEventRecord(ctx->seg_ready, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->seg_ready, 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(samples_out + k0 * CD, ds + k0 * CD, (k1 - k0) * CD * sizeof(float),
+                            cudaMemcpyDeviceToHost, ctx->copy_stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "sample download");
+    }
+    if (st != HMC_OK) return st;
+    e = cudaEventRecord(ctx->copies_done, ctx->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->copies_done, 0);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sample download");
+  }
   e = cudaMemcpyAsync(x_inout, dx, CD * sizeof(float), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && ds)
+  if (e == cudaSuccess && ds && nseg == 1)
     e = cudaMemcpyAsync(samples_out, ds, K * CD * sizeof(float), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && de)
     e = cudaMemcpyAsync(trace_step_size, de, K * sizeof(float), cudaMemcpyDeviceToHost, s);

@@ -236,6 +236,29 @@ def test_host_entry_point_equals_device_entry_point(H):
     s.close()
 
 
+def test_host_entry_point_segments_large_pinned_sample_sets(H):
+    """Kept samples of 629 MB bound for pinned host memory leave the device in
+    segments while the later transitions run: the same results as the device
+    entry point."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    B, K = 20, 150
+    p = workloads.corr_gauss(num_burnin=B, num_results=K)     # 4096 x 256 x 150 floats
+    s = Sampler(p)
+    x = dev(p.x0)
+    samples, eps, acc = s.sample_chain(x, B, K)
+    ref = [host(samples), host(eps), host(acc), host(x)]
+    del samples
+    xh = torch.from_numpy(p.x0.copy()).pin_memory()
+    sh = torch.empty((K, p.num_chains, p.dim), dtype=torch.float32, pin_memory=True)
+    eh = torch.empty(K, dtype=torch.float32, pin_memory=True)
+    ah = torch.empty((K, p.num_chains), dtype=torch.uint8, pin_memory=True)
+    H.hmc_sample_chain_host(s.ctx, xh, B, K, sh, eh, ah)
+    for got, want in zip((sh, eh, ah, xh), ref):
+        np.testing.assert_array_equal(got.numpy(), want)
+    assert ref[2].any() and not ref[2].all()
+    s.close()
+
+
 @pytest.mark.parametrize("C,D,L,B,K", [(1, 1, 1, 0, 3), (3, 5, 2, 2, 0), (9, 129, 1, 1, 2)])
 def test_edge_sizes(H, C, D, L, B, K):
     from paper_2002_01184_gb300.sampler import Sampler
