@@ -62,3 +62,30 @@ def mcse_mean(samples):
     n, C = s.shape[0], s.shape[1]
     flat = s.reshape(n * C, -1)
     return flat.std(axis=0, ddof=1) / np.sqrt(ess(s))
+
+
+def batch_means_ess(samples, batch_size):
+    """Batch-means effective sample size per state dimension for samples
+    [n, C, D] (the streaming-expectations driver's estimate, Section 4.2's
+    planned driver that keeps no trace).
+
+    Each chain's n draws are cut into nb = n // batch_size consecutive batches
+    of batch_size draws (a last partial batch is left out of the batch
+    means; every draw counts in the variance).  Per chain and dimension:
+      s2     = sample variance of the n draws (divisor n - 1),
+      sig2   = batch_size x sample variance of the nb batch means (divisor
+               nb - 1), the batch-means estimate of the asymptotic variance
+               of the chain mean times n (Geyer 1992, Section 3.2; Flegal and
+               Jones 2010).
+    Pooled over chains: ESS_d = C n mean_c(s2) / mean_c(sig2)."""
+    s = np.asarray(samples, dtype=np.float64)
+    n, C = s.shape[0], s.shape[1]
+    s = s.reshape(n, C, -1)
+    b = int(batch_size)
+    nb = n // b
+    if b < 1 or nb < 2:
+        raise ValueError("need batch_size >= 1 and at least two complete batches")
+    s2 = s.var(axis=0, ddof=1)                                     # [C, D]
+    bmeans = s[: nb * b].reshape(nb, b, C, -1).mean(axis=1)        # [nb, C, D]
+    sig2 = b * bmeans.var(axis=0, ddof=1)
+    return C * n * s2.mean(axis=0) / sig2.mean(axis=0)

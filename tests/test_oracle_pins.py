@@ -393,6 +393,44 @@ def test_ess_of_ar1_matches_closed_form():
     np.testing.assert_allclose(diagnostics.ess(z), n * C * (1 - phi) / (1 + phi), rtol=0.15)
 
 
+def test_batch_means_ess_worked_by_hand():
+    """One chain, draws 1, 3, 2, 6 in batches of 2: s2 = (4 + 0 + 1 + 9) / 3 =
+    14/3; batch means 2 and 4 (mean 3) have sample variance 2, so sig2 =
+    2 x 2 = 4 and ESS = 4 x (14/3) / 4 = 14/3.  A fifth draw beyond the last
+    complete batch enters s2 only: with 1, 3, 2, 6, 3 the draws have mean 3,
+    s2 = 14/4 = 3.5, and ESS = 5 x 3.5 / 4 = 4.375."""
+    z = np.array([1.0, 3.0, 2.0, 6.0]).reshape(4, 1, 1)
+    assert diagnostics.batch_means_ess(z, 2)[0] == pytest.approx(14.0 / 3.0, rel=1e-15)
+    z5 = np.array([1.0, 3.0, 2.0, 6.0, 3.0]).reshape(5, 1, 1)
+    assert diagnostics.batch_means_ess(z5, 2)[0] == pytest.approx(4.375, rel=1e-15)
+    with pytest.raises(ValueError):
+        diagnostics.batch_means_ess(z, 3)                # one complete batch
+
+
+def test_batch_means_ess_of_iid_draws_is_the_draw_count():
+    """Independent draws: sig2 estimates the variance itself; pooled over 200
+    chains of 20 batches the estimate's relative spread is about
+    sqrt(2 / (200 x 19)) = 2.3 %."""
+    z = np.random.default_rng(11).standard_normal((1000, 200, 2))
+    np.testing.assert_allclose(diagnostics.batch_means_ess(z, 50), 200 * 1000, rtol=0.1)
+
+
+def test_batch_means_ess_of_ar1_matches_closed_form():
+    """AR(1) with coefficient phi: the asymptotic variance is
+    (1 + phi) / (1 - phi) times the marginal variance, so ESS / (C n) ->
+    (1 - phi) / (1 + phi); batches of 400 draws (>> 1 / (1 - phi)) leave a
+    bias of order 2 phi / (b (1 - phi)^2) / 9 ~ 2 %."""
+    rng = np.random.default_rng(12)
+    phi, n, C = 0.8, 8000, 100
+    e = rng.standard_normal((n, C, 1))
+    z = np.empty_like(e)
+    z[0] = e[0] / math.sqrt(1 - phi * phi)
+    for t in range(1, n):
+        z[t] = phi * z[t - 1] + e[t]
+    np.testing.assert_allclose(diagnostics.batch_means_ess(z, 400), n * C * (1 - phi) / (1 + phi),
+                               rtol=0.1)
+
+
 def test_logreg_posterior_mean_is_near_truth():
     prob = workloads.logreg(n_data=2000, dim=6, num_chains=32, num_burnin=150, num_results=150)
     tgt = targets.make("logreg", X=prob.X, y=prob.y)
