@@ -70,9 +70,16 @@ struct hmc_ctx {
   uint64_t g_recorded = 0;      // timed event pairs inside the graph
   float* g_mean = nullptr;
   float* g_m2 = nullptr;
+  int64_t g_bsize = 0;
   // streaming-expectations outputs of the call in progress (null: none)
   float* s_mean = nullptr;
   float* s_m2 = nullptr;
+  // batch means of the streaming call in progress (s_bsize 0: none); the
+  // three [chains x dim] buffers are allocated on first use
+  int64_t s_bsize = 0;
+  float* bm_sum = nullptr;
+  float* bm_mean = nullptr;
+  float* bm_m2 = nullptr;
   std::string err;
 };
 
@@ -325,7 +332,8 @@ hmc_status enqueue_range(hmc_ctx* ctx, float* x, int64_t B, int64_t t_begin, int
       if (e != cudaSuccess) return cuda_fail(ctx, e, "exchange step");
     }
     if (k >= 0 && ctx->s_mean) {
-      e = hmc::launch_welford(CD, x, k, ctx->s_mean, ctx->s_m2, ctx->stream);
+      e = hmc::launch_welford(CD, x, k, ctx->s_mean, ctx->s_m2, ctx->s_bsize, ctx->bm_sum, ctx->bm_mean,
+                              ctx->bm_m2, ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "moment update launch");
     }
   }
@@ -356,7 +364,7 @@ hmc_status run_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sample
   if (!ctx->cfg.use_graph) return enqueue_chain(ctx, x, B, K, samples, trace_eps, trace_acc);
   const bool hit = ctx->graph && ctx->g_x == x && ctx->g_B == B && ctx->g_K == K &&
                    ctx->g_samples == samples && ctx->g_eps == trace_eps && ctx->g_acc == trace_acc &&
-                   ctx->g_mean == ctx->s_mean && ctx->g_m2 == ctx->s_m2;
+                   ctx->g_mean == ctx->s_mean && ctx->g_m2 == ctx->s_m2 && ctx->g_bsize == ctx->s_bsize;
   if (!hit) {
     drop_graph(ctx);
     cudaError_t e = cudaSuccess;
@@ -398,6 +406,7 @@ hmc_status run_chain(hmc_ctx* ctx, float* x, int64_t B, int64_t K, float* sample
     ctx->g_acc = trace_acc;
     ctx->g_mean = ctx->s_mean;
     ctx->g_m2 = ctx->s_m2;
+    ctx->g_bsize = ctx->s_bsize;
   }
   cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
@@ -633,6 +642,45 @@ hmc_status hmc_sample_chain_streaming(hmc_ctx* ctx, float* x_inout, int64_t num_
   ctx->s_mean = nullptr;
   ctx->s_m2 = nullptr;
   return st;
+}
+
+hmc_status hmc_sample_chain_streaming_ess(hmc_ctx* ctx, float* x_inout, int64_t num_burnin,
+                                          int64_t num_results, int64_t batch_size, float* mean_out,
+                                          float* m2_out, float* ess_out, float* trace_step_size,
+                                          uint8_t* trace_accept) {
+  if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
+  if (!x_inout || !mean_out || !m2_out || !ess_out)
+    return fail(ctx, HMC_E_INVALID, "x_inout, mean_out, m2_out and ess_out must be non-NULL");
+  if (num_burnin < 0 || num_results < 0) return fail(ctx, HMC_E_INVALID, "negative step count");
+  if (num_burnin + num_results > static_cast<int64_t>(std::numeric_limits<uint32_t>::max()))
+    return fail(ctx, HMC_E_INVALID, "too many transitions (transition index is 32-bit)");
+  if (batch_size < 1 || num_results / batch_size < 2)
+    return fail(ctx, HMC_E_INVALID, "need batch_size >= 1 and at least two complete batches");
+  if (ctx->K > 1)
+    return fail(ctx, HMC_E_UNSUPPORTED, "batch-means ESS pools the chains of one target, not a replica set");
+  const size_t CD = static_cast<size_t>(ctx->C) * ctx->target.dim;
+  cudaError_t e = cudaSuccess;
+  if (!ctx->bm_sum) e = ctx_alloc(ctx, &ctx->bm_sum, CD);
+  if (e == cudaSuccess && !ctx->bm_mean) e = ctx_alloc(ctx, &ctx->bm_mean, CD);
+  if (e == cudaSuccess && !ctx->bm_m2) e = ctx_alloc(ctx, &ctx->bm_m2, CD);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, e == cudaErrorMemoryAllocation ? HMC_E_OOM : HMC_E_CUDA,
+                std::string("batch-means workspace: ") + cudaGetErrorString(e));
+  }
+  ctx->s_mean = mean_out;
+  ctx->s_m2 = m2_out;
+  ctx->s_bsize = batch_size;
+  hmc_status st = run_chain(ctx, x_inout, num_burnin, num_results, nullptr, trace_step_size,
+                            trace_accept);
+  ctx->s_mean = nullptr;
+  ctx->s_m2 = nullptr;
+  ctx->s_bsize = 0;
+  if (st != HMC_OK) return st;
+  e = hmc::launch_bm_ess(ctx->C, ctx->target.dim, num_results, batch_size, m2_out, ctx->bm_m2, ess_out,
+                         ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch-means ESS launch");
+  return HMC_OK;
 }
 
 hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burnin,

@@ -164,7 +164,9 @@ cudaError_t launch_remc_swap(int64_t chains, int K, int D, float* x, float* lp, 
                              const float* betas, uint64_t seed, uint32_t t, uint8_t* swapped,
                              cudaStream_t s);
 cudaError_t launch_welford(int64_t n, const float* x, int64_t k, float* mean, float* m2,
-                           cudaStream_t s);
+                           int64_t bsize, float* bsum, float* bmean, float* bm2, cudaStream_t s);
+cudaError_t launch_bm_ess(int64_t C, int D, int64_t K, int64_t bsize, const float* m2, const float* bm2,
+                          float* ess, cudaStream_t s);
 cudaError_t launch_da_init(DAState* da, float eps0, int adapt, float delta, long long num_adapt,
                            cudaStream_t s);
 

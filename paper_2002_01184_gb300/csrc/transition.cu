@@ -314,10 +314,19 @@ cudaError_t launch_momentum(uint64_t seed, uint32_t t, int C, int D, uint32_t ch
 
 // Welford's running mean and sum of squared deviations (Welford 1962), one
 // element per thread: after kept draws 0..k, mean is their mean and m2 the
-// sum of squared deviations from it.
+// sum of squared deviations from it.  With bsize > 0 the draws also form
+// consecutive batches of bsize: bsum accumulates the current batch, and at
+// a batch's last draw its mean enters a second Welford recursion over batch
+// means (bmean, bm2).
 __global__ void k_welford(int64_t n, const float* __restrict__ x, int64_t k, float* __restrict__ mean,
-                          float* __restrict__ m2) {
+                          float* __restrict__ m2, int64_t bsize, float* __restrict__ bsum,
+                          float* __restrict__ bmean, float* __restrict__ bm2) {
   const float inv = 1.0f / static_cast<float>(k + 1);
+  const int64_t pos = bsize > 0 ? k % bsize : 0;
+  const int64_t batch = bsize > 0 ? k / bsize : 0;
+  const bool closes = bsize > 0 && pos == bsize - 1;
+  const float inv_b = bsize > 0 ? 1.0f / static_cast<float>(bsize) : 0.f;
+  const float inv_j = 1.0f / static_cast<float>(batch + 1);
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const float v = x[i];
@@ -331,13 +340,67 @@ __global__ void k_welford(int64_t n, const float* __restrict__ x, int64_t k, flo
       mean[i] = m1;
       m2[i] = fmaf(delta, v - m1, m2[i]);
     }
+    if (bsize > 0) {
+      const float sum = pos == 0 ? v : bsum[i] + v;
+      bsum[i] = sum;
+      if (closes) {
+        const float bm = sum * inv_b;
+        if (batch == 0) {
+          bmean[i] = bm;
+          bm2[i] = 0.f;
+        } else {
+          const float b0 = bmean[i];
+          const float delta = bm - b0;
+          const float b1 = fmaf(delta, inv_j, b0);
+          bmean[i] = b1;
+          bm2[i] = fmaf(delta, bm - b1, bm2[i]);
+        }
+      }
+    }
   }
 }
 
 cudaError_t launch_welford(int64_t n, const float* x, int64_t k, float* mean, float* m2,
-                           cudaStream_t s) {
+                           int64_t bsize, float* bsum, float* bmean, float* bm2, cudaStream_t s) {
   k_welford<<<static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 152 * 16)), 256, 0, s>>>(
-      n, x, k, mean, m2);
+      n, x, k, mean, m2, bsize, bsum, bmean, bm2);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Batch-means effective sample size per dimension, pooled over chains:
+// ess[d] = C K (sum_c m2 / (K - 1)) / (bsize sum_c bm2 / (nb - 1)).  A block
+// covers 32 dimensions (one per lane, coalesced rows) with its 8 warps
+// striding over chains; sums in float64.
+__global__ void __launch_bounds__(256) k_bm_ess(int64_t C, int D, int64_t K, int64_t bsize,
+                                                const float* __restrict__ m2,
+                                                const float* __restrict__ bm2, float* __restrict__ ess) {
+  __shared__ double w_s[8][32], v_s[8][32];
+  const int d = blockIdx.x * 32 + threadIdx.x;
+  double w = 0.0, v = 0.0;
+  if (d < D)
+    for (int64_t c = threadIdx.y; c < C; c += 8) {
+      w += static_cast<double>(m2[c * D + d]);
+      v += static_cast<double>(bm2[c * D + d]);
+    }
+  w_s[threadIdx.y][threadIdx.x] = w;
+  v_s[threadIdx.y][threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.y == 0 && d < D) {
+    for (int y = 1; y < 8; ++y) {
+      w += w_s[y][threadIdx.x];
+      v += v_s[y][threadIdx.x];
+    }
+    const double nb = static_cast<double>(K / bsize);
+    const double s2 = w / static_cast<double>(K - 1);
+    const double sig2 = static_cast<double>(bsize) * v / (nb - 1.0);
+    ess[d] = static_cast<float>(static_cast<double>(C) * static_cast<double>(K) * s2 / sig2);
+  }
+}
+
+cudaError_t launch_bm_ess(int64_t C, int D, int64_t K, int64_t bsize, const float* m2, const float* bm2,
+                          float* ess, cudaStream_t s) {
+  k_bm_ess<<<static_cast<unsigned>((D + 31) / 32), dim3(32, 8), 0, s>>>(C, D, K, bsize, m2, bm2, ess);
   count_launch();
   return cudaGetLastError();
 }

@@ -87,6 +87,8 @@ def _load():
                                    ctypes.POINTER(P), ctypes.POINTER(P)],
         "hmc_batch_destroy": [P],
         "hmc_sample_chain_streaming": [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P, P],
+        "hmc_sample_chain_streaming_ess": [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P, P,
+                                           P, P, P],
         "hmc_dominant_kernel_info": [P, ctypes.c_char_p, ctypes.c_int32,
                                      ctypes.POINTER(ctypes.c_int64)],
         "hmc_target_vjp_workspace_bytes": [ctypes.POINTER(hmc_target), ctypes.c_int64,
@@ -309,6 +311,14 @@ def hmc_sample_chain_streaming(ctx, x_inout, num_burnin, num_results, mean_out, 
     _check(lib.hmc_sample_chain_streaming(ctx, _ptr(x_inout), int(num_burnin), int(num_results),
                                           _ptr(mean_out), _ptr(m2_out), _ptr(trace_step_size),
                                           _ptr(trace_accept)), ctx)
+
+
+def hmc_sample_chain_streaming_ess(ctx, x_inout, num_burnin, num_results, batch_size, mean_out,
+                                   m2_out, ess_out, trace_step_size=None, trace_accept=None):
+    _check(lib.hmc_sample_chain_streaming_ess(ctx, _ptr(x_inout), int(num_burnin), int(num_results),
+                                              int(batch_size), _ptr(mean_out), _ptr(m2_out),
+                                              _ptr(ess_out), _ptr(trace_step_size),
+                                              _ptr(trace_accept)), ctx)
 
 
 def _check_batch(status, batch):
