@@ -50,6 +50,8 @@ NUTS_MAX_DEPTH = 10
 NUTS_LABEL = " NUTS max_depth=10"
 NUTS_FLOPS_PER_DIM = 15
 
+L2_FLUSH_BYTES = 256 << 20
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -67,6 +69,9 @@ def parse():
     ap.add_argument("--max-transitions-per-launch", type=int, default=0,
                     help="dense Gaussian: cap on transitions per kernel launch (0: whole chain; "
                          "1 for profilers that cannot replay cooperative cluster launches)")
+    ap.add_argument("--streaming", type=int, default=0, metavar="BATCH",
+                    help="streaming driver: running moments and batch-means ESS (batches of BATCH "
+                         "kept draws) on the device instead of the kept-sample trace")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -397,13 +402,23 @@ def main():
     C, D, K, B = p.num_chains, p.dim, p.num_results, p.num_burnin
     x0 = torch.as_tensor(p.x0).cuda()
     x = torch.empty_like(x0)
-    samples = torch.empty((K, C, D), dtype=torch.float32, device="cuda")
+    streaming = args.streaming > 0
+    samples = None if streaming else torch.empty((K, C, D), dtype=torch.float32, device="cuda")
     eps = torch.empty(K, dtype=torch.float32, device="cuda")
     acc = torch.empty((K, C), dtype=torch.uint8, device="cuda")
+    if streaming:
+        wl += f" (streaming: moments + batch-means ESS, batches of {args.streaming})"
+        mean, m2 = torch.empty_like(x0), torch.empty_like(x0)
+        ess_d = torch.empty(D, dtype=torch.float32, device="cuda")
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def step():
         x.copy_(x0)
-        hmc.hmc_sample_chain(s.ctx, x, B, K, samples, eps, acc)
+        if streaming:
+            flush.zero_()            # no trace is written: flush L2 explicitly
+            hmc.hmc_sample_chain_streaming_ess(s.ctx, x, B, K, args.streaming, mean, m2, ess_d, eps, acc)
+        else:
+            hmc.hmc_sample_chain(s.ctx, x, B, K, samples, eps, acc)
 
     hmc.hmc_profile_dominant_kernel(s.ctx, 8)      # before the graph is captured
     for _ in range(args.warmup):
@@ -445,7 +460,7 @@ def main():
     value = total_evals / (ms / 1000.0)
 
     # min-ESS/s of the last step's kept draws (not timed)
-    ess = diagnostics.ess(samples, max_dims=64)
+    ess = ess_d.double().cpu().numpy() if streaming else diagnostics.ess(samples, max_dims=64)
     min_ess = float(ess.min())
     min_ess_per_s = min_ess / (ms_per_step / 1000.0) * world
 
@@ -509,7 +524,24 @@ def main():
                     "peak_source": src, **common}
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and streaming:
+        # host state in, moments / ESS / traces out, through pinned buffers
+        xh = torch.as_tensor(p.x0).pin_memory()
+        outs = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in (x, mean, m2, ess_d, eps, acc)]
+        n_e2e = max(1, min(args.steps, 2))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            x.copy_(xh, non_blocking=True)
+            hmc.hmc_sample_chain_streaming_ess(s.ctx, x, B, K, args.streaming, mean, m2, ess_d, eps, acc)
+            for o, t in zip(outs, (x, mean, m2, ess_d, eps, acc)):
+                o.copy_(t, non_blocking=True)
+            torch.cuda.synchronize()
+        el = (time.perf_counter() - t0) / n_e2e
+        e2e = {"value": world * evals_per_step / el, "unit": "grad-evals/s",
+               "h2d_bytes_per_step": C * D * 4,
+               "d2h_bytes_per_step": sum(o.numel() * o.element_size() for o in outs),
+               "ms_per_step": 1000.0 * el}
+    elif not args.no_e2e:
         xh = torch.empty((C, D), dtype=torch.float32, pin_memory=True)
         sh = torch.empty((K, C, D), dtype=torch.float32, pin_memory=True)
         eh = torch.empty(K, dtype=torch.float32, pin_memory=True)
@@ -544,8 +576,11 @@ def main():
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl, "impl": "plain" if args.plain else "fused",
-                       "chains": C, "dim": D, "l2": "each step writes its 8.4 GB kept-sample "
-                       "buffer (> 129 MB L2), which flushes L2 between steps",
+                       "chains": C, "dim": D,
+                       "l2": ("each step first writes a 256 MB buffer (> 129 MB L2)" if streaming else
+                              f"each step writes its {K * C * D * 4 / 1e9:.1f} GB kept-sample buffer "
+                              "(> 129 MB L2), which flushes L2 between steps"),
+                       "min_ess_estimator": "batch means (device)" if streaming else "BDA3 / Geyer (host, after the run)",
                        "parallelism": f"replicas x{world}",
                        "transitions_per_launch": args.max_transitions_per_launch or "all"},
             "min_ess_per_s": min_ess_per_s, "min_ess": min_ess,

@@ -188,18 +188,22 @@ hmc_status hmc_sample_chain_streaming(hmc_ctx* ctx, float* x_inout, int64_t num_
                                       float* trace_step_size, uint8_t* trace_accept);
 
 /* The streaming driver with batch-means effective sample sizes (Section
- * 4.2's trace-free driver; the estimator is Geyer 1992's batch means, as in
- * Flegal and Jones 2010): as hmc_sample_chain_streaming, and the kept draws of
- * every chain are also cut into nb = num_results / batch_size consecutive
- * batches of batch_size draws (a last partial batch is left out of the batch
- * means).  ess_out (device, [dim], caller-owned) receives, per dimension,
+ * 4.2's trace-free driver; the estimator is the replicated batch means of
+ * Gupta and Vats 2020, batch means after Geyer 1992): as
+ * hmc_sample_chain_streaming, and the kept draws of every chain are also cut
+ * into nb = num_results / batch_size consecutive batches of batch_size draws
+ * (a last partial batch is left out of the batch means).  ess_out (device,
+ * [dim], caller-owned) receives, per dimension,
  *   chains x num_results x W / V,
  * W = mean over chains of m2 / (num_results - 1) (the sample variance),
- * V = mean over chains of batch_size x the sample variance of the chain's nb
- * batch means (divisor nb - 1).  A dimension whose batch means never vary
- * gets +inf (NaN if nothing varies).  Needs batch_size >= 1 and nb >= 2
- * (else HMC_E_INVALID); replica sets (hmc_remc_create) are HMC_E_UNSUPPORTED.
- * The context allocates 3 x chains x dim floats of workspace on first use. */
+ * V = batch_size x the sum over all chains' batches of (batch mean - grand
+ * mean of the batch means)^2 / (chains x nb - 1).  batch_size = num_results
+ * (one batch per chain) makes V the spread of the chain means across chains,
+ * which also sees autocorrelation longer than any batch.  A dimension whose
+ * batch means never vary gets +inf (NaN if nothing varies).  Needs
+ * batch_size >= 1, nb >= 1 and chains x nb >= 2 (else HMC_E_INVALID);
+ * replica sets (hmc_remc_create) are HMC_E_UNSUPPORTED.  The context
+ * allocates 3 x chains x dim floats of workspace on first use. */
 hmc_status hmc_sample_chain_streaming_ess(hmc_ctx* ctx, float* x_inout, int64_t num_burnin,
                                           int64_t num_results, int64_t batch_size, float* mean_out,
                                           float* m2_out, float* ess_out, float* trace_step_size,

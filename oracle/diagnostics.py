@@ -65,27 +65,32 @@ def mcse_mean(samples):
 
 
 def batch_means_ess(samples, batch_size):
-    """Batch-means effective sample size per state dimension for samples
-    [n, C, D] (the streaming-expectations driver's estimate, Section 4.2's
-    planned driver that keeps no trace).
+    """Replicated batch-means effective sample size per state dimension for
+    samples [n, C, D] (the streaming-expectations driver's estimate, Section
+    4.2's planned driver that keeps no trace).
 
     Each chain's n draws are cut into nb = n // batch_size consecutive batches
-    of batch_size draws (a last partial batch is left out of the batch
-    means; every draw counts in the variance).  Per chain and dimension:
-      s2     = sample variance of the n draws (divisor n - 1),
-      sig2   = batch_size x sample variance of the nb batch means (divisor
-               nb - 1), the batch-means estimate of the asymptotic variance
-               of the chain mean times n (Geyer 1992, Section 3.2; Flegal and
-               Jones 2010).
-    Pooled over chains: ESS_d = C n mean_c(s2) / mean_c(sig2)."""
+    of batch_size draws (a last partial batch is left out of the batch means;
+    every draw counts in the variance).  The C nb batch means are pooled
+    about their grand mean (Gupta and Vats 2020, replicated batch means;
+    batch means after Geyer 1992):
+      W    = mean over chains of the sample variance of the chain's n draws
+             (divisor n - 1),
+      sig2 = batch_size x sum over chains and batches of (batch mean - grand
+             mean)^2 / (C nb - 1), the estimate of n x the variance of a
+             chain mean,
+      ESS  = C n W / sig2.
+    batch_size = n makes one batch per chain: the spread of the chain means
+    across chains estimates the variance directly."""
     s = np.asarray(samples, dtype=np.float64)
     n, C = s.shape[0], s.shape[1]
     s = s.reshape(n, C, -1)
     b = int(batch_size)
-    nb = n // b
-    if b < 1 or nb < 2:
-        raise ValueError("need batch_size >= 1 and at least two complete batches")
-    s2 = s.var(axis=0, ddof=1)                                     # [C, D]
+    nb = n // b if b >= 1 else 0
+    if b < 1 or nb < 1 or C * nb < 2:
+        raise ValueError("need batch_size >= 1, one complete batch and at least two batches in all")
+    W = s.var(axis=0, ddof=1).mean(axis=0)                         # [D]
     bmeans = s[: nb * b].reshape(nb, b, C, -1).mean(axis=1)        # [nb, C, D]
-    sig2 = b * bmeans.var(axis=0, ddof=1)
-    return C * n * s2.mean(axis=0) / sig2.mean(axis=0)
+    grand = bmeans.mean(axis=(0, 1))
+    sig2 = b * ((bmeans - grand) ** 2).sum(axis=(0, 1)) / (C * nb - 1)
+    return C * n * W / sig2

@@ -293,11 +293,14 @@ hmc_status enqueue_range(hmc_ctx* ctx, float* x, int64_t B, int64_t t_begin, int
                           ? std::min<int64_t>(ctx->cfg.max_transitions_per_launch, 1ll << 30)
                           : (1ll << 30);
   const int64_t chunk = std::min(std::max<int64_t>(T, 1), cap);
-  if (ctx->use_tc && ctx->tc.pair && ctx->K == 1 && !ctx->s_mean && T > 0 &&
+  // (the streaming driver's moments are updated inside the launch)
+  if (ctx->use_tc && ctx->tc.pair && ctx->K == 1 && T > 0 &&
       (chunk == 1 || hmc::gauss_pair_persistent_ok(ctx->C))) {
     for (int64_t t0 = t_begin; t0 < t_end; t0 += chunk) {
       const int n = static_cast<int>(std::min(chunk, t_end - t0));
       StepArgs a = make_args(ctx, x, static_cast<uint64_t>(t0));
+      if (ctx->s_mean)
+        a.w = hmc::WelfordOut{ctx->s_mean, ctx->s_m2, ctx->s_bsize, ctx->bm_sum, ctx->bm_mean, ctx->bm_m2};
       cudaError_t e = hmc::launch_gauss_pair_transitions(a, ctx->tc, n, B, samples, trace_eps, trace_acc,
                                                          ctx->grid_bar, ctx->stream, &ctx->timer);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "pair transition launch");
@@ -654,8 +657,9 @@ hmc_status hmc_sample_chain_streaming_ess(hmc_ctx* ctx, float* x_inout, int64_t 
   if (num_burnin < 0 || num_results < 0) return fail(ctx, HMC_E_INVALID, "negative step count");
   if (num_burnin + num_results > static_cast<int64_t>(std::numeric_limits<uint32_t>::max()))
     return fail(ctx, HMC_E_INVALID, "too many transitions (transition index is 32-bit)");
-  if (batch_size < 1 || num_results / batch_size < 2)
-    return fail(ctx, HMC_E_INVALID, "need batch_size >= 1 and at least two complete batches");
+  if (batch_size < 1 || num_results / batch_size < 1 || ctx->C * (num_results / batch_size) < 2)
+    return fail(ctx, HMC_E_INVALID,
+                "need batch_size >= 1, one complete batch per chain and at least two batches in all");
   if (ctx->K > 1)
     return fail(ctx, HMC_E_UNSUPPORTED, "batch-means ESS pools the chains of one target, not a replica set");
   const size_t CD = static_cast<size_t>(ctx->C) * ctx->target.dim;
@@ -677,8 +681,8 @@ hmc_status hmc_sample_chain_streaming_ess(hmc_ctx* ctx, float* x_inout, int64_t 
   ctx->s_m2 = nullptr;
   ctx->s_bsize = 0;
   if (st != HMC_OK) return st;
-  e = hmc::launch_bm_ess(ctx->C, ctx->target.dim, num_results, batch_size, m2_out, ctx->bm_m2, ess_out,
-                         ctx->stream);
+  e = hmc::launch_bm_ess(ctx->C, ctx->target.dim, num_results, batch_size, m2_out, ctx->bm_mean,
+                         ctx->bm_m2, ess_out, ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "batch-means ESS launch");
   return HMC_OK;
 }

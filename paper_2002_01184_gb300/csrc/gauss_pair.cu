@@ -560,6 +560,9 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       }
       // the accepted state (gradient from the accumulators) and the kept sample
       float* samp = (k_out >= 0 && fa.samples) ? fa.samples + k_out * static_cast<int64_t>(C) * D : nullptr;
+      // streaming driver: running moments of the kept states instead of a trace
+      const bool moments = k_out >= 0 && a.w.mean != nullptr;
+      const WelfordCoef wq = welford_coef(k_out > 0 ? k_out : 0, a.w.bsize);
 #pragma unroll
       for (int cb = 0; cb < kHalf / 16; ++cb) {
         float accv[16];
@@ -574,6 +577,22 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
             }
             if (samp) samp[static_cast<int64_t>(pair_base + h * kHalf + i) * D + d] = xrow[i * 128];
           }
+        }
+      }
+      if (moments && ok) {
+#pragma unroll 1
+        for (int i0 = 0; i0 < kHalf; i0 += 8) {
+          int64_t e[8];
+          float v[8];
+          uint32_t valid = 0u;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k;
+            e[k] = static_cast<int64_t>(pair_base + h * kHalf + i) * D + d;
+            v[k] = xrow[i * 128];
+            if (i < nvalid) valid |= 1u << k;
+          }
+          welford_update_n<8>(a.w, wq, k_out, e, v, valid);
         }
       }
       // dual averaging over all chains of the posterior

@@ -229,6 +229,116 @@ __device__ __forceinline__ void accept_block_finish(DAState* da, double* partial
                              static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x));
 }
 
+// Welford's running mean and sum of squared deviations (Welford 1962) of the
+// kept draws 0..k of one element, and, with bsize > 0, the same recursion
+// over the means of consecutive batches of bsize draws (bsum accumulates
+// the current batch; at its last draw the batch mean enters bmean / bm2).
+// The per-draw constants are formed once per kept transition.
+struct WelfordCoef {
+  float inv, inv_b, inv_j;
+  int64_t pos, batch;
+  bool closes;
+};
+
+__device__ __forceinline__ WelfordCoef welford_coef(int64_t k, int64_t bsize) {
+  WelfordCoef q;
+  q.inv = 1.0f / static_cast<float>(k + 1);
+  q.pos = bsize > 0 ? k % bsize : 0;
+  q.batch = bsize > 0 ? k / bsize : 0;
+  q.closes = bsize > 0 && q.pos == bsize - 1;
+  q.inv_b = bsize > 0 ? 1.0f / static_cast<float>(bsize) : 0.f;
+  q.inv_j = 1.0f / static_cast<float>(q.batch + 1);
+  return q;
+}
+
+template <typename W>
+__device__ __forceinline__ void welford_update(const W& w, const WelfordCoef& q, int64_t k, int64_t i,
+                                               float v) {
+  if (k == 0) {
+    w.mean[i] = v;
+    w.m2[i] = 0.f;
+  } else {
+    const float m0 = w.mean[i];
+    const float delta = v - m0;
+    const float m1 = fmaf(delta, q.inv, m0);
+    w.mean[i] = m1;
+    w.m2[i] = fmaf(delta, v - m1, w.m2[i]);
+  }
+  if (w.bsize > 0) {
+    const float sum = q.pos == 0 ? v : w.bsum[i] + v;
+    w.bsum[i] = sum;
+    if (q.closes) {
+      const float bm = sum * q.inv_b;
+      if (q.batch == 0) {
+        w.bmean[i] = bm;
+        w.bm2[i] = 0.f;
+      } else {
+        const float b0 = w.bmean[i];
+        const float delta = bm - b0;
+        const float b1 = fmaf(delta, q.inv_j, b0);
+        w.bmean[i] = b1;
+        w.bm2[i] = fmaf(delta, bm - b1, w.bm2[i]);
+      }
+    }
+  }
+}
+
+// welford_update for N elements with every load issued before any store, so
+// that the N read-modify-writes overlap instead of each waiting for its
+// predecessor's stores (the compiler cannot tell that the elements' arrays
+// do not alias).  Element j is skipped unless bit j of `valid` is set.
+template <int N, typename W>
+__device__ __forceinline__ void welford_update_n(const W& w, const WelfordCoef& q, int64_t k,
+                                                 const int64_t (&idx)[N], const float (&v)[N],
+                                                 uint32_t valid) {
+  float m0[N], s0[N], b0[N], bm0[N], bs0[N];
+  const bool batches = w.bsize > 0;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    m0[j] = s0[j] = b0[j] = bm0[j] = bs0[j] = 0.f;
+    if (!((valid >> j) & 1u)) continue;
+    if (k > 0) {
+      m0[j] = w.mean[idx[j]];
+      s0[j] = w.m2[idx[j]];
+    }
+    if (batches && q.pos != 0) b0[j] = w.bsum[idx[j]];
+    if (batches && q.closes && q.batch > 0) {
+      bm0[j] = w.bmean[idx[j]];
+      bs0[j] = w.bm2[idx[j]];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (!((valid >> j) & 1u)) continue;
+    const float x = v[j];
+    if (k == 0) {
+      w.mean[idx[j]] = x;
+      w.m2[idx[j]] = 0.f;
+    } else {
+      const float delta = x - m0[j];
+      const float m1 = fmaf(delta, q.inv, m0[j]);
+      w.mean[idx[j]] = m1;
+      w.m2[idx[j]] = fmaf(delta, x - m1, s0[j]);
+    }
+    if (batches) {
+      const float sum = q.pos == 0 ? x : b0[j] + x;
+      w.bsum[idx[j]] = sum;
+      if (q.closes) {
+        const float bm = sum * q.inv_b;
+        if (q.batch == 0) {
+          w.bmean[idx[j]] = bm;
+          w.bm2[idx[j]] = 0.f;
+        } else {
+          const float delta = bm - bm0[j];
+          const float b1 = fmaf(delta, q.inv_j, bm0[j]);
+          w.bmean[idx[j]] = b1;
+          w.bm2[idx[j]] = fmaf(delta, bm - b1, bs0[j]);
+        }
+      }
+    }
+  }
+}
+
 // Split x into its tf32 head (10 explicit mantissa bits) and the exact float32
 // remainder: x = hi + lo exactly.  Used by the 3xTF32 products.
 __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {

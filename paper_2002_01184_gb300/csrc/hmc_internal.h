@@ -77,6 +77,18 @@ namespace hmc {
 
 struct DAState;
 
+// Running moments of the kept states (the streaming driver), all [C x D]:
+// Welford mean / m2 and, with bsize > 0, batch means -- bsum of the current
+// batch and a Welford bmean / bm2 over completed batches.  mean null: off.
+struct WelfordOut {
+  float* mean;
+  float* m2;
+  int64_t bsize;
+  float* bsum;
+  float* bmean;
+  float* bm2;
+};
+
 // Arguments shared by the transition kernels.  x, lp, g are the current state
 // and its cached log-prob / gradient (updated in place on acceptance).
 struct StepArgs {
@@ -98,6 +110,7 @@ struct StepArgs {
   const float* betas;     // replica exchange: row r targets p^betas[r % K]; null = 1
   int K;                  // replicas per chain (1: no tempering)
   int proposal;           // hmc_proposal_kind
+  WelfordOut w;           // the pair kernel updates these at kept transitions (streaming)
 };
 
 // Scratch of the plain (one launch per operation) transition.
@@ -165,8 +178,8 @@ cudaError_t launch_remc_swap(int64_t chains, int K, int D, float* x, float* lp, 
                              cudaStream_t s);
 cudaError_t launch_welford(int64_t n, const float* x, int64_t k, float* mean, float* m2,
                            int64_t bsize, float* bsum, float* bmean, float* bm2, cudaStream_t s);
-cudaError_t launch_bm_ess(int64_t C, int D, int64_t K, int64_t bsize, const float* m2, const float* bm2,
-                          float* ess, cudaStream_t s);
+cudaError_t launch_bm_ess(int64_t C, int D, int64_t K, int64_t bsize, const float* m2, const float* bmean,
+                          const float* bm2, float* ess, cudaStream_t s);
 cudaError_t launch_da_init(DAState* da, float eps0, int adapt, float delta, long long num_adapt,
                            cudaStream_t s);
 

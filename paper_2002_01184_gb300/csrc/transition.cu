@@ -312,95 +312,76 @@ cudaError_t launch_momentum(uint64_t seed, uint32_t t, int C, int D, uint32_t ch
   return cudaGetLastError();
 }
 
-// Welford's running mean and sum of squared deviations (Welford 1962), one
-// element per thread: after kept draws 0..k, mean is their mean and m2 the
-// sum of squared deviations from it.  With bsize > 0 the draws also form
-// consecutive batches of bsize: bsum accumulates the current batch, and at
-// a batch's last draw its mean enters a second Welford recursion over batch
-// means (bmean, bm2).
-__global__ void k_welford(int64_t n, const float* __restrict__ x, int64_t k, float* __restrict__ mean,
-                          float* __restrict__ m2, int64_t bsize, float* __restrict__ bsum,
-                          float* __restrict__ bmean, float* __restrict__ bm2) {
-  const float inv = 1.0f / static_cast<float>(k + 1);
-  const int64_t pos = bsize > 0 ? k % bsize : 0;
-  const int64_t batch = bsize > 0 ? k / bsize : 0;
-  const bool closes = bsize > 0 && pos == bsize - 1;
-  const float inv_b = bsize > 0 ? 1.0f / static_cast<float>(bsize) : 0.f;
-  const float inv_j = 1.0f / static_cast<float>(batch + 1);
+// The streaming driver's moment update after kept draw k, one element per
+// thread (welford_update).
+__global__ void k_welford(int64_t n, const float* __restrict__ x, int64_t k, WelfordOut w) {
+  const WelfordCoef q = welford_coef(k, w.bsize);
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const float v = x[i];
-    if (k == 0) {
-      mean[i] = v;
-      m2[i] = 0.f;
-    } else {
-      const float m0 = mean[i];
-      const float delta = v - m0;
-      const float m1 = fmaf(delta, inv, m0);
-      mean[i] = m1;
-      m2[i] = fmaf(delta, v - m1, m2[i]);
-    }
-    if (bsize > 0) {
-      const float sum = pos == 0 ? v : bsum[i] + v;
-      bsum[i] = sum;
-      if (closes) {
-        const float bm = sum * inv_b;
-        if (batch == 0) {
-          bmean[i] = bm;
-          bm2[i] = 0.f;
-        } else {
-          const float b0 = bmean[i];
-          const float delta = bm - b0;
-          const float b1 = fmaf(delta, inv_j, b0);
-          bmean[i] = b1;
-          bm2[i] = fmaf(delta, bm - b1, bm2[i]);
-        }
-      }
-    }
-  }
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    welford_update(w, q, k, i, x[i]);
 }
 
 cudaError_t launch_welford(int64_t n, const float* x, int64_t k, float* mean, float* m2,
                            int64_t bsize, float* bsum, float* bmean, float* bm2, cudaStream_t s) {
   k_welford<<<static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 152 * 16)), 256, 0, s>>>(
-      n, x, k, mean, m2, bsize, bsum, bmean, bm2);
+      n, x, k, WelfordOut{mean, m2, bsize, bsum, bmean, bm2});
   count_launch();
   return cudaGetLastError();
 }
 
-// Batch-means effective sample size per dimension, pooled over chains:
-// ess[d] = C K (sum_c m2 / (K - 1)) / (bsize sum_c bm2 / (nb - 1)).  A block
-// covers 32 dimensions (one per lane, coalesced rows) with its 8 warps
-// striding over chains; sums in float64.
+// Replicated batch-means effective sample size per dimension: the C nb
+// batch means pooled about their grand mean (per chain, bmean / bm2 are the
+// Welford mean and sum of squared deviations of its nb batch means), so
+// SS = sum_c [bm2_c + nb (bmean_c - grand)^2] with grand = mean_c bmean_c,
+// and ess[d] = C K (sum_c m2_c / (C (K - 1))) / (bsize SS / (C nb - 1)).  A
+// block covers 32 dimensions (one per lane, coalesced rows) with its 8 warps
+// striding over chains in two passes (grand mean, then sums); float64.
 __global__ void __launch_bounds__(256) k_bm_ess(int64_t C, int D, int64_t K, int64_t bsize,
                                                 const float* __restrict__ m2,
+                                                const float* __restrict__ bmean,
                                                 const float* __restrict__ bm2, float* __restrict__ ess) {
-  __shared__ double w_s[8][32], v_s[8][32];
+  __shared__ double a_s[8][32], b_s[8][32];
+  __shared__ double grand_s[32];
   const int d = blockIdx.x * 32 + threadIdx.x;
-  double w = 0.0, v = 0.0;
+  const double nb = static_cast<double>(K / bsize);
+  double sb = 0.0;
+  if (d < D)
+    for (int64_t c = threadIdx.y; c < C; c += 8) sb += static_cast<double>(bmean[c * D + d]);
+  a_s[threadIdx.y][threadIdx.x] = sb;
+  __syncthreads();
+  if (threadIdx.y == 0) {
+    for (int y = 1; y < 8; ++y) sb += a_s[y][threadIdx.x];
+    grand_s[threadIdx.x] = sb / static_cast<double>(C);
+  }
+  __syncthreads();
+  const double grand = grand_s[threadIdx.x];
+  double w = 0.0, ss = 0.0;
   if (d < D)
     for (int64_t c = threadIdx.y; c < C; c += 8) {
+      const double dev = static_cast<double>(bmean[c * D + d]) - grand;
       w += static_cast<double>(m2[c * D + d]);
-      v += static_cast<double>(bm2[c * D + d]);
+      ss += static_cast<double>(bm2[c * D + d]) + nb * dev * dev;
     }
-  w_s[threadIdx.y][threadIdx.x] = w;
-  v_s[threadIdx.y][threadIdx.x] = v;
+  __syncthreads();
+  a_s[threadIdx.y][threadIdx.x] = w;
+  b_s[threadIdx.y][threadIdx.x] = ss;
   __syncthreads();
   if (threadIdx.y == 0 && d < D) {
     for (int y = 1; y < 8; ++y) {
-      w += w_s[y][threadIdx.x];
-      v += v_s[y][threadIdx.x];
+      w += a_s[y][threadIdx.x];
+      ss += b_s[y][threadIdx.x];
     }
-    const double nb = static_cast<double>(K / bsize);
-    const double s2 = w / static_cast<double>(K - 1);
-    const double sig2 = static_cast<double>(bsize) * v / (nb - 1.0);
-    ess[d] = static_cast<float>(static_cast<double>(C) * static_cast<double>(K) * s2 / sig2);
+    const double Cd = static_cast<double>(C), Kd = static_cast<double>(K);
+    const double W = w / (Cd * (Kd - 1.0));
+    const double sig2 = static_cast<double>(bsize) * ss / (Cd * nb - 1.0);
+    ess[d] = static_cast<float>(Cd * Kd * W / sig2);
   }
 }
 
-cudaError_t launch_bm_ess(int64_t C, int D, int64_t K, int64_t bsize, const float* m2, const float* bm2,
-                          float* ess, cudaStream_t s) {
-  k_bm_ess<<<static_cast<unsigned>((D + 31) / 32), dim3(32, 8), 0, s>>>(C, D, K, bsize, m2, bm2, ess);
+cudaError_t launch_bm_ess(int64_t C, int D, int64_t K, int64_t bsize, const float* m2, const float* bmean,
+                          const float* bm2, float* ess, cudaStream_t s) {
+  k_bm_ess<<<static_cast<unsigned>((D + 31) / 32), dim3(32, 8), 0, s>>>(C, D, K, bsize, m2, bmean, bm2,
+                                                                        ess);
   count_launch();
   return cudaGetLastError();
 }

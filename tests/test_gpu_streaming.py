@@ -50,11 +50,12 @@ def test_streaming_moments_equal_stored_trace_moments(H, kind):
     s.close()
 
 
-@pytest.mark.parametrize("kind,bsize", [("corr_gauss", 10), ("funnel", 7)])
+@pytest.mark.parametrize("kind,bsize", [("corr_gauss", 10), ("funnel", 7), ("corr_gauss", 60)])
 def test_streaming_batch_means_ess_equals_oracle_on_stored_trace(H, kind, bsize):
     """Batch-means ESS from the streaming driver against the oracle's
     estimator applied to the stored trace of the same run (60 kept draws: six
-    batches of 10, or eight of 7 with 4 draws left out of the batch means)."""
+    batches of 10, eight of 7 with 4 draws left out of the batch means, or
+    one batch per chain)."""
     from oracle import diagnostics as odiag
     from paper_2002_01184_gb300.sampler import Sampler
     if kind == "corr_gauss":
@@ -84,15 +85,16 @@ def test_streaming_batch_means_ess_equals_oracle_on_stored_trace(H, kind, bsize)
     s.close()
 
 
-def test_streaming_ess_rejects_too_few_batches(H):
+@pytest.mark.parametrize("C,bsize", [(8, 0), (8, 10), (1, 5), (1, 9)])
+def test_streaming_ess_rejects_too_few_batches(H, C, bsize):
+    """9 kept draws: no batch of 0 or 10 draws; one chain needs two batches."""
     from paper_2002_01184_gb300.sampler import Sampler
-    p = workloads.funnel(dim=5, num_chains=8, num_burnin=2, num_results=9)
+    p = workloads.funnel(dim=5, num_chains=C, num_burnin=2, num_results=9)
     s = Sampler(p)
     x = torch.as_tensor(p.x0).cuda().contiguous()
     mean, m2 = torch.empty_like(x), torch.empty_like(x)
     ess = torch.empty(5, device="cuda")
-    for bsize in (0, 5, 10):
-        with pytest.raises(H.HMCError) as ei:
-            H.hmc_sample_chain_streaming_ess(s.ctx, x, 2, 9, bsize, mean, m2, ess)
-        assert ei.value.status == H.HMC_E_INVALID
+    with pytest.raises(H.HMCError) as ei:
+        H.hmc_sample_chain_streaming_ess(s.ctx, x, 2, 9, bsize, mean, m2, ess)
+    assert ei.value.status == H.HMC_E_INVALID
     s.close()

@@ -395,16 +395,22 @@ def test_ess_of_ar1_matches_closed_form():
 
 def test_batch_means_ess_worked_by_hand():
     """One chain, draws 1, 3, 2, 6 in batches of 2: s2 = (4 + 0 + 1 + 9) / 3 =
-    14/3; batch means 2 and 4 (mean 3) have sample variance 2, so sig2 =
-    2 x 2 = 4 and ESS = 4 x (14/3) / 4 = 14/3.  A fifth draw beyond the last
-    complete batch enters s2 only: with 1, 3, 2, 6, 3 the draws have mean 3,
-    s2 = 14/4 = 3.5, and ESS = 5 x 3.5 / 4 = 4.375."""
+    14/3; batch means 2 and 4 (grand mean 3) give sig2 = 2 x (1 + 1) / 1 = 4
+    and ESS = 4 x (14/3) / 4 = 14/3.  A fifth draw beyond the last complete
+    batch enters the variance only: 1, 3, 2, 6, 3 have mean 3 and
+    s2 = 14/4, so ESS = 5 x 3.5 / 4 = 4.375.  Two chains (1, 3) and (2, 6)
+    with one batch each (batch_size = n = 2): W = (2 + 8) / 2 = 5, chain means
+    2 and 4 about 3 give sig2 = 2 x 2 / 1 = 4, ESS = 2 x 2 x 5 / 4 = 5."""
     z = np.array([1.0, 3.0, 2.0, 6.0]).reshape(4, 1, 1)
     assert diagnostics.batch_means_ess(z, 2)[0] == pytest.approx(14.0 / 3.0, rel=1e-15)
     z5 = np.array([1.0, 3.0, 2.0, 6.0, 3.0]).reshape(5, 1, 1)
     assert diagnostics.batch_means_ess(z5, 2)[0] == pytest.approx(4.375, rel=1e-15)
+    z2 = np.array([[1.0, 2.0], [3.0, 6.0]]).reshape(2, 2, 1)
+    assert diagnostics.batch_means_ess(z2, 2)[0] == pytest.approx(5.0, rel=1e-15)
     with pytest.raises(ValueError):
-        diagnostics.batch_means_ess(z, 3)                # one complete batch
+        diagnostics.batch_means_ess(z, 3)                # one batch in all
+    with pytest.raises(ValueError):
+        diagnostics.batch_means_ess(z2, 3)               # no complete batch
 
 
 def test_batch_means_ess_of_iid_draws_is_the_draw_count():
@@ -429,6 +435,23 @@ def test_batch_means_ess_of_ar1_matches_closed_form():
         z[t] = phi * z[t - 1] + e[t]
     np.testing.assert_allclose(diagnostics.batch_means_ess(z, 400), n * C * (1 - phi) / (1 + phi),
                                rtol=0.1)
+
+
+def test_batch_means_ess_with_one_batch_per_chain_is_the_between_chain_estimate():
+    """batch_size = n: each chain is one batch, and sig2 = n x the variance of
+    the chain means across chains.  For stationary AR(1) chains that variance
+    is about sigma^2 tau / n with tau = (1 + phi) / (1 - phi), so ESS / (C n)
+    -> (1 - phi) / (1 + phi); 400 chains leave a relative spread of about
+    sqrt(2 / 399) = 7 %."""
+    rng = np.random.default_rng(13)
+    phi, n, C = 0.8, 2000, 400
+    e = rng.standard_normal((n, C, 1))
+    z = np.empty_like(e)
+    z[0] = e[0] / math.sqrt(1 - phi * phi)
+    for t in range(1, n):
+        z[t] = phi * z[t - 1] + e[t]
+    np.testing.assert_allclose(diagnostics.batch_means_ess(z, n), n * C * (1 - phi) / (1 + phi),
+                               rtol=0.25)
 
 
 def test_logreg_posterior_mean_is_near_truth():
