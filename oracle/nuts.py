@@ -37,8 +37,9 @@ Random numbers (readings; all from the counter generator, key = seed,
 counter (word, chain, t, tag)): p0 from tag 0 as for HMC, U from tag 1 (the
 accept uniform), the directions from tag 3 (bit j of word 0 of counter
 (0, chain, t, 3): 1 is +1), the subtree choice at leaf k of doubling j from
-word 0 of counter (k, chain, t, 4 + j), the top-level choice at doubling j
-from word 0 of counter (j, chain, t, 14).  A choice with probability a / b
+word k mod 4 of counter (floor(k / 4), chain, t, 4 + j) -- four leaves per
+generator call --, the top-level choice at doubling j from word 0 of counter
+(j, chain, t, 14).  A choice with probability a / b
 (integers) is taken iff (2 w + 1) b < a 2^33 for its word w -- exact integer
 arithmetic, so both implementations take it identically.
 """
@@ -53,9 +54,14 @@ DELTA_MAX = 1000.0
 MAX_DEPTH_LIMIT = 10
 
 
-def _word(seed, w0, chain, t, tag):
+def _words(seed, w0, chain, t, tag):
+    """The four words of counter (w0, chain, t, tag)."""
     ctr = np.array([[w0, chain, t & 0xFFFFFFFF, tag]], dtype=np.uint64)
-    return int(philox.philox4x32_10(ctr, philox.seed_key(seed))[0, 0])
+    return [int(w) for w in philox.philox4x32_10(ctr, philox.seed_key(seed))[0]]
+
+
+def _word(seed, w0, chain, t, tag):
+    return _words(seed, w0, chain, t, tag)[0]
 
 
 def _take(w, a, b):
@@ -104,7 +110,8 @@ def one_chain(x0, lp0, g0, p0, log_U, eps, max_depth, seed, chain, t, target):
                 margin = min(margin, abs((H0 - H) - log_U))
                 if log_U <= H0 - H:
                     n_sub += 1
-                    if _take(_word(seed, k, chain, t, TAG_SUBTREE + j), 1, n_sub):
+                    w = _words(seed, k >> 2, chain, t, TAG_SUBTREE + j)[k & 3]
+                    if _take(w, 1, n_sub):
                         xs, gs, lps = x.copy(), g.copy(), lp
             for i in range(1, j + 1):
                 span = 1 << i
