@@ -19,9 +19,10 @@
 // D floats.
 //
 // Random choices: directions from word 0 of counter (0, chain, t, 3), the
-// subtree's choice at leaf k of doubling j from counter (k, chain, t, 4 + j),
-// the top-level choice at doubling j from counter (j, chain, t, 14); a choice
-// of probability a / b is taken iff (2 w + 1) b < a 2^33 (exact integers).
+// subtree's choice at leaf k of doubling j from word k mod 4 of counter
+// (k / 4, chain, t, 4 + j) (one generator call per four leaves), the
+// top-level choice at doubling j from counter (j, chain, t, 14); a choice of
+// probability a / b is taken iff (2 w + 1) b < a 2^33 (exact integers).
 #include <cmath>
 
 #include "hmc_device.cuh"
@@ -90,9 +91,10 @@ size_t span_smem_bytes(int Dp, int max_depth) {
   return static_cast<size_t>(kWarps) * 2 * (max_depth > 1 ? max_depth - 1 : 0) * Dp * sizeof(float);
 }
 
-// residency: 8 blocks (32 warps) per SM at NB = 1, 4 at NB = 2, 4 (registers)
+// residency: 7 blocks (28 warps, 4256 chains on 152 SMs) per SM at NB = 1, 4
+// at NB = 2, 4 (registers)
 template <int TARGET, int NB, bool SMEM>
-__global__ void __launch_bounds__(32 * kWarps, NB == 1 ? 8 : 4) k_nuts(NutsArgs na) {
+__global__ void __launch_bounds__(32 * kWarps, NB == 1 ? 7 : 4) k_nuts(NutsArgs na) {
   extern __shared__ float4 span_smem[];
   const StepArgs& a = na.s;
   const int warp = threadIdx.x >> 5;
@@ -274,10 +276,16 @@ __global__ void __launch_bounds__(32 * kWarps, NB == 1 ? 8 : 4) k_nuts(NutsArgs 
         bool ok_sub = true;
         float lps = 0.f;
         const int leaves = 1 << jd;
+        uint4 wsub4 = make_uint4(0u, 0u, 0u, 0u);
         for (int k = 0; k < leaves; ++k) {
-          // the subtree-choice word depends on nothing the leaf computes:
-          // drawn first, its arithmetic fills the butterfly's latency
-          const uint32_t wsub = word0(a.seed, static_cast<uint32_t>(k), chain, t, kTagSubtree + jd);
+          // the subtree-choice words depend on nothing the leaves compute:
+          // drawn first, four at a time, the generator's arithmetic fills the
+          // butterfly's latency
+          if ((k & 3) == 0)
+            wsub4 = philox(make_uint4(static_cast<uint32_t>(k >> 2), chain, t, kTagSubtree + jd),
+                           static_cast<uint32_t>(a.seed), static_cast<uint32_t>(a.seed >> 32));
+          const int kq = k & 3;
+          const uint32_t wsub = kq == 0 ? wsub4.x : kq == 1 ? wsub4.y : kq == 2 ? wsub4.z : wsub4.w;
           // spans of 2^i leaves closing at leaf k (2^i | k + 1); the span of
           // two leaves (i = 1) is tested inside the leaf's butterfly
           const int close = min(jd, __ffs(k + 1) - 1);
