@@ -156,3 +156,56 @@ def test_multi_transition_launch_is_bit_identical(H, adapt):
             np.testing.assert_array_equal(u, w)
     assert runs[0][2].any() and not runs[0][2].all()
     assert np.unique(runs[0][0][:, 0, 0]).size > K // 2         # the chain moved
+
+
+@pytest.mark.parametrize("C,D,depth", [(1, 1, 1), (1, 1, 4), (33, 1, 3), (2, 4, 10)])
+def test_nuts_edge_sizes_match_oracle(H, C, D, depth):
+    """One chain, one dimension, depth 1 (a single leapfrog step) and the
+    maximum depth, against the oracle transition by transition."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = workloads.std_normal(num_chains=C, dim=D, step_size=0.7, num_leapfrog=depth)
+    p.x0 = np.random.default_rng(C + D).standard_normal((C, D)).astype(np.float32)
+    s = Sampler(p, adapt=False, proposal=H.HMC_PROPOSAL_NUTS)
+    x = dev(p.x0)
+    s.bootstrap(x)
+    tgt = otargets.std_normal
+    for t in range(6):
+        xin = host(x).astype(np.float64)
+        lp, g = tgt(xin)
+        r = s.results(s.step(x, t))
+        ref = onuts.one_step(xin, lp, g, float(np.float32(0.7)), depth, p.seed, t, tgt)
+        sure = ref["margin"] > BAND
+        xg = host(x).astype(np.float64)
+        np.testing.assert_array_equal(host(r["is_accepted"]).astype(bool)[sure], ref["is_accepted"][sure])
+        err = np.max(np.abs(xg - ref["x"]), axis=1) / np.maximum(np.max(np.abs(ref["x"]), axis=1), 1e-3)
+        assert err[sure].max(initial=0.0) < 1e-4
+        if not sure.all():                 # teacher forcing where float32 may decide otherwise
+            xg[~sure] = ref["x"][~sure]
+            x.copy_(dev(xg.astype(np.float32)))
+            s.close()
+            s = Sampler(p, adapt=False, proposal=H.HMC_PROPOSAL_NUTS)
+            s.bootstrap(x)
+    s.close()
+
+
+def test_nuts_chain_is_independent_of_the_batch(H):
+    """Chain c's transitions depend only on (seed, chain index, t): chain 5 of
+    a 64-chain run equals a one-chain run with chain_offset 5."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = workloads.funnel(dim=20, num_chains=64)
+    p.step_size, p.num_leapfrog, p.adapt = 0.1, 7, False
+    full = Sampler(p, adapt=False, proposal=H.HMC_PROPOSAL_NUTS)
+    x = dev(p.x0)
+    full.bootstrap(x)
+    p1 = workloads.funnel(dim=20, num_chains=1)
+    p1.x0 = p.x0[5:6].copy()
+    p1.step_size, p1.num_leapfrog, p1.adapt = 0.1, 7, False
+    one = Sampler(p1, adapt=False, proposal=H.HMC_PROPOSAL_NUTS, chain_offset=5)
+    x1 = dev(p1.x0)
+    one.bootstrap(x1)
+    for t in range(5):
+        full.step(x, t)
+        one.step(x1, t)
+        np.testing.assert_array_equal(host(x1)[0], host(x)[5])
+    full.close()
+    one.close()
