@@ -87,3 +87,44 @@ def test_integer_choice_rule():
     assert not nuts._take(0, 0, 5)                                   # probability 0
     # probability 1/2 splits the words at 2^31
     assert nuts._take(2 ** 31 - 1, 1, 2) and not nuts._take(2 ** 31, 1, 2)
+
+
+def test_last_doubling_takes_the_candidate_uniformly_when_every_leaf_is_valid():
+    """With a tiny step the energy is conserved to ~eps^2, so every leaf is in
+    the slice, and a 3-level tree on a 1-D standard normal started at its mode
+    never turns (the momentum keeps its sign over 7 steps of 1e-3).  The
+    efficient NUTS then replaces the candidate with probability
+    min(1, n'/n) = 1 at every doubling (n' = n = 2^j), and inside a subtree
+    leaf k replaces it with probability 1/(k + 1): the new state is uniform
+    over the four leaves of the last doubling and never an earlier state.
+    Uniform progressive sampling over the whole trajectory, or keeping the
+    subtree's first or last leaf, would fail this."""
+    eps, depth, C, seed, t = 1e-3, 3, 4000, 21, 2
+
+    def tgt(x):
+        return -0.5 * np.sum(x * x, axis=1), -x
+
+    x = np.zeros((C, 1))
+    lp, g = tgt(x)
+    out = nuts.one_step(x, lp, g, eps, depth, seed, t, tgt)
+    assert out["is_accepted"].all() and np.all(out["leaves"] == 7) and np.all(out["depth"] == 3)
+    p0 = philox.momentum(seed, t, C, 1)[:, 0]
+    counts = np.zeros(4)
+    for c in range(C):
+        dirs = nuts._word(seed, 0, c, t, nuts.TAG_DIRECTION)
+        ends = {+1: (0.0, p0[c]), -1: (0.0, p0[c])}
+        for j in range(depth):
+            v = 1 if (dirs >> j) & 1 else -1
+            q, m = ends[v]
+            leaves = []
+            for _ in range(1 << j):          # velocity Verlet on -x^2/2, step v eps
+                m = m - 0.5 * v * eps * q
+                q = q + v * eps * m
+                m = m - 0.5 * v * eps * q
+                leaves.append(q)
+            ends[v] = (q, m)
+        hit = np.flatnonzero(np.abs(np.array(leaves) - out["x"][c, 0]) < 1e-12)
+        assert hit.size == 1, (c, leaves, out["x"][c, 0])
+        counts[hit[0]] += 1
+    chi2 = np.sum((counts - C / 4) ** 2 / (C / 4))
+    assert chi2 < 16.3, counts          # 3 degrees of freedom, p = 0.001
