@@ -15,15 +15,17 @@
 //     CTA holds 32 of the 64 chains.
 //   * Accumulators: each CTA's tensor memory holds its 128 output dims for
 //     all 64 chains.
-//   * Epilogue (warps 2-9 of both CTAs): one output dim per thread, 32 chains
-//     per thread; momenta and trajectory positions in registers, the chains'
-//     current state (position and gradient, this CTA's dims) in shared
-//     memory across transitions.  The next positions of this CTA's own
-//     chains go straight into its tile; those of the peer's chains are staged
-//     locally (in the destination's layout) and each staging warp pushes its
-//     K-chunk (head and remainder, 4 KB each) to the peer by bulk DSMEM copy,
-//     completing on the peer's tile barrier -- element-wise remote stores
-//     stalled every warp's shared-memory traffic.
+//   * Epilogue (warps 2-9 of both CTAs): one output dim per thread and 32
+//     chains per thread, 16 of the peer's and 16 of its own; momenta and
+//     trajectory positions in registers, the chains' current state (position
+//     and gradient, this CTA's dims) in shared memory across transitions.
+//     Each step a thread first updates its peer chains, whose next positions
+//     are staged locally (in the destination's layout); each warp then
+//     pushes its 16 rows of a K-chunk (head and remainder, 2 KB each) to the
+//     peer by bulk DSMEM copy, completing on the peer's tile barrier, and
+//     updates its own chains, written straight into its tile, while the copy
+//     is in flight -- element-wise remote stores stalled every warp's
+//     shared-memory traffic.
 //   * Readiness is tracked per half of K: in each CTA's tile the K-chunks of
 //     its own dims are written locally (own_full, which every epilogue thread
 //     joins once it has read the accumulators) and the other four arrive by
@@ -232,7 +234,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 
   // epilogue-thread state (warps 2-9)
   const int ew = warp - 2;
-  const int h = ew >> 2;                  // chain half 0 / 1 (= the CTA holding those chains)
+  const int sub = ew >> 2;                // rows 16 sub .. 16 sub + 15 of each chain half
   const int quarter = warp & 3;           // tensor-memory lane quarter
   const int dl = quarter * 32 + lane;     // this CTA's dim index 0..127
   const int d = static_cast<int>(rank) * 128 + dl;
@@ -332,54 +334,68 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     }
   } else {
     // ---- epilogue, both CTAs
-    const bool own = static_cast<uint32_t>(h) == rank;   // warp-uniform
-    // Destination of this thread's positions (dim d, chain rows 0-31 of half
-    // h): this CTA's tile if the chains are ours, else staging, laid out as
-    // K-chunks 4 rank .. 4 rank + 3 of the peer's tile (1024-byte aligned both
-    // sides, so the swizzle carries over).  Row i's byte offset is
-    // col + (i / 8) * 1024 + sw[i % 8]; the eight sw terms are per thread.
-    const int dcol = own ? d : dl;
-    const uint32_t col = static_cast<uint32_t>((dcol >> 5) * kBChunk + (dcol & 3) * 4);
-    const uint32_t dst_hi0 = ptx::smem_u32(own ? Bhi : Stg) + col;
-    const uint32_t lo_off = own ? kBBytes : kStageHalf;
+    // Element i (0..31) of this thread is dim d of pair row rowi(i): the
+    // first 16 are 16 of the peer's chains, written to staging and pushed to
+    // the peer as soon as they are done; the last 16 are 16 of this CTA's
+    // own chains, written straight into its tile.  Each step's copy thus
+    // starts after half of the epilogue, and the other half overlaps it.
+    auto rowi = [&](int i) {
+      return static_cast<int>(i < 16 ? peer : rank) * kHalf + sub * 16 + (i & 15);
+    };
+    // Destinations, laid out as the K-chunks of a tile (1024-byte aligned on
+    // both sides, so the swizzle carries over): staging chunk `quarter` is
+    // the peer's K-chunk 4 rank + quarter.  Row r of a chunk sits at
+    // (r / 8) * 1024 + sw[r % 8] from the column's base (d and dl agree mod 32).
+    const uint32_t st_hi0 = ptx::smem_u32(Stg) + static_cast<uint32_t>((dl >> 5) * kBChunk + (dl & 3) * 4);
+    const uint32_t own_hi0 = ptx::smem_u32(Bhi) + static_cast<uint32_t>((d >> 5) * kBChunk + (d & 3) * 4);
     uint32_t sw[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) sw[r] = r * 128 + (((((dcol & 31) >> 2) ^ r) & 7) << 4);
-    const int nvalid = dvalid ? min(kHalf, C - (pair_base + h * kHalf)) : 0;
-    float* xrow = xs + (h * kHalf) * 128 + dl;           // + i * 128: chain row i of half h
-    float* grow = gs + (h * kHalf) * 128 + dl;
-    auto store_x = [&](int i, float xi) {   // position of row i, split, into tile / staging
-      if (i < nvalid) {
+    for (int r = 0; r < 8; ++r) sw[r] = r * 128 + (((((dl & 31) >> 2) ^ r) & 7) << 4);
+    const int nv_peer = dvalid ? max(0, min(16, C - (pair_base + static_cast<int>(peer) * kHalf + sub * 16))) : 0;
+    const int nv_own = dvalid ? max(0, min(16, C - (pair_base + static_cast<int>(rank) * kHalf + sub * 16))) : 0;
+    auto valid = [&](int i) { return i < 16 ? i < nv_peer : i - 16 < nv_own; };
+    auto xrow = [&](int i) -> float& { return xs[rowi(i) * 128 + dl]; };
+    auto grow = [&](int i) -> float& { return gs[rowi(i) * 128 + dl]; };
+    auto store_x = [&](int i, float xi) {   // position of element i, split, into staging / tile
+      if (valid(i)) {
         float hi, lo;
         split_tf32(xi, hi, lo);
-        const uint32_t a0 = dst_hi0 + (i >> 3) * 1024 + sw[i & 7];
+        const int r = sub * 16 + (i & 15);
+        const uint32_t a0 = (i < 16 ? st_hi0 : own_hi0) + (r >> 3) * 1024 + sw[r & 7];
+        const uint32_t lo_off = i < 16 ? kStageHalf : kBBytes;
         asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0), "f"(hi) : "memory");
         asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0 + lo_off), "f"(lo) : "memory");
       }
     };
-    // The next positions are written: every thread arrives on own_full once
-    // its accumulator reads are done; an own-chain thread arms the peer's
-    // incoming copy bytes; each staging warp pushes its K-chunk -- staging
-    // chunk `quarter`, the peer's K-chunk 4 rank + quarter -- completing on
-    // the peer's in_full.
-    auto publish = [&]() {
-      proxy_fence_cta();          // generic stores -> async proxy (MMA, bulk copy)
-      ptx::tc_fence_before();     // this thread's accumulator reads precede the next MMA
-      ptx::mbar_arrive_local(own_full);
-      if (own) {
-        if ((ew & 3) == 0 && lane == 0) ptx::mbar_arrive_expect_tx(in_full, kStageBytes);
-      } else {
-        __syncwarp();
-        if (lane == 0) {
-          const uint32_t bar = ptx::mapa(ptx::smem_u32(in_full), peer);
-          const uint32_t chunk = (4 * rank + quarter) * kBChunk;
-          uint8_t* sb = Stg + quarter * kBChunk;
-          ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Bhi + chunk), peer), sb, kBChunk, bar);
-          ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Blo + chunk), peer), sb + kStageHalf, kBChunk, bar);
-        }
+    // The peer's half is written: the warp pushes its 16 rows of staging
+    // chunk `quarter` (head and remainder, 2 KB each) to the peer's tile,
+    // completing on the peer's in_full.
+    auto publish_stage = [&]() {
+      proxy_fence_cta();          // generic stores -> async proxy (bulk copy)
+      __syncwarp();
+      if (lane == 0) {
+        const uint32_t bar = ptx::mapa(ptx::smem_u32(in_full), peer);
+        const uint32_t rows = static_cast<uint32_t>(sub) * (kBChunk / 2);
+        const uint32_t chunk = (4 * rank + quarter) * kBChunk + rows;
+        uint8_t* sb = Stg + quarter * kBChunk + rows;
+        ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Bhi + chunk), peer), sb, kBChunk / 2, bar);
+        ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Blo + chunk), peer), sb + kStageHalf, kBChunk / 2,
+                                  bar);
       }
     };
-    const uint32_t acc_addr = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + kColAcc + h * kHalf;
+    // The own half is written: every thread arrives on own_full once its
+    // accumulator reads are done; one thread arms the incoming copy bytes.
+    auto publish_own = [&]() {
+      proxy_fence_cta();          // generic stores -> async proxy (MMA)
+      ptx::tc_fence_before();     // this thread's accumulator reads precede the next MMA
+      ptx::mbar_arrive_local(own_full);
+      if (ew == 0 && lane == 0) ptx::mbar_arrive_expect_tx(in_full, kStageBytes);
+    };
+    // accumulator columns of elements 16 cb .. 16 cb + 15 (column = pair row)
+    const uint32_t acc_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + kColAcc;
+    auto acc_col = [&](int cb) {
+      return static_cast<uint32_t>(static_cast<int>(cb == 0 ? peer : rank) * kHalf + sub * 16);
+    };
     auto wait_acc = [&](int s) {
       if (!ptx::mbar_wait(acc_full, s & 1)) {
         atomicCAS(fa.err, 0, 4);
@@ -387,13 +403,13 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       }
       ptx::tc_fence_after();
     };
-    const uint32_t chain0 = static_cast<uint32_t>(pair_base + h * kHalf) + a.chain_offset;
-    // momenta of transition tn for rows i0 .. i1-1, parked for the next begin
+    auto chain_of = [&](int i) { return static_cast<uint32_t>(pair_base + rowi(i)) + a.chain_offset; };
+    // momenta of transition tn for elements i0 .. i1-1, parked for the next begin
     auto draw_next = [&](int i0, int i1, uint32_t tn) {
       for (int i = i0; i < i1; ++i)
-        if (i < nvalid)
-          fa.p0next[static_cast<int64_t>(pair_base + h * kHalf + i) * D + d] =
-              momentum1(a.seed, static_cast<uint32_t>(d), chain0 + i, tn);
+        if (valid(i))
+          fa.p0next[static_cast<int64_t>(pair_base + rowi(i)) * D + d] =
+              momentum1(a.seed, static_cast<uint32_t>(d), chain_of(i), tn);
     };
     const int per_wait = (kHalf + L - 1) / L;   // rows drawn ahead of each gradient wait
 
@@ -402,7 +418,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     // quarter split chunks 0-3 and 4-6
     {
       const int kc_end = min(nk, kTmemChunks);
-      for (int kc = h == 0 ? 0 : 4; kc < (h == 0 ? min(kc_end, 4) : kc_end); ++kc) {
+      for (int kc = sub == 0 ? 0 : 4; kc < (sub == 0 ? min(kc_end, 4) : kc_end); ++kc) {
 #pragma unroll
         for (int q16 = 0; q16 < 2; ++q16) {
           float vh[16], vl[16];
@@ -425,15 +441,15 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     // the chains' current state, this CTA's dims
 #pragma unroll 4
     for (int i = 0; i < kHalf; ++i) {
-      const bool valid = i < nvalid;
-      const int64_t e = static_cast<int64_t>(pair_base + h * kHalf + i) * D + d;
-      xrow[i * 128] = valid ? a.x[e] : 0.f;
-      grow[i * 128] = valid ? a.g[e] : 0.f;
+      const bool v = valid(i);
+      const int64_t e = static_cast<int64_t>(pair_base + rowi(i)) * D + d;
+      xrow(i) = v ? a.x[e] : 0.f;
+      grow(i) = v ? a.g[e] : 0.f;
     }
     // momenta of the first transition, straight into registers
 #pragma unroll
     for (int i = 0; i < kHalf; ++i)
-      p[i] = i < nvalid ? momentum1(a.seed, static_cast<uint32_t>(d), chain0 + i, a.t) : 0.f;
+      p[i] = valid(i) ? momentum1(a.seed, static_cast<uint32_t>(d), chain_of(i), a.t) : 0.f;
 
     for (int j = 0; j < T; ++j) {
       const uint32_t t = a.t + static_cast<uint32_t>(j);
@@ -442,23 +458,24 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       if (j > 0) {
 #pragma unroll
         for (int i = 0; i < kHalf; ++i)
-          p[i] = i < nvalid ? fa.p0next[static_cast<int64_t>(pair_base + h * kHalf + i) * D + d] : 0.f;
+          p[i] = valid(i) ? fa.p0next[static_cast<int64_t>(pair_base + rowi(i)) * D + d] : 0.f;
       }
       // |p0|^2 partials of this warp's dims, one per chain
       {
         float v[kHalf];
 #pragma unroll
         for (int i = 0; i < kHalf; ++i) v[i] = p[i] * p[i];
-        red[(2 * 4 + quarter) * 64 + h * kHalf + lane] = transpose_reduce32(v, lane);
+        red[(2 * 4 + quarter) * 64 + rowi(lane)] = transpose_reduce32(v, lane);
       }
-      // begin: p = p0 + eps/2 g0, x1 = x0 + eps p
+      // begin: p = p0 + eps/2 g0, x1 = x0 + eps p (the peer's half first)
 #pragma unroll
       for (int i = 0; i < kHalf; ++i) {
-        p[i] = fmaf(0.5f * eps, grow[i * 128], p[i]);
-        x[i] = fmaf(eps, p[i], xrow[i * 128]);
+        p[i] = fmaf(0.5f * eps, grow(i), p[i]);
+        x[i] = fmaf(eps, p[i], xrow(i));
         store_x(i, x[i]);
+        if (i == 15) publish_stage();
       }
-      publish();
+      publish_own();
       const int s0 = j * L;                 // gradient steps of this transition: s0 .. s0 + L - 1
       // steps 1 .. L-1: merged kick + drift
       for (int l = 1; l < L; ++l) {
@@ -467,7 +484,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 #pragma unroll
         for (int cb = 0; cb < kHalf / 16; ++cb) {
           float accv[16];
-          ptx::tmem_ld16(acc_addr + cb * 16, accv);
+          ptx::tmem_ld16(acc_base + acc_col(cb), accv);
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
             const int i = cb * 16 + k;
@@ -475,8 +492,9 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
             x[i] = fmaf(eps, p[i], x[i]);
             store_x(i, x[i]);
           }
+          if (cb == 0) publish_stage();
         }
-        publish();
+        publish_own();
       }
       // step L: final half kick; <x, g> and |p|^2 partials
       if (more) draw_next(min(kHalf, (L - 1) * per_wait), kHalf, t + 1);
@@ -486,18 +504,18 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 #pragma unroll
         for (int cb = 0; cb < kHalf / 16; ++cb) {
           float accv[16];
-          ptx::tmem_ld16(acc_addr + cb * 16, accv);
+          ptx::tmem_ld16(acc_base + acc_col(cb), accv);
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
             const int i = cb * 16 + k;
             p[i] = fmaf(-0.5f * eps, accv[k], p[i]);
-            v[i] = i < nvalid ? -x[i] * accv[k] : 0.f;
+            v[i] = valid(i) ? -x[i] * accv[k] : 0.f;
           }
         }
-        red[(0 * 4 + quarter) * 64 + h * kHalf + lane] = transpose_reduce32(v, lane);
+        red[(0 * 4 + quarter) * 64 + rowi(lane)] = transpose_reduce32(v, lane);
 #pragma unroll
-        for (int i = 0; i < kHalf; ++i) v[i] = i < nvalid ? p[i] * p[i] : 0.f;
-        red[(1 * 4 + quarter) * 64 + h * kHalf + lane] = transpose_reduce32(v, lane);
+        for (int i = 0; i < kHalf; ++i) v[i] = valid(i) ? p[i] * p[i] : 0.f;
+        red[(1 * 4 + quarter) * 64 + rowi(lane)] = transpose_reduce32(v, lane);
       }
       epi_barrier();
       // Only the epilogue warps run this loop, so the two CTAs meet on
@@ -566,16 +584,16 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 #pragma unroll
       for (int cb = 0; cb < kHalf / 16; ++cb) {
         float accv[16];
-        ptx::tmem_ld16(acc_addr + cb * 16, accv);
+        ptx::tmem_ld16(acc_base + acc_col(cb), accv);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const int i = cb * 16 + k;
-          if (ok && i < nvalid) {
-            if (acc_flag[h * kHalf + i]) {
-              xrow[i * 128] = x[i];
-              grow[i * 128] = -accv[k];
+          if (ok && valid(i)) {
+            if (acc_flag[rowi(i)]) {
+              xrow(i) = x[i];
+              grow(i) = -accv[k];
             }
-            if (samp) samp[static_cast<int64_t>(pair_base + h * kHalf + i) * D + d] = xrow[i * 128];
+            if (samp) samp[static_cast<int64_t>(pair_base + rowi(i)) * D + d] = xrow(i);
           }
         }
       }
@@ -584,15 +602,15 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         for (int i0 = 0; i0 < kHalf; i0 += 8) {
           int64_t e[8];
           float v[8];
-          uint32_t valid = 0u;
+          uint32_t vmask = 0u;
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             const int i = i0 + k;
-            e[k] = static_cast<int64_t>(pair_base + h * kHalf + i) * D + d;
-            v[k] = xrow[i * 128];
-            if (i < nvalid) valid |= 1u << k;
+            e[k] = static_cast<int64_t>(pair_base + rowi(i)) * D + d;
+            v[k] = xrow(i);
+            if (valid(i)) vmask |= 1u << k;
           }
-          welford_update_n<8>(a.w, wq, k_out, e, v, valid);
+          welford_update_n<8>(a.w, wq, k_out, e, v, vmask);
         }
       }
       // dual averaging over all chains of the posterior
@@ -640,10 +658,10 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     // the chains' final state back to global memory
 #pragma unroll 4
     for (int i = 0; i < kHalf; ++i) {
-      if (ok && i < nvalid) {
-        const int64_t e = static_cast<int64_t>(pair_base + h * kHalf + i) * D + d;
-        a.x[e] = xrow[i * 128];
-        a.g[e] = grow[i * 128];
+      if (ok && valid(i)) {
+        const int64_t e = static_cast<int64_t>(pair_base + rowi(i)) * D + d;
+        a.x[e] = xrow(i);
+        a.g[e] = grow(i);
       }
     }
     if (persistent && blockIdx.x == 0 && threadIdx.x == 64 && !*abort_s) *a.da = *da_s;
