@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--streaming", type=int, default=0, metavar="BATCH",
                     help="streaming driver: running moments and batch-means ESS (batches of BATCH "
                          "kept draws) on the device instead of the kept-sample trace")
+    ap.add_argument("--replicas", type=int, default=1, metavar="K",
+                    help="replica exchange (Section 2.2): the chains form chains/K sets of K "
+                         "tempered replicas, inverse temperatures 4^(-k/(K-1)), fixed step size")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -96,6 +99,35 @@ def make_problem(name):
         p = workloads.funnel(dim=100, num_chains=4096)
         return p, "funnel d=100 C=4096 L=10 DA(0.8) B=500 K=1000"
     return workloads.std_normal(), "std_normal D=1 C=100 L=3 eps=1.5 B=300 K=100"
+
+
+class ReplicaSet:
+    """A replica-exchange context over the workload's chains: chains / K sets
+    of K replicas (rows c K + k), inverse temperatures 4^(-k / (K - 1)); the
+    step size is fixed at the workload's adapted value."""
+
+    def __init__(self, p, K, impl, stream, proposal):
+        from paper_2002_01184_gb300 import hmc
+        import torch
+        if p.num_chains % K:
+            raise SystemExit(f"--replicas {K} must divide the {p.num_chains} chains")
+        self.betas = [4.0 ** (-k / (K - 1)) for k in range(K)]
+        self.P = None if p.P is None else torch.as_tensor(p.P).cuda().contiguous()
+        self.X = None if p.X is None else torch.as_tensor(p.X).cuda().contiguous()
+        self.y = None if p.y is None else torch.as_tensor(p.y).cuda().contiguous()
+        if p.kind == "corr_gauss":
+            p.step_size = 0.445            # the adapted step size of the untempered chains
+        p.adapt = False
+        target = hmc.make_target(p.kind, p.dim, self.P, self.X, self.y)
+        cfg = hmc.make_config(p.num_leapfrog, p.step_size, p.seed, False, p.target_accept, 0, impl,
+                              proposal=proposal)
+        self.ctx = hmc.hmc_remc_create(target, p.num_chains // K, self.betas, cfg, stream)
+
+    def close(self):
+        from paper_2002_01184_gb300 import hmc
+        if self.ctx:
+            hmc.hmc_destroy(self.ctx)
+            self.ctx = None
 
 
 def peaks():
@@ -397,8 +429,13 @@ def main():
     elif proposal == hmc.HMC_PROPOSAL_NUTS:
         p.num_leapfrog = NUTS_MAX_DEPTH    # the context's num_leapfrog is the maximum tree depth
         wl += NUTS_LABEL
-    s = Sampler(p, impl=impl, stream=stream, max_transitions_per_launch=args.max_transitions_per_launch,
-                proposal=proposal)
+    if args.replicas > 1:
+        s = ReplicaSet(p, args.replicas, impl, stream, proposal)
+        wl += (f" (replica exchange: {p.num_chains // args.replicas} x {args.replicas} replicas, "
+               f"betas {', '.join(f'{b:.3f}' for b in s.betas)}, step size {p.step_size} fixed)")
+    else:
+        s = Sampler(p, impl=impl, stream=stream, max_transitions_per_launch=args.max_transitions_per_launch,
+                    proposal=proposal)
     C, D, K, B = p.num_chains, p.dim, p.num_results, p.num_burnin
     x0 = torch.as_tensor(p.x0).cuda()
     x = torch.empty_like(x0)

@@ -807,8 +807,13 @@ hmc_status hmc_remc_create(const hmc_target* target, int64_t num_chains, int32_t
   if (num_chains < 1 || num_chains > (1ll << 30) / num_replicas)
     return fail(nullptr, HMC_E_INVALID, "num_chains out of range");
   hmc_config c = *config;
-  // the dense targets' tensor-core kernels do not temper: plain path for them
-  if (target && (target->id == HMC_T_CORR_GAUSS || target->id == HMC_T_LOGREG)) c.impl = HMC_IMPL_PLAIN;
+  // Of the dense targets' tensor-core kernels only the CTA-pair Gaussian
+  // kernel tempers (one launch per transition, the exchange step between
+  // launches); the others run the plain path.
+  if (target && target->id == HMC_T_LOGREG) c.impl = HMC_IMPL_PLAIN;
+  if (target && target->id == HMC_T_CORR_GAUSS &&
+      !(c.impl == HMC_IMPL_FUSED && hmc::gauss_fused_supported(*target)))
+    c.impl = HMC_IMPL_PLAIN;
   hmc_ctx* ctx = nullptr;
   hmc_status st = hmc_create(target, num_chains * num_replicas, &c, cuda_stream, &ctx);
   if (st != HMC_OK) return st;

@@ -69,8 +69,10 @@ constexpr uint32_t kStageHalf = 4 * kBChunk;      // 4 K-chunks (this CTA's 128 
 constexpr uint32_t kStageBytes = 2 * kStageHalf;  // head + remainder
 constexpr uint32_t kStateBytes = kPairChains * 128 * 4;   // one of position / gradient
 // barriers (8), tmem slot, red [3][4][64], red_pair [3][64], peer_in [3][64],
-// acc_flag [64], prob_s [64], DA state copy, flags, DA coefficients, pair sum
-constexpr uint32_t kSmall = 8 * 8 + 16 + (3 * 4 * 64 + 3 * 64 + 3 * 64 + 64 + 64) * 4 + 128 + 16 + 32 + 16;
+// acc_flag [64], prob_s [64], DA state copy, flags, DA coefficients, pair
+// sum, inverse temperatures [64]
+constexpr uint32_t kSmall =
+    8 * 8 + 16 + (3 * 4 * 64 + 3 * 64 + 3 * 64 + 64 + 64) * 4 + 128 + 16 + 32 + 16 + 64 * 4;
 constexpr size_t kSmemUsed =
     2 * kBBytes + 2 * kAHalf + kStageBytes + 2 * kStateBytes + kSmall + 1024;
 // Above half of an SM's shared memory, so that one CTA runs per SM: a CTA
@@ -158,6 +160,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned gen) {
   return true;
 }
 
+// TEMPERED (replica exchange, Section 2.2): row r of the pair targets
+// p^beta_r, beta_r = betas[(pair_base + r) % K].  Its gradient is
+// -beta_r P x = -P (beta_r x), so the MMA operand tiles hold beta_r x and the
+// epilogue, the energies and the cached log p / gradient come out tempered
+// with no other change.
+template <bool TEMPERED>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ CUtensorMap mPlo,
              PairArgs fa) {
@@ -189,6 +197,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   int* abort_s = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(da_s) + 128);
   DACoef* coef_s = reinterpret_cast<DACoef*>(reinterpret_cast<uint8_t*>(da_s) + 144);
   double* psum_s = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(da_s) + 176);
+  float* beta_s = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(da_s) + 192);   // [64]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = ptx::cluster_rank();              // 0: leader, 1: peer
@@ -218,6 +227,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     ptx::tmem_alloc_pair(tmem_slot, kTmemCols);
     ptx::tmem_relinquish_pair();
   }
+  if (TEMPERED && threadIdx.x < kPairChains)
+    beta_s[threadIdx.x] = a.betas[(pair_base + static_cast<int>(threadIdx.x)) % a.K];
   // B tiles and staging start zeroed: dims >= D are never written
   for (uint32_t i = threadIdx.x; i < 2 * kBBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -358,6 +369,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     auto grow = [&](int i) -> float& { return gs[rowi(i) * 128 + dl]; };
     auto store_x = [&](int i, float xi) {   // position of element i, split, into staging / tile
       if (valid(i)) {
+        if (TEMPERED) xi *= beta_s[rowi(i)];
         float hi, lo;
         split_tf32(xi, hi, lo);
         const int r = sub * 16 + (i & 15);
@@ -696,7 +708,10 @@ cudaError_t launch_gauss_pair_image(const float* Phi, const float* Plo, int D, f
 }
 
 cudaError_t gauss_pair_setup() {
-  return cudaFuncSetAttribute(k_gauss_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_gauss_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSmem));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gauss_pair<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(kSmem));
 }
 
@@ -718,7 +733,7 @@ bool gauss_pair_persistent_ok(int64_t C) {
     cfg.numAttrs = 1;
     int n = 0;
     if (gauss_pair_setup() != cudaSuccess ||
-        cudaOccupancyMaxActiveClusters(&n, k_gauss_pair, &cfg) != cudaSuccess) {
+        cudaOccupancyMaxActiveClusters(&n, k_gauss_pair<false>, &cfg) != cudaSuccess) {
       cudaGetLastError();
       n = 0;
     }
@@ -753,7 +768,8 @@ cudaError_t launch_gauss_pair_transitions(const StepArgs& a, GaussTc& tc, int T,
   cfg.attrs = attr;
   cfg.numAttrs = T > 1 ? 2 : 1;
   if (timer) timer->begin(s);
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_gauss_pair, tc.mPhi128, tc.mPlo128, fa);
+  cudaError_t e = a.betas ? cudaLaunchKernelEx(&cfg, k_gauss_pair<true>, tc.mPhi128, tc.mPlo128, fa)
+                          : cudaLaunchKernelEx(&cfg, k_gauss_pair<false>, tc.mPhi128, tc.mPlo128, fa);
   if (timer) timer->end(s);
   count_launch();
   if (e != cudaSuccess) return e;

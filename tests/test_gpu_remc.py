@@ -28,12 +28,20 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
+# the dense Gaussian cases run the CTA-pair tensor-core kernel, tempered:
+# one K-chunk, several, and all eight (chunk 7 read from shared memory)
 @pytest.mark.parametrize("kind,C,K,D,eps,L", [("std_normal", 40, 4, 3, 0.5, 3),
                                               ("funnel", 24, 3, 12, 0.05, 5),
-                                              ("corr_gauss", 20, 3, 8, 0.1, 4)])
+                                              ("corr_gauss", 20, 3, 8, 0.1, 4),
+                                              ("corr_gauss", 50, 4, 64, 0.08, 6),
+                                              ("corr_gauss", 17, 3, 256, 0.05, 3)])
 def test_replica_exchange_transition_matches_oracle(H, kind, C, K, D, eps, L):
     from paper_2002_01184_gb300.sampler import _CudaArray
     betas = np.array([1.0, 0.6, 0.35, 0.2][:K], dtype=np.float32)
+    if D >= 64:
+        # adjacent log-densities differ by ~ D dbeta / 2 in high dimension: keep
+        # the spacing near sqrt(0.6 / D) so that swaps happen
+        betas = (1.0 - np.sqrt(0.6 / D) * np.arange(K)).astype(np.float32)
     P = None
     if kind == "corr_gauss":
         prob = workloads.corr_gauss(dim=D, num_chains=C * K)
@@ -44,6 +52,8 @@ def test_replica_exchange_transition_matches_oracle(H, kind, C, K, D, eps, L):
     target = H.make_target(kind, D, P)
     cfg = H.make_config(L, eps, seed=5, use_graph=False)
     ctx = H.hmc_remc_create(target, C, betas, cfg)
+    if kind == "corr_gauss":
+        assert H.hmc_dominant_kernel_info(ctx)[0] == "k_gauss_pair"
     x0 = (np.random.default_rng(1).standard_normal((C * K, D)) /
           np.sqrt(np.tile(betas, C))[:, None]).astype(np.float32)
     x = torch.as_tensor(x0).cuda().contiguous()
