@@ -294,7 +294,10 @@ hmc_status enqueue_range(hmc_ctx* ctx, float* x, int64_t B, int64_t t_begin, int
                           : (1ll << 30);
   const int64_t chunk = std::min(std::max<int64_t>(T, 1), cap);
   // (the streaming driver's moments are updated inside the launch)
-  if (ctx->use_tc && ctx->tc.pair && ctx->K == 1 && T > 0 &&
+  // (replica sets whose size divides a pair's 64 chains take the exchange
+  // step inside the launch)
+  const bool pair_remc = ctx->K > 1 && 64 % ctx->K == 0;
+  if (ctx->use_tc && ctx->tc.pair && (ctx->K == 1 || pair_remc) && T > 0 &&
       (chunk == 1 || hmc::gauss_pair_persistent_ok(ctx->C))) {
     for (int64_t t0 = t_begin; t0 < t_end; t0 += chunk) {
       const int n = static_cast<int>(std::min(chunk, t_end - t0));
@@ -302,7 +305,8 @@ hmc_status enqueue_range(hmc_ctx* ctx, float* x, int64_t B, int64_t t_begin, int
       if (ctx->s_mean)
         a.w = hmc::WelfordOut{ctx->s_mean, ctx->s_m2, ctx->s_bsize, ctx->bm_sum, ctx->bm_mean, ctx->bm_m2};
       cudaError_t e = hmc::launch_gauss_pair_transitions(a, ctx->tc, n, B, samples, trace_eps, trace_acc,
-                                                         ctx->grid_bar, ctx->stream, &ctx->timer);
+                                                         ctx->grid_bar, ctx->stream, &ctx->timer,
+                                                         pair_remc ? ctx->swapped : nullptr);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "pair transition launch");
     }
     ctx->dom_transitions = chunk;

@@ -70,9 +70,10 @@ constexpr uint32_t kStageBytes = 2 * kStageHalf;  // head + remainder
 constexpr uint32_t kStateBytes = kPairChains * 128 * 4;   // one of position / gradient
 // barriers (8), tmem slot, red [3][4][64], red_pair [3][64], peer_in [3][64],
 // acc_flag [64], prob_s [64], DA state copy, flags, DA coefficients, pair
-// sum, inverse temperatures [64]
+// sum, inverse temperatures [64], tempered log p after the decision [64],
+// exchange flags [64]
 constexpr uint32_t kSmall =
-    8 * 8 + 16 + (3 * 4 * 64 + 3 * 64 + 3 * 64 + 64 + 64) * 4 + 128 + 16 + 32 + 16 + 64 * 4;
+    8 * 8 + 16 + (3 * 4 * 64 + 3 * 64 + 3 * 64 + 64 + 64) * 4 + 128 + 16 + 32 + 16 + 3 * 64 * 4;
 constexpr size_t kSmemUsed =
     2 * kBBytes + 2 * kAHalf + kStageBytes + 2 * kStateBytes + kSmall + 1024;
 // Above half of an SM's shared memory, so that one CTA runs per SM: a CTA
@@ -92,6 +93,8 @@ struct PairArgs {
   float* trace_eps;     // [k] or null
   uint8_t* trace_acc;   // [k][C] or null
   unsigned* grid_bar;   // T > 1: grid barrier counter, zero at launch; null: one transition
+  uint8_t* swapped;     // exchange: [outer chains x (K - 1)] swap flags of the last transition
+  int exchange;         // replica sets (K | 64): the exchange step after every transition
 };
 
 // Index of element e of float4 j of lane `lane` in the tensor-memory image:
@@ -125,6 +128,8 @@ __global__ void k_tmem_image(const float* __restrict__ Phi, const float* __restr
 }
 
 __device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// the leader's 64 deciding threads (epilogue warps 2 and 3)
+__device__ __forceinline__ void deciders_barrier() { asm volatile("bar.sync 2, 64;" ::: "memory"); }
 __device__ __forceinline__ void proxy_fence_cta() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -164,7 +169,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned gen) {
 // p^beta_r, beta_r = betas[(pair_base + r) % K].  Its gradient is
 // -beta_r P x = -P (beta_r x), so the MMA operand tiles hold beta_r x and the
 // epilogue, the energies and the cached log p / gradient come out tempered
-// with no other change.
+// with no other change.  With fa.exchange (K divides 64, so a pair holds
+// whole replica sets) the launch also takes the exchange step after every
+// transition: the leader's deciding threads decide the adjacent pairs
+// (k, k + 1), k = t mod 2, 2 + t mod 2, ..., through remc_swap_accept, and
+// both CTAs swap the rows of their dims in shared memory, rescaling the
+// cached gradients, before the kept sample is written.
 template <bool TEMPERED>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ CUtensorMap mPlo,
@@ -198,6 +208,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   DACoef* coef_s = reinterpret_cast<DACoef*>(reinterpret_cast<uint8_t*>(da_s) + 144);
   double* psum_s = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(da_s) + 176);
   float* beta_s = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(da_s) + 192);   // [64]
+  float* lpn_s = beta_s + 64;                             // [64] exchange: log p after the decision
+  int* swp_s = reinterpret_cast<int*>(lpn_s + 64);        // [64] exchange: row r and r + 1 swap
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = ptx::cluster_rank();              // 0: leader, 1: peer
@@ -568,8 +580,12 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
           const uint32_t gchain = static_cast<uint32_t>(chain) + a.chain_offset;
           acc = accept_log_uniform(a.seed, gchain, t) < la;
           prob = accept_prob(la);
+          if (TEMPERED && fa.exchange) {
+            lpn_s[c] = acc ? lp1 : lp0;
+          } else if (ok && acc) {
+            a.lp[chain] = lp1;
+          }
           if (ok) {
-            if (acc) a.lp[chain] = lp1;
             a.is_accepted[chain] = static_cast<uint8_t>(acc);
             a.log_accept[chain] = la;
             if (k_out >= 0 && fa.trace_acc) fa.trace_acc[k_out * C + chain] = static_cast<uint8_t>(acc);
@@ -578,6 +594,37 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         acc_flag[c] = acc;
         ptx::st_cluster_s32(ptx::mapa(ptx::smem_u32(&acc_flag[c]), 1), acc);
         prob_s[c] = prob;
+        if (TEMPERED && fa.exchange) {
+          // the exchange step: row c decides the pair (c, c + 1) when it is
+          // the lower replica of an active pair, then every row writes its
+          // log p (swapped and rescaled where its pair swapped)
+          deciders_barrier();
+          const int Kr = a.K;
+          const int row = pair_base + c;
+          const int k = row % Kr;
+          const uint32_t cout = static_cast<uint32_t>(row / Kr);
+          int sw = 0;
+          if (row < C && k < Kr - 1) {
+            if ((k & 1) == static_cast<int>(t & 1u)) {
+              float raw0, raw1;
+              sw = remc_swap_accept(lpn_s[c], lpn_s[c + 1], beta_s[c], beta_s[c + 1], a.seed,
+                                    static_cast<uint32_t>(k), cout, t, &raw0, &raw1);
+            }
+            if (ok) fa.swapped[static_cast<int64_t>(cout) * (Kr - 1) + k] = static_cast<uint8_t>(sw);
+          }
+          swp_s[c] = sw;
+          ptx::st_cluster_s32(ptx::mapa(ptx::smem_u32(&swp_s[c]), 1), sw);
+          deciders_barrier();
+          if (row < C && ok) {
+            float lpf = lpn_s[c];
+            if (swp_s[c]) {                        // lower row of a swapped pair
+              lpf = beta_s[c] * (lpn_s[c + 1] / beta_s[c + 1]);
+            } else if (k > 0 && swp_s[c - 1]) {    // upper row of a swapped pair
+              lpf = beta_s[c] * (lpn_s[c - 1] / beta_s[c - 1]);
+            }
+            a.lp[row] = lpf;
+          }
+        }
         if (blockIdx.x == 0 && c == 0 && k_out >= 0 && fa.trace_eps && ok) fa.trace_eps[k_out] = eps;
         ptx::mbar_arrive_cluster(ptx::mapa(ptx::smem_u32(dec_in), 1));
       }
@@ -605,8 +652,36 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
               xrow(i) = x[i];
               grow(i) = -accv[k];
             }
-            if (samp) samp[static_cast<int64_t>(pair_base + rowi(i)) * D + d] = xrow(i);
+            if (samp && !(TEMPERED && fa.exchange))
+              samp[static_cast<int64_t>(pair_base + rowi(i)) * D + d] = xrow(i);
           }
+        }
+      }
+      if (TEMPERED && fa.exchange) {
+        // swap the state rows of this CTA's dims: the owner of the lower row
+        // of each swapped pair exchanges both rows (gradients rescaled as the
+        // exchange kernel does), then the kept sample is written
+        epi_barrier();
+#pragma unroll
+        for (int i = 0; i < kHalf; ++i) {
+          const int r = rowi(i);
+          if (ok && valid(i) && swp_s[r]) {
+            float* x0 = &xs[r * 128 + dl];
+            float* g0 = &gs[r * 128 + dl];
+            const float xa = x0[0], xb = x0[128];
+            const float ga = g0[0], gb = g0[128];
+            const float b0 = beta_s[r], b1 = beta_s[r + 1];
+            x0[0] = xb;
+            x0[128] = xa;
+            g0[0] = gb / b1 * b0;
+            g0[128] = ga / b0 * b1;
+          }
+        }
+        epi_barrier();
+        if (samp) {
+#pragma unroll
+          for (int i = 0; i < kHalf; ++i)
+            if (ok && valid(i)) samp[static_cast<int64_t>(pair_base + rowi(i)) * D + d] = xrow(i);
         }
       }
       if (moments && ok) {
@@ -746,9 +821,11 @@ bool gauss_pair_persistent_ok(int64_t C) {
 // here) and a cooperative launch; partials needs 2 x pairs doubles.
 cudaError_t launch_gauss_pair_transitions(const StepArgs& a, GaussTc& tc, int T, long long keep_from,
                                           float* samples, float* trace_eps, uint8_t* trace_acc,
-                                          unsigned* grid_bar, cudaStream_t s, KernelTimer* timer) {
+                                          unsigned* grid_bar, cudaStream_t s, KernelTimer* timer,
+                                          uint8_t* swapped) {
+  if (swapped && (!a.betas || a.K < 2 || kPairChains % a.K != 0)) return cudaErrorInvalidValue;
   PairArgs fa{a, tc.err, tc.Ptm, tc.p, T, keep_from, samples, trace_eps, trace_acc,
-              T > 1 ? grid_bar : nullptr};
+              T > 1 ? grid_bar : nullptr, swapped, swapped ? 1 : 0};
   if (T > 1) {
     cudaError_t e = cudaMemsetAsync(grid_bar, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;

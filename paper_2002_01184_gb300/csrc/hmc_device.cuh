@@ -85,6 +85,23 @@ __device__ __forceinline__ float accept_log_uniform(uint64_t seed, uint32_t chai
   return log_word_uniform(w.x);
 }
 
+// Replica exchange (Section 2.2) after transition t: replicas k and k + 1 of
+// outer chain c, with tempered log-densities lp0 = b0 log p(x0) and
+// lp1 = b1 log p(x1), swap iff log u < (b0 - b1) (log p(x1) - log p(x0)), u
+// from counter (k, c, t, 2).  raw0 / raw1 receive log p(x0) / log p(x1).
+// Every kernel that exchanges replicas decides through this function, so
+// they agree bit for bit.
+__device__ __forceinline__ bool remc_swap_accept(float lp0, float lp1, float b0, float b1, uint64_t seed,
+                                                 uint32_t k, uint32_t c, uint32_t t, float* raw0,
+                                                 float* raw1) {
+  *raw0 = lp0 / b0;
+  *raw1 = lp1 / b1;
+  const float la = (b0 - b1) * (*raw1 - *raw0);
+  const uint4 u = philox(make_uint4(k, c, t, 2u), static_cast<uint32_t>(seed),
+                         static_cast<uint32_t>(seed >> 32));
+  return log_word_uniform(u.x) < la;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -228,10 +228,13 @@ bool gauss_pair_persistent_ok(int64_t C);
 // T transitions from a.t / a.t_full in one launch; transition t_full >=
 // keep_from writes output k = t_full - keep_from (samples [k][C x D],
 // trace_eps [k], trace_acc [k][C]; each may be null).  T > 1 uses grid_bar
-// (one device counter) and needs gauss_pair_persistent_ok.
+// (one device counter) and needs gauss_pair_persistent_ok.  With swapped
+// non-null (a replica set: a.betas, a.K dividing 64) every transition is
+// followed by the exchange step, its flags left in swapped.
 cudaError_t launch_gauss_pair_transitions(const StepArgs& a, GaussTc& tc, int T, long long keep_from,
                                           float* samples, float* trace_eps, uint8_t* trace_acc,
-                                          unsigned* grid_bar, cudaStream_t s, KernelTimer* timer);
+                                          unsigned* grid_bar, cudaStream_t s, KernelTimer* timer,
+                                          uint8_t* swapped = nullptr);
 unsigned gauss_fused_grid(int64_t C);
 cudaError_t gauss_fused_setup();
 cudaError_t launch_gauss_fused_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,

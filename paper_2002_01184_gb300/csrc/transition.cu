@@ -428,14 +428,9 @@ __global__ void k_remc_swap(int64_t chains, int K, int D, float* __restrict__ x,
   }
   const int64_t r0 = c * K + k, r1 = r0 + 1;
   const float b0 = betas[k], b1 = betas[k + 1];
-  const float raw0 = lp[r0] / b0, raw1 = lp[r1] / b1;
-  const float la = (b0 - b1) * (raw1 - raw0);
-  int sw = 0;
-  if (lane == 0) {
-    const uint4 u = philox(make_uint4(static_cast<uint32_t>(k), static_cast<uint32_t>(c), t, 2u),
-                           static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32));
-    sw = log_word_uniform(u.x) < la;
-  }
+  float raw0, raw1;
+  int sw = remc_swap_accept(lp[r0], lp[r1], b0, b1, seed, static_cast<uint32_t>(k), static_cast<uint32_t>(c),
+                            t, &raw0, &raw1);
   sw = __shfl_sync(0xffffffffu, sw, 0);
   if (sw) {
     for (int d = lane; d < D; d += 32) {

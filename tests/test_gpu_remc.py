@@ -113,3 +113,40 @@ def test_tempered_marginals_on_gpu(H):
         sk2 = s[:, :, k, :] ** 2
         assert abs(sk2.mean() - 1.0 / betas[k]) < 3 * diagnostics.mcse_mean(sk2)[0]
     H.hmc_destroy(ctx)
+
+
+@pytest.mark.parametrize("cap", [0, 1, 7])
+def test_replica_exchange_in_the_pair_launch_equals_step_by_step(H, cap):
+    """sample_chain of a dense-Gaussian replica set runs the exchange step
+    inside the CTA-pair launch (all transitions in one launch, one per launch,
+    or launches of 7): the same kept states, final state and last swap flags
+    as hmc_step followed by the exchange kernel, transition by transition."""
+    from paper_2002_01184_gb300.sampler import _CudaArray
+    C, K, D, L, eps, B, Kk = 48, 4, 64, 5, 0.08, 6, 9
+    betas = (1.0 - np.sqrt(0.6 / D) * np.arange(K)).astype(np.float32)
+    prob = workloads.corr_gauss(dim=D, num_chains=C * K)
+    P = torch.as_tensor(prob.P).cuda()
+    target = H.make_target("corr_gauss", D, P)
+    x0 = (np.random.default_rng(3).standard_normal((C * K, D)) /
+          np.sqrt(np.tile(betas, C))[:, None]).astype(np.float32)
+    ctx1 = H.hmc_remc_create(target, C, betas, H.make_config(L, eps, seed=5, use_graph=False))
+    x1 = torch.as_tensor(x0).cuda().contiguous()
+    H.hmc_bootstrap(ctx1, x1)
+    ref = []
+    for t in range(B + Kk):
+        H.hmc_step(ctx1, x1, t)
+        if t >= B:
+            ref.append(host(x1).copy())
+    sw1 = host(torch.as_tensor(_CudaArray(H.hmc_remc_swaps(ctx1), (C, K - 1), "|u1"), device="cuda")).copy()
+    ctx2 = H.hmc_remc_create(target, C, betas,
+                             H.make_config(L, eps, seed=5, max_transitions_per_launch=cap))
+    x2 = torch.as_tensor(x0).cuda().contiguous()
+    samples = torch.empty((Kk, C * K, D), dtype=torch.float32, device="cuda")
+    H.hmc_sample_chain(ctx2, x2, B, Kk, samples, None, None)
+    sw2 = host(torch.as_tensor(_CudaArray(H.hmc_remc_swaps(ctx2), (C, K - 1), "|u1"), device="cuda"))
+    np.testing.assert_array_equal(host(samples), np.stack(ref))
+    np.testing.assert_array_equal(host(x2), host(x1))
+    np.testing.assert_array_equal(sw2, sw1)
+    assert sw1.any()
+    H.hmc_destroy(ctx1)
+    H.hmc_destroy(ctx2)
