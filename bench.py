@@ -373,6 +373,7 @@ def run_serve(args):
     jobs = server.run(reqs, max_wall=max(60.0, 6 * args.serve_duration))
     clk = clocks.stop()
     summ = serve.summarize(jobs, server.wall)
+    summ["host_s"] = dict(server.host_s)
     line = {"metric": "leapfrog grad-evals/s", "value": summ["grad_evals_per_s"],
             "unit": "grad-evals/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": 1000.0 * server.wall, "higher_is_better": True, "scaling": "weak",

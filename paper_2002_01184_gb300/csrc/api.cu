@@ -171,10 +171,13 @@ bool valid_config(const hmc_config* c, int64_t C, std::string* why) {
   return true;
 }
 
+// Workspace comes from the stream-ordered allocator on the context's stream:
+// creating and destroying contexts (a server admits and retires jobs all the
+// time) then never synchronises the device, as cudaMalloc / cudaFree can.
 template <typename T>
 cudaError_t ctx_alloc(hmc_ctx* ctx, T** p, size_t count) {
   void* v = nullptr;
-  cudaError_t e = cudaMalloc(&v, std::max<size_t>(count * sizeof(T), 16));
+  cudaError_t e = cudaMallocAsync(&v, std::max<size_t>(count * sizeof(T), 16), ctx->stream);
   if (e == cudaSuccess) {
     ctx->allocations.push_back(v);
     *p = static_cast<T*>(v);
@@ -198,9 +201,9 @@ void release(hmc_ctx* ctx) {
   ctx->seg_ready = nullptr;
   if (ctx->copies_done) cudaEventDestroy(ctx->copies_done);
   ctx->copies_done = nullptr;
-  for (void* p : ctx->allocations) cudaFree(p);
+  for (void* p : ctx->allocations) cudaFreeAsync(p, ctx->stream);
   ctx->allocations.clear();
-  if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->stage) cudaFreeAsync(ctx->stage, ctx->stream);
   ctx->stage = nullptr;
 }
 
@@ -259,8 +262,9 @@ cudaError_t enqueue_transition(hmc_ctx* ctx, const StepArgs& a) {
 hmc_status check_device_flag(hmc_ctx* ctx) {
   if (!ctx->use_tc && !ctx->use_lrtc) return HMC_OK;
   int flag = 0;
-  cudaError_t e = cudaMemcpy(&flag, ctx->use_tc ? ctx->tc.err : ctx->lr_err, sizeof(int),
-                             cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpyAsync(&flag, ctx->use_tc ? ctx->tc.err : ctx->lr_err, sizeof(int),
+                                  cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "read device error flag");
   if (flag)
     return fail(ctx, HMC_E_TIMEOUT,
@@ -586,7 +590,8 @@ hmc_status hmc_nuts_leapfrog_count(hmc_ctx* ctx, uint64_t* out) {
     return fail(ctx, HMC_E_INVALID, "the context does not run NUTS");
   unsigned long long v = 0;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
-  if (e == cudaSuccess) e = cudaMemcpy(&v, ctx->nuts_leaves, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, ctx->nuts_leaves, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "read leapfrog count");
   *out = static_cast<uint64_t>(v);
   return HMC_OK;
@@ -707,10 +712,10 @@ hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burni
   const size_t off_a = off_e + (trace_step_size ? a256(K * sizeof(float)) : 0);
   const size_t total = off_a + (trace_accept ? a256(K * ctx->C) : 0);
   if (total > ctx->stage_bytes) {
-    if (ctx->stage) cudaFree(ctx->stage);
+    if (ctx->stage) cudaFreeAsync(ctx->stage, ctx->stream);
     ctx->stage = nullptr;
     ctx->stage_bytes = 0;
-    cudaError_t e = cudaMalloc(&ctx->stage, total);
+    cudaError_t e = cudaMallocAsync(&ctx->stage, total, ctx->stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(ctx, e == cudaErrorMemoryAllocation ? HMC_E_OOM : HMC_E_CUDA,
@@ -826,7 +831,7 @@ hmc_status hmc_remc_create(const hmc_target* target, int64_t num_chains, int32_t
   cudaError_t e = ctx_alloc(ctx, &ctx->betas, static_cast<size_t>(num_replicas));
   if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->swapped, static_cast<size_t>(num_chains * (num_replicas - 1)));
   if (e == cudaSuccess)
-    e = cudaMemcpy(ctx->betas, betas, sizeof(float) * num_replicas, cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(ctx->betas, betas, sizeof(float) * num_replicas, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(ctx->swapped, 0, static_cast<size_t>(num_chains * (num_replicas - 1)),
                         ctx->stream);

@@ -36,3 +36,18 @@ def ess(samples, max_dims=None, chunk_dims=16):
         tau = torch.clamp(tau, min=1.0 / torch.log10(torch.tensor(float(max(n * C, 10)))).item())
         out.append(n * C / tau)
     return torch.cat(out).cpu()
+
+
+def ess_batch_means(samples, max_dims=None):
+    """Replicated batch-means ESS with one batch per chain (the estimator of
+    the streaming driver with batch_size = n): per dimension
+    C n W / (n var_c(chain mean)), W the mean within-chain variance.  A few
+    reductions and no FFT, for callers that need a cheap figure per request.
+    Returns a float64 tensor on the host."""
+    n, C, D = samples.shape
+    s = samples if max_dims is None or max_dims >= D else samples[:, :, torch.linspace(
+        0, D - 1, max_dims).round().long().unique().to(samples.device)]
+    s = s.double()
+    W = s.var(dim=0, unbiased=True).mean(dim=0)
+    V = n * s.mean(dim=0).var(dim=0, unbiased=True)
+    return (C * n * W / V).cpu()

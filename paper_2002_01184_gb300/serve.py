@@ -63,12 +63,14 @@ class Server:
         self.free_slots = list(range(slots))
         self.active = []
         self.done = []
+        self.host_s = {"admit": 0.0, "finish": 0.0}   # host time in the two steps
 
     # -- admission ---------------------------------------------------------
     def fits(self, job):
         return bool(self.free_slots) and self.used + job_bytes(job.problem, self.keep_samples) <= self.budget
 
     def admit(self, job, now):
+        h0 = time.perf_counter()
         p = job.problem
         slot = self.free_slots.pop(0)
         stream = self.streams[slot]
@@ -77,7 +79,7 @@ class Server:
         self.used += job._bytes
         job.admitted = now
         with torch.cuda.stream(stream):
-            job._sampler = Sampler(p, stream=stream, use_graph=False)
+            job._sampler = Sampler(p, stream=stream, use_graph=True)
             x = torch.empty((p.num_chains, p.dim), dtype=torch.float32, device="cuda")
             x.copy_(torch.from_numpy(p.x0).pin_memory(), non_blocking=True)
             job._x = x
@@ -90,6 +92,7 @@ class Server:
             ev.record(stream)
             job._event = ev
         self.active.append(job)
+        self.host_s["admit"] += time.perf_counter() - h0
 
     # -- completion ----------------------------------------------------------
     def poll(self, now_fn):
@@ -102,13 +105,16 @@ class Server:
         self.active = still
 
     def finish(self, job, now):
+        h0 = time.perf_counter()
         p = job.problem
         stream = self.streams[job._slot]
         with torch.cuda.stream(stream):
             res = {"x": job._x.cpu().numpy(), "step_size": job._eps.cpu().numpy(),
                    "accept_rate": float(job._acc.float().mean().item()) if p.num_results else None}
-            if job._samples is not None and p.num_results >= 4:
-                res["min_ess"] = float(diagnostics.ess(job._samples, max_dims=self.ess_dims).min())
+            if job._samples is not None and p.num_results >= 4 and p.num_chains >= 2:
+                # the cheap batch-means figure (one batch per chain): the FFT
+                # estimator's plans and launches cost more than the job itself
+                res["min_ess"] = float(diagnostics.ess_batch_means(job._samples, max_dims=self.ess_dims).min())
                 res["mean"] = job._samples.mean(dim=(0, 1)).cpu().numpy()
             torch.cuda.current_stream().synchronize()
         job.finished = now
@@ -118,6 +124,7 @@ class Server:
         self.used -= job._bytes
         self.free_slots.append(job._slot)
         self.done.append(job)
+        self.host_s["finish"] += time.perf_counter() - h0
 
     # -- the loop ------------------------------------------------------------
     def run(self, requests, time_scale=1.0, max_wall=None):
