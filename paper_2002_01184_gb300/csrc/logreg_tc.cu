@@ -412,32 +412,54 @@ __global__ void k_lr_begin(LrStepArgs b) {
 }
 
 // gradient and log p from the range partials (fixed order) and the prior;
-// leapfrog update (merged kicks + drift), or the final half kick
+// leapfrog update (merged kicks + drift), or the final half kick.  One warp
+// per chain, four dims per lane (float4: every buffer here is the library's
+// own, 16-byte aligned, and D % 4 == 0 on this path), so that a lane's
+// loads of all range partials are in flight together.
 __global__ void k_lr_update(LrStepArgs b) {
   const StepArgs& a = b.s;
   const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (c >= a.C) return;
-  const int D = a.D;
-  const int64_t row = static_cast<int64_t>(c) * D;
+  const int D4 = a.D >> 2;
+  const int64_t row4 = static_cast<int64_t>(c) * D4;
+  const int64_t split4 = static_cast<int64_t>(a.C) * D4;
   const float eps = a.da->eps;
+  const float4* thi = reinterpret_cast<const float4*>(b.thi);
+  const float4* tlo = reinterpret_cast<const float4*>(b.tlo);
+  const float4* Gp = reinterpret_cast<const float4*>(b.Gpart);
+  float4* p4 = reinterpret_cast<float4*>(b.p);
   float sq = 0.f;
-  for (int d = lane; d < D; d += 32) {
-    const float th = b.thi[row + d] + b.tlo[row + d];
-    float g = 0.f;
-    for (int s = 0; s < b.nsplit; ++s) g += b.Gpart[(static_cast<int64_t>(s) * a.C + c) * D + d];
-    g -= th;
-    sq = fmaf(th, th, sq);
+  for (int j = lane; j < D4; j += 32) {
+    const int64_t e = row4 + j;
+    const float4 h = thi[e], l = tlo[e];
+    const float th[4] = {h.x + l.x, h.y + l.y, h.z + l.z, h.w + l.w};
+    float g[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int s = 0; s < b.nsplit; ++s) {
+      const float4 v = Gp[s * split4 + e];
+      g[0] += v.x; g[1] += v.y; g[2] += v.z; g[3] += v.w;
+    }
+    const float4 pv = p4[e];
+    const float pin[4] = {pv.x, pv.y, pv.z, pv.w};
+    float pout[4], hi[4], lo[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      g[k] -= th[k];
+      sq = fmaf(th[k], th[k], sq);
+      if (!b.last) {
+        pout[k] = fmaf(eps, g[k], pin[k]);
+        split_tf32(fmaf(eps, pout[k], th[k]), hi[k], lo[k]);
+      } else {
+        pout[k] = fmaf(0.5f * eps, g[k], pin[k]);
+      }
+    }
+    p4[e] = make_float4(pout[0], pout[1], pout[2], pout[3]);
     if (!b.last) {
-      const float p = fmaf(eps, g, b.p[row + d]);
-      b.p[row + d] = p;
-      float hi, lo;
-      split_tf32(fmaf(eps, p, th), hi, lo);
-      b.thi[row + d] = hi;
-      b.tlo[row + d] = lo;
+      reinterpret_cast<float4*>(b.thi)[e] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      reinterpret_cast<float4*>(b.tlo)[e] = make_float4(lo[0], lo[1], lo[2], lo[3]);
     } else {
-      b.p[row + d] = fmaf(0.5f * eps, g, b.p[row + d]);
-      b.gL[row + d] = g;
+      reinterpret_cast<float4*>(b.gL)[e] = make_float4(g[0], g[1], g[2], g[3]);
     }
   }
   if (b.last) {
