@@ -49,8 +49,10 @@ struct hmc_ctx {
   float* nuts_scratch = nullptr;           // NUTS: trajectory ends, candidates, span starts
   unsigned long long* nuts_leaves = nullptr;   // NUTS: leapfrog steps so far
   int64_t dom_transitions = 1;   // transitions per launch of the dominant kernel (last chain)
-  bool use_lrtc = false;        // tensor-core logistic-regression path
+  bool use_lrtc = false;        // tensor-core logistic-regression path (CTA pairs, dim <= 128)
   hmc::LogregTc lrtc;
+  bool use_lrgemm = false;      // tensor-core logistic regression, one-CTA tile products (dim > 128)
+  hmc::LogregGemm lrg;
   int* lr_err = nullptr;
   // replica exchange (Section 2.2): K replicas per chain, rows c*K + k
   int K = 1;
@@ -250,6 +252,7 @@ cudaError_t enqueue_transition(hmc_ctx* ctx, const StepArgs& a) {
   if (ctx->use_tc) return hmc::launch_gauss_tc_transition(a, ctx->tc, ctx->stream, &ctx->timer);
   if (ctx->use_lrtc)
     return hmc::launch_logreg_tc_transition(a, ctx->lrtc, ctx->lr_err, ctx->stream, &ctx->timer);
+  if (ctx->use_lrgemm) return hmc::launch_logreg_gemm_transition(a, ctx->lrg, ctx->stream, &ctx->timer);
   if (uses_fused_logreg(ctx))
     return hmc::launch_logreg_fused_transition(ctx->target, a, ctx->stream, &ctx->timer);
   if (uses_fused_elementwise(ctx))
@@ -260,9 +263,10 @@ cudaError_t enqueue_transition(hmc_ctx* ctx, const StepArgs& a) {
 
 // After a stream synchronisation: report a bounded device wait that gave up.
 hmc_status check_device_flag(hmc_ctx* ctx) {
-  if (!ctx->use_tc && !ctx->use_lrtc) return HMC_OK;
+  if (!ctx->use_tc && !ctx->use_lrtc && !ctx->use_lrgemm) return HMC_OK;
   int flag = 0;
-  cudaError_t e = cudaMemcpyAsync(&flag, ctx->use_tc ? ctx->tc.err : ctx->lr_err, sizeof(int),
+  cudaError_t e = cudaMemcpyAsync(&flag, ctx->use_tc ? ctx->tc.err : ctx->use_lrtc ? ctx->lr_err : ctx->lrg.err,
+                                  sizeof(int),
                                   cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "read device error flag");
@@ -505,6 +509,15 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->lr_err, 1);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->lr_err, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = hmc::logreg_tc_setup(&ctx->lrtc, *target, num_chains, w, ctx->stream);
+  }
+  // long data passes the pair kernel does not take (dim > 128 or not a
+  // multiple of 4): one-CTA tensor-core products
+  ctx->use_lrgemm = ctx->cfg.impl == HMC_IMPL_FUSED && !ctx->use_lrtc &&
+                    hmc::logreg_gemm_supported(*target) && target->n_data > 2048;
+  if (e == cudaSuccess && ctx->use_lrgemm) {
+    char* w = nullptr;
+    e = ctx_alloc(ctx, &w, hmc::logreg_gemm_workspace_bytes(*target, num_chains));
+    if (e == cudaSuccess) e = hmc::logreg_gemm_setup(&ctx->lrg, *target, num_chains, w, ctx->stream);
   }
   if (e == cudaSuccess && uses_fused_logreg(ctx)) e = hmc::logreg_fused_setup(*target);
   if (e == cudaSuccess && !uses_fused_elementwise(ctx) && !ctx->use_tc) {
@@ -903,7 +916,7 @@ const char* hmc_last_error(const hmc_ctx* ctx) {
 }
 
 int32_t hmc_uses_tensor_cores(const hmc_ctx* ctx) {
-  return ctx && (ctx->use_tc || ctx->use_lrtc) ? 1 : 0;
+  return ctx && (ctx->use_tc || ctx->use_lrtc || ctx->use_lrgemm) ? 1 : 0;
 }
 
 hmc_status hmc_dominant_kernel_info(const hmc_ctx* ctx, char* name, int32_t name_len,
@@ -924,6 +937,8 @@ hmc_status hmc_dominant_kernel_info(const hmc_ctx* ctx, char* name, int32_t name
     n = "k_gauss_tc_step";
   } else if (ctx->use_lrtc) {
     n = "k_lr_grad";
+  } else if (ctx->use_lrgemm) {
+    n = "k_gauss_tc_step<logreg>";   // both products of one gradient
   } else if (uses_fused_logreg(ctx)) {
     n = "k_logreg_fused";
     per = ctx->C * ctx->cfg.num_leapfrog;

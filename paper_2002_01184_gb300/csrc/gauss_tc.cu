@@ -45,8 +45,27 @@ constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;  // 48 KB
 constexpr size_t kSmemBytes = kStages * kStageBytes + 1024 + 256;
 static_assert(kBM * (kBN + 1) * 4 <= kStages * kStageBytes, "epilogue staging must fit the ring");
 
+// Epilogues of the tile product (the pipeline is the same for all three):
+//   kEpiGauss   G = -X P: the dense Gaussian's leapfrog update
+//   kEpiLrResid Z = Theta X^T (columns are data rows): R = y - sigmoid(Z)
+//               to HBM as tf32 head / remainder, 0 past the last row; on
+//               the last step the rows' log-likelihood terms per tile
+//   kEpiLrStep  G = R X (columns are dims): g = G - theta (the N(0, I)
+//               prior) and the leapfrog update; on the last step the
+//               prior's -|theta|^2 / 2 per tile
+constexpr int kEpiGauss = 0, kEpiLrResid = 1, kEpiLrStep = 2;
+
 struct TcStepArgs {
   int C, D;
+  int ld;                   // row length of the trajectory buffers (>= D)
+  int K;                    // contraction length (the Gaussian and Z: D; G: Npad)
+  int ncols;                // output columns (D, or Npad for Z)
+  int nvalid;               // Z: data rows N (R = 0 for columns >= N)
+  const float* y;           // Z: labels [Npad]
+  float* rhi;               // Z: R head / remainder [C x ldr]
+  float* rlo;
+  int ldr;
+  int lp_col0;              // lp_part column of this product's first tile
   int last;                 // 0: middle step, 1: final step of the trajectory
   const float* xhi_in;      // x_l split (this tile's elements are re-read here)
   const float* xlo_in;
@@ -54,12 +73,13 @@ struct TcStepArgs {
   float* xlo_out;
   float* p;                 // momentum, updated in place
   float* g_out;             // final step: gradient at x_L
-  float* lp_part;           // final step: [C x ntn] tile partials of <x, g>/2
-  int ntn;                  // column tiles
+  float* lp_part;           // final step: [C x ntn] tile partials of log p
+  int ntn;                  // lp_part row stride
   const DAState* da;
   int* err;                 // set to 1 if a bounded wait gave up
 };
 
+template <int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                 const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
@@ -74,7 +94,7 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
-  const int nk = (a.D + kBK - 1) / kBK;
+  const int nk = (a.K + kBK - 1) / kBK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -169,33 +189,58 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
       const int r = ew + 4 * rr;
       const int m = m0 + r;
       if (!ok || m >= a.C) continue;                  // warp-uniform
-      const int64_t rowoff = static_cast<int64_t>(m) * a.D;
       float part = 0.f;
+      if (EPI == kEpiLrResid) {
+        const int64_t rowoff = static_cast<int64_t>(m) * a.ldr;
 #pragma unroll
-      for (int h = 0; h < kBN / 32; ++h) {
-        const int cl = lane + 32 * h;
-        const int n = n0 + cl;
-        if (n < a.D) {
-          const int64_t e = rowoff + n;
-          const float g = -stg[r * kLd + cl];
-          const float x = xhi_in[e] + xlo_in[e];
-          if (!a.last) {
-            const float p = fmaf(eps, g, pm[e]);
-            pm[e] = p;
+        for (int h = 0; h < kBN / 32; ++h) {
+          const int cl = lane + 32 * h;
+          const int n = n0 + cl;
+          if (n < a.ncols) {
+            float res = 0.f;
+            if (n < a.nvalid) {
+              const float z = stg[r * kLd + cl];
+              const float yv = a.y[n];
+              res = residual_f(yv, z);
+              if (a.last) part += loglik_f(yv, z);
+            }
             float hi, lo;
-            split_tf32(fmaf(eps, p, x), hi, lo);
-            xhi_out[e] = hi;
-            xlo_out[e] = lo;
-          } else {
-            pm[e] = fmaf(0.5f * eps, g, pm[e]);
-            g_out[e] = g;
-            part = fmaf(x, g, part);
+            split_tf32(res, hi, lo);
+            a.rhi[rowoff + n] = hi;
+            a.rlo[rowoff + n] = lo;
+          }
+        }
+      } else {
+        const int64_t rowoff = static_cast<int64_t>(m) * a.ld;
+#pragma unroll
+        for (int h = 0; h < kBN / 32; ++h) {
+          const int cl = lane + 32 * h;
+          const int n = n0 + cl;
+          if (n < a.D) {
+            const int64_t e = rowoff + n;
+            const float x = xhi_in[e] + xlo_in[e];
+            const float g = EPI == kEpiGauss ? -stg[r * kLd + cl] : stg[r * kLd + cl] - x;
+            if (!a.last) {
+              const float p = fmaf(eps, g, pm[e]);
+              pm[e] = p;
+              float hi, lo;
+              split_tf32(fmaf(eps, p, x), hi, lo);
+              xhi_out[e] = hi;
+              xlo_out[e] = lo;
+            } else {
+              pm[e] = fmaf(0.5f * eps, g, pm[e]);
+              g_out[e] = g;
+              part = EPI == kEpiGauss ? fmaf(x, g, part) : fmaf(x, x, part);
+            }
           }
         }
       }
       if (a.last) {
         part = warp_sum(part);
-        if (lane == 0) a.lp_part[static_cast<int64_t>(m) * a.ntn + blockIdx.y] = 0.5f * part;
+        // Gaussian: log p = <x, g> / 2; logistic regression: the rows'
+        // log-likelihood terms, or the prior's -|theta|^2 / 2
+        const float v = EPI == kEpiLrResid ? part : (EPI == kEpiGauss ? 0.5f * part : -0.5f * part);
+        if (lane == 0) a.lp_part[static_cast<int64_t>(m) * a.ntn + a.lp_col0 + blockIdx.y] = v;
       }
     }
   }
@@ -211,6 +256,7 @@ constexpr int kWarpsPerBlock = 8;
 
 struct TcBeginAccept {
   StepArgs s;
+  int ld;            // row length of p, xhi, xlo, gL (>= D; the state x, g has rows of D)
   float* p;
   float* xhi;        // begin: x1 split out; accept: x_L split in
   float* xlo;
@@ -227,7 +273,7 @@ __global__ void k_gauss_tc_begin(TcBeginAccept b) {
   const int lane = threadIdx.x & 31;
   if (c >= a.C) return;
   const int D = a.D;
-  const int64_t row = static_cast<int64_t>(c) * D;
+  const int64_t row = static_cast<int64_t>(c) * D, rowi = static_cast<int64_t>(c) * b.ld;
   const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
   const float eps = a.da->eps;
   float kin = 0.f;
@@ -235,14 +281,14 @@ __global__ void k_gauss_tc_begin(TcBeginAccept b) {
     const float4 z = momentum4(a.seed, static_cast<uint32_t>(j), chain, a.t);
     const float zz[4] = {z.x, z.y, z.z, z.w};
     for (int i = 0; i < 4 && 4 * j + i < D; ++i) {
-      const int64_t e = row + 4 * j + i;
+      const int64_t e = row + 4 * j + i, ei = rowi + 4 * j + i;
       kin = fmaf(zz[i], zz[i], kin);
       const float p = fmaf(0.5f * eps, a.g[e], zz[i]);
-      b.p[e] = p;
+      b.p[ei] = p;
       float hi, lo;
       split_tf32(fmaf(eps, p, a.x[e]), hi, lo);
-      b.xhi[e] = hi;
-      b.xlo[e] = lo;
+      b.xhi[ei] = hi;
+      b.xlo[ei] = lo;
     }
   }
   kin = warp_sum(kin);
@@ -259,10 +305,10 @@ __global__ void k_gauss_tc_accept(TcBeginAccept b) {
   float prob = 0.f;
   if (has_chain) {
     const int D = a.D;
-    const int64_t row = static_cast<int64_t>(c) * D;
+    const int64_t row = static_cast<int64_t>(c) * D, rowi = static_cast<int64_t>(c) * b.ld;
     const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
     float kin = 0.f;
-    for (int d = lane; d < D; d += 32) kin = fmaf(b.p[row + d], b.p[row + d], kin);
+    for (int d = lane; d < D; d += 32) kin = fmaf(b.p[rowi + d], b.p[rowi + d], kin);
     kin = 0.5f * warp_sum(kin);
     float lp1 = 0.f;
     if (lane == 0)
@@ -274,10 +320,10 @@ __global__ void k_gauss_tc_accept(TcBeginAccept b) {
     if (lane == 0) acc = accept_log_uniform(a.seed, chain, a.t) < la;
     acc = __shfl_sync(0xffffffffu, acc, 0);
     for (int d = lane; d < D; d += 32) {
-      const int64_t e = row + d;
+      const int64_t e = row + d, ei = rowi + d;
       if (acc) {
-        a.x[e] = b.xhi[e] + b.xlo[e];
-        a.g[e] = b.gL[e];
+        a.x[e] = b.xhi[ei] + b.xlo[ei];
+        a.g[e] = b.gL[ei];
       }
       if (a.sample_out) a.sample_out[e] = a.x[e];
     }
@@ -379,7 +425,7 @@ cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws
     ok = make_map(&tc->mAhi[i], tc->xhi[i], C, t.dim, kBM) &&
          make_map(&tc->mAlo[i], tc->xlo[i], C, t.dim, kBM);
   if (!ok) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_gauss_tc_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiGauss>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(kSmemBytes));
   if (e != cudaSuccess) return e;
   if (gauss_fused_supported(t)) {
@@ -409,6 +455,7 @@ cudaError_t launch_gauss_tc_transition(const StepArgs& a, GaussTc& tc, cudaStrea
   b.lp_part = tc.lp_part;
   b.h0 = tc.h0;
   b.ntn = tc.ntn;
+  b.ld = a.D;
   b.xhi = tc.xhi[0];
   b.xlo = tc.xlo[0];
   const unsigned nb = static_cast<unsigned>((a.C + kWarpsPerBlock - 1) / kWarpsPerBlock);
@@ -419,6 +466,10 @@ cudaError_t launch_gauss_tc_transition(const StepArgs& a, GaussTc& tc, cudaStrea
     TcStepArgs st{};
     st.C = a.C;
     st.D = a.D;
+    st.ld = a.D;
+    st.K = a.D;
+    st.ncols = a.D;
+    st.lp_col0 = 0;
     st.last = l == a.L;
     const int in = (l - 1) & 1, out = l & 1;
     st.xhi_in = tc.xhi[in];
@@ -432,12 +483,161 @@ cudaError_t launch_gauss_tc_transition(const StepArgs& a, GaussTc& tc, cudaStrea
     st.da = a.da;
     st.err = tc.err;
     if (timer) timer->begin(s);
-    k_gauss_tc_step<<<grid, kThreads, kSmemBytes, s>>>(tc.mAhi[in], tc.mAlo[in], tc.mBhi, tc.mBlo, st);
+    k_gauss_tc_step<kEpiGauss><<<grid, kThreads, kSmemBytes, s>>>(tc.mAhi[in], tc.mAlo[in], tc.mBhi, tc.mBlo,
+                                                                   st);
     if (timer) timer->end(s);
     count_launch();
   }
   b.xhi = tc.xhi[(a.L - 1) & 1];
   b.xlo = tc.xlo[(a.L - 1) & 1];
+  k_gauss_tc_accept<<<nb, 32 * kWarpsPerBlock, 0, s>>>(b);
+  count_launch();
+  return cudaGetLastError();
+}
+
+
+bool logreg_gemm_supported(const hmc_target& t) {
+  return t.id == HMC_T_LOGREG && t.n_data >= 1 && encode_fn() != nullptr;
+}
+
+namespace {
+// data rows padded to whole 64-row tiles (the residual product's columns,
+// the gradient product's K)
+int64_t lr_npad(int64_t n) { return (n + kBN - 1) / kBN * kBN; }
+size_t a1k(size_t b) { return (b + 1023) & ~static_cast<size_t>(1023); }
+}  // namespace
+
+size_t logreg_gemm_workspace_bytes(const hmc_target& t, int64_t C) {
+  const size_t npad = static_cast<size_t>(lr_npad(t.n_data)), D = static_cast<size_t>((t.dim + 3) / 4 * 4);
+  const size_t ND = npad * D, CN = static_cast<size_t>(C) * npad, CD = static_cast<size_t>(C) * D;
+  const size_t ntot = npad / kBN + (D + kBN - 1) / kBN;
+  return 4 * a1k(ND * 4) + a1k(npad * 4) + 2 * a1k(CN * 4) + 6 * a1k(CD * 4) +
+         a1k(static_cast<size_t>(C) * ntot * 4) + a1k(static_cast<size_t>(C) * 4) + a1k(sizeof(int));
+}
+
+cudaError_t logreg_gemm_setup(LogregGemm* g, const hmc_target& t, int64_t C, void* ws, cudaStream_t s) {
+  const int64_t npad = lr_npad(t.n_data);
+  const int ld = (t.dim + 3) / 4 * 4;      // rows padded for the 16-byte TMA strides
+  const size_t D = static_cast<size_t>(ld);
+  const size_t ND = static_cast<size_t>(npad) * D, CN = static_cast<size_t>(C) * npad,
+               CD = static_cast<size_t>(C) * D;
+  g->npad = static_cast<int>(npad);
+  g->nvalid = static_cast<int>(t.n_data);
+  g->ld = ld;
+  g->nrt = static_cast<int>(npad / kBN);
+  g->ndt = static_cast<int>((D + kBN - 1) / kBN);
+  g->ntot = g->nrt + g->ndt;
+  char* w = static_cast<char*>(ws);
+  auto take = [&](size_t bytes) { char* q = w; w += a1k(bytes); return reinterpret_cast<float*>(q); };
+  g->Xhi = take(ND * 4);
+  g->Xlo = take(ND * 4);
+  g->XThi = take(ND * 4);
+  g->XTlo = take(ND * 4);
+  g->ypad = take(static_cast<size_t>(npad) * 4);
+  g->Rhi = take(CN * 4);
+  g->Rlo = take(CN * 4);
+  for (int i = 0; i < 2; ++i) {
+    g->xhi[i] = take(CD * 4);
+    g->xlo[i] = take(CD * 4);
+  }
+  g->p = take(CD * 4);
+  g->gL = take(CD * 4);
+  g->lp_part = take(static_cast<size_t>(C) * g->ntot * 4);
+  g->h0 = take(static_cast<size_t>(C) * 4);
+  g->err = reinterpret_cast<int*>(take(sizeof(int)));
+  bool ok = make_map(&g->mXhi, g->Xhi, npad, ld, kBN) && make_map(&g->mXlo, g->Xlo, npad, ld, kBN) &&
+            make_map(&g->mRhi, g->Rhi, C, static_cast<int>(npad), kBM) &&
+            make_map(&g->mRlo, g->Rlo, C, static_cast<int>(npad), kBM) &&
+            make_map(&g->mXThi, g->XThi, ld, static_cast<int>(npad), kBN) &&
+            make_map(&g->mXTlo, g->XTlo, ld, static_cast<int>(npad), kBN);
+  for (int i = 0; i < 2 && ok; ++i)
+    ok = make_map(&g->mThi[i], g->xhi[i], C, ld, kBM) && make_map(&g->mTlo[i], g->xlo[i], C, ld, kBM);
+  if (!ok) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiLrResid>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiLrStep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemBytes));
+  if (e == cudaSuccess)
+    e = launch_lr_prepare(static_cast<int>(t.n_data), static_cast<int>(npad), t.dim, ld, t.X, t.y, g->Xhi,
+                          g->Xlo, g->XThi, g->XTlo, g->ypad, s);
+  // the padding columns of the trajectory buffers are read as operands but
+  // never written: zero once (the workspace is contiguous from xhi[0] to gL)
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(g->xhi[0], 0, reinterpret_cast<char*>(g->gL) + a1k(CD * 4) -
+                                          reinterpret_cast<char*>(g->xhi[0]), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->err, 0, sizeof(int), s);
+  return e;
+}
+
+
+// begin; L x (Z = Theta X^T with the residual epilogue, then G = R X with
+// the prior and the leapfrog update); accept.  The timer brackets one
+// gradient (both products).
+cudaError_t launch_logreg_gemm_transition(const StepArgs& a, LogregGemm& g, cudaStream_t s,
+                                          KernelTimer* timer) {
+  TcBeginAccept b{};
+  b.s = a;
+  b.p = g.p;
+  b.gL = g.gL;
+  b.lp_part = g.lp_part;
+  b.h0 = g.h0;
+  b.ntn = g.ntot;
+  b.ld = g.ld;
+  b.xhi = g.xhi[0];
+  b.xlo = g.xlo[0];
+  const unsigned nb = static_cast<unsigned>((a.C + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  k_gauss_tc_begin<<<nb, 32 * kWarpsPerBlock, 0, s>>>(b);
+  count_launch();
+  const unsigned mt = static_cast<unsigned>((a.C + kBM - 1) / kBM);
+  for (int l = 1; l <= a.L; ++l) {
+    const int in = (l - 1) & 1, out = l & 1;
+    const bool last = l == a.L;
+    TcStepArgs z{};
+    z.C = a.C;
+    z.D = a.D;
+    z.ld = g.ld;
+    z.K = g.ld;
+    z.ncols = g.npad;
+    z.nvalid = g.nvalid;
+    z.y = g.ypad;
+    z.rhi = g.Rhi;
+    z.rlo = g.Rlo;
+    z.ldr = g.npad;
+    z.lp_col0 = 0;
+    z.last = last;
+    z.lp_part = g.lp_part;
+    z.ntn = g.ntot;
+    z.da = a.da;
+    z.err = g.err;
+    TcStepArgs st{};
+    st.C = a.C;
+    st.D = a.D;
+    st.ld = g.ld;
+    st.K = g.npad;
+    st.ncols = a.D;
+    st.last = last;
+    st.xhi_in = g.xhi[in];
+    st.xlo_in = g.xlo[in];
+    st.xhi_out = g.xhi[out];
+    st.xlo_out = g.xlo[out];
+    st.p = g.p;
+    st.g_out = g.gL;
+    st.lp_part = g.lp_part;
+    st.ntn = g.ntot;
+    st.lp_col0 = g.nrt;
+    st.da = a.da;
+    st.err = g.err;
+    if (timer) timer->begin(s);
+    k_gauss_tc_step<kEpiLrResid><<<dim3(mt, g.nrt), kThreads, kSmemBytes, s>>>(g.mThi[in], g.mTlo[in], g.mXhi,
+                                                                             g.mXlo, z);
+    k_gauss_tc_step<kEpiLrStep><<<dim3(mt, g.ndt), kThreads, kSmemBytes, s>>>(g.mRhi, g.mRlo, g.mXThi,
+                                                                            g.mXTlo, st);
+    if (timer) timer->end(s);
+    count_launch(2);
+  }
+  b.xhi = g.xhi[(a.L - 1) & 1];
+  b.xlo = g.xlo[(a.L - 1) & 1];
   k_gauss_tc_accept<<<nb, 32 * kWarpsPerBlock, 0, s>>>(b);
   count_launch();
   return cudaGetLastError();

@@ -356,6 +356,21 @@ __device__ __forceinline__ void welford_update_n(const W& w, const WelfordCoef& 
   }
 }
 
+// Logistic regression (the tensor-core products' epilogues).  y - sigmoid(z)
+// for the gradient with the fast exponential and divide (a few ulp; the
+// gradient tolerance is orders of magnitude looser):
+__device__ __forceinline__ float residual_f(float y, float z) {
+  const float e = __expf(-fabsf(z));
+  const float inv = __fdividef(1.f, 1.f + e);
+  return y - (z >= 0.f ? inv : e * inv);
+}
+
+// y z - softplus(z) for log p, correctly rounded building blocks (the
+// accept test compares sums over all rows)
+__device__ __forceinline__ float loglik_f(float y, float z) {
+  return y * z - (fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))));
+}
+
 // Split x into its tf32 head (10 explicit mantissa bits) and the exact float32
 // remainder: x = hi + lo exactly.  Used by the 3xTF32 products.
 __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {

@@ -209,6 +209,45 @@ struct GaussTc {
   bool pair = false;         // ... on CTA pairs (cta_group::2)
 };
 
+// X -> tf32 head / remainder [Npad x ld] and the transposed copies [ld x Npad];
+// rows >= N and columns >= D zero; y -> ypad [Npad] (logreg_tc.cu)
+cudaError_t launch_lr_prepare(int N, int Npad, int D, int ld, const float* X, const float* y, float* Xhi,
+                              float* Xlo, float* XThi, float* XTlo, float* ypad, cudaStream_t s);
+
+// Logistic regression for dims the CTA-pair kernel does not take (dim > 128;
+// rows padded to ld = dim rounded up to 4 inside the workspace): each leapfrog gradient is two one-CTA tcgen05 products
+// (gauss_tc.cu's tile pipeline): Z = Theta X^T with R = y - sigmoid(Z) in
+// the epilogue (R to HBM as tf32 head / remainder), then G = R X with the
+// prior and the leapfrog update in the epilogue.
+struct LogregGemm {
+  CUtensorMap mThi[2], mTlo[2];  // positions [C x D], 128-row boxes (A of Z)
+  CUtensorMap mXhi, mXlo;        // X [Npad x D], 64-row boxes (B of Z)
+  CUtensorMap mRhi, mRlo;        // R [C x Npad], 128-row boxes (A of G)
+  CUtensorMap mXThi, mXTlo;      // X^T [D x Npad], 64-row boxes (B of G)
+  float* Xhi = nullptr;
+  float* Xlo = nullptr;
+  float* XThi = nullptr;
+  float* XTlo = nullptr;
+  float* ypad = nullptr;
+  float* Rhi = nullptr;
+  float* Rlo = nullptr;
+  float* xhi[2] = {nullptr, nullptr};
+  float* xlo[2] = {nullptr, nullptr};
+  float* p = nullptr;
+  float* gL = nullptr;
+  float* lp_part = nullptr;      // [C x ntot]: row tiles' log-likelihood, then dim tiles' prior
+  float* h0 = nullptr;
+  int* err = nullptr;
+  int npad = 0, nrt = 0, ndt = 0, ntot = 0;
+  int nvalid = 0;                // data rows N
+  int ld = 0;                    // padded row length of the workspace arrays
+};
+bool logreg_gemm_supported(const hmc_target& t);
+size_t logreg_gemm_workspace_bytes(const hmc_target& t, int64_t C);
+cudaError_t logreg_gemm_setup(LogregGemm* g, const hmc_target& t, int64_t C, void* ws, cudaStream_t s);
+cudaError_t launch_logreg_gemm_transition(const StepArgs& a, LogregGemm& g, cudaStream_t s,
+                                          KernelTimer* timer);
+
 bool gauss_tc_supported(const hmc_target& t);
 size_t gauss_tc_workspace_bytes(const hmc_target& t, int64_t C);
 cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s);

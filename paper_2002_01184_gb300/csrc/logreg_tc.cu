@@ -68,20 +68,6 @@ struct LrTcArgs {
   int* err;
 };
 
-// y - sigmoid(z) for the gradient: the fast exponential and divide (a few
-// ulp; the gradient tolerance is orders of magnitude looser)
-__device__ __forceinline__ float residual_f(float y, float z) {
-  const float e = __expf(-fabsf(z));
-  const float inv = __fdividef(1.f, 1.f + e);
-  return y - (z >= 0.f ? inv : e * inv);
-}
-
-// y z - softplus(z) for log p, correctly rounded building blocks (the
-// accept test compares sums over all rows)
-__device__ __forceinline__ float loglik_f(float y, float z) {
-  return y * z - (fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))));
-}
-
 __global__ void __launch_bounds__(kThreads, 1)
 k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUtensorMap mTlo,
           const __grid_constant__ CUtensorMap mXhi, const __grid_constant__ CUtensorMap mXlo,
@@ -512,16 +498,17 @@ __global__ void k_lr_accept(LrStepArgs b) {
   accept_block_finish<kWarpsPerBlock>(a.da, a.partials, prob, has_chain, a.C, a.t_full);
 }
 
-// X -> head / remainder, and the transposed copy [D x Npad]; rows >= N zero
-__global__ void k_lr_prepare(int N, int Npad, int D, const float* __restrict__ X,
+// X -> head / remainder [Npad x ld], and the transposed copy [ld x Npad];
+// rows >= N and columns >= D zero (ld >= D: the padded row length)
+__global__ void k_lr_prepare(int N, int Npad, int D, int ld, const float* __restrict__ X,
                              const float* __restrict__ y, float* __restrict__ Xhi,
                              float* __restrict__ Xlo, float* __restrict__ XThi,
                              float* __restrict__ XTlo, float* __restrict__ ypad) {
-  const int64_t total = static_cast<int64_t>(Npad) * D;
+  const int64_t total = static_cast<int64_t>(Npad) * ld;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int n = static_cast<int>(i / D), d = static_cast<int>(i % D);
-    const float v = n < N ? X[static_cast<int64_t>(n) * D + d] : 0.f;
+    const int n = static_cast<int>(i / ld), d = static_cast<int>(i % ld);
+    const float v = n < N && d < D ? X[static_cast<int64_t>(n) * D + d] : 0.f;
     float hi, lo;
     split_tf32(v, hi, lo);
     Xhi[i] = hi;
@@ -578,6 +565,15 @@ Plan plan(const hmc_target& t, int64_t C) {
 
 }  // namespace
 
+cudaError_t launch_lr_prepare(int N, int Npad, int D, int ld, const float* X, const float* y, float* Xhi,
+                              float* Xlo, float* XThi, float* XTlo, float* ypad, cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(Npad) * ld;
+  k_lr_prepare<<<static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 152 * 16)), 256, 0, s>>>(
+      N, Npad, D, ld, X, y, Xhi, Xlo, XThi, XTlo, ypad);
+  count_launch();
+  return cudaGetLastError();
+}
+
 bool logreg_tc_supported(const hmc_target& t) {
   return t.id == HMC_T_LOGREG && t.dim <= kMaxD && t.dim % 4 == 0 && encode() != nullptr;
 }
@@ -625,7 +621,7 @@ cudaError_t logreg_tc_setup(LogregTc* tc, const hmc_target& t, int64_t C, void* 
   if (e != cudaSuccess) return e;
   const int64_t total = static_cast<int64_t>(p.npad) * t.dim;
   k_lr_prepare<<<static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 152 * 16)), 256, 0, s>>>(
-      static_cast<int>(t.n_data), p.npad, t.dim, t.X, t.y, tc->Xhi, tc->Xlo, tc->XThi, tc->XTlo,
+      static_cast<int>(t.n_data), p.npad, t.dim, t.dim, t.X, t.y, tc->Xhi, tc->Xlo, tc->XThi, tc->XTlo,
       tc->ypad);
   count_launch();
   return cudaGetLastError();

@@ -96,7 +96,12 @@ def test_tensor_core_and_plain_paths_agree(H):
 
 # logistic regression on tensor cores: (chains, dim, data rows, step, L) --
 # ragged chain groups, ragged last data tile, dims below / at the 128 limit
-LOGREG_CASES = [(130, 64, 2500, 0.01, 3), (200, 128, 4100, 0.005, 2), (64, 20, 2049, 0.02, 4)]
+LOGREG_CASES = [(130, 64, 2500, 0.01, 3), (200, 128, 4100, 0.005, 2), (64, 20, 2049, 0.02, 4),
+                # dims past the pair kernel's 128: one-CTA tile products (dim 260 leaves a
+                # ragged K-chunk, 2500 a ragged data tile)
+                (150, 160, 2500, 0.008, 3), (70, 260, 3001, 0.005, 2), (300, 512, 2100, 0.003, 2),
+                # rows padded to a multiple of 4 inside the workspace
+                (90, 203, 2300, 0.005, 2), (40, 37, 2100, 0.01, 3)]
 
 
 @pytest.mark.parametrize("C,D,N,eps,L", LOGREG_CASES)
@@ -107,7 +112,8 @@ def test_tensor_core_logreg_transition_matches_oracle(H, C, D, N, eps, L):
     p.x0 = (0.05 * np.random.default_rng(D).standard_normal((C, D))).astype(np.float32)
     s = Sampler(p, adapt=False)
     assert H.hmc_uses_tensor_cores(s.ctx)
-    assert H.hmc_dominant_kernel_info(s.ctx)[0] == "k_lr_grad"
+    pair = D <= 128 and D % 4 == 0
+    assert H.hmc_dominant_kernel_info(s.ctx)[0] == ("k_lr_grad" if pair else "k_gauss_tc_step<logreg>")
     x = torch.as_tensor(p.x0).cuda().contiguous()
     s.bootstrap(x)
     tgt = otargets.make("logreg", X=p.X, y=p.y)
