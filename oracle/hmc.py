@@ -97,6 +97,8 @@ def one_step(x, lp, g, eps, num_leapfrog, seed, t, target, chain_offset=0):
         "log_accept_ratio": log_alpha,
         "log_u": log_u,
         "proposed_x": x1,
+        "h0": h0,
+        "h1": h1,
     }
 
 

@@ -23,6 +23,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "hmc_device.cuh"
@@ -34,6 +35,7 @@ namespace hmc {
 namespace {
 
 constexpr int kBM = 128;          // chains per tile (MMA M)
+constexpr int64_t kNumSms = 152;
 constexpr int kBN = 64;           // gradient columns per tile (MMA N)
 constexpr int kBK = 32;           // K chunk: 32 floats = one 128-B swizzle row
 constexpr int kStages = 4;
@@ -53,7 +55,9 @@ static_assert(kBM * (kBN + 1) * 4 <= kStages * kStageBytes, "epilogue staging mu
 //   kEpiLrStep  G = R X (columns are dims): g = G - theta (the N(0, I)
 //               prior) and the leapfrog update; on the last step the
 //               prior's -|theta|^2 / 2 per tile
-constexpr int kEpiGauss = 0, kEpiLrResid = 1, kEpiLrStep = 2;
+//   kEpiStore   the raw product of K-split blockIdx.z, for a separate sum
+//               (G = R X when its few tiles would leave SMs idle)
+constexpr int kEpiGauss = 0, kEpiLrResid = 1, kEpiLrStep = 2, kEpiStore = 3;
 
 struct TcStepArgs {
   int C, D;
@@ -66,6 +70,8 @@ struct TcStepArgs {
   float* rlo;
   int ldr;
   int lp_col0;              // lp_part column of this product's first tile
+  int kc_split;             // kEpiStore: K-chunks per split (split = blockIdx.z)
+  float* part;              // kEpiStore: [splits x C x ld] products
   int last;                 // 0: middle step, 1: final step of the trajectory
   const float* xhi_in;      // x_l split (this tile's elements are re-read here)
   const float* xlo_in;
@@ -94,7 +100,9 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
-  const int nk = (a.K + kBK - 1) / kBK;
+  const int nk_all = (a.K + kBK - 1) / kBK;
+  const int kc0 = EPI == kEpiStore ? static_cast<int>(blockIdx.z) * a.kc_split : 0;
+  const int nk = EPI == kEpiStore ? min(a.kc_split, nk_all - kc0) : nk_all;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -127,10 +135,11 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
       }
       uint8_t* st = smem + s * kStageBytes;
       ptx::mbar_arrive_expect_tx(&full[s], kStageBytes);
-      ptx::tma_load_2d(st, &mAhi, &full[s], kc * kBK, m0);
-      ptx::tma_load_2d(st + kABytes, &mAlo, &full[s], kc * kBK, m0);
-      ptx::tma_load_2d(st + 2 * kABytes, &mBhi, &full[s], kc * kBK, n0);
-      ptx::tma_load_2d(st + 2 * kABytes + kBBytes, &mBlo, &full[s], kc * kBK, n0);
+      const int kx = (kc0 + kc) * kBK;
+      ptx::tma_load_2d(st, &mAhi, &full[s], kx, m0);
+      ptx::tma_load_2d(st + kABytes, &mAlo, &full[s], kx, m0);
+      ptx::tma_load_2d(st + 2 * kABytes, &mBhi, &full[s], kx, n0);
+      ptx::tma_load_2d(st + 2 * kABytes + kBBytes, &mBlo, &full[s], kx, n0);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
@@ -190,6 +199,15 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
       const int m = m0 + r;
       if (!ok || m >= a.C) continue;                  // warp-uniform
       float part = 0.f;
+      if (EPI == kEpiStore) {
+        float* out = a.part + (static_cast<int64_t>(blockIdx.z) * a.C + m) * a.ld;
+#pragma unroll
+        for (int h = 0; h < kBN / 32; ++h) {
+          const int n = n0 + lane + 32 * h;
+          if (n < a.D) out[n] = stg[r * kLd + lane + 32 * h];
+        }
+        continue;
+      }
       if (EPI == kEpiLrResid) {
         const int64_t rowoff = static_cast<int64_t>(m) * a.ldr;
 #pragma unroll
@@ -337,6 +355,74 @@ __global__ void k_gauss_tc_accept(TcBeginAccept b) {
     prob = accept_prob(la);
   }
   accept_block_finish<kWarpsPerBlock>(a.da, a.partials, prob, has_chain, a.C, a.t_full);
+}
+
+// The logistic regression's split-K gradient: the splits' products summed in
+// split order, minus theta (the prior), and the leapfrog update -- the
+// kEpiLrStep epilogue for a product computed in K-splits.  Warp per chain,
+// four dims per lane (ld % 4 == 0; the library's own buffers).
+struct LrSumArgs {
+  int C, D, ld, S, last, nrt, ntot;
+  const float* part;        // [S x C x ld]
+  const float* xhi_in;
+  const float* xlo_in;
+  float* xhi_out;
+  float* xlo_out;
+  float* p;
+  float* g_out;
+  float* lp_part;
+  const DAState* da;
+};
+
+__global__ void k_lr_gemm_update(LrSumArgs b) {
+  const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= b.C) return;
+  const int ld4 = b.ld >> 2;
+  const int64_t row4 = static_cast<int64_t>(c) * ld4, split4 = static_cast<int64_t>(b.C) * ld4;
+  const float eps = b.da->eps;
+  const float4* part = reinterpret_cast<const float4*>(b.part);
+  float sq = 0.f;
+  for (int j = lane; j < ld4; j += 32) {
+    const int64_t e = row4 + j;
+    const float4 h = reinterpret_cast<const float4*>(b.xhi_in)[e];
+    const float4 l = reinterpret_cast<const float4*>(b.xlo_in)[e];
+    const float th[4] = {h.x + l.x, h.y + l.y, h.z + l.z, h.w + l.w};
+    float g[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int sp = 0; sp < b.S; ++sp) {
+      const float4 v = part[sp * split4 + e];
+      g[0] += v.x; g[1] += v.y; g[2] += v.z; g[3] += v.w;
+    }
+    const float4 pv = reinterpret_cast<float4*>(b.p)[e];
+    const float pin[4] = {pv.x, pv.y, pv.z, pv.w};
+    float pout[4], hi[4], lo[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      // padding dims (>= D) hold zeros everywhere and stay zero
+      g[k] = 4 * j + k < b.D ? g[k] - th[k] : 0.f;
+      if (!b.last) {
+        pout[k] = fmaf(eps, g[k], pin[k]);
+        split_tf32(fmaf(eps, pout[k], th[k]), hi[k], lo[k]);
+      } else {
+        pout[k] = fmaf(0.5f * eps, g[k], pin[k]);
+        sq = fmaf(th[k], th[k], sq);
+      }
+    }
+    reinterpret_cast<float4*>(b.p)[e] = make_float4(pout[0], pout[1], pout[2], pout[3]);
+    if (!b.last) {
+      reinterpret_cast<float4*>(b.xhi_out)[e] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      reinterpret_cast<float4*>(b.xlo_out)[e] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+    } else {
+      reinterpret_cast<float4*>(b.g_out)[e] = make_float4(g[0], g[1], g[2], g[3]);
+    }
+  }
+  if (b.last) {
+    sq = warp_sum(sq);
+    // the prior's -|theta|^2 / 2 in the first prior column, the others zero
+    for (int k = lane; k < b.ntot - b.nrt; k += 32)
+      b.lp_part[static_cast<int64_t>(c) * b.ntot + b.nrt + k] = k == 0 ? -0.5f * sq : 0.f;
+  }
 }
 
 // P -> (tf32 head, float32 remainder)
@@ -504,6 +590,8 @@ namespace {
 // data rows padded to whole 64-row tiles (the residual product's columns,
 // the gradient product's K)
 int64_t lr_npad(int64_t n) { return (n + kBN - 1) / kBN * kBN; }
+// the most K-splits of the gradient product G = R X
+constexpr int kMaxSplit = 8;
 size_t a1k(size_t b) { return (b + 1023) & ~static_cast<size_t>(1023); }
 }  // namespace
 
@@ -512,7 +600,8 @@ size_t logreg_gemm_workspace_bytes(const hmc_target& t, int64_t C) {
   const size_t ND = npad * D, CN = static_cast<size_t>(C) * npad, CD = static_cast<size_t>(C) * D;
   const size_t ntot = npad / kBN + (D + kBN - 1) / kBN;
   return 4 * a1k(ND * 4) + a1k(npad * 4) + 2 * a1k(CN * 4) + 6 * a1k(CD * 4) +
-         a1k(static_cast<size_t>(C) * ntot * 4) + a1k(static_cast<size_t>(C) * 4) + a1k(sizeof(int));
+         a1k(static_cast<size_t>(C) * ntot * 4) + a1k(static_cast<size_t>(C) * 4) + a1k(sizeof(int)) +
+         a1k(kMaxSplit * CD * 4);
 }
 
 cudaError_t logreg_gemm_setup(LogregGemm* g, const hmc_target& t, int64_t C, void* ws, cudaStream_t s) {
@@ -545,6 +634,7 @@ cudaError_t logreg_gemm_setup(LogregGemm* g, const hmc_target& t, int64_t C, voi
   g->lp_part = take(static_cast<size_t>(C) * g->ntot * 4);
   g->h0 = take(static_cast<size_t>(C) * 4);
   g->err = reinterpret_cast<int*>(take(sizeof(int)));
+  g->part = take(kMaxSplit * CD * 4);
   bool ok = make_map(&g->mXhi, g->Xhi, npad, ld, kBN) && make_map(&g->mXlo, g->Xlo, npad, ld, kBN) &&
             make_map(&g->mRhi, g->Rhi, C, static_cast<int>(npad), kBM) &&
             make_map(&g->mRlo, g->Rlo, C, static_cast<int>(npad), kBM) &&
@@ -557,6 +647,9 @@ cudaError_t logreg_gemm_setup(LogregGemm* g, const hmc_target& t, int64_t C, voi
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiLrStep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemBytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiStore>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kSmemBytes));
   if (e == cudaSuccess)
     e = launch_lr_prepare(static_cast<int>(t.n_data), static_cast<int>(npad), t.dim, ld, t.X, t.y, g->Xhi,
@@ -590,6 +683,16 @@ cudaError_t launch_logreg_gemm_transition(const StepArgs& a, LogregGemm& g, cuda
   k_gauss_tc_begin<<<nb, 32 * kWarpsPerBlock, 0, s>>>(b);
   count_launch();
   const unsigned mt = static_cast<unsigned>((a.C + kBM - 1) / kBM);
+  // G = R X has K = Npad but only mt x ndt tiles: split K when the tiles
+  // would not fill two waves of the SMs, and sum the splits afterwards
+  const int nk_all = g.npad / kBK;
+  const int64_t tiles = static_cast<int64_t>(mt) * g.ndt;
+  int S = 1, kc_split = nk_all;
+  if (tiles < 2 * kNumSms && nk_all >= 2) {
+    S = static_cast<int>(std::min<int64_t>({kMaxSplit, (2 * kNumSms + tiles - 1) / tiles, nk_all}));
+    kc_split = (nk_all + S - 1) / S;
+    S = (nk_all + kc_split - 1) / kc_split;      // every split has at least one chunk
+  }
   for (int l = 1; l <= a.L; ++l) {
     const int in = (l - 1) & 1, out = l & 1;
     const bool last = l == a.L;
@@ -631,8 +734,19 @@ cudaError_t launch_logreg_gemm_transition(const StepArgs& a, LogregGemm& g, cuda
     if (timer) timer->begin(s);
     k_gauss_tc_step<kEpiLrResid><<<dim3(mt, g.nrt), kThreads, kSmemBytes, s>>>(g.mThi[in], g.mTlo[in], g.mXhi,
                                                                              g.mXlo, z);
-    k_gauss_tc_step<kEpiLrStep><<<dim3(mt, g.ndt), kThreads, kSmemBytes, s>>>(g.mRhi, g.mRlo, g.mXThi,
-                                                                            g.mXTlo, st);
+    if (S == 1) {
+      k_gauss_tc_step<kEpiLrStep><<<dim3(mt, g.ndt), kThreads, kSmemBytes, s>>>(g.mRhi, g.mRlo, g.mXThi,
+                                                                              g.mXTlo, st);
+    } else {
+      st.kc_split = kc_split;
+      st.part = g.part;
+      k_gauss_tc_step<kEpiStore><<<dim3(mt, g.ndt, S), kThreads, kSmemBytes, s>>>(g.mRhi, g.mRlo, g.mXThi,
+                                                                                g.mXTlo, st);
+      LrSumArgs u{a.C, a.D, g.ld, S, last ? 1 : 0, g.nrt, g.ntot, g.part, g.xhi[in], g.xlo[in],
+                  g.xhi[out], g.xlo[out], g.p, g.gL, g.lp_part, a.da};
+      k_lr_gemm_update<<<nb, 32 * kWarpsPerBlock, 0, s>>>(u);
+      count_launch();
+    }
     if (timer) timer->end(s);
     count_launch(2);
   }

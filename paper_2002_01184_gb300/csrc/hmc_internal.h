@@ -241,6 +241,7 @@ struct LogregGemm {
   int npad = 0, nrt = 0, ndt = 0, ntot = 0;
   int nvalid = 0;                // data rows N
   int ld = 0;                    // padded row length of the workspace arrays
+  float* part = nullptr;         // split-K products of G = R X [splits x C x ld]
 };
 bool logreg_gemm_supported(const hmc_target& t);
 size_t logreg_gemm_workspace_bytes(const hmc_target& t, int64_t C);

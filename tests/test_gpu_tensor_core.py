@@ -101,7 +101,10 @@ LOGREG_CASES = [(130, 64, 2500, 0.01, 3), (200, 128, 4100, 0.005, 2), (64, 20, 2
                 # ragged K-chunk, 2500 a ragged data tile)
                 (150, 160, 2500, 0.008, 3), (70, 260, 3001, 0.005, 2), (300, 512, 2100, 0.003, 2),
                 # rows padded to a multiple of 4 inside the workspace
-                (90, 203, 2300, 0.005, 2), (40, 37, 2100, 0.01, 3)]
+                (90, 203, 2300, 0.005, 2), (40, 37, 2100, 0.01, 3),
+                # 38 x 8 = 304 tiles of G = R X fill two waves of the SMs: no K-split
+                # (the cases above split K and sum the splits)
+                (4864, 452, 2100, 0.003, 1)]
 
 
 @pytest.mark.parametrize("C,D,N,eps,L", LOGREG_CASES)
@@ -133,5 +136,5 @@ def test_tensor_core_logreg_transition_matches_oracle(H, C, D, N, eps, L):
         gg = host(r["grad"])
         row = np.max(np.abs(g_new), axis=1, keepdims=True)
         assert np.max(np.abs(gg - g_new) / np.maximum(row, 1e-6)) < 1e-4
-    assert n_same >= 3 * C - 2
+    assert n_same >= 3 * C - max(2, C // 500)      # decisions inside the float32 band
     s.close()
