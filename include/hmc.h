@@ -233,8 +233,8 @@ hmc_status hmc_synchronize(hmc_ctx* ctx);
 
 /* 1 if the context's transitions run the tensor-core (tcgen05, 3xTF32)
  * kernels under HMC_IMPL_FUSED: CORR_GAUSS with dim % 4 == 0, or LOGREG with
- * n_data > 2048 (CTA pairs for dim % 4 == 0 and dim <= 128, one-CTA tile
- * products otherwise).  0 otherwise. */
+ * n_data > 2048 or chains x n_data x dim > 2^22 (CTA pairs for dim % 4 == 0
+ * and dim <= 128, one-CTA tile products otherwise).  0 otherwise. */
 int32_t hmc_uses_tensor_cores(const hmc_ctx* ctx);
 
 /* Measurement support (no counterpart in the paper): the name of the kernel

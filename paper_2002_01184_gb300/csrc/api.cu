@@ -214,7 +214,7 @@ bool fused_impl(const hmc_ctx* ctx) {
 }
 
 bool uses_fused_logreg(const hmc_ctx* ctx) {
-  return fused_impl(ctx) && !ctx->use_lrtc && hmc::logreg_fused_supported(ctx->target);
+  return fused_impl(ctx) && !ctx->use_lrtc && !ctx->use_lrgemm && hmc::logreg_fused_supported(ctx->target);
 }
 
 bool uses_fused_elementwise(const hmc_ctx* ctx) {
@@ -499,10 +499,12 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     ctx->tc.pair = ctx->tc.fused && ctx->cfg.impl == HMC_IMPL_FUSED;
     if (e == cudaSuccess && ctx->tc.pair) e = ctx_alloc(ctx, &ctx->grid_bar, 1);
   }
-  // logistic regressions with long data passes: tensor-core products; short
-  // ones: the shared-memory SIMT transition
-  ctx->use_lrtc = ctx->cfg.impl == HMC_IMPL_FUSED && hmc::logreg_tc_supported(*target) &&
-                  target->n_data > 2048;
+  // logistic regressions with long data passes or much work per gradient
+  // (chains x rows x dim above 2^22): tensor-core products; small ones: the
+  // shared-memory SIMT transition
+  const bool lr_big = target->id == HMC_T_LOGREG &&
+                      (target->n_data > 2048 || num_chains * target->n_data * target->dim > (1ll << 22));
+  ctx->use_lrtc = ctx->cfg.impl == HMC_IMPL_FUSED && hmc::logreg_tc_supported(*target) && lr_big;
   if (e == cudaSuccess && ctx->use_lrtc) {
     char* w = nullptr;
     e = ctx_alloc(ctx, &w, hmc::logreg_tc_workspace_bytes(*target, num_chains));
@@ -513,7 +515,7 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   // long data passes the pair kernel does not take (dim > 128 or not a
   // multiple of 4): one-CTA tensor-core products
   ctx->use_lrgemm = ctx->cfg.impl == HMC_IMPL_FUSED && !ctx->use_lrtc &&
-                    hmc::logreg_gemm_supported(*target) && target->n_data > 2048;
+                    hmc::logreg_gemm_supported(*target) && lr_big;
   if (e == cudaSuccess && ctx->use_lrgemm) {
     char* w = nullptr;
     e = ctx_alloc(ctx, &w, hmc::logreg_gemm_workspace_bytes(*target, num_chains));

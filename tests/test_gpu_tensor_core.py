@@ -104,7 +104,9 @@ LOGREG_CASES = [(130, 64, 2500, 0.01, 3), (200, 128, 4100, 0.005, 2), (64, 20, 2
                 (90, 203, 2300, 0.005, 2), (40, 37, 2100, 0.01, 3),
                 # 38 x 8 = 304 tiles of G = R X fill two waves of the SMs: no K-split
                 # (the cases above split K and sum the splits)
-                (4864, 452, 2100, 0.003, 1)]
+                (4864, 452, 2100, 0.003, 1),
+                # short data passes with much work per gradient (chains x rows x dim > 2^22)
+                (600, 100, 1500, 0.005, 2), (500, 90, 1000, 0.006, 2)]
 
 
 @pytest.mark.parametrize("C,D,N,eps,L", LOGREG_CASES)
