@@ -35,7 +35,6 @@ namespace hmc {
 namespace {
 
 constexpr int kBM = 128;          // chains per tile (MMA M)
-constexpr int64_t kNumSms = 152;
 constexpr int kBN = 64;           // gradient columns per tile (MMA N)
 constexpr int kBK = 32;           // K chunk: 32 floats = one 128-B swizzle row
 constexpr int kStages = 4;
@@ -613,6 +612,10 @@ cudaError_t logreg_gemm_setup(LogregGemm* g, const hmc_target& t, int64_t C, voi
   g->npad = static_cast<int>(npad);
   g->nvalid = static_cast<int>(t.n_data);
   g->ld = ld;
+  int dev = 0;
+  cudaError_t qe = cudaGetDevice(&dev);
+  if (qe == cudaSuccess) qe = cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (qe != cudaSuccess) return qe;
   g->nrt = static_cast<int>(npad / kBN);
   g->ndt = static_cast<int>((D + kBN - 1) / kBN);
   g->ntot = g->nrt + g->ndt;
@@ -688,8 +691,9 @@ cudaError_t launch_logreg_gemm_transition(const StepArgs& a, LogregGemm& g, cuda
   const int nk_all = g.npad / kBK;
   const int64_t tiles = static_cast<int64_t>(mt) * g.ndt;
   int S = 1, kc_split = nk_all;
-  if (tiles < 2 * kNumSms && nk_all >= 2) {
-    S = static_cast<int>(std::min<int64_t>({kMaxSplit, (2 * kNumSms + tiles - 1) / tiles, nk_all}));
+  const int64_t sms = g.sms;
+  if (tiles < 2 * sms && nk_all >= 2) {
+    S = static_cast<int>(std::min<int64_t>({kMaxSplit, (2 * sms + tiles - 1) / tiles, nk_all}));
     kc_split = (nk_all + S - 1) / S;
     S = (nk_all + kc_split - 1) / kc_split;      // every split has at least one chunk
   }

@@ -214,8 +214,9 @@ struct GaussTc {
 cudaError_t launch_lr_prepare(int N, int Npad, int D, int ld, const float* X, const float* y, float* Xhi,
                               float* Xlo, float* XThi, float* XTlo, float* ypad, cudaStream_t s);
 
-// Logistic regression for dims the CTA-pair kernel does not take (dim > 128;
-// rows padded to ld = dim rounded up to 4 inside the workspace): each leapfrog gradient is two one-CTA tcgen05 products
+// Logistic regression for dims the CTA-pair kernel does not take (dim > 128
+// or not a multiple of 4; rows padded to ld = dim rounded up to 4 inside the
+// workspace): each leapfrog gradient is two one-CTA tcgen05 products
 // (gauss_tc.cu's tile pipeline): Z = Theta X^T with R = y - sigmoid(Z) in
 // the epilogue (R to HBM as tf32 head / remainder), then G = R X with the
 // prior and the leapfrog update in the epilogue.
@@ -242,6 +243,7 @@ struct LogregGemm {
   int nvalid = 0;                // data rows N
   int ld = 0;                    // padded row length of the workspace arrays
   float* part = nullptr;         // split-K products of G = R X [splits x C x ld]
+  int sms = 0;                   // the device's SM count (K-split decision)
 };
 bool logreg_gemm_supported(const hmc_target& t);
 size_t logreg_gemm_workspace_bytes(const hmc_target& t, int64_t C);
