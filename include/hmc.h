@@ -43,7 +43,7 @@ typedef enum {
   HMC_E_OOM = 2,          /* device workspace allocation failed */
   HMC_E_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
   HMC_E_TIMEOUT = 4,      /* a bounded device-side wait gave up */
-  HMC_E_UNSUPPORTED = 5   /* valid request this build does not implement */
+  HMC_E_UNSUPPORTED = 5   /* valid request the library does not implement */
 } hmc_status;
 
 /* Target families.  Log-densities are up to an additive constant.
