@@ -393,6 +393,27 @@ def test_ess_of_ar1_matches_closed_form():
     np.testing.assert_allclose(diagnostics.ess(z), n * C * (1 - phi) / (1 + phi), rtol=0.15)
 
 
+def test_mcse_of_the_mean_matches_the_spread_of_replicated_means():
+    """The Monte Carlo standard error of the mean is its sampling spread: over
+    400 independent AR(1) runs (phi = 0.5, 8 chains x 500 draws) the standard
+    deviation of the runs' means agrees with the average reported MCSE, and
+    with the closed form sqrt(tau / (C n)) sigma, tau = (1 + phi) / (1 - phi)."""
+    rng = np.random.default_rng(14)
+    phi, n, C, R = 0.5, 500, 8, 400
+    e = rng.standard_normal((n, R * C))
+    z = np.empty_like(e)
+    z[0] = e[0] / math.sqrt(1 - phi * phi)
+    for t in range(1, n):
+        z[t] = phi * z[t - 1] + e[t]
+    z = z.reshape(n, R, C)
+    means = z.mean(axis=(0, 2))
+    mcse = np.array([diagnostics.mcse_mean(z[:, r, :, None])[0] for r in range(R)])
+    sigma = 1.0 / math.sqrt(1 - phi * phi)
+    closed = sigma * math.sqrt((1 + phi) / (1 - phi) / (C * n))
+    assert means.std(ddof=1) == pytest.approx(closed, rel=0.12)
+    assert mcse.mean() == pytest.approx(closed, rel=0.06)
+
+
 def test_batch_means_ess_worked_by_hand():
     """One chain, draws 1, 3, 2, 6 in batches of 2: s2 = (4 + 0 + 1 + 9) / 3 =
     14/3; batch means 2 and 4 (grand mean 3) give sig2 = 2 x (1 + 1) / 1 = 4
