@@ -76,6 +76,9 @@ def parse():
                     help="replica exchange (Section 2.2): the chains form chains/K sets of K "
                          "tempered replicas, inverse temperatures 4^(-k/(K-1)), fixed step size")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain-baseline", action="store_true",
+                    help="skip the comparison run of the plain one-launch-per-operation path "
+                         "(same workload, same GPU) that fills vs_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch-scale", type=float, default=0.04,
@@ -280,6 +283,43 @@ def cpu_oracle_rate(p, seconds, proposal="leapfrog"):
             "sample": f"first {n} {kind} transitions of the workload ({C} of {p.num_chains} chains, "
                       f"fixed step size), numpy float64 with BLAS on all host cores",
             "ms_per_transition": 1000.0 * el / n}
+
+
+def plain_baseline(p, stream, x, x0, samples, eps, acc, value, min_ess_per_s):
+    """One untimed warm-up and one timed sample_chain of the plain path
+    (HMC_IMPL_PLAIN) on the same workload, reusing the bench's buffers after
+    its own figures are taken; returns the vs_baseline object (per GPU)."""
+    import torch
+    from paper_2002_01184_gb300 import diagnostics, hmc
+    from paper_2002_01184_gb300.sampler import Sampler
+    C, K, B = p.num_chains, p.num_results, p.num_burnin
+    s = Sampler(p, impl=hmc.HMC_IMPL_PLAIN, stream=stream)
+    try:
+        def run():
+            x.copy_(x0)
+            hmc.hmc_sample_chain(s.ctx, x, B, K, samples, eps, acc)
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        evals = C * p.num_leapfrog * (B + K) + C
+        plain_value = evals / (ms / 1000.0)
+        plain_ess = float(diagnostics.ess(samples).min())
+        plain_ess_s = plain_ess / (ms / 1000.0)
+        return {"baseline": "plain HMC on the same GPU: one kernel launch per operation per "
+                            "leapfrog step (SIMT float32 products), same workload, seed, L and "
+                            "dual averaging; 1 warm-up + 1 timed step",
+                "value": plain_value, "unit": "grad-evals/s", "ms_per_step": ms,
+                "min_ess": plain_ess, "min_ess_per_s": plain_ess_s,
+                "accept_rate": float(acc.float().mean().item()) if K else None,
+                "ratio": value / plain_value,
+                "min_ess_per_s_ratio": (min_ess_per_s / plain_ess_s) if plain_ess_s else None}
+    finally:
+        s.close()
 
 
 def run_uneven_batch(args):
@@ -497,10 +537,12 @@ def main():
     ms_per_step = ms / args.steps
     value = total_evals / (ms / 1000.0)
 
-    # min-ESS/s of the last step's kept draws (not timed)
-    ess = ess_d.double().cpu().numpy() if streaming else diagnostics.ess(samples, max_dims=64)
+    # min-ESS/s of the last step's kept draws over every dimension (not timed)
+    ess = ess_d.double().cpu().numpy() if streaming else diagnostics.ess(samples).numpy()
     min_ess = float(ess.min())
     min_ess_per_s = min_ess / (ms_per_step / 1000.0) * world
+    final_eps = float(eps[-1].item()) if K else None
+    accept_rate = float(acc.float().mean().item()) if K else None
 
     pk, src = peaks()
     flops = grad_flops_per_eval(p)
@@ -602,6 +644,14 @@ def main():
                "d2h_bytes_per_step": (K * C * D + C * D) * 4 + K * 4 + K * C,
                "ms_per_step": 1000.0 * el}
 
+    # The comparison target: the plain path (one kernel launch per operation
+    # per leapfrog step, SIMT products) on the same workload and GPU, with
+    # the same seed, L and adaptation -- statistically the same chains.
+    vs = None
+    if (not args.no_plain_baseline and not args.plain and not streaming and args.replicas == 1
+            and proposal == hmc.HMC_PROPOSAL_LEAPFROG and p.kind in ("corr_gauss", "logreg")):
+        vs = plain_baseline(p, stream, x, x0, samples, eps, acc, value / world, min_ess_per_s / world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(p, args.cpu_seconds, args.proposal)
@@ -612,7 +662,7 @@ def main():
             "metric": "leapfrog grad-evals/s", "value": value, "unit": "grad-evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": vs, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl, "impl": "plain" if args.plain else "fused",
                        "chains": C, "dim": D,
                        "l2": ("each step first writes a 256 MB buffer (> 129 MB L2)" if streaming else
@@ -622,8 +672,7 @@ def main():
                        "parallelism": f"replicas x{world}",
                        "transitions_per_launch": args.max_transitions_per_launch or "all"},
             "min_ess_per_s": min_ess_per_s, "min_ess": min_ess,
-            "final_step_size": float(eps[-1].item()) if K else None,
-            "accept_rate": float(acc.float().mean().item()) if K else None,
+            "final_step_size": final_eps, "accept_rate": accept_rate,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk,
         }

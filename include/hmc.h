@@ -79,7 +79,8 @@ typedef enum {
   HMC_IMPL_PLAIN = 1,             /* one kernel launch per operation per
                                      leapfrog step */
   HMC_IMPL_FUSED_SINGLE_CTA = 2   /* as FUSED, but the dense-Gaussian
-                                     transition on single CTAs (32 chains) */
+                                     transition on single CTAs (32 chains,
+                                     each CTA streaming P by TMA) */
 } hmc_impl;
 
 /* Inner (uncalibrated) kernel of the Metropolis-Hastings composition,
@@ -423,6 +424,10 @@ hmc_status hmc_target_vjp(const hmc_target* target, int64_t num_chains, const fl
  * and outputs only, as in hmc_target_log_prob_and_grad.
  *   - The first call on a device resolves the array's device address (with
  *     that device current); make that first call before any stream capture.
+ *     The address is cached for the device's primary context: after
+ *     cudaDeviceReset (which destroys that context and unloads the module)
+ *     the cached address is stale, so do not call this entry point again in
+ *     a process that has reset the device.
  *   - Requests needing more scratch than 64 MiB (LOGREG with a large
  *     chains x n_data) return HMC_E_INVALID with the sizes in the error text.
  *   - All calls share the one array and it keeps the last call's contents;

@@ -39,9 +39,7 @@ constexpr uint32_t kAStage = 2 * kAHalf;          // head + remainder
 
 template <int NC>
 struct Cfg {
-  // P chunks are shared by every CTA: a cluster of kCluster CTAs loads each
-  // stage once, every CTA fetching 128 / kCluster rows and multicasting them
-  static constexpr int kCluster = 4;
+  // every CTA streams its own copy of each P stage (P stays L2-resident)
   static constexpr uint32_t kBChunk = NC * 128;               // NC rows x 128 B
   static constexpr uint32_t kBBytes = kChunks * kBChunk;      // one of head / remainder
   static constexpr int kStages = NC == 32 ? 4 : 2;
@@ -80,7 +78,7 @@ __device__ __forceinline__ float pick(const float4& v, int i) {
   return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-template <int NC, int CL>
+template <int NC>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ CUtensorMap mPlo,
               FusedArgs fa) {
@@ -107,12 +105,10 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
   const int ntm = (D + 127) >> 7;
   const int c0 = blockIdx.x * NC;
 
-  const uint32_t crank = CL > 1 ? ptx::cluster_rank() : 0u;
-  constexpr uint16_t kMask = static_cast<uint16_t>((1u << CL) - 1u);
   if (threadIdx.x == 0) {
     for (int s = 0; s < K::kStages; ++s) {
       ptx::mbar_init(&full[s], 1);
-      ptx::mbar_init(&empty[s], CL);       // released by the MMA of every CTA
+      ptx::mbar_init(&empty[s], 1);        // released by this CTA's MMAs
     }
     ptx::mbar_init(acc_full, 1);
     ptx::mbar_init(x_ready, kEpiThreads);
@@ -130,7 +126,6 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
   proxy_fence_smem();
   ptx::tc_fence_before();
   __syncthreads();
-  if (CL > 1) ptx::cluster_sync();        // every CTA's barriers exist before any multicast
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const float eps = a.da->eps;
@@ -151,17 +146,8 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
             }
             uint8_t* st = Ast + s * kAStage;
             ptx::mbar_arrive_expect_tx(&full[s], kAStage);
-            if (CL == 1) {
-              ptx::tma_load_2d(st, &mPhi, &full[s], kc * 32, mt * 128);
-              ptx::tma_load_2d(st + kAHalf, &mPlo, &full[s], kc * 32, mt * 128);
-            } else {
-              constexpr int kRows = 128 / CL;
-              const uint32_t off = crank * (kAHalf / CL);
-              ptx::tma_load_2d_multicast(st + off, &mPhi, &full[s], kc * 32,
-                                         mt * 128 + static_cast<int>(crank) * kRows, kMask);
-              ptx::tma_load_2d_multicast(st + kAHalf + off, &mPlo, &full[s], kc * 32,
-                                         mt * 128 + static_cast<int>(crank) * kRows, kMask);
-            }
+            ptx::tma_load_2d(st, &mPhi, &full[s], kc * 32, mt * 128);
+            ptx::tma_load_2d(st + kAHalf, &mPlo, &full[s], kc * 32, mt * 128);
           }
     }
   } else if (warp == 1) {
@@ -200,8 +186,7 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
               ptx::mma_tf32(d_tmem, dahi, dblo, idesc, 1u);
               ptx::mma_tf32(d_tmem, dahi, dbhi, idesc, 1u);
             }
-            if (CL == 1) ptx::mma_commit(&empty[s]);
-            else ptx::mma_commit_multicast(&empty[s], kMask);
+            ptx::mma_commit(&empty[s]);
           }
         }
         ptx::mma_commit(acc_full);
@@ -370,8 +355,6 @@ k_gauss_fused(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ 
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem, K::kTmemCols);
   }
-  // no CTA leaves while a peer may still multicast into it or arrive on it
-  if (CL > 1) ptx::cluster_sync();
   // dual averaging: this block's acceptance probabilities in chain order
   double sum = 0.0;
   if (threadIdx.x == 0)
@@ -407,19 +390,11 @@ bool gauss_fused_supported(const hmc_target& t) {
   return t.id == HMC_T_CORR_GAUSS && t.dim % 4 == 0 && t.dim <= kMaxDim;
 }
 
-// CTAs the transition launches for C chains (a whole number of clusters).
-unsigned gauss_fused_grid(int64_t C) {
-  constexpr int CL = Cfg<32>::kCluster;
-  const int64_t ctas = (C + 31) / 32;
-  return static_cast<unsigned>((ctas + CL - 1) / CL * CL);
-}
+// CTAs the transition launches for C chains.
+unsigned gauss_fused_grid(int64_t C) { return static_cast<unsigned>((C + 31) / 32); }
 
 cudaError_t gauss_fused_setup() {
-  cudaError_t e = cudaFuncSetAttribute(k_gauss_fused<32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(Cfg<32>::kSmem));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_gauss_fused<32, Cfg<32>::kCluster>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_gauss_fused<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(Cfg<32>::kSmem));
 }
 
@@ -435,21 +410,9 @@ cudaError_t launch_gauss_fused_transition(const StepArgs& a, GaussTc& tc, cudaSt
   cudaError_t em = launch_gauss_momentum(a, tc, s);
   if (em != cudaSuccess) return em;
   FusedArgs fa{a, tc.err, tc.p, tc.h0};
-  constexpr int CL = Cfg<32>::kCluster;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(gauss_fused_grid(a.C));
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = Cfg<32>::kSmem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
   if (timer) timer->begin(s);
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_gauss_fused<32, CL>, tc.mPhi32, tc.mPlo32, fa);
+  k_gauss_fused<32><<<gauss_fused_grid(a.C), kThreads, Cfg<32>::kSmem, s>>>(tc.mPhi128, tc.mPlo128, fa);
+  cudaError_t e = cudaGetLastError();
   if (timer) timer->end(s);
   count_launch();
   if (e != cudaSuccess) return e;

@@ -503,9 +503,7 @@ cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws
   bool ok = make_map(&tc->mBhi, tc->Phi, t.dim, t.dim, kBN) &&
             make_map(&tc->mBlo, tc->Plo, t.dim, t.dim, kBN) &&
             make_map(&tc->mPhi128, tc->Phi, t.dim, t.dim, 128) &&
-            make_map(&tc->mPlo128, tc->Plo, t.dim, t.dim, 128) &&
-            make_map(&tc->mPhi32, tc->Phi, t.dim, t.dim, 32) &&
-            make_map(&tc->mPlo32, tc->Plo, t.dim, t.dim, 32);
+            make_map(&tc->mPlo128, tc->Plo, t.dim, t.dim, 128);
   for (int i = 0; i < 2 && ok; ++i)
     ok = make_map(&tc->mAhi[i], tc->xhi[i], C, t.dim, kBM) &&
          make_map(&tc->mAlo[i], tc->xlo[i], C, t.dim, kBM);

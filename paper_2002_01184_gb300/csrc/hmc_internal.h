@@ -193,7 +193,6 @@ namespace hmc {
 struct GaussTc {
   CUtensorMap mAhi[2], mAlo[2], mBhi, mBlo;
   CUtensorMap mPhi128, mPlo128;  // P head / remainder, 32 x 128 boxes
-  CUtensorMap mPhi32, mPlo32;    // 32 x 32 boxes (one CTA's share of a multicast stage)
   float* Phi = nullptr;      // tf32 head / remainder of P
   float* Plo = nullptr;
   float* Ptm = nullptr;      // P in the pair kernel's tensor-memory fill order

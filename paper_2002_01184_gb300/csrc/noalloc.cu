@@ -16,6 +16,10 @@
 // the array's name as a device address, so the first call on each device
 // (with that device current) resolves the address with cudaGetSymbolAddress
 // and caches it; that first call should come before any stream capture.
+// The cached address belongs to the device's primary context: cudaDeviceReset
+// destroys that context and unloads the module, after which the cached
+// address is stale (the header tells callers not to use this entry point
+// again after a reset).
 // Every call on a device shares the one array and it keeps the last call's
 // contents; nothing in it needs to start at zero (each kernel writes every
 // scratch element it later reads), but calls whose kernels overlap on the

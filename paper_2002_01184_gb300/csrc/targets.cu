@@ -237,11 +237,23 @@ struct LogregPlan {
 
 inline size_t align256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
 
+// SM count of the current device (the split-K decision below fills four
+// waves of it); 152, a GB300's count, when no device can be queried.
+int current_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    return 152;
+  }
+  return sms;
+}
+
 LogregPlan logreg_plan(int64_t C, int D, int64_t N) {
   LogregPlan p{};
   p.ntiles_n = static_cast<int>((N + kBN - 1) / kBN);
   const int64_t out_tiles = ((C + kBM - 1) / kBM) * ((D + kBN - 1) / kBN);
-  int64_t s = (4 * 152 + out_tiles - 1) / out_tiles;
+  int64_t s = (4 * static_cast<int64_t>(current_sm_count()) + out_tiles - 1) / out_tiles;
   s = std::max<int64_t>(1, std::min<int64_t>(s, (N + 511) / 512));
   int64_t chunk = (N + s - 1) / s;
   chunk = (chunk + kBK - 1) / kBK * kBK;
