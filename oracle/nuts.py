@@ -73,7 +73,9 @@ def one_chain(x0, lp0, g0, p0, log_U, eps, max_depth, seed, chain, t, target):
     """One NUTS transition of a single chain from (x0, p0).  ``target`` maps a
     (1, D) array to (log_prob[1], grad[1, D]).  Returns a dict with the new
     state, its log p and gradient, whether it moved, the statistic, the tree
-    depth and leaf count, and the smallest decision margin met (for tests)."""
+    depth and leaf count, the smallest decision margin met and why the tree
+    stopped (for tests: "max_depth", "divergence", ("u_turn", i) for a span
+    of 2^i leaves inside a subtree, "u_turn_top" for the whole trajectory)."""
     x0 = np.asarray(x0, dtype=np.float64)
     p0 = np.asarray(p0, dtype=np.float64)
     H0 = -lp0 + 0.5 * p0 @ p0
@@ -85,6 +87,7 @@ def one_chain(x0, lp0, g0, p0, log_U, eps, max_depth, seed, chain, t, target):
     margin = np.inf
     dirs = _word(seed, 0, chain, t, TAG_DIRECTION)
     depth = 0
+    stop = "max_depth"
     for j in range(max_depth):
         v = 1 if (dirs >> j) & 1 else -1
         x, p, g, lp = (e.copy() if isinstance(e, np.ndarray) else e for e in ends[v])
@@ -104,6 +107,7 @@ def one_chain(x0, lp0, g0, p0, log_U, eps, max_depth, seed, chain, t, target):
             # divergence (Hoffman and Gelman: log u < Delta_max - H, else stop)
             if not finite or H - H0 >= DELTA_MAX - log_U:
                 ok_sub = False
+                stop = "divergence"
             a_sum += float(np.exp(min(H0 - H, 0.0))) if finite else 0.0
             n_a += 1
             if finite:
@@ -124,6 +128,8 @@ def one_chain(x0, lp0, g0, p0, log_U, eps, max_depth, seed, chain, t, target):
                     scale = np.linalg.norm(dx) * max(np.linalg.norm(pf), np.linalg.norm(p))
                     margin = min(margin, abs(d1) / max(scale, 1e-300), abs(d2) / max(scale, 1e-300))
                     if d1 < 0 or d2 < 0:
+                        if ok_sub:
+                            stop = ("u_turn", i)       # the innermost span that turned
                         ok_sub = False
             if not ok_sub:
                 break
@@ -141,9 +147,10 @@ def one_chain(x0, lp0, g0, p0, log_U, eps, max_depth, seed, chain, t, target):
         scale = np.linalg.norm(dx) * max(np.linalg.norm(pl), np.linalg.norm(pr))
         margin = min(margin, abs(d1) / max(scale, 1e-300), abs(d2) / max(scale, 1e-300))
         if d1 < 0 or d2 < 0:
+            stop = "u_turn_top"
             break
     return {"x": xm, "lp": lpm, "g": gm, "moved": moved, "stat": a_sum / max(n_a, 1),
-            "depth": depth, "leaves": n_a, "margin": margin}
+            "depth": depth, "leaves": n_a, "margin": margin, "stop": stop}
 
 
 def one_step(x, lp, g, eps, max_depth, seed, t, target, chain_offset=0):

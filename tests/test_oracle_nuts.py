@@ -128,3 +128,165 @@ def test_last_doubling_takes_the_candidate_uniformly_when_every_leaf_is_valid():
         counts[hit[0]] += 1
     chi2 = np.sum((counts - C / 4) ** 2 / (C / 4))
     assert chi2 < 16.3, counts          # 3 degrees of freedom, p = 0.001
+
+
+# ---- the unrolled loop against the recursion it restates --------------------
+#
+# Hoffman and Gelman's efficient NUTS (their Algorithm 3) builds each
+# doubling's subtree by recursion: BuildTree at height 0 takes one leapfrog
+# step; at height j it builds a subtree of height j - 1, and only if that one
+# did not stop, a second one from its far end, then tests the U-turn
+# criterion on the ends of the whole height-j subtree.  The function below
+# restates that recursion directly, in its own order, with nothing shared with
+# oracle/nuts.py but the counter generator.  Its subtree candidate is drawn
+# from the same words as the oracle's (the recursion's random merges with
+# probability n''/(n' + n'') and the oracle's per-leaf 1/n' replacements give
+# the same uniform law over the subtree's valid leaves but spend different
+# random numbers, so the choice is made here by the per-leaf rule over the
+# valid leaves the recursion returns).  Everything the recursion decides --
+# how many leaves are built, where and why the tree stops, which leaves are
+# valid -- is the recursion's own.
+
+def _recursive_tree(x0, lp0, g0, p0, log_U, eps, max_depth, seed, chain, t, target):
+    H0 = -lp0 + 0.5 * p0 @ p0
+
+    def leapfrog(x, p, g, v):
+        p = p + 0.5 * v * eps * g
+        x = x + v * eps * p
+        lpa, ga = target(x[None, :])
+        g = ga[0]
+        p = p + 0.5 * v * eps * g
+        return x, p, g, float(lpa[0])
+
+    def build(x, p, g, lp, v, j, k0):
+        """Subtree of height j from (x, p) in direction v; its leaves are
+        numbered k0, k0 + 1, ... in build order.  Returns a dict: first / last
+        leaf states, the valid leaves [(k, x, g, lp)], whether it may go on
+        (s), the leaves built with their energies, and the stop reason."""
+        if j == 0:
+            x, p, g, lp = leapfrog(x, p, g, v)
+            H = -lp + 0.5 * p @ p
+            finite = bool(np.isfinite(H))
+            valid = finite and log_U <= H0 - H
+            s = finite and (H - H0 < nuts.DELTA_MAX - log_U)
+            return {"first": (x, p), "last": (x, p, g, lp),
+                    "valid": [(k0, x, g, lp)] if valid else [], "s": s, "H": [H],
+                    "stop": None if s else "divergence"}
+        a = build(x, p, g, lp, v, j - 1, k0)
+        if not a["s"]:
+            return a
+        b = build(*a["last"], v, j - 1, k0 + (1 << (j - 1)))
+        out = {"first": a["first"], "last": b["last"], "valid": a["valid"] + b["valid"],
+               "s": b["s"], "H": a["H"] + b["H"], "stop": b["stop"]}
+        if b["s"]:
+            xf, pf = a["first"]
+            xl, pl = b["last"][0], b["last"][1]
+            dx = v * (xl - xf)                 # x+ - x- in time order
+            if dx @ pf < 0 or dx @ pl < 0:
+                out["s"], out["stop"] = False, ("u_turn", j)
+        return out
+
+    ends = {+1: (x0, p0, g0, lp0), -1: (x0, p0, g0, lp0)}
+    state = (x0, g0, lp0)
+    n, moved, energies, depth, stop = 1, False, [], 0, "max_depth"
+    dirs = nuts._word(seed, 0, chain, t, nuts.TAG_DIRECTION)
+    for j in range(max_depth):
+        v = 1 if (dirs >> j) & 1 else -1
+        tree = build(*ends[v], v, j, 0)
+        ends[v] = tree["last"]
+        energies += tree["H"]
+        depth = j + 1
+        if not tree["s"]:
+            stop = tree["stop"]
+            break
+        cand = None
+        for m, (k, x, g, lp) in enumerate(tree["valid"], start=1):
+            w = nuts._words(seed, k >> 2, chain, t, nuts.TAG_SUBTREE + j)[k & 3]
+            if nuts._take(w, 1, m):
+                cand = (x, g, lp)
+        n_sub = len(tree["valid"])
+        if n_sub and nuts._take(nuts._word(seed, j, chain, t, nuts.TAG_TOP), n_sub, n):
+            state, moved = cand, True
+        n += n_sub
+        dx = ends[+1][0] - ends[-1][0]
+        if dx @ ends[-1][1] < 0 or dx @ ends[+1][1] < 0:
+            stop = "u_turn_top"
+            break
+    H = np.array(energies)
+    stat = np.where(np.isfinite(H), np.exp(np.minimum(H0 - H, 0.0)), 0.0).mean()
+    return {"x": state[0], "lp": state[2], "moved": moved, "depth": depth, "leaves": len(energies),
+            "stop": stop, "stat": stat}
+
+
+def _funnel_and_gauss_cases():
+    """(name, target, states, step sizes) covering shallow and deep trees,
+    divergences, and trees stopped by spans inside a subtree."""
+    rng = np.random.default_rng(11)
+    D = 6
+    A = rng.standard_normal((D, D))
+    gauss = targets.make("corr_gauss", P=A @ A.T / D + 0.05 * np.eye(D))
+    funnel = targets.make("funnel")
+    xg = rng.standard_normal((12, D)) * 2.0
+    xf = np.concatenate([rng.normal(0.0, 3.0, (12, 1)), rng.standard_normal((12, 9))], axis=1)
+    return [("corr_gauss", gauss, xg, (0.05, 0.2, 0.6, 1.9)),
+            ("funnel", funnel, xf, (0.02, 0.15, 0.5, 1.5))]
+
+
+def _compare_with_recursion(one_chain):
+    seen = set()
+    for name, tgt, x, steps in _funnel_and_gauss_cases():
+        C, D = x.shape
+        lp, g = tgt(x)
+        for max_depth in (1, 3, 6, 10):
+            for eps in steps:
+                t = int(1000 * eps) + max_depth
+                p0 = philox.momentum(5, t, C, D)
+                log_U = np.log(philox.accept_uniform(5, t, C))
+                for c in range(C):
+                    args = (x[c], float(lp[c]), g[c], p0[c], float(log_U[c]), eps, max_depth, 5, c, t, tgt)
+                    o = one_chain(*args)
+                    r = _recursive_tree(*args)
+                    for key in ("depth", "leaves", "moved", "stop"):
+                        if o[key] != r[key]:
+                            return False, (name, max_depth, eps, c, key, o[key], r[key]), seen
+                    if not (np.allclose(o["x"], r["x"], rtol=1e-12, atol=1e-12)
+                            and abs(o["stat"] - r["stat"]) <= 1e-12):
+                        return False, (name, max_depth, eps, c, "state"), seen
+                    stop = r["stop"]
+                    seen.add(("inner_u_turn" if isinstance(stop, tuple) and stop[1] < r["depth"] - 1
+                              else "subtree_u_turn" if isinstance(stop, tuple) else stop))
+                    if r["depth"] >= 6:
+                        seen.add("deep")
+    return True, None, seen
+
+
+def test_unrolled_loop_equals_the_recursive_build_tree():
+    """Chain by chain, for depths 1-10 on a correlated Gaussian and the funnel:
+    the same depth, leaf count, stop reason, statistic and new state as
+    Hoffman and Gelman's recursive BuildTree.  The cases include trees stopped
+    by a span strictly inside the last subtree, by the subtree's own span, by
+    the whole trajectory, by divergence and by the depth cap."""
+    ok, where, seen = _compare_with_recursion(nuts.one_chain)
+    assert ok, where
+    for kind in ("inner_u_turn", "subtree_u_turn", "u_turn_top", "divergence", "max_depth", "deep"):
+        assert kind in seen, (kind, seen)
+
+
+def _mutated_one_chain(old, new):
+    """oracle/nuts.py's one_chain with one planted mistake (for the test below)."""
+    import inspect
+    src = inspect.getsource(nuts)
+    assert old in src, old
+    ns = {"__name__": "oracle.nuts_mutant", "__package__": "oracle"}
+    exec(compile(src.replace(old, new), "nuts_mutant", "exec"), ns)
+    return ns["one_chain"]
+
+
+def test_the_comparison_catches_planted_span_mistakes():
+    """Mistakes the other pins would miss -- spans closed one leaf early, or a
+    span tested against the leaf after its first -- break the equality with
+    the recursion (planted in a copy of the oracle, on the CPU)."""
+    early = _mutated_one_chain("if (k + 1) % span == 0:", "if (k + 2) % span == 0:")
+    assert not _compare_with_recursion(early)[0]
+    shifted = _mutated_one_chain("if k % span == 0:", "if k % span == min(1, span - 1):")
+    assert not _compare_with_recursion(shifted)[0]
