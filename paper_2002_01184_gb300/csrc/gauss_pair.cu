@@ -2,30 +2,32 @@
 // (tcgen05 cta_group::2).  A pair owns 64 chains; one launch runs T
 // consecutive transitions of them (Section 2.1's transition, Section 4.2's
 // driver loop), so that P stays resident across transitions and no launch
-// sits between them.  Each leapfrog gradient G^T = P X^T is one stream of
-// M = 256 (all output dims), N = 64 (the pair's chains), K = 8 MMAs issued by
-// the pair's leader.
-//   * A (P head / remainder, 3xTF32) is resident for the whole launch: each
-//     CTA's 128 rows of P, K-chunks 0-6 (dims 0-223) in its tensor memory and
-//     chunk 7 (dims 224-255) in shared memory.  The MMAs then read only the
-//     positions from shared memory: at 64 chains an MMA that also read A from
-//     shared memory would be bound by shared-memory bandwidth, not by the
-//     tensor pipe.
-//   * B (positions, head / remainder tiles, 128-byte-swizzled K-major): each
-//     CTA holds 32 of the 64 chains.
-//   * Accumulators: each CTA's tensor memory holds its 128 output dims for
-//     all 64 chains.
+// sits between them.  Each leapfrog gradient G^T = P X^T (3xTF32) is one
+// stream of M = 256 (all output dims) MMAs issued by the pair's leader, two
+// per K-step of 8 dims:
+//   * B (positions) stacks each CTA's 32 chains' tf32 heads and remainders
+//     as 64 rows of one 128-byte-swizzled K-major tile, so one N = 128 MMA
+//     with A = P head forms P_hi x_hi and P_hi x_lo for all 64 chains, and
+//     one N = 64 MMA with A = P remainder over the head rows alone adds
+//     P_lo x_hi -- two instructions where three separate products of N = 64
+//     took three (the MMAs are bound by their issue rate at this N).
+//   * Accumulators (128 tensor-memory columns): column (CTA q, row r) of the
+//     N = 128 product; the N = 64 product is written at column offset 32, so
+//     that each chain's P_lo x_hi lands in one of its own two columns.  A
+//     chain's gradient is the sum of its two columns.
+//   * A (P head / remainder) is resident for the whole launch: each CTA's 128
+//     rows of P, K-chunks 0-5 (dims 0-191) in its tensor memory and chunks 6-7
+//     in shared memory.
 //   * Epilogue (warps 2-9 of both CTAs): one output dim per thread and 32
 //     chains per thread, 16 of the peer's and 16 of its own; momenta and
-//     trajectory positions in registers, the chains' current state (position
-//     and gradient, this CTA's dims) in shared memory across transitions.
-//     Each step a thread first updates its peer chains, whose next positions
-//     are staged locally (in the destination's layout); each warp then
-//     pushes its 16 rows of a K-chunk (head and remainder, 2 KB each) to the
-//     peer by bulk DSMEM copy, completing on the peer's tile barrier, and
-//     updates its own chains, written straight into its tile, while the copy
-//     is in flight -- element-wise remote stores stalled every warp's
-//     shared-memory traffic.
+//     trajectory positions in registers, the chains' current positions (this
+//     CTA's dims) in shared memory and their cached gradients in global
+//     memory (L2) across transitions.  Each step a thread first updates its
+//     peer chains, whose next positions are staged locally (in the
+//     destination's layout); each warp then pushes its 16 rows of a K-chunk
+//     (head and remainder, 2 KB each) to the peer by bulk DSMEM copy,
+//     completing on the peer's tile barrier, and updates its own chains,
+//     written straight into its tile, while the copy is in flight.
 //   * Readiness is tracked per half of K: in each CTA's tile the K-chunks of
 //     its own dims are written locally (own_full, which every epilogue thread
 //     joins once it has read the accumulators) and the other four arrive by
@@ -38,9 +40,10 @@
 //     global memory.
 // H_L, the Metropolis-Hastings decision and the dual-averaging partial are
 // formed by the leader from both CTAs' partial sums.  With T > 1 the launch
-// is cooperative: after every transition all CTAs meet at a grid barrier and
-// each applies the same dual-averaging update to its own copy of the state;
-// a launch of one transition instead lets its last CTA update the state.
+// is cooperative: after every transition that adapts the step size (and
+// after the last one) all CTAs meet at a grid barrier and each applies the
+// same dual-averaging update to its own copy of the state; a launch of one
+// transition instead lets its last CTA update the state.
 #include <cuda.h>
 
 #include <cmath>
@@ -55,32 +58,36 @@ namespace {
 
 constexpr int kMaxDim = 256;
 constexpr int kChunks = kMaxDim / 32;             // K-chunks of 32 dims
-constexpr int kTmemChunks = 7;                    // P chunks held in tensor memory
+constexpr int kTmemChunks = 6;                    // P chunks held in tensor memory
+constexpr int kSmemChunks = kChunks - kTmemChunks;   // P chunks held in shared memory
 constexpr int kThreads = 320;
-constexpr int kPairChains = 64;                   // MMA N
-constexpr int kHalf = 32;                         // chains per CTA (B rows)
-constexpr uint32_t kBChunk = kHalf * 128;         // 32 rows x 128 B
-constexpr uint32_t kBBytes = kChunks * kBChunk;   // head or remainder tile
-constexpr uint32_t kAHalf = 128 * 128;            // 128 rows x 32 floats
+constexpr int kPairChains = 64;                   // chains of a pair
+constexpr int kHalf = 32;                         // chains per CTA
+constexpr uint32_t kRowBytes = 128;               // one row of a K-chunk: 32 floats
+constexpr uint32_t kLoOff = kHalf * kRowBytes;    // remainder rows follow the head rows
+constexpr uint32_t kBChunk = 2 * kLoOff;          // 64 rows (32 head, 32 remainder) x 128 B
+constexpr uint32_t kBBytes = kChunks * kBChunk;   // the position tile
+constexpr uint32_t kAHalf = 128 * 128;            // 128 rows of P x 32 floats
+constexpr uint32_t kABytes = kSmemChunks * 2 * kAHalf;   // P chunks 6-7, head and remainder
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColAcc = 0;                   // accumulators: 64 columns
-constexpr uint32_t kColP = 64;                    // chunk kc: head at kColP + 64 kc, remainder + 32
-constexpr uint32_t kStageHalf = 4 * kBChunk;      // 4 K-chunks (this CTA's 128 dims) x 32 chains
-constexpr uint32_t kStageBytes = 2 * kStageHalf;  // head + remainder
-constexpr uint32_t kStateBytes = kPairChains * 128 * 4;   // one of position / gradient
+constexpr uint32_t kColAcc = 0;                   // accumulators: 128 columns
+constexpr uint32_t kColLoProduct = 32;            // the N = 64 product's column offset
+constexpr uint32_t kColP = 128;                   // chunk kc: head at kColP + 64 kc, remainder + 32
+constexpr uint32_t kStageBytes = 4 * kBChunk;     // 4 K-chunks (this CTA's 128 dims) x 32 chains
+constexpr uint32_t kStateBytes = kPairChains * 128 * 4;   // current positions, this CTA's dims
 // barriers (8), tmem slot, red [3][4][64], red_pair [3][64], peer_in [3][64],
 // acc_flag [64], prob_s [64], DA state copy, flags, DA coefficients, pair
 // sum, inverse temperatures [64], tempered log p after the decision [64],
 // exchange flags [64]
 constexpr uint32_t kSmall =
     8 * 8 + 16 + (3 * 4 * 64 + 3 * 64 + 3 * 64 + 64 + 64) * 4 + 128 + 16 + 32 + 16 + 3 * 64 * 4;
-constexpr size_t kSmemUsed =
-    2 * kBBytes + 2 * kAHalf + kStageBytes + 2 * kStateBytes + kSmall + 1024;
+constexpr size_t kSmemUsed = kBBytes + kABytes + kStageBytes + kStateBytes + kSmall + 1024;
 // Above half of an SM's shared memory, so that one CTA runs per SM: a CTA
 // allocates all 512 tensor-memory columns and must never queue in
 // tcgen05.alloc behind another CTA of the launch.
 constexpr size_t kSmem = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
 static_assert(kSmem <= 227 * 1024, "shared memory");
+static_assert(kColP + 2 * 32 * kTmemChunks == kTmemCols, "tensor-memory columns");
 
 struct PairArgs {
   StepArgs s;           // s.t / s.t_full: the first transition of the launch
@@ -173,8 +180,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned gen) {
 // whole replica sets) the launch also takes the exchange step after every
 // transition: the leader's deciding threads decide the adjacent pairs
 // (k, k + 1), k = t mod 2, 2 + t mod 2, ..., through remc_swap_accept, and
-// both CTAs swap the rows of their dims in shared memory, rescaling the
-// cached gradients, before the kept sample is written.
+// both CTAs swap the rows of their dims, rescaling the cached gradients,
+// before the kept sample is written.
 template <bool TEMPERED>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ CUtensorMap mPlo,
@@ -183,13 +190,11 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  uint8_t* Bhi = smem;
-  uint8_t* Blo = smem + kBBytes;
-  uint8_t* A7 = smem + 2 * kBBytes;                        // P chunk 7: head, remainder
-  uint8_t* Stg = A7 + 2 * kAHalf;                          // staging: head, remainder
+  uint8_t* Bt = smem;                                      // positions: [8 K-chunks][head 32 rows, remainder 32 rows]
+  uint8_t* As = Bt + kBBytes;                              // P chunks 6-7: [chunk][head, remainder]
+  uint8_t* Stg = As + kABytes;                             // staging, laid out as 4 K-chunks of Bt
   float* xs = reinterpret_cast<float*>(Stg + kStageBytes); // [64 chains][128 dims] current position
-  float* gs = xs + kPairChains * 128;                      // [64 chains][128 dims] its gradient
-  uint64_t* a7_full = reinterpret_cast<uint64_t*>(gs + kPairChains * 128);
+  uint64_t* a7_full = reinterpret_cast<uint64_t*>(xs + kPairChains * 128);
   uint64_t* acc_full = a7_full + 1;
   uint64_t* own_full = acc_full + 1;      // all epilogue threads: accumulators read, own K-chunks written
   uint64_t* in_full = own_full + 1;       // this CTA's tile: the peer's K-chunks copied in
@@ -215,6 +220,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   const uint32_t rank = ptx::cluster_rank();              // 0: leader, 1: peer
   const int C = a.C, D = a.D, L = a.L, T = fa.T;
   const int nk = (D + 31) >> 5;
+  const int nsm = nk > kTmemChunks ? nk - kTmemChunks : 0;   // P chunks in shared memory
   const int pair_base = (blockIdx.x >> 1) * kPairChains;
   const bool persistent = fa.grid_bar != nullptr;
   constexpr uint16_t kPairMask = 0x3;
@@ -241,9 +247,9 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   }
   if (TEMPERED && threadIdx.x < kPairChains)
     beta_s[threadIdx.x] = a.betas[(pair_base + static_cast<int>(threadIdx.x)) % a.K];
-  // B tiles and staging start zeroed: dims >= D are never written
-  for (uint32_t i = threadIdx.x; i < 2 * kBBytes / 16; i += kThreads)
-    reinterpret_cast<uint4*>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  // position tile and staging start zeroed: dims >= D and chains >= C are never written
+  for (uint32_t i = threadIdx.x; i < kBBytes / 16; i += kThreads)
+    reinterpret_cast<uint4*>(Bt)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (uint32_t i = threadIdx.x; i < kStageBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(Stg)[i] = make_uint4(0u, 0u, 0u, 0u);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -265,49 +271,49 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   float p[kHalf], x[kHalf];
 
   if (warp == 0) {
-    if (lane == 0 && nk > kTmemChunks) {
-      // ---- P chunk 7 of this CTA's rows, once, completing on the leader's barrier
-      if (rank == 0) ptx::mbar_arrive_expect_tx(a7_full, 4 * kAHalf);
+    if (lane == 0 && nsm > 0) {
+      // ---- P chunks 6-7 of this CTA's rows, once, completing on the leader's barrier
+      if (rank == 0) ptx::mbar_arrive_expect_tx(a7_full, 2u * 2u * static_cast<uint32_t>(nsm) * kAHalf);
       const uint32_t bar = ptx::mapa(ptx::smem_u32(a7_full), 0);
-      ptx::tma_load_2d_to_bar(A7, &mPhi, bar, kTmemChunks * 32, static_cast<int>(rank) * 128);
-      ptx::tma_load_2d_to_bar(A7 + kAHalf, &mPlo, bar, kTmemChunks * 32, static_cast<int>(rank) * 128);
+      for (int c = 0; c < nsm; ++c) {
+        uint8_t* dst = As + c * 2 * kAHalf;
+        const int col = (kTmemChunks + c) * 32;
+        ptx::tma_load_2d_to_bar(dst, &mPhi, bar, col, static_cast<int>(rank) * 128);
+        ptx::tma_load_2d_to_bar(dst + kAHalf, &mPlo, bar, col, static_cast<int>(rank) * 128);
+      }
     }
   } else if (warp == 1) {
     if (lane == 0 && rank == 0) {
-      // ---- MMA issuer (leader): M = 256 across the pair, N = 64 chains
-      constexpr uint32_t idesc = ptx::idesc_tf32(256, kPairChains);
-      if (nk > kTmemChunks && !ptx::mbar_wait(a7_full, 0)) {
+      // ---- MMA issuer (leader): M = 256 across the pair
+      constexpr uint32_t idesc_wide = ptx::idesc_tf32(256, 2 * kPairChains);   // head + remainder rows
+      constexpr uint32_t idesc_head = ptx::idesc_tf32(256, kPairChains);       // head rows only
+      if (nsm > 0 && !ptx::mbar_wait(a7_full, 0)) {
         atomicCAS(fa.err, 0, 1);
         ok = false;
       }
-      // one K-chunk: 4 k-steps x 3 products
+      // one K-chunk: 4 K-steps x 2 products (P_hi [x_hi; x_lo], then P_lo x_hi)
       auto chunk_mmas = [&](int kc, bool& first) {
-        const uint32_t bhi = ptx::smem_u32(Bhi + kc * kBChunk);
-        const uint32_t blo = ptx::smem_u32(Blo + kc * kBChunk);
+        const uint32_t b = ptx::smem_u32(Bt + kc * kBChunk);
         if (kc < kTmemChunks) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const uint64_t dbhi = ptx::sw128_kmajor_desc(bhi + 32 * j);
-            const uint64_t dblo = ptx::sw128_kmajor_desc(blo + 32 * j);
+            const uint64_t db = ptx::sw128_kmajor_desc(b + 32 * j);
             const uint32_t ahi = tmem + kColP + 64 * kc + 8 * j;
             const uint32_t alo = ahi + 32;
-            ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, alo, dbhi, idesc, first ? 0u : 1u);
-            ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, ahi, dblo, idesc, 1u);
-            ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, ahi, dbhi, idesc, 1u);
+            ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, ahi, db, idesc_wide, first ? 0u : 1u);
+            ptx::mma_tf32_pair_tmem_a(tmem + kColAcc + kColLoProduct, alo, db, idesc_head, 1u);
             first = false;
           }
         } else {
-          const uint32_t ahi = ptx::smem_u32(A7);
+          const uint32_t ahi = ptx::smem_u32(As + (kc - kTmemChunks) * 2 * kAHalf);
           const uint32_t alo = ahi + kAHalf;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const uint64_t dahi = ptx::sw128_kmajor_desc(ahi + 32 * j);
             const uint64_t dalo = ptx::sw128_kmajor_desc(alo + 32 * j);
-            const uint64_t dbhi = ptx::sw128_kmajor_desc(bhi + 32 * j);
-            const uint64_t dblo = ptx::sw128_kmajor_desc(blo + 32 * j);
-            ptx::mma_tf32_pair(tmem + kColAcc, dalo, dbhi, idesc, first ? 0u : 1u);
-            ptx::mma_tf32_pair(tmem + kColAcc, dahi, dblo, idesc, 1u);
-            ptx::mma_tf32_pair(tmem + kColAcc, dahi, dbhi, idesc, 1u);
+            const uint64_t db = ptx::sw128_kmajor_desc(b + 32 * j);
+            ptx::mma_tf32_pair(tmem + kColAcc, dahi, db, idesc_wide, first ? 0u : 1u);
+            ptx::mma_tf32_pair(tmem + kColAcc + kColLoProduct, dalo, db, idesc_head, 1u);
             first = false;
           }
         }
@@ -365,20 +371,22 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     auto rowi = [&](int i) {
       return static_cast<int>(i < 16 ? peer : rank) * kHalf + sub * 16 + (i & 15);
     };
-    // Destinations, laid out as the K-chunks of a tile (1024-byte aligned on
-    // both sides, so the swizzle carries over): staging chunk `quarter` is
-    // the peer's K-chunk 4 rank + quarter.  Row r of a chunk sits at
-    // (r / 8) * 1024 + sw[r % 8] from the column's base (d and dl agree mod 32).
+    // Destinations, laid out as the K-chunks of the tile (1024-byte aligned
+    // on both sides, so the swizzle carries over): staging chunk `quarter` is
+    // the peer's K-chunk 4 rank + quarter.  Head row r of a chunk sits at
+    // (r / 8) * 1024 + sw[r % 8] from the column's base (d and dl agree mod
+    // 32), its remainder kLoOff further.
     const uint32_t st_hi0 = ptx::smem_u32(Stg) + static_cast<uint32_t>((dl >> 5) * kBChunk + (dl & 3) * 4);
-    const uint32_t own_hi0 = ptx::smem_u32(Bhi) + static_cast<uint32_t>((d >> 5) * kBChunk + (d & 3) * 4);
+    const uint32_t own_hi0 = ptx::smem_u32(Bt) + static_cast<uint32_t>((d >> 5) * kBChunk + (d & 3) * 4);
     uint32_t sw[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) sw[r] = r * 128 + (((((dl & 31) >> 2) ^ r) & 7) << 4);
+    for (int r = 0; r < 8; ++r) sw[r] = r * kRowBytes + (((((dl & 31) >> 2) ^ r) & 7) << 4);
     const int nv_peer = dvalid ? max(0, min(16, C - (pair_base + static_cast<int>(peer) * kHalf + sub * 16))) : 0;
     const int nv_own = dvalid ? max(0, min(16, C - (pair_base + static_cast<int>(rank) * kHalf + sub * 16))) : 0;
     auto valid = [&](int i) { return i < 16 ? i < nv_peer : i - 16 < nv_own; };
     auto xrow = [&](int i) -> float& { return xs[rowi(i) * 128 + dl]; };
-    auto grow = [&](int i) -> float& { return gs[rowi(i) * 128 + dl]; };
+    // element index of (pair row of element i, dim d) in the [C x D] arrays
+    auto elem = [&](int i) { return static_cast<int64_t>(pair_base + rowi(i)) * D + d; };
     auto store_x = [&](int i, float xi) {   // position of element i, split, into staging / tile
       if (valid(i)) {
         if (TEMPERED) xi *= beta_s[rowi(i)];
@@ -386,9 +394,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         split_tf32(xi, hi, lo);
         const int r = sub * 16 + (i & 15);
         const uint32_t a0 = (i < 16 ? st_hi0 : own_hi0) + (r >> 3) * 1024 + sw[r & 7];
-        const uint32_t lo_off = i < 16 ? kStageHalf : kBBytes;
         asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0), "f"(hi) : "memory");
-        asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0 + lo_off), "f"(lo) : "memory");
+        asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0 + kLoOff), "f"(lo) : "memory");
       }
     };
     // The peer's half is written: the warp pushes its 16 rows of staging
@@ -399,12 +406,12 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       __syncwarp();
       if (lane == 0) {
         const uint32_t bar = ptx::mapa(ptx::smem_u32(in_full), peer);
-        const uint32_t rows = static_cast<uint32_t>(sub) * (kBChunk / 2);
+        const uint32_t rows = static_cast<uint32_t>(sub) * 16 * kRowBytes;
         const uint32_t chunk = (4 * rank + quarter) * kBChunk + rows;
         uint8_t* sb = Stg + quarter * kBChunk + rows;
-        ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Bhi + chunk), peer), sb, kBChunk / 2, bar);
-        ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Blo + chunk), peer), sb + kStageHalf, kBChunk / 2,
-                                  bar);
+        ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Bt + chunk), peer), sb, 16 * kRowBytes, bar);
+        ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Bt + chunk + kLoOff), peer), sb + kLoOff,
+                                  16 * kRowBytes, bar);
       }
     };
     // The own half is written: every thread arrives on own_full once its
@@ -415,10 +422,13 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       ptx::mbar_arrive_local(own_full);
       if (ew == 0 && lane == 0) ptx::mbar_arrive_expect_tx(in_full, kStageBytes);
     };
-    // accumulator columns of elements 16 cb .. 16 cb + 15 (column = pair row)
+    // The gradient of elements 16 cb .. 16 cb + 15 is minus the sum of their
+    // two accumulator columns: (CTA q, row r) -> column 64 q + r and 64 q + r + 32.
     const uint32_t acc_base = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + kColAcc;
-    auto acc_col = [&](int cb) {
-      return static_cast<uint32_t>(static_cast<int>(cb == 0 ? peer : rank) * kHalf + sub * 16);
+    auto load_acc = [&](int cb, float (&acc)[16]) {
+      const uint32_t col = acc_base + static_cast<uint32_t>(static_cast<int>(cb == 0 ? peer : rank) * 64 + sub * 16);
+      ptx::tmem_ld8x2_sum(col, col + 32, acc);
+      ptx::tmem_ld8x2_sum(col + 8, col + 40, acc + 8);
     };
     auto wait_acc = [&](int s) {
       if (!ptx::mbar_wait(acc_full, s & 1)) {
@@ -432,17 +442,17 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     auto draw_next = [&](int i0, int i1, uint32_t tn) {
       for (int i = i0; i < i1; ++i)
         if (valid(i))
-          fa.p0next[static_cast<int64_t>(pair_base + rowi(i)) * D + d] =
-              momentum1(a.seed, static_cast<uint32_t>(d), chain_of(i), tn);
+          fa.p0next[elem(i)] = momentum1(a.seed, static_cast<uint32_t>(d), chain_of(i), tn);
     };
     const int per_wait = (kHalf + L - 1) / L;   // rows drawn ahead of each gradient wait
 
     // P rows of this CTA (row = output dim d = TMEM lane) into tensor memory
     // from the pre-arranged image (coalesced): the two warps of a lane
-    // quarter split chunks 0-3 and 4-6
+    // quarter split chunks 0-2 and 3-5
     {
       const int kc_end = min(nk, kTmemChunks);
-      for (int kc = sub == 0 ? 0 : 4; kc < (sub == 0 ? min(kc_end, 4) : kc_end); ++kc) {
+      constexpr int kSplit = kTmemChunks / 2;
+      for (int kc = sub == 0 ? 0 : kSplit; kc < (sub == 0 ? min(kc_end, kSplit) : kc_end); ++kc) {
 #pragma unroll
         for (int q16 = 0; q16 < 2; ++q16) {
           float vh[16], vl[16];
@@ -462,27 +472,23 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       }
       ptx::tmem_wait_st();
     }
-    // the chains' current state, this CTA's dims
+    // the chains' current positions, this CTA's dims (their gradients stay
+    // in a.g, which the accepted proposals overwrite)
 #pragma unroll 4
-    for (int i = 0; i < kHalf; ++i) {
-      const bool v = valid(i);
-      const int64_t e = static_cast<int64_t>(pair_base + rowi(i)) * D + d;
-      xrow(i) = v ? a.x[e] : 0.f;
-      grow(i) = v ? a.g[e] : 0.f;
-    }
+    for (int i = 0; i < kHalf; ++i) xrow(i) = valid(i) ? a.x[elem(i)] : 0.f;
     // momenta of the first transition, straight into registers
 #pragma unroll
     for (int i = 0; i < kHalf; ++i)
       p[i] = valid(i) ? momentum1(a.seed, static_cast<uint32_t>(d), chain_of(i), a.t) : 0.f;
 
+    int nbar = 0;                           // grid barriers met so far (T > 1)
     for (int j = 0; j < T; ++j) {
       const uint32_t t = a.t + static_cast<uint32_t>(j);
       const bool more = j + 1 < T;
       const float eps = persistent ? da_s->eps : a.da->eps;
       if (j > 0) {
 #pragma unroll
-        for (int i = 0; i < kHalf; ++i)
-          p[i] = valid(i) ? fa.p0next[static_cast<int64_t>(pair_base + rowi(i)) * D + d] : 0.f;
+        for (int i = 0; i < kHalf; ++i) p[i] = valid(i) ? fa.p0next[elem(i)] : 0.f;
       }
       // |p0|^2 partials of this warp's dims, one per chain
       {
@@ -491,13 +497,30 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         for (int i = 0; i < kHalf; ++i) v[i] = p[i] * p[i];
         red[(2 * 4 + quarter) * 64 + rowi(lane)] = transpose_reduce32(v, lane);
       }
-      // begin: p = p0 + eps/2 g0, x1 = x0 + eps p (the peer's half first)
+      // begin: p = p0 + eps/2 g0, x1 = x0 + eps p (the peer's half first);
+      // the cached gradients are read eight at a time, the next eight in
+      // flight while the current ones are used
+      {
+        float g0[8], gn[8];
 #pragma unroll
-      for (int i = 0; i < kHalf; ++i) {
-        p[i] = fmaf(0.5f * eps, grow(i), p[i]);
-        x[i] = fmaf(eps, p[i], xrow(i));
-        store_x(i, x[i]);
-        if (i == 15) publish_stage();
+        for (int k = 0; k < 8; ++k) g0[k] = valid(k) ? a.g[elem(k)] : 0.f;
+#pragma unroll
+        for (int i0 = 0; i0 < kHalf; i0 += 8) {
+          if (i0 + 8 < kHalf) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) gn[k] = valid(i0 + 8 + k) ? a.g[elem(i0 + 8 + k)] : 0.f;
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int i = i0 + k;
+            p[i] = fmaf(0.5f * eps, g0[k], p[i]);
+            x[i] = fmaf(eps, p[i], xrow(i));
+            store_x(i, x[i]);
+          }
+          if (i0 + 8 == 16) publish_stage();
+#pragma unroll
+          for (int k = 0; k < 8; ++k) g0[k] = gn[k];
+        }
       }
       publish_own();
       const int s0 = j * L;                 // gradient steps of this transition: s0 .. s0 + L - 1
@@ -508,7 +531,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 #pragma unroll
         for (int cb = 0; cb < kHalf / 16; ++cb) {
           float accv[16];
-          ptx::tmem_ld16(acc_base + acc_col(cb), accv);
+          load_acc(cb, accv);
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
             const int i = cb * 16 + k;
@@ -528,7 +551,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 #pragma unroll
         for (int cb = 0; cb < kHalf / 16; ++cb) {
           float accv[16];
-          ptx::tmem_ld16(acc_base + acc_col(cb), accv);
+          load_acc(cb, accv);
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
             const int i = cb * 16 + k;
@@ -643,17 +666,16 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 #pragma unroll
       for (int cb = 0; cb < kHalf / 16; ++cb) {
         float accv[16];
-        ptx::tmem_ld16(acc_base + acc_col(cb), accv);
+        load_acc(cb, accv);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const int i = cb * 16 + k;
           if (ok && valid(i)) {
             if (acc_flag[rowi(i)]) {
               xrow(i) = x[i];
-              grow(i) = -accv[k];
+              a.g[elem(i)] = -accv[k];
             }
-            if (samp && !(TEMPERED && fa.exchange))
-              samp[static_cast<int64_t>(pair_base + rowi(i)) * D + d] = xrow(i);
+            if (samp && !(TEMPERED && fa.exchange)) samp[elem(i)] = xrow(i);
           }
         }
       }
@@ -667,21 +689,21 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
           const int r = rowi(i);
           if (ok && valid(i) && swp_s[r]) {
             float* x0 = &xs[r * 128 + dl];
-            float* g0 = &gs[r * 128 + dl];
+            float* g0 = a.g + elem(i);
             const float xa = x0[0], xb = x0[128];
-            const float ga = g0[0], gb = g0[128];
+            const float ga = g0[0], gb = g0[D];
             const float b0 = beta_s[r], b1 = beta_s[r + 1];
             x0[0] = xb;
             x0[128] = xa;
             g0[0] = gb / b1 * b0;
-            g0[128] = ga / b0 * b1;
+            g0[D] = ga / b0 * b1;
           }
         }
         epi_barrier();
         if (samp) {
 #pragma unroll
           for (int i = 0; i < kHalf; ++i)
-            if (ok && valid(i)) samp[static_cast<int64_t>(pair_base + rowi(i)) * D + d] = xrow(i);
+            if (ok && valid(i)) samp[elem(i)] = xrow(i);
         }
       }
       if (moments && ok) {
@@ -693,7 +715,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             const int i = i0 + k;
-            e[k] = static_cast<int64_t>(pair_base + rowi(i)) * D + d;
+            e[k] = elem(i);
             v[k] = xrow(i);
             if (valid(i)) vmask |= 1u << k;
           }
@@ -702,36 +724,45 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       }
       // dual averaging over all chains of the posterior
       if (persistent) {
-        // Every CTA publishes a partial (the pair's sum in the leader, zero
-        // in the peer) and meets the grid barrier once (warp 2, lane 0)
-        // while warp 3 forms the update's coefficients; then warp 2 sums
-        // the partials in the order of the one-transition reduction, so
-        // both launch shapes take the same step sizes.
-        double* part = a.partials + (j & 1) * static_cast<int>(gridDim.x);
-        if (warp == 2) {
-          double v = rank == 0 ? static_cast<double>(prob_s[lane]) + static_cast<double>(prob_s[lane + 32]) : 0.0;
-          v = warp_sum_d(v);
-          if (lane == 0) {
-            part[blockIdx.x] = v;
-            if (!grid_barrier(fa.grid_bar, static_cast<unsigned>(j + 1))) {
-              atomicCAS(fa.err, 0, 7);
-              *abort_s = 1;
+        // Transitions that adapt (and the launch's last, whose statistic the
+        // state reports) meet at the grid barrier: every CTA publishes a
+        // partial (the pair's sum in the leader, zero in the peer) and meets
+        // the barrier once (warp 2, lane 0) while warp 3 forms the update's
+        // coefficients; then warp 2 sums the partials in the order of the
+        // one-transition reduction, so both launch shapes take the same step
+        // sizes.  The others only check the error flag: a step size that
+        // does not adapt needs no statistic.
+        const bool adapts = da_s->adapt && t_full < da_s->num_adapt;
+        if (adapts || !more) {
+          double* part = a.partials + (nbar & 1) * static_cast<int>(gridDim.x);
+          ++nbar;
+          if (warp == 2) {
+            double v = rank == 0 ? static_cast<double>(prob_s[lane]) + static_cast<double>(prob_s[lane + 32]) : 0.0;
+            v = warp_sum_d(v);
+            if (lane == 0) {
+              part[blockIdx.x] = v;
+              if (!grid_barrier(fa.grid_bar, static_cast<unsigned>(nbar))) {
+                atomicCAS(fa.err, 0, 7);
+                *abort_s = 1;
+              }
+            }
+          } else if (warp == 3 && lane == 0) {
+            *coef_s = da_prepare(da_s, t_full);
+          }
+          epi_barrier();
+          if (warp == 2 && *reinterpret_cast<volatile int*>(abort_s) == 0) {
+            __threadfence();
+            double acc = 0.0;
+            for (int b = lane; b < static_cast<int>(gridDim.x); b += 32)
+              acc += reinterpret_cast<volatile double*>(part)[b];
+            acc = warp_sum_d(acc);
+            if (lane == 0) {
+              da_apply(da_s, *coef_s, acc / static_cast<double>(C), t_full);
+              if (*reinterpret_cast<volatile int*>(fa.err) != 0) *abort_s = 1;
             }
           }
-        } else if (warp == 3 && lane == 0) {
-          *coef_s = da_prepare(da_s, t_full);
-        }
-        epi_barrier();
-        if (warp == 2 && *reinterpret_cast<volatile int*>(abort_s) == 0) {
-          __threadfence();
-          double acc = 0.0;
-          for (int b = lane; b < static_cast<int>(gridDim.x); b += 32)
-            acc += reinterpret_cast<volatile double*>(part)[b];
-          acc = warp_sum_d(acc);
-          if (lane == 0) {
-            da_apply(da_s, *coef_s, acc / static_cast<double>(C), t_full);
-            if (*reinterpret_cast<volatile int*>(fa.err) != 0) *abort_s = 1;
-          }
+        } else if (warp == 2 && lane == 0 && *reinterpret_cast<volatile int*>(fa.err) != 0) {
+          *abort_s = 1;
         }
         epi_barrier();
         if (*reinterpret_cast<volatile int*>(abort_s)) break;
@@ -742,15 +773,10 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         if (lane == 0) *psum_s = v;
       }
     }
-    // the chains' final state back to global memory
+    // the chains' final positions back to global memory (the gradients are there)
 #pragma unroll 4
-    for (int i = 0; i < kHalf; ++i) {
-      if (ok && valid(i)) {
-        const int64_t e = static_cast<int64_t>(pair_base + rowi(i)) * D + d;
-        a.x[e] = xrow(i);
-        a.g[e] = grow(i);
-      }
-    }
+    for (int i = 0; i < kHalf; ++i)
+      if (ok && valid(i)) a.x[elem(i)] = xrow(i);
     if (persistent && blockIdx.x == 0 && threadIdx.x == 64 && !*abort_s) *a.da = *da_s;
   }
   // every copy into this CTA's tile has landed (immediate unless a wait gave up)

@@ -256,7 +256,7 @@ cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws
 bool gauss_fused_supported(const hmc_target& t);
 unsigned gauss_pair_grid(int64_t C);
 // floats of the pair kernel's tensor-memory image of P (dim <= 256)
-constexpr size_t kGaussPairImageFloats = 2 * 7 * 2 * 2 * 4 * 4 * 32 * 4;
+constexpr size_t kGaussPairImageFloats = 2 * 6 * 2 * 2 * 4 * 4 * 32 * 4;
 cudaError_t launch_gauss_pair_image(const float* Phi, const float* Plo, int D, float* image,
                                     cudaStream_t s);
 cudaError_t launch_gauss_momentum(const StepArgs& a, GaussTc& tc, cudaStream_t s);
