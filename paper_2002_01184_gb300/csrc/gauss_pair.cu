@@ -16,8 +16,10 @@
 //     that each chain's P_lo x_hi lands in one of its own two columns.  A
 //     chain's gradient is the sum of its two columns.
 //   * A (P head / remainder) is resident for the whole launch: each CTA's 128
-//     rows of P, K-chunks 0-5 (dims 0-191) in its tensor memory and chunks 6-7
-//     in shared memory.
+//     rows of P, the head of every K-chunk and the remainder of K-chunks 0-3
+//     in its tensor memory, the remainder of K-chunks 4-7 in shared memory
+//     (A operands read from shared memory slow the MMAs down more for the
+//     N = 128 product than for the N = 64 one).
 //   * Epilogue (warps 2-9 of both CTAs): one output dim per thread and 32
 //     chains per thread, 16 of the peer's and 16 of its own; momenta and
 //     trajectory positions in registers, the chains' current positions (this
@@ -58,8 +60,8 @@ namespace {
 
 constexpr int kMaxDim = 256;
 constexpr int kChunks = kMaxDim / 32;             // K-chunks of 32 dims
-constexpr int kTmemChunks = 6;                    // P chunks held in tensor memory
-constexpr int kSmemChunks = kChunks - kTmemChunks;   // P chunks held in shared memory
+constexpr int kLoTmemChunks = 4;                  // P remainder chunks held in tensor memory
+constexpr int kHalfChunks = kChunks + kLoTmemChunks;   // 32-column P blocks in tensor memory
 constexpr int kThreads = 320;
 constexpr int kPairChains = 64;                   // chains of a pair
 constexpr int kHalf = 32;                         // chains per CTA
@@ -68,26 +70,26 @@ constexpr uint32_t kLoOff = kHalf * kRowBytes;    // remainder rows follow the h
 constexpr uint32_t kBChunk = 2 * kLoOff;          // 64 rows (32 head, 32 remainder) x 128 B
 constexpr uint32_t kBBytes = kChunks * kBChunk;   // the position tile
 constexpr uint32_t kAHalf = 128 * 128;            // 128 rows of P x 32 floats
-constexpr uint32_t kABytes = kSmemChunks * 2 * kAHalf;   // P chunks 6-7, head and remainder
+constexpr uint32_t kABytes = (kChunks - kLoTmemChunks) * kAHalf;   // P remainder chunks 4-7
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColAcc = 0;                   // accumulators: 128 columns
 constexpr uint32_t kColLoProduct = 32;            // the N = 64 product's column offset
-constexpr uint32_t kColP = 128;                   // chunk kc: head at kColP + 64 kc, remainder + 32
+constexpr uint32_t kColP = 128;                   // P block h (head chunk h, then remainder chunk h - 8) at kColP + 32 h
 constexpr uint32_t kStageBytes = 4 * kBChunk;     // 4 K-chunks (this CTA's 128 dims) x 32 chains
 constexpr uint32_t kStateBytes = kPairChains * 128 * 4;   // current positions, this CTA's dims
 // barriers (8), tmem slot, red [3][4][64], red_pair [3][64], peer_in [3][64],
 // acc_flag [64], prob_s [64], DA state copy, flags, DA coefficients, pair
 // sum, inverse temperatures [64], tempered log p after the decision [64],
-// exchange flags [64]
+// exchange flags [64], log u [64], current log p [64]
 constexpr uint32_t kSmall =
-    8 * 8 + 16 + (3 * 4 * 64 + 3 * 64 + 3 * 64 + 64 + 64) * 4 + 128 + 16 + 32 + 16 + 3 * 64 * 4;
+    8 * 8 + 16 + (3 * 4 * 64 + 3 * 64 + 3 * 64 + 64 + 64) * 4 + 128 + 16 + 32 + 16 + 5 * 64 * 4;
 constexpr size_t kSmemUsed = kBBytes + kABytes + kStageBytes + kStateBytes + kSmall + 1024;
 // Above half of an SM's shared memory, so that one CTA runs per SM: a CTA
 // allocates all 512 tensor-memory columns and must never queue in
 // tcgen05.alloc behind another CTA of the launch.
 constexpr size_t kSmem = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
 static_assert(kSmem <= 227 * 1024, "shared memory");
-static_assert(kColP + 2 * 32 * kTmemChunks == kTmemCols, "tensor-memory columns");
+static_assert(kColP + 32 * kHalfChunks == kTmemCols, "tensor-memory columns");
 
 struct PairArgs {
   StepArgs s;           // s.t / s.t_full: the first transition of the launch
@@ -105,32 +107,31 @@ struct PairArgs {
 };
 
 // Index of element e of float4 j of lane `lane` in the tensor-memory image:
-// rank, K-chunk kc (0-6), head / remainder hl, 16-column half q16, lane
-// quarter q.  A warp's j-th float4 load of a 16-column block is 512
-// contiguous bytes.
-__host__ __device__ constexpr int image_index(int rank, int kc, int hl, int q16, int q, int j, int lane) {
-  return (((((rank * kTmemChunks + kc) * 2 + hl) * 2 + q16) * 4 + q) * 4 + j) * 128 + lane * 4;
+// rank, 32-column P block h (0-7: head chunks 0-7, 8-11: remainder chunks
+// 0-3), 16-column half q16, lane quarter q.  A warp's j-th float4 load of a
+// 16-column block is 512 contiguous bytes.
+__host__ __device__ constexpr int image_index(int rank, int h, int q16, int q, int j, int lane) {
+  return ((((rank * kHalfChunks + h) * 2 + q16) * 4 + q) * 4 + j) * 128 + lane * 4;
 }
 
 __global__ void k_tmem_image(const float* __restrict__ Phi, const float* __restrict__ Plo, int D,
                              float* __restrict__ image) {
-  constexpr int n = 2 * kTmemChunks * 2 * 2 * 4 * 4 * 32;   // float4 slots
+  constexpr int n = 2 * kHalfChunks * 2 * 4 * 4 * 32;   // float4 slots
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
     int r = v;
     const int lane = r % 32; r /= 32;
     const int j = r % 4; r /= 4;
     const int q = r % 4; r /= 4;
     const int q16 = r % 2; r /= 2;
-    const int hl = r % 2; r /= 2;
-    const int kc = r % kTmemChunks;
-    const int rank = r / kTmemChunks;
+    const int h = r % kHalfChunks;
+    const int rank = r / kHalfChunks;
     const int row = rank * 128 + q * 32 + lane;
-    const int col = kc * 32 + q16 * 16 + j * 4;
-    const float* src = hl == 0 ? Phi : Plo;
+    const int col = (h < kChunks ? h : h - kChunks) * 32 + q16 * 16 + j * 4;
+    const float* src = h < kChunks ? Phi : Plo;
     float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
     if (row < D && col < D)            // D % 4 == 0: all four in or out
       val = *reinterpret_cast<const float4*>(src + static_cast<int64_t>(row) * D + col);
-    *reinterpret_cast<float4*>(image + image_index(rank, kc, hl, q16, q, j, lane)) = val;
+    *reinterpret_cast<float4*>(image + image_index(rank, h, q16, q, j, lane)) = val;
   }
 }
 
@@ -191,7 +192,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint8_t* Bt = smem;                                      // positions: [8 K-chunks][head 32 rows, remainder 32 rows]
-  uint8_t* As = Bt + kBBytes;                              // P chunks 6-7: [chunk][head, remainder]
+  uint8_t* As = Bt + kBBytes;                              // P remainder chunks 4-7
   uint8_t* Stg = As + kABytes;                             // staging, laid out as 4 K-chunks of Bt
   float* xs = reinterpret_cast<float*>(Stg + kStageBytes); // [64 chains][128 dims] current position
   uint64_t* a7_full = reinterpret_cast<uint64_t*>(xs + kPairChains * 128);
@@ -200,12 +201,11 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   uint64_t* in_full = own_full + 1;       // this CTA's tile: the peer's K-chunks copied in
   uint64_t* fwd_own = in_full + 1;        // leader: the peer's own_full, forwarded
   uint64_t* fwd_in = fwd_own + 1;         // leader: the peer's in_full, forwarded
-  uint64_t* sums_in = fwd_in + 1;         // leader: the peer's partial sums have landed
-  uint64_t* dec_in = sums_in + 1;         // peer: the leader's decisions have landed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(dec_in + 1);
+  uint64_t* sums_in = fwd_in + 1;         // the other CTA's partial sums have landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sums_in + 2);
   float* red = reinterpret_cast<float*>(tmem_slot + 4);   // [3 sums][4 quarters][64 chains]
   float* red_pair = red + 3 * 4 * 64;                     // [3][64] this CTA's sums
-  float* peer_in = red_pair + 3 * 64;                     // [3][64] the peer's sums (leader)
+  float* peer_in = red_pair + 3 * 64;                     // [3][64] the other CTA's sums
   int* acc_flag = reinterpret_cast<int*>(peer_in + 3 * 64);   // [64]
   float* prob_s = reinterpret_cast<float*>(acc_flag + 64);    // [64]
   DAState* da_s = reinterpret_cast<DAState*>(prob_s + 64);    // this CTA's copy (T > 1)
@@ -215,12 +215,14 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   float* beta_s = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(da_s) + 192);   // [64]
   float* lpn_s = beta_s + 64;                             // [64] exchange: log p after the decision
   int* swp_s = reinterpret_cast<int*>(lpn_s + 64);        // [64] exchange: row r and r + 1 swap
+  float* lu_s = reinterpret_cast<float*>(swp_s + 64);     // [64] log u of this transition's accept test
+  float* lpc_s = lu_s + 64;                               // [64] log p of the chains' current state
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = ptx::cluster_rank();              // 0: leader, 1: peer
   const int C = a.C, D = a.D, L = a.L, T = fa.T;
   const int nk = (D + 31) >> 5;
-  const int nsm = nk > kTmemChunks ? nk - kTmemChunks : 0;   // P chunks in shared memory
+  const int nsm = nk > kLoTmemChunks ? nk - kLoTmemChunks : 0;   // P remainder chunks in shared memory
   const int pair_base = (blockIdx.x >> 1) * kPairChains;
   const bool persistent = fa.grid_bar != nullptr;
   constexpr uint16_t kPairMask = 0x3;
@@ -233,8 +235,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     ptx::mbar_init(in_full, 1);           // armed with the copy bytes by one own-chain thread
     ptx::mbar_init(fwd_own, 1);
     ptx::mbar_init(fwd_in, 1);
-    ptx::mbar_init(sums_in, kPairChains);  // the peer's 64 summing threads
-    ptx::mbar_init(dec_in, kPairChains);   // the leader's 64 deciding threads
+    ptx::mbar_init(sums_in, kPairChains);  // the other CTA's 64 summing threads
     ptx::fence_mbar_init();
     ptx::prefetch_tensormap(&mPhi);
     ptx::prefetch_tensormap(&mPlo);
@@ -272,15 +273,12 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 
   if (warp == 0) {
     if (lane == 0 && nsm > 0) {
-      // ---- P chunks 6-7 of this CTA's rows, once, completing on the leader's barrier
-      if (rank == 0) ptx::mbar_arrive_expect_tx(a7_full, 2u * 2u * static_cast<uint32_t>(nsm) * kAHalf);
+      // ---- P remainder chunks 4-7 of this CTA's rows, once, completing on the leader's barrier
+      if (rank == 0) ptx::mbar_arrive_expect_tx(a7_full, 2u * static_cast<uint32_t>(nsm) * kAHalf);
       const uint32_t bar = ptx::mapa(ptx::smem_u32(a7_full), 0);
-      for (int c = 0; c < nsm; ++c) {
-        uint8_t* dst = As + c * 2 * kAHalf;
-        const int col = (kTmemChunks + c) * 32;
-        ptx::tma_load_2d_to_bar(dst, &mPhi, bar, col, static_cast<int>(rank) * 128);
-        ptx::tma_load_2d_to_bar(dst + kAHalf, &mPlo, bar, col, static_cast<int>(rank) * 128);
-      }
+      for (int c = 0; c < nsm; ++c)
+        ptx::tma_load_2d_to_bar(As + c * kAHalf, &mPlo, bar, (kLoTmemChunks + c) * 32,
+                                static_cast<int>(rank) * 128);
     }
   } else if (warp == 1) {
     if (lane == 0 && rank == 0) {
@@ -291,29 +289,30 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         atomicCAS(fa.err, 0, 1);
         ok = false;
       }
-      // one K-chunk: 4 K-steps x 2 products (P_hi [x_hi; x_lo], then P_lo x_hi)
+      // one K-chunk: 4 K-steps x 2 products (P_hi [x_hi; x_lo] with the head
+      // from tensor memory, then P_lo x_hi with the remainder from tensor
+      // memory for chunks 0-3 and from shared memory for chunks 4-7)
       auto chunk_mmas = [&](int kc, bool& first) {
         const uint32_t b = ptx::smem_u32(Bt + kc * kBChunk);
-        if (kc < kTmemChunks) {
+        if (kc < kLoTmemChunks) {
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const uint64_t db = ptx::sw128_kmajor_desc(b + 32 * j);
-            const uint32_t ahi = tmem + kColP + 64 * kc + 8 * j;
-            const uint32_t alo = ahi + 32;
+            const uint32_t ahi = tmem + kColP + 32 * kc + 8 * j;
+            const uint32_t alo = tmem + kColP + 32 * (kChunks + kc) + 8 * j;
             ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, ahi, db, idesc_wide, first ? 0u : 1u);
             ptx::mma_tf32_pair_tmem_a(tmem + kColAcc + kColLoProduct, alo, db, idesc_head, 1u);
             first = false;
           }
         } else {
-          const uint32_t ahi = ptx::smem_u32(As + (kc - kTmemChunks) * 2 * kAHalf);
-          const uint32_t alo = ahi + kAHalf;
+          const uint32_t alo = ptx::smem_u32(As + (kc - kLoTmemChunks) * kAHalf);
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            const uint64_t dahi = ptx::sw128_kmajor_desc(ahi + 32 * j);
-            const uint64_t dalo = ptx::sw128_kmajor_desc(alo + 32 * j);
             const uint64_t db = ptx::sw128_kmajor_desc(b + 32 * j);
-            ptx::mma_tf32_pair(tmem + kColAcc, dahi, db, idesc_wide, first ? 0u : 1u);
-            ptx::mma_tf32_pair(tmem + kColAcc + kColLoProduct, dalo, db, idesc_head, 1u);
+            const uint32_t ahi = tmem + kColP + 32 * kc + 8 * j;
+            ptx::mma_tf32_pair_tmem_a(tmem + kColAcc, ahi, db, idesc_wide, first ? 0u : 1u);
+            ptx::mma_tf32_pair(tmem + kColAcc + kColLoProduct, ptx::sw128_kmajor_desc(alo + 32 * j), db,
+                               idesc_head, 1u);
             first = false;
           }
         }
@@ -448,26 +447,22 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 
     // P rows of this CTA (row = output dim d = TMEM lane) into tensor memory
     // from the pre-arranged image (coalesced): the two warps of a lane
-    // quarter split chunks 0-2 and 3-5
+    // quarter split the twelve 32-column blocks (head chunks 0-7, remainder
+    // chunks 0-3) six and six
     {
-      const int kc_end = min(nk, kTmemChunks);
-      constexpr int kSplit = kTmemChunks / 2;
-      for (int kc = sub == 0 ? 0 : kSplit; kc < (sub == 0 ? min(kc_end, kSplit) : kc_end); ++kc) {
+      constexpr int kSplit = kHalfChunks / 2;
+      for (int h = sub == 0 ? 0 : kSplit; h < (sub == 0 ? kSplit : kHalfChunks); ++h) {
+        if ((h < kChunks ? h : h - kChunks) >= nk) continue;
 #pragma unroll
         for (int q16 = 0; q16 < 2; ++q16) {
-          float vh[16], vl[16];
+          float v[16];
 #pragma unroll
           for (int q4 = 0; q4 < 4; ++q4) {
             const float4 u = *reinterpret_cast<const float4*>(
-                fa.Ptm + image_index(static_cast<int>(rank), kc, 0, q16, quarter, q4, lane));
-            const float4 w = *reinterpret_cast<const float4*>(
-                fa.Ptm + image_index(static_cast<int>(rank), kc, 1, q16, quarter, q4, lane));
-            vh[4 * q4] = u.x; vh[4 * q4 + 1] = u.y; vh[4 * q4 + 2] = u.z; vh[4 * q4 + 3] = u.w;
-            vl[4 * q4] = w.x; vl[4 * q4 + 1] = w.y; vl[4 * q4 + 2] = w.z; vl[4 * q4 + 3] = w.w;
+                fa.Ptm + image_index(static_cast<int>(rank), h, q16, quarter, q4, lane));
+            v[4 * q4] = u.x; v[4 * q4 + 1] = u.y; v[4 * q4 + 2] = u.z; v[4 * q4 + 3] = u.w;
           }
-          const uint32_t tcol = tmem + (static_cast<uint32_t>(quarter * 32) << 16) + kColP + 64 * kc + 16 * q16;
-          ptx::tmem_st16(tcol, vh);
-          ptx::tmem_st16(tcol + 32, vl);
+          ptx::tmem_st16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + kColP + 32 * h + 16 * q16, v);
         }
       }
       ptx::tmem_wait_st();
@@ -476,53 +471,44 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     // in a.g, which the accepted proposals overwrite)
 #pragma unroll 4
     for (int i = 0; i < kHalf; ++i) xrow(i) = valid(i) ? a.x[elem(i)] : 0.f;
-    // momenta of the first transition, straight into registers
+    // At the top of every transition p holds the cached gradients g0 and x
+    // the transition's momenta p0 (for the first one drawn here, for the
+    // others loaded during the previous transition's accept step).
 #pragma unroll
-    for (int i = 0; i < kHalf; ++i)
-      p[i] = valid(i) ? momentum1(a.seed, static_cast<uint32_t>(d), chain_of(i), a.t) : 0.f;
+    for (int i = 0; i < kHalf; ++i) {
+      p[i] = valid(i) ? a.g[elem(i)] : 0.f;
+      x[i] = valid(i) ? momentum1(a.seed, static_cast<uint32_t>(d), chain_of(i), a.t) : 0.f;
+    }
+    // the deciding threads (warps 2-3 of both CTAs, chain pair_base + c):
+    // the current log p of their chain, kept in shared memory from here on
+    const int c = ew * 32 + lane;                 // 0..255; chains 0..63 decide
+    if (c < kPairChains) lpc_s[c] = pair_base + c < C ? a.lp[pair_base + c] : 0.f;
 
     int nbar = 0;                           // grid barriers met so far (T > 1)
     for (int j = 0; j < T; ++j) {
       const uint32_t t = a.t + static_cast<uint32_t>(j);
       const bool more = j + 1 < T;
       const float eps = persistent ? da_s->eps : a.da->eps;
-      if (j > 0) {
-#pragma unroll
-        for (int i = 0; i < kHalf; ++i) p[i] = valid(i) ? fa.p0next[elem(i)] : 0.f;
-      }
       // |p0|^2 partials of this warp's dims, one per chain
       {
         float v[kHalf];
 #pragma unroll
-        for (int i = 0; i < kHalf; ++i) v[i] = p[i] * p[i];
+        for (int i = 0; i < kHalf; ++i) v[i] = x[i] * x[i];
         red[(2 * 4 + quarter) * 64 + rowi(lane)] = transpose_reduce32(v, lane);
       }
-      // begin: p = p0 + eps/2 g0, x1 = x0 + eps p (the peer's half first);
-      // the cached gradients are read eight at a time, the next eight in
-      // flight while the current ones are used
-      {
-        float g0[8], gn[8];
+      // begin: p = p0 + eps/2 g0, x1 = x0 + eps p (the peer's half first)
 #pragma unroll
-        for (int k = 0; k < 8; ++k) g0[k] = valid(k) ? a.g[elem(k)] : 0.f;
-#pragma unroll
-        for (int i0 = 0; i0 < kHalf; i0 += 8) {
-          if (i0 + 8 < kHalf) {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) gn[k] = valid(i0 + 8 + k) ? a.g[elem(i0 + 8 + k)] : 0.f;
-          }
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const int i = i0 + k;
-            p[i] = fmaf(0.5f * eps, g0[k], p[i]);
-            x[i] = fmaf(eps, p[i], xrow(i));
-            store_x(i, x[i]);
-          }
-          if (i0 + 8 == 16) publish_stage();
-#pragma unroll
-          for (int k = 0; k < 8; ++k) g0[k] = gn[k];
-        }
+      for (int i = 0; i < kHalf; ++i) {
+        const float pn = fmaf(0.5f * eps, p[i], x[i]);
+        p[i] = pn;
+        x[i] = fmaf(eps, pn, xrow(i));
+        store_x(i, x[i]);
+        if (i == 15) publish_stage();
       }
       publish_own();
+      // the accept test's log u, off the critical path
+      if (c < kPairChains && pair_base + c < C)
+        lu_s[c] = accept_log_uniform(a.seed, static_cast<uint32_t>(pair_base + c) + a.chain_offset, t);
       const int s0 = j * L;                 // gradient steps of this transition: s0 .. s0 + L - 1
       // steps 1 .. L-1: merged kick + drift
       for (int l = 1; l < L; ++l) {
@@ -564,30 +550,36 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         for (int i = 0; i < kHalf; ++i) v[i] = valid(i) ? p[i] * p[i] : 0.f;
         red[(1 * 4 + quarter) * 64 + rowi(lane)] = transpose_reduce32(v, lane);
       }
+      // the momenta are spent: p takes the cached gradients, in flight while
+      // the chains are decided (the accepted ones are replaced below)
+      if (more) {
+#pragma unroll
+        for (int i = 0; i < kHalf; ++i) p[i] = valid(i) ? a.g[elem(i)] : 0.f;
+      }
       epi_barrier();
-      // Only the epilogue warps run this loop, so the two CTAs meet on
-      // mbarriers: the peer's sums land in the leader (sums_in), the
-      // leader's decisions land in the peer (dec_in).
-      const int c = ew * 32 + lane;                 // 0..255; chains 0..63 handled below
+      // Only the epilogue warps run this loop, so the two CTAs meet on an
+      // mbarrier: each sends its partial sums to the other (sums_in), and
+      // both decide every chain of the pair from the same two partials (a + b
+      // equals b + a in float32, so the decisions agree bit for bit); the
+      // leader writes the kernel results.
       if (c < kPairChains) {
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
           float sum = 0.f;
           for (int q = 0; q < 4; ++q) sum += red[(v * 4 + q) * 64 + c];
-          if (rank == 0)
-            red_pair[v * 64 + c] = sum;
-          else
-            ptx::st_cluster_f32(ptx::mapa(ptx::smem_u32(&peer_in[v * 64 + c]), 0), sum);
+          red_pair[v * 64 + c] = sum;
+          ptx::st_cluster_f32(ptx::mapa(ptx::smem_u32(&peer_in[v * 64 + c]), peer), sum);
         }
-        if (rank != 0) ptx::mbar_arrive_cluster(ptx::mapa(ptx::smem_u32(sums_in), 0));
+        ptx::mbar_arrive_cluster(ptx::mapa(ptx::smem_u32(sums_in), peer));
       }
       const long long t_full = a.t_full + j;
       const long long k_out = t_full - fa.keep_from;
-      if (rank == 0 && ew < 2) {
+      if (c < kPairChains) {
         if (!ptx::mbar_wait_cluster(sums_in, j & 1)) {
           atomicCAS(fa.err, 0, 8);
           ok = false;
         }
+        const bool lead = rank == 0;
         // H_L and the Metropolis-Hastings decision, chain c of the pair
         const int chain = pair_base + c;
         float prob = 0.f;
@@ -596,30 +588,29 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
           const float xg = red_pair[c] + peer_in[c];
           const float pp = red_pair[64 + c] + peer_in[64 + c];
           const float kin0 = 0.5f * (red_pair[128 + c] + peer_in[128 + c]);
-          const float lp0 = a.lp[chain];
+          const float lp0 = lpc_s[c];
           const float lp1 = 0.5f * xg;
           float la = (-lp0 + kin0) - (-lp1 + 0.5f * pp);
           if (!isfinite(la)) la = -INFINITY;
-          const uint32_t gchain = static_cast<uint32_t>(chain) + a.chain_offset;
-          acc = accept_log_uniform(a.seed, gchain, t) < la;
+          acc = lu_s[c] < la;
           prob = accept_prob(la);
           if (TEMPERED && fa.exchange) {
             lpn_s[c] = acc ? lp1 : lp0;
-          } else if (ok && acc) {
-            a.lp[chain] = lp1;
+          } else if (acc) {
+            lpc_s[c] = lp1;
+            if (ok && lead) a.lp[chain] = lp1;
           }
-          if (ok) {
+          if (ok && lead) {
             a.is_accepted[chain] = static_cast<uint8_t>(acc);
             a.log_accept[chain] = la;
             if (k_out >= 0 && fa.trace_acc) fa.trace_acc[k_out * C + chain] = static_cast<uint8_t>(acc);
           }
         }
         acc_flag[c] = acc;
-        ptx::st_cluster_s32(ptx::mapa(ptx::smem_u32(&acc_flag[c]), 1), acc);
         prob_s[c] = prob;
         if (TEMPERED && fa.exchange) {
           // the exchange step: row c decides the pair (c, c + 1) when it is
-          // the lower replica of an active pair, then every row writes its
+          // the lower replica of an active pair, then every row takes its
           // log p (swapped and rescaled where its pair swapped)
           deciders_barrier();
           const int Kr = a.K;
@@ -633,31 +624,25 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
               sw = remc_swap_accept(lpn_s[c], lpn_s[c + 1], beta_s[c], beta_s[c + 1], a.seed,
                                     static_cast<uint32_t>(k), cout, t, &raw0, &raw1);
             }
-            if (ok) fa.swapped[static_cast<int64_t>(cout) * (Kr - 1) + k] = static_cast<uint8_t>(sw);
+            if (ok && lead) fa.swapped[static_cast<int64_t>(cout) * (Kr - 1) + k] = static_cast<uint8_t>(sw);
           }
           swp_s[c] = sw;
-          ptx::st_cluster_s32(ptx::mapa(ptx::smem_u32(&swp_s[c]), 1), sw);
           deciders_barrier();
-          if (row < C && ok) {
+          if (row < C) {
             float lpf = lpn_s[c];
             if (swp_s[c]) {                        // lower row of a swapped pair
               lpf = beta_s[c] * (lpn_s[c + 1] / beta_s[c + 1]);
             } else if (k > 0 && swp_s[c - 1]) {    // upper row of a swapped pair
               lpf = beta_s[c] * (lpn_s[c - 1] / beta_s[c - 1]);
             }
-            a.lp[row] = lpf;
+            lpc_s[c] = lpf;
+            if (ok && lead) a.lp[row] = lpf;
           }
         }
-        if (blockIdx.x == 0 && c == 0 && k_out >= 0 && fa.trace_eps && ok) fa.trace_eps[k_out] = eps;
-        ptx::mbar_arrive_cluster(ptx::mapa(ptx::smem_u32(dec_in), 1));
+        if (lead && blockIdx.x == 0 && c == 0 && k_out >= 0 && fa.trace_eps && ok) fa.trace_eps[k_out] = eps;
       }
-      // decisions visible to every epilogue thread of both CTAs
-      if (rank == 0) {
-        epi_barrier();
-      } else if (!ptx::mbar_wait_cluster(dec_in, j & 1)) {
-        atomicCAS(fa.err, 0, 9);
-        ok = false;
-      }
+      // decisions visible to every epilogue thread
+      epi_barrier();
       // the accepted state (gradient from the accumulators) and the kept sample
       float* samp = (k_out >= 0 && fa.samples) ? fa.samples + k_out * static_cast<int64_t>(C) * D : nullptr;
       // streaming driver: running moments of the kept states instead of a trace
@@ -674,9 +659,20 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
             if (acc_flag[rowi(i)]) {
               xrow(i) = x[i];
               a.g[elem(i)] = -accv[k];
+              p[i] = -accv[k];
             }
             if (samp && !(TEMPERED && fa.exchange)) samp[elem(i)] = xrow(i);
           }
+        }
+        // the next transition's momenta (drawn during this one's steps) for
+        // these 16 elements, loaded only once their positions are spent (the
+        // empty asm keeps the compiler from hoisting the loads, which would
+        // keep both sets of 16 live at once)
+        asm volatile("" ::: "memory");
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int i = cb * 16 + k;
+          x[i] = more && valid(i) ? fa.p0next[elem(i)] : 0.f;
         }
       }
       if (TEMPERED && fa.exchange) {
@@ -705,21 +701,28 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
           for (int i = 0; i < kHalf; ++i)
             if (ok && valid(i)) samp[elem(i)] = xrow(i);
         }
+        // swapped rows took new cached gradients
+        if (more) {
+#pragma unroll
+          for (int i = 0; i < kHalf; ++i) p[i] = valid(i) ? a.g[elem(i)] : 0.f;
+        }
       }
       if (moments && ok) {
+        // four elements at a time: their read-modify-writes overlap, and the
+        // next transition's momenta and gradients stay in registers
 #pragma unroll 1
-        for (int i0 = 0; i0 < kHalf; i0 += 8) {
-          int64_t e[8];
-          float v[8];
+        for (int i0 = 0; i0 < kHalf; i0 += 4) {
+          int64_t e[4];
+          float v[4];
           uint32_t vmask = 0u;
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
+          for (int k = 0; k < 4; ++k) {
             const int i = i0 + k;
             e[k] = elem(i);
             v[k] = xrow(i);
             if (valid(i)) vmask |= 1u << k;
           }
-          welford_update_n<8>(a.w, wq, k_out, e, v, vmask);
+          welford_update_n<4>(a.w, wq, k_out, e, v, vmask);
         }
       }
       // dual averaging over all chains of the posterior
@@ -802,7 +805,7 @@ unsigned gauss_pair_grid(int64_t C) {
 
 cudaError_t launch_gauss_pair_image(const float* Phi, const float* Plo, int D, float* image,
                                     cudaStream_t s) {
-  static_assert(kGaussPairImageFloats == 2 * kTmemChunks * 2 * 2 * 4 * 4 * 32 * 4, "image size");
+  static_assert(kGaussPairImageFloats == 2 * kHalfChunks * 2 * 4 * 4 * 32 * 4, "image size");
   k_tmem_image<<<static_cast<unsigned>(kGaussPairImageFloats / 4 / 256), 256, 0, s>>>(Phi, Plo, D, image);
   count_launch();
   return cudaGetLastError();
