@@ -75,7 +75,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColAcc = 0;                   // accumulators: 128 columns
 constexpr uint32_t kColLoProduct = 32;            // the N = 64 product's column offset
 constexpr uint32_t kColP = 128;                   // P block h (head chunk h, then remainder chunk h - 8) at kColP + 32 h
-constexpr uint32_t kStageBytes = 4 * kBChunk;     // 4 K-chunks (this CTA's 128 dims) x 32 chains
+constexpr uint32_t kXferBytes = 4 * kHalf * kRowBytes;   // float32 positions of 32 chains x 128 dims
 constexpr uint32_t kStateBytes = kPairChains * 128 * 4;   // current positions, this CTA's dims
 // barriers (8), tmem slot, red [3][4][64], red_pair [3][64], peer_in [3][64],
 // acc_flag [64], prob_s [64], DA state copy, flags, DA coefficients, pair
@@ -83,7 +83,7 @@ constexpr uint32_t kStateBytes = kPairChains * 128 * 4;   // current positions, 
 // exchange flags [64], log u [64], current log p [64]
 constexpr uint32_t kSmall =
     8 * 8 + 16 + (3 * 4 * 64 + 3 * 64 + 3 * 64 + 64 + 64) * 4 + 128 + 16 + 32 + 16 + 5 * 64 * 4;
-constexpr size_t kSmemUsed = kBBytes + kABytes + kStageBytes + kStateBytes + kSmall + 1024;
+constexpr size_t kSmemUsed = kBBytes + kABytes + 2 * kXferBytes + kStateBytes + kSmall + 1024;
 // Above half of an SM's shared memory, so that one CTA runs per SM: a CTA
 // allocates all 512 tensor-memory columns and must never queue in
 // tcgen05.alloc behind another CTA of the launch.
@@ -193,16 +193,18 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   uint8_t* Bt = smem;                                      // positions: [8 K-chunks][head 32 rows, remainder 32 rows]
   uint8_t* As = Bt + kBBytes;                              // P remainder chunks 4-7
-  uint8_t* Stg = As + kABytes;                             // staging, laid out as 4 K-chunks of Bt
-  float* xs = reinterpret_cast<float*>(Stg + kStageBytes); // [64 chains][128 dims] current position
+  uint8_t* Stg = As + kABytes;                             // outgoing float32 positions [4][32 rows][32 dims]
+  uint8_t* Rcv = Stg + kXferBytes;                         // incoming float32 positions, same layout
+  float* xs = reinterpret_cast<float*>(Rcv + kXferBytes);  // [64 chains][128 dims] current position
   uint64_t* a7_full = reinterpret_cast<uint64_t*>(xs + kPairChains * 128);
   uint64_t* acc_full = a7_full + 1;
   uint64_t* own_full = acc_full + 1;      // all epilogue threads: accumulators read, own K-chunks written
-  uint64_t* in_full = own_full + 1;       // this CTA's tile: the peer's K-chunks copied in
+  uint64_t* in_full = own_full + 1;       // the other CTA's float32 positions have landed in Rcv
   uint64_t* fwd_own = in_full + 1;        // leader: the peer's own_full, forwarded
-  uint64_t* fwd_in = fwd_own + 1;         // leader: the peer's in_full, forwarded
+  uint64_t* fwd_in = fwd_own + 1;         // leader: the peer's split_full, forwarded
   uint64_t* sums_in = fwd_in + 1;         // the other CTA's partial sums have landed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sums_in + 2);
+  uint64_t* split_full = sums_in + 1;     // all epilogue threads: the received positions split into the tile
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(split_full + 1);
   float* red = reinterpret_cast<float*>(tmem_slot + 4);   // [3 sums][4 quarters][64 chains]
   float* red_pair = red + 3 * 4 * 64;                     // [3][64] this CTA's sums
   float* peer_in = red_pair + 3 * 64;                     // [3][64] the other CTA's sums
@@ -232,10 +234,11 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     ptx::mbar_init(a7_full, 1);
     ptx::mbar_init(acc_full, 1);
     ptx::mbar_init(own_full, 256);        // every epilogue thread
-    ptx::mbar_init(in_full, 1);           // armed with the copy bytes by one own-chain thread
+    ptx::mbar_init(in_full, 1);           // armed with the copy bytes by one epilogue thread
+    ptx::mbar_init(split_full, 256);      // every epilogue thread
     ptx::mbar_init(fwd_own, 1);
     ptx::mbar_init(fwd_in, 1);
-    ptx::mbar_init(sums_in, kPairChains);  // the other CTA's 64 summing threads
+    ptx::mbar_init(sums_in, 1);            // armed each transition with the other CTA's 768 bytes
     ptx::fence_mbar_init();
     ptx::prefetch_tensormap(&mPhi);
     ptx::prefetch_tensormap(&mPlo);
@@ -251,7 +254,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   // position tile and staging start zeroed: dims >= D and chains >= C are never written
   for (uint32_t i = threadIdx.x; i < kBBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(Bt)[i] = make_uint4(0u, 0u, 0u, 0u);
-  for (uint32_t i = threadIdx.x; i < kStageBytes / 16; i += kThreads)
+  for (uint32_t i = threadIdx.x; i < kXferBytes / 16; i += kThreads)
     reinterpret_cast<uint4*>(Stg)[i] = make_uint4(0u, 0u, 0u, 0u);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   ptx::tc_fence_before();
@@ -321,19 +324,20 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       for (int s = 0; s < T * L && ok; ++s) {
         const uint32_t ph = s & 1;
         bool first = true;
-        // K-chunks 4-7: leader half copied in from the peer, peer half local
-        // there; own_full and fwd_own also mean both CTAs' epilogues have
-        // read the accumulators this step overwrites
-        if (!ptx::mbar_wait(own_full, ph) || !ptx::mbar_wait(in_full, ph) ||
-            !ptx::mbar_wait_cluster(fwd_own, ph)) {
+        // K-chunks 4-7: leader half received from the peer and split here,
+        // peer half local there; own_full and fwd_own also mean both CTAs'
+        // epilogues have read the accumulators this step overwrites
+        if (!ptx::mbar_wait(own_full, ph) || !ptx::mbar_wait(split_full, ph) ||
+            !ptx::mbar_wait(fwd_own, ph)) {
           atomicCAS(fa.err, 0, 2);
           ok = false;
           break;
         }
         ptx::tc_fence_after();
         for (int kc = 4; kc < nk; ++kc) chunk_mmas(kc, first);
-        // K-chunks 0-3: leader half local, peer half copied in from the leader
-        if (!ptx::mbar_wait_cluster(fwd_in, ph)) {
+        // K-chunks 0-3: leader half local, peer half received from the leader
+        // and split there
+        if (!ptx::mbar_wait(fwd_in, ph)) {
           atomicCAS(fa.err, 0, 3);
           ok = false;
           break;
@@ -352,31 +356,41 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
           atomicCAS(fa.err, 0, 5);
           break;
         }
-        ptx::mbar_arrive_cluster(own_leader);
-        if (!ptx::mbar_wait(in_full, ph)) {
+        ptx::mbar_arrive_remote(own_leader);
+        if (!ptx::mbar_wait(split_full, ph)) {
           atomicCAS(fa.err, 0, 6);
           break;
         }
-        ptx::mbar_arrive_cluster(in_leader);
+        ptx::mbar_arrive_remote(in_leader);
       }
     }
   } else {
     // ---- epilogue, both CTAs
     // Element i (0..31) of this thread is dim d of pair row rowi(i): the
-    // first 16 are 16 of the peer's chains, written to staging and pushed to
-    // the peer as soon as they are done; the last 16 are 16 of this CTA's
-    // own chains, written straight into its tile.  Each step's copy thus
-    // starts after half of the epilogue, and the other half overlaps it.
+    // first 16 are 16 of the peer's chains, whose float32 positions are
+    // staged and pushed to the peer as soon as they are done; the last 16
+    // are 16 of this CTA's own chains, split into head and remainder and
+    // written straight into its tile.  Each step's copy thus starts after
+    // half of the epilogue, and the other half overlaps it; the receiving
+    // CTA splits the positions it gets into its own tile.  (Sending float32
+    // instead of head and remainder halves the bytes crossing the pair:
+    // 32 KB took about 0.9 us.)
     auto rowi = [&](int i) {
       return static_cast<int>(i < 16 ? peer : rank) * kHalf + sub * 16 + (i & 15);
     };
-    // Destinations, laid out as the K-chunks of the tile (1024-byte aligned
-    // on both sides, so the swizzle carries over): staging chunk `quarter` is
-    // the peer's K-chunk 4 rank + quarter.  Head row r of a chunk sits at
-    // (r / 8) * 1024 + sw[r % 8] from the column's base (d and dl agree mod
-    // 32), its remainder kLoOff further.
-    const uint32_t st_hi0 = ptx::smem_u32(Stg) + static_cast<uint32_t>((dl >> 5) * kBChunk + (dl & 3) * 4);
+    // Tile addresses: head row r of K-chunk kc, column c, sits at
+    // kc * kBChunk + (r / 8) * 1024 + sw[r % 8] + (c % 4) * 4 (the 128-byte
+    // swizzle; sw depends on c / 4, and c = lane), its remainder kLoOff
+    // further.
     const uint32_t own_hi0 = ptx::smem_u32(Bt) + static_cast<uint32_t>((d >> 5) * kBChunk + (d & 3) * 4);
+    // the received positions of quarter q (the other CTA's dims) go to K-chunk 4 peer + q
+    const uint32_t rcv_hi0 =
+        ptx::smem_u32(Bt) + static_cast<uint32_t>((4 * static_cast<int>(peer) + quarter) * kBChunk + (lane & 3) * 4);
+    // float32 transfer buffers: [quarter][row 0..31][lane], 128 B per row;
+    // this thread's rows are 16 sub .. 16 sub + 15
+    const uint32_t xfer_off = static_cast<uint32_t>(((quarter * kHalf + sub * 16) * 32 + lane) * 4);
+    const uint32_t stg_a = ptx::smem_u32(Stg) + xfer_off;
+    const uint32_t rcv_a = ptx::smem_u32(Rcv) + xfer_off;
     uint32_t sw[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) sw[r] = r * kRowBytes + (((((dl & 31) >> 2) ^ r) & 7) << 4);
@@ -386,31 +400,33 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     auto xrow = [&](int i) -> float& { return xs[rowi(i) * 128 + dl]; };
     // element index of (pair row of element i, dim d) in the [C x D] arrays
     auto elem = [&](int i) { return static_cast<int64_t>(pair_base + rowi(i)) * D + d; };
-    auto store_x = [&](int i, float xi) {   // position of element i, split, into staging / tile
+    // position of element i: the peer's chains as float32 into staging,
+    // this CTA's own split into its tile
+    auto store_x = [&](int i, float xi) {
       if (valid(i)) {
         if (TEMPERED) xi *= beta_s[rowi(i)];
-        float hi, lo;
-        split_tf32(xi, hi, lo);
-        const int r = sub * 16 + (i & 15);
-        const uint32_t a0 = (i < 16 ? st_hi0 : own_hi0) + (r >> 3) * 1024 + sw[r & 7];
-        asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0), "f"(hi) : "memory");
-        asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0 + kLoOff), "f"(lo) : "memory");
+        if (i < 16) {
+          asm volatile("st.shared.f32 [%0], %1;" ::"r"(stg_a + i * kRowBytes), "f"(xi) : "memory");
+        } else {
+          float hi, lo;
+          split_tf32(xi, hi, lo);
+          const int r = sub * 16 + (i & 15);
+          const uint32_t a0 = own_hi0 + (r >> 3) * 1024 + sw[r & 7];
+          asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0), "f"(hi) : "memory");
+          asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0 + kLoOff), "f"(lo) : "memory");
+        }
       }
     };
-    // The peer's half is written: the warp pushes its 16 rows of staging
-    // chunk `quarter` (head and remainder, 2 KB each) to the peer's tile,
-    // completing on the peer's in_full.
+    // The peer's half is written: the warp pushes its 16 staged rows (2 KB
+    // of float32 positions) to the peer's receive buffer, completing on the
+    // peer's in_full.
     auto publish_stage = [&]() {
       proxy_fence_cta();          // generic stores -> async proxy (bulk copy)
       __syncwarp();
       if (lane == 0) {
-        const uint32_t bar = ptx::mapa(ptx::smem_u32(in_full), peer);
-        const uint32_t rows = static_cast<uint32_t>(sub) * 16 * kRowBytes;
-        const uint32_t chunk = (4 * rank + quarter) * kBChunk + rows;
-        uint8_t* sb = Stg + quarter * kBChunk + rows;
-        ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Bt + chunk), peer), sb, 16 * kRowBytes, bar);
-        ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Bt + chunk + kLoOff), peer), sb + kLoOff,
-                                  16 * kRowBytes, bar);
+        const uint32_t off = static_cast<uint32_t>(quarter * kHalf + sub * 16) * kRowBytes;
+        ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Rcv + off), peer), Stg + off, 16 * kRowBytes,
+                                  ptx::mapa(ptx::smem_u32(in_full), peer));
       }
     };
     // The own half is written: every thread arrives on own_full once its
@@ -419,7 +435,36 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       proxy_fence_cta();          // generic stores -> async proxy (MMA)
       ptx::tc_fence_before();     // this thread's accumulator reads precede the next MMA
       ptx::mbar_arrive_local(own_full);
-      if (ew == 0 && lane == 0) ptx::mbar_arrive_expect_tx(in_full, kStageBytes);
+      if (ew == 0 && lane == 0) ptx::mbar_arrive_expect_tx(in_full, kXferBytes);
+    };
+    // Write s of the tile (s = 0, 1, ...): once the other CTA's positions
+    // have landed, this thread splits 16 of them (rows 16 sub .. 16 sub + 15
+    // of this CTA's chains, dim 128 peer + 32 quarter + lane) into the tile,
+    // eight at a time, and joins split_full.  Rows and dims with nothing to
+    // send arrive as zeros.
+    auto split_received = [&](int s) {
+      if (!ptx::mbar_wait(in_full, s & 1)) {
+        atomicCAS(fa.err, 0, 10);
+        ok = false;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v[k]) : "r"(rcv_a + (8 * h + k) * kRowBytes) : "memory");
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          float hi, lo;
+          split_tf32(v[k], hi, lo);
+          const int r = sub * 16 + 8 * h + k;
+          const uint32_t a0 = rcv_hi0 + (r >> 3) * 1024 + sw[k];
+          asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0), "f"(hi) : "memory");
+          asm volatile("st.shared.f32 [%0], %1;" ::"r"(a0 + kLoOff), "f"(lo) : "memory");
+        }
+      }
+      proxy_fence_cta();
+      ptx::mbar_arrive_local(split_full);
     };
     // The gradient of elements 16 cb .. 16 cb + 15 is minus the sum of their
     // two accumulator columns: (CTA q, row r) -> column 64 q + r and 64 q + r + 32.
@@ -496,16 +541,21 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         for (int i = 0; i < kHalf; ++i) v[i] = x[i] * x[i];
         red[(2 * 4 + quarter) * 64 + rowi(lane)] = transpose_reduce32(v, lane);
       }
-      // begin: p = p0 + eps/2 g0, x1 = x0 + eps p (the peer's half first)
+      // begin: p = p0 + eps/2 g0, x1 = x0 + eps p (the peer's half first);
+      // every position is loaded before the first tile store, whose memory
+      // clobber would otherwise serialise the loads
+#pragma unroll
+      for (int i = 0; i < kHalf; ++i) p[i] = fmaf(0.5f * eps, p[i], x[i]);
+#pragma unroll
+      for (int i = 0; i < kHalf; ++i) x[i] = xrow(i);
 #pragma unroll
       for (int i = 0; i < kHalf; ++i) {
-        const float pn = fmaf(0.5f * eps, p[i], x[i]);
-        p[i] = pn;
-        x[i] = fmaf(eps, pn, xrow(i));
+        x[i] = fmaf(eps, p[i], x[i]);
         store_x(i, x[i]);
         if (i == 15) publish_stage();
       }
       publish_own();
+      split_received(j * L);
       // the accept test's log u, off the critical path
       if (c < kPairChains && pair_base + c < C)
         lu_s[c] = accept_log_uniform(a.seed, static_cast<uint32_t>(pair_base + c) + a.chain_offset, t);
@@ -528,6 +578,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
           if (cb == 0) publish_stage();
         }
         publish_own();
+        split_received(s0 + l);
       }
       // step L: final half kick; <x, g> and |p|^2 partials
       if (more) draw_next(min(kHalf, (L - 1) * per_wait), kHalf, t + 1);
@@ -558,24 +609,26 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       }
       epi_barrier();
       // Only the epilogue warps run this loop, so the two CTAs meet on an
-      // mbarrier: each sends its partial sums to the other (sums_in), and
-      // both decide every chain of the pair from the same two partials (a + b
-      // equals b + a in float32, so the decisions agree bit for bit); the
-      // leader writes the kernel results.
+      // mbarrier: each sends its partial sums to the other by asynchronous
+      // stores that complete on the other's sums_in, and both decide every
+      // chain of the pair from the same two partials (a + b equals b + a in
+      // float32, so the decisions agree bit for bit); the leader writes the
+      // kernel results.
       if (c < kPairChains) {
+        const uint32_t bar = ptx::mapa(ptx::smem_u32(sums_in), peer);
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
           float sum = 0.f;
           for (int q = 0; q < 4; ++q) sum += red[(v * 4 + q) * 64 + c];
           red_pair[v * 64 + c] = sum;
-          ptx::st_cluster_f32(ptx::mapa(ptx::smem_u32(&peer_in[v * 64 + c]), peer), sum);
+          ptx::st_async_f32(ptx::mapa(ptx::smem_u32(&peer_in[v * 64 + c]), peer), sum, bar);
         }
-        ptx::mbar_arrive_cluster(ptx::mapa(ptx::smem_u32(sums_in), peer));
       }
       const long long t_full = a.t_full + j;
       const long long k_out = t_full - fa.keep_from;
       if (c < kPairChains) {
-        if (!ptx::mbar_wait_cluster(sums_in, j & 1)) {
+        if (c == 0) ptx::mbar_arrive_expect_tx(sums_in, 3 * kPairChains * 4);
+        if (!ptx::mbar_wait(sums_in, j & 1)) {
           atomicCAS(fa.err, 0, 8);
           ok = false;
         }
@@ -641,6 +694,9 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         }
         if (lead && blockIdx.x == 0 && c == 0 && k_out >= 0 && fa.trace_eps && ok) fa.trace_eps[k_out] = eps;
       }
+      // the previous kept sample's bulk stores have read the positions
+      // (warp 2 issues them) before anything below writes them
+      if (warp == 2) ptx::bulk_wait_read();
       // decisions visible to every epilogue thread
       epi_barrier();
       // the accepted state (gradient from the accumulators) and the kept sample
@@ -648,6 +704,19 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       // streaming driver: running moments of the kept states instead of a trace
       const bool moments = k_out >= 0 && a.w.mean != nullptr;
       const WelfordCoef wq = welford_coef(k_out > 0 ? k_out : 0, a.w.bsize);
+      // The decisions of this thread's 32 rows first, then only stores:
+      // shared-memory loads between the (possibly aliasing) global stores
+      // would each wait for the previous one.  The accepted positions go
+      // first, and (when a sample is kept) the proxy fence that hands them
+      // to the bulk trace copy comes before the gradient stores: a fence
+      // waits for this thread's global stores in flight.
+      uint32_t accm = 0u;
+#pragma unroll
+      for (int i = 0; i < kHalf; ++i) accm |= (acc_flag[rowi(i)] != 0 ? 1u : 0u) << i;
+#pragma unroll
+      for (int i = 0; i < kHalf; ++i)
+        if (ok && valid(i) && ((accm >> i) & 1u)) xrow(i) = x[i];
+      if (samp && !(TEMPERED && fa.exchange)) proxy_fence_cta();
 #pragma unroll
       for (int cb = 0; cb < kHalf / 16; ++cb) {
         float accv[16];
@@ -655,24 +724,10 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const int i = cb * 16 + k;
-          if (ok && valid(i)) {
-            if (acc_flag[rowi(i)]) {
-              xrow(i) = x[i];
-              a.g[elem(i)] = -accv[k];
-              p[i] = -accv[k];
-            }
-            if (samp && !(TEMPERED && fa.exchange)) samp[elem(i)] = xrow(i);
+          if (ok && valid(i) && ((accm >> i) & 1u)) {
+            a.g[elem(i)] = -accv[k];
+            p[i] = -accv[k];
           }
-        }
-        // the next transition's momenta (drawn during this one's steps) for
-        // these 16 elements, loaded only once their positions are spent (the
-        // empty asm keeps the compiler from hoisting the loads, which would
-        // keep both sets of 16 live at once)
-        asm volatile("" ::: "memory");
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const int i = cb * 16 + k;
-          x[i] = more && valid(i) ? fa.p0next[elem(i)] : 0.f;
         }
       }
       if (TEMPERED && fa.exchange) {
@@ -695,17 +750,47 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
             g0[D] = ga / b0 * b1;
           }
         }
-        epi_barrier();
-        if (samp) {
-#pragma unroll
-          for (int i = 0; i < kHalf; ++i)
-            if (ok && valid(i)) samp[elem(i)] = xrow(i);
-        }
         // swapped rows took new cached gradients
         if (more) {
 #pragma unroll
           for (int i = 0; i < kHalf; ++i) p[i] = valid(i) ? a.g[elem(i)] : 0.f;
         }
+      }
+      // The kept sample: this CTA's positions (64 rows of its dims) are
+      // complete in shared memory, and warp 2 streams them to the trace by
+      // bulk copies, 512 bytes per chain row (waited for before the next
+      // transition writes the rows).
+      if (samp) {
+        if (TEMPERED && fa.exchange) proxy_fence_cta();    // the swapped rows
+        epi_barrier();
+        const int ndim = min(128, D - static_cast<int>(rank) * 128);
+        if ((reinterpret_cast<uintptr_t>(samp) & 15u) == 0) {
+          if (warp == 2 && ok && ndim > 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int r = lane + 32 * h;
+              if (pair_base + r < C)
+                ptx::bulk_store_global(samp + static_cast<int64_t>(pair_base + r) * D + static_cast<int>(rank) * 128,
+                                       ptx::smem_u32(xs + r * 128), static_cast<uint32_t>(ndim) * 4u);
+            }
+            ptx::bulk_commit();
+          }
+        } else if (ok && ndim > 0) {
+          // a trace pointer without 16-byte alignment: coalesced plain stores
+          for (int e = ew * 32 + lane; e < kPairChains * ndim; e += 256) {
+            const int r = e / ndim, cidx = e - r * ndim;
+            if (pair_base + r < C)
+              samp[static_cast<int64_t>(pair_base + r) * D + static_cast<int>(rank) * 128 + cidx] = xs[r * 128 + cidx];
+          }
+        }
+      }
+      // the next transition's momenta (drawn during this one's steps), loaded
+      // once the positions are spent and after the proxy fence above (a fence
+      // waits for the loads in flight)
+      if (more) {
+        asm volatile("" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < kHalf; ++i) x[i] = valid(i) ? fa.p0next[elem(i)] : 0.f;
       }
       if (moments && ok) {
         // four elements at a time: their read-modify-writes overlap, and the
@@ -781,6 +866,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     for (int i = 0; i < kHalf; ++i)
       if (ok && valid(i)) a.x[elem(i)] = xrow(i);
     if (persistent && blockIdx.x == 0 && threadIdx.x == 64 && !*abort_s) *a.da = *da_s;
+    if (warp == 2) ptx::bulk_wait_all();      // the kept samples' bulk stores are done
   }
   // every copy into this CTA's tile has landed (immediate unless a wait gave up)
   if (warp == 1 && lane == 0) ptx::mbar_wait(in_full, (T * L - 1) & 1);

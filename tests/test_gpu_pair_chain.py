@@ -75,3 +75,29 @@ def test_launch_cap_splits_the_chain_without_changing_it(H, cap):
     assert whole.adaptation() == split.adaptation()
     whole.close()
     split.close()
+
+
+def test_trace_without_16_byte_alignment_matches(H):
+    """The pair kernel streams kept samples to the trace by bulk copies,
+    which need a 16-byte-aligned destination; a trace that starts one float
+    into a buffer takes the kernel's plain-store path and must hold the same
+    samples, bit for bit."""
+    from paper_2002_01184_gb300 import workloads
+    from paper_2002_01184_gb300.sampler import Sampler
+    C, D, L, B, K = 160, 132, 4, 3, 3
+    p = workloads.corr_gauss(dim=D, num_chains=C, num_burnin=B, num_results=K, num_leapfrog=L)
+    x0 = torch.as_tensor(p.x0).cuda().contiguous()
+    s = Sampler(p, adapt=True)
+    aligned = torch.empty((K, C, D), device="cuda")
+    x1 = x0.clone()
+    H.hmc_sample_chain(s.ctx, x1, B, K, aligned, None, None)
+    buf = torch.zeros(K * C * D + 1, device="cuda")
+    offset = buf[1:]
+    assert offset.data_ptr() % 16 == 4
+    x2 = x0.clone()
+    H.hmc_sample_chain(s.ctx, x2, B, K, offset, None, None)
+    H.hmc_synchronize(s.ctx)
+    assert torch.equal(x1, x2)
+    assert torch.equal(offset.view(K, C, D), aligned)
+    assert H.hmc_dominant_kernel_info(s.ctx)[0] == "k_gauss_pair"
+    s.close()
