@@ -221,6 +221,51 @@ hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burni
                                  int64_t num_results, float* samples_out,
                                  float* trace_step_size, uint8_t* trace_accept);
 
+/* sample_chain in pieces (Section 4.2's driver, split for checkpointing):
+ * run transitions t_begin .. t_end - 1 of a chain with num_burnin burn-in
+ * transitions, so that consecutive calls [0, k), [k, n) give exactly the
+ * chain of one hmc_sample_chain(num_burnin, n - num_burnin) call.  With
+ * t_begin == 0 the chain is bootstrapped at x_inout; otherwise x_inout
+ * (device) and the context's kernel results and adaptation state must hold
+ * the state after transition t_begin - 1 (left there by the previous call,
+ * or put there by hmc_restore_state: HMC_E_INVALID if neither happened).
+ * Kept transitions t >= num_burnin write output index
+ * t - max(num_burnin, t_begin) of samples_out [.. x chains x dim],
+ * trace_step_size and trace_accept (device, each may be NULL).  No CUDA
+ * graph is captured. */
+hmc_status hmc_sample_chain_range(hmc_ctx* ctx, float* x_inout, int64_t num_burnin, int64_t t_begin,
+                                  int64_t t_end, float* samples_out, float* trace_step_size,
+                                  uint8_t* trace_accept);
+
+/* Checkpoint and resume (no counterpart in the paper; the paper's kernels
+ * are pure functions of (state, kernel results), Section 4.1, which is what
+ * makes this possible).  A context's resumable state is its kernel results
+ * (the cached log p [chains] and gradient [chains x dim] of the current
+ * state) and its dual-averaging state; the chain state itself is the
+ * caller's x.
+ *   hmc_state_bytes: size of that state in bytes.
+ *   hmc_save_state: copy it to host memory `out` (at least that many bytes)
+ *     after the context's pending work; synchronises; HMC_E_TIMEOUT if a
+ *     device-side wait gave up.
+ *   hmc_restore_state: load it into a context created with the same target
+ *     (family and dim), chain count, replica count and configuration --
+ *     typically a fresh one in another process -- after which
+ *     hmc_sample_chain_range / hmc_step continue the saved chain bit for bit;
+ *     HMC_E_INVALID if the saved state belongs to another target, chain count
+ *     or build.  Synchronous. */
+hmc_status hmc_state_bytes(const hmc_ctx* ctx, uint64_t* bytes);
+hmc_status hmc_save_state(hmc_ctx* ctx, void* out, uint64_t bytes);
+hmc_status hmc_restore_state(hmc_ctx* ctx, const void* in, uint64_t bytes);
+
+/* Test support (no counterpart in the paper): for every later launch of the
+ * dense-Gaussian CTA-pair kernel, the time after which its grid barrier (the
+ * dual-averaging meeting point of a multi-transition launch) gives up, in
+ * nanoseconds (default 500000000), and a barrier generation (1, 2, ...; 0:
+ * none) that can never complete, so that a test can make the bounded wait
+ * run out: the kernel then skips its remaining transitions and returns, and
+ * hmc_synchronize reports HMC_E_TIMEOUT.  Process-wide. */
+void hmc_debug_set_grid_barrier(uint64_t wait_limit_ns, int32_t unreachable_generation);
+
 /* Copy the current dual-averaging state to host memory and synchronise:
  * out[0] = step size of the next transition, out[1] = log eps_bar,
  * out[2] = h_bar, out[3] = adaptation steps taken, out[4] = last transition's

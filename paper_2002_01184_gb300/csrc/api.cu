@@ -289,9 +289,10 @@ hmc_status bootstrap(hmc_ctx* ctx, const float* x0) {
 }
 
 // Transitions t_begin .. t_end - 1 of a chain with B burn-in transitions
-// (transition B + k writes kept sample k), after the bootstrap.
+// (transition B + k writes kept sample k - out0 of the output buffers), after
+// the bootstrap.
 hmc_status enqueue_range(hmc_ctx* ctx, float* x, int64_t B, int64_t t_begin, int64_t t_end,
-                         float* samples, float* trace_eps, uint8_t* trace_acc) {
+                         float* samples, float* trace_eps, uint8_t* trace_acc, int64_t out0 = 0) {
   const int64_t CD = ctx->C * ctx->target.dim;
   // dense Gaussian on CTA pairs: the chain's transitions in as few launches
   // as allowed (all of them in one cooperative launch by default)
@@ -312,7 +313,7 @@ hmc_status enqueue_range(hmc_ctx* ctx, float* x, int64_t B, int64_t t_begin, int
       StepArgs a = make_args(ctx, x, static_cast<uint64_t>(t0));
       if (ctx->s_mean)
         a.w = hmc::WelfordOut{ctx->s_mean, ctx->s_m2, ctx->s_bsize, ctx->bm_sum, ctx->bm_mean, ctx->bm_m2};
-      cudaError_t e = hmc::launch_gauss_pair_transitions(a, ctx->tc, n, B, samples, trace_eps, trace_acc,
+      cudaError_t e = hmc::launch_gauss_pair_transitions(a, ctx->tc, n, B + out0, samples, trace_eps, trace_acc,
                                                          ctx->grid_bar, ctx->stream, &ctx->timer,
                                                          pair_remc ? ctx->swapped : nullptr);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "pair transition launch");
@@ -329,8 +330,8 @@ hmc_status enqueue_range(hmc_ctx* ctx, float* x, int64_t B, int64_t t_begin, int
         t_end, std::max<int64_t>(t_begin, ctx->cfg.adapt ? ctx->cfg.num_adapt_steps : 0));
   for (int64_t t = t_begin; t < t_multi; ++t) {
     StepArgs a = make_args(ctx, x, static_cast<uint64_t>(t));
-    const int64_t k = t - B;
-    if (k >= 0) {
+    const int64_t k = t - B - out0;
+    if (t - B >= 0) {
       a.sample_out = samples && ctx->K == 1 ? samples + k * CD : nullptr;
       a.trace_acc = trace_acc ? trace_acc + k * ctx->C : nullptr;
       a.trace_eps = trace_eps ? trace_eps + k : nullptr;
@@ -356,7 +357,7 @@ hmc_status enqueue_range(hmc_ctx* ctx, float* x, int64_t B, int64_t t_begin, int
     const int n = static_cast<int>(std::min(chunk, t_end - t0));
     StepArgs a = make_args(ctx, x, static_cast<uint64_t>(t0));
     cudaError_t e = hmc::launch_nuts_transitions(ctx->target, a, ctx->nuts_scratch, ctx->cfg.num_leapfrog,
-                                                 ctx->nuts_leaves, n, B, samples, trace_eps, trace_acc,
+                                                 ctx->nuts_leaves, n, B + out0, samples, trace_eps, trace_acc,
                                                  ctx->stream, &ctx->timer);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "NUTS transition launch");
   }
@@ -794,6 +795,91 @@ hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burni
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "result download");
   return check_device_flag(ctx);
+}
+
+hmc_status hmc_sample_chain_range(hmc_ctx* ctx, float* x_inout, int64_t num_burnin, int64_t t_begin,
+                                  int64_t t_end, float* samples_out, float* trace_step_size,
+                                  uint8_t* trace_accept) {
+  if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
+  if (!x_inout) return fail(ctx, HMC_E_INVALID, "x_inout is NULL");
+  if (num_burnin < 0 || t_begin < 0 || t_end < t_begin)
+    return fail(ctx, HMC_E_INVALID, "need num_burnin >= 0 and 0 <= t_begin <= t_end");
+  if (t_end > static_cast<int64_t>(std::numeric_limits<uint32_t>::max()))
+    return fail(ctx, HMC_E_INVALID, "too many transitions (transition index is 32-bit)");
+  if (t_begin > 0 && !ctx->bootstrapped)
+    return fail(ctx, HMC_E_INVALID, "a range that does not start at 0 needs the previous state (hmc_restore_state)");
+  if (t_begin == 0) {
+    hmc_status st = bootstrap(ctx, x_inout);
+    if (st != HMC_OK) return st;
+  }
+  return enqueue_range(ctx, x_inout, num_burnin, t_begin, t_end, samples_out, trace_step_size, trace_accept,
+                       std::max<int64_t>(0, t_begin - num_burnin));
+}
+
+namespace {
+// Layout of a saved context state: a header, the dual-averaging state, the
+// cached log p [rows] and gradient [rows x dim] (rows = chains x replicas).
+struct SavedHeader {
+  uint64_t magic;
+  int64_t rows;
+  int32_t dim, target, replicas, da_bytes;
+};
+constexpr uint64_t kStateMagic = 0x31544154534d4348ull;   // "HCMSTAT1"
+size_t state_bytes(const hmc_ctx* ctx) {
+  return sizeof(SavedHeader) + sizeof(DAState) + sizeof(float) * static_cast<size_t>(ctx->C) +
+         sizeof(float) * static_cast<size_t>(ctx->C) * ctx->target.dim;
+}
+}  // namespace
+
+hmc_status hmc_state_bytes(const hmc_ctx* ctx, uint64_t* bytes) {
+  if (!ctx || !bytes) return fail(nullptr, HMC_E_INVALID, "NULL argument");
+  *bytes = state_bytes(ctx);
+  return HMC_OK;
+}
+
+hmc_status hmc_save_state(hmc_ctx* ctx, void* out, uint64_t bytes) {
+  if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
+  if (!out || bytes < state_bytes(ctx)) return fail(ctx, HMC_E_INVALID, "out is NULL or smaller than hmc_state_bytes");
+  if (!ctx->bootstrapped) return fail(ctx, HMC_E_INVALID, "nothing to save before hmc_bootstrap");
+  char* base = static_cast<char*>(out);
+  SavedHeader h{kStateMagic, ctx->C, ctx->target.dim, ctx->target.id, ctx->K, static_cast<int32_t>(sizeof(DAState))};
+  std::memcpy(base, &h, sizeof(h));
+  char* p = base + sizeof(h);
+  cudaError_t e = cudaMemcpyAsync(p, ctx->da, sizeof(DAState), cudaMemcpyDeviceToHost, ctx->stream);
+  p += sizeof(DAState);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p, ctx->lp, sizeof(float) * ctx->C, cudaMemcpyDeviceToHost, ctx->stream);
+  p += sizeof(float) * ctx->C;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p, ctx->g, sizeof(float) * ctx->C * ctx->target.dim, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "save state");
+  return check_device_flag(ctx);
+}
+
+hmc_status hmc_restore_state(hmc_ctx* ctx, const void* in, uint64_t bytes) {
+  if (!ctx) return fail(nullptr, HMC_E_INVALID, "ctx is NULL");
+  if (!in || bytes < state_bytes(ctx)) return fail(ctx, HMC_E_INVALID, "in is NULL or smaller than hmc_state_bytes");
+  const char* base = static_cast<const char*>(in);
+  SavedHeader h;
+  std::memcpy(&h, base, sizeof(h));
+  if (h.magic != kStateMagic || h.rows != ctx->C || h.dim != ctx->target.dim || h.target != ctx->target.id ||
+      h.replicas != ctx->K || h.da_bytes != static_cast<int32_t>(sizeof(DAState)))
+    return fail(ctx, HMC_E_INVALID, "the saved state belongs to another target, chain count or build");
+  const char* p = base + sizeof(h);
+  // the transfers are synchronous: the caller's buffer may be released on return
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->da, p, sizeof(DAState), cudaMemcpyHostToDevice);
+  p += sizeof(DAState);
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->lp, p, sizeof(float) * ctx->C, cudaMemcpyHostToDevice);
+  p += sizeof(float) * ctx->C;
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->g, p, sizeof(float) * ctx->C * ctx->target.dim, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "restore state");
+  ctx->bootstrapped = true;
+  return HMC_OK;
+}
+
+void hmc_debug_set_grid_barrier(uint64_t wait_limit_ns, int32_t unreachable_generation) {
+  hmc::set_grid_barrier_debug(static_cast<unsigned long long>(wait_limit_ns), unreachable_generation);
 }
 
 hmc_status hmc_read_adaptation(hmc_ctx* ctx, double out[5]) {

@@ -48,6 +48,7 @@
 // transition instead lets its last CTA update the state.
 #include <cuda.h>
 
+#include <atomic>
 #include <cmath>
 
 #include "hmc_device.cuh"
@@ -104,6 +105,8 @@ struct PairArgs {
   unsigned* grid_bar;   // T > 1: grid barrier counter, zero at launch; null: one transition
   uint8_t* swapped;     // exchange: [outer chains x (K - 1)] swap flags of the last transition
   int exchange;         // replica sets (K | 64): the exchange step after every transition
+  unsigned long long grid_wait_ns;   // time after which the grid barrier gives up
+  int unreachable_gen;  // > 0: this grid-barrier generation can never complete (tests)
 };
 
 // Index of element e of float4 j of lane `lane` in the tensor-memory image:
@@ -160,14 +163,16 @@ __device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane) {
 
 // Grid barrier of a cooperative launch: generation `gen` (1, 2, ...) is
 // complete when every CTA has arrived `gen` times.  Bounded: false after
-// the wait limit.
-__device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned gen) {
+// `limit_ns`.  Generation `unreachable` (tests of the give-up path) waits for
+// one arrival more than there are CTAs, so it never completes.
+__device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned gen, unsigned long long limit_ns,
+                                             int unreachable) {
   __threadfence();
   atomicAdd(counter, 1u);
-  const unsigned target = gen * gridDim.x;
+  const unsigned target = gen * gridDim.x + (static_cast<int>(gen) == unreachable ? 1u : 0u);
   const unsigned long long t0 = ptx::global_timer_ns();
   while (*reinterpret_cast<volatile unsigned*>(counter) < target) {
-    if (ptx::global_timer_ns() - t0 > ptx::kWaitLimitNs) return false;
+    if (ptx::global_timer_ns() - t0 > limit_ns) return false;
   }
   __threadfence();
   return true;
@@ -829,7 +834,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
             v = warp_sum_d(v);
             if (lane == 0) {
               part[blockIdx.x] = v;
-              if (!grid_barrier(fa.grid_bar, static_cast<unsigned>(nbar))) {
+              if (!grid_barrier(fa.grid_bar, static_cast<unsigned>(nbar), fa.grid_wait_ns, fa.unreachable_gen)) {
                 atomicCAS(fa.err, 0, 7);
                 *abort_s = 1;
               }
@@ -884,6 +889,16 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 }
 
 }  // namespace
+
+// Test support: the grid barrier's wait limit and an unreachable generation
+// (set by hmc_debug_set_grid_barrier; read at every launch).
+std::atomic<unsigned long long> g_grid_wait_ns{ptx::kWaitLimitNs};
+std::atomic<int> g_unreachable_gen{0};
+
+void set_grid_barrier_debug(unsigned long long wait_ns, int unreachable_gen) {
+  g_grid_wait_ns.store(wait_ns);
+  g_unreachable_gen.store(unreachable_gen);
+}
 
 unsigned gauss_pair_grid(int64_t C) {
   return static_cast<unsigned>(2 * ((C + kPairChains - 1) / kPairChains));
@@ -940,7 +955,8 @@ cudaError_t launch_gauss_pair_transitions(const StepArgs& a, GaussTc& tc, int T,
                                           uint8_t* swapped) {
   if (swapped && (!a.betas || a.K < 2 || kPairChains % a.K != 0)) return cudaErrorInvalidValue;
   PairArgs fa{a, tc.err, tc.Ptm, tc.p, T, keep_from, samples, trace_eps, trace_acc,
-              T > 1 ? grid_bar : nullptr, swapped, swapped ? 1 : 0};
+              T > 1 ? grid_bar : nullptr, swapped, swapped ? 1 : 0, g_grid_wait_ns.load(),
+              g_unreachable_gen.load()};
   if (T > 1) {
     cudaError_t e = cudaMemsetAsync(grid_bar, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;

@@ -276,6 +276,9 @@ cudaError_t launch_gauss_pair_transitions(const StepArgs& a, GaussTc& tc, int T,
                                           float* samples, float* trace_eps, uint8_t* trace_acc,
                                           unsigned* grid_bar, cudaStream_t s, KernelTimer* timer,
                                           uint8_t* swapped = nullptr);
+// Test support: wait limit of the pair kernel's grid barrier and a
+// generation that can never complete (0: none), for every later launch.
+void set_grid_barrier_debug(unsigned long long wait_ns, int unreachable_gen);
 unsigned gauss_fused_grid(int64_t C);
 cudaError_t gauss_fused_setup();
 cudaError_t launch_gauss_fused_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,

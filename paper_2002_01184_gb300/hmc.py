@@ -70,6 +70,10 @@ def _load():
         "hmc_sample_chain": [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P],
         "hmc_sample_chain_host": [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P],
         "hmc_read_adaptation": [P, ctypes.POINTER(ctypes.c_double)],
+        "hmc_sample_chain_range": [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P, P, P],
+        "hmc_state_bytes": [P, ctypes.POINTER(ctypes.c_uint64)],
+        "hmc_save_state": [P, P, ctypes.c_uint64],
+        "hmc_restore_state": [P, P, ctypes.c_uint64],
         "hmc_destroy": [P],
         "hmc_grad_workspace_bytes": [ctypes.POINTER(hmc_target), ctypes.c_int64,
                                      ctypes.POINTER(ctypes.c_uint64)],
@@ -116,6 +120,8 @@ def _load():
     lib.hmc_batch_last_error.restype = ctypes.c_char_p
     lib.hmc_batch_context.argtypes = [P, ctypes.c_int32]
     lib.hmc_batch_context.restype = P
+    lib.hmc_debug_set_grid_barrier.argtypes = [ctypes.c_uint64, ctypes.c_int32]
+    lib.hmc_debug_set_grid_barrier.restype = None
     lib.hmc_kernel_launch_count.argtypes = []
     lib.hmc_kernel_launch_count.restype = ctypes.c_uint64
     return lib
@@ -212,6 +218,34 @@ def hmc_sample_chain(ctx, x_inout, num_burnin, num_results, samples_out=None,
                      trace_step_size=None, trace_accept=None):
     _check(lib.hmc_sample_chain(ctx, _ptr(x_inout), int(num_burnin), int(num_results),
                                 _ptr(samples_out), _ptr(trace_step_size), _ptr(trace_accept)), ctx)
+
+
+def hmc_sample_chain_range(ctx, x_inout, num_burnin, t_begin, t_end, samples_out=None,
+                           trace_step_size=None, trace_accept=None):
+    _check(lib.hmc_sample_chain_range(ctx, _ptr(x_inout), int(num_burnin), int(t_begin), int(t_end),
+                                      _ptr(samples_out), _ptr(trace_step_size), _ptr(trace_accept)), ctx)
+
+
+def hmc_state_bytes(ctx):
+    n = ctypes.c_uint64()
+    _check(lib.hmc_state_bytes(ctx, ctypes.byref(n)), ctx)
+    return int(n.value)
+
+
+def hmc_save_state(ctx):
+    """The context's resumable state as bytes (kernel results + adaptation)."""
+    buf = ctypes.create_string_buffer(hmc_state_bytes(ctx))
+    _check(lib.hmc_save_state(ctx, buf, len(buf)), ctx)
+    return buf.raw
+
+
+def hmc_restore_state(ctx, state):
+    buf = ctypes.create_string_buffer(bytes(state), len(state))
+    _check(lib.hmc_restore_state(ctx, buf, len(state)), ctx)
+
+
+def hmc_debug_set_grid_barrier(wait_limit_ns=500_000_000, unreachable_generation=0):
+    lib.hmc_debug_set_grid_barrier(int(wait_limit_ns), int(unreachable_generation))
 
 
 def hmc_sample_chain_host(ctx, x_inout, num_burnin, num_results, samples_out=None,

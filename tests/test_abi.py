@@ -24,7 +24,7 @@ def declared_functions():
     for fn in os.listdir(os.path.join(ROOT, "include")):
         if fn.endswith(".h"):
             text = open(os.path.join(ROOT, "include", fn)).read()
-            names |= set(re.findall(r"^\s*(?:hmc_status|const char\*|uint64_t|int32_t|hmc_ctx\*)\s+(hmc_\w+)\s*\(",
+            names |= set(re.findall(r"^\s*(?:hmc_status|const char\*|uint64_t|int32_t|hmc_ctx\*|void)\s+(hmc_\w+)\s*\(",
                                     text, re.M))
     return sorted(names)
 
