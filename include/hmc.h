@@ -153,6 +153,22 @@ typedef struct hmc_ctx hmc_ctx;
 hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_config* config,
                       void* cuda_stream, hmc_ctx** out);
 
+/* Device memory accounting (no counterpart in the paper; for admission by
+ * memory budget, as a sampling server does).
+ *   hmc_create_device_bytes: bytes hmc_create would request from the device
+ *     for these arguments (its workspace: kernel results, scratch of the
+ *     path the configuration selects), without creating anything; the
+ *     target's data pointers may be NULL.  HMC_E_INVALID on bad sizes or
+ *     configuration.
+ *   hmc_context_device_bytes: bytes a context holds now -- what
+ *     hmc_create allocated, plus what later calls added (the batch-means
+ *     buffers of hmc_sample_chain_streaming_ess, the staging buffers of
+ *     hmc_sample_chain_host).  Neither counts the caller's own buffers (state,
+ *     samples, target data). */
+hmc_status hmc_create_device_bytes(const hmc_target* target, int64_t num_chains, const hmc_config* config,
+                                   uint64_t* bytes);
+hmc_status hmc_context_device_bytes(const hmc_ctx* ctx, uint64_t* bytes);
+
 /* bootstrap_results (Section 4.1): evaluate log p and its gradient at x0
  * ([chains x dim], device, read only) into the context's kernel results and
  * reset the step size and the dual-averaging state to the configuration's. */

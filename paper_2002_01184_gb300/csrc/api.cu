@@ -42,6 +42,7 @@ struct hmc_ctx {
   cudaEvent_t seg_ready = nullptr;
   cudaEvent_t copies_done = nullptr;
   std::vector<void*> allocations;
+  uint64_t device_bytes = 0;    // bytes requested from the device allocator
   hmc::KernelTimer timer;
   bool use_tc = false;          // tensor-core Gaussian path
   hmc::GaussTc tc;
@@ -113,6 +114,29 @@ hmc_status cuda_fail(hmc_ctx* ctx, cudaError_t e, const char* where) {
   return fail(ctx, HMC_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// The target's family, sizes and chain count (not its data pointers).
+bool valid_target_shape(const hmc_target* t, int64_t C, std::string* why) {
+  if (!t) { *why = "target is NULL"; return false; }
+  if (t->dim < 1) { *why = "target dim must be >= 1"; return false; }
+  if (C < 1) { *why = "num_chains must be >= 1"; return false; }
+  if (C > (1ll << 30)) { *why = "num_chains must be <= 2^30"; return false; }
+  if (C * static_cast<int64_t>(t->dim) > (1ll << 40)) { *why = "chains x dim too large"; return false; }
+  switch (t->id) {
+    case HMC_T_STD_NORMAL: return true;
+    case HMC_T_FUNNEL:
+      if (t->dim < 2) { *why = "funnel needs dim >= 2"; return false; }
+      return true;
+    case HMC_T_CORR_GAUSS: return true;
+    case HMC_T_LOGREG:
+      if (t->n_data < 1 || t->n_data > (1ll << 31) - 1) { *why = "LOGREG n_data out of range"; return false; }
+      if (C * t->n_data > (1ll << 40)) { *why = "chains x n_data too large"; return false; }
+      return true;
+    default:
+      *why = "unknown target id";
+      return false;
+  }
+}
+
 bool valid_target(const hmc_target* t, int64_t C, std::string* why) {
   if (!t) { *why = "target is NULL"; return false; }
   if (t->dim < 1) { *why = "target dim must be >= 1"; return false; }
@@ -179,12 +203,85 @@ bool valid_config(const hmc_config* c, int64_t C, std::string* why) {
 template <typename T>
 cudaError_t ctx_alloc(hmc_ctx* ctx, T** p, size_t count) {
   void* v = nullptr;
-  cudaError_t e = cudaMallocAsync(&v, std::max<size_t>(count * sizeof(T), 16), ctx->stream);
+  const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  cudaError_t e = cudaMallocAsync(&v, bytes, ctx->stream);
   if (e == cudaSuccess) {
     ctx->allocations.push_back(v);
+    ctx->device_bytes += bytes;
     *p = static_cast<T*>(v);
   }
   return e;
+}
+
+// Which paths a context takes and what hmc_create allocates for them: one
+// function, so that the size query (hmc_create_device_bytes) and hmc_create
+// cannot disagree.
+struct CreatePlan {
+  hmc_config cfg;          // the configuration as the context keeps it
+  bool use_tc = false, tc_fused = false, tc_pair = false;
+  bool use_lrtc = false, use_lrgemm = false;
+  bool fused_logreg = false, fused_elementwise = false, plain_buffers = false;
+  size_t grad_ws = 0;
+  uint64_t bytes = 0;      // sum of the allocation requests, each at least 16 bytes
+};
+
+CreatePlan plan_create(const hmc_target& t, int64_t num_chains, const hmc_config& config) {
+  CreatePlan q;
+  q.cfg = config;
+  // the random walk and NUTS run the plain path's buffers (their proposals
+  // are one elementwise op or their own kernel)
+  if (q.cfg.proposal != HMC_PROPOSAL_LEAPFROG) q.cfg.impl = HMC_IMPL_PLAIN;
+  const bool fused = q.cfg.impl == HMC_IMPL_FUSED || q.cfg.impl == HMC_IMPL_FUSED_SINGLE_CTA;
+  const size_t C = static_cast<size_t>(num_chains), D = static_cast<size_t>(t.dim);
+  auto add = [&](size_t b) { q.bytes += std::max<size_t>(b, 16); };
+  const unsigned nblk = std::max({hmc::accept_blocks(static_cast<int>(num_chains)),
+                                  hmc::gauss_fused_grid(num_chains), hmc::gauss_pair_grid(num_chains),
+                                  hmc::logreg_fused_grid(num_chains), hmc::nuts_grid(num_chains)});
+  add(4 * C);                        // log p
+  add(4 * C * D);                    // gradient
+  add(C);                            // is_accepted
+  add(4 * C);                        // log alpha
+  add(sizeof(DAState));
+  add(8 * 2 * static_cast<size_t>(nblk));   // partial sums, two transitions' worth
+  if (q.cfg.proposal == HMC_PROPOSAL_NUTS) {
+    add(4 * hmc::nuts_scratch_floats(t, num_chains));
+    add(sizeof(unsigned long long));
+  }
+  q.use_tc = fused && hmc::gauss_tc_supported(t);
+  if (q.use_tc) {
+    add(hmc::gauss_tc_workspace_bytes(t, num_chains));
+    q.tc_fused = hmc::gauss_fused_supported(t);
+    q.tc_pair = q.tc_fused && q.cfg.impl == HMC_IMPL_FUSED;
+    if (q.tc_pair) add(sizeof(unsigned));
+  }
+  // logistic regressions with long data passes or much work per gradient
+  // (chains x rows x dim above 2^22): tensor-core products; small ones: the
+  // shared-memory SIMT transition
+  const bool lr_big = t.id == HMC_T_LOGREG && (t.n_data > 2048 || num_chains * t.n_data * t.dim > (1ll << 22));
+  q.use_lrtc = q.cfg.impl == HMC_IMPL_FUSED && hmc::logreg_tc_supported(t) && lr_big;
+  if (q.use_lrtc) {
+    add(hmc::logreg_tc_workspace_bytes(t, num_chains));
+    add(sizeof(int));
+  }
+  // long data passes the pair kernel does not take (dim > 128 or not a
+  // multiple of 4): one-CTA tensor-core products
+  q.use_lrgemm = q.cfg.impl == HMC_IMPL_FUSED && !q.use_lrtc && hmc::logreg_gemm_supported(t) && lr_big;
+  if (q.use_lrgemm) add(hmc::logreg_gemm_workspace_bytes(t, num_chains));
+  q.fused_logreg = fused && !q.use_lrtc && !q.use_lrgemm && hmc::logreg_fused_supported(t);
+  q.fused_elementwise = fused && (t.id == HMC_T_STD_NORMAL || t.id == HMC_T_FUNNEL) &&
+                        t.dim <= hmc::kFusedElementwiseMaxDim;
+  q.plain_buffers = !q.fused_elementwise && !q.use_tc;
+  if (q.plain_buffers) {
+    add(4 * C * D);
+    add(4 * C * D);
+    add(4 * C * D);
+    add(4 * C);
+    add(4 * C);
+    add(4 * C);
+  }
+  q.grad_ws = hmc::grad_workspace_bytes(t, num_chains);
+  if (q.grad_ws) add(q.grad_ws);
+  return q;
 }
 
 void drop_graph(hmc_ctx* ctx) {
@@ -463,11 +560,10 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     return fail(nullptr, HMC_E_UNSUPPORTED, "NUTS runs the STD_NORMAL and FUNNEL targets with dim <= 512");
   hmc_ctx* ctx = new (std::nothrow) hmc_ctx();
   if (!ctx) return fail(nullptr, HMC_E_OOM, "host allocation failed");
+  const CreatePlan plan = plan_create(*target, num_chains, *config);
   ctx->target = *target;
   ctx->C = num_chains;
-  ctx->cfg = *config;
-  // the random walk runs the plain path (its proposal is one elementwise op)
-  if (ctx->cfg.proposal != HMC_PROPOSAL_LEAPFROG) ctx->cfg.impl = HMC_IMPL_PLAIN;
+  ctx->cfg = plan.cfg;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   const size_t C = static_cast<size_t>(num_chains), D = static_cast<size_t>(target->dim);
   cudaError_t e = cudaSuccess;
@@ -490,22 +586,16 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->nuts_leaves, 1);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->nuts_leaves, 0, sizeof(unsigned long long), ctx->stream);
   }
-  ctx->use_tc = (ctx->cfg.impl == HMC_IMPL_FUSED || ctx->cfg.impl == HMC_IMPL_FUSED_SINGLE_CTA) &&
-                hmc::gauss_tc_supported(*target);
+  ctx->use_tc = plan.use_tc;
   if (e == cudaSuccess && ctx->use_tc) {
     char* w = nullptr;
     e = ctx_alloc(ctx, &w, hmc::gauss_tc_workspace_bytes(*target, num_chains));
     if (e == cudaSuccess) e = hmc::gauss_tc_setup(&ctx->tc, *target, num_chains, w, ctx->stream);
-    ctx->tc.fused = hmc::gauss_fused_supported(*target);
-    ctx->tc.pair = ctx->tc.fused && ctx->cfg.impl == HMC_IMPL_FUSED;
+    ctx->tc.fused = plan.tc_fused;
+    ctx->tc.pair = plan.tc_pair;
     if (e == cudaSuccess && ctx->tc.pair) e = ctx_alloc(ctx, &ctx->grid_bar, 1);
   }
-  // logistic regressions with long data passes or much work per gradient
-  // (chains x rows x dim above 2^22): tensor-core products; small ones: the
-  // shared-memory SIMT transition
-  const bool lr_big = target->id == HMC_T_LOGREG &&
-                      (target->n_data > 2048 || num_chains * target->n_data * target->dim > (1ll << 22));
-  ctx->use_lrtc = ctx->cfg.impl == HMC_IMPL_FUSED && hmc::logreg_tc_supported(*target) && lr_big;
+  ctx->use_lrtc = plan.use_lrtc;
   if (e == cudaSuccess && ctx->use_lrtc) {
     char* w = nullptr;
     e = ctx_alloc(ctx, &w, hmc::logreg_tc_workspace_bytes(*target, num_chains));
@@ -513,17 +603,14 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->lr_err, 0, sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = hmc::logreg_tc_setup(&ctx->lrtc, *target, num_chains, w, ctx->stream);
   }
-  // long data passes the pair kernel does not take (dim > 128 or not a
-  // multiple of 4): one-CTA tensor-core products
-  ctx->use_lrgemm = ctx->cfg.impl == HMC_IMPL_FUSED && !ctx->use_lrtc &&
-                    hmc::logreg_gemm_supported(*target) && lr_big;
+  ctx->use_lrgemm = plan.use_lrgemm;
   if (e == cudaSuccess && ctx->use_lrgemm) {
     char* w = nullptr;
     e = ctx_alloc(ctx, &w, hmc::logreg_gemm_workspace_bytes(*target, num_chains));
     if (e == cudaSuccess) e = hmc::logreg_gemm_setup(&ctx->lrg, *target, num_chains, w, ctx->stream);
   }
-  if (e == cudaSuccess && uses_fused_logreg(ctx)) e = hmc::logreg_fused_setup(*target);
-  if (e == cudaSuccess && !uses_fused_elementwise(ctx) && !ctx->use_tc) {
+  if (e == cudaSuccess && plan.fused_logreg) e = hmc::logreg_fused_setup(*target);
+  if (e == cudaSuccess && plan.plain_buffers) {
     e = ctx_alloc(ctx, &ctx->plain.xp, C * D);
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.gp, C * D);
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.p, C * D);
@@ -531,7 +618,7 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.h0, C);
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->plain.la, C);
   }
-  ctx->grad_ws_bytes = hmc::grad_workspace_bytes(*target, num_chains);
+  ctx->grad_ws_bytes = plan.grad_ws;
   if (e == cudaSuccess && ctx->grad_ws_bytes) {
     char* w = nullptr;
     e = ctx_alloc(ctx, &w, ctx->grad_ws_bytes);
@@ -551,6 +638,22 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
                 std::string("workspace allocation: ") + cudaGetErrorString(e));
   }
   *out = ctx;
+  return HMC_OK;
+}
+
+hmc_status hmc_create_device_bytes(const hmc_target* target, int64_t num_chains, const hmc_config* config,
+                                   uint64_t* bytes) {
+  std::string why;
+  if (!bytes) return fail(nullptr, HMC_E_INVALID, "bytes is NULL");
+  if (!valid_target_shape(target, num_chains, &why)) return fail(nullptr, HMC_E_INVALID, why);
+  if (!valid_config(config, num_chains, &why)) return fail(nullptr, HMC_E_INVALID, why);
+  *bytes = plan_create(*target, num_chains, *config).bytes;
+  return HMC_OK;
+}
+
+hmc_status hmc_context_device_bytes(const hmc_ctx* ctx, uint64_t* bytes) {
+  if (!ctx || !bytes) return fail(nullptr, HMC_E_INVALID, "NULL argument");
+  *bytes = ctx->device_bytes + ctx->stage_bytes;
   return HMC_OK;
 }
 

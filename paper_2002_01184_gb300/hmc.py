@@ -72,6 +72,9 @@ def _load():
         "hmc_read_adaptation": [P, ctypes.POINTER(ctypes.c_double)],
         "hmc_sample_chain_range": [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P, P, P],
         "hmc_state_bytes": [P, ctypes.POINTER(ctypes.c_uint64)],
+        "hmc_create_device_bytes": [ctypes.POINTER(hmc_target), ctypes.c_int64, ctypes.POINTER(hmc_config),
+                                    ctypes.POINTER(ctypes.c_uint64)],
+        "hmc_context_device_bytes": [P, ctypes.POINTER(ctypes.c_uint64)],
         "hmc_save_state": [P, P, ctypes.c_uint64],
         "hmc_restore_state": [P, P, ctypes.c_uint64],
         "hmc_destroy": [P],
@@ -224,6 +227,19 @@ def hmc_sample_chain_range(ctx, x_inout, num_burnin, t_begin, t_end, samples_out
                            trace_step_size=None, trace_accept=None):
     _check(lib.hmc_sample_chain_range(ctx, _ptr(x_inout), int(num_burnin), int(t_begin), int(t_end),
                                       _ptr(samples_out), _ptr(trace_step_size), _ptr(trace_accept)), ctx)
+
+
+def hmc_create_device_bytes(target, num_chains, config):
+    n = ctypes.c_uint64()
+    _check(lib.hmc_create_device_bytes(ctypes.byref(target), int(num_chains), ctypes.byref(config),
+                                       ctypes.byref(n)))
+    return int(n.value)
+
+
+def hmc_context_device_bytes(ctx):
+    n = ctypes.c_uint64()
+    _check(lib.hmc_context_device_bytes(ctx, ctypes.byref(n)), ctx)
+    return int(n.value)
 
 
 def hmc_state_bytes(ctx):

@@ -21,16 +21,25 @@ from .sampler import Sampler
 
 
 def job_bytes(problem, keep_samples=True):
-    """Device bytes a job holds while resident: state, workspace, samples."""
+    """Device bytes a job holds while resident: the library context's
+    workspace (hmc_create_device_bytes, for the configuration the job's
+    Sampler builds), the target data the Sampler copies to the device, the
+    chain state and the job's traces."""
     C, D, K = problem.num_chains, problem.dim, problem.num_results
-    b = 4 * C * D * 12 + 4 * C * 16
+    n_data = 0 if problem.X is None else int(problem.X.shape[0])
+    target = hmc.hmc_target(hmc.TARGET_IDS[problem.kind], int(D), n_data, None, None, None)
+    config = hmc.make_config(problem.num_leapfrog, problem.step_size, problem.seed, problem.adapt,
+                             problem.target_accept, problem.num_burnin if problem.adapt else 0,
+                             hmc.HMC_IMPL_FUSED, 0, True)
+    b = hmc.hmc_create_device_bytes(target, C, config)
     if problem.P is not None:
-        b += 8 * D * D
+        b += 4 * problem.P.size
     if problem.X is not None:
         b += 4 * problem.X.size + 4 * problem.y.size
-        b += 4 * C * problem.X.shape[0]                       # residual workspace
+    b += 4 * C * D                                   # chain state
+    b += 4 * K + K * C                               # step-size and accept traces
     if keep_samples:
-        b += 4 * K * C * D + K * C + 4 * K
+        b += 4 * K * C * D
     return int(b)
 
 

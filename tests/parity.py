@@ -25,6 +25,12 @@ DECISION_BAND = 1e-5
 # than 1e-6 (|H0| + |H_L|) to their threshold may go either way
 DECISION_REL = 1e-6
 
+# |log alpha_gpu - log alpha_oracle| of every compared transition, for the
+# record the suite can write (HMC_PARITY_LOG, see conftest.py): label, the
+# largest absolute difference, the largest difference relative to
+# |H0| + |H_L|, and the number of finite chains compared
+MARGINS = []
+
 
 def chain_error(x, ref):
     """Per-chain max-norm relative error, floor 1e-3."""
@@ -65,6 +71,11 @@ def compare_transition(x_before, x_after_gpu, acc_gpu, la_gpu, ref, label=""):
     # error (float32's range ends near 3e38) -- both reject those chains
     la_ref = ref["log_accept_ratio"]
     la_gpu = np.asarray(la_gpu, dtype=np.float64)
+    fin = np.isfinite(la_ref) & np.isfinite(la_gpu)
+    if fin.any():
+        d = np.abs(la_gpu[fin] - la_ref[fin])
+        rel = d / np.maximum(np.abs(ref["h0"][fin]) + np.abs(ref["h1"][fin]), 1e-30) if "h0" in ref else d * np.nan
+        MARGINS.append((label, float(d.max()), float(np.nanmax(rel)) if "h0" in ref else None, int(fin.sum())))
     assert np.all(~np.isfinite(la_gpu[~np.isfinite(la_ref)])), f"{label}: missed divergence"
     extra = ~np.isfinite(la_gpu) & np.isfinite(la_ref)
     assert np.all(la_ref[extra] < -1e30), f"{label}: spurious divergence"

@@ -98,3 +98,17 @@ def test_null_context_and_workspace_queries(binding):
     assert b >= 2048 * 20000 * 4
     with pytest.raises(h.HMCError):
         h.hmc_target_log_prob_and_grad(t, 2048, 16, 16, 16, None, 0, stream=0)
+
+
+def test_create_device_bytes_needs_no_device_and_checks_its_arguments(binding):
+    h = binding
+    cfg = h.make_config(4, 0.1)
+    shape_only = h.hmc_target(h.TARGET_IDS["logreg"], 32, 1000, None, None, None)
+    assert h.hmc_create_device_bytes(shape_only, 64, cfg) >= 4 * 64 * 32
+    for bad in (h.hmc_target(h.TARGET_IDS["logreg"], 32, 0, None, None, None),
+                h.hmc_target(9, 32, 0, None, None, None),
+                h.hmc_target(h.TARGET_IDS["funnel"], 1, 0, None, None, None)):
+        with pytest.raises(h.HMCError):
+            h.hmc_create_device_bytes(bad, 64, cfg)
+    with pytest.raises(h.HMCError):
+        h.hmc_create_device_bytes(shape_only, 0, cfg)

@@ -299,7 +299,19 @@ def test_divergent_proposals_are_rejected(H):
 def test_correlated_gaussian_moments(H):
     """Adapted sampling of a D = 8 correlated Gaussian: along a fixed random
     direction u the kept draws have mean 0 and variance u^T P^-1 u, each
-    within 3 Monte Carlo standard errors."""
+    within 3 Monte Carlo standard errors.  Dual averaging freezes the step
+    size at its weighted average, whose acceptance need not equal the target
+    0.65 (on this target it is near 0.71); the kept transitions' acceptance
+    must be the one the float64 oracle reaches at the step size the GPU
+    froze, on the same schedule, seed and start, within 3 standard errors of
+    the difference of the two rates (each over 2048 x 300 accept indicators,
+    correlation between a chain's transitions taken as a factor of at most 4
+    in variance).  The frozen step size itself varies from run to run with
+    the adaptation's Monte Carlo noise (float32 and float64 chains part after
+    many transitions), so it is not compared to the oracle's.
+    """
+    from oracle import hmc as ohmc
+    from oracle import targets as otargets
     from paper_2002_01184_gb300.sampler import Sampler
     p = workloads.corr_gauss(dim=8, num_chains=2048, num_burnin=200, num_results=300)
     s = Sampler(p)
@@ -313,6 +325,16 @@ def test_correlated_gaussian_moments(H):
     assert abs(proj.mean()) < 3 * diagnostics.mcse_mean(proj)[0]
     sq = proj ** 2
     assert abs(sq.mean() - u @ cov @ u) < 3 * diagnostics.mcse_mean(sq)[0]
+    tgt = otargets.make("corr_gauss", P=p.P)
+    frozen = float(host(eps)[0])
+    assert np.all(host(eps) == host(eps)[0])
+    ref = ohmc.sample_chain(p.x0.astype(np.float64), tgt, p.num_leapfrog, frozen, p.seed,
+                            p.num_burnin, p.num_results, adapt=False)
+    ref_acc = np.asarray(ref["is_accepted"]).mean()
+    gpu_acc = float(host(acc).astype(np.float64).mean())
+    n = acc.numel()
+    se = np.sqrt(4 * 2 * ref_acc * (1 - ref_acc) / n)
+    assert abs(gpu_acc - ref_acc) < 3 * se, (gpu_acc, ref_acc, se)
     s.close()
 
 

@@ -48,3 +48,44 @@ def test_admission_respects_the_budget(S):
     jobs = server.run(reqs, max_wall=600)
     assert all(j.finished is not None for j in jobs)
     assert max(peak) <= need
+
+
+CASES = [
+    ("corr_gauss", dict(dim=256, num_chains=512), "fused", "leapfrog"),
+    ("corr_gauss", dict(dim=256, num_chains=512), "single", "leapfrog"),
+    ("corr_gauss", dict(dim=256, num_chains=512), "plain", "leapfrog"),
+    ("corr_gauss", dict(dim=384, num_chains=300), "fused", "leapfrog"),
+    ("logreg", dict(n_data=2500, dim=64, num_chains=256), "fused", "leapfrog"),
+    ("logreg", dict(n_data=3000, dim=160, num_chains=200), "fused", "leapfrog"),
+    ("logreg", dict(n_data=500, dim=16, num_chains=64), "fused", "leapfrog"),
+    ("funnel", dict(dim=50, num_chains=1000), "fused", "leapfrog"),
+    ("funnel", dict(dim=50, num_chains=1000), "fused", "nuts"),
+    ("std_normal", dict(dim=3, num_chains=100), "fused", "random_walk"),
+]
+
+
+@pytest.mark.parametrize("kind,kw,impl,proposal", CASES)
+def test_create_device_bytes_equal_what_a_context_allocates(S, kind, kw, impl, proposal):
+    """Admission by HBM budget relies on the library's size query: for every
+    path a configuration can select, hmc_create_device_bytes (computed
+    without creating anything, from the target's family and sizes alone)
+    equals the bytes the created context requested from the device, and the
+    server's job_bytes covers it plus the job's own buffers."""
+    from paper_2002_01184_gb300 import hmc
+    from paper_2002_01184_gb300.sampler import Sampler
+    p = getattr(workloads, kind)(**kw)
+    impl_id = {"fused": hmc.HMC_IMPL_FUSED, "single": hmc.HMC_IMPL_FUSED_SINGLE_CTA, "plain": hmc.HMC_IMPL_PLAIN}[impl]
+    prop = {"leapfrog": hmc.HMC_PROPOSAL_LEAPFROG, "nuts": hmc.HMC_PROPOSAL_NUTS,
+            "random_walk": hmc.HMC_PROPOSAL_RANDOM_WALK}[proposal]
+    if proposal == "nuts":
+        p.num_leapfrog = 10
+    s = Sampler(p, impl=impl_id, proposal=prop)
+    n_data = 0 if p.X is None else p.X.shape[0]
+    shape_only = hmc.hmc_target(hmc.TARGET_IDS[kind], p.dim, n_data, None, None, None)
+    predicted = hmc.hmc_create_device_bytes(shape_only, p.num_chains, s.config)
+    assert predicted == hmc.hmc_context_device_bytes(s.ctx)
+    assert predicted >= 4 * p.num_chains * p.dim            # at least the cached gradient
+    if impl == "fused" and proposal == "leapfrog":
+        own = 4 * p.num_chains * p.dim * (1 + p.num_results)
+        assert S.job_bytes(p) >= predicted + own
+    s.close()

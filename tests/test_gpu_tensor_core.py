@@ -140,3 +140,47 @@ def test_tensor_core_logreg_transition_matches_oracle(H, C, D, N, eps, L):
         assert np.max(np.abs(gg - g_new) / np.maximum(row, 1e-6)) < 1e-4
     assert n_same >= 3 * C - max(2, C // 500)      # decisions inside the float32 band
     s.close()
+
+
+def test_full_size_logreg_transition_matches_oracle(H):
+    """The logistic-regression workload at its full size (2048 chains, 20000
+    rows, dim 128, L = 10), in the launch configuration the bench times (the
+    CTA-pair tensor-core products, 9 data ranges x 8 chain groups), teacher-
+    forced against the float64 oracle for one transition on every chain (the
+    oracle's transition at this size takes about half a minute on the host).
+    Chains start near the posterior mode (a few Newton steps of the float64
+    log-density) so that the trajectories are the posterior's, not a
+    divergence from the prior mean."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    C, D, N, L, eps = 2048, 128, 20000, 10, 0.004
+    p = workloads.logreg(n_data=N, dim=D, num_chains=C, num_burnin=0, num_results=0, num_leapfrog=L)
+    X, y = p.X.astype(np.float64), p.y.astype(np.float64)
+    w = np.zeros(D)
+    for _ in range(8):                         # Newton on y.z - softplus(z) - |w|^2/2
+        z = X @ w
+        s_ = 1.0 / (1.0 + np.exp(-z))
+        grad = X.T @ (y - s_) - w
+        hess = -(X.T * (s_ * (1 - s_))) @ X - np.eye(D)
+        w = w - np.linalg.solve(hess, grad)
+    rng = np.random.default_rng(5)
+    p.x0 = (w + rng.standard_normal((C, D)) * (0.5 / np.sqrt(N))).astype(np.float32)
+    p.step_size = eps
+    s = Sampler(p, adapt=False)
+    assert H.hmc_dominant_kernel_info(s.ctx)[0] == "k_lr_grad"
+    x = torch.as_tensor(p.x0).cuda().contiguous()
+    s.bootstrap(x)
+    tgt = otargets.make("logreg", X=p.X, y=p.y)
+    xin = host(x).astype(np.float64)
+    lp, g = tgt(xin)
+    r = s.results(s.step(x, 0))
+    H.hmc_synchronize(s.ctx)
+    ref = ohmc.one_step(xin, lp, g, np.float32(eps), L, p.seed, 0, tgt)
+    n_same, _ = compare_transition(xin, host(x), host(r["is_accepted"]), host(r["log_accept_ratio"]),
+                                   ref, label="lr-tc full size")
+    gg = host(r["grad"])
+    _, g_new = tgt(host(x).astype(np.float64))
+    row = np.max(np.abs(g_new), axis=1, keepdims=True)
+    assert np.max(np.abs(gg - g_new) / np.maximum(row, 1e-6)) < 1e-4
+    assert n_same >= C - 2
+    assert 0.3 < float(host(r["is_accepted"]).mean()) < 1.0     # real proposals, mostly accepted
+    s.close()
