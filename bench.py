@@ -386,7 +386,7 @@ def run_uneven_batch(args):
                                    f"[64,4096]) + 16 funnels (d in [10,200]), L=10, DA(0.8), "
                                    f"B={B} K={K} (fraction {args.batch_scale} of 500+1000)",
                        "impl": "plain, one posterior after another" if args.plain
-                       else "one grouped launch per transition, CUDA graph",
+                       else "grouped members in one persistent launch, side members on their own streams",
                        "posteriors": len(probs)},
             "min_ess_per_s": ess / (ms / 1000.0), "min_ess": ess,
             "host_enqueue_ms_per_step": 1000.0 * t_enq / args.steps,

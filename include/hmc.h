@@ -396,9 +396,10 @@ hmc_status hmc_remc_swaps(const hmc_ctx* ctx, const uint8_t** swapped);
  * Many posteriors of uneven dimension, data size and chain count sampled
  * together (the independent-chain batching of Section 2 applied across
  * posteriors).  Funnels, standard normals and small logistic regressions
- * (chains x rows x dim <= 2^22) share one grouped kernel launch per
- * transition (one tile per 8 chains, largest tiles first), the whole loop as
- * one CUDA graph; larger logistic regressions run their own transitions
+ * (chains x rows x dim <= 2^22) share one persistent kernel launch for all
+ * their transitions (one tile per 8 chains, largest tiles first; a tile waits
+ * only for its own posterior's step-size update after a transition that
+ * adapts it), with the bootstraps as one CUDA graph; larger logistic regressions run their own transitions
  * (tensor-core products for dim <= 128) on streams of their own,
  * concurrently.  Each posterior keeps
  * its own state, kernel results and dual-averaging step size, so its result
@@ -430,6 +431,11 @@ hmc_status hmc_batch_sample_chain(hmc_batch* batch, float* const* x_inout,
 /* The context of posterior i (owned by the batch; for hmc_read_adaptation
  * and hmc_synchronize).  NULL if i is out of range. */
 hmc_ctx* hmc_batch_context(hmc_batch* batch, int32_t i);
+
+/* Wait for all of the batch's work; HMC_E_TIMEOUT if a bounded device-side
+ * wait gave up (the grouped launch's per-posterior adaptation barrier, or a
+ * posterior context's own). */
+hmc_status hmc_batch_synchronize(hmc_batch* batch);
 
 /* Text of the batch's last error ("" if none). */
 const char* hmc_batch_last_error(const hmc_batch* batch);

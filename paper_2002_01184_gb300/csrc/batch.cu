@@ -1,12 +1,16 @@
 // Many posteriors of uneven dimension, data size and chain count sampled
 // together (Section 2's premise -- independent chains, batched evaluation --
 // applied across posteriors).  Two kinds of members:
-//   grouped: every transition of every such posterior is one CTA tile of a
-//     single grouped launch (k_batch_transition), the tiles of all of them
-//     side by side, ordered by estimated cost so the largest start first;
-//     the whole loop (bootstraps + one grouped launch per transition) is one
-//     CUDA graph.  Funnels, standard normals and small logistic regressions
-//     (kGroupedMaxWork).
+//   grouped: every tile (8 chains) of every such posterior is a work item of
+//     one persistent cooperative launch (k_batch_persistent) that runs all
+//     their transitions: each CTA owns a fixed set of items, ordered by
+//     estimated cost so the largest start first, and runs them transition by
+//     transition.  A tile waits only after a transition that adapted its
+//     posterior's step size, until the posterior's last tile has applied the
+//     update (a per-posterior generation counter, bounded spin); transitions
+//     with a fixed step size run without any barrier.  The bootstraps and
+//     the launch are one CUDA graph.  Funnels, standard normals and small
+//     logistic regressions (kGroupedMaxWork).
 //   side: logistic regressions with longer data passes, sampled by their own
 //     context (tensor-core products for dim <= 128, tiled SIMT products
 //     otherwise) on a stream of their own, concurrently with the grouped graph.
@@ -22,6 +26,7 @@
 #include "hmc_device.cuh"
 #include "hmc_internal.h"
 #include "logreg_tile.cuh"
+#include "sm100_ptx.cuh"
 
 namespace hmc {
 
@@ -42,34 +47,81 @@ struct BatchPost {
 };
 
 template <int TARGET>
-__device__ __forceinline__ void elementwise_dispatch(const StepArgs& a, int nb, int tile, int ntiles) {
-  if (nb == 1) elementwise_tile<TARGET, 1>(a, tile, ntiles);
-  else if (nb == 2) elementwise_tile<TARGET, 2>(a, tile, ntiles);
-  else if (nb == 4) elementwise_tile<TARGET, 4>(a, tile, ntiles);
-  else elementwise_tile<TARGET, 8>(a, tile, ntiles);
+__device__ __forceinline__ bool elementwise_dispatch_r(const StepArgs& a, int nb, int tile, int ntiles,
+                                                       bool reduce) {
+  if (nb == 1) return elementwise_tile<TARGET, 1>(a, tile, ntiles, reduce);
+  if (nb == 2) return elementwise_tile<TARGET, 2>(a, tile, ntiles, reduce);
+  if (nb == 4) return elementwise_tile<TARGET, 4>(a, tile, ntiles, reduce);
+  return elementwise_tile<TARGET, 8>(a, tile, ntiles, reduce);
 }
 
-__global__ void __launch_bounds__(256) k_batch_transition(const BatchPost* __restrict__ posts,
-                                                         const int2* __restrict__ items, uint32_t t) {
-  const int2 it = items[blockIdx.x];                   // (posterior, tile)
-  const BatchPost& P = posts[it.x];
-  if (static_cast<long long>(t) >= P.B + P.K) return;  // this posterior has finished
-  StepArgs a = P.s;
-  a.t = t;
-  a.t_full = t;
-  const long long k = static_cast<long long>(t) - P.B;
-  if (k >= 0) {
-    a.sample_out = P.samples ? P.samples + k * static_cast<long long>(a.C) * a.D : nullptr;
-    a.trace_acc = P.trace_acc ? P.trace_acc + k * a.C : nullptr;
-    a.trace_eps = P.trace_eps ? P.trace_eps + k : nullptr;
-  }
-  if (P.kind == HMC_T_LOGREG) {
-    lr::LrArgs la{a, P.X, P.y, P.n_data};
-    lr::logreg_tile(la, it.y, P.ntiles);
-  } else if (P.kind == HMC_T_FUNNEL) {
-    elementwise_dispatch<HMC_T_FUNNEL>(a, P.nb, it.y, P.ntiles);
-  } else {
-    elementwise_dispatch<HMC_T_STD_NORMAL>(a, P.nb, it.y, P.ntiles);
+constexpr unsigned long long kBatchWaitNs = 500000000ull;   // 0.5 s
+
+// Every transition of every grouped posterior in one cooperative launch.
+// Item (posterior, tile) i belongs to CTA i mod gridDim; each CTA runs its
+// items for transition 0, then for transition 1, and so on.  Before
+// transition t a tile of posterior p waits until gen[p] >= t when
+// transition t - 1 adapted p's step size (the tile that applies an update
+// sets gen[p] = t + 1 after it); the reduction itself runs on adapting
+// transitions and on p's last, whose statistic the state reports, so the
+// arithmetic is the per-transition launch's.  A CTA never waits on an item
+// of a later transition than the one it runs, and all CTAs are resident, so
+// every wait ends; each is bounded all the same (err, then the kernel
+// returns).
+__global__ void __launch_bounds__(256) k_batch_persistent(const BatchPost* __restrict__ posts,
+                                                          const int2* __restrict__ items, int num_items,
+                                                          uint32_t T, unsigned* gen, int* err) {
+  __shared__ int abort_s;
+  for (uint32_t t = 0; t < T; ++t) {
+    for (int i = blockIdx.x; i < num_items; i += gridDim.x) {
+      const int2 it = items[i];                            // (posterior, tile)
+      const BatchPost& P = posts[it.x];
+      const long long total = P.B + P.K;
+      if (static_cast<long long>(t) >= total) continue;    // this posterior has finished
+      const DAState* da = P.s.da;
+      const bool adapt = da->adapt != 0;
+      if (t > 0 && adapt && static_cast<long long>(t) - 1 < da->num_adapt) {
+        if (threadIdx.x == 0) {
+          abort_s = 0;
+          const unsigned long long t0 = ptx::global_timer_ns();
+          while (*reinterpret_cast<volatile unsigned*>(&gen[it.x]) < t) {
+            if (ptx::global_timer_ns() - t0 > kBatchWaitNs) {
+              atomicCAS(err, 0, 1);
+              abort_s = 1;
+              break;
+            }
+          }
+          __threadfence();
+        }
+        __syncthreads();
+        if (abort_s) return;
+      }
+      StepArgs a = P.s;
+      a.t = t;
+      a.t_full = t;
+      const long long k = static_cast<long long>(t) - P.B;
+      if (k >= 0) {
+        a.sample_out = P.samples ? P.samples + k * static_cast<long long>(a.C) * a.D : nullptr;
+        a.trace_acc = P.trace_acc ? P.trace_acc + k * a.C : nullptr;
+        a.trace_eps = P.trace_eps ? P.trace_eps + k : nullptr;
+      }
+      const bool reduce = (adapt && static_cast<long long>(t) < da->num_adapt) ||
+                          static_cast<long long>(t) == total - 1;
+      bool updated;
+      if (P.kind == HMC_T_LOGREG) {
+        lr::LrArgs la{a, P.X, P.y, P.n_data};
+        updated = lr::logreg_tile(la, it.y, P.ntiles, reduce);
+      } else if (P.kind == HMC_T_FUNNEL) {
+        updated = elementwise_dispatch_r<HMC_T_FUNNEL>(a, P.nb, it.y, P.ntiles, reduce);
+      } else {
+        updated = elementwise_dispatch_r<HMC_T_STD_NORMAL>(a, P.nb, it.y, P.ntiles, reduce);
+      }
+      if (updated && threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(&gen[it.x], t + 1u);
+      }
+      __syncthreads();                                     // shared memory is the next item's
+    }
   }
 }
 
@@ -106,6 +158,9 @@ struct hmc_batch {
   hmc::BatchPost* dev_posts = nullptr;
   int2* dev_items = nullptr;
   int num_items = 0;
+  unsigned* dev_gen = nullptr;   // per grouped posterior: transitions whose update is applied
+  int* dev_err = nullptr;        // a bounded wait of the persistent launch gave up
+  int grid = 0;                  // CTAs of the persistent launch (all resident)
   size_t smem = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -137,6 +192,10 @@ void batch_release(hmc_batch* b) {
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->dev_posts) cudaFree(b->dev_posts);
   if (b->dev_items) cudaFree(b->dev_items);
+  if (b->dev_gen) cudaFree(b->dev_gen);
+  if (b->dev_err) cudaFree(b->dev_err);
+  b->dev_gen = nullptr;
+  b->dev_err = nullptr;
   b->graph = nullptr;
   b->fork = nullptr;
   b->cap_stream = nullptr;
@@ -241,10 +300,24 @@ hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
   if (e == cudaSuccess && !flat.empty()) e = cudaMalloc(&b->dev_items, sizeof(int2) * flat.size());
   if (e == cudaSuccess && !flat.empty())
     e = cudaMemcpy(b->dev_items, flat.data(), sizeof(int2) * flat.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !b->host_posts.empty())
+    e = cudaMalloc(&b->dev_gen, sizeof(unsigned) * b->host_posts.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->dev_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(b->dev_err, 0, sizeof(int));
   // the attribute belongs to the kernel, not to this batch: set the maximum
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(hmc::k_batch_transition, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(hmc::k_batch_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(hmc::lr::logreg_smem_bytes(hmc::lr::kLrMaxDim)));
+  // the persistent launch takes as many CTAs as can be resident at once
+  if (e == cudaSuccess && b->num_items > 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hmc::k_batch_persistent, 256, b->smem);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+    b->grid = std::min(b->num_items, sms * per_sm);
+  }
   if (e != cudaSuccess) {
     const hmc_status st = e == cudaErrorMemoryAllocation ? HMC_E_OOM : HMC_E_CUDA;
     cudaGetLastError();
@@ -317,11 +390,24 @@ hmc_status hmc_batch_sample_chain(hmc_batch* b, float* const* x_inout, const int
                           b->cap_stream);
       for (int i = 0; i < b->n && st == HMC_OK && e == cudaSuccess; ++i)
         if (b->member[i] >= 0) st = hmc::ctx_bootstrap_on(b->ctx[i], x_inout[i], b->cap_stream);
-      for (long long t = 0; t < T && st == HMC_OK && e == cudaSuccess; ++t) {
-        hmc::k_batch_transition<<<b->num_items, 256, b->smem, b->cap_stream>>>(
-            b->dev_posts, b->dev_items, static_cast<uint32_t>(t));
+      if (st == HMC_OK && e == cudaSuccess)
+        e = cudaMemsetAsync(b->dev_gen, 0, sizeof(unsigned) * b->host_posts.size(), b->cap_stream);
+      if (st == HMC_OK && e == cudaSuccess && T > 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(static_cast<unsigned>(b->grid));
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = b->smem;
+        cfg.stream = b->cap_stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, hmc::k_batch_persistent, static_cast<const hmc::BatchPost*>(b->dev_posts),
+                               static_cast<const int2*>(b->dev_items), b->num_items, static_cast<uint32_t>(T),
+                               b->dev_gen, b->dev_err);
         hmc::count_launch();
-        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaGetLastError();
       }
       cudaGraph_t g = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
@@ -350,6 +436,20 @@ hmc_status hmc_batch_sample_chain(hmc_batch* b, float* const* x_inout, const int
     if (b->member[i] >= 0) continue;
     e = cudaStreamWaitEvent(b->stream, b->side_done[i], 0);
     if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, std::string("join: ") + cudaGetErrorString(e));
+  }
+  return HMC_OK;
+}
+
+hmc_status hmc_batch_synchronize(hmc_batch* b) {
+  if (!b) return bfail(nullptr, HMC_E_INVALID, "batch is NULL");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  int flag = 0;
+  if (e == cudaSuccess && b->dev_err) e = cudaMemcpy(&flag, b->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bfail(b, HMC_E_CUDA, std::string("batch synchronize: ") + cudaGetErrorString(e));
+  if (flag) return bfail(b, HMC_E_TIMEOUT, "a bounded wait of the grouped launch gave up");
+  for (int i = 0; i < b->n; ++i) {
+    hmc_status st = hmc_synchronize(b->ctx[i]);
+    if (st != HMC_OK) return bfail(b, st, "posterior " + std::to_string(i) + ": " + hmc_last_error(b->ctx[i]));
   }
   return HMC_OK;
 }

@@ -12,8 +12,11 @@ namespace hmc {
 
 // Lane `lane` of the chain's warp owns Philox blocks j = lane + 32 b
 // (b < NB), i.e. state dims 4 j .. 4 j + 3.
+// With reduce = false the tile skips its share of the dual-averaging
+// reduction (a transition whose statistic nobody needs); returns whether this
+// tile applied the update.
 template <int TARGET, int NB>
-__device__ __forceinline__ void elementwise_tile(const StepArgs& a, int tile, int ntiles) {
+__device__ __forceinline__ bool elementwise_tile(const StepArgs& a, int tile, int ntiles, bool reduce = true) {
   constexpr int kWarpsPerBlock = 8;
   const int c = tile * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -127,7 +130,8 @@ __device__ __forceinline__ void elementwise_tile(const StepArgs& a, int tile, in
     }
     prob = accept_prob(la);
   }
-  accept_tile_finish<kWarpsPerBlock>(a.da, a.partials, prob, has_chain, a.C, a.t_full, tile, ntiles);
+  if (!reduce) return false;
+  return accept_tile_finish<kWarpsPerBlock>(a.da, a.partials, prob, has_chain, a.C, a.t_full, tile, ntiles);
 }
 
 

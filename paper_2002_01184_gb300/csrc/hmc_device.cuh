@@ -190,8 +190,9 @@ __device__ __forceinline__ void da_update(DAState* s, double alpha, long long t)
 // the last tile to arrive sums all partials in tile order (so the result does
 // not depend on arrival order), updates the state and re-arms the counter.
 // `tile` / `ntiles` index the CTAs of this posterior (the whole grid when one
-// launch serves one posterior).
-__device__ __forceinline__ void tile_partial_then_da(DAState* s, double* partials, double block_sum,
+// launch serves one posterior).  Returns, in every thread, whether this block
+// applied the update.
+__device__ __forceinline__ bool tile_partial_then_da(DAState* s, double* partials, double block_sum,
                                                      int num_chains, long long t, int tile,
                                                      int ntiles) {
   __shared__ bool last;
@@ -202,7 +203,8 @@ __device__ __forceinline__ void tile_partial_then_da(DAState* s, double* partial
     last = (prev == static_cast<unsigned int>(ntiles) - 1u);
   }
   __syncthreads();
-  if (!last) return;
+  const bool mine = last;
+  if (!mine) return false;
   __threadfence();
   double acc = 0.0;
   if (threadIdx.x < 32) {
@@ -214,6 +216,7 @@ __device__ __forceinline__ void tile_partial_then_da(DAState* s, double* partial
       __threadfence();
     }
   }
+  return true;
 }
 
 __device__ __forceinline__ void block_partial_then_da(DAState* s, double* partials, double block_sum,
@@ -226,7 +229,7 @@ __device__ __forceinline__ void block_partial_then_da(DAState* s, double* partia
 // chain pass has_chain = false), in warp order, then the deterministic grid
 // reduction and dual-averaging update.
 template <int kWarps>
-__device__ __forceinline__ void accept_tile_finish(DAState* da, double* partials, float prob,
+__device__ __forceinline__ bool accept_tile_finish(DAState* da, double* partials, float prob,
                                                    bool has_chain, int num_chains, long long t,
                                                    int tile, int ntiles) {
   __shared__ float warp_prob[kWarps];
@@ -236,7 +239,7 @@ __device__ __forceinline__ void accept_tile_finish(DAState* da, double* partials
   double sum = 0.0;
   if (threadIdx.x == 0)
     for (int i = 0; i < kWarps; ++i) sum += static_cast<double>(warp_prob[i]);
-  tile_partial_then_da(da, partials, sum, num_chains, t, tile, ntiles);
+  return tile_partial_then_da(da, partials, sum, num_chains, t, tile, ntiles);
 }
 
 template <int kWarps>

@@ -126,7 +126,9 @@ __device__ __noinline__ static void gradient(const LrArgs& a, const Smem& s, int
 }
 
 // One CTA of kLrThreads threads: chains tile * kLrTC .. + kLrTC of the posterior.
-__device__ __forceinline__ void logreg_tile(const LrArgs& a, int tile, int ntiles) {
+// With reduce = false the tile skips its share of the dual-averaging
+// reduction; returns whether this tile applied the update.
+__device__ __forceinline__ bool logreg_tile(const LrArgs& a, int tile, int ntiles, bool reduce = true) {
   extern __shared__ float smem_f[];
   const StepArgs& A = a.s;
   const int D = A.D, C = A.C;
@@ -195,7 +197,8 @@ __device__ __forceinline__ void logreg_tile(const LrArgs& a, int tile, int ntile
     }
     prob = accept_prob(la);
   }
-  accept_tile_finish<kLrThreads / 32>(A.da, A.partials, prob, has_chain, C, A.t_full, tile, ntiles);
+  if (!reduce) return false;
+  return accept_tile_finish<kLrThreads / 32>(A.da, A.partials, prob, has_chain, C, A.t_full, tile, ntiles);
 }
 
 inline size_t logreg_smem_bytes(int D) {

@@ -93,6 +93,7 @@ def _load():
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(P),
                                    ctypes.POINTER(P), ctypes.POINTER(P)],
         "hmc_batch_destroy": [P],
+        "hmc_batch_synchronize": [P],
         "hmc_sample_chain_streaming": [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P, P],
         "hmc_sample_chain_streaming_ess": [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P, P,
                                            P, P, P],
@@ -418,3 +419,7 @@ def hmc_remc_swaps(ctx):
     p = ctypes.c_void_p()
     _check(lib.hmc_remc_swaps(ctx, ctypes.byref(p)), ctx)
     return p.value
+
+
+def hmc_batch_synchronize(batch):
+    _check_batch(lib.hmc_batch_synchronize(batch), batch)

@@ -1,7 +1,8 @@
-"""Batched posteriors of uneven size in one grouped launch per transition:
-every posterior's chains must follow exactly the transitions they follow
-when the posterior is sampled alone (same seeds, same kernels), and each
-posterior adapts its own step size."""
+"""Batched posteriors of uneven size, the small ones in one persistent
+launch for all their transitions: every posterior's chains must follow
+exactly the transitions they follow when the posterior is sampled alone
+(same seeds, same kernels), each posterior adapts its own step size, and a
+grouped member's transition matches the float64 oracle."""
 import numpy as np
 import pytest
 
@@ -62,7 +63,7 @@ def test_batch_equals_each_posterior_alone(H):
                 x.copy_(dev(p.x0))
         H.hmc_batch_sample_chain(batch, xs, [p.num_burnin for p in probs],
                                  [p.num_results for p in probs], samples, eps, acc)
-        torch.cuda.synchronize()
+        H.hmc_batch_synchronize(batch)
         for i, p in enumerate(probs):
             s = Sampler(p)
             x = dev(p.x0)
@@ -82,3 +83,47 @@ def test_batch_rejects_unsupported_targets(H):
     with pytest.raises(H.HMCError) as ei:
         H.hmc_batch_create([H.make_target("corr_gauss", 8, P)], [4], [H.make_config(2, 0.1)])
     assert ei.value.status == H.HMC_E_UNSUPPORTED
+
+
+def test_grouped_members_transitions_match_oracle(H):
+    """Teacher-forced through the batch: with a fixed step size, each call
+    runs one transition (index 0) of every posterior from the state the
+    previous call left, and the float64 oracle takes the same transition from
+    the same float32 state: positions within 1e-4 per chain, accept decisions
+    equal outside the 1e-5 band (tests/parity.py's reading)."""
+    from oracle import hmc as ohmc, targets as otargets
+    from tests.parity import DECISION_BAND, POS_RTOL, chain_error
+    probs = workloads.uneven_batch(seed=9, n_logreg=3, n_funnel=2, num_burnin=0, num_results=1,
+                                   dim_range=(8, 48), n_range=(60, 300), chain_range=(9, 40),
+                                   funnel_dim_range=(10, 30))
+    dev = lambda a: torch.as_tensor(a).cuda().contiguous()
+    keep, targets, chains, configs = [], [], [], []
+    for p in probs:
+        p.adapt = False
+        p.step_size = 0.02 if p.kind == "logreg" else 0.1
+        if p.kind == "logreg":
+            p.x0 = (0.1 * np.random.default_rng(p.seed).standard_normal(p.x0.shape)).astype(np.float32)
+        Xd = dev(p.X) if p.X is not None else None
+        yd = dev(p.y) if p.y is not None else None
+        keep.append((Xd, yd))
+        targets.append(H.make_target(p.kind, p.dim, None, Xd, yd))
+        chains.append(p.num_chains)
+        configs.append(H.make_config(p.num_leapfrog, p.step_size, p.seed, False, p.target_accept, 0))
+    batch = H.hmc_batch_create(targets, chains, configs)
+    xs = [dev(p.x0) for p in probs]
+    acc = [torch.empty((1, p.num_chains), dtype=torch.uint8, device="cuda") for p in probs]
+    for rep in range(3):
+        before = [x.double().cpu().numpy() for x in xs]
+        H.hmc_batch_sample_chain(batch, xs, [0] * len(probs), [1] * len(probs), None, None, acc)
+        H.hmc_batch_synchronize(batch)
+        for i, p in enumerate(probs):
+            tgt = otargets.make(p.kind, **p.data())
+            lp, g = tgt(before[i])
+            ref = ohmc.one_step(before[i], lp, g, float(np.float32(p.step_size)), p.num_leapfrog, p.seed, 0, tgt)
+            a_gpu = acc[i][0].cpu().numpy().astype(bool)
+            near = np.abs(ref["log_u"] - ref["log_accept_ratio"]) < DECISION_BAND
+            assert np.all((a_gpu == ref["is_accepted"]) | near), (p.kind, rep)
+            same = a_gpu == ref["is_accepted"]
+            err = chain_error(xs[i].double().cpu().numpy(), ref["x"])
+            assert err[same].max() <= POS_RTOL, (p.kind, rep, err[same].max())
+    H.hmc_batch_destroy(batch)
