@@ -354,7 +354,14 @@ def run_uneven_batch(args):
         targets = [hmc.make_target(p.kind, p.dim, None, X, y) for p, (X, y) in zip(probs, data)]
         configs = [hmc.make_config(p.num_leapfrog, p.step_size, p.seed, p.adapt, p.target_accept, B)
                    for p in probs]
-        batch = hmc.hmc_batch_create(targets, [p.num_chains for p in probs], configs, stream)
+        t_tune = time.perf_counter()
+        batch = hmc.hmc_batch_create_autotuned(targets, [p.num_chains for p in probs], configs, stream)
+        t_tune = time.perf_counter() - t_tune
+        paths = [hmc.hmc_batch_member_path(batch, i)[0] for i in range(len(probs))]
+        tuner = {"create_s": t_tune,
+                 "grouped": sum(1 for q in paths if q == 0),
+                 "tensor_core_contexts": sum(1 for q in paths if q == 1),
+                 "other_contexts": sum(1 for q in paths if q == 2)}
 
         def step():
             for x, x0 in zip(xs, xs0):
@@ -365,6 +372,8 @@ def run_uneven_batch(args):
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
+    if args.plain:
+        tuner = None
     launches0 = hmc.hmc_kernel_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_host = time.perf_counter()
@@ -386,8 +395,8 @@ def run_uneven_batch(args):
                                    f"[64,4096]) + 16 funnels (d in [10,200]), L=10, DA(0.8), "
                                    f"B={B} K={K} (fraction {args.batch_scale} of 500+1000)",
                        "impl": "plain, one posterior after another" if args.plain
-                       else "grouped members in one persistent launch, side members on their own streams",
-                       "posteriors": len(probs)},
+                       else "autotuned: grouped members in one persistent launch, tensor-core members on their own streams",
+                       "posteriors": len(probs), "autotuner": tuner},
             "min_ess_per_s": ess / (ms / 1000.0), "min_ess": ess,
             "host_enqueue_ms_per_step": 1000.0 * t_enq / args.steps,
             "gpu_launches": int(launches), "clocks": clk, "roofline": None, "cpu_baseline": None,

@@ -78,9 +78,16 @@ typedef enum {
                                      Gaussians run on CTA pairs (cta_group::2) */
   HMC_IMPL_PLAIN = 1,             /* one kernel launch per operation per
                                      leapfrog step */
-  HMC_IMPL_FUSED_SINGLE_CTA = 2   /* as FUSED, but the dense-Gaussian
+  HMC_IMPL_FUSED_SINGLE_CTA = 2,  /* as FUSED, but the dense-Gaussian
                                      transition on single CTAs (32 chains,
                                      each CTA streaming P by TMA) */
+  HMC_IMPL_FUSED_TENSOR = 3,      /* as FUSED, but a logistic regression
+                                     always takes the tensor-core products
+                                     (whatever its size) */
+  HMC_IMPL_FUSED_SIMT = 4         /* as FUSED, but a logistic regression
+                                     always takes the shared-memory SIMT
+                                     transition (dim <= 512; 8 chains per
+                                     CTA tile) */
 } hmc_impl;
 
 /* Inner (uncalibrated) kernel of the Metropolis-Hastings composition,
@@ -416,6 +423,31 @@ typedef struct hmc_batch hmc_batch;
 hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
                             const int64_t* num_chains, const hmc_config* configs, void* cuda_stream,
                             hmc_batch** out);
+
+/* As hmc_batch_create, with each logistic regression's execution path
+ * chosen by measurement (an autotuner; no counterpart in the paper): the
+ * grouped launch's 8-chain shared-memory SIMT tiles, or the tensor-core
+ * products in a context of its own (128-chain x 128-row tiles on CTA pairs
+ * for dim <= 128 and dim % 4 == 0, 128 x 64 one-CTA tiles otherwise).  One
+ * transition of each path is timed on the device (after one untimed) from a
+ * zero state with the configured step size fixed, and the faster is taken;
+ * the answer is kept per shape (dim, rows, chains, leapfrog steps) for the
+ * life of the process, so later batches of the same shapes pay no
+ * measurement.  The timing runs on cuda_stream and synchronises it.  A
+ * member's result equals sampling it alone with impl HMC_IMPL_FUSED_SIMT
+ * (grouped) or HMC_IMPL_FUSED_TENSOR (tensor cores). */
+hmc_status hmc_batch_create_autotuned(int32_t num_posteriors, const hmc_target* targets,
+                                      const int64_t* num_chains, const hmc_config* configs,
+                                      void* cuda_stream, hmc_batch** out);
+
+/* How posterior i of a batch runs: *path = 0 in the grouped launch, 1 in a
+ * context of its own on the tensor-core products (autotuned), 2 in a context
+ * of its own on the path HMC_IMPL_FUSED selects (the untuned rule).  With the
+ * autotuner, ms_grouped / ms_tensor (each may be NULL) receive the measured
+ * milliseconds per transition of the two paths (+inf where a path does not
+ * apply; NaN for members the tuner did not measure). */
+hmc_status hmc_batch_member_path(const hmc_batch* batch, int32_t i, int32_t* path, double* ms_grouped,
+                                 double* ms_tensor);
 
 /* sample_chain (Section 4.2) for every posterior at once: arrays of
  * num_posteriors entries, entry i as in hmc_sample_chain for posterior i

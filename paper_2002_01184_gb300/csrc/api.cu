@@ -175,7 +175,8 @@ bool valid_config(const hmc_config* c, int64_t C, std::string* why) {
     return false;
   }
   if (c->num_adapt_steps < 0) { *why = "num_adapt_steps must be >= 0"; return false; }
-  if (c->impl != HMC_IMPL_FUSED && c->impl != HMC_IMPL_PLAIN && c->impl != HMC_IMPL_FUSED_SINGLE_CTA) {
+  if (c->impl != HMC_IMPL_FUSED && c->impl != HMC_IMPL_PLAIN && c->impl != HMC_IMPL_FUSED_SINGLE_CTA &&
+      c->impl != HMC_IMPL_FUSED_TENSOR && c->impl != HMC_IMPL_FUSED_SIMT) {
     *why = "unknown impl";
     return false;
   }
@@ -231,7 +232,7 @@ CreatePlan plan_create(const hmc_target& t, int64_t num_chains, const hmc_config
   // the random walk and NUTS run the plain path's buffers (their proposals
   // are one elementwise op or their own kernel)
   if (q.cfg.proposal != HMC_PROPOSAL_LEAPFROG) q.cfg.impl = HMC_IMPL_PLAIN;
-  const bool fused = q.cfg.impl == HMC_IMPL_FUSED || q.cfg.impl == HMC_IMPL_FUSED_SINGLE_CTA;
+  const bool fused = q.cfg.impl != HMC_IMPL_PLAIN;
   const size_t C = static_cast<size_t>(num_chains), D = static_cast<size_t>(t.dim);
   auto add = [&](size_t b) { q.bytes += std::max<size_t>(b, 16); };
   const unsigned nblk = std::max({hmc::accept_blocks(static_cast<int>(num_chains)),
@@ -251,21 +252,23 @@ CreatePlan plan_create(const hmc_target& t, int64_t num_chains, const hmc_config
   if (q.use_tc) {
     add(hmc::gauss_tc_workspace_bytes(t, num_chains));
     q.tc_fused = hmc::gauss_fused_supported(t);
-    q.tc_pair = q.tc_fused && q.cfg.impl == HMC_IMPL_FUSED;
+    q.tc_pair = q.tc_fused && q.cfg.impl != HMC_IMPL_FUSED_SINGLE_CTA;
     if (q.tc_pair) add(sizeof(unsigned));
   }
   // logistic regressions with long data passes or much work per gradient
   // (chains x rows x dim above 2^22): tensor-core products; small ones: the
   // shared-memory SIMT transition
   const bool lr_big = t.id == HMC_T_LOGREG && (t.n_data > 2048 || num_chains * t.n_data * t.dim > (1ll << 22));
-  q.use_lrtc = q.cfg.impl == HMC_IMPL_FUSED && hmc::logreg_tc_supported(t) && lr_big;
+  // (HMC_IMPL_FUSED_TENSOR and _SIMT fix the choice, for the batch's autotuner)
+  const bool lr_tensor = (q.cfg.impl == HMC_IMPL_FUSED && lr_big) || q.cfg.impl == HMC_IMPL_FUSED_TENSOR;
+  q.use_lrtc = lr_tensor && hmc::logreg_tc_supported(t);
   if (q.use_lrtc) {
     add(hmc::logreg_tc_workspace_bytes(t, num_chains));
     add(sizeof(int));
   }
   // long data passes the pair kernel does not take (dim > 128 or not a
   // multiple of 4): one-CTA tensor-core products
-  q.use_lrgemm = q.cfg.impl == HMC_IMPL_FUSED && !q.use_lrtc && hmc::logreg_gemm_supported(t) && lr_big;
+  q.use_lrgemm = lr_tensor && !q.use_lrtc && hmc::logreg_gemm_supported(t);
   if (q.use_lrgemm) add(hmc::logreg_gemm_workspace_bytes(t, num_chains));
   q.fused_logreg = fused && !q.use_lrtc && !q.use_lrgemm && hmc::logreg_fused_supported(t);
   q.fused_elementwise = fused && (t.id == HMC_T_STD_NORMAL || t.id == HMC_T_FUNNEL) &&
@@ -307,7 +310,7 @@ void release(hmc_ctx* ctx) {
 }
 
 bool fused_impl(const hmc_ctx* ctx) {
-  return ctx->cfg.impl == HMC_IMPL_FUSED || ctx->cfg.impl == HMC_IMPL_FUSED_SINGLE_CTA;
+  return ctx->cfg.impl != HMC_IMPL_PLAIN;
 }
 
 bool uses_fused_logreg(const hmc_ctx* ctx) {
@@ -1025,7 +1028,7 @@ hmc_status hmc_remc_create(const hmc_target* target, int64_t num_chains, int32_t
   // launches); the others run the plain path.
   if (target && target->id == HMC_T_LOGREG) c.impl = HMC_IMPL_PLAIN;
   if (target && target->id == HMC_T_CORR_GAUSS &&
-      !(c.impl == HMC_IMPL_FUSED && hmc::gauss_fused_supported(*target)))
+      !(c.impl != HMC_IMPL_PLAIN && c.impl != HMC_IMPL_FUSED_SINGLE_CTA && hmc::gauss_fused_supported(*target)))
     c.impl = HMC_IMPL_PLAIN;
   hmc_ctx* ctx = nullptr;
   hmc_status st = hmc_create(target, num_chains * num_replicas, &c, cuda_stream, &ctx);

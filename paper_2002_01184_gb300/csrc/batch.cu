@@ -19,7 +19,11 @@
 // its own tiles only, so every member's result equals sampling it alone.
 #include <algorithm>
 #include <cmath>
+#include <limits>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "elementwise_tile.cuh"
@@ -153,6 +157,8 @@ struct hmc_batch {
   std::vector<hmc::BatchPost> host_posts;   // grouped members only
   std::vector<int> member;                  // posterior -> index in host_posts, or -1 (side)
   std::vector<cudaStream_t> side_stream;    // per posterior (side members), else null
+  std::vector<int> path;                    // per posterior: how it runs (hmc_batch_member_path)
+  std::vector<double> ms_grouped, ms_tensor;   // the autotuner's measurements (NaN: not measured)
   std::vector<cudaEvent_t> side_done;
   cudaEvent_t fork = nullptr;
   hmc::BatchPost* dev_posts = nullptr;
@@ -210,6 +216,83 @@ double tile_cost(const hmc_target& t, const hmc_config& c) {
   return per * c.num_leapfrog * 8.0;
 }
 
+// ---- autotuner ---------------------------------------------------------------
+// A logistic regression can run as 8-chain shared-memory SIMT tiles in the
+// grouped launch or on the tensor-core products (128-chain x 128-row pair
+// tiles for dim <= 128, 128 x 64 one-CTA tiles otherwise) in a context of its
+// own.  Which is faster depends on the shape; the autotuner times one
+// transition of each path on the device (after one untimed) and keeps the
+// answer per shape for the process.
+enum { kPathGrouped = 0, kPathTensor = 1, kPathOwn = 2 };
+
+struct TuneResult {
+  int path;
+  double ms_grouped, ms_tensor;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int64_t, int64_t, int>, TuneResult> g_tune_cache;
+
+// Milliseconds per transition of `target` with C chains under `impl`, from
+// a zero state with the configuration's step size held fixed; +inf if the
+// context cannot be made.
+double time_transition(const hmc_target& t, int64_t C, const hmc_config& base, int impl, cudaStream_t s) {
+  hmc_config c = base;
+  c.impl = impl;
+  c.adapt = 0;
+  c.num_adapt_steps = 0;
+  c.use_graph = 0;
+  c.max_transitions_per_launch = 0;
+  const double inf = std::numeric_limits<double>::infinity();
+  hmc_ctx* ctx = nullptr;
+  if (hmc_create(&t, C, &c, s, &ctx) != HMC_OK) return inf;
+  float* x = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double ms = inf;
+  cudaError_t e = cudaMallocAsync(&x, sizeof(float) * C * t.dim, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, sizeof(float) * C * t.dim, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess && hmc_bootstrap(ctx, x) == HMC_OK && hmc_step(ctx, x, 0, nullptr) == HMC_OK) {
+    e = cudaEventRecord(e0, s);
+    const bool ok = e == cudaSuccess && hmc_step(ctx, x, 1, nullptr) == HMC_OK;
+    if (ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess) {
+      float f = 0.f;
+      if (cudaEventElapsedTime(&f, e0, e1) == cudaSuccess) ms = f;
+    }
+  }
+  if (hmc_synchronize(ctx) != HMC_OK) ms = inf;
+  hmc_destroy(ctx);
+  if (x) cudaFreeAsync(x, s);
+  cudaStreamSynchronize(s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGetLastError();
+  return ms;
+}
+
+TuneResult tune_logreg(const hmc_target& t, int64_t C, const hmc_config& c, cudaStream_t s) {
+  const auto key = std::make_tuple(t.dim, t.n_data, C, c.num_leapfrog);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) return it->second;
+  }
+  const double inf = std::numeric_limits<double>::infinity();
+  // (SIMT tiles for a product past 2^31 multiply-adds would take seconds per
+  // transition: the tensor cores win there without a measurement)
+  const bool simt_ok = hmc::logreg_fused_supported(t) && C * t.n_data * t.dim <= (int64_t(1) << 31);
+  const bool tensor_ok = hmc::logreg_tc_supported(t) || hmc::logreg_gemm_supported(t);
+  TuneResult r{kPathGrouped, simt_ok ? time_transition(t, C, c, HMC_IMPL_FUSED_SIMT, s) : inf,
+               tensor_ok ? time_transition(t, C, c, HMC_IMPL_FUSED_TENSOR, s) : inf};
+  r.path = r.ms_tensor < r.ms_grouped ? kPathTensor : kPathGrouped;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[key] = r;
+  return r;
+}
+
+hmc_status batch_create(int32_t num_posteriors, const hmc_target* targets, const int64_t* num_chains,
+                        const hmc_config* configs, void* cuda_stream, hmc_batch** out, bool autotune);
+
 }  // namespace
 
 extern "C" {
@@ -217,6 +300,30 @@ extern "C" {
 hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
                             const int64_t* num_chains, const hmc_config* configs, void* cuda_stream,
                             hmc_batch** out) {
+  return batch_create(num_posteriors, targets, num_chains, configs, cuda_stream, out, false);
+}
+
+hmc_status hmc_batch_create_autotuned(int32_t num_posteriors, const hmc_target* targets,
+                                      const int64_t* num_chains, const hmc_config* configs,
+                                      void* cuda_stream, hmc_batch** out) {
+  return batch_create(num_posteriors, targets, num_chains, configs, cuda_stream, out, true);
+}
+
+hmc_status hmc_batch_member_path(const hmc_batch* b, int32_t i, int32_t* path, double* ms_grouped,
+                                 double* ms_tensor) {
+  if (!b || i < 0 || i >= b->n || !path) return bfail(nullptr, HMC_E_INVALID, "bad batch, index or path");
+  *path = b->path[i];
+  if (ms_grouped) *ms_grouped = b->ms_grouped[i];
+  if (ms_tensor) *ms_tensor = b->ms_tensor[i];
+  return HMC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+hmc_status batch_create(int32_t num_posteriors, const hmc_target* targets, const int64_t* num_chains,
+                        const hmc_config* configs, void* cuda_stream, hmc_batch** out, bool autotune) {
   if (!out) return bfail(nullptr, HMC_E_INVALID, "out is NULL");
   *out = nullptr;
   if (num_posteriors < 1 || !targets || !num_chains || !configs)
@@ -242,8 +349,21 @@ hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
                    "batch posterior " + std::to_string(i) + ": batches run the leapfrog proposal only");
     }
     hmc_config c = configs[i];
-    const bool grouped = hmc::grouped_member(t, num_chains[i]);
+    bool grouped = hmc::grouped_member(t, num_chains[i]);
     c.impl = HMC_IMPL_FUSED;       // side members: tensor-core products where they apply
+    int path = grouped ? kPathGrouped : kPathOwn;
+    double msg = std::nan(""), mst = std::nan("");
+    if (autotune && t.id == HMC_T_LOGREG) {
+      const TuneResult r = tune_logreg(t, num_chains[i], c, static_cast<cudaStream_t>(cuda_stream));
+      path = r.path;
+      msg = r.ms_grouped;
+      mst = r.ms_tensor;
+      grouped = path == kPathGrouped;
+      c.impl = grouped ? HMC_IMPL_FUSED_SIMT : HMC_IMPL_FUSED_TENSOR;
+    }
+    b->path.push_back(path);
+    b->ms_grouped.push_back(msg);
+    b->ms_tensor.push_back(mst);
     // side members replay their own graph: enqueueing thousands of launches
     // eagerly would fill the launch queue and serialise the side streams
     c.use_graph = grouped ? 0 : 1;
@@ -328,6 +448,10 @@ hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
   *out = b;
   return HMC_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 hmc_status hmc_batch_sample_chain(hmc_batch* b, float* const* x_inout, const int64_t* num_burnin,
                                   const int64_t* num_results, float* const* samples_out,

@@ -17,7 +17,7 @@ STATUS_NAMES = ["HMC_OK", "HMC_E_INVALID", "HMC_E_OOM", "HMC_E_CUDA", "HMC_E_TIM
                 "HMC_E_UNSUPPORTED"]
 HMC_T_STD_NORMAL, HMC_T_CORR_GAUSS, HMC_T_LOGREG, HMC_T_FUNNEL = range(4)
 TARGET_IDS = {"std_normal": 0, "corr_gauss": 1, "logreg": 2, "funnel": 3}
-HMC_IMPL_FUSED, HMC_IMPL_PLAIN, HMC_IMPL_FUSED_SINGLE_CTA = 0, 1, 2
+HMC_IMPL_FUSED, HMC_IMPL_PLAIN, HMC_IMPL_FUSED_SINGLE_CTA, HMC_IMPL_FUSED_TENSOR, HMC_IMPL_FUSED_SIMT = range(5)
 HMC_PROPOSAL_LEAPFROG, HMC_PROPOSAL_RANDOM_WALK, HMC_PROPOSAL_NUTS = 0, 1, 2
 
 
@@ -94,6 +94,10 @@ def _load():
                                    ctypes.POINTER(P), ctypes.POINTER(P)],
         "hmc_batch_destroy": [P],
         "hmc_batch_synchronize": [P],
+        "hmc_batch_create_autotuned": [ctypes.c_int32, ctypes.POINTER(hmc_target), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(hmc_config), P, ctypes.POINTER(P)],
+        "hmc_batch_member_path": [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
         "hmc_sample_chain_streaming": [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P, P],
         "hmc_sample_chain_streaming_ess": [P, P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P, P,
                                            P, P, P],
@@ -386,6 +390,26 @@ def hmc_batch_create(targets, num_chains, configs, stream=None):
     out = ctypes.c_void_p()
     _check_batch(lib.hmc_batch_create(n, T, Cs, G, _stream(stream), ctypes.byref(out)), None)
     return out.value
+
+
+def hmc_batch_create_autotuned(targets, num_chains, configs, stream=None):
+    n = len(targets)
+    T = (hmc_target * n)(*targets)
+    Cs = (ctypes.c_int64 * n)(*[int(c) for c in num_chains])
+    G = (hmc_config * n)(*configs)
+    out = ctypes.c_void_p()
+    _check_batch(lib.hmc_batch_create_autotuned(n, T, Cs, G, _stream(stream), ctypes.byref(out)), None)
+    return out.value
+
+
+def hmc_batch_member_path(batch, i):
+    """(path, ms_grouped, ms_tensor) of posterior i: path 0 grouped launch,
+    1 own context on tensor cores (autotuned), 2 own context (untuned rule)."""
+    path = ctypes.c_int32()
+    mg, mt = ctypes.c_double(), ctypes.c_double()
+    _check_batch(lib.hmc_batch_member_path(batch, int(i), ctypes.byref(path), ctypes.byref(mg),
+                                           ctypes.byref(mt)), batch)
+    return int(path.value), float(mg.value), float(mt.value)
 
 
 def hmc_batch_sample_chain(batch, xs, num_burnin, num_results, samples=None, trace_step_size=None,

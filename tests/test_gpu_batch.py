@@ -127,3 +127,51 @@ def test_grouped_members_transitions_match_oracle(H):
             err = chain_error(xs[i].double().cpu().numpy(), ref["x"])
             assert err[same].max() <= POS_RTOL, (p.kind, rep, err[same].max())
     H.hmc_batch_destroy(batch)
+
+
+def test_autotuned_batch_equals_each_posterior_alone_on_its_chosen_path(H):
+    """The autotuner times each logistic regression's two paths (grouped SIMT
+    tiles, tensor-core products in a context of its own) and the batch runs
+    each on the faster: a member then equals sampling it alone with the
+    matching impl, bit for bit.  A second batch of the same shapes reuses
+    the cached choices."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    probs = small_batch()
+    dev = lambda a: torch.as_tensor(a).cuda().contiguous()
+    keep, targets, chains, configs = [], [], [], []
+    for p in probs:
+        Xd = dev(p.X) if p.X is not None else None
+        yd = dev(p.y) if p.y is not None else None
+        keep.append((Xd, yd))
+        targets.append(H.make_target(p.kind, p.dim, None, Xd, yd))
+        chains.append(p.num_chains)
+        configs.append(H.make_config(p.num_leapfrog, p.step_size, p.seed, p.adapt, p.target_accept,
+                                     p.num_burnin))
+    batch = H.hmc_batch_create_autotuned(targets, chains, configs)
+    paths = [H.hmc_batch_member_path(batch, i) for i in range(len(probs))]
+    for p, (path, mg, mt) in zip(probs, paths):
+        if p.kind == "logreg":
+            assert path in (0, 1)
+            assert np.isfinite(min(mg, mt)) and (mt < mg) == (path == 1)
+        else:
+            assert path == 0
+    xs = [dev(p.x0) for p in probs]
+    samples = [torch.empty((p.num_results, p.num_chains, p.dim), device="cuda") for p in probs]
+    H.hmc_batch_sample_chain(batch, xs, [p.num_burnin for p in probs], [p.num_results for p in probs], samples)
+    H.hmc_batch_synchronize(batch)
+    for i, (p, (path, _, _)) in enumerate(zip(probs, paths)):
+        impl = H.HMC_IMPL_FUSED
+        if p.kind == "logreg":
+            impl = H.HMC_IMPL_FUSED_TENSOR if path == 1 else H.HMC_IMPL_FUSED_SIMT
+        s = Sampler(p, impl=impl)
+        x = dev(p.x0)
+        smp, _, _ = s.sample_chain(x, p.num_burnin, p.num_results)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(xs[i].cpu().numpy(), x.cpu().numpy())
+        np.testing.assert_array_equal(samples[i].cpu().numpy(), smp.cpu().numpy())
+        s.close()
+    again = H.hmc_batch_create_autotuned(targets, chains, configs)
+    cached = [H.hmc_batch_member_path(again, i) for i in range(len(probs))]
+    np.testing.assert_array_equal(np.array(cached), np.array(paths))    # NaN-aware: untimed members
+    H.hmc_batch_destroy(again)
+    H.hmc_batch_destroy(batch)
