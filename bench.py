@@ -513,8 +513,11 @@ def main():
     torch.cuda.synchronize()
     evals_per_step = C * p.num_leapfrog * (B + K) + C
     nuts = proposal == hmc.HMC_PROPOSAL_NUTS
+    nuts_dense = nuts and p.kind in ("corr_gauss", "logreg")
     if nuts:
         leaves0 = hmc.hmc_nuts_leapfrog_count(s.ctx)
+    if nuts_dense:
+        iters0 = hmc.hmc_nuts_leaf_iterations(s.ctx)
     clocks = ClockSampler(local)
     clocks.start()
     hmc.hmc_profile_dominant_kernel(s.ctx, 8)
@@ -536,6 +539,16 @@ def main():
         # the trees' sizes vary: count the leapfrog steps the timed steps built
         # (identical every step: same start, same seed) and the bootstrap
         evals_per_step = (hmc.hmc_nuts_leapfrog_count(s.ctx) - leaves0) / args.steps + C
+    nuts_info = None
+    if nuts_dense:
+        # lockstep leaves: each loop iteration is one batched gradient (tile
+        # products of the chains still building) and one leaf kernel; the
+        # launch count above has each transition's loop body once
+        iters = (hmc.hmc_nuts_leaf_iterations(s.ctx) - iters0) / args.steps
+        per_iter = 2 if p.kind == "corr_gauss" else 3
+        launches += int(round((iters - (B + K)) * per_iter * args.steps))
+        nuts_info = {"leaf_iterations_per_step": iters, "leapfrog_steps_per_step": evals_per_step - C,
+                     "useful_row_fraction": (evals_per_step - C) / (iters * C)}
     try:
         prof = hmc.hmc_profile_read(s.ctx)
     except hmc.HMCError as exc:              # timing support only
@@ -685,6 +698,8 @@ def main():
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk,
         }
+        if nuts_info:
+            line["nuts_lockstep"] = nuts_info
         print(json.dumps(line), flush=True)
     s.close()
     if world > 1:

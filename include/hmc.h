@@ -104,9 +104,20 @@ typedef enum {
   HMC_PROPOSAL_NUTS = 2          /* the No-U-Turn Sampler (Section 2.3) with the
                                     recursion unrolled: num_leapfrog is the
                                     maximum tree depth (1..10, at most 2^depth - 1
-                                    leapfrog steps per transition); targets
-                                    STD_NORMAL and FUNNEL with dim <= 512
-                                    (HMC_E_UNSUPPORTED otherwise); the step size
+                                    leapfrog steps per transition); dim <= 512,
+                                    for CORR_GAUSS a multiple of 4
+                                    (HMC_E_UNSUPPORTED otherwise).  STD_NORMAL
+                                    and FUNNEL: one warp per chain, each chain's
+                                    tree independent; CORR_GAUSS and LOGREG: the
+                                    chains advance in lockstep, one leaf per
+                                    iteration (tensor-core gradient products of
+                                    the chains still building, then one leaf
+                                    kernel), the iterations a conditional node
+                                    of a CUDA graph: a call that enqueues
+                                    transitions on a stream that is not
+                                    capturing captures them on the context's
+                                    private stream and launches the graph; the
+                                    impl field is ignored; the step size
                                     adapts to the mean over a tree's leaves of
                                     min(1, exp(H0 - H)); is_accepted reports
                                     whether the state moved, log_accept_ratio
@@ -335,6 +346,14 @@ hmc_status hmc_profile_read(hmc_ctx* ctx, double* avg_ms, uint64_t* samples, uin
  * transition).  Synchronises the context's stream.  HMC_E_INVALID if the
  * context does not run NUTS. */
 hmc_status hmc_nuts_leapfrog_count(hmc_ctx* ctx, uint64_t* out);
+
+/* NUTS on a dense target (CORR_GAUSS, LOGREG): the leaf iterations run on
+ * this context since it was created -- one batched gradient of the chains
+ * still building their trees each, so hmc_nuts_leapfrog_count /
+ * (iterations x num_chains) is the fraction of chain rows that did useful
+ * work.  Synchronises the context's stream.  HMC_E_INVALID for any other
+ * context. */
+hmc_status hmc_nuts_leaf_iterations(hmc_ctx* ctx, uint64_t* out);
 
 /* The composition's two halves as separate calls (Section 4.1:
  * MetropolisHastings wrapping an uncalibrated kernel).  hmc_step is exactly

@@ -49,6 +49,8 @@ struct hmc_ctx {
   unsigned* grid_bar = nullptr;  // grid barrier of the multi-transition pair launch
   float* nuts_scratch = nullptr;           // NUTS: trajectory ends, candidates, span starts
   unsigned long long* nuts_leaves = nullptr;   // NUTS: leapfrog steps so far
+  bool nuts_dense = false;      // NUTS on a dense target: lockstep leaves, tensor-core products
+  hmc::NutsDense nd;
   int64_t dom_transitions = 1;   // transitions per launch of the dominant kernel (last chain)
   bool use_lrtc = false;        // tensor-core logistic-regression path (CTA pairs, dim <= 128)
   hmc::LogregTc lrtc;
@@ -222,6 +224,7 @@ struct CreatePlan {
   bool use_tc = false, tc_fused = false, tc_pair = false;
   bool use_lrtc = false, use_lrgemm = false;
   bool fused_logreg = false, fused_elementwise = false, plain_buffers = false;
+  bool nuts_dense = false;
   size_t grad_ws = 0;
   uint64_t bytes = 0;      // sum of the allocation requests, each at least 16 bytes
 };
@@ -247,6 +250,25 @@ CreatePlan plan_create(const hmc_target& t, int64_t num_chains, const hmc_config
   if (q.cfg.proposal == HMC_PROPOSAL_NUTS) {
     add(4 * hmc::nuts_scratch_floats(t, num_chains));
     add(sizeof(unsigned long long));
+    // dense targets: the tensor-core products' workspace, the trees' state,
+    // the active flags, the loop counters and the iteration count
+    q.nuts_dense = (t.id == HMC_T_CORR_GAUSS || t.id == HMC_T_LOGREG) && hmc::nuts_dense_supported(t);
+    if (q.nuts_dense) {
+      if (t.id == HMC_T_CORR_GAUSS) {
+        q.use_tc = true;
+        add(hmc::gauss_tc_workspace_bytes(t, num_chains));
+      } else {
+        q.use_lrgemm = true;
+        add(hmc::logreg_gemm_workspace_bytes(t, num_chains));
+      }
+      add(hmc::nuts_dense_chain_bytes(num_chains));
+      add(C);
+      add(4 * sizeof(unsigned));
+      add(sizeof(unsigned long long));
+      q.grad_ws = hmc::grad_workspace_bytes(t, num_chains);
+      if (q.grad_ws) add(q.grad_ws);
+      return q;
+    }
   }
   q.use_tc = fused && hmc::gauss_tc_supported(t);
   if (q.use_tc) {
@@ -299,6 +321,8 @@ void release(hmc_ctx* ctx) {
   ctx->cap_stream = nullptr;
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   ctx->copy_stream = nullptr;
+  if (ctx->nd.side) cudaStreamDestroy(ctx->nd.side);
+  ctx->nd.side = nullptr;
   if (ctx->seg_ready) cudaEventDestroy(ctx->seg_ready);
   ctx->seg_ready = nullptr;
   if (ctx->copies_done) cudaEventDestroy(ctx->copies_done);
@@ -346,6 +370,8 @@ StepArgs make_args(hmc_ctx* ctx, float* x, uint64_t t) {
 }
 
 cudaError_t enqueue_transition(hmc_ctx* ctx, const StepArgs& a) {
+  if (ctx->nuts_dense)      // (the stream is capturing: see run_captured)
+    return hmc::launch_nuts_dense_transition(ctx->target, a, ctx->nd, ctx->stream, &ctx->timer);
   if (ctx->cfg.proposal == HMC_PROPOSAL_NUTS)
     return hmc::launch_nuts_transition(ctx->target, a, ctx->nuts_scratch, ctx->cfg.num_leapfrog,
                                        ctx->nuts_leaves, ctx->stream, &ctx->timer);
@@ -370,6 +396,8 @@ hmc_status check_device_flag(hmc_ctx* ctx) {
                                   cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "read device error flag");
+  if (flag == 2 && ctx->nuts_dense)
+    return fail(ctx, HMC_E_TIMEOUT, "the NUTS leaf loop ran past 2^max_depth iterations and was stopped");
   if (flag)
     return fail(ctx, HMC_E_TIMEOUT,
                 "a tensor-core kernel's bounded wait gave up (site " + std::to_string(flag) + ")");
@@ -388,11 +416,59 @@ hmc_status bootstrap(hmc_ctx* ctx, const float* x0) {
   return HMC_OK;
 }
 
+// Work whose enqueueing needs a capturing stream (the dense NUTS leaf loop is
+// a conditional graph node): run `body` directly when the context's stream
+// is capturing already (the sample_chain graph, or a caller's capture);
+// otherwise capture it on the private stream, then instantiate, launch on
+// the context's stream and release the graph (freed when it completes).
+template <typename F>
+hmc_status run_captured(hmc_ctx* ctx, F&& body) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(ctx->stream, &cs);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "capture query");
+  if (cs == cudaStreamCaptureStatusActive) return body();
+  if (!ctx->cap_stream) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "capture stream");
+  cudaStream_t user = ctx->stream;
+  ctx->stream = ctx->cap_stream;
+  e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    ctx->stream = user;
+    return cuda_fail(ctx, e, "begin capture");
+  }
+  hmc_status st = body();
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(ctx->cap_stream, &g);
+  ctx->stream = user;
+  if (st != HMC_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "end capture");
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+  e = cudaGraphLaunch(ex, user);
+  cudaGraphExecDestroy(ex);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+  return HMC_OK;
+}
+
 // Transitions t_begin .. t_end - 1 of a chain with B burn-in transitions
 // (transition B + k writes kept sample k - out0 of the output buffers), after
 // the bootstrap.
 hmc_status enqueue_range(hmc_ctx* ctx, float* x, int64_t B, int64_t t_begin, int64_t t_end,
                          float* samples, float* trace_eps, uint8_t* trace_acc, int64_t out0 = 0) {
+  if (ctx->nuts_dense) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(ctx->stream, &cs);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "capture query");
+    if (cs != cudaStreamCaptureStatusActive)
+      return run_captured(ctx, [&] {
+        return enqueue_range(ctx, x, B, t_begin, t_end, samples, trace_eps, trace_acc, out0);
+      });
+  }
   const int64_t CD = ctx->C * ctx->target.dim;
   // dense Gaussian on CTA pairs: the chain's transitions in as few launches
   // as allowed (all of them in one cooperative launch by default)
@@ -425,7 +501,7 @@ hmc_status enqueue_range(hmc_ctx* ctx, float* x, int64_t B, int64_t t_begin, int
   // launches as allowed, so that each chain's tree sizes average out over
   // the run (those that adapt need every chain's statistic in between)
   int64_t t_multi = t_end;
-  if (ctx->cfg.proposal == HMC_PROPOSAL_NUTS && ctx->K == 1 && !ctx->s_mean)
+  if (ctx->cfg.proposal == HMC_PROPOSAL_NUTS && !ctx->nuts_dense && ctx->K == 1 && !ctx->s_mean)
     t_multi = std::min<int64_t>(
         t_end, std::max<int64_t>(t_begin, ctx->cfg.adapt ? ctx->cfg.num_adapt_steps : 0));
   for (int64_t t = t_begin; t < t_multi; ++t) {
@@ -559,8 +635,10 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   *out = nullptr;
   if (!valid_target(target, num_chains, &why)) return fail(nullptr, HMC_E_INVALID, why);
   if (!valid_config(config, num_chains, &why)) return fail(nullptr, HMC_E_INVALID, why);
-  if (config->proposal == HMC_PROPOSAL_NUTS && !hmc::nuts_supported(*target))
-    return fail(nullptr, HMC_E_UNSUPPORTED, "NUTS runs the STD_NORMAL and FUNNEL targets with dim <= 512");
+  if (config->proposal == HMC_PROPOSAL_NUTS && !hmc::nuts_supported(*target) &&
+      !hmc::nuts_dense_supported(*target))
+    return fail(nullptr, HMC_E_UNSUPPORTED,
+                "NUTS runs targets with dim <= 512 (CORR_GAUSS: dim a multiple of 4)");
   hmc_ctx* ctx = new (std::nothrow) hmc_ctx();
   if (!ctx) return fail(nullptr, HMC_E_OOM, "host allocation failed");
   const CreatePlan plan = plan_create(*target, num_chains, *config);
@@ -611,6 +689,27 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     char* w = nullptr;
     e = ctx_alloc(ctx, &w, hmc::logreg_gemm_workspace_bytes(*target, num_chains));
     if (e == cudaSuccess) e = hmc::logreg_gemm_setup(&ctx->lrg, *target, num_chains, w, ctx->stream);
+  }
+  ctx->nuts_dense = plan.nuts_dense;
+  if (e == cudaSuccess && ctx->nuts_dense) {
+    hmc::NutsDense& nd = ctx->nd;
+    nd.mode = target->id == HMC_T_CORR_GAUSS ? 0 : 1;
+    nd.tc = &ctx->tc;
+    nd.lrg = &ctx->lrg;
+    nd.err = nd.mode == 0 ? ctx->tc.err : ctx->lrg.err;
+    nd.scratch = ctx->nuts_scratch;
+    nd.leaves = ctx->nuts_leaves;
+    nd.max_depth = ctx->cfg.num_leapfrog;
+    char* ch = nullptr;
+    e = ctx_alloc(ctx, &ch, hmc::nuts_dense_chain_bytes(num_chains));
+    nd.chains = ch;
+    if (e == cudaSuccess) e = ctx_alloc(ctx, &nd.active, C);
+    if (e == cudaSuccess) e = ctx_alloc(ctx, &nd.ctr, 4);
+    if (e == cudaSuccess) e = ctx_alloc(ctx, &nd.iters, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(nd.ctr, 0, 4 * sizeof(unsigned), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(nd.iters, 0, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = hmc::nuts_dense_prepare();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&nd.side, cudaStreamNonBlocking);
   }
   if (e == cudaSuccess && plan.fused_logreg) e = hmc::logreg_fused_setup(*target);
   if (e == cudaSuccess && plan.plain_buffers) {
@@ -673,7 +772,16 @@ hmc_status hmc_step(hmc_ctx* ctx, float* x_inout, uint64_t t, hmc_kernel_results
   if (t > std::numeric_limits<uint32_t>::max())
     return fail(ctx, HMC_E_INVALID, "transition index must fit in 32 bits");
   StepArgs a = make_args(ctx, x_inout, t);
-  cudaError_t e = enqueue_transition(ctx, a);
+  cudaError_t e = cudaSuccess;
+  if (ctx->nuts_dense) {
+    hmc_status st = run_captured(ctx, [&] {
+      const cudaError_t le = enqueue_transition(ctx, make_args(ctx, x_inout, t));
+      return le == cudaSuccess ? HMC_OK : cuda_fail(ctx, le, "transition launch");
+    });
+    if (st != HMC_OK) return st;
+  } else {
+    e = enqueue_transition(ctx, a);
+  }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "transition launch");
   if (ctx->K > 1) {
     e = hmc::launch_remc_swap(ctx->outer_chains, ctx->K, ctx->target.dim, x_inout, ctx->lp, ctx->g,
@@ -715,6 +823,18 @@ hmc_status hmc_nuts_leapfrog_count(hmc_ctx* ctx, uint64_t* out) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(&v, ctx->nuts_leaves, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "read leapfrog count");
+  *out = static_cast<uint64_t>(v);
+  return HMC_OK;
+}
+
+hmc_status hmc_nuts_leaf_iterations(hmc_ctx* ctx, uint64_t* out) {
+  if (!ctx || !out) return fail(ctx, HMC_E_INVALID, "NULL argument");
+  if (!ctx->nuts_dense) return fail(ctx, HMC_E_INVALID, "the context does not run NUTS on a dense target");
+  unsigned long long v = 0;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, ctx->nd.iters, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "read leaf iterations");
   *out = static_cast<uint64_t>(v);
   return HMC_OK;
 }
@@ -1119,7 +1239,10 @@ hmc_status hmc_dominant_kernel_info(const hmc_ctx* ctx, char* name, int32_t name
     return fail(nullptr, HMC_E_INVALID, "NULL argument");
   const char* n = "";
   int64_t per = ctx->C;
-  if (ctx->cfg.proposal == HMC_PROPOSAL_NUTS) {
+  if (ctx->nuts_dense) {
+    // a whole transition (leaf iterations of tile products + leaf kernel)
+    n = "nuts_dense_transition";
+  } else if (ctx->cfg.proposal == HMC_PROPOSAL_NUTS) {
     n = "k_nuts";          // leapfrog steps per launch vary: hmc_nuts_leapfrog_count
   } else if (ctx->use_tc && ctx->tc.fused && ctx->tc.pair) {
     n = "k_gauss_pair";

@@ -82,6 +82,7 @@ struct TcStepArgs {
   int ntn;                  // lp_part row stride
   const DAState* da;
   int* err;                 // set to 1 if a bounded wait gave up
+  const uint8_t* active;    // null, or per-chain flags: a tile with none set is skipped
 };
 
 template <int EPI>
@@ -99,6 +100,12 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+  if (a.active) {
+    // NUTS: a tile whose chains have all finished their trees has no work
+    const int r = threadIdx.x;
+    const bool mine = r < kBM && m0 + r < a.C && a.active[m0 + r] != 0;
+    if (!__syncthreads_or(mine)) return;
+  }
   const int nk_all = (a.K + kBK - 1) / kBK;
   const int kc0 = EPI == kEpiStore ? static_cast<int>(blockIdx.z) * a.kc_split : 0;
   const int nk = EPI == kEpiStore ? min(a.kc_split, nk_all - kc0) : nk_all;
@@ -510,6 +517,9 @@ cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws
   if (!ok) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiGauss>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(kSmemBytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiStore>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemBytes));
   if (e != cudaSuccess) return e;
   if (gauss_fused_supported(t)) {
     e = gauss_fused_setup();
@@ -579,6 +589,26 @@ cudaError_t launch_gauss_tc_transition(const StepArgs& a, GaussTc& tc, cudaStrea
 }
 
 
+cudaError_t launch_gauss_tc_product(GaussTc& tc, int C, int D, const DAState* da, const uint8_t* active,
+                                    cudaStream_t s) {
+  TcStepArgs st{};
+  st.C = C;
+  st.D = D;
+  st.ld = D;
+  st.K = D;
+  st.ncols = D;
+  st.kc_split = (D + kBK - 1) / kBK;
+  st.part = tc.gL;
+  st.da = da;
+  st.err = tc.err;
+  st.active = active;
+  const dim3 grid((C + kBM - 1) / kBM, tc.ntn, 1);
+  k_gauss_tc_step<kEpiStore><<<grid, kThreads, kSmemBytes, s>>>(tc.mAhi[0], tc.mAlo[0], tc.mBhi, tc.mBlo, st);
+  count_launch();
+  return cudaGetLastError();
+}
+
+
 bool logreg_gemm_supported(const hmc_target& t) {
   return t.id == HMC_T_LOGREG && t.n_data >= 1 && encode_fn() != nullptr;
 }
@@ -590,6 +620,23 @@ int64_t lr_npad(int64_t n) { return (n + kBN - 1) / kBN * kBN; }
 // the most K-splits of the gradient product G = R X
 constexpr int kMaxSplit = 8;
 size_t a1k(size_t b) { return (b + 1023) & ~static_cast<size_t>(1023); }
+
+// G = R X has K = Npad but only (C / 128) x ndt tiles: split K when the tiles
+// would not fill two waves of the SMs, and sum the splits afterwards
+void lr_splits(const LogregGemm& g, int C, int* S_out, int* kc_out) {
+  const int64_t mt = (C + kBM - 1) / kBM;
+  const int nk_all = g.npad / kBK;
+  const int64_t tiles = mt * g.ndt;
+  int S = 1, kc_split = nk_all;
+  const int64_t sms = g.sms;
+  if (tiles < 2 * sms && nk_all >= 2) {
+    S = static_cast<int>(std::min<int64_t>({kMaxSplit, (2 * sms + tiles - 1) / tiles, nk_all}));
+    kc_split = (nk_all + S - 1) / S;
+    S = (nk_all + kc_split - 1) / kc_split;      // every split has at least one chunk
+  }
+  *S_out = S;
+  *kc_out = kc_split;
+}
 }  // namespace
 
 size_t logreg_gemm_workspace_bytes(const hmc_target& t, int64_t C) {
@@ -684,17 +731,8 @@ cudaError_t launch_logreg_gemm_transition(const StepArgs& a, LogregGemm& g, cuda
   k_gauss_tc_begin<<<nb, 32 * kWarpsPerBlock, 0, s>>>(b);
   count_launch();
   const unsigned mt = static_cast<unsigned>((a.C + kBM - 1) / kBM);
-  // G = R X has K = Npad but only mt x ndt tiles: split K when the tiles
-  // would not fill two waves of the SMs, and sum the splits afterwards
-  const int nk_all = g.npad / kBK;
-  const int64_t tiles = static_cast<int64_t>(mt) * g.ndt;
-  int S = 1, kc_split = nk_all;
-  const int64_t sms = g.sms;
-  if (tiles < 2 * sms && nk_all >= 2) {
-    S = static_cast<int>(std::min<int64_t>({kMaxSplit, (2 * sms + tiles - 1) / tiles, nk_all}));
-    kc_split = (nk_all + S - 1) / S;
-    S = (nk_all + kc_split - 1) / kc_split;      // every split has at least one chunk
-  }
+  int S = 1, kc_split = 1;
+  lr_splits(g, a.C, &S, &kc_split);
   for (int l = 1; l <= a.L; ++l) {
     const int in = (l - 1) & 1, out = l & 1;
     const bool last = l == a.L;
@@ -756,6 +794,49 @@ cudaError_t launch_logreg_gemm_transition(const StepArgs& a, LogregGemm& g, cuda
   b.xlo = g.xlo[(a.L - 1) & 1];
   k_gauss_tc_accept<<<nb, 32 * kWarpsPerBlock, 0, s>>>(b);
   count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_logreg_gemm_products(LogregGemm& g, int C, int D, const DAState* da,
+                                        const uint8_t* active, int* splits, cudaStream_t s) {
+  const unsigned mt = static_cast<unsigned>((C + kBM - 1) / kBM);
+  int S = 1, kc_split = 1;
+  lr_splits(g, C, &S, &kc_split);
+  TcStepArgs z{};
+  z.C = C;
+  z.D = D;
+  z.ld = g.ld;
+  z.K = g.ld;
+  z.ncols = g.npad;
+  z.nvalid = g.nvalid;
+  z.y = g.ypad;
+  z.rhi = g.Rhi;
+  z.rlo = g.Rlo;
+  z.ldr = g.npad;
+  z.lp_col0 = 0;
+  z.last = 1;                  // the rows' log-likelihood partials: log p at every leaf
+  z.lp_part = g.lp_part;
+  z.ntn = g.ntot;
+  z.da = da;
+  z.err = g.err;
+  z.active = active;
+  TcStepArgs st{};
+  st.C = C;
+  st.D = D;
+  st.ld = g.ld;
+  st.K = g.npad;
+  st.ncols = D;
+  st.kc_split = kc_split;
+  st.part = g.part;
+  st.da = da;
+  st.err = g.err;
+  st.active = active;
+  k_gauss_tc_step<kEpiLrResid><<<dim3(mt, g.nrt), kThreads, kSmemBytes, s>>>(g.mThi[0], g.mTlo[0], g.mXhi,
+                                                                           g.mXlo, z);
+  k_gauss_tc_step<kEpiStore><<<dim3(mt, g.ndt, S), kThreads, kSmemBytes, s>>>(g.mRhi, g.mRlo, g.mXThi, g.mXTlo,
+                                                                            st);
+  count_launch(2);
+  *splits = S;
   return cudaGetLastError();
 }
 

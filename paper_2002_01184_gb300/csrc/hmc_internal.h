@@ -249,6 +249,8 @@ size_t logreg_gemm_workspace_bytes(const hmc_target& t, int64_t C);
 cudaError_t logreg_gemm_setup(LogregGemm* g, const hmc_target& t, int64_t C, void* ws, cudaStream_t s);
 cudaError_t launch_logreg_gemm_transition(const StepArgs& a, LogregGemm& g, cudaStream_t s,
                                           KernelTimer* timer);
+cudaError_t launch_logreg_gemm_products(LogregGemm& g, int C, int D, const DAState* da,
+                                        const uint8_t* active, int* splits, cudaStream_t s);
 
 bool gauss_tc_supported(const hmc_target& t);
 size_t gauss_tc_workspace_bytes(const hmc_target& t, int64_t C);
@@ -285,6 +287,15 @@ cudaError_t launch_gauss_fused_transition(const StepArgs& a, GaussTc& tc, cudaSt
                                           KernelTimer* timer);
 cudaError_t launch_gauss_tc_transition(const StepArgs& a, GaussTc& tc, cudaStream_t s,
                                        KernelTimer* timer);
+// NUTS on the dense targets: the gradient products of the positions in the
+// first trajectory buffer (xhi[0] / xlo[0]).  `active` marks the chains still
+// building their trees; a 128-chain tile with none marked is skipped.
+//   Gaussian: X P into tc.gL [C x D] (the gradient is its negative).
+//   Logistic regression: R = y - sigmoid(Theta X^T) with the rows'
+//   log-likelihood partials in lp_part columns 0 .. nrt - 1, then the
+//   *splits K-splits of R X into g.part [splits x C x ld].
+cudaError_t launch_gauss_tc_product(GaussTc& tc, int C, int D, const DAState* da, const uint8_t* active,
+                                    cudaStream_t s);
 
 }  // namespace hmc
 
@@ -316,3 +327,31 @@ cudaError_t launch_logreg_tc_transition(const StepArgs& a, LogregTc& tc, int* er
 
 }  // namespace hmc
 
+namespace hmc {
+
+// NUTS on the dense targets (nuts_dense.cu): the chains advance one leaf per
+// iteration of a CUDA-graph WHILE node; see that file.
+struct NutsDense {
+  int mode = 0;                   // 0: Gaussian (GaussTc products), 1: logistic regression (LogregGemm)
+  GaussTc* tc = nullptr;
+  LogregGemm* lrg = nullptr;
+  void* chains = nullptr;         // per-chain tree state [C]
+  uint8_t* active = nullptr;      // [C] chains still building their trees
+  unsigned* ctr = nullptr;        // [4] leaf-loop counters
+  int* err = nullptr;             // the products' flag; 2: the leaf loop ran past its bound
+  float* scratch = nullptr;       // [C][kNutsSlots][ld]
+  unsigned long long* leaves = nullptr;   // leapfrog steps of the chains (useful gradients)
+  unsigned long long* iters = nullptr;    // leaf iterations (batched gradients) so far
+  int max_depth = 10;
+  cudaStream_t side = nullptr;    // stream the loop body is captured on
+};
+bool nuts_dense_supported(const hmc_target& t);
+size_t nuts_dense_chain_bytes(int64_t C);
+cudaError_t nuts_dense_prepare();
+// One transition; `s` must be capturing into a graph (the leaf loop is a
+// conditional node of it).  sample_out / trace_acc / trace_eps of `a` are
+// this transition's output rows or null.
+cudaError_t launch_nuts_dense_transition(const hmc_target& t, const StepArgs& a, NutsDense& nd, cudaStream_t s,
+                                         KernelTimer* timer);
+
+}  // namespace hmc

@@ -18,60 +18,16 @@
 // ends and the two candidates in a per-chain scratch of kNutsSlots slots of
 // D floats.
 //
-// Random choices: directions from word 0 of counter (0, chain, t, 3), the
-// subtree's choice at leaf k of doubling j from word k mod 4 of counter
-// (k / 4, chain, t, 4 + j) (one generator call per four leaves), the
-// top-level choice at doubling j from counter (j, chain, t, 14); a choice of
-// probability a / b is taken iff (2 w + 1) b < a 2^33 (exact integers).
+// The random streams and the choice rule are those of nuts_common.cuh.
 #include <cmath>
 
-#include "hmc_device.cuh"
-#include "hmc_internal.h"
+#include "nuts_common.cuh"
 
 namespace hmc {
 
 namespace {
 
 constexpr int kWarps = 4;
-constexpr uint32_t kTagDirection = 3u, kTagSubtree = 4u, kTagTop = 14u;
-constexpr float kDeltaMax = 1000.f;
-constexpr int kMaxDepth = 10;
-// slots: 0-2 left end x, p, g; 3-5 right end; 6-7 candidate x, g;
-// 8-9 subtree candidate x, g; 10 + 2 (i - 1), + 1: first leaf x, p of level i
-// (scratch form of the span starts)
-constexpr int kSlotLeft = 0, kSlotRight = 3, kSlotCand = 6, kSlotSub = 8, kSlotSpan = 10;
-static_assert(kSlotSpan + 2 * (kMaxDepth - 1) <= kNutsSlots, "scratch slots");
-
-__device__ __forceinline__ uint32_t word0(uint64_t seed, uint32_t w, uint32_t chain, uint32_t t,
-                                          uint32_t tag) {
-  return philox(make_uint4(w, chain, t, tag), static_cast<uint32_t>(seed),
-                static_cast<uint32_t>(seed >> 32)).x;
-}
-
-// probability a / b, b > 0: (2 w + 1) b < a 2^33
-__device__ __forceinline__ bool take(uint32_t w, uint32_t a, uint32_t b) {
-  return (2ull * w + 1ull) * b < (static_cast<unsigned long long>(a) << 33);
-}
-
-// two warp sums in one butterfly (each the same tree as warp_sum)
-__device__ __forceinline__ void warp_sum2(float& u, float& v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    u += __shfl_xor_sync(0xffffffffu, u, o);
-    v += __shfl_xor_sync(0xffffffffu, v, o);
-  }
-}
-
-// four warp sums in one butterfly
-__device__ __forceinline__ void warp_sum4(float& u, float& v, float& w, float& z) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    u += __shfl_xor_sync(0xffffffffu, u, o);
-    v += __shfl_xor_sync(0xffffffffu, v, o);
-    w += __shfl_xor_sync(0xffffffffu, w, o);
-    z += __shfl_xor_sync(0xffffffffu, z, o);
-  }
-}
 
 struct NutsArgs {
   StepArgs s;                      // transition s.t_full is the launch's first
@@ -264,7 +220,7 @@ __global__ void __launch_bounds__(32 * kWarps, NB == 1 ? 7 : 4) k_nuts(NutsArgs 
       moved = 0;
       float a_sum = 0.f;
       uint32_t n_a = 0;
-      const uint32_t dirs = word0(a.seed, 0u, chain, t, kTagDirection);
+      const uint32_t dirs = nuts_word0(a.seed, 0u, chain, t, kNutsTagDirection);
       for (int jd = 0; jd < na.max_depth; ++jd) {
         const int v = ((dirs >> jd) & 1u) ? 1 : -1;
         const float ev = static_cast<float>(v) * eps;
@@ -282,7 +238,7 @@ __global__ void __launch_bounds__(32 * kWarps, NB == 1 ? 7 : 4) k_nuts(NutsArgs 
           // drawn first, four at a time, the generator's arithmetic fills the
           // butterfly's latency
           if ((k & 3) == 0)
-            wsub4 = philox(make_uint4(static_cast<uint32_t>(k >> 2), chain, t, kTagSubtree + jd),
+            wsub4 = philox(make_uint4(static_cast<uint32_t>(k >> 2), chain, t, kNutsTagSubtree + jd),
                            static_cast<uint32_t>(a.seed), static_cast<uint32_t>(a.seed >> 32));
           const int kq = k & 3;
           const uint32_t wsub = kq == 0 ? wsub4.x : kq == 1 ? wsub4.y : kq == 2 ? wsub4.z : wsub4.w;
@@ -311,12 +267,12 @@ __global__ void __launch_bounds__(32 * kWarps, NB == 1 ? 7 : 4) k_nuts(NutsArgs 
           bool turn;
           lp = leaf_sums(hv, static_cast<float>(v), close >= 1, xf, pf, &H, &turn);
           const bool finite = isfinite(H);
-          if (!finite || H - H0 >= kDeltaMax - logU) ok_sub = false;     // divergence
+          if (!finite || H - H0 >= kNutsDeltaMax - logU) ok_sub = false;     // divergence
           a_sum += finite ? accept_prob(H0 - H) : 0.f;
           ++n_a;
           if (finite && logU <= H0 - H) {
             ++n_sub;
-            if (take(wsub, 1u, n_sub)) {
+            if (nuts_take(wsub, 1u, n_sub)) {
               store(kSlotSub, x);
               store(kSlotSub + 1, g);
               lps = lp;
@@ -356,7 +312,7 @@ __global__ void __launch_bounds__(32 * kWarps, NB == 1 ? 7 : 4) k_nuts(NutsArgs 
         store(side, x); store(side + 1, p); store(side + 2, g);
         lp_end[v > 0 ? 1 : 0] = lp;
         if (!ok_sub) break;
-        if (n_sub > 0 && take(word0(a.seed, static_cast<uint32_t>(jd), chain, t, kTagTop), n_sub, n)) {
+        if (n_sub > 0 && nuts_take(nuts_word0(a.seed, static_cast<uint32_t>(jd), chain, t, kNutsTagTop), n_sub, n)) {
           float t1[NB][4], t2[NB][4];
           load(kSlotSub, t1);
           load(kSlotSub + 1, t2);

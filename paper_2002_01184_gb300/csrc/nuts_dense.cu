@@ -1,0 +1,566 @@
+// The No-U-Turn Sampler (Section 2.3) for the dense targets -- the
+// correlated Gaussian and the Bayesian logistic regression -- whose gradient
+// is a matrix product over all chains (Section 2.1's batched evaluation).
+//
+// The transition and its random streams are those of the elementwise NUTS
+// kernel (nuts.cu; Hoffman and Gelman's efficient NUTS with the recursion
+// unrolled, O(max_depth) kept states).  What differs is the schedule: as in
+// the paper's vectorised NUTS, the chains advance in lockstep, one leaf per
+// iteration, with a mask for the chains whose trees have stopped.  One
+// iteration is
+//   (1) the batched gradient at every chain's drifted position: the 3xTF32
+//       tcgen05 tile products of gauss_tc.cu, which skip a 128-chain tile
+//       whose chains have all stopped;
+//   (2) one warp-per-chain kernel that finishes the leaf -- the gradient's
+//       epilogue (sign, prior, split sum, log p), second half kick, energy,
+//       slice and divergence tests, the candidate choice, the U-turn tests of
+//       the spans that close, the subtree's and the trajectory's bookkeeping
+//       -- and starts the next leaf (first half kick and drift of the chains
+//       still building).
+// The iterations are the body of a CUDA-graph conditional WHILE node: the leaf
+// kernel's last block clears the condition when no chain is left, so a
+// transition costs as many iterations as its deepest tree and the host never
+// waits on the device in between.  A chain's result depends only on its own
+// row of every product, so it is the same in any batch.
+//
+// Per chain, the tree's scalars (NdChain) and a scratch of kNutsSlots rows of
+// the padded row length (the two trajectory ends, the candidates, the span
+// starts) stay in HBM between iterations; the working position is kept as its
+// tf32 head and remainder -- the products' A operand -- and the momentum in the
+// trajectory buffers of the tensor-core workspace.
+#include <cmath>
+
+#include "nuts_common.cuh"
+
+namespace hmc {
+
+namespace {
+
+constexpr int kNdWarps = 8;
+
+// the tree of one chain between iterations
+struct NdChain {
+  float H0, logU, lp_left, lp_right;
+  float lpm, lps, lpw, a_sum;       // candidate, subtree candidate, working log p; sum of accept stats
+  uint32_t dirs, n, n_sub, n_a;     // direction bits, valid leaves (tree, subtree), leaves built
+  int j, k, active, moved;          // doubling, leaf in it, still building, candidate moved
+};
+static_assert(sizeof(NdChain) == 64, "chain record");
+
+constexpr int kModeGauss = 0, kModeLogreg = 1;
+
+struct NdArgs {
+  StepArgs s;
+  int ld;                 // row length of the working buffers and slots (D rounded up to 4)
+  int max_depth;
+  float* xhi;             // working position, tf32 head / remainder [C x ld]
+  float* xlo;
+  float* p;               // working momentum [C x ld]
+  const float* part;      // products: X P, or the K-splits of R X
+  int S;                  // K-splits (logistic regression)
+  const float* lp_part;   // logistic regression: rows' log-likelihood partials [C x ntot]
+  int ntot, nrt;
+  float* scratch;         // [C][kNutsSlots][ld]
+  NdChain* st;
+  uint8_t* active;
+  unsigned* ctr;          // [0] chains left, [1] blocks arrived, [2] iterations of this transition
+  int* err;
+  unsigned long long* leaves;
+  unsigned long long* iters;
+  cudaGraphConditionalHandle handle;
+};
+
+template <int NB>
+struct Lanes {
+  const int lane;
+  const int ld;
+  __device__ bool ok(int b) const { return 4 * (lane + 32 * b) < ld; }
+  __device__ float4* at(float* base, int64_t row, int b) const {
+    return reinterpret_cast<float4*>(base + row) + (lane + 32 * b);
+  }
+  __device__ void put(float* base, int64_t row, const float (&v)[NB][4]) const {
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (ok(b)) *at(base, row, b) = make_float4(v[b][0], v[b][1], v[b][2], v[b][3]);
+  }
+  __device__ void get(const float* base, int64_t row, float (&v)[NB][4]) const {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (ok(b)) w = *at(const_cast<float*>(base), row, b);
+      v[b][0] = w.x; v[b][1] = w.y; v[b][2] = w.z; v[b][3] = w.w;
+    }
+  }
+};
+
+// (dx . pa) < 0 or (dx . pb) < 0
+template <int NB>
+__device__ __forceinline__ bool u_turn(const float (&dx)[NB][4], const float (&pa)[NB][4],
+                                       const float (&pb)[NB][4]) {
+  float d1 = 0.f, d2 = 0.f;
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      d1 = fmaf(dx[b][i], pa[b][i], d1);
+      d2 = fmaf(dx[b][i], pb[b][i], d2);
+    }
+  warp_sum2(d1, d2);
+  return d1 < 0.f || d2 < 0.f;
+}
+
+// working position (x) and momentum (p) after the first half kick and the
+// drift of a leaf of direction v: written for the next products
+template <int NB>
+__device__ __forceinline__ void half_kick_drift(const NdArgs& na, const Lanes<NB>& L, int64_t row, float hv,
+                                                float ev, float (&x)[NB][4], float (&p)[NB][4],
+                                                const float (&g)[NB][4]) {
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    float hi[4], lo[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      p[b][i] = fmaf(hv, g[b][i], p[b][i]);
+      x[b][i] = fmaf(ev, p[b][i], x[b][i]);
+      split_tf32(x[b][i], hi[i], lo[i]);
+    }
+    if (L.ok(b)) {
+      *L.at(na.xhi, row, b) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      *L.at(na.xlo, row, b) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      *L.at(na.p, row, b) = make_float4(p[b][0], p[b][1], p[b][2], p[b][3]);
+    }
+  }
+}
+
+__device__ __forceinline__ int dir_of(const NdChain& cs, int j) { return ((cs.dirs >> j) & 1u) ? 1 : -1; }
+
+// Start of a transition (warp per chain): p0 ~ N(0, I), H0, log U, both
+// trajectory ends and the candidate at the current state, then the first half
+// kick and drift of leaf 0 of doubling 0.
+template <int NB>
+__global__ void __launch_bounds__(32 * kNdWarps) k_nuts_dense_begin(NdArgs na) {
+  const StepArgs& a = na.s;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kNdWarps + (threadIdx.x >> 5);
+  if (blockIdx.x == 0 && threadIdx.x == 0) na.ctr[2] = 0u;
+  if (c >= a.C) return;
+  const int D = a.D, ld = na.ld;
+  const Lanes<NB> L{lane, ld};
+  const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
+  const float eps = a.da->eps;
+  const int64_t srow = static_cast<int64_t>(c) * D;           // the state's rows have D floats
+  const int64_t wrow = static_cast<int64_t>(c) * ld;
+  float* base = na.scratch + static_cast<int64_t>(c) * kNutsSlots * ld;
+  float x[NB][4], p[NB][4], g[NB][4];
+  float pp = 0.f;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int q = lane + 32 * b;
+    const float4 z = momentum4(a.seed, static_cast<uint32_t>(q), chain, a.t);
+    const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int d = 4 * q + i;
+      const bool in = d < D;
+      x[b][i] = in ? a.x[srow + d] : 0.f;
+      g[b][i] = in ? a.g[srow + d] : 0.f;
+      p[b][i] = in ? zz[i] : 0.f;
+      pp = fmaf(p[b][i], p[b][i], pp);
+    }
+  }
+  pp = warp_sum(pp);
+  const float lp = a.lp[c];
+  NdChain cs;
+  cs.H0 = -lp + 0.5f * pp;
+  cs.logU = accept_log_uniform(a.seed, chain, a.t);
+  cs.lp_left = cs.lp_right = cs.lpm = cs.lpw = lp;
+  cs.lps = 0.f;
+  cs.a_sum = 0.f;
+  cs.dirs = nuts_word0(a.seed, 0u, chain, a.t, kNutsTagDirection);
+  cs.n = 1u;
+  cs.n_sub = cs.n_a = 0u;
+  cs.j = cs.k = 0;
+  cs.active = 1;
+  cs.moved = 0;
+  L.put(base, kSlotLeft * ld, x);
+  L.put(base, (kSlotLeft + 1) * ld, p);
+  L.put(base, (kSlotLeft + 2) * ld, g);
+  L.put(base, kSlotRight * ld, x);
+  L.put(base, (kSlotRight + 1) * ld, p);
+  L.put(base, (kSlotRight + 2) * ld, g);
+  L.put(base, kSlotCand * ld, x);
+  L.put(base, (kSlotCand + 1) * ld, g);
+  const float ev = static_cast<float>(dir_of(cs, 0)) * eps;
+  half_kick_drift(na, L, wrow, 0.5f * ev, ev, x, p, g);
+  if (lane == 0) {
+    na.st[c] = cs;
+    na.active[c] = 1;
+  }
+}
+
+// One leaf of every chain still building its tree, then the loop condition.
+template <int MODE, int NB>
+__global__ void __launch_bounds__(32 * kNdWarps) k_nuts_dense_leaf(NdArgs na) {
+  const StepArgs& a = na.s;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kNdWarps + (threadIdx.x >> 5);
+  bool still = false;
+  if (c < a.C && na.st[c].active) {
+    NdChain cs = na.st[c];
+    const int D = a.D, ld = na.ld;
+    const Lanes<NB> L{lane, ld};
+    const int64_t row = static_cast<int64_t>(c) * ld;
+    const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
+    const uint32_t t = a.t;
+    const float eps = a.da->eps;
+    float* base = na.scratch + static_cast<int64_t>(c) * kNutsSlots * ld;
+    auto slot = [&](int s) { return static_cast<int64_t>(s) * ld; };
+    int v = dir_of(cs, cs.j);
+    float hv = 0.5f * static_cast<float>(v) * eps;
+    // spans of 2^i leaves closing here (2^i | k + 1); the first one's start
+    // is read before the butterfly so that its U-turn sums join it
+    const int close = min(cs.j, __ffs(cs.k + 1) - 1);
+    float x[NB][4], p[NB][4], g[NB][4], xf[NB][4], pf[NB][4];
+    {
+      float hi[NB][4], lo[NB][4];
+      L.get(na.xhi, row, hi);
+      L.get(na.xlo, row, lo);
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[b][i] = hi[b][i] + lo[b][i];
+    }
+    L.get(na.p, row, p);
+    if (close >= 1) {
+      L.get(base, slot(kSlotSpan), xf);
+      L.get(base, slot(kSlotSpan + 1), pf);
+    } else {
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xf[b][i] = pf[b][i] = 0.f;
+    }
+    // the gradient at x from the products, the second half kick, and the sums
+    float s0 = 0.f, pp = 0.f, d1 = 0.f, d2 = 0.f;
+    const int64_t split = static_cast<int64_t>(a.C) * ld;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      float4 gv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (L.ok(b)) {
+        const float4* pr = reinterpret_cast<const float4*>(na.part + row) + (lane + 32 * b);
+        gv = *pr;
+        if (MODE == kModeLogreg)
+          for (int sp = 1; sp < na.S; ++sp) {
+            const float4 u = pr[sp * (split / 4)];
+            gv.x += u.x; gv.y += u.y; gv.z += u.z; gv.w += u.w;
+          }
+      }
+      const float gg[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int d = 4 * (lane + 32 * b) + i;
+        // Gaussian: g = -x P; logistic regression: g = R X - theta (the
+        // N(0, I) prior), zero on the padding
+        g[b][i] = MODE == kModeGauss ? -gg[i] : (d < D ? gg[i] - x[b][i] : 0.f);
+        p[b][i] = fmaf(hv, g[b][i], p[b][i]);
+        s0 = MODE == kModeGauss ? fmaf(x[b][i], g[b][i], s0) : fmaf(x[b][i], x[b][i], s0);
+        pp = fmaf(p[b][i], p[b][i], pp);
+        const float dx = static_cast<float>(v) * (x[b][i] - xf[b][i]);
+        d1 = fmaf(dx, pf[b][i], d1);
+        d2 = fmaf(dx, p[b][i], d2);
+      }
+    }
+    float rows = 0.f;
+    if (MODE == kModeLogreg) {
+      for (int r = lane; r < na.nrt; r += 32) rows += na.lp_part[static_cast<int64_t>(c) * na.ntot + r];
+      rows = warp_sum(rows);
+    }
+    warp_sum4(s0, pp, d1, d2);
+    // Gaussian: log p = <x, g> / 2; logistic regression: the rows'
+    // log-likelihood minus |theta|^2 / 2
+    const float lp = MODE == kModeGauss ? 0.5f * s0 : rows - 0.5f * s0;
+    const float H = -lp + 0.5f * pp;
+    bool ok = true;
+    const bool finite = isfinite(H);
+    if (!finite || H - cs.H0 >= kNutsDeltaMax - cs.logU) ok = false;       // divergence
+    cs.a_sum += finite ? accept_prob(cs.H0 - H) : 0.f;
+    cs.n_a += 1u;
+    if (finite && cs.logU <= cs.H0 - H) {
+      cs.n_sub += 1u;
+      if (nuts_take(nuts_subtree_word(a.seed, static_cast<uint32_t>(cs.k), chain, t, cs.j), 1u, cs.n_sub)) {
+        L.put(base, slot(kSlotSub), x);
+        L.put(base, slot(kSlotSub + 1), g);
+        cs.lps = lp;
+      }
+    }
+    if (close >= 1 && (d1 < 0.f || d2 < 0.f)) ok = false;
+    for (int i = 2; i <= close && ok; ++i) {
+      float xs[NB][4], ps[NB][4];
+      L.get(base, slot(kSlotSpan + 2 * (i - 1)), xs);
+      L.get(base, slot(kSlotSpan + 2 * (i - 1) + 1), ps);
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xs[b][q] = static_cast<float>(v) * (x[b][q] - xs[b][q]);
+      if (u_turn(xs, ps, p)) ok = false;
+    }
+    if (ok) {
+      // spans of 2^i leaves opening here (2^i | k); none opens and closes at one leaf
+      const int open = cs.k == 0 ? cs.j : min(cs.j, __ffs(cs.k) - 1);
+      for (int i = 1; i <= open; ++i) {
+        L.put(base, slot(kSlotSpan + 2 * (i - 1)), x);
+        L.put(base, slot(kSlotSpan + 2 * (i - 1) + 1), p);
+      }
+    }
+    cs.lpw = lp;
+    bool done = !ok;
+    if (ok && cs.k + 1 == (1 << cs.j)) {
+      // the subtree is complete: it becomes the trajectory's end on its side
+      const int side = v > 0 ? kSlotRight : kSlotLeft;
+      L.put(base, slot(side), x);
+      L.put(base, slot(side + 1), p);
+      L.put(base, slot(side + 2), g);
+      if (v > 0) cs.lp_right = lp;
+      else cs.lp_left = lp;
+      if (cs.n_sub > 0u &&
+          nuts_take(nuts_word0(a.seed, static_cast<uint32_t>(cs.j), chain, t, kNutsTagTop), cs.n_sub, cs.n)) {
+        float t1[NB][4], t2[NB][4];
+        L.get(base, slot(kSlotSub), t1);
+        L.get(base, slot(kSlotSub + 1), t2);
+        L.put(base, slot(kSlotCand), t1);
+        L.put(base, slot(kSlotCand + 1), t2);
+        cs.lpm = cs.lps;
+        cs.moved = 1;
+      }
+      cs.n += cs.n_sub;
+      // the whole trajectory's ends
+      float xl[NB][4], pl[NB][4], xr[NB][4], pr[NB][4];
+      L.get(base, slot(kSlotLeft), xl);
+      L.get(base, slot(kSlotLeft + 1), pl);
+      L.get(base, slot(kSlotRight), xr);
+      L.get(base, slot(kSlotRight + 1), pr);
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xr[b][q] -= xl[b][q];
+      if (u_turn(xr, pl, pr) || cs.j + 1 >= na.max_depth) {
+        done = true;
+      } else {
+        // next doubling: grow from the end on its side
+        cs.j += 1;
+        cs.k = 0;
+        cs.n_sub = 0u;
+        v = dir_of(cs, cs.j);
+        const int from = v > 0 ? kSlotRight : kSlotLeft;
+        L.get(base, slot(from), x);
+        L.get(base, slot(from + 1), p);
+        L.get(base, slot(from + 2), g);
+        cs.lpw = v > 0 ? cs.lp_right : cs.lp_left;
+      }
+    } else if (ok) {
+      cs.k += 1;
+    }
+    if (done) {
+      cs.active = 0;
+    } else {
+      const float ev = static_cast<float>(v) * eps;
+      half_kick_drift(na, L, row, 0.5f * ev, ev, x, p, g);
+      still = true;
+    }
+    if (lane == 0) {
+      na.st[c] = cs;
+      na.active[c] = still ? 1 : 0;
+    }
+  }
+  // the loop condition: any chain left (the last block to arrive decides);
+  // a tree has at most 2^max_depth - 1 leaves, so more iterations than that
+  // mean a fault of the bookkeeping: the loop stops and the flag reports it
+  const int left = __syncthreads_count((threadIdx.x & 31) == 0 && still);
+  if (threadIdx.x == 0) {
+    if (left) atomicAdd(&na.ctr[0], static_cast<unsigned>(left));
+    __threadfence();
+    const unsigned prev = atomicAdd(&na.ctr[1], 1u);
+    if (prev == gridDim.x - 1u) {
+      __threadfence();
+      const unsigned total = atomicAdd(&na.ctr[0], 0u);
+      const unsigned it = na.ctr[2] + 1u;
+      bool more = total > 0u;
+      if (more && it >= (1u << na.max_depth)) {
+        more = false;
+        atomicExch(na.err, 2);
+      }
+      na.ctr[0] = 0u;
+      na.ctr[1] = 0u;
+      na.ctr[2] = it;
+      *na.iters += 1ull;
+      __threadfence();
+      cudaGraphSetConditional(na.handle, more ? 1u : 0u);
+    }
+  }
+}
+
+// End of a transition (warp per chain): the candidate becomes the state;
+// kernel results, kept sample, traces, leaf count; the acceptance statistic
+// (mean over the leaves built) enters dual averaging.
+__global__ void __launch_bounds__(32 * kNdWarps) k_nuts_dense_finish(NdArgs na) {
+  const StepArgs& a = na.s;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kNdWarps + (threadIdx.x >> 5);
+  const bool has = c < a.C;
+  const float eps = a.da->eps;
+  float prob = 0.f;
+  unsigned n_a = 0u;
+  if (has) {
+    const NdChain cs = na.st[c];
+    const int D = a.D, ld = na.ld;
+    const float* base = na.scratch + static_cast<int64_t>(c) * kNutsSlots * ld;
+    const int64_t srow = static_cast<int64_t>(c) * D;
+    for (int d = lane; d < D; d += 32) {
+      const float xv = base[kSlotCand * ld + d];
+      a.x[srow + d] = xv;
+      a.g[srow + d] = base[(kSlotCand + 1) * ld + d];
+      if (a.sample_out) a.sample_out[srow + d] = xv;
+    }
+    prob = cs.a_sum / static_cast<float>(cs.n_a);
+    n_a = cs.n_a;
+    if (lane == 0) {
+      a.lp[c] = cs.lpm;
+      a.is_accepted[c] = static_cast<uint8_t>(cs.moved);
+      a.log_accept[c] = logf(prob);
+      if (a.trace_acc) a.trace_acc[c] = static_cast<uint8_t>(cs.moved);
+      if (c == 0 && a.trace_eps) a.trace_eps[0] = eps;
+    }
+  }
+  __shared__ unsigned long long blk_leaves;
+  if (threadIdx.x == 0) blk_leaves = 0ull;
+  __syncthreads();
+  if (has && lane == 0) atomicAdd(&blk_leaves, static_cast<unsigned long long>(n_a));
+  __syncthreads();
+  if (threadIdx.x == 0 && blk_leaves) atomicAdd(na.leaves, blk_leaves);
+  accept_tile_finish<kNdWarps>(a.da, a.partials, prob, has, a.C, a.t_full, static_cast<int>(blockIdx.x),
+                               static_cast<int>(gridDim.x));
+}
+
+template <int NB>
+cudaError_t set_leaf_attrs() {
+  cudaError_t e = cudaFuncSetAttribute(k_nuts_dense_leaf<kModeGauss, NB>,
+                                       cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_nuts_dense_leaf<kModeLogreg, NB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             0);
+  return e;
+}
+
+template <int NB>
+cudaError_t enqueue_nb(const hmc_target& t, const NdArgs& base_args, NutsDense& nd, cudaStream_t s,
+                       KernelTimer* timer) {
+  const StepArgs& a = base_args.s;
+  const unsigned nb = static_cast<unsigned>((a.C + kNdWarps - 1) / kNdWarps);
+  NdArgs na = base_args;
+  if (timer) timer->begin(s);
+  k_nuts_dense_begin<NB><<<nb, 32 * kNdWarps, 0, s>>>(na);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // the leaf loop: a WHILE node after everything captured so far
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &graph, &deps, nullptr, &ndeps);
+  if (e != cudaSuccess) return e;
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureImplicit;
+  cudaGraphConditionalHandle handle = 0;
+  e = cudaGraphConditionalHandleCreate(&handle, graph, 1u, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  e = cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &cp);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e != cudaSuccess) return e;
+  // the body: products, then the leaf kernel
+  e = cudaStreamBeginCaptureToGraph(nd.side, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  na.handle = handle;
+  if (nd.mode == kModeGauss) {
+    e = launch_gauss_tc_product(*nd.tc, a.C, a.D, a.da, nd.active, nd.side);
+  } else {
+    int S = 1;
+    e = launch_logreg_gemm_products(*nd.lrg, a.C, a.D, a.da, nd.active, &S, nd.side);
+    na.S = S;
+  }
+  if (e == cudaSuccess) {
+    if (nd.mode == kModeGauss)
+      k_nuts_dense_leaf<kModeGauss, NB><<<nb, 32 * kNdWarps, 0, nd.side>>>(na);
+    else
+      k_nuts_dense_leaf<kModeLogreg, NB><<<nb, 32 * kNdWarps, 0, nd.side>>>(na);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  cudaGraph_t captured = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(nd.side, &captured);
+  if (e != cudaSuccess) return e;
+  if (e2 != cudaSuccess) return e2;
+  k_nuts_dense_finish<<<nb, 32 * kNdWarps, 0, s>>>(na);
+  count_launch();
+  if (timer) timer->end(s);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool nuts_dense_supported(const hmc_target& t) {
+  if (t.dim > kNutsMaxDim) return false;
+  return (t.id == HMC_T_CORR_GAUSS && gauss_tc_supported(t)) || (t.id == HMC_T_LOGREG && logreg_gemm_supported(t));
+}
+
+size_t nuts_dense_chain_bytes(int64_t C) { return static_cast<size_t>(C) * sizeof(NdChain); }
+
+cudaError_t nuts_dense_prepare() {
+  cudaError_t e = set_leaf_attrs<1>();
+  if (e == cudaSuccess) e = set_leaf_attrs<2>();
+  if (e == cudaSuccess) e = set_leaf_attrs<4>();
+  return e;
+}
+
+cudaError_t launch_nuts_dense_transition(const hmc_target& t, const StepArgs& a, NutsDense& nd, cudaStream_t s,
+                                         KernelTimer* timer) {
+  NdArgs na{};
+  na.s = a;
+  na.ld = (t.dim + 3) / 4 * 4;
+  na.max_depth = nd.max_depth;
+  if (nd.mode == kModeGauss) {
+    na.xhi = nd.tc->xhi[0];
+    na.xlo = nd.tc->xlo[0];
+    na.p = nd.tc->p;
+    na.part = nd.tc->gL;
+  } else {
+    na.xhi = nd.lrg->xhi[0];
+    na.xlo = nd.lrg->xlo[0];
+    na.p = nd.lrg->p;
+    na.part = nd.lrg->part;
+    na.lp_part = nd.lrg->lp_part;
+    na.ntot = nd.lrg->ntot;
+    na.nrt = nd.lrg->nrt;
+  }
+  na.S = 1;
+  na.scratch = nd.scratch;
+  na.st = static_cast<NdChain*>(nd.chains);
+  na.active = nd.active;
+  na.ctr = nd.ctr;
+  na.err = nd.err;
+  na.leaves = nd.leaves;
+  na.iters = nd.iters;
+  const int nb = (na.ld + 127) / 128;
+  if (nb <= 1) return enqueue_nb<1>(t, na, nd, s, timer);
+  if (nb == 2) return enqueue_nb<2>(t, na, nd, s, timer);
+  return enqueue_nb<4>(t, na, nd, s, timer);
+}
+
+}  // namespace hmc

@@ -66,6 +66,7 @@ def _load():
         "hmc_step": [P, P, ctypes.c_uint64, ctypes.POINTER(hmc_kernel_results)],
         "hmc_propose": [P, P, ctypes.c_uint64, ctypes.POINTER(hmc_proposal)],
         "hmc_nuts_leapfrog_count": [P, ctypes.POINTER(ctypes.c_uint64)],
+        "hmc_nuts_leaf_iterations": [P, ctypes.POINTER(ctypes.c_uint64)],
         "hmc_mh_select": [P, P, ctypes.c_uint64, ctypes.POINTER(hmc_kernel_results)],
         "hmc_sample_chain": [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P],
         "hmc_sample_chain_host": [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P],
@@ -207,6 +208,12 @@ def hmc_step(ctx, x_inout, t):
 def hmc_nuts_leapfrog_count(ctx):
     out = ctypes.c_uint64()
     _check(lib.hmc_nuts_leapfrog_count(ctx, ctypes.byref(out)), ctx)
+    return int(out.value)
+
+
+def hmc_nuts_leaf_iterations(ctx):
+    out = ctypes.c_uint64()
+    _check(lib.hmc_nuts_leaf_iterations(ctx, ctypes.byref(out)), ctx)
     return int(out.value)
 
 
