@@ -257,6 +257,10 @@ CreatePlan plan_create(const hmc_target& t, int64_t num_chains, const hmc_config
       if (t.id == HMC_T_CORR_GAUSS) {
         q.use_tc = true;
         add(hmc::gauss_tc_workspace_bytes(t, num_chains));
+      } else if (hmc::logreg_tc_supported(t)) {
+        q.use_lrtc = true;       // dim <= 128, a multiple of 4: the CTA-pair kernel
+        add(hmc::logreg_tc_workspace_bytes(t, num_chains));
+        add(sizeof(int));
       } else {
         q.use_lrgemm = true;
         add(hmc::logreg_gemm_workspace_bytes(t, num_chains));
@@ -693,10 +697,11 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   ctx->nuts_dense = plan.nuts_dense;
   if (e == cudaSuccess && ctx->nuts_dense) {
     hmc::NutsDense& nd = ctx->nd;
-    nd.mode = target->id == HMC_T_CORR_GAUSS ? 0 : 1;
+    nd.mode = target->id == HMC_T_CORR_GAUSS ? 0 : ctx->use_lrtc ? 2 : 1;
     nd.tc = &ctx->tc;
     nd.lrg = &ctx->lrg;
-    nd.err = nd.mode == 0 ? ctx->tc.err : ctx->lrg.err;
+    nd.lrtc = &ctx->lrtc;
+    nd.err = nd.mode == 0 ? ctx->tc.err : nd.mode == 2 ? ctx->lr_err : ctx->lrg.err;
     nd.scratch = ctx->nuts_scratch;
     nd.leaves = ctx->nuts_leaves;
     nd.max_depth = ctx->cfg.num_leapfrog;

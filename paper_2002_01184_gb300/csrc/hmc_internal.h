@@ -324,6 +324,10 @@ size_t logreg_tc_workspace_bytes(const hmc_target& t, int64_t C);
 cudaError_t logreg_tc_setup(LogregTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s);
 cudaError_t launch_logreg_tc_transition(const StepArgs& a, LogregTc& tc, int* err, cudaStream_t s,
                                         KernelTimer* timer);
+// NUTS: one gradient of the positions in tc.thi / tc.tlo into the per-range
+// partials tc.Gpart [nsplit x C x D] and tc.lp_part [nsplit x C]; CTA pairs
+// whose 256 chains have no flag set in `active` are skipped.
+cudaError_t launch_logreg_tc_grad(LogregTc& tc, int C, int D, const uint8_t* active, int* err, cudaStream_t s);
 
 }  // namespace hmc
 
@@ -332,9 +336,11 @@ namespace hmc {
 // NUTS on the dense targets (nuts_dense.cu): the chains advance one leaf per
 // iteration of a CUDA-graph WHILE node; see that file.
 struct NutsDense {
-  int mode = 0;                   // 0: Gaussian (GaussTc products), 1: logistic regression (LogregGemm)
+  int mode = 0;                   // 0: Gaussian (GaussTc products), 1: logistic regression
+                                  // (LogregGemm products), 2: logistic regression (LogregTc pairs)
   GaussTc* tc = nullptr;
   LogregGemm* lrg = nullptr;
+  LogregTc* lrtc = nullptr;
   void* chains = nullptr;         // per-chain tree state [C]
   uint8_t* active = nullptr;      // [C] chains still building their trees
   unsigned* ctr = nullptr;        // [4] leaf-loop counters

@@ -66,6 +66,7 @@ struct LrTcArgs {
   float* Gpart;          // [nsplit x C x D]
   float* lp_part;        // [nsplit x C]
   int* err;
+  const uint8_t* active; // null, or per-chain flags: a pair whose 256 chains have none set is skipped
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -91,6 +92,14 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
   float* lpred = reinterpret_cast<float*>(St);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (a.active) {
+    // NUTS: both CTAs of the pair read the same 256 flags and skip together,
+    // before anything the pair shares
+    const int r = threadIdx.x;
+    const int m = (blockIdx.x >> 1) * kPairM + r;
+    const bool mine = r < kPairM && m < a.C && a.active[m] != 0;
+    if (!__syncthreads_or(mine)) return;
+  }
   const uint32_t rank = ptx::cluster_rank();             // 0: leader, 1: peer
   const int m0 = (blockIdx.x >> 1) * kPairM + static_cast<int>(rank) * kM;   // this CTA's chains
   const int split = blockIdx.y;
@@ -625,6 +634,39 @@ cudaError_t logreg_tc_setup(LogregTc* tc, const hmc_target& t, int64_t C, void* 
       tc->ypad);
   count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_logreg_tc_grad(LogregTc& tc, int C, int D, const uint8_t* active, int* err, cudaStream_t s) {
+  LrTcArgs g{};
+  g.C = C;
+  g.D = D;
+  g.ntiles = tc.ntiles;
+  g.tiles_per_split = tc.tps;
+  g.nsplit = tc.nsplit;
+  g.dpad = tc.dpad;
+  g.y = tc.ypad;
+  g.Gpart = tc.Gpart;
+  g.lp_part = tc.lp_part;
+  g.err = err;
+  g.N = tc.n_data;
+  g.need_lp = 1;
+  g.active = active;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * tc.groups, tc.nsplit);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_lr_grad, tc.mThi, tc.mTlo, tc.mXhi, tc.mXlo, tc.mXThi,
+                                           tc.mXTlo, g);
+  count_launch();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_logreg_tc_transition(const StepArgs& a, LogregTc& tc, int* err, cudaStream_t s,

@@ -9,8 +9,9 @@
 // iteration, with a mask for the chains whose trees have stopped.  One
 // iteration is
 //   (1) the batched gradient at every chain's drifted position: the 3xTF32
-//       tcgen05 tile products of gauss_tc.cu, which skip a 128-chain tile
-//       whose chains have all stopped;
+//       tcgen05 products of gauss_tc.cu (one-CTA tiles) or, for a logistic
+//       regression of dim <= 128 (a multiple of 4), logreg_tc.cu's CTA-pair
+//       kernel; a tile whose chains have all stopped is skipped;
 //   (2) one warp-per-chain kernel that finishes the leaf -- the gradient's
 //       epilogue (sign, prior, split sum, log p), second half kick, energy,
 //       slice and divergence tests, the candidate choice, the U-turn tests of
@@ -47,7 +48,10 @@ struct NdChain {
 };
 static_assert(sizeof(NdChain) == 64, "chain record");
 
-constexpr int kModeGauss = 0, kModeLogreg = 1;
+// products: gauss_tc.cu's tiles (Gaussian, logistic regression) or
+// logreg_tc.cu's CTA pairs (logistic regression, dim <= 128); the last two
+// share the leaf kernel
+constexpr int kModeGauss = 0, kModeLogreg = 1, kModeLogregPair = 2;
 
 struct NdArgs {
   StepArgs s;
@@ -56,10 +60,11 @@ struct NdArgs {
   float* xhi;             // working position, tf32 head / remainder [C x ld]
   float* xlo;
   float* p;               // working momentum [C x ld]
-  const float* part;      // products: X P, or the K-splits of R X
-  int S;                  // K-splits (logistic regression)
-  const float* lp_part;   // logistic regression: rows' log-likelihood partials [C x ntot]
-  int ntot, nrt;
+  const float* part;      // products: X P, or the S partial sums of R X [S x C x ld]
+  int S;                  // partial sums (logistic regression)
+  const float* lp_part;   // logistic regression: log-likelihood partials, chain c's
+  int nlp;                // nlp of them at lp_part[c * lp_cs + r * lp_rs]
+  int64_t lp_cs, lp_rs;
   float* scratch;         // [C][kNutsSlots][ld]
   NdChain* st;
   uint8_t* active;
@@ -272,7 +277,7 @@ __global__ void __launch_bounds__(32 * kNdWarps) k_nuts_dense_leaf(NdArgs na) {
     }
     float rows = 0.f;
     if (MODE == kModeLogreg) {
-      for (int r = lane; r < na.nrt; r += 32) rows += na.lp_part[static_cast<int64_t>(c) * na.ntot + r];
+      for (int r = lane; r < na.nlp; r += 32) rows += na.lp_part[c * na.lp_cs + r * na.lp_rs];
       rows = warp_sum(rows);
     }
     warp_sum4(s0, pp, d1, d2);
@@ -490,14 +495,17 @@ cudaError_t enqueue_nb(const hmc_target& t, const NdArgs& base_args, NutsDense& 
   na.handle = handle;
   if (nd.mode == kModeGauss) {
     e = launch_gauss_tc_product(*nd.tc, a.C, a.D, a.da, nd.active, nd.side);
-  } else {
+  } else if (nd.mode == kModeLogreg) {
     int S = 1;
     e = launch_logreg_gemm_products(*nd.lrg, a.C, a.D, a.da, nd.active, &S, nd.side);
     na.S = S;
+  } else {
+    e = launch_logreg_tc_grad(*nd.lrtc, a.C, a.D, nd.active, nd.err, nd.side);
   }
   if (e == cudaSuccess) {
     if (nd.mode == kModeGauss)
       k_nuts_dense_leaf<kModeGauss, NB><<<nb, 32 * kNdWarps, 0, nd.side>>>(na);
+    // (both logistic-regression product forms leave S partial sums)
     else
       k_nuts_dense_leaf<kModeLogreg, NB><<<nb, 32 * kNdWarps, 0, nd.side>>>(na);
     count_launch();
@@ -517,7 +525,8 @@ cudaError_t enqueue_nb(const hmc_target& t, const NdArgs& base_args, NutsDense& 
 
 bool nuts_dense_supported(const hmc_target& t) {
   if (t.dim > kNutsMaxDim) return false;
-  return (t.id == HMC_T_CORR_GAUSS && gauss_tc_supported(t)) || (t.id == HMC_T_LOGREG && logreg_gemm_supported(t));
+  return (t.id == HMC_T_CORR_GAUSS && gauss_tc_supported(t)) ||
+         (t.id == HMC_T_LOGREG && (logreg_tc_supported(t) || logreg_gemm_supported(t)));
 }
 
 size_t nuts_dense_chain_bytes(int64_t C) { return static_cast<size_t>(C) * sizeof(NdChain); }
@@ -535,21 +544,33 @@ cudaError_t launch_nuts_dense_transition(const hmc_target& t, const StepArgs& a,
   na.s = a;
   na.ld = (t.dim + 3) / 4 * 4;
   na.max_depth = nd.max_depth;
+  na.S = 1;
   if (nd.mode == kModeGauss) {
     na.xhi = nd.tc->xhi[0];
     na.xlo = nd.tc->xlo[0];
     na.p = nd.tc->p;
     na.part = nd.tc->gL;
-  } else {
+  } else if (nd.mode == kModeLogreg) {
+    // (S is set when the products are enqueued)
     na.xhi = nd.lrg->xhi[0];
     na.xlo = nd.lrg->xlo[0];
     na.p = nd.lrg->p;
     na.part = nd.lrg->part;
     na.lp_part = nd.lrg->lp_part;
-    na.ntot = nd.lrg->ntot;
-    na.nrt = nd.lrg->nrt;
+    na.nlp = nd.lrg->nrt;             // the row tiles' columns of [C x ntot]
+    na.lp_cs = nd.lrg->ntot;
+    na.lp_rs = 1;
+  } else {
+    na.xhi = nd.lrtc->thi;
+    na.xlo = nd.lrtc->tlo;
+    na.p = nd.lrtc->p;
+    na.part = nd.lrtc->Gpart;
+    na.S = nd.lrtc->nsplit;
+    na.lp_part = nd.lrtc->lp_part;
+    na.nlp = nd.lrtc->nsplit;         // [nsplit x C]
+    na.lp_cs = 1;
+    na.lp_rs = a.C;
   }
-  na.S = 1;
   na.scratch = nd.scratch;
   na.st = static_cast<NdChain*>(nd.chains);
   na.active = nd.active;

@@ -59,11 +59,13 @@ def logreg_problem(C, D, N, eps, depth, seed=12):
 
 
 # (kind, chains, dim, data rows, step size, max depth): several 128-chain
-# tiles with a ragged last tile; dims with one and two 128-float lane blocks,
-# a logistic regression whose rows are padded (dim 5 -> 8) and ragged data
-# tiles (N = 300, 257)
+# tiles with a ragged last tile; dims with one and two 128-float lane blocks;
+# logistic regressions on the CTA-pair kernel (dim a multiple of 4, <= 128:
+# two pairs, the second ragged, data rows split over ranges) and on the
+# one-CTA tile products (rows padded, dim 5 -> 8; dim 130; ragged data tiles)
 CASES = [("corr_gauss", 300, 64, 0, 0.3, 6), ("corr_gauss", 130, 256, 0, 0.25, 5),
          ("corr_gauss", 37, 8, 0, 0.5, 10),
+         ("logreg", 300, 32, 1000, 0.03, 6), ("logreg", 280, 128, 2000, 0.01, 5),
          ("logreg", 200, 5, 300, 0.06, 6), ("logreg", 130, 130, 257, 0.02, 5)]
 
 
