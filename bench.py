@@ -87,6 +87,10 @@ def parse():
     ap.add_argument("--serve-duration", type=float, default=10.0)
     ap.add_argument("--serve-scale", type=float, default=0.1,
                     help="serve: scale of chains, samples and data rows of every request")
+    ap.add_argument("--serve-workers", type=int, default=4,
+                    help="serve: admission threads (context creation, graph capture, teardown)")
+    ap.add_argument("--serve-max-wall", type=float, default=0.0,
+                    help="serve: stop after this many seconds (0: 6 x the duration, at least 60)")
     ap.add_argument("--small", action="store_true",
                     help="20 burn-in + 20 kept transitions (profiling runs)")
     return ap.parse_args()
@@ -418,11 +422,14 @@ def run_serve(args):
     launches0 = hmc.hmc_kernel_launch_count()
     clocks = ClockSampler(0)
     clocks.start()
-    server = serve.Server(hbm_budget_bytes=150 * 2 ** 30, slots=32)
-    jobs = server.run(reqs, max_wall=max(60.0, 6 * args.serve_duration))
+    server = serve.Server(hbm_budget_bytes=150 * 2 ** 30, slots=32, workers=args.serve_workers)
+    max_wall = args.serve_max_wall or max(60.0, 6 * args.serve_duration)
+    jobs = server.run(reqs, max_wall=max_wall)
     clk = clocks.stop()
     summ = serve.summarize(jobs, server.wall)
     summ["host_s"] = dict(server.host_s)
+    summ["backlog_at_end"] = server.backlog
+    summ["stopped_at_max_wall"] = server.backlog > 0
     line = {"metric": "leapfrog grad-evals/s", "value": summ["grad_evals_per_s"],
             "unit": "grad-evals/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": 1000.0 * server.wall, "higher_is_better": True, "scaling": "weak",
@@ -430,9 +437,11 @@ def run_serve(args):
             "config": {"workload": f"served stream: Poisson {args.serve_rate}/s for "
                                    f"{args.serve_duration} s, requests from corr_gauss / logreg / "
                                    f"uneven families, chains/samples/data rows scaled by "
-                                   f"{args.serve_scale}, HBM budget 150 GB, 32 slots",
+                                   f"{args.serve_scale}, HBM budget 150 GB, 32 slots, "
+                                   f"{args.serve_workers} admission threads, run stopped after "
+                                   f"{max_wall:.0f} s of wall time at the latest",
                        "impl": "continuous batching (slot streams, admission by HBM budget)"},
-            "serve": summ, "min_ess_per_s": summ["min_ess_per_s"],
+            "serve": summ, "min_ess_per_s": summ["ess_per_s"],
             "gpu_launches": int(hmc.hmc_kernel_launch_count() - launches0), "clocks": clk,
             "roofline": None, "cpu_baseline": None, "e2e": None}
     print(json.dumps(line), flush=True)

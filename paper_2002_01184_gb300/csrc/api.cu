@@ -284,7 +284,15 @@ CreatePlan plan_create(const hmc_target& t, int64_t num_chains, const hmc_config
   // logistic regressions with long data passes or much work per gradient
   // (chains x rows x dim above 2^22): tensor-core products; small ones: the
   // shared-memory SIMT transition
-  const bool lr_big = t.id == HMC_T_LOGREG && (t.n_data > 2048 || num_chains * t.n_data * t.dim > (1ll << 22));
+  // A context whose shared-memory grid (one CTA per 8 chains) covers under
+  // half of the SMs streams each gradient's data pass through few SMs, at
+  // about 9e9 multiply-adds/s per CTA (8 chains x 2000 rows x 128 dims:
+  // 0.46 ms per leapfrog step): from 10^4 data entries on, the tensor-core
+  // products' fixed ~15 us per gradient costs less.
+  const bool lr_narrow = t.id == HMC_T_LOGREG && (num_chains + 7) / 8 < hmc::current_sm_count() / 2 &&
+                         t.n_data * t.dim > 10000;
+  const bool lr_big = t.id == HMC_T_LOGREG &&
+                      (t.n_data > 2048 || num_chains * t.n_data * t.dim > (1ll << 22) || lr_narrow);
   // (HMC_IMPL_FUSED_TENSOR and _SIMT fix the choice, for the batch's autotuner)
   const bool lr_tensor = (q.cfg.impl == HMC_IMPL_FUSED && lr_big) || q.cfg.impl == HMC_IMPL_FUSED_TENSOR;
   q.use_lrtc = lr_tensor && hmc::logreg_tc_supported(t);

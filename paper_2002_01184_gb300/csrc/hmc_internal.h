@@ -63,6 +63,9 @@ cudaError_t launch_vjp(const hmc_target& t, int64_t C, const float* x, const flo
 // Set the error text that hmc_last_error(NULL) returns on this thread.
 void set_global_error(const std::string& msg);
 
+// SM count of the current device; 152, a GB300's, when none can be queried.
+int current_sm_count();
+
 // Bytes of scratch the batched gradient of `t` needs for C chains.
 size_t grad_workspace_bytes(const hmc_target& t, int64_t C);
 

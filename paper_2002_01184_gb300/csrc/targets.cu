@@ -20,6 +20,19 @@ namespace hmc {
 
 std::atomic<uint64_t> g_launches{0};
 
+// SM count of the current device (the logistic regression's split-K and
+// path decisions); 152, a GB300's count, when no device can be queried.
+int current_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    return 152;
+  }
+  return sms;
+}
+
+
 namespace {
 
 constexpr int kBM = 64, kBN = 64, kBK = 16, kGemmThreads = 256;
@@ -236,18 +249,6 @@ struct LogregPlan {
 };
 
 inline size_t align256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
-
-// SM count of the current device (the split-K decision below fills four
-// waves of it); 152, a GB300's count, when no device can be queried.
-int current_sm_count() {
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
-    cudaGetLastError();
-    return 152;
-  }
-  return sms;
-}
 
 LogregPlan logreg_plan(int64_t C, int D, int64_t N) {
   LogregPlan p{};
