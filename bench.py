@@ -42,13 +42,9 @@ FP32_LANES_PER_SM = 128
 # (kernel, target, chains, dim, leapfrog steps).  Absent -> traffic is null.
 PROFILED_TRAFFIC = {}
 
-# NUTS (Section 2.3): default maximum tree depth, and the float32 operations
-# of one leaf per dimension -- leapfrog kick, drift, kick (6), the kinetic
-# energy (2), the elementwise target's value and gradient (about 2), and on
-# average one closing span's U-turn test (difference and two dot products, 5)
+# NUTS (Section 2.3): default maximum tree depth
 NUTS_MAX_DEPTH = 10
 NUTS_LABEL = " NUTS max_depth=10"
-NUTS_FLOPS_PER_DIM = 15
 
 L2_FLUSH_BYTES = 256 << 20
 
@@ -144,6 +140,29 @@ def peaks():
             d = json.load(f)
         return d, "measured"
     return dict(FALLBACK), "fallback"
+
+
+def nuts_leaf_latency(p, eps, transitions=64):
+    """Seconds per leaf of one NUTS chain alone (one warp on the GPU) on the
+    workload's target and dim at step size eps: `transitions` fixed-step
+    transitions in one launch, timed on the device."""
+    import copy
+    import torch
+    from paper_2002_01184_gb300 import hmc
+    from paper_2002_01184_gb300.sampler import Sampler
+    q = copy.copy(p)
+    q.num_chains, q.x0 = 1, p.x0[:1].copy()
+    s = Sampler(q, adapt=False, step_size=eps, proposal=hmc.HMC_PROPOSAL_NUTS)
+    x = torch.as_tensor(q.x0).cuda()
+    s.sample_chain(x, 0, 4)                    # warm-up
+    l0 = hmc.hmc_nuts_leapfrog_count(s.ctx)
+    hmc.hmc_profile_dominant_kernel(s.ctx, 1)
+    s.sample_chain(x, 0, transitions)
+    torch.cuda.synchronize()
+    pr = hmc.hmc_profile_read(s.ctx)
+    leaves = hmc.hmc_nuts_leapfrog_count(s.ctx) - l0
+    s.close()
+    return pr["avg_ms"] * pr["samples"] / 1000.0 / max(leaves, 1)
 
 
 def grad_flops_per_eval(p):
@@ -583,12 +602,19 @@ def main():
         # fixed-step-size run): one more, untimed step with every launch
         # timed gives the k_nuts time of a whole step
         hmc.hmc_profile_dominant_kernel(s.ctx, 1)
+        crit0 = hmc.hmc_nuts_leaf_iterations(s.ctx)
         step()
         torch.cuda.synchronize()
+        crit_per_step = hmc.hmc_nuts_leaf_iterations(s.ctx) - crit0
         pn = hmc.hmc_profile_read(s.ctx)
         prof = {"samples": 0}
         if pn["samples"] and pn["samples"] == pn["launches"]:
             prof = {"avg_ms": pn["avg_ms"] * pn["samples"], "samples": pn["samples"]}
+        elif pn["samples"]:
+            # more launches than the timer keeps (the last 2048): their mean
+            # times the step's launch count
+            prof = {"avg_ms": pn["avg_ms"] * pn["launches"], "samples": pn["samples"],
+                    "sampled_of": pn["launches"]}
         evals_per_launch = evals_per_step - C              # per step
     roof = None
     if prof["samples"]:
@@ -598,7 +624,8 @@ def main():
                   "timed_launches": prof["samples"], "grad_evals_per_launch": evals_per_launch}
         if nuts:
             common = {"kernel": kname, "kernel_ms_per_step": prof["avg_ms"],
-                      "launches_per_step": prof["samples"], "leapfrog_steps_per_step": evals_per_launch}
+                      "launches_per_step": prof.get("sampled_of", prof["samples"]),
+                      "timed_launches": prof["samples"], "leapfrog_steps_per_step": evals_per_launch}
         if flops is not None and hmc.hmc_uses_tensor_cores(s.ctx):
             # 3xTF32: algorithmic flops (2 D^2 per gradient evaluation) against
             # the dense TF32 peak / 3 (three tf32 products per float32 product)
@@ -609,14 +636,18 @@ def main():
                     "peak_source": f"{src} bf16 {pk['bf16_tflops']:.0f} TFLOP/s x (1.1/2.25 nominal tf32:bf16) / 3",
                     **common}
         elif nuts:
-            # warp per chain, state in registers: float32 ALU work per leaf
-            achieved = NUTS_FLOPS_PER_DIM * D * evals_per_launch / kernel_s / 1e12
-            sm_max = pk.get("sm_max_mhz", 2070.0)
-            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-            roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
-                    "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
-                    "flops_per_leaf": f"{NUTS_FLOPS_PER_DIM} x dim", **common}
+            # warp per chain: a launch cannot end before its longest chain has
+            # built its leaves one after another.  Bound: that critical path
+            # at the per-leaf latency of one chain running alone (measured
+            # here on the same target, dim and final step size)
+            t_leaf = nuts_leaf_latency(p, final_eps)
+            achieved = crit_per_step / kernel_s
+            peak = 1.0 / t_leaf
+            roof = {"bound": "latency", "achieved": achieved, "peak": peak,
+                    "unit": "critical-path leaves/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": f"measured: one chain alone, {t_leaf * 1e9:.0f} ns per leaf",
+                    "critical_path_leaves_per_step": crit_per_step,
+                    "leapfrog_steps_per_critical_leaf": evals_per_launch / crit_per_step, **common}
         elif flops is not None:
             # SIMT float32 products: FP32-pipe roofline from unit counts and clock
             achieved = flops * evals_per_launch / kernel_s / 1e12

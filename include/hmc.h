@@ -347,12 +347,14 @@ hmc_status hmc_profile_read(hmc_ctx* ctx, double* avg_ms, uint64_t* samples, uin
  * context does not run NUTS. */
 hmc_status hmc_nuts_leapfrog_count(hmc_ctx* ctx, uint64_t* out);
 
-/* NUTS on a dense target (CORR_GAUSS, LOGREG): the leaf iterations run on
- * this context since it was created -- one batched gradient of the chains
- * still building their trees each, so hmc_nuts_leapfrog_count /
- * (iterations x num_chains) is the fraction of chain rows that did useful
- * work.  Synchronises the context's stream.  HMC_E_INVALID for any other
- * context. */
+/* NUTS: the leaf steps on the schedule's critical path since the context was
+ * created.  Dense targets (CORR_GAUSS, LOGREG): the lockstep loop's
+ * iterations, one batched gradient of the chains still building their trees
+ * each (hmc_nuts_leapfrog_count / (iterations x num_chains) is the fraction
+ * of chain rows that did useful work).  STD_NORMAL, FUNNEL: the sum over
+ * launches of the longest chain's leaf count in the launch, the serial work
+ * no launch can finish before.  Synchronises the context's stream.
+ * HMC_E_INVALID if the context does not run NUTS. */
 hmc_status hmc_nuts_leaf_iterations(hmc_ctx* ctx, uint64_t* out);
 
 /* The composition's two halves as separate calls (Section 4.1:

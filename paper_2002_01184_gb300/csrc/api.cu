@@ -48,7 +48,9 @@ struct hmc_ctx {
   hmc::GaussTc tc;
   unsigned* grid_bar = nullptr;  // grid barrier of the multi-transition pair launch
   float* nuts_scratch = nullptr;           // NUTS: trajectory ends, candidates, span starts
-  unsigned long long* nuts_leaves = nullptr;   // NUTS: leapfrog steps so far
+  // NUTS: [0] leapfrog steps so far, [1] leaf steps on the schedule's
+  // critical path so far, [2] the running launch's longest chain (scratch)
+  unsigned long long* nuts_leaves = nullptr;
   bool nuts_dense = false;      // NUTS on a dense target: lockstep leaves, tensor-core products
   hmc::NutsDense nd;
   int64_t dom_transitions = 1;   // transitions per launch of the dominant kernel (last chain)
@@ -249,7 +251,7 @@ CreatePlan plan_create(const hmc_target& t, int64_t num_chains, const hmc_config
   add(8 * 2 * static_cast<size_t>(nblk));   // partial sums, two transitions' worth
   if (q.cfg.proposal == HMC_PROPOSAL_NUTS) {
     add(4 * hmc::nuts_scratch_floats(t, num_chains));
-    add(sizeof(unsigned long long));
+    add(3 * sizeof(unsigned long long));
     // dense targets: the tensor-core products' workspace, the trees' state,
     // the active flags, the loop counters and the iteration count
     q.nuts_dense = (t.id == HMC_T_CORR_GAUSS || t.id == HMC_T_LOGREG) && hmc::nuts_dense_supported(t);
@@ -268,7 +270,6 @@ CreatePlan plan_create(const hmc_target& t, int64_t num_chains, const hmc_config
       add(hmc::nuts_dense_chain_bytes(num_chains));
       add(C);
       add(4 * sizeof(unsigned));
-      add(sizeof(unsigned long long));
       q.grad_ws = hmc::grad_workspace_bytes(t, num_chains);
       if (q.grad_ws) add(q.grad_ws);
       return q;
@@ -676,8 +677,8 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
   if (e == cudaSuccess && ctx->cfg.proposal == HMC_PROPOSAL_NUTS) {
     e = hmc::nuts_prepare();
     if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->nuts_scratch, hmc::nuts_scratch_floats(*target, num_chains));
-    if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->nuts_leaves, 1);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->nuts_leaves, 0, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = ctx_alloc(ctx, &ctx->nuts_leaves, 3);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->nuts_leaves, 0, 3 * sizeof(unsigned long long), ctx->stream);
   }
   ctx->use_tc = plan.use_tc;
   if (e == cudaSuccess && ctx->use_tc) {
@@ -718,9 +719,8 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     nd.chains = ch;
     if (e == cudaSuccess) e = ctx_alloc(ctx, &nd.active, C);
     if (e == cudaSuccess) e = ctx_alloc(ctx, &nd.ctr, 4);
-    if (e == cudaSuccess) e = ctx_alloc(ctx, &nd.iters, 1);
+    nd.iters = ctx->nuts_leaves + 1;
     if (e == cudaSuccess) e = cudaMemsetAsync(nd.ctr, 0, 4 * sizeof(unsigned), ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(nd.iters, 0, sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = hmc::nuts_dense_prepare();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&nd.side, cudaStreamNonBlocking);
   }
@@ -842,10 +842,11 @@ hmc_status hmc_nuts_leapfrog_count(hmc_ctx* ctx, uint64_t* out) {
 
 hmc_status hmc_nuts_leaf_iterations(hmc_ctx* ctx, uint64_t* out) {
   if (!ctx || !out) return fail(ctx, HMC_E_INVALID, "NULL argument");
-  if (!ctx->nuts_dense) return fail(ctx, HMC_E_INVALID, "the context does not run NUTS on a dense target");
+  if (ctx->cfg.proposal != HMC_PROPOSAL_NUTS || !ctx->nuts_leaves)
+    return fail(ctx, HMC_E_INVALID, "the context does not run NUTS");
   unsigned long long v = 0;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, ctx->nd.iters, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&v, ctx->nuts_leaves + 1, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "read leaf iterations");
   *out = static_cast<uint64_t>(v);

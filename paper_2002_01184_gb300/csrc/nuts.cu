@@ -34,7 +34,8 @@ struct NutsArgs {
   float* scratch;                  // [C][kNutsSlots][Dp]
   int Dp;                          // D rounded up to 4
   int max_depth;
-  unsigned long long* leaves;      // total leapfrog steps (gradient evaluations)
+  unsigned long long* leaves;      // [0] leapfrog steps (gradient evaluations), [1] critical
+                                   // path (the launches' longest chains), [2] this launch's longest
   int T;                           // transitions in this launch (T > 1: none adapts)
   long long keep_from;             // transition whose new state is kept sample 0
   float* samples;                  // [K][C][D] kept states, or null
@@ -371,11 +372,18 @@ __global__ void __launch_bounds__(32 * kWarps, NB == 1 ? 7 : 4) k_nuts(NutsArgs 
       a.is_accepted[c] = static_cast<uint8_t>(moved);
       a.log_accept[c] = logf(prob);
       atomicAdd(na.leaves, leaves_total);
+      atomicMax(na.leaves + 2, leaves_total);
     }
   }
   // the last transition's statistic (the only one that can adapt)
-  accept_tile_finish<kWarps>(a.da, a.partials, prob, has_chain, a.C, a.t_full + na.T - 1,
-                             static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x));
+  const bool last = accept_tile_finish<kWarps>(a.da, a.partials, prob, has_chain, a.C, a.t_full + na.T - 1,
+                                               static_cast<int>(blockIdx.x), static_cast<int>(gridDim.x));
+  // the launch lasts at least as long as its longest chain's leaves: the
+  // critical path (the block that arrived last adds it)
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    na.leaves[1] += atomicExch(na.leaves + 2, 0ull);
+  }
 }
 
 template <int TARGET, int NB, bool SMEM>
