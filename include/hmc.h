@@ -312,9 +312,11 @@ hmc_status hmc_read_adaptation(hmc_ctx* ctx, double out[5]);
 hmc_status hmc_synchronize(hmc_ctx* ctx);
 
 /* 1 if the context's transitions run the tensor-core (tcgen05, 3xTF32)
- * kernels under HMC_IMPL_FUSED: CORR_GAUSS with dim % 4 == 0, or LOGREG with
- * n_data > 2048 or chains x n_data x dim > 2^22 (CTA pairs for dim % 4 == 0
- * and dim <= 128, one-CTA tile products otherwise).  0 otherwise. */
+ * kernels: CORR_GAUSS with dim % 4 == 0 under HMC_IMPL_FUSED; LOGREG under
+ * HMC_IMPL_FUSED_TENSOR, or under HMC_IMPL_FUSED with n_data > 2048, chains x
+ * n_data x dim > 2^22, or fewer than (SMs / 2) x 8 chains and n_data x dim
+ * > 10^4 (CTA pairs for dim <= 128, one-CTA tile products otherwise); NUTS
+ * on either dense target.  0 otherwise. */
 int32_t hmc_uses_tensor_cores(const hmc_ctx* ctx);
 
 /* Measurement support (no counterpart in the paper): the name of the kernel
@@ -449,7 +451,7 @@ hmc_status hmc_batch_create(int32_t num_posteriors, const hmc_target* targets,
  * chosen by measurement (an autotuner; no counterpart in the paper): the
  * grouped launch's 8-chain shared-memory SIMT tiles, or the tensor-core
  * products in a context of its own (128-chain x 128-row tiles on CTA pairs
- * for dim <= 128 and dim % 4 == 0, 128 x 64 one-CTA tiles otherwise).  One
+ * for dim <= 128, 128 x 64 one-CTA tiles otherwise).  One
  * transition of each path is timed on the device (after one untimed) from a
  * zero state with the configured step size fixed, and the faster is taken;
  * the answer is kept per shape (dim, rows, chains, leapfrog steps) for the

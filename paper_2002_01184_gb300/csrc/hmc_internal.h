@@ -320,6 +320,7 @@ struct LogregTc {
   float *thi = nullptr, *tlo = nullptr, *p = nullptr, *gL = nullptr, *lpL = nullptr, *h0 = nullptr;
   float *Gpart = nullptr, *lp_part = nullptr;
   int npad = 0, ntiles = 0, nsplit = 0, tps = 0, groups = 0, dpad = 0, n_data = 0;
+  int ld = 0;     // row length of the [C x ld] / [Npad x ld] arrays: dim rounded up to 4
 };
 
 bool logreg_tc_supported(const hmc_target& t);

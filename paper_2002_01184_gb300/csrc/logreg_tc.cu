@@ -21,7 +21,8 @@
 // summed in a fixed order by k_lr_update, which also applies the leapfrog
 // update.  A transition is: begin (momentum, half kick, drift), L x (grad,
 // update), accept.  For D <= 128 (tensor memory holds Z, R head / remainder
-// and G at once).
+// and G at once); the workspace's rows are padded to a multiple of 4 floats
+// (zeros), so any such D runs here.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -61,6 +62,7 @@ static_assert(8 * (2 * kStages + 5) + 16 <= 256, "barriers");
 
 struct LrTcArgs {
   int C, D, N, ntiles, tiles_per_split, nsplit, dpad;
+  int ld;                // row length of the workspace arrays (D rounded up to 4)
   int need_lp;           // log-likelihood partials too (last leapfrog step only)
   const float* y;        // [Npad]
   float* Gpart;          // [nsplit x C x D]
@@ -327,7 +329,7 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
       }
       ptx::tc_fence_after();
     }
-    float* gout = a.Gpart + (static_cast<int64_t>(split) * a.C + chain) * a.D;
+    float* gout = a.Gpart + (static_cast<int64_t>(split) * a.C + chain) * a.ld;
 #pragma unroll 1
     for (int cb = 0; cb < kGroupCols / 16; ++cb) {
       const int d0 = kGroupCols * group + 16 * cb;
@@ -342,7 +344,7 @@ k_lr_grad(const __grid_constant__ CUtensorMap mThi, const __grid_constant__ CUte
       if (ok && chain < a.C)
 #pragma unroll
         for (int k = 0; k < 16; ++k)
-          if (d0 + k < a.D) gout[d0 + k] = gv[k];
+          if (d0 + k < a.ld) gout[d0 + k] = gv[k];    // (zero past D: X's padding)
     }
     lpred[group * 128 + r] = lp_acc;
   }
@@ -369,10 +371,11 @@ constexpr int kWarpsPerBlock = 8;
 
 struct LrStepArgs {
   StepArgs s;
-  float* thi;       // [C x D] positions, tf32 head / remainder (A operand)
+  int ld;           // row length of the workspace arrays below (D rounded up to 4; zero past D)
+  float* thi;       // [C x ld] positions, tf32 head / remainder (A operand)
   float* tlo;
-  float* p;         // [C x D] momenta
-  float* gL;        // [C x D] gradient at the end of the trajectory
+  float* p;         // [C x ld] momenta
+  float* gL;        // [C x ld] gradient at the end of the trajectory
   float* lpL;       // [C]
   float* h0;        // [C]
   const float* Gpart;
@@ -388,7 +391,7 @@ __global__ void k_lr_begin(LrStepArgs b) {
   const int lane = threadIdx.x & 31;
   if (c >= a.C) return;
   const int D = a.D;
-  const int64_t row = static_cast<int64_t>(c) * D;
+  const int64_t row = static_cast<int64_t>(c) * D, wrow = static_cast<int64_t>(c) * b.ld;
   const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
   const float eps = a.da->eps;
   float kin = 0.f;
@@ -396,11 +399,11 @@ __global__ void k_lr_begin(LrStepArgs b) {
     const float z = momentum1(a.seed, static_cast<uint32_t>(d), chain, a.t);
     kin = fmaf(z, z, kin);
     const float p = fmaf(0.5f * eps, a.g[row + d], z);
-    b.p[row + d] = p;
+    b.p[wrow + d] = p;
     float hi, lo;
     split_tf32(fmaf(eps, p, a.x[row + d]), hi, lo);
-    b.thi[row + d] = hi;
-    b.tlo[row + d] = lo;
+    b.thi[wrow + d] = hi;
+    b.tlo[wrow + d] = lo;
   }
   kin = warp_sum(kin);
   if (lane == 0) b.h0[c] = -a.lp[c] + 0.5f * kin;
@@ -409,14 +412,14 @@ __global__ void k_lr_begin(LrStepArgs b) {
 // gradient and log p from the range partials (fixed order) and the prior;
 // leapfrog update (merged kicks + drift), or the final half kick.  One warp
 // per chain, four dims per lane (float4: every buffer here is the library's
-// own, 16-byte aligned, and D % 4 == 0 on this path), so that a lane's
-// loads of all range partials are in flight together.
+// own, 16-byte aligned, with rows of ld = D rounded up to 4), so that a
+// lane's loads of all range partials are in flight together.
 __global__ void k_lr_update(LrStepArgs b) {
   const StepArgs& a = b.s;
   const int c = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (c >= a.C) return;
-  const int D4 = a.D >> 2;
+  const int D4 = b.ld >> 2;           // (the padding stays zero: X's padding columns are zero)
   const int64_t row4 = static_cast<int64_t>(c) * D4;
   const int64_t split4 = static_cast<int64_t>(a.C) * D4;
   const float eps = a.da->eps;
@@ -476,10 +479,10 @@ __global__ void k_lr_accept(LrStepArgs b) {
   float prob = 0.f;
   if (has_chain) {
     const int D = a.D;
-    const int64_t row = static_cast<int64_t>(c) * D;
+    const int64_t row = static_cast<int64_t>(c) * D, wrow = static_cast<int64_t>(c) * b.ld;
     const uint32_t chain = static_cast<uint32_t>(c) + a.chain_offset;
     float kin = 0.f;
-    for (int d = lane; d < D; d += 32) kin = fmaf(b.p[row + d], b.p[row + d], kin);
+    for (int d = lane; d < D; d += 32) kin = fmaf(b.p[wrow + d], b.p[wrow + d], kin);
     kin = 0.5f * warp_sum(kin);
     const float lp1 = b.lpL[c];
     float la = b.h0[c] - (-lp1 + kin);
@@ -488,10 +491,10 @@ __global__ void k_lr_accept(LrStepArgs b) {
     if (lane == 0) acc = accept_log_uniform(a.seed, chain, a.t) < la;
     acc = __shfl_sync(0xffffffffu, acc, 0);
     for (int d = lane; d < D; d += 32) {
-      const int64_t e = row + d;
+      const int64_t e = row + d, w = wrow + d;
       if (acc) {
-        a.x[e] = b.thi[e] + b.tlo[e];
-        a.g[e] = b.gL[e];
+        a.x[e] = b.thi[w] + b.tlo[w];
+        a.g[e] = b.gL[w];
       }
       if (a.sample_out) a.sample_out[e] = a.x[e];
     }
@@ -555,6 +558,10 @@ bool map2d(CUtensorMap* m, const float* base, int64_t rows, int64_t cols, unsign
 
 inline size_t a1k(size_t b) { return (b + 1023) & ~static_cast<size_t>(1023); }
 
+// row length of the workspace arrays: the dim rounded up to 4 floats (TMA
+// strides are multiples of 16 bytes); the padding columns hold zeros
+inline int lr_ld(int dim) { return (dim + 3) / 4 * 4; }
+
 struct Plan {
   int npad, ntiles, groups, nsplit, tps, dpad;
 };
@@ -584,12 +591,13 @@ cudaError_t launch_lr_prepare(int N, int Npad, int D, int ld, const float* X, co
 }
 
 bool logreg_tc_supported(const hmc_target& t) {
-  return t.id == HMC_T_LOGREG && t.dim <= kMaxD && t.dim % 4 == 0 && encode() != nullptr;
+  return t.id == HMC_T_LOGREG && t.dim <= kMaxD && encode() != nullptr;
 }
 
 size_t logreg_tc_workspace_bytes(const hmc_target& t, int64_t C) {
   const Plan p = plan(t, C);
-  const size_t CD = static_cast<size_t>(C) * t.dim, ND = static_cast<size_t>(p.npad) * t.dim;
+  const size_t ld = static_cast<size_t>(lr_ld(t.dim));
+  const size_t CD = static_cast<size_t>(C) * ld, ND = static_cast<size_t>(p.npad) * ld;
   return 4 * a1k(ND * 4) + a1k(p.npad * 4) + 4 * a1k(CD * 4) + a1k(C * 4) * 2 +
          a1k(static_cast<size_t>(p.nsplit) * CD * 4) + a1k(static_cast<size_t>(p.nsplit) * C * 4);
 }
@@ -603,7 +611,8 @@ cudaError_t logreg_tc_setup(LogregTc* tc, const hmc_target& t, int64_t C, void* 
   tc->groups = p.groups;
   tc->dpad = p.dpad;
   tc->n_data = static_cast<int>(t.n_data);
-  const size_t CD = static_cast<size_t>(C) * t.dim, ND = static_cast<size_t>(p.npad) * t.dim;
+  tc->ld = lr_ld(t.dim);
+  const size_t CD = static_cast<size_t>(C) * tc->ld, ND = static_cast<size_t>(p.npad) * tc->ld;
   char* w = static_cast<char*>(ws);
   auto take = [&](size_t b) { char* q = w; w += a1k(b); return reinterpret_cast<float*>(q); };
   tc->Xhi = take(ND * 4);
@@ -619,20 +628,25 @@ cudaError_t logreg_tc_setup(LogregTc* tc, const hmc_target& t, int64_t C, void* 
   tc->h0 = take(C * 4);
   tc->Gpart = take(static_cast<size_t>(p.nsplit) * CD * 4);
   tc->lp_part = take(static_cast<size_t>(p.nsplit) * C * 4);
-  const bool ok = map2d(&tc->mThi, tc->thi, C, t.dim, 128) && map2d(&tc->mTlo, tc->tlo, C, t.dim, 128) &&
-                  map2d(&tc->mXhi, tc->Xhi, p.npad, t.dim, 64) &&
-                  map2d(&tc->mXlo, tc->Xlo, p.npad, t.dim, 64) &&
-                  map2d(&tc->mXThi, tc->XThi, t.dim, p.npad, 64) &&
-                  map2d(&tc->mXTlo, tc->XTlo, t.dim, p.npad, 64);
+  const int ld = tc->ld;
+  const bool ok = map2d(&tc->mThi, tc->thi, C, ld, 128) && map2d(&tc->mTlo, tc->tlo, C, ld, 128) &&
+                  map2d(&tc->mXhi, tc->Xhi, p.npad, ld, 64) &&
+                  map2d(&tc->mXlo, tc->Xlo, p.npad, ld, 64) &&
+                  map2d(&tc->mXThi, tc->XThi, ld, p.npad, 64) &&
+                  map2d(&tc->mXTlo, tc->XTlo, ld, p.npad, 64);
   if (!ok) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_lr_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(kSmem));
   if (e != cudaSuccess) return e;
-  const int64_t total = static_cast<int64_t>(p.npad) * t.dim;
+  const int64_t total = static_cast<int64_t>(p.npad) * ld;
   k_lr_prepare<<<static_cast<unsigned>(std::min<int64_t>((total + 255) / 256, 152 * 16)), 256, 0, s>>>(
-      static_cast<int>(t.n_data), p.npad, t.dim, t.dim, t.X, t.y, tc->Xhi, tc->Xlo, tc->XThi, tc->XTlo,
+      static_cast<int>(t.n_data), p.npad, t.dim, ld, t.X, t.y, tc->Xhi, tc->Xlo, tc->XThi, tc->XTlo,
       tc->ypad);
   count_launch();
+  // the positions' and momenta's padding columns (ld > D) are read but never
+  // written: zero once (thi, tlo, p, gL are contiguous)
+  e = cudaMemsetAsync(tc->thi, 0, reinterpret_cast<char*>(tc->gL) + a1k(CD * 4) - reinterpret_cast<char*>(tc->thi), s);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -651,6 +665,7 @@ cudaError_t launch_logreg_tc_grad(LogregTc& tc, int C, int D, const uint8_t* act
   g.N = tc.n_data;
   g.need_lp = 1;
   g.active = active;
+  g.ld = tc.ld;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2 * tc.groups, tc.nsplit);
   cfg.blockDim = dim3(kThreads);
@@ -673,6 +688,7 @@ cudaError_t launch_logreg_tc_transition(const StepArgs& a, LogregTc& tc, int* er
                                         KernelTimer* timer) {
   LrStepArgs b{};
   b.s = a;
+  b.ld = tc.ld;
   b.thi = tc.thi;
   b.tlo = tc.tlo;
   b.p = tc.p;
@@ -697,6 +713,7 @@ cudaError_t launch_logreg_tc_transition(const StepArgs& a, LogregTc& tc, int* er
   g.lp_part = tc.lp_part;
   g.err = err;
   g.N = tc.n_data;
+  g.ld = tc.ld;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2 * tc.groups, tc.nsplit);
   cfg.blockDim = dim3(kThreads);

@@ -118,8 +118,10 @@ LOGREG_CASES = [(130, 64, 2500, 0.01, 3), (200, 128, 4100, 0.005, 2), (64, 20, 2
                 # dims past the pair kernel's 128: one-CTA tile products (dim 260 leaves a
                 # ragged K-chunk, 2500 a ragged data tile)
                 (150, 160, 2500, 0.008, 3), (70, 260, 3001, 0.005, 2), (300, 512, 2100, 0.003, 2),
-                # rows padded to a multiple of 4 inside the workspace
-                (90, 203, 2300, 0.005, 2), (40, 37, 2100, 0.01, 3),
+                # rows padded to a multiple of 4 inside the workspace: one-CTA
+                # tiles (203), CTA pairs (37, 63, 127 over two ragged pairs)
+                (90, 203, 2300, 0.005, 2), (40, 37, 2100, 0.01, 3), (300, 63, 2200, 0.01, 2),
+                (140, 127, 2400, 0.006, 2),
                 # 38 x 8 = 304 tiles of G = R X fill two waves of the SMs: no K-split
                 # (the cases above split K and sum the splits)
                 (4864, 452, 2100, 0.003, 1),
@@ -135,7 +137,7 @@ def test_tensor_core_logreg_transition_matches_oracle(H, C, D, N, eps, L):
     p.x0 = (0.05 * np.random.default_rng(D).standard_normal((C, D))).astype(np.float32)
     s = Sampler(p, adapt=False)
     assert H.hmc_uses_tensor_cores(s.ctx)
-    pair = D <= 128 and D % 4 == 0
+    pair = D <= 128
     assert H.hmc_dominant_kernel_info(s.ctx)[0] == ("k_lr_grad" if pair else "k_gauss_tc_step<logreg>")
     x = torch.as_tensor(p.x0).cuda().contiguous()
     s.bootstrap(x)
