@@ -210,6 +210,31 @@ def test_sample_chain_graph_equals_steps(H, kind):
     assert la == lb and ia == ib
 
 
+@pytest.mark.parametrize("kind", ["corr_gauss", "logreg"])
+def test_host_entry_point_equals_device_entry_point(H, kind):
+    """hmc_sample_chain_host (state and traces in pinned host memory) runs
+    the same transitions as the device entry point."""
+    from paper_2002_01184_gb300.sampler import Sampler
+    p, _ = make(kind, 130, 16, 400, 0.4 if kind == "corr_gauss" else 0.08, 6)
+    p.adapt, p.num_burnin, p.num_results, p.target_accept = True, 5, 6, 0.8
+    s = Sampler(p, adapt=True, proposal=H.HMC_PROPOSAL_NUTS)
+    x = dev(p.x0)
+    samples, eps, acc = s.sample_chain(x, p.num_burnin, p.num_results)
+    torch.cuda.synchronize()
+    C, D, K = p.num_chains, p.dim, p.num_results
+    xh = torch.as_tensor(p.x0).clone().pin_memory()
+    sh = torch.empty((K, C, D), dtype=torch.float32).pin_memory()
+    eh = torch.empty(K, dtype=torch.float32).pin_memory()
+    ah = torch.empty((K, C), dtype=torch.uint8).pin_memory()
+    H.hmc_sample_chain_host(s.ctx, xh, p.num_burnin, K, sh, eh, ah)
+    H.hmc_synchronize(s.ctx)
+    np.testing.assert_array_equal(xh.numpy(), host(x))
+    np.testing.assert_array_equal(sh.numpy(), host(samples))
+    np.testing.assert_array_equal(eh.numpy(), host(eps))
+    np.testing.assert_array_equal(ah.numpy(), host(acc))
+    s.close()
+
+
 def test_dense_nuts_samples_the_gaussian(H):
     """sample_chain with NUTS and dual averaging on a 16-D correlated
     Gaussian: means and marginal variances of N(0, P^-1) within Monte Carlo

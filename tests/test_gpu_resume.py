@@ -36,12 +36,22 @@ def problems():
         # the tensor-core logistic regression (long data pass)
         "logreg": workloads.logreg(n_data=2500, dim=64, num_chains=256, num_burnin=4, num_results=4,
                                    num_leapfrog=5),
+        # NUTS on the dense targets: every range is captured with its leaf
+        # loops (num_leapfrog is the maximum tree depth)
+        "nuts_corr_gauss": workloads.corr_gauss(dim=64, num_chains=200, num_burnin=6, num_results=5,
+                                                num_leapfrog=6),
+        "nuts_logreg": workloads.logreg(n_data=1500, dim=24, num_chains=150, num_burnin=5, num_results=4,
+                                        num_leapfrog=6),
     }
 
 
-def run_whole(H, p):
+def proposal(H, kind):
+    return H.HMC_PROPOSAL_NUTS if kind.startswith("nuts") else H.HMC_PROPOSAL_LEAPFROG
+
+
+def run_whole(H, p, prop):
     from paper_2002_01184_gb300.sampler import Sampler
-    s = Sampler(p, adapt=True)
+    s = Sampler(p, adapt=True, proposal=prop)
     x = torch.as_tensor(p.x0).cuda().contiguous()
     samples, eps, acc = s.sample_chain(x, p.num_burnin, p.num_results)
     H.hmc_synchronize(s.ctx)
@@ -50,18 +60,19 @@ def run_whole(H, p):
     return out
 
 
-@pytest.mark.parametrize("kind", ["corr_gauss", "funnel", "logreg"])
+@pytest.mark.parametrize("kind", ["corr_gauss", "funnel", "logreg", "nuts_corr_gauss", "nuts_logreg"])
 @pytest.mark.parametrize("where", ["burn-in", "sampling"])
 def test_split_run_resumed_in_a_fresh_context_is_bit_identical(H, kind, where):
     from paper_2002_01184_gb300.sampler import Sampler
     p = problems()[kind]
+    prop = proposal(H, kind)
     B, K = p.num_burnin, p.num_results
     n = B + K
     k = B - 2 if where == "burn-in" else B + 2
-    x_ref, s_ref, e_ref, a_ref, da_ref = run_whole(H, p)
+    x_ref, s_ref, e_ref, a_ref, da_ref = run_whole(H, p, prop)
     C, D = p.num_chains, p.dim
     x = torch.as_tensor(p.x0).cuda().contiguous()
-    first = Sampler(p, adapt=True)
+    first = Sampler(p, adapt=True, proposal=prop)
     k1 = max(0, k - B)                         # kept transitions of the first piece
     s1 = torch.empty((max(k1, 1), C, D), device="cuda")
     e1 = torch.empty(max(k1, 1), device="cuda")
@@ -69,7 +80,7 @@ def test_split_run_resumed_in_a_fresh_context_is_bit_identical(H, kind, where):
     H.hmc_sample_chain_range(first.ctx, x, B, 0, k, s1, e1, a1)
     state = H.hmc_save_state(first.ctx)
     first.close()
-    second = Sampler(p, adapt=True)
+    second = Sampler(p, adapt=True, proposal=prop)
     H.hmc_restore_state(second.ctx, state)
     k2 = K - k1
     s2 = torch.empty((k2, C, D), device="cuda")

@@ -23,14 +23,19 @@ def H():
     return hmc
 
 
-@pytest.mark.parametrize("kind", ["corr_gauss", "funnel"])
+@pytest.mark.parametrize("kind", ["corr_gauss", "funnel", "nuts_corr_gauss"])
 def test_streaming_moments_equal_stored_trace_moments(H, kind):
     from paper_2002_01184_gb300.sampler import Sampler
+    prop = H.HMC_PROPOSAL_LEAPFROG
     if kind == "corr_gauss":
         p = workloads.corr_gauss(dim=64, num_chains=300, num_burnin=20, num_results=40)
+    elif kind == "nuts_corr_gauss":
+        # NUTS on a dense target: the moment updates ride in the captured graph
+        p = workloads.corr_gauss(dim=32, num_chains=150, num_burnin=10, num_results=20, num_leapfrog=6)
+        prop = H.HMC_PROPOSAL_NUTS
     else:
         p = workloads.funnel(dim=17, num_chains=100, num_burnin=20, num_results=40)
-    s = Sampler(p)
+    s = Sampler(p, proposal=prop)
     x = torch.as_tensor(p.x0).cuda().contiguous()
     samples, eps, acc = s.sample_chain(x, p.num_burnin, p.num_results)
     x2 = torch.as_tensor(p.x0).cuda().contiguous()
