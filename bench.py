@@ -410,6 +410,18 @@ def run_uneven_batch(args):
     clk = clocks.stop()
     launches = hmc.hmc_kernel_launch_count() - launches0
     ess = min(float(diagnostics.ess(smp, max_dims=16).min()) for smp in samples)
+    # the GEMM share: the logistic regressions' algorithmic flops (4 N D per
+    # gradient evaluation) over the whole step's time, against the 3xTF32
+    # peak -- a lower bound on the products' own fraction, since the step's
+    # time also holds the funnels and the leapfrog updates
+    pk, src = peaks()
+    gemm = sum(4.0 * p.n_data * p.dim * (p.num_chains * p.num_leapfrog * (B + K) + p.num_chains)
+               for p in probs if p.kind == "logreg")
+    peak = pk["bf16_tflops"] * TF32_PER_BF16 / 3.0
+    achieved = gemm / (ms / 1000.0) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "scope": "the logistic regressions' algorithmic flops over the whole step",
+            "peak_source": f"{src} bf16 {pk['bf16_tflops']:.0f} TFLOP/s x (1.1/2.25 nominal tf32:bf16) / 3"}
     line = {"metric": "leapfrog grad-evals/s", "value": evals / (ms / 1000.0), "unit": "grad-evals/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -422,7 +434,7 @@ def run_uneven_batch(args):
                        "posteriors": len(probs), "autotuner": tuner},
             "min_ess_per_s": ess / (ms / 1000.0), "min_ess": ess,
             "host_enqueue_ms_per_step": 1000.0 * t_enq / args.steps,
-            "gpu_launches": int(launches), "clocks": clk, "roofline": None, "cpu_baseline": None,
+            "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "cpu_baseline": None,
             "e2e": None}
     print(json.dumps(line), flush=True)
 

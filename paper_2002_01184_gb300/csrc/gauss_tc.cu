@@ -35,28 +35,37 @@ namespace hmc {
 namespace {
 
 constexpr int kBM = 128;          // chains per tile (MMA M)
-constexpr int kBN = 64;           // gradient columns per tile (MMA N)
+constexpr int kBN = 64;           // output columns per tile (MMA N) of the Gaussian's products
 constexpr int kBK = 32;           // K chunk: 32 floats = one 128-B swizzle row
-constexpr int kStages = 4;
 constexpr int kThreads = 192;
-constexpr uint32_t kTmemCols = 64;
 constexpr uint32_t kABytes = kBM * kBK * 4;                  // 16 KB
-constexpr uint32_t kBBytes = kBN * kBK * 4;                  // 8 KB
-constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;  // 48 KB
-constexpr size_t kSmemBytes = kStages * kStageBytes + 1024 + 256;
-static_assert(kBM * (kBN + 1) * 4 <= kStages * kStageBytes, "epilogue staging must fit the ring");
+
+// A tile of BN output columns (MMA N = 64, 128 or 256): the stage ring fills
+// the same 192 KB of shared memory with 4, 3 or 2 stages; the accumulator
+// takes BN tensor-memory columns.  Wider tiles re-read their A operand (the
+// chains' rows) fewer times: the logistic regression's products use them.
+template <int BN>
+struct Tile {
+  static constexpr int kStages = BN == 64 ? 4 : BN == 128 ? 3 : 2;
+  static constexpr uint32_t kBBytes = BN * kBK * 4;
+  static constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
+  static constexpr size_t kSmem = kStages * kStageBytes + 1024 + 256;
+  static constexpr uint32_t kTmemCols = BN;
+  static_assert(BN == 64 || BN == 128 || BN == 256, "tile width");
+  static_assert(kBM * (BN + 1) * 4 <= kStages * kStageBytes, "epilogue staging must fit the ring");
+  static_assert(kSmem <= 227 * 1024, "shared memory");
+};
+constexpr size_t kSmemBytes = Tile<kBN>::kSmem;
 
 // Epilogues of the tile product (the pipeline is the same for all three):
 //   kEpiGauss   G = -X P: the dense Gaussian's leapfrog update
 //   kEpiLrResid Z = Theta X^T (columns are data rows): R = y - sigmoid(Z)
 //               to HBM as tf32 head / remainder, 0 past the last row; on
 //               the last step the rows' log-likelihood terms per tile
-//   kEpiLrStep  G = R X (columns are dims): g = G - theta (the N(0, I)
-//               prior) and the leapfrog update; on the last step the
-//               prior's -|theta|^2 / 2 per tile
 //   kEpiStore   the raw product of K-split blockIdx.z, for a separate sum
-//               (G = R X when its few tiles would leave SMs idle)
-constexpr int kEpiGauss = 0, kEpiLrResid = 1, kEpiLrStep = 2, kEpiStore = 3;
+//               (G = R X, summed with the prior and the leapfrog update by
+//               k_lr_gemm_update; the dense Gaussian's X P under NUTS)
+constexpr int kEpiGauss = 0, kEpiLrResid = 1, kEpiStore = 3;
 
 struct TcStepArgs {
   int C, D;
@@ -85,7 +94,7 @@ struct TcStepArgs {
   const uint8_t* active;    // null, or per-chain flags: a tile with none set is skipped
 };
 
-template <int EPI>
+template <int EPI, int BN = kBN>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                 const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
@@ -93,13 +102,17 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  constexpr int kStages = Tile<BN>::kStages;
+  constexpr uint32_t kBBytes = Tile<BN>::kBBytes;
+  constexpr uint32_t kStageBytes = Tile<BN>::kStageBytes;
+  constexpr uint32_t kTmemCols = Tile<BN>::kTmemCols;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
   uint64_t* empty = full + kStages;
   uint64_t* acc_full = empty + kStages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
   if (a.active) {
     // NUTS: a tile whose chains have all finished their trees has no work
     const int r = threadIdx.x;
@@ -149,7 +162,7 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
-    constexpr uint32_t idesc = ptx::idesc_tf32(kBM, kBN);
+    constexpr uint32_t idesc = ptx::idesc_tf32(kBM, BN);
     for (int kc = 0; kc < nk; ++kc) {
       const int s = kc % kStages, round = kc / kStages;
       if (!ptx::mbar_wait(&full[s], round & 1)) {
@@ -182,9 +195,9 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
     ptx::tc_fence_after();
     const int quarter = warp & 3;
     float* stg = reinterpret_cast<float*>(smem);
-    constexpr int kLd = kBN + 1;
-#pragma unroll
-    for (int c0 = 0; c0 < kBN; c0 += 16) {
+    constexpr int kLd = BN + 1;
+#pragma unroll 4
+    for (int c0 = 0; c0 < BN; c0 += 16) {
       float acc[16];
       ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + c0, acc);
 #pragma unroll
@@ -208,7 +221,7 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
       if (EPI == kEpiStore) {
         float* out = a.part + (static_cast<int64_t>(blockIdx.z) * a.C + m) * a.ld;
 #pragma unroll
-        for (int h = 0; h < kBN / 32; ++h) {
+        for (int h = 0; h < BN / 32; ++h) {
           const int n = n0 + lane + 32 * h;
           if (n < a.D) out[n] = stg[r * kLd + lane + 32 * h];
         }
@@ -217,7 +230,7 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
       if (EPI == kEpiLrResid) {
         const int64_t rowoff = static_cast<int64_t>(m) * a.ldr;
 #pragma unroll
-        for (int h = 0; h < kBN / 32; ++h) {
+        for (int h = 0; h < BN / 32; ++h) {
           const int cl = lane + 32 * h;
           const int n = n0 + cl;
           if (n < a.ncols) {
@@ -237,13 +250,13 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
       } else {
         const int64_t rowoff = static_cast<int64_t>(m) * a.ld;
 #pragma unroll
-        for (int h = 0; h < kBN / 32; ++h) {
+        for (int h = 0; h < BN / 32; ++h) {
           const int cl = lane + 32 * h;
           const int n = n0 + cl;
           if (n < a.D) {
             const int64_t e = rowoff + n;
             const float x = xhi_in[e] + xlo_in[e];
-            const float g = EPI == kEpiGauss ? -stg[r * kLd + cl] : stg[r * kLd + cl] - x;
+            const float g = -stg[r * kLd + cl];
             if (!a.last) {
               const float p = fmaf(eps, g, pm[e]);
               pm[e] = p;
@@ -254,7 +267,7 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
             } else {
               pm[e] = fmaf(0.5f * eps, g, pm[e]);
               g_out[e] = g;
-              part = EPI == kEpiGauss ? fmaf(x, g, part) : fmaf(x, x, part);
+              part = fmaf(x, g, part);
             }
           }
         }
@@ -263,7 +276,7 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
         part = warp_sum(part);
         // Gaussian: log p = <x, g> / 2; logistic regression: the rows'
         // log-likelihood terms, or the prior's -|theta|^2 / 2
-        const float v = EPI == kEpiLrResid ? part : (EPI == kEpiGauss ? 0.5f * part : -0.5f * part);
+        const float v = EPI == kEpiLrResid ? part : 0.5f * part;
         if (lane == 0) a.lp_part[static_cast<int64_t>(m) * a.ntn + a.lp_col0 + blockIdx.y] = v;
       }
     }
@@ -364,9 +377,8 @@ __global__ void k_gauss_tc_accept(TcBeginAccept b) {
 }
 
 // The logistic regression's split-K gradient: the splits' products summed in
-// split order, minus theta (the prior), and the leapfrog update -- the
-// kEpiLrStep epilogue for a product computed in K-splits.  Warp per chain,
-// four dims per lane (ld % 4 == 0; the library's own buffers).
+// split order, minus theta (the prior), and the leapfrog update.  Warp per
+// chain, four dims per lane (ld % 4 == 0; the library's own buffers).
 struct LrSumArgs {
   int C, D, ld, S, last, nrt, ntot;
   const float* part;        // [S x C x ld]
@@ -618,8 +630,35 @@ namespace {
 // the gradient product's K)
 int64_t lr_npad(int64_t n) { return (n + kBN - 1) / kBN * kBN; }
 // the most K-splits of the gradient product G = R X
-constexpr int kMaxSplit = 8;
+constexpr int kMaxSplit = 16;
 size_t a1k(size_t b) { return (b + 1023) & ~static_cast<size_t>(1023); }
+
+// Tile widths: Z = Theta X^T in 128-row tiles of the data (each re-reads
+// the chains' rows of Theta); G = R X in one tile over the dims up to 256
+// wide (each re-reads R, C x Npad, from HBM: four times at 64 columns for a
+// dim of 256)
+struct LrTiles {
+  int bnz, bng, nrt, ndt;
+};
+template <int EPI>
+void launch_tile(int bn, dim3 grid, const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mc,
+                 const CUtensorMap& md, const TcStepArgs& st, cudaStream_t s) {
+  if (bn == 64)
+    k_gauss_tc_step<EPI, 64><<<grid, kThreads, Tile<64>::kSmem, s>>>(ma, mb, mc, md, st);
+  else if (bn == 128)
+    k_gauss_tc_step<EPI, 128><<<grid, kThreads, Tile<128>::kSmem, s>>>(ma, mb, mc, md, st);
+  else
+    k_gauss_tc_step<EPI, 256><<<grid, kThreads, Tile<256>::kSmem, s>>>(ma, mb, mc, md, st);
+}
+
+LrTiles lr_tiles(int64_t npad, int ld) {
+  LrTiles q{};
+  q.bnz = 128;
+  q.bng = ld <= 64 ? 64 : ld <= 128 ? 128 : 256;
+  q.nrt = static_cast<int>((npad + q.bnz - 1) / q.bnz);
+  q.ndt = (ld + q.bng - 1) / q.bng;
+  return q;
+}
 
 // G = R X has K = Npad but only (C / 128) x ndt tiles: split K when the tiles
 // would not fill two waves of the SMs, and sum the splits afterwards
@@ -642,7 +681,8 @@ void lr_splits(const LogregGemm& g, int C, int* S_out, int* kc_out) {
 size_t logreg_gemm_workspace_bytes(const hmc_target& t, int64_t C) {
   const size_t npad = static_cast<size_t>(lr_npad(t.n_data)), D = static_cast<size_t>((t.dim + 3) / 4 * 4);
   const size_t ND = npad * D, CN = static_cast<size_t>(C) * npad, CD = static_cast<size_t>(C) * D;
-  const size_t ntot = npad / kBN + (D + kBN - 1) / kBN;
+  const LrTiles q = lr_tiles(static_cast<int64_t>(npad), static_cast<int>(D));
+  const size_t ntot = static_cast<size_t>(q.nrt + q.ndt);
   return 4 * a1k(ND * 4) + a1k(npad * 4) + 2 * a1k(CN * 4) + 6 * a1k(CD * 4) +
          a1k(static_cast<size_t>(C) * ntot * 4) + a1k(static_cast<size_t>(C) * 4) + a1k(sizeof(int)) +
          a1k(kMaxSplit * CD * 4);
@@ -661,8 +701,11 @@ cudaError_t logreg_gemm_setup(LogregGemm* g, const hmc_target& t, int64_t C, voi
   cudaError_t qe = cudaGetDevice(&dev);
   if (qe == cudaSuccess) qe = cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
   if (qe != cudaSuccess) return qe;
-  g->nrt = static_cast<int>(npad / kBN);
-  g->ndt = static_cast<int>((D + kBN - 1) / kBN);
+  const LrTiles q = lr_tiles(npad, ld);
+  g->bnz = q.bnz;
+  g->bng = q.bng;
+  g->nrt = q.nrt;
+  g->ndt = q.ndt;
   g->ntot = g->nrt + g->ndt;
   char* w = static_cast<char*>(ws);
   auto take = [&](size_t bytes) { char* q = w; w += a1k(bytes); return reinterpret_cast<float*>(q); };
@@ -683,22 +726,27 @@ cudaError_t logreg_gemm_setup(LogregGemm* g, const hmc_target& t, int64_t C, voi
   g->h0 = take(static_cast<size_t>(C) * 4);
   g->err = reinterpret_cast<int*>(take(sizeof(int)));
   g->part = take(kMaxSplit * CD * 4);
-  bool ok = make_map(&g->mXhi, g->Xhi, npad, ld, kBN) && make_map(&g->mXlo, g->Xlo, npad, ld, kBN) &&
+  // (a box may be taller than the array: the rows past its end load as zeros)
+  bool ok = make_map(&g->mXhi, g->Xhi, npad, ld, q.bnz) && make_map(&g->mXlo, g->Xlo, npad, ld, q.bnz) &&
             make_map(&g->mRhi, g->Rhi, C, static_cast<int>(npad), kBM) &&
             make_map(&g->mRlo, g->Rlo, C, static_cast<int>(npad), kBM) &&
-            make_map(&g->mXThi, g->XThi, ld, static_cast<int>(npad), kBN) &&
-            make_map(&g->mXTlo, g->XTlo, ld, static_cast<int>(npad), kBN);
+            make_map(&g->mXThi, g->XThi, ld, static_cast<int>(npad), q.bng) &&
+            make_map(&g->mXTlo, g->XTlo, ld, static_cast<int>(npad), q.bng);
   for (int i = 0; i < 2 && ok; ++i)
     ok = make_map(&g->mThi[i], g->xhi[i], C, ld, kBM) && make_map(&g->mTlo[i], g->xlo[i], C, ld, kBM);
   if (!ok) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiLrResid>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
+  cudaError_t e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiLrResid, 128>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(Tile<128>::kSmem));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiLrStep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kSmemBytes));
+    e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiStore, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(Tile<64>::kSmem));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiStore>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kSmemBytes));
+    e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiStore, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(Tile<128>::kSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiStore, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(Tile<256>::kSmem));
   if (e == cudaSuccess)
     e = launch_lr_prepare(static_cast<int>(t.n_data), static_cast<int>(npad), t.dim, ld, t.X, t.y, g->Xhi,
                           g->Xlo, g->XThi, g->XTlo, g->ypad, s);
@@ -772,16 +820,14 @@ cudaError_t launch_logreg_gemm_transition(const StepArgs& a, LogregGemm& g, cuda
     st.da = a.da;
     st.err = g.err;
     if (timer) timer->begin(s);
-    k_gauss_tc_step<kEpiLrResid><<<dim3(mt, g.nrt), kThreads, kSmemBytes, s>>>(g.mThi[in], g.mTlo[in], g.mXhi,
-                                                                             g.mXlo, z);
-    if (S == 1) {
-      k_gauss_tc_step<kEpiLrStep><<<dim3(mt, g.ndt), kThreads, kSmemBytes, s>>>(g.mRhi, g.mRlo, g.mXThi,
-                                                                              g.mXTlo, st);
-    } else {
+    k_gauss_tc_step<kEpiLrResid, 128><<<dim3(mt, g.nrt), kThreads, Tile<128>::kSmem, s>>>(
+        g.mThi[in], g.mTlo[in], g.mXhi, g.mXlo, z);
+    {
+      // the split products G = R X, then their sum with the prior and the
+      // leapfrog update (k_lr_gemm_update)
       st.kc_split = kc_split;
       st.part = g.part;
-      k_gauss_tc_step<kEpiStore><<<dim3(mt, g.ndt, S), kThreads, kSmemBytes, s>>>(g.mRhi, g.mRlo, g.mXThi,
-                                                                                g.mXTlo, st);
+      launch_tile<kEpiStore>(g.bng, dim3(mt, g.ndt, S), g.mRhi, g.mRlo, g.mXThi, g.mXTlo, st, s);
       LrSumArgs u{a.C, a.D, g.ld, S, last ? 1 : 0, g.nrt, g.ntot, g.part, g.xhi[in], g.xlo[in],
                   g.xhi[out], g.xlo[out], g.p, g.gL, g.lp_part, a.da};
       k_lr_gemm_update<<<nb, 32 * kWarpsPerBlock, 0, s>>>(u);
@@ -831,10 +877,9 @@ cudaError_t launch_logreg_gemm_products(LogregGemm& g, int C, int D, const DASta
   st.da = da;
   st.err = g.err;
   st.active = active;
-  k_gauss_tc_step<kEpiLrResid><<<dim3(mt, g.nrt), kThreads, kSmemBytes, s>>>(g.mThi[0], g.mTlo[0], g.mXhi,
-                                                                           g.mXlo, z);
-  k_gauss_tc_step<kEpiStore><<<dim3(mt, g.ndt, S), kThreads, kSmemBytes, s>>>(g.mRhi, g.mRlo, g.mXThi, g.mXTlo,
-                                                                            st);
+  k_gauss_tc_step<kEpiLrResid, 128><<<dim3(mt, g.nrt), kThreads, Tile<128>::kSmem, s>>>(
+      g.mThi[0], g.mTlo[0], g.mXhi, g.mXlo, z);
+  launch_tile<kEpiStore>(g.bng, dim3(mt, g.ndt, S), g.mRhi, g.mRlo, g.mXThi, g.mXTlo, st, s);
   count_launch(2);
   *splits = S;
   return cudaGetLastError();

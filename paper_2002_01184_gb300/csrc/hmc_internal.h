@@ -216,17 +216,18 @@ struct GaussTc {
 cudaError_t launch_lr_prepare(int N, int Npad, int D, int ld, const float* X, const float* y, float* Xhi,
                               float* Xlo, float* XThi, float* XTlo, float* ypad, cudaStream_t s);
 
-// Logistic regression for dims the CTA-pair kernel does not take (dim > 128
-// or not a multiple of 4; rows padded to ld = dim rounded up to 4 inside the
-// workspace): each leapfrog gradient is two one-CTA tcgen05 products
-// (gauss_tc.cu's tile pipeline): Z = Theta X^T with R = y - sigmoid(Z) in
-// the epilogue (R to HBM as tf32 head / remainder), then G = R X with the
-// prior and the leapfrog update in the epilogue.
+// Logistic regression for dims the CTA-pair kernel does not take (dim > 128;
+// rows padded to ld = dim rounded up to 4 inside the workspace): each
+// leapfrog gradient is two one-CTA tcgen05 products (gauss_tc.cu's tile
+// pipeline): Z = Theta X^T in 128-row data tiles with R = y - sigmoid(Z) in
+// the epilogue (R to HBM as tf32 head / remainder), then G = R X in K-split
+// tiles up to 256 dims wide, summed with the prior and the leapfrog update
+// by k_lr_gemm_update.
 struct LogregGemm {
   CUtensorMap mThi[2], mTlo[2];  // positions [C x D], 128-row boxes (A of Z)
-  CUtensorMap mXhi, mXlo;        // X [Npad x D], 64-row boxes (B of Z)
+  CUtensorMap mXhi, mXlo;        // X [Npad x D], bnz-row boxes (B of Z)
   CUtensorMap mRhi, mRlo;        // R [C x Npad], 128-row boxes (A of G)
-  CUtensorMap mXThi, mXTlo;      // X^T [D x Npad], 64-row boxes (B of G)
+  CUtensorMap mXThi, mXTlo;      // X^T [D x Npad], bng-row boxes (B of G)
   float* Xhi = nullptr;
   float* Xlo = nullptr;
   float* XThi = nullptr;
@@ -242,6 +243,7 @@ struct LogregGemm {
   float* h0 = nullptr;
   int* err = nullptr;
   int npad = 0, nrt = 0, ndt = 0, ntot = 0;
+  int bnz = 64, bng = 64;        // tile widths of Z (data rows) and G = R X (dims)
   int nvalid = 0;                // data rows N
   int ld = 0;                    // padded row length of the workspace arrays
   float* part = nullptr;         // split-K products of G = R X [splits x C x ld]
