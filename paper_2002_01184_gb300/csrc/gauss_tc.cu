@@ -16,10 +16,11 @@
 // remainder (x = hi + lo exactly): the A operands the next product loads by
 // TMA.  Both buffers are ping-ponged between steps.
 //
-// Tile pipeline (192 threads): warp 0 allocates tensor memory and one lane
+// Tile pipeline (576 threads): warp 0 allocates tensor memory and one lane
 // issues the TMA loads of the A (x hi/lo: 128 x 32) and B (P hi/lo: 64 x 32)
-// K-chunks into a 4-stage ring; one lane of warp 1 issues the MMAs; warps 2-5
-// read the accumulator (one TMEM lane quarter each) and run the epilogue.
+// K-chunks into a ring of stages; one lane of warp 1 issues the MMAs; warps
+// 2-17 read the accumulator (four warps per TMEM lane quarter) and run the
+// epilogue.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -37,7 +38,12 @@ namespace {
 constexpr int kBM = 128;          // chains per tile (MMA M)
 constexpr int kBN = 64;           // output columns per tile (MMA N) of the Gaussian's products
 constexpr int kBK = 32;           // K chunk: 32 floats = one 128-B swizzle row
-constexpr int kThreads = 192;
+// warp 0 TMA, warp 1 MMA, 16 epilogue warps: four per tensor-memory lane
+// quarter, each moving a quarter of the tile's columns; then all sixteen walk
+// the tile's rows (with four, a tile's epilogue ran one warp per SM
+// sub-partition and, bound by latency, took longer than its MMAs)
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kABytes = kBM * kBK * 4;                  // 16 KB
 
 // A tile of BN output columns (MMA N = 64, 128 or 256): the stage ring fills
@@ -194,16 +200,18 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
     if (!ok) atomicExch(a.err, 1);
     ptx::tc_fence_after();
     const int quarter = warp & 3;
+    const int cgroup = (warp - 2) >> 2;               // which quarter of the columns
     float* stg = reinterpret_cast<float*>(smem);
     constexpr int kLd = BN + 1;
-#pragma unroll 4
-    for (int c0 = 0; c0 < BN; c0 += 16) {
+    constexpr int kCols = BN / 4;                     // 16, 32 or 64 per warp
+#pragma unroll
+    for (int c0 = cgroup * kCols; c0 < (cgroup + 1) * kCols; c0 += 16) {
       float acc[16];
       ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + c0, acc);
 #pragma unroll
       for (int j = 0; j < 16; ++j) stg[(quarter * 32 + lane) * kLd + c0 + j] = acc[j];
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
     const float eps = a.da->eps;
     const float* __restrict__ xhi_in = a.xhi_in;
     const float* __restrict__ xlo_in = a.xlo_in;
@@ -212,9 +220,9 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
     float* __restrict__ pm = a.p;
     float* __restrict__ g_out = a.g_out;
     const int ew = warp - 2;
-#pragma unroll 4
-    for (int rr = 0; rr < kBM / 4; ++rr) {
-      const int r = ew + 4 * rr;
+#pragma unroll 2
+    for (int rr = 0; rr < kBM / kEpiWarps; ++rr) {
+      const int r = ew + kEpiWarps * rr;
       const int m = m0 + r;
       if (!ok || m >= a.C) continue;                  // warp-uniform
       float part = 0.f;
