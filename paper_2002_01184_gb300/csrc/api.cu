@@ -269,7 +269,7 @@ CreatePlan plan_create(const hmc_target& t, int64_t num_chains, const hmc_config
       }
       add(hmc::nuts_dense_chain_bytes(num_chains));
       add(C);
-      add(4 * sizeof(unsigned));
+      add(8 * sizeof(unsigned));
       q.grad_ws = hmc::grad_workspace_bytes(t, num_chains);
       if (q.grad_ws) add(q.grad_ws);
       return q;
@@ -718,9 +718,9 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     e = ctx_alloc(ctx, &ch, hmc::nuts_dense_chain_bytes(num_chains));
     nd.chains = ch;
     if (e == cudaSuccess) e = ctx_alloc(ctx, &nd.active, C);
-    if (e == cudaSuccess) e = ctx_alloc(ctx, &nd.ctr, 4);
+    if (e == cudaSuccess) e = ctx_alloc(ctx, &nd.ctr, 8);
     nd.iters = ctx->nuts_leaves + 1;
-    if (e == cudaSuccess) e = cudaMemsetAsync(nd.ctr, 0, 4 * sizeof(unsigned), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(nd.ctr, 0, 8 * sizeof(unsigned), ctx->stream);
     if (e == cudaSuccess) e = hmc::nuts_dense_prepare();
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&nd.side, cudaStreamNonBlocking);
   }

@@ -349,7 +349,8 @@ struct NutsDense {
   LogregTc* lrtc = nullptr;
   void* chains = nullptr;         // per-chain tree state [C]
   uint8_t* active = nullptr;      // [C] chains still building their trees
-  unsigned* ctr = nullptr;        // [4] leaf-loop counters
+  unsigned* ctr = nullptr;        // [8] leaf-loop counters: [0-2] the graph loop's, [3] the
+                                  // persistent loop's grid barrier, [4-5] its chains left
   int* err = nullptr;             // the products' flag; 2: the leaf loop ran past its bound
   float* scratch = nullptr;       // [C][kNutsSlots][ld]
   unsigned long long* leaves = nullptr;   // leapfrog steps of the chains (useful gradients)

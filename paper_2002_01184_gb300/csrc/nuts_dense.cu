@@ -31,7 +31,10 @@
 // trajectory buffers of the tensor-core workspace.
 #include <cmath>
 
+#include <cuda.h>
+
 #include "nuts_common.cuh"
+#include "sm100_ptx.cuh"
 
 namespace hmc {
 
@@ -203,14 +206,13 @@ __global__ void __launch_bounds__(32 * kNdWarps) k_nuts_dense_begin(NdArgs na) {
   }
 }
 
-// One leaf of every chain still building its tree, then the loop condition.
+// One leaf of chain c (active, its gradient products done; the whole warp):
+// returns whether the chain is still building its tree.
 template <int MODE, int NB>
-__global__ void __launch_bounds__(32 * kNdWarps) k_nuts_dense_leaf(NdArgs na) {
+__device__ __forceinline__ bool nuts_leaf(const NdArgs& na, int c, int lane) {
   const StepArgs& a = na.s;
-  const int lane = threadIdx.x & 31;
-  const int c = blockIdx.x * kNdWarps + (threadIdx.x >> 5);
   bool still = false;
-  if (c < a.C && na.st[c].active) {
+  {
     NdChain cs = na.st[c];
     const int D = a.D, ld = na.ld;
     const Lanes<NB> L{lane, ld};
@@ -377,6 +379,17 @@ __global__ void __launch_bounds__(32 * kNdWarps) k_nuts_dense_leaf(NdArgs na) {
       na.active[c] = still ? 1 : 0;
     }
   }
+  return still;
+}
+
+// One leaf of every chain still building its tree, then the loop condition.
+template <int MODE, int NB>
+__global__ void __launch_bounds__(32 * kNdWarps) k_nuts_dense_leaf(NdArgs na) {
+  const StepArgs& a = na.s;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kNdWarps + (threadIdx.x >> 5);
+  bool still = false;
+  if (c < a.C && na.st[c].active) still = nuts_leaf<MODE, NB>(na, c, lane);
   // the loop condition: any chain left (the last block to arrive decides);
   // a tree has at most 2^max_depth - 1 leaves, so more iterations than that
   // mean a fault of the bookkeeping: the loop stops and the flag reports it
@@ -446,6 +459,231 @@ __global__ void __launch_bounds__(32 * kNdWarps) k_nuts_dense_finish(NdArgs na) 
                                static_cast<int>(gridDim.x));
 }
 
+// ---- the dense Gaussian's leaf loop in one persistent cooperative launch
+//
+// The graph loop above pays two kernel launches, the products' set-up
+// (barriers, tensor memory) and the WHILE node's relaunch every leaf: about
+// 15 us whatever the size.  For the Gaussian the whole loop runs instead in
+// one cooperative launch of one CTA per SM: each iteration is the tile
+// products X P of the 128-chain tiles still building (3xTF32 tcgen05, 64
+// output dims per tile, tiles dealt round-robin to the CTAs; the pipeline's
+// barriers and tensor memory set up once), a grid barrier, the leaf of every
+// active chain (warp per chain over all warps of the grid), and a second
+// grid barrier that also counts the chains left.  Grid barriers are bounded
+// (a wait that gives up sets the error flag and every CTA leaves the loop).
+constexpr int kPlBM = 128, kPlBN = 64, kPlBK = 32, kPlStages = 4;
+constexpr int kPlWarps = 18;                         // 0 TMA, 1 MMA, 2-17 epilogue (all 18: leaves)
+constexpr int kPlThreads = 32 * kPlWarps;
+constexpr uint32_t kPlABytes = kPlBM * kPlBK * 4;    // 16 KB: 128 chains x 32 dims
+constexpr uint32_t kPlBBytes = kPlBN * kPlBK * 4;    // 8 KB: 64 rows of P x 32 dims
+constexpr uint32_t kPlStage = 2 * kPlABytes + 2 * kPlBBytes;
+// ring + alignment slack + barriers (10 x 8 B), tensor-memory slot (16 B),
+// the tile list (kPlMaxTiles ints) and two flags
+constexpr size_t kPlSmem = kPlStages * kPlStage + 1024 + 512;
+constexpr int kPlMaxTiles = 64;                      // tiles of one CTA per iteration (the host checks)
+static_assert(10 * 8 + 16 + 4 * kPlMaxTiles + 8 <= 512, "small shared-memory area");
+
+__device__ __forceinline__ bool pl_grid_barrier(unsigned* counter, unsigned gen) {
+  __threadfence();
+  atomicAdd(counter, 1u);
+  const unsigned target = gen * gridDim.x;
+  const unsigned long long t0 = ptx::global_timer_ns();
+  while (*reinterpret_cast<volatile unsigned*>(counter) < target) {
+    if (ptx::global_timer_ns() - t0 > ptx::kWaitLimitNs) return false;
+  }
+  __threadfence();
+  return true;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kPlThreads, 1)
+k_nuts_gauss_loop(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                  const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                  NdArgs na) {
+  const StepArgs& a = na.s;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kPlStages * kPlStage);
+  uint64_t* empty = full + kPlStages;
+  uint64_t* acc_full = empty + kPlStages;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 1);
+  int* tile_id = reinterpret_cast<int*>(tmem_slot + 4);       // [kPlMaxTiles] this iteration's tiles
+  int* flags = tile_id + kPlMaxTiles;                          // [0] tiles, [1] leave the loop
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int C = a.C, D = a.D;
+  const int nk = (D + kPlBK - 1) / kPlBK;
+  const int mt = (C + kPlBM - 1) / kPlBM, ntn = (D + kPlBN - 1) / kPlBN;
+  const int ntiles = mt * ntn;
+  unsigned* bar = na.ctr + 3;            // grid barrier counter (zeroed before the launch)
+  unsigned* left = na.ctr + 4;           // [2] chains left, by iteration parity
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kPlStages; ++i) {
+      ptx::mbar_init(&full[i], 1);
+      ptx::mbar_init(&empty[i], 1);
+    }
+    ptx::mbar_init(acc_full, 1);
+    ptx::mbar_init(acc_empty, 32 * (kPlWarps - 2));
+    ptx::fence_mbar_init();
+    ptx::prefetch_tensormap(&mAhi);
+    ptx::prefetch_tensormap(&mAlo);
+    ptx::prefetch_tensormap(&mBhi);
+    ptx::prefetch_tensormap(&mBlo);
+    flags[1] = 0;
+  }
+  if (warp == 0) {
+    ptx::tmem_alloc(tmem_slot, kPlBN);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // pipeline positions, kept by the thread of each role across iterations
+  int pit = 0;          // producer: stages filled
+  int mit = 0;          // issuer: stages consumed
+  int mtile = 0;        // issuer: tiles committed
+  int etile = 0;        // epilogue: tiles drained
+  unsigned gen = 0;     // grid barriers met
+  const int gwarps = static_cast<int>(gridDim.x) * kPlWarps;
+  const int gw = static_cast<int>(blockIdx.x) * kPlWarps + warp;
+  for (int it = 0;; ++it) {
+    // ---- this CTA's tiles with an active chain (tiles blockIdx.x + k gridDim.x)
+    if (threadIdx.x == 0) flags[0] = 0;
+    __syncthreads();
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int m0 = (t / ntn) * kPlBM;
+      const int r = threadIdx.x;
+      const bool mine = r < kPlBM && m0 + r < C && na.active[m0 + r] != 0;
+      if (__syncthreads_or(mine) && threadIdx.x == 0 && flags[0] < kPlMaxTiles) tile_id[flags[0]++] = t;
+    }
+    __syncthreads();
+    const int nt = flags[0];
+    if (warp == 0 && lane == 0) {
+      // ---- TMA producer: x (head / remainder) of the tile's 128 chains, 64 rows of P
+      for (int k = 0; k < nt; ++k) {
+        const int t = tile_id[k];
+        const int m0 = (t / ntn) * kPlBM, n0 = (t % ntn) * kPlBN;
+        for (int kc = 0; kc < nk; ++kc, ++pit) {
+          const int st = pit % kPlStages, round = pit / kPlStages;
+          if (pit >= kPlStages && !ptx::mbar_wait(&empty[st], (round - 1) & 1)) {
+            atomicExch(na.err, 1);
+            break;
+          }
+          uint8_t* sp = smem + st * kPlStage;
+          ptx::mbar_arrive_expect_tx(&full[st], kPlStage);
+          const int kx = kc * kPlBK;
+          ptx::tma_load_2d(sp, &mAhi, &full[st], kx, m0);
+          ptx::tma_load_2d(sp + kPlABytes, &mAlo, &full[st], kx, m0);
+          ptx::tma_load_2d(sp + 2 * kPlABytes, &mBhi, &full[st], kx, n0);
+          ptx::tma_load_2d(sp + 2 * kPlABytes + kPlBBytes, &mBlo, &full[st], kx, n0);
+        }
+      }
+    } else if (warp == 1 && lane == 0) {
+      // ---- MMA issuer: 3xTF32, A_lo B_hi + A_hi B_lo + A_hi B_hi
+      constexpr uint32_t idesc = ptx::idesc_tf32(kPlBM, kPlBN);
+      for (int k = 0; k < nt; ++k, ++mtile) {
+        // the accumulator is free once the previous tile's epilogue read it
+        if (mtile > 0 && !ptx::mbar_wait(acc_empty, (mtile - 1) & 1)) atomicExch(na.err, 1);
+        ptx::tc_fence_after();
+        for (int kc = 0; kc < nk; ++kc, ++mit) {
+          const int st = mit % kPlStages, round = mit / kPlStages;
+          if (!ptx::mbar_wait(&full[st], round & 1)) {
+            atomicExch(na.err, 1);
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t sp = ptx::smem_u32(smem + st * kPlStage);
+#pragma unroll
+          for (int j = 0; j < kPlBK / 8; ++j) {
+            const uint64_t a_hi = ptx::sw128_kmajor_desc(sp + 32 * j);
+            const uint64_t a_lo = ptx::sw128_kmajor_desc(sp + kPlABytes + 32 * j);
+            const uint64_t b_hi = ptx::sw128_kmajor_desc(sp + 2 * kPlABytes + 32 * j);
+            const uint64_t b_lo = ptx::sw128_kmajor_desc(sp + 2 * kPlABytes + kPlBBytes + 32 * j);
+            ptx::mma_tf32(tmem, a_lo, b_hi, idesc, (kc | j) != 0 ? 1u : 0u);
+            ptx::mma_tf32(tmem, a_hi, b_lo, idesc, 1u);
+            ptx::mma_tf32(tmem, a_hi, b_hi, idesc, 1u);
+          }
+          ptx::mma_commit(&empty[st]);
+        }
+        ptx::mma_commit(acc_full);
+      }
+    } else if (warp >= 2) {
+      // ---- epilogue: warp (quarter q, column group g) stores X P for rows
+      // 32 q .. 32 q + 31 of the tile, columns 16 g .. 16 g + 15, each lane
+      // one row (64 contiguous bytes)
+      const int quarter = warp & 3, cg = (warp - 2) >> 2;
+      for (int k = 0; k < nt; ++k, ++etile) {
+        const int t = tile_id[k];
+        const int m0 = (t / ntn) * kPlBM, n0 = (t % ntn) * kPlBN;
+        if (!ptx::mbar_wait(acc_full, etile & 1)) atomicExch(na.err, 1);
+        ptx::tc_fence_after();
+        float v[16];
+        ptx::tmem_ld16(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + 16 * cg, v);
+        ptx::tc_fence_before();
+        ptx::mbar_arrive_local(acc_empty);
+        const int m = m0 + quarter * 32 + lane;
+        const int n = n0 + 16 * cg;
+        if (m < C) {
+          // D % 4 == 0 on this path: a float4 lies wholly inside or past the row
+          float4* out = reinterpret_cast<float4*>(const_cast<float*>(na.part) + static_cast<int64_t>(m) * D + n);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (n + 4 * q < D) out[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+      }
+    }
+    // ---- the products are in: every CTA's leaves may read them
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (!pl_grid_barrier(bar, ++gen)) {
+        atomicExch(na.err, 3);
+        flags[1] = 1;
+      }
+      if (blockIdx.x == 0) left[(it + 1) & 1] = 0u;     // the slot the next iteration counts in
+    }
+    __syncthreads();
+    if (flags[1]) break;
+    // ---- one leaf of every active chain
+    int mine = 0;
+    for (int c = gw; c < C; c += gwarps)
+      if (na.st[c].active && nuts_leaf<kModeGauss, NB>(na, c, lane)) ++mine;
+    // positions written for the next products' TMA loads (another proxy)
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    if (lane == 0 && mine) atomicAdd(&left[it & 1], static_cast<unsigned>(mine));
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (!pl_grid_barrier(bar, ++gen)) {
+        atomicExch(na.err, 3);
+        flags[1] = 1;
+      } else {
+        const unsigned total = *reinterpret_cast<volatile unsigned*>(&left[it & 1]);
+        if (blockIdx.x == 0) *na.iters += 1ull;
+        if (total == 0u) {
+          flags[1] = 1;
+        } else if (it + 1 >= (1 << na.max_depth)) {
+          if (blockIdx.x == 0) atomicExch(na.err, 2);
+          flags[1] = 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (flags[1]) break;
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, kPlBN);
+  }
+}
+
 template <int NB>
 cudaError_t set_leaf_attrs() {
   cudaError_t e = cudaFuncSetAttribute(k_nuts_dense_leaf<kModeGauss, NB>,
@@ -454,6 +692,39 @@ cudaError_t set_leaf_attrs() {
     e = cudaFuncSetAttribute(k_nuts_dense_leaf<kModeLogreg, NB>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              0);
   return e;
+}
+
+// CTAs of the Gaussian's persistent leaf loop for C chains, 0 if it does not
+// apply (every CTA's tiles must fit its list, all CTAs resident at once)
+int gauss_loop_grid(int C, int D, int* sms_out = nullptr) {
+  static int sms = 0, occ = -1;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+  }
+  if (occ < 0) {
+    int o = 0;
+    const int nb = (D + 3) / 4 * 4 <= 128 ? 1 : (D + 3) / 4 * 4 <= 256 ? 2 : 4;
+    cudaError_t e = nb == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nuts_gauss_loop<1>, kPlThreads, kPlSmem)
+                  : nb == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nuts_gauss_loop<2>, kPlThreads, kPlSmem)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_nuts_gauss_loop<4>, kPlThreads, kPlSmem);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    occ = o;
+  }
+  if (occ < 1) return 0;
+  if (sms_out) *sms_out = sms;
+  const int ntiles = ((C + kPlBM - 1) / kPlBM) * ((D + kPlBN - 1) / kPlBN);
+  const int want = std::max(ntiles, (C + kPlWarps - 1) / kPlWarps);
+  const int grid = std::min(sms * occ, want);
+  if (static_cast<int64_t>(grid) * kPlMaxTiles < ntiles) return 0;
+  return grid;
 }
 
 template <int NB>
@@ -467,6 +738,31 @@ cudaError_t enqueue_nb(const hmc_target& t, const NdArgs& base_args, NutsDense& 
   count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  const int pgrid = nd.mode == kModeGauss ? gauss_loop_grid(a.C, a.D) : 0;
+  if (pgrid > 0) {
+    // the whole leaf loop in one cooperative launch (grid barrier and the
+    // two chains-left counters zeroed first)
+    e = cudaMemsetAsync(nd.ctr + 3, 0, 3 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(pgrid));
+    cfg.blockDim = dim3(kPlThreads);
+    cfg.dynamicSmemBytes = kPlSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    GaussTc& tc = *nd.tc;
+    e = cudaLaunchKernelEx(&cfg, k_nuts_gauss_loop<NB>, tc.mAhi[0], tc.mAlo[0], tc.mBhi, tc.mBlo, na);
+    count_launch();
+    if (e != cudaSuccess) return e;
+    k_nuts_dense_finish<<<nb, 32 * kNdWarps, 0, s>>>(na);
+    count_launch();
+    if (timer) timer->end(s);
+    return cudaGetLastError();
+  }
   // the leaf loop: a WHILE node after everything captured so far
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaGraph_t graph = nullptr;
@@ -499,7 +795,7 @@ cudaError_t enqueue_nb(const hmc_target& t, const NdArgs& base_args, NutsDense& 
     int S = 1;
     e = launch_logreg_gemm_products(*nd.lrg, a.C, a.D, a.da, nd.active, &S, nd.side);
     na.S = S;
-  } else {
+  } else {     // kModeLogregPair
     e = launch_logreg_tc_grad(*nd.lrtc, a.C, a.D, nd.active, nd.err, nd.side);
   }
   if (e == cudaSuccess) {
@@ -535,11 +831,21 @@ cudaError_t nuts_dense_prepare() {
   cudaError_t e = set_leaf_attrs<1>();
   if (e == cudaSuccess) e = set_leaf_attrs<2>();
   if (e == cudaSuccess) e = set_leaf_attrs<4>();
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_nuts_gauss_loop<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kPlSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_nuts_gauss_loop<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kPlSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_nuts_gauss_loop<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kPlSmem));
   return e;
 }
 
 cudaError_t launch_nuts_dense_transition(const hmc_target& t, const StepArgs& a, NutsDense& nd, cudaStream_t s,
                                          KernelTimer* timer) {
+  if (nd.mode != kModeGauss && nd.mode != kModeLogreg && nd.mode != kModeLogregPair) return cudaErrorInvalidValue;
   NdArgs na{};
   na.s = a;
   na.ld = (t.dim + 3) / 4 * 4;
