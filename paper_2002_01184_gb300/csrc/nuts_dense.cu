@@ -10,19 +10,22 @@
 // iteration is
 //   (1) the batched gradient at every chain's drifted position: the 3xTF32
 //       tcgen05 products of gauss_tc.cu (one-CTA tiles) or, for a logistic
-//       regression of dim <= 128 (a multiple of 4), logreg_tc.cu's CTA-pair
-//       kernel; a tile whose chains have all stopped is skipped;
+//       regression of dim <= 128, logreg_tc.cu's CTA-pair kernel; a tile
+//       whose chains have all stopped is skipped;
 //   (2) one warp-per-chain kernel that finishes the leaf -- the gradient's
 //       epilogue (sign, prior, split sum, log p), second half kick, energy,
 //       slice and divergence tests, the candidate choice, the U-turn tests of
 //       the spans that close, the subtree's and the trajectory's bookkeeping
 //       -- and starts the next leaf (first half kick and drift of the chains
 //       still building).
-// The iterations are the body of a CUDA-graph conditional WHILE node: the leaf
-// kernel's last block clears the condition when no chain is left, so a
-// transition costs as many iterations as its deepest tree and the host never
-// waits on the device in between.  A chain's result depends only on its own
-// row of every product, so it is the same in any batch.
+// For the logistic regression the iterations are the body of a CUDA-graph
+// conditional WHILE node: the leaf kernel's last block clears the condition
+// when no chain is left.  For the Gaussian the whole loop is one persistent
+// cooperative launch (k_nuts_gauss_loop, below), products and leaves
+// separated by bounded grid barriers.  Either way a transition costs as many
+// iterations as its deepest tree and the host never waits on the device in
+// between.  A chain's result depends only on its own row of every product,
+// so it is the same in any batch.
 //
 // Per chain, the tree's scalars (NdChain) and a scratch of kNutsSlots rows of
 // the padded row length (the two trajectory ends, the candidates, the span

@@ -1,6 +1,7 @@
 """NUTS on the dense targets (Section 2.3 over the correlated Gaussian and
 the Bayesian logistic regression): the chains advance in lockstep, one leaf
-per iteration of a CUDA-graph loop whose gradients are tensor-core products.
+per iteration whose gradients are tensor-core products (a persistent launch
+for the Gaussian, a CUDA-graph loop for the logistic regression).
 Teacher-forced transitions against the float64 oracle, the loop's length,
 independence of the batch, the graph path against single steps, and the
 moments of an adapted chain."""
