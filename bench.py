@@ -89,13 +89,20 @@ def parse():
                     help="serve: stop after this many seconds (0: 6 x the duration, at least 60)")
     ap.add_argument("--small", action="store_true",
                     help="20 burn-in + 20 kept transitions (profiling runs)")
+    ap.add_argument("--logreg-shape", default=None, metavar="D,N,C",
+                    help="logreg: dim, data rows and chains instead of 128, 20000, 2048 (e.g. one "
+                         "of the uneven batch's shapes, for profiling)")
     return ap.parse_args()
 
 
-def make_problem(name):
+def make_problem(name, logreg_shape=None):
     from paper_2002_01184_gb300 import workloads
     if name == "corr_gauss":
         return workloads.corr_gauss(), "corr_gauss D=256 P=AA^T/D+0.1I C=4096 L=16 DA(0.65) B=1000 K=2000"
+    if name == "logreg" and logreg_shape:
+        D, N, C = (int(v) for v in logreg_shape.split(","))
+        return (workloads.logreg(n_data=N, dim=D, num_chains=C),
+                f"logreg N={N} D={D} C={C} L=10 DA(0.8) B=500 K=1000")
     if name == "logreg":
         return workloads.logreg(), "logreg N=20000 D=128 C=2048 L=10 DA(0.8) B=500 K=1000"
     if name == "funnel":
@@ -254,7 +261,7 @@ def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return
-    p, wl = make_problem(args.workload)
+    p, wl = make_problem(args.workload, args.logreg_shape)
     if args.proposal == "nuts":
         p.num_leapfrog = NUTS_MAX_DEPTH
         wl += NUTS_LABEL
@@ -504,7 +511,7 @@ def main():
     from paper_2002_01184_gb300 import diagnostics, hmc
     from paper_2002_01184_gb300.sampler import Sampler
 
-    p, wl = make_problem(args.workload)
+    p, wl = make_problem(args.workload, args.logreg_shape)
     if args.small:
         p.num_burnin, p.num_results = 20, 20
         wl += " (profiling run: B=20 K=20)"
