@@ -126,7 +126,10 @@ LOGREG_CASES = [(130, 64, 2500, 0.01, 3), (200, 128, 4100, 0.005, 2), (64, 20, 2
                 # (the cases above split K and sum the splits)
                 (4864, 452, 2100, 0.003, 1),
                 # short data passes with much work per gradient (chains x rows x dim > 2^22)
-                (600, 100, 1500, 0.005, 2), (500, 90, 1000, 0.006, 2)]
+                (600, 100, 1500, 0.005, 2), (500, 90, 1000, 0.006, 2),
+                # CTA pairs whose ranges of (chain group, data tile) items cross
+                # from one group into the next (3 groups x 157 tiles over the pairs)
+                (600, 64, 20000, 0.002, 2)]
 
 
 @pytest.mark.parametrize("C,D,N,eps,L", LOGREG_CASES)
