@@ -50,9 +50,12 @@ constexpr uint32_t kABytes = kBM * kBK * 4;                  // 16 KB
 // the same 192 KB of shared memory with 4, 3 or 2 stages; the accumulator
 // takes BN tensor-memory columns.  Wider tiles re-read their A operand (the
 // chains' rows) fewer times: the logistic regression's products use them.
-template <int BN>
+template <int BN, int ST = (BN == 64 ? 4 : BN == 128 ? 3 : 2)>
 struct Tile {
-  static constexpr int kStages = BN == 64 ? 4 : BN == 128 ? 3 : 2;
+  static constexpr int kStages = ST;
+  // two CTAs per SM when the ring is small enough (so that one's epilogue
+  // overlaps the other's products)
+  static constexpr int kCtasPerSm = (BN == 64 && ST == 2) ? 2 : 1;
   static constexpr uint32_t kBBytes = BN * kBK * 4;
   static constexpr uint32_t kStageBytes = 2 * kABytes + 2 * kBBytes;
   static constexpr size_t kSmem = kStages * kStageBytes + 1024 + 256;
@@ -100,18 +103,19 @@ struct TcStepArgs {
   const uint8_t* active;    // null, or per-chain flags: a tile with none set is skipped
 };
 
-template <int EPI, int BN = kBN>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int EPI, int BN = kBN, int ST = Tile<BN>::kStages>
+__global__ void __launch_bounds__(kThreads, Tile<BN, ST>::kCtasPerSm)
 k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                 const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
                 TcStepArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  constexpr int kStages = Tile<BN>::kStages;
-  constexpr uint32_t kBBytes = Tile<BN>::kBBytes;
-  constexpr uint32_t kStageBytes = Tile<BN>::kStageBytes;
-  constexpr uint32_t kTmemCols = Tile<BN>::kTmemCols;
+  using T = Tile<BN, ST>;
+  constexpr int kStages = T::kStages;
+  constexpr uint32_t kBBytes = T::kBBytes;
+  constexpr uint32_t kStageBytes = T::kStageBytes;
+  constexpr uint32_t kTmemCols = T::kTmemCols;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
   uint64_t* empty = full + kStages;
   uint64_t* acc_full = empty + kStages;
@@ -641,10 +645,12 @@ int64_t lr_npad(int64_t n) { return (n + kBN - 1) / kBN * kBN; }
 constexpr int kMaxSplit = 16;
 size_t a1k(size_t b) { return (b + 1023) & ~static_cast<size_t>(1023); }
 
-// Tile widths: Z = Theta X^T in 128-row tiles of the data (each re-reads
-// the chains' rows of Theta); G = R X in one tile over the dims up to 256
-// wide (each re-reads R, C x Npad, from HBM: four times at 64 columns for a
-// dim of 256)
+// Tile widths: Z = Theta X^T in 64-row tiles of the data with a 2-stage ring
+// (96 KB), so that two CTAs share an SM and one's epilogue (the residual,
+// R to HBM) overlaps the other's products -- 128-row tiles at one CTA per SM
+// measured 5 % slower on a dim-254, 19102-row, 1204-chain gradient; G = R X
+// in one tile over the dims up to 256 wide (each re-reads R, C x Npad, from
+// HBM: four times at 64 columns for a dim of 256)
 struct LrTiles {
   int bnz, bng, nrt, ndt;
 };
@@ -661,7 +667,7 @@ void launch_tile(int bn, dim3 grid, const CUtensorMap& ma, const CUtensorMap& mb
 
 LrTiles lr_tiles(int64_t npad, int ld) {
   LrTiles q{};
-  q.bnz = 128;
+  q.bnz = 64;
   q.bng = ld <= 64 ? 64 : ld <= 128 ? 128 : 256;
   q.nrt = static_cast<int>((npad + q.bnz - 1) / q.bnz);
   q.ndt = (ld + q.bng - 1) / q.bng;
@@ -743,9 +749,9 @@ cudaError_t logreg_gemm_setup(LogregGemm* g, const hmc_target& t, int64_t C, voi
   for (int i = 0; i < 2 && ok; ++i)
     ok = make_map(&g->mThi[i], g->xhi[i], C, ld, kBM) && make_map(&g->mTlo[i], g->xlo[i], C, ld, kBM);
   if (!ok) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiLrResid, 128>,
+  cudaError_t e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiLrResid, 64, 2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(Tile<128>::kSmem));
+                                       static_cast<int>(Tile<64, 2>::kSmem));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiStore, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(Tile<64>::kSmem));
@@ -828,7 +834,7 @@ cudaError_t launch_logreg_gemm_transition(const StepArgs& a, LogregGemm& g, cuda
     st.da = a.da;
     st.err = g.err;
     if (timer) timer->begin(s);
-    k_gauss_tc_step<kEpiLrResid, 128><<<dim3(mt, g.nrt), kThreads, Tile<128>::kSmem, s>>>(
+    k_gauss_tc_step<kEpiLrResid, 64, 2><<<dim3(mt, g.nrt), kThreads, Tile<64, 2>::kSmem, s>>>(
         g.mThi[in], g.mTlo[in], g.mXhi, g.mXlo, z);
     {
       // the split products G = R X, then their sum with the prior and the
@@ -885,7 +891,7 @@ cudaError_t launch_logreg_gemm_products(LogregGemm& g, int C, int D, const DASta
   st.da = da;
   st.err = g.err;
   st.active = active;
-  k_gauss_tc_step<kEpiLrResid, 128><<<dim3(mt, g.nrt), kThreads, Tile<128>::kSmem, s>>>(
+  k_gauss_tc_step<kEpiLrResid, 64, 2><<<dim3(mt, g.nrt), kThreads, Tile<64, 2>::kSmem, s>>>(
       g.mThi[0], g.mTlo[0], g.mXhi, g.mXlo, z);
   launch_tile<kEpiStore>(g.bng, dim3(mt, g.ndt, S), g.mRhi, g.mRlo, g.mXThi, g.mXTlo, st, s);
   count_launch(2);

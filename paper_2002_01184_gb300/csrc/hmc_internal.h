@@ -219,7 +219,7 @@ cudaError_t launch_lr_prepare(int N, int Npad, int D, int ld, const float* X, co
 // Logistic regression for dims the CTA-pair kernel does not take (dim > 128;
 // rows padded to ld = dim rounded up to 4 inside the workspace): each
 // leapfrog gradient is two one-CTA tcgen05 products (gauss_tc.cu's tile
-// pipeline): Z = Theta X^T in 128-row data tiles with R = y - sigmoid(Z) in
+// pipeline): Z = Theta X^T in 64-row data tiles (two CTAs per SM) with R = y - sigmoid(Z) in
 // the epilogue (R to HBM as tf32 head / remainder), then G = R X in K-split
 // tiles up to 256 dims wide, summed with the prior and the leapfrog update
 // by k_lr_gemm_update.
