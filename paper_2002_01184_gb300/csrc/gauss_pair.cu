@@ -96,7 +96,8 @@ struct PairArgs {
   StepArgs s;           // s.t / s.t_full: the first transition of the launch
   int* err;
   const float* Ptm;     // P chunks 0-6 in tensor-memory fill order (k_tmem_image)
-  float* p0next;        // [C x D] momenta of the next transition (scratch)
+  float* p0next;        // momenta of the next transition, per-thread blocks (scratch)
+  float* gb;            // cached gradients, per-thread blocks (scratch; not with the exchange step)
   int T;                // transitions in this launch
   long long keep_from;  // transition t_full >= keep_from writes output k = t_full - keep_from
   float* samples;       // [k][C x D] or null
@@ -107,6 +108,7 @@ struct PairArgs {
   int exchange;         // replica sets (K | 64): the exchange step after every transition
   unsigned long long grid_wait_ns;   // time after which the grid barrier gives up
   int unreachable_gen;  // > 0: this grid-barrier generation can never complete (tests)
+  int samp_tma;         // the kept samples go out as tensor stores through the sample map
 };
 
 // Index of element e of float4 j of lane `lane` in the tensor-memory image:
@@ -191,7 +193,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned gen, un
 template <bool TEMPERED>
 __global__ void __launch_bounds__(kThreads, 1)
 k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ CUtensorMap mPlo,
-             PairArgs fa) {
+             const __grid_constant__ CUtensorMap mSamp, PairArgs fa) {
   const StepArgs& a = fa.s;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -217,6 +219,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   float* prob_s = reinterpret_cast<float*>(acc_flag + 64);    // [64]
   DAState* da_s = reinterpret_cast<DAState*>(prob_s + 64);    // this CTA's copy (T > 1)
   int* abort_s = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(da_s) + 128);
+  uint32_t* acc_mask_s = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(da_s) + 136);   // [2]
   DACoef* coef_s = reinterpret_cast<DACoef*>(reinterpret_cast<uint8_t*>(da_s) + 144);
   double* psum_s = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(da_s) + 176);
   float* beta_s = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(da_s) + 192);   // [64]
@@ -405,6 +408,28 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     auto xrow = [&](int i) -> float& { return xs[rowi(i) * 128 + dl]; };
     // element index of (pair row of element i, dim d) in the [C x D] arrays
     auto elem = [&](int i) { return static_cast<int64_t>(pair_base + rowi(i)) * D + d; };
+    // The per-thread blocks of the scratch arrays fa.gb and fa.p0next: slot i
+    // of the thread of dim d (d < D) is float i % 4 of float4
+    // ((pair * 2 + sub) * 8 + i / 4) * D + d, so that a warp moves 512
+    // contiguous bytes per float4 access (8 accesses for the 32 slots where
+    // the [C x D] layout took 32).
+    const int64_t blk4 = (static_cast<int64_t>(blockIdx.x >> 1) * 2 + sub) * 8 * D + d;
+    const bool xchg = TEMPERED && fa.exchange;   // the cached gradients stay [C x D] (rows swap)
+    // this thread's 32 slots from / to a per-thread block array
+    auto blk_load = [&](const float* base, float (&v)[kHalf]) {
+      const float4* b4 = reinterpret_cast<const float4*>(base) + blk4;
+#pragma unroll
+      for (int j = 0; j < kHalf / 4; ++j) {
+        const float4 u = b4[static_cast<int64_t>(j) * D];
+        v[4 * j] = u.x; v[4 * j + 1] = u.y; v[4 * j + 2] = u.z; v[4 * j + 3] = u.w;
+      }
+    };
+    auto blk_store = [&](float* base, const float (&v)[kHalf]) {
+      float4* b4 = reinterpret_cast<float4*>(base) + blk4;
+#pragma unroll
+      for (int j = 0; j < kHalf / 4; ++j)
+        b4[static_cast<int64_t>(j) * D] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    };
     // position of element i: the peer's chains as float32 into staging,
     // this CTA's own split into its tile
     auto store_x = [&](int i, float xi) {
@@ -487,13 +512,42 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       ptx::tc_fence_after();
     };
     auto chain_of = [&](int i) { return static_cast<uint32_t>(pair_base + rowi(i)) + a.chain_offset; };
-    // momenta of transition tn for elements i0 .. i1-1, parked for the next begin
-    auto draw_next = [&](int i0, int i1, uint32_t tn) {
-      for (int i = i0; i < i1; ++i)
-        if (valid(i))
-          fa.p0next[elem(i)] = momentum1(a.seed, static_cast<uint32_t>(d), chain_of(i), tn);
+    // The momenta of slots 4 g .. 4 g + 3 at transition tn (zero for chains
+    // >= C).  One Philox block (counter (d / 4, chain, tn)) holds a chain's
+    // momenta of dims 4 (d / 4) .. 4 (d / 4) + 3, the dims of this thread's
+    // lane quad (D % 4 == 0): lane m of the quad draws the block of slot
+    // 4 g + m's chain, and four rounds of shuffles hand each lane its own dim
+    // of all four blocks -- the same normals as one block per slot, for a
+    // quarter of the Philox rounds and half of the Box-Muller transforms.
+    // Every lane of the warp takes part.
+    auto draw_quad = [&](int g, uint32_t tn, float (&v)[4]) {
+      const int m = lane & 3;
+      const float4 n = momentum4(a.seed, static_cast<uint32_t>(d >> 2), chain_of(4 * g + m), tn);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int snd = (m - k) & 3;      // component the reading lane m - k needs
+        const float send = snd == 0 ? n.x : snd == 1 ? n.y : snd == 2 ? n.z : n.w;
+        const int src = (m + k) & 3;      // slot 4 g + src's chain, drawn by quad lane src
+        const float got = __shfl_sync(0xffffffffu, send, (lane & ~3) | src);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = src == e ? got : v[e];
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = valid(4 * g + e) ? v[e] : 0.f;
     };
-    const int per_wait = (kHalf + L - 1) / L;   // rows drawn ahead of each gradient wait
+    // momenta of transition tn for slot groups g0 .. g1-1, parked for the
+    // next begin as one float4 of the block per group
+    auto draw_next = [&](int g0, int g1, uint32_t tn) {
+      float4* b4 = reinterpret_cast<float4*>(fa.p0next) + blk4;
+      for (int g = g0; g < g1; ++g) {
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        draw_quad(g, tn, v);
+        if (dvalid) b4[static_cast<int64_t>(g) * D] = make_float4(v[0], v[1], v[2], v[3]);
+      }
+    };
+    // slot groups drawn ahead of each gradient wait
+    constexpr int kGroups = kHalf / 4;
+    const int per_wait = (kGroups + L - 1) / L;
 
     // P rows of this CTA (row = output dim d = TMEM lane) into tensor memory
     // from the pre-arranged image (coalesced): the two warps of a lane
@@ -525,9 +579,16 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     // the transition's momenta p0 (for the first one drawn here, for the
     // others loaded during the previous transition's accept step).
 #pragma unroll
-    for (int i = 0; i < kHalf; ++i) {
-      p[i] = valid(i) ? a.g[elem(i)] : 0.f;
-      x[i] = valid(i) ? momentum1(a.seed, static_cast<uint32_t>(d), chain_of(i), a.t) : 0.f;
+    for (int i = 0; i < kHalf; ++i) p[i] = valid(i) ? a.g[elem(i)] : 0.f;
+    // the launch's cached gradients in this thread's block (the accept steps
+    // keep them there; the last one writes them back to a.g)
+    if (!xchg && dvalid) blk_store(fa.gb, p);
+#pragma unroll
+    for (int g = 0; g < kGroups; ++g) {
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      draw_quad(g, a.t, v);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) x[4 * g + e] = v[e];
     }
     // the deciding threads (warps 2-3 of both CTAs, chain pair_base + c):
     // the current log p of their chain, kept in shared memory from here on
@@ -567,7 +628,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       const int s0 = j * L;                 // gradient steps of this transition: s0 .. s0 + L - 1
       // steps 1 .. L-1: merged kick + drift
       for (int l = 1; l < L; ++l) {
-        if (more) draw_next(min(kHalf, (l - 1) * per_wait), min(kHalf, l * per_wait), t + 1);
+        if (more) draw_next(min(kGroups, (l - 1) * per_wait), min(kGroups, l * per_wait), t + 1);
         wait_acc(s0 + l - 1);
 #pragma unroll
         for (int cb = 0; cb < kHalf / 16; ++cb) {
@@ -586,7 +647,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         split_received(s0 + l);
       }
       // step L: final half kick; <x, g> and |p|^2 partials
-      if (more) draw_next(min(kHalf, (L - 1) * per_wait), kHalf, t + 1);
+      if (more) draw_next(min(kGroups, (L - 1) * per_wait), kGroups, t + 1);
       wait_acc(s0 + L - 1);
       {
         float v[kHalf];
@@ -606,12 +667,14 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         for (int i = 0; i < kHalf; ++i) v[i] = valid(i) ? p[i] * p[i] : 0.f;
         red[(1 * 4 + quarter) * 64 + rowi(lane)] = transpose_reduce32(v, lane);
       }
-      // the momenta are spent: p takes the cached gradients, in flight while
-      // the chains are decided (the accepted ones are replaced below)
-      if (more) {
-#pragma unroll
-        for (int i = 0; i < kHalf; ++i) p[i] = valid(i) ? a.g[elem(i)] : 0.f;
-      }
+      // The momenta are spent: p takes the cached gradients (8 float4 loads
+      // from this thread's block, in flight while the chains are decided; the
+      // accepted ones are replaced below).  32 scalar loads of the [C x D]
+      // cache here measured 1 us of issue time per transition.  The error
+      // flag is read here too and checked at the end of the transition.
+      if (!xchg && dvalid) blk_load(fa.gb, p);
+      int err_seen = 0;
+      if (persistent && warp == 2 && lane == 0) err_seen = *reinterpret_cast<volatile int*>(fa.err);
       epi_barrier();
       // Only the epilogue warps run this loop, so the two CTAs meet on an
       // mbarrier: each sends its partial sums to the other by asynchronous
@@ -656,16 +719,17 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
             lpn_s[c] = acc ? lp1 : lp0;
           } else if (acc) {
             lpc_s[c] = lp1;
-            if (ok && lead) a.lp[chain] = lp1;
           }
-          if (ok && lead) {
-            a.is_accepted[chain] = static_cast<uint8_t>(acc);
-            a.log_accept[chain] = la;
-            if (k_out >= 0 && fa.trace_acc) fa.trace_acc[k_out * C + chain] = static_cast<uint8_t>(acc);
-          }
+          // log u is spent: its slot keeps log alpha for the kernel results,
+          // written after the accept step (a proxy fence there would
+          // otherwise wait for these global stores)
+          lu_s[c] = la;
         }
         acc_flag[c] = acc;
         prob_s[c] = prob;
+        // the decisions of rows 32 ew .. 32 ew + 31 as one word
+        const unsigned accw = __ballot_sync(0xffffffffu, acc != 0);
+        if (lane == 0) acc_mask_s[ew] = accw;
         if (TEMPERED && fa.exchange) {
           // the exchange step: row c decides the pair (c, c + 1) when it is
           // the lower replica of an active pair, then every row takes its
@@ -709,15 +773,18 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       // streaming driver: running moments of the kept states instead of a trace
       const bool moments = k_out >= 0 && a.w.mean != nullptr;
       const WelfordCoef wq = welford_coef(k_out > 0 ? k_out : 0, a.w.bsize);
-      // The decisions of this thread's 32 rows first, then only stores:
-      // shared-memory loads between the (possibly aliasing) global stores
-      // would each wait for the previous one.  The accepted positions go
-      // first, and (when a sample is kept) the proxy fence that hands them
-      // to the bulk trace copy comes before the gradient stores: a fence
-      // waits for this thread's global stores in flight.
-      uint32_t accm = 0u;
-#pragma unroll
-      for (int i = 0; i < kHalf; ++i) accm |= (acc_flag[rowi(i)] != 0 ? 1u : 0u) << i;
+      // The decisions of this thread's 32 rows first, then only global
+      // accesses: shared-memory loads between the (possibly aliasing) global
+      // stores would each wait for the previous one.  The accepted positions
+      // go first, and (when a sample is kept) the proxy fence that hands them
+      // to the trace's tensor store comes before the gradient accesses: a
+      // fence waits for this thread's global accesses in flight.  An accepted
+      // chain's gradient comes from the accumulators (and is stored as the
+      // new cached gradient), a rejected chain's is loaded from the cache.
+      // bit i: element i's chain was accepted (rows 16 sub .. 16 sub + 15 of
+      // the peer's half, then of this CTA's)
+      const uint32_t accm = ((acc_mask_s[peer] >> (16 * sub)) & 0xffffu) |
+                            (((acc_mask_s[rank] >> (16 * sub)) & 0xffffu) << 16);
 #pragma unroll
       for (int i = 0; i < kHalf; ++i)
         if (ok && valid(i) && ((accm >> i) & 1u)) xrow(i) = x[i];
@@ -730,10 +797,31 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         for (int k = 0; k < 16; ++k) {
           const int i = cb * 16 + k;
           if (ok && valid(i) && ((accm >> i) & 1u)) {
-            a.g[elem(i)] = -accv[k];
+            if (xchg) a.g[elem(i)] = -accv[k];
             p[i] = -accv[k];
           }
         }
+      }
+      // the cached gradients: back to this thread's block, or, after the
+      // launch's last transition, to a.g (with the exchange step a.g is the
+      // cache throughout, and the exchange below reloads p)
+      if (!xchg && ok) {
+        if (more) {
+          if (dvalid) blk_store(fa.gb, p);
+        } else {
+#pragma unroll
+          for (int i = 0; i < kHalf; ++i)
+            if (valid(i)) a.g[elem(i)] = p[i];
+        }
+      }
+      // the kernel results of chain c of the pair (the leader's deciders)
+      if (rank == 0 && c < kPairChains && pair_base + c < C && ok) {
+        const int chain = pair_base + c;
+        const int acc = acc_flag[c];
+        if (!(TEMPERED && fa.exchange) && acc) a.lp[chain] = lpc_s[c];
+        a.is_accepted[chain] = static_cast<uint8_t>(acc);
+        a.log_accept[chain] = lu_s[c];
+        if (k_out >= 0 && fa.trace_acc) fa.trace_acc[k_out * C + chain] = static_cast<uint8_t>(acc);
       }
       if (TEMPERED && fa.exchange) {
         // swap the state rows of this CTA's dims: the owner of the lower row
@@ -755,33 +843,33 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
             g0[D] = ga / b0 * b1;
           }
         }
-        // swapped rows took new cached gradients
+        // swapped rows took new cached gradients (the other row of a pair
+        // may belong to another thread of this dim)
+        epi_barrier();
         if (more) {
 #pragma unroll
           for (int i = 0; i < kHalf; ++i) p[i] = valid(i) ? a.g[elem(i)] : 0.f;
         }
       }
       // The kept sample: this CTA's positions (64 rows of its dims) are
-      // complete in shared memory, and warp 2 streams them to the trace by
-      // bulk copies, 512 bytes per chain row (waited for before the next
-      // transition writes the rows).
+      // complete in shared memory, and one thread writes them to the trace as
+      // one tensor store of the [64 chains x 128 dims] box (rows >= C and dims
+      // >= D fall outside the tensor and are not written), waited for before
+      // the next transition writes the rows.  (One bulk copy per chain row,
+      // issued by the lanes of one warp, measured 2.1 us per transition.)
       if (samp) {
         if (TEMPERED && fa.exchange) proxy_fence_cta();    // the swapped rows
         epi_barrier();
         const int ndim = min(128, D - static_cast<int>(rank) * 128);
-        if ((reinterpret_cast<uintptr_t>(samp) & 15u) == 0) {
-          if (warp == 2 && ok && ndim > 0) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int r = lane + 32 * h;
-              if (pair_base + r < C)
-                ptx::bulk_store_global(samp + static_cast<int64_t>(pair_base + r) * D + static_cast<int>(rank) * 128,
-                                       ptx::smem_u32(xs + r * 128), static_cast<uint32_t>(ndim) * 4u);
-            }
+        if (fa.samp_tma) {
+          if (warp == 2 && lane == 0 && ok && ndim > 0) {
+            ptx::tma_store_3d(&mSamp, ptx::smem_u32(xs), static_cast<int>(rank) * 128, pair_base,
+                              static_cast<int>(k_out));
             ptx::bulk_commit();
           }
         } else if (ok && ndim > 0) {
-          // a trace pointer without 16-byte alignment: coalesced plain stores
+          // no sample map (a trace pointer without 16-byte alignment):
+          // coalesced plain stores
           for (int e = ew * 32 + lane; e < kPairChains * ndim; e += 256) {
             const int r = e / ndim, cidx = e - r * ndim;
             if (pair_base + r < C)
@@ -794,8 +882,12 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       // waits for the loads in flight)
       if (more) {
         asm volatile("" ::: "memory");
+        if (dvalid) {
+          blk_load(fa.p0next, x);
+        } else {
 #pragma unroll
-        for (int i = 0; i < kHalf; ++i) x[i] = valid(i) ? fa.p0next[elem(i)] : 0.f;
+          for (int i = 0; i < kHalf; ++i) x[i] = 0.f;
+        }
       }
       if (moments && ok) {
         // four elements at a time: their read-modify-writes overlap, and the
@@ -851,10 +943,10 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
             acc = warp_sum_d(acc);
             if (lane == 0) {
               da_apply(da_s, *coef_s, acc / static_cast<double>(C), t_full);
-              if (*reinterpret_cast<volatile int*>(fa.err) != 0) *abort_s = 1;
+              if (err_seen != 0) *abort_s = 1;
             }
           }
-        } else if (warp == 2 && lane == 0 && *reinterpret_cast<volatile int*>(fa.err) != 0) {
+        } else if (warp == 2 && lane == 0 && err_seen != 0) {
           *abort_s = 1;
         }
         epi_barrier();
@@ -954,9 +1046,14 @@ cudaError_t launch_gauss_pair_transitions(const StepArgs& a, GaussTc& tc, int T,
                                           unsigned* grid_bar, cudaStream_t s, KernelTimer* timer,
                                           uint8_t* swapped) {
   if (swapped && (!a.betas || a.K < 2 || kPairChains % a.K != 0)) return cudaErrorInvalidValue;
-  PairArgs fa{a, tc.err, tc.Ptm, tc.p, T, keep_from, samples, trace_eps, trace_acc,
+  // the kept samples of this launch, outputs 0 .. t_full + T - 1 - keep_from,
+  // as one [64 chains x 128 dims] tensor store per CTA and transition
+  CUtensorMap mSamp{};
+  const long long nkeep = a.t_full + T - keep_from;
+  const bool samp_tma = samples && nkeep > 0 && make_sample_map(&mSamp, samples, a.D, a.C, nkeep);
+  PairArgs fa{a, tc.err, tc.Ptm, tc.pair_p, tc.pair_g, T, keep_from, samples, trace_eps, trace_acc,
               T > 1 ? grid_bar : nullptr, swapped, swapped ? 1 : 0, g_grid_wait_ns.load(),
-              g_unreachable_gen.load()};
+              g_unreachable_gen.load(), samp_tma ? 1 : 0};
   if (T > 1) {
     cudaError_t e = cudaMemsetAsync(grid_bar, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
@@ -976,8 +1073,8 @@ cudaError_t launch_gauss_pair_transitions(const StepArgs& a, GaussTc& tc, int T,
   cfg.attrs = attr;
   cfg.numAttrs = T > 1 ? 2 : 1;
   if (timer) timer->begin(s);
-  cudaError_t e = a.betas ? cudaLaunchKernelEx(&cfg, k_gauss_pair<true>, tc.mPhi128, tc.mPlo128, fa)
-                          : cudaLaunchKernelEx(&cfg, k_gauss_pair<false>, tc.mPhi128, tc.mPlo128, fa);
+  cudaError_t e = a.betas ? cudaLaunchKernelEx(&cfg, k_gauss_pair<true>, tc.mPhi128, tc.mPlo128, mSamp, fa)
+                          : cudaLaunchKernelEx(&cfg, k_gauss_pair<false>, tc.mPhi128, tc.mPlo128, mSamp, fa);
   if (timer) timer->end(s);
   count_launch();
   if (e != cudaSuccess) return e;

@@ -495,6 +495,26 @@ bool make_map(CUtensorMap* map, const float* base, int64_t rows, int cols, int b
   return r == CUDA_SUCCESS;
 }
 
+}  // namespace
+
+// [K x C x D] float32 samples as a 3-D tensor (D innermost), box of 128 dims x
+// 64 chains x 1 sample, no swizzle: the layout of a [64][128] row-major tile.
+bool make_sample_map(CUtensorMap* map, const float* base, int D, int64_t C, int64_t K) {
+  auto fn = encode_fn();
+  if (!fn || D % 4 != 0 || (reinterpret_cast<uintptr_t>(base) & 15u) != 0 || C < 1 || K < 1) return false;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(D), static_cast<cuuint64_t>(C), static_cast<cuuint64_t>(K)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(D) * sizeof(float),
+                           static_cast<cuuint64_t>(C) * static_cast<cuuint64_t>(D) * sizeof(float)};
+  cuuint32_t box[3] = {128, 64, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+namespace {
+
 inline unsigned blocks_for(int64_t n) {
   return static_cast<unsigned>(std::min<int64_t>((n + 255) / 256, 152 * 16));
 }
@@ -510,7 +530,8 @@ size_t gauss_tc_workspace_bytes(const hmc_target& t, int64_t C) {
   const size_t ntn = (t.dim + kBN - 1) / kBN;
   auto a = [](size_t b) { return (b + 1023) & ~static_cast<size_t>(1023); };
   const size_t image = t.dim <= 256 ? a(kGaussPairImageFloats * 4) : 0;
-  return 2 * a(DD * 4) + 6 * a(CD * 4) + a(C * ntn * 4) + a(C * 4) + a(sizeof(int)) + image;
+  const size_t blocks = t.dim <= 256 ? 2 * a(static_cast<size_t>(gauss_pair_padded_chains(C)) * t.dim * 4) : 0;
+  return 2 * a(DD * 4) + 6 * a(CD * 4) + a(C * ntn * 4) + a(C * 4) + a(sizeof(int)) + image + blocks;
 }
 
 cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s) {
@@ -531,6 +552,11 @@ cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws
   tc->h0 = take(C * 4);
   tc->err = reinterpret_cast<int*>(take(sizeof(int)));
   tc->Ptm = t.dim <= 256 ? take(kGaussPairImageFloats * 4) : nullptr;
+  if (t.dim <= 256) {
+    const size_t blk = static_cast<size_t>(gauss_pair_padded_chains(C)) * t.dim * 4;
+    tc->pair_g = take(blk);
+    tc->pair_p = take(blk);
+  }
   bool ok = make_map(&tc->mBhi, tc->Phi, t.dim, t.dim, kBN) &&
             make_map(&tc->mBlo, tc->Plo, t.dim, t.dim, kBN) &&
             make_map(&tc->mPhi128, tc->Phi, t.dim, t.dim, 128) &&

@@ -206,6 +206,10 @@ struct GaussTc {
   float* lp_part = nullptr;  // [C x ntn]
   float* h0 = nullptr;       // initial Hamiltonian
   int* err = nullptr;        // device flag: a bounded wait gave up
+  // dim <= 256, the pair kernel's per-thread blocks: the cached gradients and
+  // the next transition's momenta, [pairs][2][8][dim][4] floats each
+  float* pair_g = nullptr;
+  float* pair_p = nullptr;
   int ntn = 0;
   bool fused = false;        // one launch per transition (dim <= 256)
   bool pair = false;         // ... on CTA pairs (cta_group::2)
@@ -258,10 +262,15 @@ cudaError_t launch_logreg_gemm_products(LogregGemm& g, int C, int D, const DASta
                                         const uint8_t* active, int* splits, cudaStream_t s);
 
 bool gauss_tc_supported(const hmc_target& t);
+// Tensor map of [K x C x D] float32 samples, box 128 dims x 64 chains x 1
+// (false: no encoder, D % 4 != 0 or a base without 16-byte alignment).
+bool make_sample_map(CUtensorMap* map, const float* base, int D, int64_t C, int64_t K);
 size_t gauss_tc_workspace_bytes(const hmc_target& t, int64_t C);
 cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws, cudaStream_t s);
 bool gauss_fused_supported(const hmc_target& t);
 unsigned gauss_pair_grid(int64_t C);
+// C rounded up to whole pairs of 64 chains
+inline int64_t gauss_pair_padded_chains(int64_t C) { return (C + 63) / 64 * 64; }
 // floats of the pair kernel's tensor-memory image of P (dim <= 256)
 constexpr size_t kGaussPairImageFloats = 2 * 6 * 2 * 2 * 4 * 4 * 32 * 4;
 cudaError_t launch_gauss_pair_image(const float* Phi, const float* Plo, int D, float* image,

@@ -152,6 +152,16 @@ __device__ __forceinline__ void bulk_store_global(void* dst, uint32_t src_smem, 
                "r"(bytes)
                : "memory");
 }
+// Tensor store of one 3-D box from this CTA's shared memory (128-byte
+// aligned, the box's elements in row-major order) to the tensor `map`
+// describes, at element coordinates (x, y, z), in this thread's current bulk
+// group; elements outside the tensor are not written.  x times the element
+// size must be a multiple of 16 bytes and no coordinate may be negative.
+__device__ __forceinline__ void tma_store_3d(const void* map, uint32_t src_smem, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(map),
+               "r"(src_smem), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read() {
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");

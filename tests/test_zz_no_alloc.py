@@ -7,10 +7,15 @@ not be affected by what the first left in the shared scratch array).
 
 This file sorts last so that a run stopping at the first failure has already
 run every other test; it also passes alone in a fresh process, where its
-first call performs the per-device set-up."""
+first call performs the per-device set-up.
+
+It is also compared with the float64 oracle directly, for every target
+(Section 3's log-densities and their gradients), so that it does not rest
+only on the regular entry point's own parity."""
 import numpy as np
 import pytest
 
+from oracle import targets as otargets
 from paper_2002_01184_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -84,3 +89,22 @@ def test_no_alloc_entry_point_rejects_oversized_requests(H):
         H.hmc_target_log_prob_and_grad_noalloc(t, 1024, dev(x), lp, g)
     assert ei.value.status == H.HMC_E_INVALID
     assert "scratch" in str(ei.value)
+
+
+ORACLE_CASES = [
+    ("std_normal", workloads.std_normal, dict(num_chains=37, dim=13)),
+    ("funnel", workloads.funnel, dict(num_chains=41, dim=50)),
+    ("corr_gauss", workloads.corr_gauss, dict(num_chains=130, dim=70)),
+    ("corr_gauss", workloads.corr_gauss, dict(num_chains=300, dim=256)),
+    ("logreg", workloads.logreg, dict(n_data=1000, dim=65, num_chains=129)),
+]
+
+
+@pytest.mark.parametrize("kind,make,kw", ORACLE_CASES)
+def test_no_alloc_entry_point_matches_oracle(H, kind, make, kw):
+    prob = make(**kw)
+    C, D = prob.num_chains, prob.dim
+    x = (0.3 * np.random.default_rng(5).standard_normal((C, D))).astype(np.float32)
+    lp, g, _, _, _, _ = evaluate_both(H, prob, x)
+    lp_ref, g_ref = otargets.make(kind, **prob.data())(x.astype(np.float64))
+    assert_same(lp, g, lp_ref, g_ref)
