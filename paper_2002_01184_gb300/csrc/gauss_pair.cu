@@ -447,15 +447,17 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         }
       }
     };
-    // The peer's half is written: the warp pushes its 16 staged rows (2 KB
-    // of float32 positions) to the peer's receive buffer, completing on the
-    // peer's in_full.
-    auto publish_stage = [&]() {
+    // Half h of the peer's half is written: the warp pushes its staged rows
+    // 8 h .. 8 h + 7 (1 KB of float32 positions) to the peer's receive
+    // buffer, completing on the peer's in_full.  (The transfer is bound by
+    // the bandwidth between the two SMs: the first half starts it while the
+    // second is computed.)
+    auto publish_stage = [&](int h) {
       proxy_fence_cta();          // generic stores -> async proxy (bulk copy)
       __syncwarp();
       if (lane == 0) {
-        const uint32_t off = static_cast<uint32_t>(quarter * kHalf + sub * 16) * kRowBytes;
-        ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Rcv + off), peer), Stg + off, 16 * kRowBytes,
+        const uint32_t off = static_cast<uint32_t>(quarter * kHalf + sub * 16 + 8 * h) * kRowBytes;
+        ptx::bulk_copy_to_cluster(ptx::mapa(ptx::smem_u32(Rcv + off), peer), Stg + off, 8 * kRowBytes,
                                   ptx::mapa(ptx::smem_u32(in_full), peer));
       }
     };
@@ -596,6 +598,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     if (c < kPairChains) lpc_s[c] = pair_base + c < C ? a.lp[pair_base + c] : 0.f;
 
     int nbar = 0;                           // grid barriers met so far (T > 1)
+    int err_seen = 0;                       // warp 2 lane 0: the error flag at the last boundary
     for (int j = 0; j < T; ++j) {
       const uint32_t t = a.t + static_cast<uint32_t>(j);
       const bool more = j + 1 < T;
@@ -618,7 +621,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       for (int i = 0; i < kHalf; ++i) {
         x[i] = fmaf(eps, p[i], x[i]);
         store_x(i, x[i]);
-        if (i == 15) publish_stage();
+        if (i == 7 || i == 15) publish_stage(i >> 3);
       }
       publish_own();
       split_received(j * L);
@@ -640,8 +643,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
             p[i] = fmaf(-eps, accv[k], p[i]);
             x[i] = fmaf(eps, p[i], x[i]);
             store_x(i, x[i]);
+            if (cb == 0 && (k == 7 || k == 15)) publish_stage(k >> 3);
           }
-          if (cb == 0) publish_stage();
         }
         publish_own();
         split_received(s0 + l);
@@ -670,12 +673,18 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       // The momenta are spent: p takes the cached gradients (8 float4 loads
       // from this thread's block, in flight while the chains are decided; the
       // accepted ones are replaced below).  32 scalar loads of the [C x D]
-      // cache here measured 1 us of issue time per transition.  The error
-      // flag is read here too and checked at the end of the transition.
+      // cache here measured 1 us of issue time per transition.
       if (!xchg && dvalid) blk_load(fa.gb, p);
-      int err_seen = 0;
-      if (persistent && warp == 2 && lane == 0) err_seen = *reinterpret_cast<volatile int*>(fa.err);
+      // The error flag: the value read at the previous boundary raises the
+      // abort flag, which every epilogue thread reads after the barrier below
+      // (and acts on at the end of this transition), and this boundary's read
+      // stays in flight: no barrier of its own.
+      if (persistent && warp == 2 && lane == 0) {
+        if (err_seen != 0) *abort_s = 1;
+        err_seen = *reinterpret_cast<volatile int*>(fa.err);
+      }
       epi_barrier();
+      const bool stop = persistent && *reinterpret_cast<volatile int*>(abort_s) != 0;
       // Only the epilogue warps run this loop, so the two CTAs meet on an
       // mbarrier: each sends its partial sums to the other by asynchronous
       // stores that complete on the other's sums_in, and both decide every
@@ -772,7 +781,6 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       float* samp = (k_out >= 0 && fa.samples) ? fa.samples + k_out * static_cast<int64_t>(C) * D : nullptr;
       // streaming driver: running moments of the kept states instead of a trace
       const bool moments = k_out >= 0 && a.w.mean != nullptr;
-      const WelfordCoef wq = welford_coef(k_out > 0 ? k_out : 0, a.w.bsize);
       // The decisions of this thread's 32 rows first, then only global
       // accesses: shared-memory loads between the (possibly aliasing) global
       // stores would each wait for the previous one.  The accepted positions
@@ -890,6 +898,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         }
       }
       if (moments && ok) {
+        // (the coefficients take 64-bit divisions: only when moments are kept)
+        const WelfordCoef wq = welford_coef(k_out, a.w.bsize);
         // four elements at a time: their read-modify-writes overlap, and the
         // next transition's momenta and gradients stay in registers
 #pragma unroll 1
@@ -946,11 +956,11 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
               if (err_seen != 0) *abort_s = 1;
             }
           }
-        } else if (warp == 2 && lane == 0 && err_seen != 0) {
-          *abort_s = 1;
+          epi_barrier();
+          if (*reinterpret_cast<volatile int*>(abort_s)) break;
+        } else if (stop) {
+          break;
         }
-        epi_barrier();
-        if (*reinterpret_cast<volatile int*>(abort_s)) break;
       } else if (warp == 2) {
         // one transition: the pair's sum for the last-CTA update below
         double v = rank == 0 ? static_cast<double>(prob_s[lane]) + static_cast<double>(prob_s[lane + 32]) : 0.0;
