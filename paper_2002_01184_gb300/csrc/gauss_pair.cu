@@ -96,7 +96,8 @@ struct PairArgs {
   StepArgs s;           // s.t / s.t_full: the first transition of the launch
   int* err;
   const float* Ptm;     // P chunks 0-6 in tensor-memory fill order (k_tmem_image)
-  float* p0next;        // momenta of the next transition, per-thread blocks (scratch)
+  float* p0next;        // momenta of transition t in slot t % 2, per-thread blocks (scratch)
+  int64_t p0_slot;      // floats per slot of p0next
   float* gb;            // cached gradients, per-thread blocks (scratch; not with the exchange step)
   int T;                // transitions in this launch
   long long keep_from;  // transition t_full >= keep_from writes output k = t_full - keep_from
@@ -161,6 +162,37 @@ __device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane) {
     }
   }
   return v[0];
+}
+
+// The momenta of slots 4 g .. 4 g + 3 of the epilogue thread of dim d (D % 4
+// == 0) at transition tn: slot i < 16 is chain chain_peer + i, slot i >= 16
+// chain chain_own + i - 16; slots past nv_peer / nv_own (chains >= C) are
+// zero.  One Philox block (counter (d / 4, chain, tn)) holds a chain's
+// momenta of dims 4 (d / 4) .. 4 (d / 4) + 3, the dims of the lane quad:
+// lane m of the quad draws the block of slot 4 g + m's chain, and four
+// rounds of shuffles hand each lane its own dim of all four blocks -- the
+// same normals as one block per slot, for a quarter of the Philox rounds and
+// half of the Box-Muller transforms.  Every lane of the warp takes part.
+__device__ __forceinline__ void draw_quad(uint64_t seed, int d, int lane, uint32_t chain_peer, uint32_t chain_own,
+                                          int nv_peer, int nv_own, int g, uint32_t tn, float (&v)[4]) {
+  const int m = lane & 3;
+  const int im = 4 * g + m;
+  const uint32_t chain = im < 16 ? chain_peer + static_cast<uint32_t>(im) : chain_own + static_cast<uint32_t>(im - 16);
+  const float4 n = momentum4(seed, static_cast<uint32_t>(d >> 2), chain, tn);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int snd = (m - k) & 3;      // component the reading lane m - k needs
+    const float send = snd == 0 ? n.x : snd == 1 ? n.y : snd == 2 ? n.z : n.w;
+    const int src = (m + k) & 3;      // slot 4 g + src's chain, drawn by quad lane src
+    const float got = __shfl_sync(0xffffffffu, send, (lane & ~3) | src);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = src == e ? got : v[e];
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int ie = 4 * g + e;
+    v[e] = (ie < 16 ? ie < nv_peer : ie - 16 < nv_own) ? v[e] : 0.f;
+  }
 }
 
 // Grid barrier of a cooperative launch: generation `gen` (1, 2, ...) is
@@ -514,42 +546,39 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       ptx::tc_fence_after();
     };
     auto chain_of = [&](int i) { return static_cast<uint32_t>(pair_base + rowi(i)) + a.chain_offset; };
-    // The momenta of slots 4 g .. 4 g + 3 at transition tn (zero for chains
-    // >= C).  One Philox block (counter (d / 4, chain, tn)) holds a chain's
-    // momenta of dims 4 (d / 4) .. 4 (d / 4) + 3, the dims of this thread's
-    // lane quad (D % 4 == 0): lane m of the quad draws the block of slot
-    // 4 g + m's chain, and four rounds of shuffles hand each lane its own dim
-    // of all four blocks -- the same normals as one block per slot, for a
-    // quarter of the Philox rounds and half of the Box-Muller transforms.
-    // Every lane of the warp takes part.
-    auto draw_quad = [&](int g, uint32_t tn, float (&v)[4]) {
-      const int m = lane & 3;
-      const float4 n = momentum4(a.seed, static_cast<uint32_t>(d >> 2), chain_of(4 * g + m), tn);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int snd = (m - k) & 3;      // component the reading lane m - k needs
-        const float send = snd == 0 ? n.x : snd == 1 ? n.y : snd == 2 ? n.z : n.w;
-        const int src = (m + k) & 3;      // slot 4 g + src's chain, drawn by quad lane src
-        const float got = __shfl_sync(0xffffffffu, send, (lane & ~3) | src);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) v[e] = src == e ? got : v[e];
-      }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) v[e] = valid(4 * g + e) ? v[e] : 0.f;
-    };
-    // momenta of transition tn for slot groups g0 .. g1-1, parked for the
-    // next begin as one float4 of the block per group
-    auto draw_next = [&](int g0, int g1, uint32_t tn) {
-      float4* b4 = reinterpret_cast<float4*>(fa.p0next) + blk4;
-      for (int g = g0; g < g1; ++g) {
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        draw_quad(g, tn, v);
-        if (dvalid) b4[static_cast<int64_t>(g) * D] = make_float4(v[0], v[1], v[2], v[3]);
-      }
-    };
-    // slot groups drawn ahead of each gradient wait
     constexpr int kGroups = kHalf / 4;
-    const int per_wait = (kGroups + L - 1) / L;
+    // The next transition's momenta, parked in the per-thread blocks: 64
+    // items (epilogue warp w, slot group g) per transition, each one float4
+    // per lane of w's block.  The six epilogue warps off the MMA issuer's
+    // sub-partition (warp % 4 != 1) draw them all, item k + 6 n for the k-th
+    // of them, n items per gradient wait: drawing in warps 5 and 9 measured
+    // 0.1 us per step more MMA issue time.  Transition tn's momenta go to
+    // slot tn % 2, so that no warp overwrites momenta another has yet to load.
+    const bool drawer = (warp & 3) != 1;
+    const int dk = warp < 5 ? warp - 2 : warp - 3;           // 0..5 for the drawers
+    const int n_items = drawer ? (8 * kGroups - dk + 5) / 6 : 0;
+    const int per_wait = (8 * kGroups / 6 + 1 + L - 1) / L;   // items of a drawer per wait (at most 11)
+    auto draw_next = [&](int n0, int n1, uint32_t tn) {
+      for (int n = n0; n < min(n1, n_items); ++n) {
+        const int item = dk + 6 * n;
+        const int tw = 2 + (item >> 3), g = item & 7;          // warp whose slots, slot group
+        const int tq = tw & 3, tsub = (tw - 2) >> 2;
+        if (static_cast<int>(rank) * 128 + tq * 32 >= D) continue;   // warp-uniform: no dims
+        const int dt = static_cast<int>(rank) * 128 + tq * 32 + lane;
+        const bool dv = dt < D;
+        const int rp = pair_base + static_cast<int>(peer) * kHalf + tsub * 16;
+        const int ro = pair_base + static_cast<int>(rank) * kHalf + tsub * 16;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        draw_quad(a.seed, dt, lane, static_cast<uint32_t>(rp) + a.chain_offset,
+                  static_cast<uint32_t>(ro) + a.chain_offset, dv ? max(0, min(16, C - rp)) : 0,
+                  dv ? max(0, min(16, C - ro)) : 0, g, tn, v);
+        if (dv) {
+          const int64_t b4 = (static_cast<int64_t>(blockIdx.x >> 1) * 2 + tsub) * 8 * D + dt;
+          reinterpret_cast<float4*>(fa.p0next + (tn & 1u) * fa.p0_slot)[b4 + static_cast<int64_t>(g) * D] =
+              make_float4(v[0], v[1], v[2], v[3]);
+        }
+      }
+    };
 
     // P rows of this CTA (row = output dim d = TMEM lane) into tensor memory
     // from the pre-arranged image (coalesced): the two warps of a lane
@@ -588,7 +617,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 #pragma unroll
     for (int g = 0; g < kGroups; ++g) {
       float v[4] = {0.f, 0.f, 0.f, 0.f};
-      draw_quad(g, a.t, v);
+      draw_quad(a.seed, d, lane, chain_of(0), chain_of(16), nv_peer, nv_own, g, a.t, v);
 #pragma unroll
       for (int e = 0; e < 4; ++e) x[4 * g + e] = v[e];
     }
@@ -631,7 +660,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       const int s0 = j * L;                 // gradient steps of this transition: s0 .. s0 + L - 1
       // steps 1 .. L-1: merged kick + drift
       for (int l = 1; l < L; ++l) {
-        if (more) draw_next(min(kGroups, (l - 1) * per_wait), min(kGroups, l * per_wait), t + 1);
+        if (more) draw_next((l - 1) * per_wait, l * per_wait, t + 1);
         wait_acc(s0 + l - 1);
 #pragma unroll
         for (int cb = 0; cb < kHalf / 16; ++cb) {
@@ -650,7 +679,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         split_received(s0 + l);
       }
       // step L: final half kick; <x, g> and |p|^2 partials
-      if (more) draw_next(min(kGroups, (L - 1) * per_wait), kGroups, t + 1);
+      if (more) draw_next((L - 1) * per_wait, n_items, t + 1);
       wait_acc(s0 + L - 1);
       {
         float v[kHalf];
@@ -891,7 +920,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       if (more) {
         asm volatile("" ::: "memory");
         if (dvalid) {
-          blk_load(fa.p0next, x);
+          blk_load(fa.p0next + ((t + 1u) & 1u) * fa.p0_slot, x);
         } else {
 #pragma unroll
           for (int i = 0; i < kHalf; ++i) x[i] = 0.f;
@@ -1061,7 +1090,7 @@ cudaError_t launch_gauss_pair_transitions(const StepArgs& a, GaussTc& tc, int T,
   CUtensorMap mSamp{};
   const long long nkeep = a.t_full + T - keep_from;
   const bool samp_tma = samples && nkeep > 0 && make_sample_map(&mSamp, samples, a.D, a.C, nkeep);
-  PairArgs fa{a, tc.err, tc.Ptm, tc.pair_p, tc.pair_g, T, keep_from, samples, trace_eps, trace_acc,
+  PairArgs fa{a, tc.err, tc.Ptm, tc.pair_p, gauss_pair_padded_chains(a.C) * a.D, tc.pair_g, T, keep_from, samples, trace_eps, trace_acc,
               T > 1 ? grid_bar : nullptr, swapped, swapped ? 1 : 0, g_grid_wait_ns.load(),
               g_unreachable_gen.load(), samp_tma ? 1 : 0};
   if (T > 1) {

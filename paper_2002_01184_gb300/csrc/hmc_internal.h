@@ -206,8 +206,8 @@ struct GaussTc {
   float* lp_part = nullptr;  // [C x ntn]
   float* h0 = nullptr;       // initial Hamiltonian
   int* err = nullptr;        // device flag: a bounded wait gave up
-  // dim <= 256, the pair kernel's per-thread blocks: the cached gradients and
-  // the next transition's momenta, [pairs][2][8][dim][4] floats each
+  // dim <= 256, the pair kernel's per-thread blocks of [pairs][2][8][dim][4]
+  // floats: the cached gradients, and two slots of next-transition momenta
   float* pair_g = nullptr;
   float* pair_p = nullptr;
   int ntn = 0;
