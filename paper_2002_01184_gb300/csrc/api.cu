@@ -46,7 +46,6 @@ struct hmc_ctx {
   hmc::KernelTimer timer;
   bool use_tc = false;          // tensor-core Gaussian path
   hmc::GaussTc tc;
-  unsigned* grid_bar = nullptr;  // grid barrier of the multi-transition pair launch
   float* nuts_scratch = nullptr;           // NUTS: trajectory ends, candidates, span starts
   // NUTS: [0] leapfrog steps so far, [1] leaf steps on the schedule's
   // critical path so far, [2] the running launch's longest chain (scratch)
@@ -280,7 +279,6 @@ CreatePlan plan_create(const hmc_target& t, int64_t num_chains, const hmc_config
     add(hmc::gauss_tc_workspace_bytes(t, num_chains));
     q.tc_fused = hmc::gauss_fused_supported(t);
     q.tc_pair = q.tc_fused && q.cfg.impl != HMC_IMPL_FUSED_SINGLE_CTA;
-    if (q.tc_pair) add(sizeof(unsigned));
   }
   // logistic regressions with long data passes or much work per gradient
   // (chains x rows x dim above 2^22): tensor-core products; small ones: the
@@ -503,8 +501,7 @@ hmc_status enqueue_range(hmc_ctx* ctx, float* x, int64_t B, int64_t t_begin, int
       if (ctx->s_mean)
         a.w = hmc::WelfordOut{ctx->s_mean, ctx->s_m2, ctx->s_bsize, ctx->bm_sum, ctx->bm_mean, ctx->bm_m2};
       cudaError_t e = hmc::launch_gauss_pair_transitions(a, ctx->tc, n, B + out0, samples, trace_eps, trace_acc,
-                                                         ctx->grid_bar, ctx->stream, &ctx->timer,
-                                                         pair_remc ? ctx->swapped : nullptr);
+                                                         ctx->stream, &ctx->timer, pair_remc ? ctx->swapped : nullptr);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "pair transition launch");
     }
     ctx->dom_transitions = chunk;
@@ -687,7 +684,6 @@ hmc_status hmc_create(const hmc_target* target, int64_t num_chains, const hmc_co
     if (e == cudaSuccess) e = hmc::gauss_tc_setup(&ctx->tc, *target, num_chains, w, ctx->stream);
     ctx->tc.fused = plan.tc_fused;
     ctx->tc.pair = plan.tc_pair;
-    if (e == cudaSuccess && ctx->tc.pair) e = ctx_alloc(ctx, &ctx->grid_bar, 1);
   }
   ctx->use_lrtc = plan.use_lrtc;
   if (e == cudaSuccess && ctx->use_lrtc) {

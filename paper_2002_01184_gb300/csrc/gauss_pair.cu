@@ -104,7 +104,9 @@ struct PairArgs {
   float* samples;       // [k][C x D] or null
   float* trace_eps;     // [k] or null
   uint8_t* trace_acc;   // [k][C] or null
-  unsigned* grid_bar;   // T > 1: grid barrier counter, zero at launch; null: one transition
+  unsigned long long* stat;   // 3 statistic words (grid_barrier_sum), zero at launch
+  int stat_frac;        // fraction bits of the fixed-point statistic
+  double stat_scale;    // 2^-stat_frac / C
   uint8_t* swapped;     // exchange: [outer chains x (K - 1)] swap flags of the last transition
   int exchange;         // replica sets (K | 64): the exchange step after every transition
   unsigned long long grid_wait_ns;   // time after which the grid barrier gives up
@@ -195,20 +197,74 @@ __device__ __forceinline__ void draw_quad(uint64_t seed, int d, int lane, uint32
   }
 }
 
-// Grid barrier of a cooperative launch: generation `gen` (1, 2, ...) is
-// complete when every CTA has arrived `gen` times.  Bounded: false after
-// `limit_ns`.  Generation `unreachable` (tests of the give-up path) waits for
-// one arrival more than there are CTAs, so it never completes.
-__device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned gen, unsigned long long limit_ns,
-                                             int unreachable) {
-  __threadfence();
-  atomicAdd(counter, 1u);
-  const unsigned target = gen * gridDim.x + (static_cast<int>(gen) == unreachable ? 1u : 0u);
-  const unsigned long long t0 = ptx::global_timer_ns();
-  while (*reinterpret_cast<volatile unsigned*>(counter) < target) {
-    if (ptx::global_timer_ns() - t0 > limit_ns) return false;
+// The acceptance statistic of dual averaging (the mean acceptance
+// probability over all chains) in fixed point: a chain's probability, a
+// float32 in [0, 1], as a multiple of 2^-f, f = stat_frac_bits(C) (38 up to
+// 8191 chains), so that the sum over C chains stays below 2^51.  Integer
+// addition makes the sum independent of the order in which the CTAs add.
+// One 64-bit word carries a generation's sum (bits 0-51) and its arrival
+// count (bits 52-63), so the grid barrier and the reduction are one atomic
+// per CTA.  (The statistic differs from a float64 sum by at most 2^-39 per
+// chain at f = 38, far inside the tolerance the step sizes are checked to.)
+constexpr unsigned long long kArriveOne = 1ull << 52;
+constexpr unsigned long long kStatMask = kArriveOne - 1;
+
+int stat_frac_bits(int64_t C) {
+  int b = 0;
+  while ((int64_t{1} << b) <= C) ++b;     // C < 2^b
+  return b <= 13 ? 38 : 51 - b;
+}
+
+__device__ __forceinline__ unsigned long long prob_fixed(float p, int frac) {
+  return __float2ull_rn(ldexpf(p, frac));      // exact scaling
+}
+// the mean from a sum word: scale = 2^-frac / C, formed on the host (one
+// multiply here instead of a float64 division)
+__device__ __forceinline__ double stat_mean(unsigned long long word, double scale) {
+  return static_cast<double>(word & kStatMask) * scale;
+}
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long* w, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(w), "l"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* w) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(w) : "memory");
+  return v;
+}
+
+// Grid barrier and statistic sum of a cooperative launch, generation `gen`
+// (1, 2, ...) in word gen % 3 of `words` (all three zero at launch): adds
+// this CTA's arrival and partial sum, waits until every CTA has arrived and
+// returns the generation's word in *total.  The CTA whose arrival completes
+// generation gen clears word (gen + 1) % 3, which generation gen - 1 used:
+// every CTA has read it before arriving here, and generation gen + 2 adds
+// to it only after every CTA (this one included, whose acq_rel arrival
+// orders the clearing store first) has arrived at generation gen + 1.
+// Bounded: false after `limit_ns`.  Generation `unreachable` (tests of the
+// give-up path) waits for one arrival more than there are CTAs.  (Not
+// inlined: inlined, it made the register allocator spill in the kernel.)
+__device__ __noinline__ bool grid_barrier_sum(unsigned long long* words, unsigned gen, unsigned long long part,
+                                                 unsigned long long limit_ns, int unreachable,
+                                                 unsigned long long* total) {
+  unsigned long long* w = words + gen % 3u;
+  const unsigned long long target = gridDim.x + (static_cast<int>(gen) == unreachable ? 1u : 0u);
+  unsigned long long cur = atom_add_acq_rel(w, kArriveOne + part) + kArriveOne + part;
+  if ((cur >> 52) == target) {
+    words[(gen + 1u) % 3u] = 0ull;
+  } else {
+    const unsigned long long t0 = ptx::global_timer_ns();
+    while (((cur = ld_acquire_u64(w)) >> 52) < target) {
+      if (ptx::global_timer_ns() - t0 > limit_ns) return false;
+    }
   }
-  __threadfence();
+  *total = cur;
   return true;
 }
 
@@ -253,7 +309,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   int* abort_s = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(da_s) + 128);
   uint32_t* acc_mask_s = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(da_s) + 136);   // [2]
   DACoef* coef_s = reinterpret_cast<DACoef*>(reinterpret_cast<uint8_t*>(da_s) + 144);
-  double* psum_s = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(da_s) + 176);
+  // the pair's fixed-point statistic, then the generation's word
+  unsigned long long* psum_s = reinterpret_cast<unsigned long long*>(reinterpret_cast<uint8_t*>(da_s) + 176);
   float* beta_s = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(da_s) + 192);   // [64]
   float* lpn_s = beta_s + 64;                             // [64] exchange: log p after the decision
   int* swp_s = reinterpret_cast<int*>(lpn_s + 64);        // [64] exchange: row r and r + 1 swap
@@ -266,7 +323,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   const int nk = (D + 31) >> 5;
   const int nsm = nk > kLoTmemChunks ? nk - kLoTmemChunks : 0;   // P remainder chunks in shared memory
   const int pair_base = (blockIdx.x >> 1) * kPairChains;
-  const bool persistent = fa.grid_bar != nullptr;
+  const bool persistent = T > 1;
   constexpr uint16_t kPairMask = 0x3;
   static_assert(sizeof(DAState) <= 128, "DA state copy");
 
@@ -949,24 +1006,31 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       // dual averaging over all chains of the posterior
       if (persistent) {
         // Transitions that adapt (and the launch's last, whose statistic the
-        // state reports) meet at the grid barrier: every CTA publishes a
-        // partial (the pair's sum in the leader, zero in the peer) and meets
-        // the barrier once (warp 2, lane 0) while warp 3 forms the update's
-        // coefficients; then warp 2 sums the partials in the order of the
-        // one-transition reduction, so both launch shapes take the same step
-        // sizes.  The others only check the error flag: a step size that
-        // does not adapt needs no statistic.
+        // state reports) meet at the grid barrier, which also sums the
+        // fixed-point statistic (the pair's sum from the leader, zero from
+        // the peer; warp 2, lane 0), while warp 3 forms the update's
+        // coefficients.  Every CTA then applies the same update to its own
+        // copy of the state, as the one-transition launch does to the
+        // context's.  The others only check the error flag: a step size
+        // that does not adapt needs no statistic.
         const bool adapts = da_s->adapt && t_full < da_s->num_adapt;
         if (adapts || !more) {
-          double* part = a.partials + (nbar & 1) * static_cast<int>(gridDim.x);
           ++nbar;
           if (warp == 2) {
-            double v = rank == 0 ? static_cast<double>(prob_s[lane]) + static_cast<double>(prob_s[lane + 32]) : 0.0;
-            v = warp_sum_d(v);
+            unsigned long long v = rank == 0 ? prob_fixed(prob_s[lane], fa.stat_frac) +
+                                                   prob_fixed(prob_s[lane + 32], fa.stat_frac)
+                                             : 0ull;
+            v = warp_sum_u64(v);
             if (lane == 0) {
-              part[blockIdx.x] = v;
-              if (!grid_barrier(fa.grid_bar, static_cast<unsigned>(nbar), fa.grid_wait_ns, fa.unreachable_gen)) {
+              unsigned long long total = 0ull;
+              if (!grid_barrier_sum(fa.stat, static_cast<unsigned>(nbar), v, fa.grid_wait_ns, fa.unreachable_gen,
+                                    &total)) {
                 atomicCAS(fa.err, 0, 7);
+                *abort_s = 1;
+              } else if (err_seen == 0) {
+                // (warp 3's coefficients are ready after the barrier below)
+                *psum_s = total;
+              } else {
                 *abort_s = 1;
               }
             }
@@ -974,17 +1038,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
             *coef_s = da_prepare(da_s, t_full);
           }
           epi_barrier();
-          if (warp == 2 && *reinterpret_cast<volatile int*>(abort_s) == 0) {
-            __threadfence();
-            double acc = 0.0;
-            for (int b = lane; b < static_cast<int>(gridDim.x); b += 32)
-              acc += reinterpret_cast<volatile double*>(part)[b];
-            acc = warp_sum_d(acc);
-            if (lane == 0) {
-              da_apply(da_s, *coef_s, acc / static_cast<double>(C), t_full);
-              if (err_seen != 0) *abort_s = 1;
-            }
-          }
+          if (warp == 2 && lane == 0 && *reinterpret_cast<volatile int*>(abort_s) == 0)
+            da_apply(da_s, *coef_s, stat_mean(*psum_s, fa.stat_scale), t_full);
           epi_barrier();
           if (*reinterpret_cast<volatile int*>(abort_s)) break;
         } else if (stop) {
@@ -992,8 +1047,9 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         }
       } else if (warp == 2) {
         // one transition: the pair's sum for the last-CTA update below
-        double v = rank == 0 ? static_cast<double>(prob_s[lane]) + static_cast<double>(prob_s[lane + 32]) : 0.0;
-        v = warp_sum_d(v);
+        unsigned long long v =
+            rank == 0 ? prob_fixed(prob_s[lane], fa.stat_frac) + prob_fixed(prob_s[lane + 32], fa.stat_frac) : 0ull;
+        v = warp_sum_u64(v);
         if (lane == 0) *psum_s = v;
       }
     }
@@ -1013,9 +1069,15 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     ptx::tmem_dealloc_pair(tmem, kTmemCols);
   }
   ptx::cluster_sync();
-  if (!persistent) {
-    // one transition: the last CTA to finish applies the dual-averaging update
-    block_partial_then_da(a.da, a.partials, threadIdx.x == 0 ? *psum_s : 0.0, C, a.t_full);
+  if (!persistent && threadIdx.x == 64) {
+    // One transition: every CTA adds its statistic to word 0 and its arrival
+    // to word 1 (acq_rel: the sum is in place before the arrival counts); the
+    // CTA that arrives last applies the dual-averaging update with the same
+    // arithmetic as the multi-transition launch.  (The grid need not be
+    // resident at once, so the sum and the count are separate words here.)
+    atomicAdd(fa.stat, *psum_s);
+    if (atom_add_acq_rel(fa.stat + 1, 1ull) + 1ull == gridDim.x)
+      da_update(a.da, stat_mean(ld_acquire_u64(fa.stat), fa.stat_scale), a.t_full);
   }
 }
 
@@ -1078,23 +1140,23 @@ bool gauss_pair_persistent_ok(int64_t C) {
   return static_cast<int64_t>(gauss_pair_grid(C) / 2) <= max_clusters;
 }
 
-// T transitions starting at a.t / a.t_full.  T > 1 needs grid_bar (zeroed
-// here) and a cooperative launch; partials needs 2 x pairs doubles.
+// T transitions starting at a.t / a.t_full.  T > 1 needs a cooperative
+// launch; the statistic words (tc.pair_stat) are zeroed here.
 cudaError_t launch_gauss_pair_transitions(const StepArgs& a, GaussTc& tc, int T, long long keep_from,
                                           float* samples, float* trace_eps, uint8_t* trace_acc,
-                                          unsigned* grid_bar, cudaStream_t s, KernelTimer* timer,
-                                          uint8_t* swapped) {
+                                          cudaStream_t s, KernelTimer* timer, uint8_t* swapped) {
   if (swapped && (!a.betas || a.K < 2 || kPairChains % a.K != 0)) return cudaErrorInvalidValue;
   // the kept samples of this launch, outputs 0 .. t_full + T - 1 - keep_from,
   // as one [64 chains x 128 dims] tensor store per CTA and transition
   CUtensorMap mSamp{};
   const long long nkeep = a.t_full + T - keep_from;
   const bool samp_tma = samples && nkeep > 0 && make_sample_map(&mSamp, samples, a.D, a.C, nkeep);
-  PairArgs fa{a, tc.err, tc.Ptm, tc.pair_p, gauss_pair_padded_chains(a.C) * a.D, tc.pair_g, T, keep_from, samples, trace_eps, trace_acc,
-              T > 1 ? grid_bar : nullptr, swapped, swapped ? 1 : 0, g_grid_wait_ns.load(),
-              g_unreachable_gen.load(), samp_tma ? 1 : 0};
-  if (T > 1) {
-    cudaError_t e = cudaMemsetAsync(grid_bar, 0, sizeof(unsigned), s);
+  PairArgs fa{a, tc.err, tc.Ptm, tc.pair_p, gauss_pair_padded_chains(a.C) * a.D, tc.pair_g,
+              T, keep_from, samples, trace_eps, trace_acc, tc.pair_stat, stat_frac_bits(a.C),
+              std::ldexp(1.0, -stat_frac_bits(a.C)) / static_cast<double>(a.C),
+              swapped, swapped ? 1 : 0, g_grid_wait_ns.load(), g_unreachable_gen.load(), samp_tma ? 1 : 0};
+  {
+    cudaError_t e = cudaMemsetAsync(tc.pair_stat, 0, 3 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg = {};
@@ -1125,7 +1187,7 @@ cudaError_t launch_gauss_pair_transition(const StepArgs& a, GaussTc& tc, cudaStr
   // one transition: its outputs, if any, are output 0
   const bool keep = a.sample_out || a.trace_eps || a.trace_acc;
   return launch_gauss_pair_transitions(a, tc, 1, keep ? a.t_full : a.t_full + 1, a.sample_out,
-                                       a.trace_eps, a.trace_acc, nullptr, s, timer);
+                                       a.trace_eps, a.trace_acc, s, timer);
 }
 
 }  // namespace hmc

@@ -176,9 +176,12 @@ __device__ __forceinline__ void da_apply(DAState* s, const DACoef& c, double alp
   s->h_bar = __dadd_rn(__dmul_rn(1.0 - c.w, s->h_bar), __dmul_rn(c.w, __dsub_rn(s->delta, alpha)));
   s->log_eps = __dsub_rn(s->mu, __dmul_rn(c.sq, s->h_bar));
   s->log_eps_bar = __dadd_rn(__dmul_rn(c.eta, s->log_eps), __dmul_rn(1.0 - c.eta, s->log_eps_bar));
-  // after the last adaptation step the step size freezes at eps_bar
+  // after the last adaptation step the step size freezes at eps_bar; the
+  // kernels use the step size as float32, formed by a float32 exp of the
+  // rounded logarithm (within 3e-7 of float64 exp, which is slow on this
+  // part and sits on the critical path of every adapting transition)
   const double next = (t + 1 >= s->num_adapt) ? s->log_eps_bar : s->log_eps;
-  s->eps = static_cast<float>(exp(next));
+  s->eps = expf(static_cast<float>(next));
 }
 
 __device__ __forceinline__ void da_update(DAState* s, double alpha, long long t) {

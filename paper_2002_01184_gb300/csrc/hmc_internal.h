@@ -210,6 +210,8 @@ struct GaussTc {
   // floats: the cached gradients, and two slots of next-transition momenta
   float* pair_g = nullptr;
   float* pair_p = nullptr;
+  // the pair kernel's acceptance statistic words (3; see gauss_pair.cu)
+  unsigned long long* pair_stat = nullptr;
   int ntn = 0;
   bool fused = false;        // one launch per transition (dim <= 256)
   bool pair = false;         // ... on CTA pairs (cta_group::2)
@@ -284,14 +286,13 @@ cudaError_t launch_gauss_pair_transition(const StepArgs& a, GaussTc& tc, cudaStr
 bool gauss_pair_persistent_ok(int64_t C);
 // T transitions from a.t / a.t_full in one launch; transition t_full >=
 // keep_from writes output k = t_full - keep_from (samples [k][C x D],
-// trace_eps [k], trace_acc [k][C]; each may be null).  T > 1 uses grid_bar
-// (one device counter) and needs gauss_pair_persistent_ok.  With swapped
+// trace_eps [k], trace_acc [k][C]; each may be null).  T > 1 needs
+// gauss_pair_persistent_ok (a cooperative launch).  With swapped
 // non-null (a replica set: a.betas, a.K dividing 64) every transition is
 // followed by the exchange step, its flags left in swapped.
 cudaError_t launch_gauss_pair_transitions(const StepArgs& a, GaussTc& tc, int T, long long keep_from,
                                           float* samples, float* trace_eps, uint8_t* trace_acc,
-                                          unsigned* grid_bar, cudaStream_t s, KernelTimer* timer,
-                                          uint8_t* swapped = nullptr);
+                                          cudaStream_t s, KernelTimer* timer, uint8_t* swapped = nullptr);
 // Test support: wait limit of the pair kernel's grid barrier and a
 // generation that can never complete (0: none), for every later launch.
 void set_grid_barrier_debug(unsigned long long wait_ns, int unreachable_gen);
