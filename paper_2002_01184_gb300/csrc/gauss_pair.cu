@@ -48,6 +48,7 @@
 // transition instead lets its last CTA update the state.
 #include <cuda.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 
@@ -105,7 +106,7 @@ struct PairArgs {
   float* trace_eps;     // [k] or null
   uint8_t* trace_acc;   // [k][C] or null
   unsigned long long* stat;   // 3 statistic words (grid_barrier_sum), zero at launch
-  int stat_frac;        // fraction bits of the fixed-point statistic
+  float stat_hi_scale;  // 2^(f - 19), f the fraction bits of the fixed-point statistic
   double stat_scale;    // 2^-stat_frac / C
   uint8_t* swapped;     // exchange: [outer chains x (K - 1)] swap flags of the last transition
   int exchange;         // replica sets (K | 64): the exchange step after every transition
@@ -212,11 +213,18 @@ constexpr unsigned long long kStatMask = kArriveOne - 1;
 int stat_frac_bits(int64_t C) {
   int b = 0;
   while ((int64_t{1} << b) <= C) ++b;     // C < 2^b
-  return b <= 13 ? 38 : 51 - b;
+  return b <= 13 ? 38 : std::max(20, 51 - b);
 }
 
-__device__ __forceinline__ unsigned long long prob_fixed(float p, int frac) {
-  return __float2ull_rn(ldexpf(p, frac));      // exact scaling
+// round(p 2^frac) to nearest even, from two 32-bit conversions: with
+// hi_scale = 2^(frac - 19), u = trunc(p hi_scale) and the fraction r of p
+// hi_scale (both exact), the value is u 2^19 + rint(r 2^19).  (A conversion
+// to 64 bits takes the float64 pipe, which is slow on this part.)
+__device__ __forceinline__ unsigned long long prob_fixed(float p, float hi_scale) {
+  const float v = p * hi_scale;
+  const float u = truncf(v);
+  return (static_cast<unsigned long long>(static_cast<unsigned>(u)) << 19) +
+         __float2uint_rn((v - u) * 524288.0f);
 }
 // the mean from a sum word: scale = 2^-frac / C, formed on the host (one
 // multiply here instead of a float64 division)
@@ -1017,8 +1025,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         if (adapts || !more) {
           ++nbar;
           if (warp == 2) {
-            unsigned long long v = rank == 0 ? prob_fixed(prob_s[lane], fa.stat_frac) +
-                                                   prob_fixed(prob_s[lane + 32], fa.stat_frac)
+            unsigned long long v = rank == 0 ? prob_fixed(prob_s[lane], fa.stat_hi_scale) +
+                                                   prob_fixed(prob_s[lane + 32], fa.stat_hi_scale)
                                              : 0ull;
             v = warp_sum_u64(v);
             if (lane == 0) {
@@ -1048,7 +1056,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       } else if (warp == 2) {
         // one transition: the pair's sum for the last-CTA update below
         unsigned long long v =
-            rank == 0 ? prob_fixed(prob_s[lane], fa.stat_frac) + prob_fixed(prob_s[lane + 32], fa.stat_frac) : 0ull;
+            rank == 0 ? prob_fixed(prob_s[lane], fa.stat_hi_scale) + prob_fixed(prob_s[lane + 32], fa.stat_hi_scale)
+                      : 0ull;
         v = warp_sum_u64(v);
         if (lane == 0) *psum_s = v;
       }
@@ -1152,7 +1161,8 @@ cudaError_t launch_gauss_pair_transitions(const StepArgs& a, GaussTc& tc, int T,
   const long long nkeep = a.t_full + T - keep_from;
   const bool samp_tma = samples && nkeep > 0 && make_sample_map(&mSamp, samples, a.D, a.C, nkeep);
   PairArgs fa{a, tc.err, tc.Ptm, tc.pair_p, gauss_pair_padded_chains(a.C) * a.D, tc.pair_g,
-              T, keep_from, samples, trace_eps, trace_acc, tc.pair_stat, stat_frac_bits(a.C),
+              T, keep_from, samples, trace_eps, trace_acc, tc.pair_stat,
+              std::ldexp(1.0f, stat_frac_bits(a.C) - 19),
               std::ldexp(1.0, -stat_frac_bits(a.C)) / static_cast<double>(a.C),
               swapped, swapped ? 1 : 0, g_grid_wait_ns.load(), g_unreachable_gen.load(), samp_tma ? 1 : 0};
   {
