@@ -100,6 +100,7 @@ struct PairArgs {
   float* p0next;        // momenta of transition t in slot t % 2, per-thread blocks (scratch)
   int64_t p0_slot;      // floats per slot of p0next
   float* gb;            // cached gradients, per-thread blocks (scratch; not with the exchange step)
+  float* wb;            // streaming: running mean, m2, batch sum, per-thread blocks (3 x p0_slot floats)
   int T;                // transitions in this launch
   long long keep_from;  // transition t_full >= keep_from writes output k = t_full - keep_from
   float* samples;       // [k][C x D] or null
@@ -527,6 +528,36 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       for (int j = 0; j < kHalf / 4; ++j)
         b4[static_cast<int64_t>(j) * D] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
     };
+    // Streaming driver: this thread's running moments (mean, m2 and, with
+    // batches, the batch sum) stay in per-thread blocks during the launch,
+    // read from the [C x D] arrays at its start and written back at its
+    // end; a kept transition then takes 8 float4 loads and stores per array
+    // where the [C x D] layout took 32 scalar ones.
+    const bool wblocks = a.w.mean != nullptr && a.t_full + T > fa.keep_from && dvalid;
+    const int n_wfields = a.w.bsize > 0 ? 3 : 2;
+    auto wfield = [&](int k) { return reinterpret_cast<float4*>(fa.wb + k * fa.p0_slot) + blk4; };
+    auto warray = [&](int k) { return k == 0 ? a.w.mean : k == 1 ? a.w.m2 : a.w.bsum; };
+    auto wblk_sync = [&](bool in) {
+      for (int k = 0; k < n_wfields; ++k) {
+        float4* b4 = wfield(k);
+        float* arr = warray(k);
+#pragma unroll 1
+        for (int g = 0; g < kHalf / 4; ++g) {
+          if (in) {
+            float v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = valid(4 * g + e) ? arr[elem(4 * g + e)] : 0.f;
+            b4[static_cast<int64_t>(g) * D] = make_float4(v[0], v[1], v[2], v[3]);
+          } else {
+            const float4 u = b4[static_cast<int64_t>(g) * D];
+            const float v[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (valid(4 * g + e)) arr[elem(4 * g + e)] = v[e];
+          }
+        }
+      }
+    };
     // position of element i: the peer's chains as float32 into staging,
     // this CTA's own split into its tile
     auto store_x = [&](int i, float xi) {
@@ -671,6 +702,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     // in a.g, which the accepted proposals overwrite)
 #pragma unroll 4
     for (int i = 0; i < kHalf; ++i) xrow(i) = valid(i) ? a.x[elem(i)] : 0.f;
+    if (wblocks) wblk_sync(true);
     // At the top of every transition p holds the cached gradients g0 and x
     // the transition's momenta p0 (for the first one drawn here, for the
     // others loaded during the previous transition's accept step).
@@ -991,24 +1023,54 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
           for (int i = 0; i < kHalf; ++i) x[i] = 0.f;
         }
       }
-      if (moments && ok) {
+      if (moments && ok && dvalid) {
         // (the coefficients take 64-bit divisions: only when moments are kept)
         const WelfordCoef wq = welford_coef(k_out, a.w.bsize);
-        // four elements at a time: their read-modify-writes overlap, and the
-        // next transition's momenta and gradients stay in registers
+        const bool batches = a.w.bsize > 0;
+        float4* mb = wfield(0);
+        float4* sb = wfield(1);
+        float4* bb = wfield(2);
+        // Welford's update (as welford_update) per slot, four slots a float4;
+        // the batch means of a closing batch stay [C x D]
 #pragma unroll 1
-        for (int i0 = 0; i0 < kHalf; i0 += 4) {
-          int64_t e[4];
-          float v[4];
-          uint32_t vmask = 0u;
+        for (int g = 0; g < kHalf / 4; ++g) {
+          const int64_t o = static_cast<int64_t>(g) * D;
+          const float4 m4 = mb[o], s4 = sb[o];
+          const float4 c4 = batches ? bb[o] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float m0[4] = {m4.x, m4.y, m4.z, m4.w}, s0[4] = {s4.x, s4.y, s4.z, s4.w};
+          const float b0[4] = {c4.x, c4.y, c4.z, c4.w};
+          float m1[4], s1[4], b1[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int i = i0 + k;
-            e[k] = elem(i);
-            v[k] = xrow(i);
-            if (valid(i)) vmask |= 1u << k;
+          for (int e = 0; e < 4; ++e) {
+            const int i = 4 * g + e;
+            const float xv = xrow(i);
+            if (k_out == 0) {
+              m1[e] = xv;
+              s1[e] = 0.f;
+            } else {
+              const float delta = xv - m0[e];
+              m1[e] = fmaf(delta, wq.inv, m0[e]);
+              s1[e] = fmaf(delta, xv - m1[e], s0[e]);
+            }
+            b1[e] = wq.pos == 0 ? xv : b0[e] + xv;
+            if (batches && wq.closes && valid(i)) {
+              const float bm = b1[e] * wq.inv_b;
+              const int64_t ei = elem(i);
+              if (wq.batch == 0) {
+                a.w.bmean[ei] = bm;
+                a.w.bm2[ei] = 0.f;
+              } else {
+                const float bm0 = a.w.bmean[ei], bs0 = a.w.bm2[ei];
+                const float delta = bm - bm0;
+                const float bn = fmaf(delta, wq.inv_j, bm0);
+                a.w.bmean[ei] = bn;
+                a.w.bm2[ei] = fmaf(delta, bm - bn, bs0);
+              }
+            }
           }
-          welford_update_n<4>(a.w, wq, k_out, e, v, vmask);
+          mb[o] = make_float4(m1[0], m1[1], m1[2], m1[3]);
+          sb[o] = make_float4(s1[0], s1[1], s1[2], s1[3]);
+          if (batches) bb[o] = make_float4(b1[0], b1[1], b1[2], b1[3]);
         }
       }
       // dual averaging over all chains of the posterior
@@ -1066,6 +1128,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 #pragma unroll 4
     for (int i = 0; i < kHalf; ++i)
       if (ok && valid(i)) a.x[elem(i)] = xrow(i);
+    if (wblocks && ok) wblk_sync(false);
     if (persistent && blockIdx.x == 0 && threadIdx.x == 64 && !*abort_s) *a.da = *da_s;
     if (warp == 2) ptx::bulk_wait_all();      // the kept samples' bulk stores are done
   }
@@ -1160,7 +1223,7 @@ cudaError_t launch_gauss_pair_transitions(const StepArgs& a, GaussTc& tc, int T,
   CUtensorMap mSamp{};
   const long long nkeep = a.t_full + T - keep_from;
   const bool samp_tma = samples && nkeep > 0 && make_sample_map(&mSamp, samples, a.D, a.C, nkeep);
-  PairArgs fa{a, tc.err, tc.Ptm, tc.pair_p, gauss_pair_padded_chains(a.C) * a.D, tc.pair_g,
+  PairArgs fa{a, tc.err, tc.Ptm, tc.pair_p, gauss_pair_padded_chains(a.C) * a.D, tc.pair_g, tc.pair_w,
               T, keep_from, samples, trace_eps, trace_acc, tc.pair_stat,
               std::ldexp(1.0f, stat_frac_bits(a.C) - 19),
               std::ldexp(1.0, -stat_frac_bits(a.C)) / static_cast<double>(a.C),

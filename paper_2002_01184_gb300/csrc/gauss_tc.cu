@@ -530,7 +530,7 @@ size_t gauss_tc_workspace_bytes(const hmc_target& t, int64_t C) {
   const size_t ntn = (t.dim + kBN - 1) / kBN;
   auto a = [](size_t b) { return (b + 1023) & ~static_cast<size_t>(1023); };
   const size_t image = t.dim <= 256 ? a(kGaussPairImageFloats * 4) : 0;
-  const size_t blocks = t.dim <= 256 ? 3 * a(static_cast<size_t>(gauss_pair_padded_chains(C)) * t.dim * 4) + a(24) : 0;
+  const size_t blocks = t.dim <= 256 ? 6 * a(static_cast<size_t>(gauss_pair_padded_chains(C)) * t.dim * 4) + a(24) : 0;
   return 2 * a(DD * 4) + 6 * a(CD * 4) + a(C * ntn * 4) + a(C * 4) + a(sizeof(int)) + image + blocks;
 }
 
@@ -556,6 +556,7 @@ cudaError_t gauss_tc_setup(GaussTc* tc, const hmc_target& t, int64_t C, void* ws
     const size_t blk = static_cast<size_t>(gauss_pair_padded_chains(C)) * t.dim * 4;
     tc->pair_g = take(blk);
     tc->pair_p = take(2 * blk);
+    tc->pair_w = take(3 * blk);
     tc->pair_stat = reinterpret_cast<unsigned long long*>(take(3 * sizeof(unsigned long long)));
   }
   bool ok = make_map(&tc->mBhi, tc->Phi, t.dim, t.dim, kBN) &&

@@ -207,9 +207,11 @@ struct GaussTc {
   float* h0 = nullptr;       // initial Hamiltonian
   int* err = nullptr;        // device flag: a bounded wait gave up
   // dim <= 256, the pair kernel's per-thread blocks of [pairs][2][8][dim][4]
-  // floats: the cached gradients, and two slots of next-transition momenta
+  // floats: the cached gradients, two slots of next-transition momenta, and
+  // the streaming driver's running mean, m2 and batch sum
   float* pair_g = nullptr;
   float* pair_p = nullptr;
+  float* pair_w = nullptr;
   // the pair kernel's acceptance statistic words (3; see gauss_pair.cu)
   unsigned long long* pair_stat = nullptr;
   int ntn = 0;
