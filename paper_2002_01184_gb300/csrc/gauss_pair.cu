@@ -512,7 +512,12 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     // contiguous bytes per float4 access (8 accesses for the 32 slots where
     // the [C x D] layout took 32).
     const int64_t blk4 = (static_cast<int64_t>(blockIdx.x >> 1) * 2 + sub) * 8 * D + d;
-    const bool xchg = TEMPERED && fa.exchange;   // the cached gradients stay [C x D] (rows swap)
+    // With the exchange step, rows swap: when the replica count divides 16
+    // both rows of a swapped pair are this thread's (xblk) and the cached
+    // gradients keep their per-thread blocks; otherwise they stay [C x D].
+    const bool xchg = TEMPERED && fa.exchange;
+    const bool xblk = xchg && a.K > 0 && 16 % a.K == 0;
+    const bool gblocks = !xchg || xblk;
     // this thread's 32 slots from / to a per-thread block array
     auto blk_load = [&](const float* base, float (&v)[kHalf]) {
       const float4* b4 = reinterpret_cast<const float4*>(base) + blk4;
@@ -710,7 +715,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
     for (int i = 0; i < kHalf; ++i) p[i] = valid(i) ? a.g[elem(i)] : 0.f;
     // the launch's cached gradients in this thread's block (the accept steps
     // keep them there; the last one writes them back to a.g)
-    if (!xchg && dvalid) blk_store(fa.gb, p);
+    if (gblocks && dvalid) blk_store(fa.gb, p);
 #pragma unroll
     for (int g = 0; g < kGroups; ++g) {
       float v[4] = {0.f, 0.f, 0.f, 0.f};
@@ -800,7 +805,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       // from this thread's block, in flight while the chains are decided; the
       // accepted ones are replaced below).  32 scalar loads of the [C x D]
       // cache here measured 1 us of issue time per transition.
-      if (!xchg && dvalid) blk_load(fa.gb, p);
+      if (gblocks && dvalid) blk_load(fa.gb, p);
       // The error flag: the value read at the previous boundary raises the
       // abort flag, which every epilogue thread reads after the barrier below
       // (and acts on at the end of this transition), and this boundary's read
@@ -931,15 +936,37 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         for (int k = 0; k < 16; ++k) {
           const int i = cb * 16 + k;
           if (ok && valid(i) && ((accm >> i) & 1u)) {
-            if (xchg) a.g[elem(i)] = -accv[k];
+            if (xchg && !xblk) a.g[elem(i)] = -accv[k];
             p[i] = -accv[k];
           }
         }
       }
+      // the exchange step's row swaps when both rows are this thread's: the
+      // positions in the shared rows, the cached gradients in p, rescaled as
+      // the exchange kernel does (swapped pairs are disjoint: a row swapped
+      // as the upper one is never the lower one of another)
+      if (xblk) {
+#pragma unroll
+        for (int i = 0; i < kHalf - 1; ++i) {
+          if ((i & 15) == 15) continue;
+          const int r = rowi(i);
+          if (ok && valid(i) && swp_s[r]) {
+            float* x0 = &xs[r * 128 + dl];
+            const float xa = x0[0], xb = x0[128];
+            const float b0 = beta_s[r], b1 = beta_s[r + 1];
+            x0[0] = xb;
+            x0[128] = xa;
+            const float ga = p[i], gb = p[i + 1];
+            p[i] = gb / b1 * b0;
+            p[i + 1] = ga / b0 * b1;
+          }
+        }
+      }
       // the cached gradients: back to this thread's block, or, after the
-      // launch's last transition, to a.g (with the exchange step a.g is the
-      // cache throughout, and the exchange below reloads p)
-      if (!xchg && ok) {
+      // launch's last transition, to a.g (with the exchange step and a
+      // replica count not dividing 16, a.g is the cache throughout, and the
+      // exchange below reloads p)
+      if (gblocks && ok) {
         if (more) {
           if (dvalid) blk_store(fa.gb, p);
         } else {
@@ -957,7 +984,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         a.log_accept[chain] = lu_s[c];
         if (k_out >= 0 && fa.trace_acc) fa.trace_acc[k_out * C + chain] = static_cast<uint8_t>(acc);
       }
-      if (TEMPERED && fa.exchange) {
+      if (xchg && !xblk) {
         // swap the state rows of this CTA's dims: the owner of the lower row
         // of each swapped pair exchanges both rows (gradients rescaled as the
         // exchange kernel does), then the kept sample is written

@@ -115,15 +115,22 @@ def test_tempered_marginals_on_gpu(H):
     H.hmc_destroy(ctx)
 
 
+@pytest.mark.parametrize("K,C", [(4, 48), (32, 8)])
 @pytest.mark.parametrize("cap", [0, 1, 7])
-def test_replica_exchange_in_the_pair_launch_equals_step_by_step(H, cap):
+def test_replica_exchange_in_the_pair_launch_equals_step_by_step(H, cap, K, C):
     """sample_chain of a dense-Gaussian replica set runs the exchange step
     inside the CTA-pair launch (all transitions in one launch, one per launch,
     or launches of 7): the same kept states, final state and last swap flags
-    as hmc_step followed by the exchange kernel, transition by transition."""
+    as hmc_step followed by the exchange kernel, transition by transition.
+    With 4 replicas both rows of every swapped pair belong to one epilogue
+    thread (swapped in registers); with 32 a pair can straddle two threads
+    (swapped through the [C x D] gradient cache)."""
     from paper_2002_01184_gb300.sampler import _CudaArray
-    C, K, D, L, eps, B, Kk = 48, 4, 64, 5, 0.08, 6, 9
-    betas = (1.0 - np.sqrt(0.6 / D) * np.arange(K)).astype(np.float32)
+    D, L, eps, B, Kk = 64, 5, 0.08, 6, 9
+    if K == 4:
+        betas = (1.0 - np.sqrt(0.6 / D) * np.arange(K)).astype(np.float32)
+    else:
+        betas = (0.97 ** np.arange(K)).astype(np.float32)
     prob = workloads.corr_gauss(dim=D, num_chains=C * K)
     P = torch.as_tensor(prob.P).cuda()
     target = H.make_target("corr_gauss", D, P)
