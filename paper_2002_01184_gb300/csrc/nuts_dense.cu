@@ -640,8 +640,9 @@ k_nuts_gauss_loop(const __grid_constant__ CUtensorMap mAhi, const __grid_constan
         }
       }
     }
-    // ---- the products are in: every CTA's leaves may read them
-    __threadfence();
+    // ---- the products are in: every CTA's leaves may read them (the CTA
+    // barrier, then thread 0's fence in the grid barrier, publish every
+    // thread's stores, as a grid-wide sync does)
     __syncthreads();
     if (threadIdx.x == 0) {
       if (!pl_grid_barrier(bar, ++gen)) {
@@ -659,7 +660,6 @@ k_nuts_gauss_loop(const __grid_constant__ CUtensorMap mAhi, const __grid_constan
     // positions written for the next products' TMA loads (another proxy)
     asm volatile("fence.proxy.async.global;" ::: "memory");
     if (lane == 0 && mine) atomicAdd(&left[it & 1], static_cast<unsigned>(mine));
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
       if (!pl_grid_barrier(bar, ++gen)) {
