@@ -36,9 +36,9 @@ struct hmc_ctx {
   // device staging for hmc_sample_chain_host, grown on demand
   void* stage = nullptr;
   size_t stage_bytes = 0;
-  // hmc_sample_chain_host: kept samples leave on copy_stream, segment by
-  // segment, while the next segment's transitions run
-  cudaStream_t copy_stream = nullptr;
+  // hmc_sample_chain_host: kept samples leave on the copy streams, segment
+  // by segment, while the next segment's transitions run
+  cudaStream_t copy_stream[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t seg_ready = nullptr;
   cudaEvent_t copies_done = nullptr;
   std::vector<void*> allocations;
@@ -94,9 +94,13 @@ namespace {
 thread_local std::string g_global_err;
 
 // kept-sample segments of hmc_sample_chain_host: at least this many bytes
-// each, at most this many segments
+// each, at most this many segments; each segment's copy is split over this
+// many streams (a single device-to-host copy measured 32-100 GB/s on the
+// same workload, below what the link carries)
 constexpr size_t kSegmentBytes = 256ull << 20;
 constexpr int64_t kMaxSegments = 16;
+constexpr int kCopyStreams = 4;
+static_assert(sizeof(hmc_ctx::copy_stream) / sizeof(cudaStream_t) == kCopyStreams, "copy streams");
 
 bool host_pinned(const void* p) {
   cudaPointerAttributes at{};
@@ -330,8 +334,10 @@ void release(hmc_ctx* ctx) {
   drop_graph(ctx);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   ctx->cap_stream = nullptr;
-  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
-  ctx->copy_stream = nullptr;
+  for (cudaStream_t& cs : ctx->copy_stream) {
+    if (cs) cudaStreamDestroy(cs);
+    cs = nullptr;
+  }
   if (ctx->nd.side) cudaStreamDestroy(ctx->nd.side);
   ctx->nd.side = nullptr;
   if (ctx->seg_ready) cudaEventDestroy(ctx->seg_ready);
@@ -998,7 +1004,8 @@ hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burni
     hmc_status st = run_chain(ctx, dx, num_burnin, num_results, ds, de, dacc);
     if (st != HMC_OK) return st;
   } else {
-    if (!ctx->copy_stream) e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+    for (int c = 0; c < kCopyStreams && e == cudaSuccess; ++c)
+      if (!ctx->copy_stream[c]) e = cudaStreamCreateWithFlags(&ctx->copy_stream[c], cudaStreamNonBlocking);
     if (e == cudaSuccess && !ctx->seg_ready) e = cudaEventCreateWithFlags(&ctx->seg_ready, cudaEventDisableTiming);
     if (e == cudaSuccess && !ctx->copies_done)
       e = cudaEventCreateWithFlags(&ctx->copies_done, cudaEventDisableTiming);
@@ -1010,15 +1017,22 @@ hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burni
       st = enqueue_range(ctx, dx, num_burnin, num_burnin + k0, num_burnin + k1, ds, de, dacc);
       if (st != HMC_OK) break;
       e = cudaEventRecord(ctx->seg_ready, s);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->seg_ready, 0);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(samples_out + k0 * CD, ds + k0 * CD, (k1 - k0) * CD * sizeof(float),
-                            cudaMemcpyDeviceToHost, ctx->copy_stream);
+      // the segment's bytes in kCopyStreams contiguous pieces, one per stream
+      const size_t seg0 = static_cast<size_t>(k0) * CD, seg_n = static_cast<size_t>(k1 - k0) * CD;
+      for (int c = 0; c < kCopyStreams && e == cudaSuccess; ++c) {
+        const size_t a0 = seg0 + seg_n * c / kCopyStreams, a1 = seg0 + seg_n * (c + 1) / kCopyStreams;
+        e = cudaStreamWaitEvent(ctx->copy_stream[c], ctx->seg_ready, 0);
+        if (e == cudaSuccess && a1 > a0)
+          e = cudaMemcpyAsync(samples_out + a0, ds + a0, (a1 - a0) * sizeof(float), cudaMemcpyDeviceToHost,
+                              ctx->copy_stream[c]);
+      }
       if (e != cudaSuccess) return cuda_fail(ctx, e, "sample download");
     }
     if (st != HMC_OK) return st;
-    e = cudaEventRecord(ctx->copies_done, ctx->copy_stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->copies_done, 0);
+    for (int c = 0; c < kCopyStreams && e == cudaSuccess; ++c) {
+      e = cudaEventRecord(ctx->copies_done, ctx->copy_stream[c]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->copies_done, 0);
+    }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sample download");
   }
   e = cudaMemcpyAsync(x_inout, dx, CD * sizeof(float), cudaMemcpyDeviceToHost, s);
