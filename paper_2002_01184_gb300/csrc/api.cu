@@ -996,7 +996,7 @@ hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burni
   int64_t nseg = 1;
   // (not for NUTS: its fixed-step-size run is one launch whose length is its
   // slowest chain's, and each segment would pay that chain's tail again)
-  if (ds && K > 1 && ctx->K == 1 && ctx->cfg.proposal != HMC_PROPOSAL_NUTS &&
+  if (ds && K > 1 && ctx->cfg.proposal != HMC_PROPOSAL_NUTS &&
       sample_bytes >= 2 * kSegmentBytes && host_pinned(samples_out))
     nseg = std::min<int64_t>({kMaxSegments, static_cast<int64_t>(K),
                               static_cast<int64_t>(sample_bytes / kSegmentBytes)});

@@ -157,3 +157,35 @@ def test_replica_exchange_in_the_pair_launch_equals_step_by_step(H, cap, K, C):
     assert sw1.any()
     H.hmc_destroy(ctx1)
     H.hmc_destroy(ctx2)
+
+
+def test_replica_set_host_entry_point_segments_large_pinned_sample_sets(H):
+    """A replica set's kept samples (629 MB, bound for pinned host memory)
+    leave the device in segments while the later transitions, exchange step
+    included, run: the same samples, state and last swap flags as the device
+    entry point."""
+    from paper_2002_01184_gb300.sampler import _CudaArray
+    C, K, D, L, eps, B, Kk = 1024, 4, 256, 4, 0.3, 10, 150
+    betas = (1.0 - np.sqrt(0.6 / D) * np.arange(K)).astype(np.float32)
+    prob = workloads.corr_gauss(dim=D, num_chains=C * K)
+    P = torch.as_tensor(prob.P).cuda()
+    target = H.make_target("corr_gauss", D, P)
+    x0 = (np.random.default_rng(4).standard_normal((C * K, D)) /
+          np.sqrt(np.tile(betas, C))[:, None]).astype(np.float32)
+    ctx = H.hmc_remc_create(target, C, betas, H.make_config(L, eps, seed=6))
+    x = torch.as_tensor(x0).cuda().contiguous()
+    samples = torch.empty((Kk, C * K, D), dtype=torch.float32, device="cuda")
+    H.hmc_sample_chain(ctx, x, B, Kk, samples, None, None)
+    ref_s, ref_x = host(samples), host(x)
+    ref_sw = host(torch.as_tensor(_CudaArray(H.hmc_remc_swaps(ctx), (C, K - 1), "|u1"), device="cuda")).copy()
+    del samples
+    xh = torch.from_numpy(x0.copy()).pin_memory()
+    sh = torch.empty((Kk, C * K, D), dtype=torch.float32, pin_memory=True)
+    H.hmc_sample_chain_host(ctx, xh, B, Kk, sh, None, None)
+    sw = host(torch.as_tensor(_CudaArray(H.hmc_remc_swaps(ctx), (C, K - 1), "|u1"), device="cuda"))
+    np.testing.assert_array_equal(sh.numpy(), ref_s)
+    np.testing.assert_array_equal(xh.numpy(), ref_x)
+    np.testing.assert_array_equal(sw, ref_sw)
+    assert ref_sw.any()
+    H.hmc_destroy(ctx)
+
