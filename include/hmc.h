@@ -249,8 +249,9 @@ hmc_status hmc_sample_chain_streaming_ess(hmc_ctx* ctx, float* x_inout, int64_t 
  * to the device, samples, copies the results back and synchronises the
  * context's stream before returning.  When samples_out is pinned and holds
  * at least 512 MiB, the kept samples are copied back in segments (at most
- * 16, each at least 256 MiB) on a second stream while the later transitions
- * run (except under NUTS); the results are the same. */
+ * 16, each at least 256 MiB, each split over four copy streams) while the
+ * later transitions run (replica sets included; not under NUTS); the
+ * results are the same. */
 hmc_status hmc_sample_chain_host(hmc_ctx* ctx, float* x_inout, int64_t num_burnin,
                                  int64_t num_results, float* samples_out,
                                  float* trace_step_size, uint8_t* trace_accept);
