@@ -301,6 +301,212 @@ k_gauss_tc_step(const __grid_constant__ CUtensorMap mAhi, const __grid_constant_
   }
 }
 
+// Z = Theta X^T with the residual epilogue as one persistent launch (the
+// leapfrog steps of HMC; NUTS, which skips tiles whose chains have finished,
+// keeps k_gauss_tc_step).  One CTA per SM takes tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... of 128 chains x 64 data rows; the TMA ring runs
+// on across its tiles and the accumulator is double-buffered in tensor
+// memory, so the MMAs of one tile run while the epilogue turns the previous
+// tile's Z into R.  The four warps of a tensor-memory lane quarter each
+// compute 16 columns of its 32 rows, stage them in the quarter's shared
+// rows, meet, and store 8 whole rows each (128-byte stores).  (One tile per
+// CTA left each CTA's ring fill, MMAs and epilogue in sequence; a persistent
+// form whose threads stored their own row's columns was bound by those
+// scattered stores.)
+constexpr int kZpStages = 3;
+constexpr int kZpBN = 64;                               // data rows per tile
+constexpr uint32_t kZpABytes = kBM * kBK * 4;          // 16 KB: 128 chains x 32 dims
+constexpr uint32_t kZpBBytes = kZpBN * kBK * 4;        // 8 KB: 64 data rows x 32 dims
+constexpr uint32_t kZpStage = 2 * kZpABytes + 2 * kZpBBytes;
+constexpr int kZpLd = kZpBN + 1;                       // staged row stride (floats)
+constexpr uint32_t kZpStgBytes = 4 * 2 * 32 * kZpLd * 4;   // [quarter][hi, lo][32 rows][kZpLd]
+// ring, staging, log-likelihood partials [4 column groups][128 rows],
+// barriers and tensor-memory slot, alignment slack
+constexpr size_t kZpSmem = kZpStages * kZpStage + kZpStgBytes + 4 * kBM * 4 + 256 + 1024;
+static_assert(kZpSmem <= 227 * 1024, "shared memory");
+static_assert(8 * (2 * kZpStages + 4) + 16 <= 256, "barriers");
+static_assert(kEpiWarps == 16 && kZpBN == 4 * 16, "four column groups of 16 per lane quarter");
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_lr_z_persist(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+               const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+               TcStepArgs a, int mt, int ntiles) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  float* stg = reinterpret_cast<float*>(smem + kZpStages * kZpStage);           // staging
+  float* lps = stg + kZpStgBytes / 4;                                          // [4][kBM]
+  uint64_t* full = reinterpret_cast<uint64_t*>(lps + 4 * kBM);
+  uint64_t* empty = full + kZpStages;
+  uint64_t* acc_full = empty + kZpStages;      // [2]
+  uint64_t* acc_empty = acc_full + 2;          // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = (a.K + kBK - 1) / kBK;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kZpStages; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&acc_full[b], 1);
+      ptx::mbar_init(&acc_empty[b], 32 * kEpiWarps);
+    }
+    ptx::fence_mbar_init();
+    ptx::prefetch_tensormap(&mAhi);
+    ptx::prefetch_tensormap(&mAlo);
+    ptx::prefetch_tensormap(&mBhi);
+    ptx::prefetch_tensormap(&mBlo);
+  }
+  if (warp == 0) {
+    ptx::tmem_alloc(tmem_slot, 2 * kZpBN);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // tile t: chains (t % mt) 128, data rows (t / mt) 64
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer: one ring across all of this CTA's tiles
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int m0 = (t % mt) * kBM, n0 = (t / mt) * kZpBN;
+      for (int kc = 0; kc < nk; ++kc, ++it) {
+        const int s = it % kZpStages, round = it / kZpStages;
+        if (it >= kZpStages && !ptx::mbar_wait(&empty[s], (round - 1) & 1)) {
+          atomicExch(a.err, 1);
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + s * kZpStage;
+        ptx::mbar_arrive_expect_tx(&full[s], kZpStage);
+        const int kx = kc * kBK;
+        ptx::tma_load_2d(st, &mAhi, &full[s], kx, m0);
+        ptx::tma_load_2d(st + kZpABytes, &mAlo, &full[s], kx, m0);
+        ptx::tma_load_2d(st + 2 * kZpABytes, &mBhi, &full[s], kx, n0);
+        ptx::tma_load_2d(st + 2 * kZpABytes + kZpBBytes, &mBlo, &full[s], kx, n0);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: tile k into accumulator buffer k % 2, once the
+    // epilogue has read that buffer's previous tile
+    constexpr uint32_t idesc = ptx::idesc_tf32(kBM, kZpBN);
+    int it = 0, k = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++k) {
+      const int b = k & 1;
+      if (k >= 2 && !ptx::mbar_wait(&acc_empty[b], ((k >> 1) - 1) & 1)) {
+        atomicExch(a.err, 1);
+        break;
+      }
+      ptx::tc_fence_after();
+      const uint32_t acc = tmem + static_cast<uint32_t>(kZpBN * b);
+      for (int kc = 0; kc < nk; ++kc, ++it) {
+        const int s = it % kZpStages, round = it / kZpStages;
+        if (!ptx::mbar_wait(&full[s], round & 1)) {
+          atomicExch(a.err, 1);
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t st = ptx::smem_u32(smem + s * kZpStage);
+#pragma unroll
+        for (int j = 0; j < kBK / 8; ++j) {
+          const uint64_t a_hi = ptx::sw128_kmajor_desc(st + 32 * j);
+          const uint64_t a_lo = ptx::sw128_kmajor_desc(st + kZpABytes + 32 * j);
+          const uint64_t b_hi = ptx::sw128_kmajor_desc(st + 2 * kZpABytes + 32 * j);
+          const uint64_t b_lo = ptx::sw128_kmajor_desc(st + 2 * kZpABytes + kZpBBytes + 32 * j);
+          ptx::mma_tf32(acc, a_lo, b_hi, idesc, (kc | j) != 0 ? 1u : 0u);
+          ptx::mma_tf32(acc, a_hi, b_lo, idesc, 1u);
+          ptx::mma_tf32(acc, a_hi, b_hi, idesc, 1u);
+        }
+        ptx::mma_commit(&empty[s]);
+      }
+      if (ok) ptx::mma_commit(&acc_full[b]);
+    }
+  } else if (warp >= 2) {
+    // ---- epilogue: warp (quarter q, column group cg) computes columns
+    // 16 cg .. 16 cg + 15 of rows 32 q .. 32 q + 31 (thread = row), stages
+    // them, and after the quarter's barrier stores rows 8 cg .. 8 cg + 7
+    // whole (two 128-byte stores per row and array)
+    const int quarter = warp & 3, cg = (warp - 2) >> 2;
+    float* qh = stg + quarter * 2 * 32 * kZpLd;      // the quarter's staged R head
+    float* ql = qh + 32 * kZpLd;                      // and remainder
+    const uint32_t qbar = 2u + static_cast<uint32_t>(quarter);   // named barrier of the quarter's 4 warps
+    bool bad = false;              // a wait gave up: later tiles skip their waits and stores
+    int k = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+      const int b = k & 1;
+      const int m0 = (t % mt) * kBM, n0 = (t / mt) * kZpBN, n = n0 + 16 * cg;
+      const int m = m0 + quarter * 32 + lane;
+      if (!bad && !ptx::mbar_wait(&acc_full[b], (k >> 1) & 1)) {
+        atomicExch(a.err, 1);
+        bad = true;
+      }
+      ptx::tc_fence_after();
+      float v[16];
+      ptx::tmem_ld16(tmem + static_cast<uint32_t>(kZpBN * b + 16 * cg) + (static_cast<uint32_t>(quarter * 32) << 16),
+                     v);
+      ptx::tc_fence_before();
+      ptx::mbar_arrive_local(&acc_empty[b]);
+      // R = y - sigmoid(Z) for the 16 columns (labels the same for every lane)
+      float yv[16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 u = reinterpret_cast<const float4*>(a.y + n)[q];
+        yv[4 * q] = u.x; yv[4 * q + 1] = u.y; yv[4 * q + 2] = u.z; yv[4 * q + 3] = u.w;
+      }
+      float part = 0.f;
+      // the quarter's staged rows of the previous tile are stored: restage
+      if (k > 0) asm volatile("bar.sync %0, 128;" ::"r"(qbar) : "memory");
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        float res = 0.f;
+        if (n + j < a.nvalid) {
+          res = residual_f(yv[j], v[j]);
+          if (a.last) part += loglik_f(yv[j], v[j]);
+        }
+        float hi, lo;
+        split_tf32(res, hi, lo);
+        qh[lane * kZpLd + 16 * cg + j] = hi;
+        ql[lane * kZpLd + 16 * cg + j] = lo;
+      }
+      if (a.last) lps[cg * kBM + quarter * 32 + lane] = part;
+      asm volatile("bar.sync %0, 128;" ::"r"(qbar) : "memory");
+      if (!bad) {
+        // rows 8 cg .. 8 cg + 7 of the quarter, lanes along the columns
+#pragma unroll 2
+        for (int rr = 8 * cg; rr < 8 * cg + 8; ++rr) {
+          const int mr = m0 + quarter * 32 + rr;
+          if (mr >= a.C) continue;                    // warp-uniform
+          float* oh = a.rhi + static_cast<int64_t>(mr) * a.ldr + n0;
+          float* ol = a.rlo + static_cast<int64_t>(mr) * a.ldr + n0;
+          oh[lane] = qh[rr * kZpLd + lane];
+          oh[lane + 32] = qh[rr * kZpLd + lane + 32];
+          ol[lane] = ql[rr * kZpLd + lane];
+          ol[lane + 32] = ql[rr * kZpLd + lane + 32];
+        }
+        // the rows' log-likelihood terms: the four column groups in order
+        if (a.last && cg == 0 && m < a.C) {
+          const float* l = lps + quarter * 32 + lane;
+          a.lp_part[static_cast<int64_t>(m) * a.ntn + a.lp_col0 + t / mt] =
+              ((l[0] + l[kBM]) + l[2 * kBM]) + l[3 * kBM];
+        }
+      }
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, 2 * kZpBN);
+  }
+}
+
 constexpr int kWarpsPerBlock = 8;
 
 struct TcBeginAccept {
@@ -777,9 +983,13 @@ cudaError_t logreg_gemm_setup(LogregGemm* g, const hmc_target& t, int64_t C, voi
   for (int i = 0; i < 2 && ok; ++i)
     ok = make_map(&g->mThi[i], g->xhi[i], C, ld, kBM) && make_map(&g->mTlo[i], g->xlo[i], C, ld, kBM);
   if (!ok) return cudaErrorInvalidValue;
+  static_assert(kZpBN == 64, "the data tensor maps' box is 64 rows (lr_tiles)");
   cudaError_t e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiLrResid, 64, 2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(Tile<64, 2>::kSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_lr_z_persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kZpSmem));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_gauss_tc_step<kEpiStore, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(Tile<64>::kSmem));
@@ -862,8 +1072,11 @@ cudaError_t launch_logreg_gemm_transition(const StepArgs& a, LogregGemm& g, cuda
     st.da = a.da;
     st.err = g.err;
     if (timer) timer->begin(s);
-    k_gauss_tc_step<kEpiLrResid, 64, 2><<<dim3(mt, g.nrt), kThreads, Tile<64, 2>::kSmem, s>>>(
-        g.mThi[in], g.mTlo[in], g.mXhi, g.mXlo, z);
+    {
+      const int zt = static_cast<int>(mt) * g.nrt;      // Z tiles, one persistent CTA per SM
+      k_lr_z_persist<<<static_cast<unsigned>(std::min(zt, g.sms)), kThreads, kZpSmem, s>>>(
+          g.mThi[in], g.mTlo[in], g.mXhi, g.mXlo, z, static_cast<int>(mt), zt);
+    }
     {
       // the split products G = R X, then their sum with the prior and the
       // leapfrog update (k_lr_gemm_update)
