@@ -39,12 +39,14 @@
 //     peer half needs the copy plus the forward, a quarter-step of MMAs later.
 //   * The momenta of the next transition are drawn while the epilogue waits
 //     for the MMAs (counter-based, so the draw order is free) and parked in
-//     global memory.
-// H_L, the Metropolis-Hastings decision and the dual-averaging partial are
-// formed by the leader from both CTAs' partial sums.  With T > 1 the launch
-// is cooperative: after every transition that adapts the step size (and
-// after the last one) all CTAs meet at a grid barrier and each applies the
-// same dual-averaging update to its own copy of the state; a launch of one
+//     global memory, in per-thread float4 blocks; the cached gradients of
+//     the launch live in such blocks too.
+// Both CTAs form H_L and decide every chain of the pair from their two
+// partial sums; each CTA writes its kept sample as one tensor store.  With
+// T > 1 the launch is cooperative: after every transition that adapts the
+// step size (and after the last one) all CTAs meet at a grid barrier that
+// also sums the fixed-point acceptance statistic, and each applies the same
+// dual-averaging update to its own copy of the state; a launch of one
 // transition instead lets its last CTA update the state.
 #include <cuda.h>
 
