@@ -84,9 +84,11 @@ constexpr uint32_t kStateBytes = kPairChains * 128 * 4;   // current positions, 
 // barriers (8), tmem slot, red [3][4][64], red_pair [3][64], peer_in [3][64],
 // acc_flag [64], prob_s [64], DA state copy, flags, DA coefficients, pair
 // sum, inverse temperatures [64], tempered log p after the decision [64],
-// exchange flags [64], log u [64], current log p [64]
+// exchange flags [64], log u [64], current log p [64], |p0|^2 partials
+// [2 transition parities][4 quarters][64]
 constexpr uint32_t kSmall =
-    8 * 8 + 16 + (3 * 4 * 64 + 3 * 64 + 3 * 64 + 64 + 64) * 4 + 128 + 16 + 32 + 16 + 5 * 64 * 4;
+    8 * 8 + 16 + (3 * 4 * 64 + 3 * 64 + 3 * 64 + 64 + 64) * 4 + 128 + 16 + 32 + 16 + 5 * 64 * 4 +
+    2 * 4 * 64 * 4;
 constexpr size_t kSmemUsed = kBBytes + kABytes + 2 * kXferBytes + kStateBytes + kSmall + 1024;
 // Above half of an SM's shared memory, so that one CTA runs per SM: a CTA
 // allocates all 512 tensor-memory columns and must never queue in
@@ -327,6 +329,7 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
   int* swp_s = reinterpret_cast<int*>(lpn_s + 64);        // [64] exchange: row r and r + 1 swap
   float* lu_s = reinterpret_cast<float*>(swp_s + 64);     // [64] log u of this transition's accept test
   float* lpc_s = lu_s + 64;                               // [64] log p of the chains' current state
+  float* kin_s = lpc_s + 64;                              // [2][4][64] |p0|^2 of transition t at t % 2
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = ptx::cluster_rank();              // 0: leader, 1: peer
@@ -666,7 +669,14 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
         const int item = dk + 6 * n;
         const int tw = 2 + (item >> 3), g = item & 7;          // warp whose slots, slot group
         const int tq = tw & 3, tsub = (tw - 2) >> 2;
-        if (static_cast<int>(rank) * 128 + tq * 32 >= D) continue;   // warp-uniform: no dims
+        if (static_cast<int>(rank) * 128 + tq * 32 >= D) {   // warp-uniform: no dims, no momenta,
+          if (lane < 4) {                                     // and zero |p0|^2 partials
+            const int i = 4 * g + lane;
+            const int row = (i < 16 ? static_cast<int>(peer) : static_cast<int>(rank)) * kHalf + tsub * 16 + (i & 15);
+            kin_s[((tn & 1u) * 4 + static_cast<uint32_t>(tq)) * 64 + row] = 0.f;
+          }
+          continue;
+        }
         const int dt = static_cast<int>(rank) * 128 + tq * 32 + lane;
         const bool dv = dt < D;
         const int rp = pair_base + static_cast<int>(peer) * kHalf + tsub * 16;
@@ -679,6 +689,25 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
           const int64_t b4 = (static_cast<int64_t>(blockIdx.x >> 1) * 2 + tsub) * 8 * D + dt;
           reinterpret_cast<float4*>(fa.p0next + (tn & 1u) * fa.p0_slot)[b4 + static_cast<int64_t>(g) * D] =
               make_float4(v[0], v[1], v[2], v[3]);
+        }
+        // the four chains' |p0|^2 over warp tw's 32 dims, for transition tn's
+        // decision: the xor butterfly pairs the lanes as the transpose
+        // reduction at the top of a transition does, so the sums agree bit
+        // for bit (each step adds two partial sums, and a + b == b + a)
+        float w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w[e] = dv ? v[e] * v[e] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) w[e] += __shfl_xor_sync(0xffffffffu, w[e], o);
+        if (lane == 0) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int i = 4 * g + e;
+            const int row = (i < 16 ? static_cast<int>(peer) : static_cast<int>(rank)) * kHalf + tsub * 16 + (i & 15);
+            kin_s[((tn & 1u) * 4 + static_cast<uint32_t>(tq)) * 64 + row] = w[e];
+          }
         }
       }
     };
@@ -736,12 +765,14 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
       const uint32_t t = a.t + static_cast<uint32_t>(j);
       const bool more = j + 1 < T;
       const float eps = persistent ? da_s->eps : a.da->eps;
-      // |p0|^2 partials of this warp's dims, one per chain
-      {
+      // |p0|^2 partials of this warp's dims, one per chain: for the launch's
+      // first transition here; later ones were summed by the warps that drew
+      // the momenta
+      if (j == 0) {
         float v[kHalf];
 #pragma unroll
         for (int i = 0; i < kHalf; ++i) v[i] = x[i] * x[i];
-        red[(2 * 4 + quarter) * 64 + rowi(lane)] = transpose_reduce32(v, lane);
+        kin_s[((t & 1u) * 4 + static_cast<uint32_t>(quarter)) * 64 + rowi(lane)] = transpose_reduce32(v, lane);
       }
       // begin: p = p0 + eps/2 g0, x1 = x0 + eps p (the peer's half first);
       // every position is loaded before the first tile store, whose memory
@@ -829,7 +860,8 @@ k_gauss_pair(const __grid_constant__ CUtensorMap mPhi, const __grid_constant__ C
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
           float sum = 0.f;
-          for (int q = 0; q < 4; ++q) sum += red[(v * 4 + q) * 64 + c];
+          const float* part = v < 2 ? red + v * 4 * 64 : kin_s + (t & 1u) * 4 * 64;
+          for (int q = 0; q < 4; ++q) sum += part[q * 64 + c];
           red_pair[v * 64 + c] = sum;
           ptx::st_async_f32(ptx::mapa(ptx::smem_u32(&peer_in[v * 64 + c]), peer), sum, bar);
         }
